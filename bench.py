@@ -1,0 +1,322 @@
+"""Benchmark: MLMC time-to-RMSE of the mixed-precision MPML estimator on one GB300.
+
+Workload (one "step"): the whole hot path of one adaptive MLMC estimate --
+Philox draws, tensor-core KL synthesis, every fine and coarse solve of every
+level in persistent launches (FP32 inner CG with a 16-bit-stored coefficient
+on coarse levels, FP64 iterative refinement to the per-level accuracy of
+Eq. (4.12)), QoI and level statistics, and the N_l updates of Alg. 4.1 --
+on the five-level hierarchy h = 1/16 .. 1/256 with a 64-term KL field
+(exponential covariance, sigma^2 = 1, correlation length 0.3), f = 1,
+Q = int u, N_init = 100 on every level, target RMSE 1e-3.
+
+value    = seconds per estimate (device time between CUDA events on the stream).
+e2e      = the same through the C ABI from host data: context creation (basis
+           tables built on the host and uploaded), estimate, result to host.
+roofline = the persistent solve kernel: algorithmic bytes / event time, against
+           the measured HBM copy bandwidth.
+cpu_baseline / --impl reference = the CPU FP64 oracle on a bounded sample of
+           the same workload, extrapolated to the estimate's sample counts.
+"""
+import argparse
+import json
+import os
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "MLMC time-to-RMSE (s) & solved DOF/s: mixed vs FP64 on 1 GB300; HBM GB/s"
+WORKLOAD = dict(n0=16, m=2, L_max=4, kind=0, K=64, sigma2=1.0, corr_len=0.3, q=2.0, qoi=0, f=1.0)
+TOL, N_INIT = 1e-3, 100
+L2_FLUSH_BYTES = 512 << 20
+
+
+def workload_desc():
+    return ("mixed-precision batched MLMC: 5 levels h=1/16..1/256, KL 64 terms (exp. covariance sigma^2=1, "
+            "corr length 0.3), f=1, Q=int u; FP32 inner CG (FP16-stored coefficient while delta_l>=1e-4) with "
+            "FP64 iterative refinement to delta_l of Eq. (4.12), k_p=0.05; N_init=100 per level, N_l from the "
+            "optimal formula for RMSE 1e-3")
+
+
+def peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(path) as fh:
+            d = json.load(fh)
+        return float(d["hbm_gbs"]), float(d["bf16_tflops"]), "measured"
+    except Exception:
+        return 6800.0, 1900.0, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled every 200 ms during the timed region."""
+
+    def __init__(self, index):
+        self.index, self.rows, self.proc = index, [], None
+
+    def __enter__(self):
+        q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.index), "--query-gpu=" + q,
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except Exception:
+            self.proc = None
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.rows.append([c.strip() for c in line.split(",")])
+
+    def __exit__(self, *a):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+
+    def summary(self):
+        sm = [float(r[1]) for r in self.rows if len(r) >= 9 and r[1].replace(".", "").isdigit()]
+        mx = [float(r[2]) for r in self.rows if len(r) >= 9 and r[2].replace(".", "").isdigit()]
+        reasons = set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for r in self.rows:
+            if len(r) >= 9:
+                for nm, v in zip(names, r[5:9]):
+                    if v.lower() == "active":
+                        reasons.add(nm)
+        sm.sort()
+        return {"sm_mhz": sm[len(sm) // 2] if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+# ---------------------------------------------------------------------------
+# CPU oracle on a bounded sample (only the cpu_baseline leg and --impl reference run this)
+def _oracle_level_job(args):
+    level, first, count = args
+    sys.path.insert(0, ROOT)
+    from oracle import mlmc as o_mlmc
+    P = o_mlmc.Problem(n0=WORKLOAD["n0"], m=WORKLOAD["m"], L_max=WORKLOAD["L_max"], field_kind=WORKLOAD["kind"],
+                       K=WORKLOAD["K"], sigma2=WORKLOAD["sigma2"], corr_len=WORKLOAD["corr_len"], seed=0)
+    t0 = time.perf_counter()
+    Qf, Qc = P.level_samples(level, first, count)
+    return level, time.perf_counter() - t0, list(Qf - Qc)
+
+
+def oracle_throughput(per_level, procs):
+    """Samples/s per level of the oracle with `procs` worker processes (spawn)."""
+    import multiprocessing as mp
+    ctx = mp.get_context("spawn")
+    out = {}
+    with ctx.Pool(procs) as pool:
+        pool.map(_oracle_level_job, [(0, 0, 1)] * procs)   # warm the workers (imports, basis tables)
+        for level, count in per_level.items():
+            jobs = [(level, 10_000 + i * count, count) for i in range(procs)]
+            t0 = time.perf_counter()
+            res = pool.map(_oracle_level_job, jobs)
+            wall = time.perf_counter() - t0
+            Y = [y for r in res for y in r[2]]
+            out[level] = {"samples_per_s": procs * count / wall, "Y": Y}
+    return out
+
+
+def cpu_extrapolated_seconds(N, procs, per_level=None):
+    per_level = per_level or {0: 8, 1: 4, 2: 2, 3: 1, 4: 1}
+    thr = oracle_throughput(per_level, procs)
+    secs = sum(N[l] / thr[l]["samples_per_s"] for l in range(len(N)))
+    sample = "; ".join("level %d: %d samples" % (l, procs * per_level[l]) for l in sorted(per_level))
+    return secs, sample, thr
+
+
+# ---------------------------------------------------------------------------
+def run_reference(args):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return 0
+    import math
+    procs = min(16, os.cpu_count() or 1)
+    # pilot of the oracle itself: variances for the N_l formula (fixed 5-level hierarchy)
+    pilot = oracle_throughput({0: 8, 1: 4, 2: 2, 3: 1, 4: 1}, procs)
+    V = []
+    for l in range(5):
+        Y = pilot[l]["Y"]
+        mu = sum(Y) / len(Y)
+        V.append(sum((y - mu) ** 2 for y in Y) / len(Y))
+    C = [4.0 ** l for l in range(5)]
+    s = sum(math.sqrt(v * c) for v, c in zip(V, C))
+    N = [max(N_INIT, int(math.ceil(math.sqrt(v / c) * 2.0 / TOL ** 2 * s))) for v, c in zip(V, C)]
+    times = []
+    for it in range(args.warmup + args.steps):
+        secs, sample, _ = cpu_extrapolated_seconds(N, procs)
+        if it >= args.warmup:
+            times.append(secs)
+    val = sum(times) / len(times)
+    line = {"metric": METRIC, "value": val, "unit": "s", "n_gpus": args.gpus, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": val * 1e3, "higher_is_better": False, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64", "data": "synthetic", "impl": "reference",
+            "config": {"workload": workload_desc(), "N_l": N},
+            "cpu_baseline": {"value": val, "unit": "s", "cores": procs, "kind": "oracle",
+                             "sample": "per step: " + sample + " (banded-Cholesky FP64 solves, fine+coarse), "
+                                       "extrapolated to N_l from an oracle pilot"},
+            "e2e": {"value": val, "unit": "s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line))
+    return 0
+
+
+# ---------------------------------------------------------------------------
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="libmlmc", choices=["libmlmc", "reference"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-fp64", action="store_true")
+    args = ap.parse_args()
+    if args.impl == "reference":
+        return run_reference(args)
+
+    import torch
+    import __graft_entry__
+    __graft_entry__.build()
+    import paper_2503_05533_gb300 as M
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    hbm_peak, _, peak_src = peaks()
+
+    def opts(form=M.MLMC_FORM_MIXED):
+        o = M.mlmc_default_options()
+        o.tol, o.L_start, o.N_init, o.form = TOL, WORKLOAD["L_max"], N_INIT, form
+        o.fixed_delta = 1e-10
+        return o
+
+    def problem(seed):
+        return M.make_problem(seed=seed, **WORKLOAD)
+
+    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
+    stream = torch.cuda.current_stream()
+
+    def timed_runs(form, steps, warmup, seed0, profile=False):
+        h = M.mlmc_create(problem(seed0), local)
+        try:
+            if profile:
+                M.mlmc_profile_enable(h, True)
+            for w in range(warmup):
+                M.mlmc_estimate(h, opts(form))
+            if profile:
+                M.mlmc_profile_reset(h)
+            torch.cuda.synchronize()
+            if dist:
+                dist.barrier()
+            torch.cuda.synchronize()
+            l0 = M.mlmc_launch_count()
+            ms, results = [], []
+            for s in range(steps):
+                flush.fill_(float(s))                      # L2 flush between timed steps (outside the events)
+                e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                e0.record(stream)
+                res = M.mlmc_estimate(h, opts(form))
+                e1.record(stream)
+                e1.synchronize()
+                ms.append(e0.elapsed_time(e1))
+                results.append(M.result_dict(res))
+            torch.cuda.synchronize()
+            if dist:
+                dist.barrier()
+            launches = M.mlmc_launch_count() - l0
+            prof = M.mlmc_profile_get(h) if profile else None
+        finally:
+            M.mlmc_destroy(h)
+        return ms, results, launches, prof
+
+    with ClockSampler(local) as clk:
+        ms, results, launches, prof = timed_runs(M.MLMC_FORM_MIXED, args.steps, args.warmup, 1000 + rank, True)
+    total_ms = sum(ms)
+    if dist:
+        t = torch.tensor([total_ms], dtype=torch.float64, device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        total_ms = t.item()
+    ms_per_step = total_ms / args.steps
+    dofs = sum(sum(r["dofs"]) for r in results) / len(results)
+    iters = [sum(r["inner_iters"]) for r in results]
+
+    # FP64 forms on the same workload and seeds (plain FP64 MLMC and FP64 with the adaptive delta_l)
+    fp64 = {}
+    if not args.no_fp64:
+        for name, form in (("fp64_fixed_1e-10", M.MLMC_FORM_FP64_FIXED), ("fp64_adaptive", M.MLMC_FORM_FP64_ADAPTIVE)):
+            fms, fres, _, _ = timed_runs(form, 1, 1, 1000 + rank)
+            fp64[name] = {"seconds": fms[0] / 1e3, "N_l": fres[0]["N"], "inner_iters": sum(fres[0]["inner_iters"]),
+                          "estimate": fres[0]["estimate"]}
+
+    # e2e through the C ABI from host data
+    e2e_s, h2d, d2h = [], 0, 0
+    for s in range(args.steps):
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        h = M.mlmc_create(problem(2000 + s), local)
+        res = M.mlmc_estimate(h, opts())
+        p = M.mlmc_profile_get(h)
+        M.mlmc_destroy(h)
+        torch.cuda.synchronize()
+        e2e_s.append(time.perf_counter() - t0)
+        h2d, d2h = p["h2d_bytes"], p["d2h_bytes"]
+
+    line = None
+    if rank == 0:
+        achieved = prof["solve_bytes"] / (prof["solve_ms"] * 1e-3) / 1e9 if prof["solve_ms"] > 0 else 0.0
+        kl_gbs = prof["kl_bytes"] / (prof["kl_ms"] * 1e-3) / 1e9 if prof["kl_ms"] > 0 else 0.0
+        kl_tf = prof["kl_flops"] / (prof["kl_ms"] * 1e-3) / 1e12 if prof["kl_ms"] > 0 else 0.0
+        step_s = ms_per_step / 1e3
+        line = {
+            "metric": METRIC, "value": step_s, "unit": "s", "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": False, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f32+f64", "data": "synthetic",
+            "config": {"workload": workload_desc(), "l2": "flushed between timed steps (512 MiB write)",
+                       "seed": "1000 + rank", "parallelism": "replicas" if world > 1 else "single GPU"},
+            "solved_dof_per_s": dofs / step_s,
+            "rmse": [r["rmse"] for r in results], "N_l": results[-1]["N"], "rounds": results[-1]["rounds"],
+            "inner_iters_per_step": sum(iters) / len(iters),
+            "fp64": fp64,
+            "roofline": {"bound": "hbm", "kernel": "persistent_solve", "achieved": achieved, "peak": hbm_peak,
+                         "unit": "GB/s", "frac": achieved / hbm_peak, "peak_source": peak_src + " (burst copy)",
+                         "traffic": None, "launches": prof["solve_launches"],
+                         "kernel_ms_per_step": prof["solve_ms"] / args.steps,
+                         "share_of_step": prof["solve_ms"] / total_ms if total_ms > 0 else None},
+            "kl_synthesis": {"achieved_gbs": kl_gbs, "tensor_tflops": kl_tf, "ms_per_step": prof["kl_ms"] / args.steps},
+            "e2e": {"value": sum(e2e_s) / len(e2e_s), "unit": "s", "h2d_bytes_per_step": h2d,
+                    "d2h_bytes_per_step": d2h},
+            "gpu_launches": launches,
+            "clocks": clk.summary(),
+        }
+    if dist:
+        dist.barrier()
+        dist.destroy_process_group()
+    if rank == 0:
+        if world == 1 and not args.no_cpu_baseline:
+            procs = min(16, os.cpu_count() or 1)
+            secs, sample, _ = cpu_extrapolated_seconds(results[-1]["N"], procs)
+            line["cpu_baseline"] = {"value": secs, "unit": "s", "cores": procs, "kind": "oracle",
+                                    "sample": sample + " (FP64 banded Cholesky, fine+coarse per sample), "
+                                              "extrapolated to the estimate's N_l"}
+        print(json.dumps(line))
+    return 0
+
+
+if __name__ == "__main__":
+    sys.exit(main())

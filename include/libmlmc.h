@@ -1,0 +1,328 @@
+/*
+ * libmlmc -- the data-parallel hot path of mixed-precision multilevel Monte
+ * Carlo (MPML) for -div(a grad u) = f on the unit square with a lognormal
+ * random coefficient, on one NVIDIA GB300 (sm_103a).
+ *
+ * Method: Martinek, Carson, Scheichl, "Exploiting Inexact Computations in
+ * Multilevel Monte Carlo and Other Sampling Methods", arXiv 2503.05533.
+ * Passages are cited as Sec./Eq./Alg. of that paper.
+ *
+ * Conventions shared by every entry point
+ * ---------------------------------------
+ *  - Grids.  A grid with n cells per side has (n+1)^2 nodes (x_i, y_j) =
+ *    (i/n, j/n); a nodal array stores node (i, j) at index j*(n+1) + i
+ *    ("dense nodal layout").  Batches of S grids are contiguous:
+ *    sample s starts at s*(n+1)^2.  Level l uses n_l = n0 * m^l.
+ *  - Memory.  Every array argument documented "device" is a device pointer
+ *    owned by the caller (e.g. allocated by PyTorch); the library never frees
+ *    it.  "host" arrays are ordinary host memory.  The context owns its own
+ *    workspaces (basis tables, solver scratch) and frees them in mlmc_destroy.
+ *  - Streams.  `stream` is a cudaStream_t passed as void* (NULL = legacy
+ *    default stream).  Calls enqueue work on it and return without
+ *    synchronising, except where a call says it synchronises.
+ *  - Errors.  Every call returns an mlmc_status and never aborts, traps or
+ *    exits.  On failure the context records a message, mlmc_last_error(ctx).
+ *    Device-side waits are bounded: a wait that runs out makes the call return
+ *    MLMC_E_TIMEOUT with the GPU still usable.
+ */
+#ifndef LIBMLMC_H
+#define LIBMLMC_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define MLMC_MAX_LEVELS 16
+
+typedef enum {
+    MLMC_OK = 0,
+    MLMC_E_ARG = 1,          /* invalid argument: null pointer, size out of range, bad enum */
+    MLMC_E_NOMEM = 2,        /* a device or host allocation failed */
+    MLMC_E_CUDA = 3,         /* a CUDA runtime call failed; text in mlmc_last_error */
+    MLMC_E_NOCONV = 4,       /* some solve stopped before its tolerance (see per-solve flags) */
+    MLMC_E_NONFINITE = 5,    /* a non-finite value appeared (coefficient overflow, NaN input) */
+    MLMC_E_TIMEOUT = 6,      /* a bounded device-side wait ran out; the kernel returned early */
+    MLMC_E_UNSUPPORTED = 7   /* a valid request this build does not implement */
+} mlmc_status;
+
+/* Arithmetic of a solve's inner (correction) solver and storage of its
+ * coefficient, Alg. 2.1 precisions (u_f, u_s) in Sec. 2.3.  The outer
+ * residual r = b - A x and the update x += d are always FP64 (u = u_r =
+ * double).  S = storage only: the coefficient is stored in 16 bits and
+ * widened to FP32 inside the stencil, all Krylov arithmetic being FP32. */
+typedef enum {
+    MLMC_FP64 = 0,    /* inner FP64, coefficient FP64 (plain double solve)       */
+    MLMC_FP32 = 1,    /* inner FP32, coefficient stored FP32                     */
+    MLMC_BF16S = 2,   /* inner FP32, coefficient stored bfloat16                 */
+    MLMC_FP16S = 3    /* inner FP32, coefficient stored IEEE half                */
+} mlmc_prec;
+
+typedef enum { MLMC_CG = 0, MLMC_MINRES = 1 } mlmc_solver;   /* Sec. 2.2 */
+
+/* per-solve flag bits (int32 arrays returned by the solves) */
+#define MLMC_F_CONVERGED 1   /* ||b - A x||_2 / ||b||_2 < delta reached (Eq. (2.1), C = 1) */
+#define MLMC_F_MAXIT     2   /* iteration budget exhausted before delta */
+#define MLMC_F_STAGNATED 4   /* an outer refinement step reduced the residual by less than 2x */
+#define MLMC_F_NONFINITE 8   /* NaN / Inf in the residual (e.g. coefficient overflow, Sec. 5.2) */
+
+/* Random log-coefficient, log a(x) = sum_{k<K} xi_k Phi_k(x), xi_k ~ N(0,1). */
+typedef struct {
+    int kind;          /* 0: separable exponential covariance sigma2 exp(-|dx1|/corr_len - |dx2|/corr_len)
+                          1: the paper's field, Sec. 5.1 Eq. (5.2): Phi_j = sigma j^-q sin(2 pi j x1) cos(2 pi j x2)
+                          2: one spatially constant mode, Phi_0 = sigma                                    */
+    int K;             /* number of terms, 1 <= K <= 256 (kind 2: K = 1)                                  */
+    double sigma2;     /* variance sigma^2 > 0                                                             */
+    double corr_len;   /* correlation length (kind 0), > 0                                                 */
+    double q;          /* decay exponent (kind 1)                                                          */
+} mlmc_field;
+
+/* The level hierarchy and QoI of Problem 4.5 (Sec. 4.3) and Sec. 5.1. */
+typedef struct {
+    int n0;            /* cells per side on level 0 (h_0 = 1/n0), 2 <= n0                                 */
+    int m;             /* refinement factor between levels, m >= 2 (h_l = h_0 m^-l)                        */
+    int L_max;         /* finest level that may be used, 0 <= L_max < MLMC_MAX_LEVELS, n0 m^L_max <= 2048  */
+    mlmc_field field;
+    int qoi;           /* 0: Q = int_D u_h ; 1: Q = int_B u_h over the box B below                         */
+    double box[4];     /* x0, x1, y0, y1 of B (sides on grid lines of level 0)                              */
+    double f;          /* constant right-hand side f (Sec. 5.1 uses f = 1)                                 */
+    uint64_t seed;     /* Philox key                                                                       */
+} mlmc_problem;
+
+typedef struct mlmc_ctx mlmc_ctx;
+
+/* Level accumulator for Y_l = Q_l - Q_{l-1} (Eq. (4.1)): count, Welford mean
+ * and sum of squared deviations (s_l^2 = m2 / n, Eq. (4.2)), and
+ * Kahan-compensated sums of Y and Y^2. */
+typedef struct {
+    int64_t n;
+    double mean, m2;
+    double sum, sum_c, sumsq, sumsq_c;
+} mlmc_acc;
+
+/* ------------------------------------------------------------------------- */
+/* Context                                                                    */
+
+/* Create a context on CUDA device `device`: validates `prob`, builds the KL
+ * basis tables for every level grid 0..L_max on the host and uploads them.
+ * *out is set to NULL on failure; the message is then in mlmc_last_error(NULL). */
+mlmc_status mlmc_create(const mlmc_problem* prob, int device, mlmc_ctx** out);
+void mlmc_destroy(mlmc_ctx* ctx);                 /* NULL is ignored */
+const char* mlmc_last_error(const mlmc_ctx* ctx); /* never NULL; "" when no error */
+const char* mlmc_version(void);
+int64_t mlmc_launch_count(void);                  /* kernels launched by this library so far (process) */
+
+/* ------------------------------------------------------------------------- */
+/* A1 + A2: random inputs and the coefficient field (Sec. 5.1, Eq. (5.2);
+ * independence of levels, Sec. 4.1).
+ *
+ * xi[s][k] = Phi^-1(u) with u from Philox4x32-10 (key = seed, counter =
+ * (sample lo, sample hi, level, k >> 1), words (0,1) for even k and (2,3) for
+ * odd k, u = (M + 1/2) 2^-52 for the 52-bit M = (w_a << 20) | (w_b >> 12)) and
+ * Wichura's AS241 inverse normal; sample indices are first .. first+S-1.
+ * a[s][v] = exp(sum_k xi[s][k] Phi_k(x_v)) on the (n_l+1)^2 nodes of level l.
+ *   xi    device FP64 [S][K], out (may be NULL when not wanted)
+ *   a     device [S][(n_l+1)^2] dense nodal layout, out; FP64 if field_prec ==
+ *         MLMC_FP64 (FP64 contraction and exp), else FP32 (tensor-core
+ *         contraction with split FP16 operands and FP32 accumulation, then exp)
+ * S = 0 is a no-op.  Errors: MLMC_E_ARG for level outside [0, L_max], S < 0,
+ * null a with S > 0, field_prec not FP64/FP32. */
+mlmc_status mlmc_sample_fields(mlmc_ctx* ctx, int level, uint64_t first, int S,
+                               double* xi, void* a, mlmc_prec field_prec, void* stream);
+
+/* A2 alone: the same field from caller-given coefficients xi (device FP64
+ * [S][K]) on the grid of level `level`.  Used by the gradient path. */
+mlmc_status mlmc_synthesize_fields(mlmc_ctx* ctx, int level, int S, const double* xi,
+                                   void* a, mlmc_prec field_prec, void* stream);
+
+/* ------------------------------------------------------------------------- */
+/* A3 + A4: the P1 stiffness operator applied matrix-free (Sec. 3.1; uniform
+ * grid, cells split along the SW-NE diagonal, a_T = mean of its vertex values,
+ * which makes A a 5-point operator).  y = A x on the (n-1)^2 interior nodes,
+ * y = 0 on boundary nodes; x's boundary values are ignored (Dirichlet u = 0).
+ *   a  device [S][(a_n+1)^2] nodal coefficient, FP64 (a_prec = MLMC_FP64) or
+ *      FP32 (MLMC_FP32); a_n = n or a multiple of n (the grid-n operator then
+ *      uses every (a_n/n)-th node: a coarse view of a fine field)
+ *   x, y  device [S][(n+1)^2], FP64 if vec_prec == MLMC_FP64 else FP32
+ *   op_prec  storage of the coefficient inside the operator (MLMC_FP64 needs
+ *      vec_prec FP64; FP32/BF16S/FP16S need vec_prec FP32)
+ * Errors: MLMC_E_ARG for n < 2, S < 0, a_n % n != 0, inconsistent precisions. */
+mlmc_status mlmc_apply_operator(int n, int S, const void* a, mlmc_prec a_prec, int a_n,
+                                mlmc_prec op_prec, const void* x, void* y, mlmc_prec vec_prec,
+                                void* stream);
+
+/* ------------------------------------------------------------------------- */
+/* A5 + A6 + A7: solve S independent systems A(a_s) x_s = b (b_i = f h^2) to
+ * relative residual delta (Eq. (2.1) with C = 1; accuracy choice Eq. (4.12))
+ * by iterative refinement (Alg. 2.1): r = b - A x in FP64 with the FP64
+ * operator of the master coefficient; stop when ||r|| / ||b|| < delta; else
+ * solve A d = r approximately with the inner Krylov method (CG or MINRES,
+ * Sec. 2.2) in precision `prec`, and x += d in FP64.  All S solves run in one
+ * persistent cooperative kernel.  Then Q_s = G(u_s) (Problem 4.5; the QoI of
+ * the context's problem).
+ *   n      cells per side of the solve grid, 2 <= n <= 2048
+ *   a      device master coefficient [S][(a_n+1)^2], FP64 or FP32 (a_prec)
+ *   a_n    grid of `a`: n, or a multiple of n (coarse member of a level pair)
+ *   delta  target relative residual, > 0
+ *   max_iters  inner-iteration budget per solve (summed over refinement steps)
+ *   u      device FP64 [S][(n+1)^2] solution (dense nodal, zero boundary) or NULL
+ *   Q      device FP64 [S] out
+ *   iters  device int32 [S] inner iterations, or NULL
+ *   relres device FP64 [S] final ||b - A x|| / ||b|| (FP64), or NULL
+ *   flags  device int32 [S] MLMC_F_* bits, or NULL
+ * Returns MLMC_OK when the kernel ran; per-solve failures are in `flags`.
+ * MLMC_E_TIMEOUT if a bounded grid barrier ran out.  Synchronises `stream`
+ * once, after the kernel, to read the kernel's error word. */
+mlmc_status mlmc_level_solve(mlmc_ctx* ctx, int n, int S, const void* a, mlmc_prec a_prec, int a_n,
+                             mlmc_prec prec, mlmc_solver solver, double delta, int max_iters,
+                             double* u, double* Q, int32_t* iters, double* relres, int32_t* flags,
+                             void* stream);
+
+/* ------------------------------------------------------------------------- */
+/* A8: level statistics.  Y_s = Qf[s] - Qc[s] (Qc NULL at level 0), Eq. (4.1);
+ * the batch's (n, mean, m2, Kahan sums) is computed on the device in a fixed
+ * order and merged into *acc (host) with Chan's pairwise update.
+ * Synchronises `stream`.  S = 0 leaves *acc unchanged. */
+mlmc_status mlmc_level_stats(mlmc_ctx* ctx, int S, const double* Qf, const double* Qc,
+                             mlmc_acc* acc, void* stream);
+
+/* Host-side Chan merge of two accumulators: *into <- *into (+) *other. */
+void mlmc_acc_merge(mlmc_acc* into, const mlmc_acc* other);
+
+/* ------------------------------------------------------------------------- */
+/* A9: the accuracy rule, Eq. (4.7): delta_l = (kp h_l^beta1)^(1/beta2) for
+ * l < L and delta_L = min((kp h_L^beta1)^(1/beta2), (kp h_L^alpha1)^(1/alpha2));
+ * for the P1 problem (alpha1, alpha2, beta1, beta2) = (2, 1, 4, 2), Eq. (4.12).
+ * prec[l] is this library's choice of inner precision for accuracy delta_l on
+ * grid h_l, from the conditions of Cor. 3.4 with kappa(A) ~ contrast h^-2
+ * (Lemma 3.3): FP64 when contrast h^-2 u_single > 0.5 (condition 1 fails
+ * for single); else FP16-stored coefficient (MLMC_FP16S) when delta_l >= 1e-4
+ * (a refinement step then contracts the residual by ~u_half, so at most two
+ * steps are needed); else FP32.  `contrast` <= 0 means 1.
+ *   h      host [L+1] mesh sizes, decreasing, > 0
+ *   delta  host [L+1] out;  prec host [L+1] out (may be NULL)
+ * Pure host code (no GPU). */
+mlmc_status mlmc_adapt_precision(int L, const double* h, double kp, double alpha1, double alpha2,
+                                 double beta1, double beta2, double contrast,
+                                 double* delta, mlmc_prec* prec);
+
+/* ------------------------------------------------------------------------- */
+/* A10 + A11: the estimate loop, Alg. 4.1, with every round's samples of all
+ * levels solved in one persistent launch. */
+typedef enum {
+    MLMC_FORM_MIXED = 0,          /* per-level accuracy delta_l (Eq. (4.12)), per-level inner precision  */
+    MLMC_FORM_FP64_ADAPTIVE = 1,  /* per-level delta_l, FP64 inner                                        */
+    MLMC_FORM_FP64_FIXED = 2      /* standard MLMC: fixed accuracy fixed_delta on all levels, FP64         */
+} mlmc_form;
+
+typedef struct {
+    double tol;            /* target RMSE TOL (variance budget TOL^2/2, bias test below)            */
+    int L_start;           /* finest level of the first round: 1 = Alg. 4.1; L_max = fixed hierarchy */
+    int N_init;            /* samples on a newly started level (Alg. 4.1, N_init), >= 2             */
+    double kp;             /* k_p of Eq. (4.7), in (0, 1); the paper uses 0.05                       */
+    double alpha1, alpha2, beta1, beta2;   /* rates of Lemma 4.6 (2, 1, 4, 2)                      */
+    double alpha;          /* bias rate in the bias test (2)                                         */
+    double gamma;          /* cost model C_l = m^(gamma l) (Alg. 4.1 "estimate C_l"), e.g. 2         */
+    double r;              /* bias-test constant: |Y_hat_L| <= (r m^alpha - 1) TOL / sqrt(2), r = 1    */
+    int form;              /* mlmc_form                                                              */
+    double fixed_delta;    /* accuracy of MLMC_FORM_FP64_FIXED (e.g. 1e-10)                          */
+    int force_prec;        /* -1: per-level rule of mlmc_adapt_precision; else an mlmc_prec for all  */
+    int solver;            /* mlmc_solver                                                            */
+    int max_iters;         /* inner-iteration budget per solve                                       */
+    int max_rounds;        /* safety cap on Alg. 4.1 rounds                                          */
+    const int64_t* fixed_N;/* non-NULL: no adaptivity, exactly fixed_N[l] samples on levels 0..L_start */
+    double contrast;       /* contrast estimate for the precision rule (<= 0: 1)                     */
+} mlmc_options;
+
+typedef struct {
+    double estimate;                 /* Q_hat = sum_l Y_hat_l (Eq. (4.1))                        */
+    double rmse;                     /* sqrt(bias^2 + sum_l s_l^2 / N_l), bias = |Y_hat_L|/(m^alpha-1) */
+    double var_est;                  /* sum_l s_l^2 / N_l                                          */
+    int L;                           /* finest level used                                         */
+    int rounds;                      /* Alg. 4.1 rounds                                           */
+    int bias_failed;                 /* bias test still failing at L_max                          */
+    int32_t flags_or;                /* OR of all per-solve flags                                 */
+    int64_t N[MLMC_MAX_LEVELS];      /* samples per level                                         */
+    double Yhat[MLMC_MAX_LEVELS];    /* level means                                               */
+    double s2[MLMC_MAX_LEVELS];      /* level variances (1/N normalisation, Eq. (4.2))            */
+    double delta[MLMC_MAX_LEVELS];   /* accuracy used per level (fine member)                     */
+    int32_t prec[MLMC_MAX_LEVELS];   /* inner precision used per level                            */
+    int64_t inner_iters[MLMC_MAX_LEVELS];   /* inner iterations summed over the level's solves    */
+    int64_t dofs[MLMC_MAX_LEVELS];   /* unknowns solved per level (fine + coarse members)         */
+    mlmc_acc acc[MLMC_MAX_LEVELS];   /* final level accumulators                                  */
+    double seconds;                  /* wall time of the call                                     */
+} mlmc_result;
+
+/* Fill *opts with the paper's defaults: kp 0.05, (2,1,4,2), alpha 2, gamma 2,
+ * r 1, N_init 100, L_start 1, mixed form, CG, fixed_delta 1e-10. */
+void mlmc_default_options(mlmc_options* opts);
+
+/* Run Alg. 4.1 on the GPU; synchronises; results in *res (host). */
+mlmc_status mlmc_estimate(mlmc_ctx* ctx, const mlmc_options* opts, mlmc_result* res);
+
+/* The same host loop with a caller-supplied level sampler instead of the GPU
+ * (for testing the loop without a GPU).  sampler(user, level, first, count,
+ * delta[L+1], Y[count]) fills Y with count samples of Y_level and returns 0
+ * (non-zero aborts with MLMC_E_ARG).  The cost model is m^(gamma l). */
+typedef int (*mlmc_sampler_fn)(void* user, int level, int64_t first, int count,
+                               const double* delta, double* Y);
+mlmc_status mlmc_estimate_host(int m, int L_max, int n0, const mlmc_options* opts,
+                               mlmc_sampler_fn sampler, void* user, mlmc_result* res);
+
+/* ------------------------------------------------------------------------- */
+/* A12: dQ/dxi for S samples on level grid `level` (QoI of the context).
+ * Field from xi (device FP64 [S][K]); the forward solve A x = b and the
+ * adjoint solve A lambda = g (g_i = G(phi_i)) run together in one persistent
+ * launch, to accuracy delta in precision prec; then
+ * G_v = -(1/3) sum_{T contains v} |T| grad(lambda_h).grad(u_h)|_T and
+ * dQ/dxi[s][k] = sum_v Phi_k(x_v) a_v G_v (the transposed KL contraction).
+ * u is recomputed here rather than kept from an earlier forward pass (the
+ * autograd wrapper's forward stores only Q).  The field is FP64 when
+ * prec == MLMC_FP64, else FP32 from the tensor-core synthesis.
+ *   Q      device FP64 [S] out;  dQdxi  device FP64 [S][K] out
+ * Synchronises `stream` (inside the solve). */
+mlmc_status mlmc_adjoint_grad(mlmc_ctx* ctx, int level, int S, const double* xi, mlmc_prec prec,
+                              double delta, int max_iters, double* Q, double* dQdxi, void* stream);
+
+/* ------------------------------------------------------------------------- */
+/* Diagnostics.  Timeout of every bounded device-side wait of this context, in
+ * seconds (default 10).  Used to test the MLMC_E_TIMEOUT path. */
+mlmc_status mlmc_set_wait_timeout(mlmc_ctx* ctx, double seconds);
+
+/* Measurement.  With profiling on, the context records CUDA events on the
+ * launching stream around every persistent solve and tensor-core synthesis
+ * launch and, after each solve, derives the launch's algorithmic bytes from
+ * the per-system inner-iteration and refinement counts:
+ *   per unknown and inner iteration 8 p_v + 2 p_s bytes (p_v vector bytes,
+ *   p_s coefficient storage bytes), per unknown and refinement step
+ *   (residual + update) 44 + 3 p_v + p_m bytes (p_m master coefficient bytes),
+ *   plus 8 + p_m + p_s bytes per unknown for set-up and the QoI.
+ * The synthesis counts its FP32 output (4 bytes per node and sample) plus one
+ * read of both split operands, and 3 x 2 S_pad K_pad N_pad executed tensor
+ * FLOPs (three MMAs per split product).  Event times are resolved lazily. */
+typedef struct {
+    int64_t solve_launches;
+    double solve_ms;           /* summed event time of the persistent solve launches */
+    double solve_bytes;        /* their algorithmic bytes */
+    int64_t inner_iters;       /* inner iterations summed over systems */
+    int64_t unknown_iters;     /* sum over systems of interior unknowns x inner iterations */
+    int64_t kl_launches;
+    double kl_ms, kl_bytes, kl_flops;
+    int64_t h2d_bytes, d2h_bytes;  /* host<->device bytes moved by this context's calls */
+} mlmc_profile;
+mlmc_status mlmc_profile_enable(mlmc_ctx* ctx, int on);
+mlmc_status mlmc_profile_get(mlmc_ctx* ctx, mlmc_profile* out);   /* synchronises the device */
+mlmc_status mlmc_profile_reset(mlmc_ctx* ctx);
+
+/* Diagnostics.  Make every grid barrier of this context's persistent solves
+ * also wait for `extra` CTAs that are never launched (extra = 0 restores
+ * normal operation), so that every such wait runs out after the timeout.
+ * Exists only to test that an expired wait returns MLMC_E_TIMEOUT and leaves
+ * the GPU usable. */
+mlmc_status mlmc_debug_set_barrier_extra(mlmc_ctx* ctx, int extra);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* LIBMLMC_H */

@@ -1,0 +1,733 @@
+// libmlmc C ABI (include/libmlmc.h): context, entry points, the estimate loop
+// of Alg. 4.1 and the round scheduler that puts every sample of every level
+// of a round into one persistent solve launch per precision class.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <chrono>
+#include <cmath>
+#include <cstring>
+#include <functional>
+#include <map>
+#include <new>
+#include <string>
+#include <vector>
+
+#include "internal.h"
+
+namespace mlmc {
+
+std::atomic<int64_t> g_launches{0};
+
+std::string& create_error() {
+    static thread_local std::string s;
+    return s;
+}
+
+cudaError_t DevBuf::reserve(size_t want) {
+    if (want <= bytes && ptr) return cudaSuccess;
+    release();
+    const size_t grow = std::max(want, bytes + bytes / 4);
+    cudaError_t e = cudaMalloc(&ptr, grow);
+    if (e != cudaSuccess) {
+        ptr = nullptr;
+        bytes = 0;
+        e = cudaMalloc(&ptr, want);
+        if (e != cudaSuccess) {
+            ptr = nullptr;
+            return e;
+        }
+        bytes = want;
+        return cudaSuccess;
+    }
+    bytes = grow;
+    return cudaSuccess;
+}
+
+void DevBuf::release() {
+    if (ptr) cudaFree(ptr);
+    ptr = nullptr;
+    bytes = 0;
+}
+
+
+// Chan et al. pairwise merge; compensated sums merged with TwoSum.
+static void two_sum_add(double& s, double& c, double x) {
+    const double t = s + x;
+    const double e = (std::fabs(s) >= std::fabs(x)) ? ((s - t) + x) : ((x - t) + s);
+    s = t;
+    c += e;
+}
+
+void acc_merge(mlmc_acc* a, const mlmc_acc& b) {
+    if (b.n == 0) return;
+    if (a->n == 0) {
+        *a = b;
+        return;
+    }
+    const double na = (double)a->n, nb = (double)b.n, n = na + nb;
+    const double d = b.mean - a->mean;
+    a->mean = a->mean + d * (nb / n);
+    a->m2 = a->m2 + b.m2 + d * d * (na * nb / n);
+    a->n += b.n;
+    a->sum_c += b.sum_c;
+    two_sum_add(a->sum, a->sum_c, b.sum);
+    a->sumsq_c += b.sumsq_c;
+    two_sum_add(a->sumsq, a->sumsq_c, b.sumsq);
+}
+
+static void acc_push(mlmc_acc* a, double y) {
+    a->n += 1;
+    const double d = y - a->mean;
+    a->mean += d / (double)a->n;
+    a->m2 += d * (y - a->mean);
+    two_sum_add(a->sum, a->sum_c, y);
+    two_sum_add(a->sumsq, a->sumsq_c, y * y);
+}
+
+double qoi_weight_node(const mlmc_problem& p, int n, int i, int j) {
+    const double h2 = 1.0 / ((double)n * n);
+    if (p.qoi == 0) return h2;
+    const int bx0 = (int)std::lround(p.box[0] * n), bx1 = (int)std::lround(p.box[1] * n);
+    const int by0 = (int)std::lround(p.box[2] * n), by1 = (int)std::lround(p.box[3] * n);
+    auto in = [&](int ci, int cj) { return (ci >= bx0 && ci < bx1 && cj >= by0 && cj < by1) ? 1 : 0; };
+    const int cnt = 2 * in(i, j) + in(i - 1, j) + 2 * in(i - 1, j - 1) + in(i, j - 1);
+    return h2 * cnt / 6.0;
+}
+
+}  // namespace mlmc
+
+using namespace mlmc;
+
+namespace {
+
+int level_n(const mlmc_problem& p, int l) {
+    long long n = p.n0;
+    for (int i = 0; i < l; ++i) n *= p.m;
+    return (int)n;
+}
+
+bool is_field_prec(mlmc_prec p) { return p == MLMC_FP64 || p == MLMC_FP32; }
+bool is_prec(int p) { return p >= MLMC_FP64 && p <= MLMC_FP16S; }
+
+mlmc_status fail(mlmc_ctx* ctx, mlmc_status code, const std::string& msg) {
+    if (ctx) ctx->err = msg;
+    return code;
+}
+
+mlmc_status check_problem(const mlmc_problem* p, std::string& err) {
+    if (!p) { err = "null problem"; return MLMC_E_ARG; }
+    if (p->n0 < 2 || p->m < 2 || p->L_max < 0 || p->L_max >= MLMC_MAX_LEVELS) {
+        err = "need n0 >= 2, m >= 2, 0 <= L_max < MLMC_MAX_LEVELS";
+        return MLMC_E_ARG;
+    }
+    long long n = p->n0;
+    for (int l = 0; l < p->L_max; ++l) n *= p->m;
+    if (n > 2048) { err = "finest grid above 2048 cells per side"; return MLMC_E_ARG; }
+    const mlmc_field& f = p->field;
+    if (f.K < 1 || f.K > 256 || !(f.sigma2 > 0) || f.kind < 0 || f.kind > 2) {
+        err = "field: need kind in 0..2, 1 <= K <= 256, sigma2 > 0";
+        return MLMC_E_ARG;
+    }
+    if (f.kind == 0 && !(f.corr_len > 0)) { err = "field: corr_len must be > 0"; return MLMC_E_ARG; }
+    if (f.kind == 2 && f.K != 1) { err = "field kind 2 needs K = 1"; return MLMC_E_ARG; }
+    if (p->qoi != 0 && p->qoi != 1) { err = "qoi must be 0 or 1"; return MLMC_E_ARG; }
+    if (p->qoi == 1) {
+        const double* b = p->box;
+        if (!(b[0] >= 0 && b[0] < b[1] && b[1] <= 1 && b[2] >= 0 && b[2] < b[3] && b[3] <= 1)) {
+            err = "qoi box must satisfy 0 <= x0 < x1 <= 1, 0 <= y0 < y1 <= 1";
+            return MLMC_E_ARG;
+        }
+        for (int k = 0; k < 4; ++k) {
+            const double v = b[k] * p->n0;
+            if (std::fabs(v - std::round(v)) > 1e-9) { err = "qoi box sides must lie on level-0 grid lines"; return MLMC_E_ARG; }
+        }
+    }
+    if (!std::isfinite(p->f)) { err = "f must be finite"; return MLMC_E_ARG; }
+    return MLMC_OK;
+}
+
+// Field of S samples on level l from xi (device) into a (device), in field precision.
+mlmc_status synth(mlmc_ctx* ctx, int level, int S, const double* xi, void* a, mlmc_prec field_prec,
+                  cudaStream_t st) {
+    const int n = level_n(ctx->prob, level);
+    GridBasis& gb = ctx->basis.at(n);
+    cudaError_t e = (field_prec == MLMC_FP64) ? launch_kl_fp64(gb, S, xi, static_cast<double*>(a), st)
+                                              : launch_kl_fp32(ctx, gb, S, xi, static_cast<float*>(a), st);
+    if (e != cudaSuccess) return fail(ctx, MLMC_E_CUDA, std::string("KL synthesis: ") + cudaGetErrorString(e));
+    return MLMC_OK;
+}
+
+// Inner precision rule (documented at mlmc_adapt_precision).
+mlmc_prec pick_prec(double h, double delta, double contrast) {
+    if (contrast <= 0) contrast = 1.0;
+    const double u_single = 0x1p-24;
+    if (contrast / (h * h) * u_single > 0.5) return MLMC_FP64;
+    if (delta >= 1e-4) return MLMC_FP16S;
+    return MLMC_FP32;
+}
+
+// ---------------------------------------------------------------------------
+// Alg. 4.1 host loop, shared by the GPU estimate and the host-sampler variant.
+struct Request {
+    int level;
+    int64_t first;
+    int count;
+};
+using RoundFn = std::function<mlmc_status(const std::vector<Request>&, const std::vector<double>& delta_fine,
+                                          const std::vector<double>& delta_coarse, std::vector<mlmc_acc>& out,
+                                          mlmc_result* res)>;
+
+mlmc_status alg41(int m, int L_max, int n0, const mlmc_options& o, const RoundFn& round, mlmc_result* res) {
+    const auto t0 = std::chrono::steady_clock::now();
+    std::memset(res, 0, sizeof(*res));
+    const bool fixed = o.fixed_N != nullptr;
+    int L = std::min(std::max(o.L_start, 0), L_max);
+    std::vector<int64_t> N(L + 1, o.N_init);
+    if (fixed)
+        for (int l = 0; l <= L; ++l) N[l] = o.fixed_N[l];
+    std::vector<mlmc_acc> acc(L + 1);
+    std::memset(acc.data(), 0, sizeof(mlmc_acc) * acc.size());
+    int rounds = 0;
+    bool bias_failed = false;
+    const double thr = (o.r * std::pow((double)m, o.alpha) - 1.0) * o.tol / std::sqrt(2.0);
+    std::vector<double> delta;
+    while (rounds < std::max(1, o.max_rounds)) {
+        ++rounds;
+        std::vector<double> h(L + 1);
+        for (int l = 0; l <= L; ++l) h[l] = 1.0 / ((double)n0 * std::pow((double)m, l));
+        delta.assign(L + 1, 0.0);
+        std::vector<mlmc_prec> prec(L + 1);
+        mlmc_adapt_precision(L, h.data(), o.kp, o.alpha1, o.alpha2, o.beta1, o.beta2, o.contrast, delta.data(),
+                             prec.data());
+        if (o.form == MLMC_FORM_FP64_FIXED) std::fill(delta.begin(), delta.end(), o.fixed_delta);
+        // the coarse member of level l is solved to the accuracy of level l-1 (Lemma 4.6's use of delta_{l-1})
+        std::vector<double> dcoarse(L + 1, 0.0);
+        for (int l = 1; l <= L; ++l) dcoarse[l] = delta[l - 1];
+        std::vector<Request> req;
+        for (int l = 0; l <= L; ++l)
+            if (N[l] > acc[l].n) req.push_back({l, acc[l].n, (int)(N[l] - acc[l].n)});
+        if (!req.empty()) {
+            std::vector<mlmc_acc> got(req.size());
+            std::memset(got.data(), 0, sizeof(mlmc_acc) * got.size());
+            const mlmc_status st = round(req, delta, dcoarse, got, res);
+            if (st != MLMC_OK) return st;
+            for (size_t i = 0; i < req.size(); ++i) acc_merge(&acc[req[i].level], got[i]);
+        }
+        if (fixed) break;
+        std::vector<double> V(L + 1), C(L + 1);
+        double sum_vc = 0.0;
+        for (int l = 0; l <= L; ++l) {
+            V[l] = acc[l].n > 0 ? acc[l].m2 / (double)acc[l].n : 0.0;
+            C[l] = std::pow((double)m, o.gamma * l);
+            sum_vc += std::sqrt(V[l] * C[l]);
+        }
+        std::vector<int64_t> Nopt(L + 1);
+        bool enough = true;
+        for (int l = 0; l <= L; ++l) {
+            Nopt[l] = (int64_t)std::ceil(std::sqrt(V[l] / C[l]) * (2.0 / (o.tol * o.tol)) * sum_vc);
+            N[l] = std::max<int64_t>(Nopt[l], acc[l].n);
+            if (acc[l].n < Nopt[l]) enough = false;
+        }
+        bias_failed = std::fabs(acc[L].mean) > thr;
+        if (bias_failed && L < L_max) {
+            ++L;
+            N.push_back(o.N_init);
+            mlmc_acc z;
+            std::memset(&z, 0, sizeof(z));
+            acc.push_back(z);
+            continue;
+        }
+        if (enough) break;
+    }
+    res->L = L;
+    res->rounds = rounds;
+    res->bias_failed = bias_failed ? 1 : 0;
+    double est = 0.0, var = 0.0;
+    for (int l = 0; l <= L; ++l) {
+        res->N[l] = acc[l].n;
+        res->Yhat[l] = acc[l].mean;
+        res->s2[l] = acc[l].n > 0 ? acc[l].m2 / (double)acc[l].n : 0.0;
+        res->delta[l] = l < (int)delta.size() ? delta[l] : 0.0;
+        res->acc[l] = acc[l];
+        est += acc[l].mean;
+        if (acc[l].n > 0) var += res->s2[l] / (double)acc[l].n;
+    }
+    const double bias = std::fabs(acc[L].mean) / (std::pow((double)m, o.alpha) - 1.0);
+    res->estimate = est;
+    res->var_est = var;
+    res->rmse = std::sqrt(bias * bias + var);
+    res->seconds = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+    return MLMC_OK;
+}
+
+mlmc_status check_options(const mlmc_options* o, int L_max, std::string& err) {
+    if (!o) { err = "null options"; return MLMC_E_ARG; }
+    if (!(o->tol > 0) || o->N_init < 2 || !(o->kp > 0 && o->kp < 1) || o->L_start < 0 || o->L_start > L_max) {
+        err = "options: need tol > 0, N_init >= 2, 0 < kp < 1, 0 <= L_start <= L_max";
+        return MLMC_E_ARG;
+    }
+    if (o->form < 0 || o->form > 2 || (o->force_prec >= 0 && !is_prec(o->force_prec)) ||
+        (o->solver != MLMC_CG && o->solver != MLMC_MINRES) || o->max_iters < 1) {
+        err = "options: bad form, precision, solver or max_iters";
+        return MLMC_E_ARG;
+    }
+    if (o->fixed_N)
+        for (int l = 0; l <= o->L_start; ++l)
+            if (o->fixed_N[l] < 1) { err = "fixed_N entries must be >= 1"; return MLMC_E_ARG; }
+    return MLMC_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+const char* mlmc_version(void) { return "libmlmc 0.1 (sm_103a)"; }
+
+int64_t mlmc_launch_count(void) { return g_launches.load(); }
+
+const char* mlmc_last_error(const mlmc_ctx* ctx) {
+    return ctx ? ctx->err.c_str() : create_error().c_str();
+}
+
+mlmc_status mlmc_create(const mlmc_problem* prob, int device, mlmc_ctx** out) {
+    if (!out) return MLMC_E_ARG;
+    *out = nullptr;
+    create_error().clear();
+    mlmc_status st = check_problem(prob, create_error());
+    if (st != MLMC_OK) return st;
+    int ndev = 0;
+    cudaError_t e = cudaGetDeviceCount(&ndev);
+    if (e != cudaSuccess || device < 0 || device >= ndev) {
+        create_error() = std::string("no CUDA device ") + std::to_string(device) + ": " +
+                         (e != cudaSuccess ? cudaGetErrorString(e) : "out of range");
+        return MLMC_E_CUDA;
+    }
+    if ((e = cudaSetDevice(device)) != cudaSuccess) {
+        create_error() = std::string("cudaSetDevice: ") + cudaGetErrorString(e);
+        return MLMC_E_CUDA;
+    }
+    mlmc_ctx* ctx = new (std::nothrow) mlmc_ctx();
+    if (!ctx) return MLMC_E_NOMEM;
+    ctx->prob = *prob;
+    ctx->device = device;
+    cudaDeviceGetAttribute(&ctx->num_sms, cudaDevAttrMultiProcessorCount, device);
+    for (int l = 0; l <= prob->L_max; ++l) {
+        const int n = level_n(*prob, l);
+        std::string err;
+        e = upload_basis(ctx->basis[n], prob->field, n, err);
+        ctx->prof.acc.h2d_bytes += (int64_t)sizeof(double) * prob->field.K * (1 + 2 * (n + 1));
+        if (e != cudaSuccess) {
+            create_error() = "basis upload for n=" + std::to_string(n) + ": " +
+                             (err.empty() ? std::string(cudaGetErrorString(e)) : err);
+            mlmc_destroy(ctx);
+            return e == cudaErrorMemoryAllocation ? MLMC_E_NOMEM : MLMC_E_CUDA;
+        }
+    }
+    *out = ctx;
+    return MLMC_OK;
+}
+
+void mlmc_destroy(mlmc_ctx* ctx) {
+    if (!ctx) return;
+    cudaSetDevice(ctx->device);
+    cudaDeviceSynchronize();
+    for (auto& kv : ctx->basis) {
+        kv.second.phi64.release();
+        kv.second.phi16.release();
+    }
+    for (auto& p : ctx->prof.kl_pending) {
+        cudaEventDestroy(p.a);
+        cudaEventDestroy(p.b);
+    }
+    Workspace& w = ctx->ws;
+    for (DevBuf* b : {&w.solver, &w.fields, &w.xi, &w.q, &w.misc, &w.split, &w.adj}) b->release();
+    if (w.pinned) cudaFreeHost(w.pinned);
+    delete ctx;
+}
+
+mlmc_status mlmc_set_wait_timeout(mlmc_ctx* ctx, double seconds) {
+    if (!ctx || !(seconds > 0)) return MLMC_E_ARG;
+    ctx->wait_timeout_s = seconds;
+    return MLMC_OK;
+}
+
+mlmc_status mlmc_profile_enable(mlmc_ctx* ctx, int on) {
+    if (!ctx) return MLMC_E_ARG;
+    ctx->prof.on = on != 0;
+    return MLMC_OK;
+}
+
+mlmc_status mlmc_profile_get(mlmc_ctx* ctx, mlmc_profile* out) {
+    if (!ctx || !out) return MLMC_E_ARG;
+    cudaSetDevice(ctx->device);
+    MLMC_CUDA_RET(ctx->err, cudaDeviceSynchronize());
+    for (auto& p : ctx->prof.kl_pending) {
+        float ms = 0.f;
+        if (cudaEventElapsedTime(&ms, p.a, p.b) == cudaSuccess) {
+            ctx->prof.acc.kl_launches += 1;
+            ctx->prof.acc.kl_ms += ms;
+            ctx->prof.acc.kl_bytes += p.bytes;
+            ctx->prof.acc.kl_flops += p.flops;
+        }
+        cudaEventDestroy(p.a);
+        cudaEventDestroy(p.b);
+    }
+    ctx->prof.kl_pending.clear();
+    *out = ctx->prof.acc;
+    return MLMC_OK;
+}
+
+mlmc_status mlmc_profile_reset(mlmc_ctx* ctx) {
+    if (!ctx) return MLMC_E_ARG;
+    mlmc_profile tmp;
+    mlmc_status s = mlmc_profile_get(ctx, &tmp);
+    std::memset(&ctx->prof.acc, 0, sizeof(ctx->prof.acc));
+    return s;
+}
+
+mlmc_status mlmc_debug_set_barrier_extra(mlmc_ctx* ctx, int extra) {
+    if (!ctx || extra < 0) return MLMC_E_ARG;
+    ctx->barrier_extra = extra;
+    return MLMC_OK;
+}
+
+mlmc_status mlmc_sample_fields(mlmc_ctx* ctx, int level, uint64_t first, int S, double* xi, void* a,
+                               mlmc_prec field_prec, void* stream) {
+    if (!ctx) return MLMC_E_ARG;
+    if (level < 0 || level > ctx->prob.L_max || S < 0 || (S > 0 && !a) || !is_field_prec(field_prec))
+        return fail(ctx, MLMC_E_ARG, "sample_fields: bad level, S, output or field precision");
+    if (S == 0) return MLMC_OK;
+    cudaSetDevice(ctx->device);
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    double* xbuf = xi;
+    if (!xbuf) {
+        MLMC_CUDA_RET(ctx->err, ctx->ws.xi.reserve(sizeof(double) * (size_t)S * ctx->prob.field.K));
+        xbuf = ctx->ws.xi.as<double>();
+    }
+    MLMC_CUDA_RET(ctx->err, launch_philox_normals(ctx->prob.seed, level, first, S, ctx->prob.field.K, xbuf, st));
+    return synth(ctx, level, S, xbuf, a, field_prec, st);
+}
+
+mlmc_status mlmc_synthesize_fields(mlmc_ctx* ctx, int level, int S, const double* xi, void* a,
+                                   mlmc_prec field_prec, void* stream) {
+    if (!ctx) return MLMC_E_ARG;
+    if (level < 0 || level > ctx->prob.L_max || S < 0 || (S > 0 && (!a || !xi)) || !is_field_prec(field_prec))
+        return fail(ctx, MLMC_E_ARG, "synthesize_fields: bad level, S, pointers or field precision");
+    if (S == 0) return MLMC_OK;
+    cudaSetDevice(ctx->device);
+    return synth(ctx, level, S, xi, a, field_prec, static_cast<cudaStream_t>(stream));
+}
+
+mlmc_status mlmc_apply_operator(int n, int S, const void* a, mlmc_prec a_prec, int a_n, mlmc_prec op_prec,
+                                const void* x, void* y, mlmc_prec vec_prec, void* stream) {
+    if (n < 2 || S < 0 || a_n < n || a_n % n != 0 || !is_field_prec(a_prec) || !is_prec(op_prec) ||
+        !is_field_prec(vec_prec))
+        return MLMC_E_ARG;
+    if ((op_prec == MLMC_FP64) != (vec_prec == MLMC_FP64)) return MLMC_E_ARG;
+    if (S == 0) return MLMC_OK;
+    if (!a || !x || !y) return MLMC_E_ARG;
+    const cudaError_t e = launch_apply_operator(n, S, a, a_prec == MLMC_FP64, a_n, op_prec, x, y,
+                                                vec_prec == MLMC_FP64, static_cast<cudaStream_t>(stream));
+    return e == cudaSuccess ? MLMC_OK : MLMC_E_CUDA;
+}
+
+mlmc_status mlmc_level_solve(mlmc_ctx* ctx, int n, int S, const void* a, mlmc_prec a_prec, int a_n,
+                             mlmc_prec prec, mlmc_solver solver, double delta, int max_iters, double* u,
+                             double* Q, int32_t* iters, double* relres, int32_t* flags, void* stream) {
+    if (!ctx) return MLMC_E_ARG;
+    if (n < 2 || n > 2048 || S < 0 || a_n < n || a_n % n != 0 || !is_field_prec(a_prec) || !is_prec(prec) ||
+        (solver != MLMC_CG && solver != MLMC_MINRES) || !(delta > 0) || max_iters < 1)
+        return fail(ctx, MLMC_E_ARG, "level_solve: bad n, S, a_n, precision, solver, delta or max_iters");
+    if (S == 0) return MLMC_OK;
+    if (!a || !Q) return fail(ctx, MLMC_E_ARG, "level_solve: null a or Q");
+    cudaSetDevice(ctx->device);
+    SolveGroup g;
+    g.n = n;
+    g.S = S;
+    g.a = a;
+    g.a_fp64 = (a_prec == MLMC_FP64);
+    g.a_n = a_n;
+    g.delta = delta;
+    g.Q = Q;
+    g.u = u;
+    g.iters = iters;
+    g.relres = relres;
+    g.flags = flags;
+    SolveConfig cfg;
+    cfg.prec = prec;
+    cfg.solver = solver;
+    cfg.max_iters = max_iters;
+    return run_solve_batch(ctx, {g}, cfg, static_cast<cudaStream_t>(stream));
+}
+
+void mlmc_acc_merge(mlmc_acc* into, const mlmc_acc* other) {
+    if (into && other) acc_merge(into, *other);
+}
+
+mlmc_status mlmc_level_stats(mlmc_ctx* ctx, int S, const double* Qf, const double* Qc, mlmc_acc* acc,
+                             void* stream) {
+    if (!ctx || S < 0 || !acc || (S > 0 && !Qf)) return ctx ? fail(ctx, MLMC_E_ARG, "level_stats: bad args") : MLMC_E_ARG;
+    if (S == 0) return MLMC_OK;
+    cudaSetDevice(ctx->device);
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    MLMC_CUDA_RET(ctx->err, ctx->ws.misc.reserve(sizeof(mlmc_acc)));
+    MLMC_CUDA_RET(ctx->err, launch_level_stats(S, Qf, Qc, ctx->ws.misc.as<mlmc_acc>(), st));
+    mlmc_acc got;
+    MLMC_CUDA_RET(ctx->err, cudaMemcpyAsync(&got, ctx->ws.misc.ptr, sizeof(got), cudaMemcpyDeviceToHost, st));
+    MLMC_CUDA_RET(ctx->err, cudaStreamSynchronize(st));
+    ctx->prof.acc.d2h_bytes += (int64_t)sizeof(got);
+    acc_merge(acc, got);
+    return MLMC_OK;
+}
+
+mlmc_status mlmc_adapt_precision(int L, const double* h, double kp, double alpha1, double alpha2, double beta1,
+                                 double beta2, double contrast, double* delta, mlmc_prec* prec) {
+    if (L < 0 || !h || !delta || !(kp > 0) || !(alpha2 > 0) || !(beta2 > 0)) return MLMC_E_ARG;
+    for (int l = 0; l <= L; ++l) {
+        if (!(h[l] > 0)) return MLMC_E_ARG;
+        delta[l] = std::pow(kp * std::pow(h[l], beta1), 1.0 / beta2);
+    }
+    delta[L] = std::min(delta[L], std::pow(kp * std::pow(h[L], alpha1), 1.0 / alpha2));
+    if (prec)
+        for (int l = 0; l <= L; ++l) prec[l] = pick_prec(h[l], delta[l], contrast);
+    return MLMC_OK;
+}
+
+void mlmc_default_options(mlmc_options* o) {
+    if (!o) return;
+    std::memset(o, 0, sizeof(*o));
+    o->tol = 1e-3;
+    o->L_start = 1;
+    o->N_init = 100;
+    o->kp = 0.05;
+    o->alpha1 = 2.0;
+    o->alpha2 = 1.0;
+    o->beta1 = 4.0;
+    o->beta2 = 2.0;
+    o->alpha = 2.0;
+    o->gamma = 2.0;
+    o->r = 1.0;
+    o->form = MLMC_FORM_MIXED;
+    o->fixed_delta = 1e-10;
+    o->force_prec = -1;
+    o->solver = MLMC_CG;
+    o->max_iters = 100000;
+    o->max_rounds = 100;
+    o->fixed_N = nullptr;
+    o->contrast = 1.0;
+}
+
+mlmc_status mlmc_estimate_host(int m, int L_max, int n0, const mlmc_options* opts, mlmc_sampler_fn sampler,
+                               void* user, mlmc_result* res) {
+    std::string err;
+    if (!sampler || !res || m < 2 || n0 < 2 || L_max < 0 || L_max >= MLMC_MAX_LEVELS) return MLMC_E_ARG;
+    if (check_options(opts, L_max, err) != MLMC_OK) return MLMC_E_ARG;
+    RoundFn round = [&](const std::vector<Request>& req, const std::vector<double>& df, const std::vector<double>&,
+                        std::vector<mlmc_acc>& out, mlmc_result*) -> mlmc_status {
+        std::vector<double> Y;
+        for (size_t i = 0; i < req.size(); ++i) {
+            Y.assign(req[i].count, 0.0);
+            if (sampler(user, req[i].level, req[i].first, req[i].count, df.data(), Y.data()) != 0) return MLMC_E_ARG;
+            for (double y : Y) acc_push(&out[i], y);
+        }
+        return MLMC_OK;
+    };
+    return alg41(m, L_max, n0, *opts, round, res);
+}
+
+mlmc_status mlmc_estimate(mlmc_ctx* ctx, const mlmc_options* opts, mlmc_result* res) {
+    if (!ctx || !res) return MLMC_E_ARG;
+    if (check_options(opts, ctx->prob.L_max, ctx->err) != MLMC_OK) return MLMC_E_ARG;
+    cudaSetDevice(ctx->device);
+    const mlmc_options o = *opts;
+    const mlmc_problem& p = ctx->prob;
+    const int K = p.field.K;
+    const cudaStream_t st = nullptr;
+    const mlmc_prec field_prec = (o.form == MLMC_FORM_MIXED) ? MLMC_FP32 : MLMC_FP64;
+    const size_t felem = field_prec == MLMC_FP64 ? sizeof(double) : sizeof(float);
+    int32_t flags_or = 0;
+    std::vector<int64_t> iters_lvl(MLMC_MAX_LEVELS, 0), dofs_lvl(MLMC_MAX_LEVELS, 0);
+    std::vector<int32_t> prec_lvl(MLMC_MAX_LEVELS, -1);
+
+    RoundFn round = [&](const std::vector<Request>& req, const std::vector<double>& df, const std::vector<double>& dc,
+                        std::vector<mlmc_acc>& out, mlmc_result*) -> mlmc_status {
+        // ---- memory plan of the round
+        const int L = (int)df.size() - 1;
+        std::vector<double> h(L + 1);
+        for (int l = 0; l <= L; ++l) h[l] = 1.0 / level_n(p, l);
+        std::vector<mlmc_prec> prec_rule(L + 1);
+        std::vector<double> dtmp(L + 1);
+        mlmc_adapt_precision(L, h.data(), o.kp, o.alpha1, o.alpha2, o.beta1, o.beta2, o.contrast, dtmp.data(),
+                             prec_rule.data());
+        auto prec_of = [&](int l) -> mlmc_prec {
+            if (o.form != MLMC_FORM_MIXED) return MLMC_FP64;
+            if (o.force_prec >= 0) return (mlmc_prec)o.force_prec;
+            return prec_rule[l];
+        };
+        size_t fbytes = 0, xbytes = 0, qn = 0;
+        std::vector<size_t> foff(req.size()), xoff(req.size()), qoff(req.size());
+        for (size_t i = 0; i < req.size(); ++i) {
+            const int n = level_n(p, req[i].level);
+            foff[i] = fbytes;
+            fbytes += (size_t)req[i].count * (n + 1) * (n + 1) * felem;
+            fbytes = (fbytes + 255) / 256 * 256;
+            xoff[i] = xbytes;
+            xbytes += (size_t)req[i].count * K * sizeof(double);
+            qoff[i] = qn;
+            qn += (size_t)req[i].count;
+        }
+        MLMC_CUDA_RET(ctx->err, ctx->ws.fields.reserve(fbytes));
+        MLMC_CUDA_RET(ctx->err, ctx->ws.xi.reserve(std::max<size_t>(xbytes, 8)));
+        // Qf, Qc (doubles), iters and flags for fine and coarse (int32)
+        const size_t qbytes = qn * (2 * sizeof(double) + 4 * sizeof(int32_t));
+        MLMC_CUDA_RET(ctx->err, ctx->ws.q.reserve(qbytes));
+        MLMC_CUDA_RET(ctx->err, ctx->ws.misc.reserve(sizeof(mlmc_acc) * req.size()));
+        char* fb = ctx->ws.fields.as<char>();
+        double* xb = ctx->ws.xi.as<double>();
+        double* Qf = ctx->ws.q.as<double>();
+        double* Qc = Qf + qn;
+        int32_t* itf = reinterpret_cast<int32_t*>(Qc + qn);
+        int32_t* itc = itf + qn;
+        int32_t* flf = itc + qn;
+        int32_t* flc = flf + qn;
+        MLMC_CUDA_RET(ctx->err, cudaMemsetAsync(Qc, 0, qn * sizeof(double), st));
+        MLMC_CUDA_RET(ctx->err, cudaMemsetAsync(itc, 0, qn * sizeof(int32_t), st));
+        MLMC_CUDA_RET(ctx->err, cudaMemsetAsync(flc, 0, qn * sizeof(int32_t), st));
+        // ---- fields of every request
+        for (size_t i = 0; i < req.size(); ++i) {
+            const mlmc_status s = mlmc_sample_fields(ctx, req[i].level, (uint64_t)req[i].first, req[i].count,
+                                                     xb + xoff[i] / sizeof(double), fb + foff[i], field_prec,
+                                                     (void*)st);
+            if (s != MLMC_OK) return s;
+        }
+        // ---- one persistent launch per inner-precision class: every fine and coarse member
+        std::map<int, std::vector<SolveGroup>> classes;
+        for (size_t i = 0; i < req.size(); ++i) {
+            const int l = req[i].level;
+            const int n = level_n(p, l);
+            SolveGroup gf;
+            gf.n = n;
+            gf.S = req[i].count;
+            gf.a = fb + foff[i];
+            gf.a_fp64 = field_prec == MLMC_FP64;
+            gf.a_n = n;
+            gf.delta = df[l];
+            gf.Q = Qf + qoff[i];
+            gf.iters = itf + qoff[i];
+            gf.flags = flf + qoff[i];
+            classes[prec_of(l)].push_back(gf);
+            prec_lvl[l] = prec_of(l);
+            dofs_lvl[l] += (int64_t)req[i].count * (n - 1) * (n - 1);
+            if (l > 0) {
+                SolveGroup gc = gf;
+                gc.n = n / p.m;
+                gc.delta = dc[l];
+                gc.Q = Qc + qoff[i];
+                gc.iters = itc + qoff[i];
+                gc.flags = flc + qoff[i];
+                classes[prec_of(l - 1)].push_back(gc);
+                dofs_lvl[l] += (int64_t)req[i].count * (gc.n - 1) * (gc.n - 1);
+            }
+        }
+        for (auto& kv : classes) {
+            SolveConfig cfg;
+            cfg.prec = kv.first;
+            cfg.solver = o.solver;
+            cfg.max_iters = o.max_iters;
+            const mlmc_status s = run_solve_batch(ctx, kv.second, cfg, st);
+            if (s != MLMC_OK) return s;
+        }
+        // ---- level statistics of the batch
+        mlmc_acc* dacc = ctx->ws.misc.as<mlmc_acc>();
+        for (size_t i = 0; i < req.size(); ++i) {
+            MLMC_CUDA_RET(ctx->err, launch_level_stats(req[i].count, Qf + qoff[i],
+                                                        req[i].level > 0 ? Qc + qoff[i] : nullptr, dacc + i, st));
+        }
+        MLMC_CUDA_RET(ctx->err, cudaMemcpyAsync(out.data(), dacc, sizeof(mlmc_acc) * req.size(),
+                                                cudaMemcpyDeviceToHost, st));
+        std::vector<int32_t> hit(4 * qn);
+        MLMC_CUDA_RET(ctx->err, cudaMemcpyAsync(hit.data(), itf, 4 * qn * sizeof(int32_t), cudaMemcpyDeviceToHost, st));
+        MLMC_CUDA_RET(ctx->err, cudaStreamSynchronize(st));
+        ctx->prof.acc.d2h_bytes += (int64_t)(sizeof(mlmc_acc) * req.size() + 4 * qn * sizeof(int32_t));
+        for (size_t i = 0; i < req.size(); ++i) {
+            for (int s = 0; s < req[i].count; ++s) {
+                const size_t q = qoff[i] + s;
+                iters_lvl[req[i].level] += hit[q] + hit[qn + q];
+                const int32_t ff = hit[2 * qn + q], fc = hit[3 * qn + q];
+                flags_or |= ff;
+                if (req[i].level > 0) flags_or |= fc;
+            }
+        }
+        return MLMC_OK;
+    };
+    const mlmc_status s = alg41(p.m, p.L_max, p.n0, o, round, res);
+    if (s != MLMC_OK) return s;
+    for (int l = 0; l <= res->L; ++l) {
+        res->prec[l] = prec_lvl[l];
+        res->inner_iters[l] = iters_lvl[l];
+        res->dofs[l] = dofs_lvl[l];
+    }
+    res->flags_or = flags_or;
+    const int32_t bad = MLMC_F_MAXIT | MLMC_F_STAGNATED | MLMC_F_NONFINITE;
+    if (flags_or & MLMC_F_NONFINITE) return fail(ctx, MLMC_E_NONFINITE, "estimate: a solve met a non-finite value");
+    if (flags_or & bad) return fail(ctx, MLMC_E_NOCONV, "estimate: some solves stopped before their tolerance");
+    return MLMC_OK;
+}
+
+mlmc_status mlmc_adjoint_grad(mlmc_ctx* ctx, int level, int S, const double* xi, mlmc_prec prec, double delta,
+                              int max_iters, double* Q, double* dQdxi, void* stream) {
+    if (!ctx) return MLMC_E_ARG;
+    if (level < 0 || level > ctx->prob.L_max || S < 0 || !is_prec(prec) || !(delta > 0) || max_iters < 1)
+        return fail(ctx, MLMC_E_ARG, "adjoint_grad: bad level, S, precision, delta or max_iters");
+    if (S == 0) return MLMC_OK;
+    if (!xi || !Q || !dQdxi) return fail(ctx, MLMC_E_ARG, "adjoint_grad: null pointer");
+    cudaSetDevice(ctx->device);
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    const int n = level_n(ctx->prob, level);
+    const size_t V = (size_t)(n + 1) * (n + 1);
+    const mlmc_prec fp = (prec == MLMC_FP64) ? MLMC_FP64 : MLMC_FP32;
+    const size_t felem = fp == MLMC_FP64 ? sizeof(double) : sizeof(float);
+    // layout: a [S][V] (field precision) | u [S][V] | lam [S][V] | w [S][V] (FP64)
+    const size_t abytes = (S * V * felem + 255) / 256 * 256;
+    MLMC_CUDA_RET(ctx->err, ctx->ws.adj.reserve(abytes + 3 * S * V * sizeof(double)));
+    char* base = ctx->ws.adj.as<char>();
+    void* a = base;
+    double* u = reinterpret_cast<double*>(base + abytes);
+    double* lam = u + S * V;
+    double* w = lam + S * V;
+    mlmc_status s = synth(ctx, level, S, xi, a, fp, st);
+    if (s != MLMC_OK) return s;
+    // ||g||_2 of the adjoint right-hand side
+    double g2 = 0.0;
+    for (int j = 1; j < n; ++j)
+        for (int i = 1; i < n; ++i) {
+            const double g = qoi_weight_node(ctx->prob, n, i, j);
+            g2 += g * g;
+        }
+    const double gnorm = std::sqrt(g2);
+    MLMC_CUDA_RET(ctx->err, ctx->ws.misc.reserve(sizeof(double) * S));
+    SolveGroup gf;
+    gf.n = n;
+    gf.S = S;
+    gf.a = a;
+    gf.a_fp64 = fp == MLMC_FP64;
+    gf.a_n = n;
+    gf.delta = delta;
+    gf.Q = Q;
+    gf.u = u;
+    SolveGroup ga = gf;
+    ga.Q = ctx->ws.misc.as<double>();
+    ga.u = lam;
+    ga.rhs_weights = &gnorm;
+    SolveConfig cfg;
+    cfg.prec = prec;
+    cfg.max_iters = max_iters;
+    s = run_solve_batch(ctx, {gf, ga}, cfg, st);
+    if (s != MLMC_OK) return s;
+    MLMC_CUDA_RET(ctx->err, launch_adjoint_elements(n, S, a, fp == MLMC_FP64, u, lam, w, st));
+    MLMC_CUDA_RET(ctx->err, launch_kl_transpose_fp64(ctx->basis.at(n), S, w, dQdxi, st));
+    return MLMC_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,149 @@
+"""C-ABI boundary checks that need no GPU: the library loads, exports every
+symbol include/libmlmc.h declares, and its pure-host logic (accuracy rule,
+Algorithm 4.1 loop, accumulator merge) agrees with the oracle."""
+import ctypes
+import math
+import os
+import re
+
+import numpy as np
+import pytest
+
+from conftest import ROOT, golden_rows
+from oracle import mlmc as o_mlmc
+
+
+@pytest.fixture(scope="session")
+def L():
+    import __graft_entry__
+    __graft_entry__.build()
+    import paper_2503_05533_gb300 as M
+    return M
+
+
+def _declared_functions():
+    text = open(os.path.join(ROOT, "include", "libmlmc.h")).read()
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    names = set(re.findall(r"\b(mlmc_[a-z0-9_]+)\s*\(", text))
+    typedef_fn = set(re.findall(r"\(\s*\*\s*(mlmc_[a-z0-9_]+)\s*\)", text))
+    return sorted(names - typedef_fn)
+
+
+def test_library_exports_every_declared_symbol(L):
+    names = _declared_functions()
+    assert len(names) >= 17
+    so = ctypes.CDLL(L.capi.LIB_PATH)
+    missing = [n for n in names if not hasattr(so, n)]
+    assert not missing, missing
+    # and the binding wraps each of them under the same name
+    assert all(hasattr(L.capi, n) for n in names)
+    assert "sm_103a" in L.mlmc_version()
+
+
+def test_struct_layouts_match_header(L):
+    # offsets of the C structs as compiled by the host compiler
+    import ctypes as C
+    assert C.sizeof(L.capi.mlmc_acc) == 56
+    assert C.sizeof(L.capi.mlmc_field) == 32
+    assert L.capi.mlmc_problem.seed.offset == C.sizeof(L.capi.mlmc_problem) - 8
+
+
+def test_accuracy_rule_matches_table_1_and_oracle(L):
+    rows = golden_rows("table1_delta.txt")
+    for Lf in range(1, 5):
+        h = [(1.0 / 8.0) * 2.0 ** -l for l in range(Lf + 1)]
+        d, prec = L.mlmc_adapt_precision(h, 0.05)
+        assert np.allclose(d, o_mlmc.delta_rule_fem(h, 0.05), rtol=1e-14)
+        for r in rows:
+            if int(r[0]) == Lf:
+                e = math.floor(math.log10(float(r[2])))
+                assert abs(d[int(r[1])] - float(r[2])) <= 10.0 ** (e - 1) * 1.0001
+    # precision choice: 16-bit storage while delta >= 1e-4, FP32 below, FP64 only for huge kappa
+    d, prec = L.mlmc_adapt_precision([1 / 16, 1 / 32, 1 / 64, 1 / 128, 1 / 256], 0.05)
+    assert prec[0] == L.MLMC_FP16S and prec[-1] == L.MLMC_FP32
+    _, p64 = L.mlmc_adapt_precision([1 / 1024], 0.05, contrast=1e3)
+    assert p64 == [L.MLMC_FP64]
+    with pytest.raises(L.MlmcError):
+        L.mlmc_adapt_precision([0.0], 0.05)
+
+
+class _Mock:
+    def __init__(self, mu, sd, seed):
+        self.mu, self.sd, self.seed = mu, sd, seed
+        self.calls = []
+
+    def draws(self, l, first, count):
+        # values depend only on (level, sample index): both loops see the same Y
+        out = np.empty(count)
+        for i in range(count):
+            g = np.random.default_rng([self.seed, l, first + i])
+            out[i] = self.mu[l] + self.sd[l] * g.standard_normal()
+        return out
+
+    def __call__(self, l, first, count, deltas):
+        self.calls.append((l, first, count))
+        return self.draws(l, first, count)
+
+
+class _P:
+    def __init__(self, L_max, n0, m=2):
+        self.L_max, self.n0, self.m = L_max, n0, m
+
+    def h(self, l):
+        return 1.0 / (self.n0 * self.m ** l)
+
+
+@pytest.mark.parametrize("L_start", [1, 3])
+def test_algorithm_4_1_host_loop_matches_oracle(L, L_start):
+    tol = 1e-3
+    thr = o_mlmc.bias_threshold(2, 2.0, tol)
+    mu = [0.05, 4 * thr, thr, thr / 8, thr / 30]
+    sd = [2e-2, 2e-3, 4e-4, 1e-4, 3e-5]
+    o = L.mlmc_default_options()
+    o.tol, o.N_init, o.L_start = tol, 40, L_start
+    mock_c = _Mock(mu, sd, 3)
+    res = L.mlmc_estimate_host(2, 4, 8, o, mock_c)
+    mock_o = _Mock(mu, sd, 3)
+    ref = o_mlmc.estimate(_P(4, 8), tol, N_init=40, L_start=L_start, sampler=mock_o)
+    r = L.result_dict(res)
+    assert r["L"] == ref["L"] and r["N"] == list(ref["N"]) and r["rounds"] == ref["rounds"]
+    assert mock_c.calls == mock_o.calls
+    assert np.allclose(r["Yhat"], ref["Yhat"], rtol=1e-12, atol=1e-15)
+    assert np.allclose(r["s2"], ref["s2"], rtol=1e-10, atol=0)
+    assert abs(r["estimate"] - ref["estimate"]) < 1e-13
+    assert abs(r["rmse"] - ref["rmse"]) <= 1e-12 * ref["rmse"]
+
+
+def test_fixed_samples_mode(L):
+    o = L.mlmc_default_options()
+    o.L_start = 2
+    N = (ctypes.c_int64 * 3)(30, 20, 10)
+    o.fixed_N = ctypes.cast(N, ctypes.POINTER(ctypes.c_int64))
+    mock = _Mock([1.0, 0.1, 0.01], [0.1, 0.01, 0.001], 9)
+    r = L.result_dict(L.mlmc_estimate_host(2, 2, 4, o, mock))
+    assert r["N"] == [30, 20, 10] and r["rounds"] == 1
+    Y0 = mock.draws(0, 0, 30)
+    assert abs(r["Yhat"][0] - Y0.mean()) < 1e-14
+
+
+def test_acc_merge_matches_two_pass(L):
+    g = np.random.default_rng(4)
+    Y = g.standard_normal(1001) * 3e-3 + 0.2
+    parts = np.split(Y, [1, 17, 500, 999])
+    total = L.capi.mlmc_acc()
+    for p in parts:
+        a = L.capi.mlmc_acc()
+        a.n, a.mean = len(p), float(p.mean())
+        a.m2 = float(((p - p.mean()) ** 2).sum())
+        a.sum, a.sumsq = float(p.sum()), float((p * p).sum())
+        L.mlmc_acc_merge(total, a)
+    m, v = o_mlmc.mean_var(Y)
+    assert total.n == len(Y)
+    assert abs(total.mean - m) < 1e-15 and abs(total.m2 / total.n - v) < 1e-12 * v
+
+
+def test_host_loop_rejects_bad_options(L):
+    o = L.mlmc_default_options()
+    o.tol = -1.0
+    with pytest.raises(L.MlmcError):
+        L.mlmc_estimate_host(2, 2, 4, o, _Mock([0, 0, 0], [1, 1, 1], 0))

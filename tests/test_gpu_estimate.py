@@ -1,0 +1,147 @@
+"""The estimate loop (Alg. 4.1) and the round scheduler on the GPU against the
+sequential oracle, including the full-size mixed-precision workload."""
+import ctypes
+
+import numpy as np
+import pytest
+import scipy.sparse.linalg as spla
+
+from gpu_common import device, lib, torch
+from oracle import fem as o_fem
+from oracle import kl as o_kl
+from oracle import mlmc as o_mlmc
+from oracle import rng as o_rng
+
+pytestmark = pytest.mark.gpu
+
+CFG1 = dict(n0=8, m=2, L_max=2, kind=0, K=16, sigma2=1.0, corr_len=0.3, seed=0)
+
+
+@pytest.fixture(scope="module")
+def M():
+    device()
+    return lib()
+
+
+def _fixed(M, N):
+    arr = (ctypes.c_int64 * len(N))(*N)
+    return arr, ctypes.cast(arr, ctypes.POINTER(ctypes.c_int64))
+
+
+def test_fixed_sample_mlmc_config1_fp64(M):
+    # 3 levels h = 1/8, 1/16, 1/32; K = 16, sigma^2 = 1, corr 0.3; N_l = 1000/500/250
+    N = [1000, 500, 250]
+    h = M.mlmc_create(M.make_problem(**CFG1), 0)
+    try:
+        o = M.mlmc_default_options()
+        o.form = M.MLMC_FORM_FP64_FIXED
+        o.fixed_delta = 1e-13
+        o.L_start = 2
+        keep, o.fixed_N = _fixed(M, N)
+        r = M.result_dict(M.mlmc_estimate(h, o))
+    finally:
+        M.mlmc_destroy(h)
+    P = o_mlmc.Problem(n0=8, m=2, L_max=2, field_kind=0, K=16, sigma2=1.0, corr_len=0.3, seed=0)
+    ref = o_mlmc.estimate_fixed(P, N)
+    assert r["N"] == N
+    assert np.allclose(r["Yhat"], ref["Yhat"], rtol=1e-9, atol=1e-15)
+    assert np.allclose(r["s2"], ref["s2"], rtol=1e-7, atol=0)
+    assert abs(r["estimate"] - ref["estimate"]) <= 1e-10 * abs(ref["estimate"])
+
+
+def test_adaptive_alg41_fp64_matches_oracle(M):
+    tol = 2e-3
+    h = M.mlmc_create(M.make_problem(**CFG1), 0)
+    try:
+        o = M.mlmc_default_options()
+        o.form = M.MLMC_FORM_FP64_ADAPTIVE
+        o.tol, o.N_init = tol, 50
+        r = M.result_dict(M.mlmc_estimate(h, o))
+    finally:
+        M.mlmc_destroy(h)
+    P = o_mlmc.Problem(n0=8, m=2, L_max=2, field_kind=0, K=16, sigma2=1.0, corr_len=0.3, seed=0)
+    ref = o_mlmc.estimate(P, tol, N_init=50)
+    # same samples, same rule: only solver tolerances delta_l separate the two
+    assert r["L"] == ref["L"]
+    assert np.all(np.abs(np.array(r["N"]) - ref["N"]) <= np.maximum(2, 0.01 * ref["N"]))
+    assert abs(r["estimate"] - ref["estimate"]) <= max(1e-3 * abs(ref["estimate"]), 0.5 * ref["rmse"])
+    assert r["rmse"] <= tol * 1.5
+
+
+def test_mixed_vs_fp64_same_samples(M):
+    # MPML and MLMC with the same N_l and seeds differ only by the computational error
+    N = [400, 200, 100]
+    out = {}
+    for form in (M.MLMC_FORM_MIXED, M.MLMC_FORM_FP64_FIXED):
+        h = M.mlmc_create(M.make_problem(**CFG1), 0)
+        try:
+            o = M.mlmc_default_options()
+            o.form = form
+            o.L_start = 2
+            keep, o.fixed_N = _fixed(M, N)
+            out[form] = M.result_dict(M.mlmc_estimate(h, o))
+        finally:
+            M.mlmc_destroy(h)
+    mp, ml = out[M.MLMC_FORM_MIXED], out[M.MLMC_FORM_FP64_FIXED]
+    deltas = np.array(mp["delta"])
+    # |dQ| <= c delta_l |Q| level by level (c covers the relative-residual -> QoI constant)
+    for l in range(3):
+        assert abs(mp["Yhat"][l] - ml["Yhat"][l]) <= 50 * deltas[l] * 0.05 + 1e-9
+    assert abs(mp["estimate"] - ml["estimate"]) <= 0.1 * ml["rmse"] if ml["rmse"] > 0 else True
+    assert mp["prec"][0] == M.MLMC_FP16S
+
+
+def test_full_size_mixed_workload_sampled(M):
+    # launch configuration of the benchmark: 5 levels h = 1/16 .. 1/256, K = 64,
+    # sigma^2 = 1, corr 0.3; finest level batch of 100 samples, FP32 master field from
+    # the tensor cores, inner precision and delta from the accuracy rule.
+    S, level, K = 100, 4, 64
+    h = M.mlmc_create(M.make_problem(n0=16, m=2, L_max=4, kind=0, K=K, sigma2=1.0, corr_len=0.3, seed=0), 0)
+    try:
+        n = 256
+        hs = [1.0 / (16 * 2 ** l) for l in range(5)]
+        deltas, precs = M.mlmc_adapt_precision(hs, 0.05)
+        a = torch.empty((S, (n + 1) ** 2), dtype=torch.float32, device=device())
+        M.mlmc_sample_fields(h, level, 0, S, None, a, M.MLMC_FP32)
+        Q = torch.empty(S, dtype=torch.float64, device=device())
+        U = torch.empty((S, (n + 1) ** 2), dtype=torch.float64, device=device())
+        rr = torch.empty(S, dtype=torch.float64, device=device())
+        fl = torch.empty(S, dtype=torch.int32, device=device())
+        M.mlmc_level_solve(h, n, S, a, M.MLMC_FP32, n, precs[4], M.MLMC_CG, deltas[4], 200000, U, Q, None, rr, fl)
+        torch.cuda.synchronize()
+        assert np.all(fl.cpu().numpy() == M.MLMC_F_CONVERGED)
+        assert np.all(rr.cpu().numpy() < deltas[4])
+        xi = o_rng.draw_xi(0, level, 0, S, K)
+        phi = o_kl.basis(0, K, n, 1.0, 0.3)
+        for s in (0, 57):
+            a_o = o_kl.coefficient(xi[s:s + 1], phi)[0]
+            x, Qo = o_fem.solve_sample(n, a_o)
+            A = o_fem.assemble(n, a_o)
+            lmin = spla.eigsh(A, k=1, sigma=0, which="LM", return_eigenvectors=False)[0]
+            g = o_fem.qoi_weights(n)
+            b = o_fem.load_vector(n)
+            u = U[s].cpu().numpy().reshape(n + 1, n + 1)[1:n, 1:n].ravel()
+            res = np.linalg.norm(b - A @ u) / np.linalg.norm(b)
+            # residual against the oracle's FP64 operator: delta plus the FP32 field's perturbation
+            assert res < deltas[4] + 4e-6
+            bound = np.linalg.norm(g) * res * np.linalg.norm(b) / lmin
+            assert abs(Q[s].item() - Qo) <= bound * 1.01
+            assert abs(Q[s].item() - Qo) <= 1e-5 * abs(Qo)
+    finally:
+        M.mlmc_destroy(h)
+
+
+def test_bench_configuration_estimate_runs_clean(M):
+    h = M.mlmc_create(M.make_problem(n0=16, m=2, L_max=4, kind=0, K=64, sigma2=1.0, corr_len=0.3, seed=0), 0)
+    try:
+        o = M.mlmc_default_options()
+        o.tol, o.L_start, o.N_init = 1e-3, 4, 100
+        r = M.result_dict(M.mlmc_estimate(h, o))
+    finally:
+        M.mlmc_destroy(h)
+    assert r["L"] == 4 and r["flags_or"] & ~M.MLMC_F_CONVERGED == 0
+    assert r["var_est"] <= (1e-3) ** 2 / 2 * 1.0001
+    assert all(nl >= 100 for nl in r["N"])
+    # E[Q] of the unit-coefficient problem is 0.0351; a lognormal coefficient with
+    # sigma^2 = 1 raises it (E[1/a] = e^{1/2} for a constant field)
+    assert 0.035 < r["estimate"] < 0.1

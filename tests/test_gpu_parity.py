@@ -1,0 +1,318 @@
+"""GPU parity of every stage of the hot path against the CPU FP64 oracle.
+
+All calls go through the C ABI (paper_2503_05533_gb300.capi).  Inputs are either
+the method's own random draws (both sides implement the Philox4x32-10 + AS241
+generator) or seeded synthetic fields from tests/inputs.py, rounded to FP32 so
+that both precisions of the GPU path see exactly the oracle's values.
+"""
+import numpy as np
+import pytest
+import scipy.sparse.linalg as spla
+
+from gpu_common import device, lib, round_storage, to_dev, torch
+from inputs import random_vectors, rough_field, smooth_lognormal_field
+from oracle import fem as o_fem
+from oracle import kl as o_kl
+from oracle import mlmc as o_mlmc
+from oracle import rng as o_rng
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def M():
+    device()
+    return lib()
+
+
+def _ctx(M, **kw):
+    base = dict(n0=8, m=2, L_max=2, kind=0, K=16, sigma2=1.0, corr_len=0.3, seed=0)
+    base.update(kw)
+    return M.mlmc_create(M.make_problem(**base), 0)
+
+
+# ---------------------------------------------------------------- A1: xi
+@pytest.mark.parametrize("seed,level,first,S,K", [(0, 0, 0, 257, 16), (7, 3, 5, 3, 7),
+                                                  ((1 << 40) + 3, 1, (1 << 32) - 2, 5, 256),
+                                                  (123, 4, 1000, 1000, 64)])
+def test_xi_bit_exact(M, seed, level, first, S, K):
+    h = _ctx(M, L_max=4, K=K, seed=seed)
+    try:
+        xi = torch.empty((S, K), dtype=torch.float64, device=device())
+        a = torch.empty((S, 9 * 9 * 2 ** (2 * level) * 4), dtype=torch.float64, device=device())
+        M.mlmc_sample_fields(h, level, first, S, xi, a, M.MLMC_FP64)
+        torch.cuda.synchronize()
+        ref = o_rng.draw_xi(seed, level, first, S, K)
+        got = xi.cpu().numpy()
+        assert np.array_equal(got.view(np.uint64), ref.view(np.uint64))
+    finally:
+        M.mlmc_destroy(h)
+
+
+# ---------------------------------------------------------------- A2: field (FP64 form)
+@pytest.mark.parametrize("kind,K,n0,sigma2,corr", [(0, 16, 8, 1.0, 0.3), (0, 64, 12, 1.5, 0.1),
+                                                   (1, 4, 8, 4.0, 0.3), (2, 1, 6, 0.49, 0.3)])
+def test_field_fp64(M, kind, K, n0, sigma2, corr):
+    h = _ctx(M, n0=n0, L_max=1, kind=kind, K=K, sigma2=sigma2, corr_len=corr, seed=5)
+    try:
+        S, n = 37, 2 * n0
+        xi = torch.empty((S, K), dtype=torch.float64, device=device())
+        a = torch.empty((S, (n + 1) ** 2), dtype=torch.float64, device=device())
+        M.mlmc_sample_fields(h, 1, 100, S, xi, a, M.MLMC_FP64)
+        torch.cuda.synchronize()
+        ref = o_kl.coefficient(o_rng.draw_xi(5, 1, 100, S, K), o_kl.basis(kind, K, n, sigma2, corr, 2.0))
+        assert np.allclose(a.cpu().numpy(), ref, rtol=1e-13, atol=0)
+    finally:
+        M.mlmc_destroy(h)
+
+
+def test_synthesize_from_given_xi(M):
+    h = _ctx(M, L_max=1, K=16)
+    try:
+        S, n = 9, 16
+        xi_np = np.random.default_rng(3).standard_normal((S, 16))
+        a = torch.empty((S, (n + 1) ** 2), dtype=torch.float64, device=device())
+        M.mlmc_synthesize_fields(h, 1, S, to_dev(xi_np), a, M.MLMC_FP64)
+        torch.cuda.synchronize()
+        ref = o_kl.coefficient(xi_np, o_kl.basis(0, 16, n, 1.0, 0.3))
+        assert np.allclose(a.cpu().numpy(), ref, rtol=1e-13, atol=0)
+    finally:
+        M.mlmc_destroy(h)
+
+
+# ---------------------------------------------------------------- A3/A4: operator
+def _oracle_apply(n, a_nodal, x_nodal):
+    A = o_fem.assemble(n, a_nodal)
+    X = x_nodal.reshape(n + 1, n + 1)[1:n, 1:n].ravel()
+    y = np.zeros((n + 1, n + 1))
+    y[1:n, 1:n] = (A @ X).reshape(n - 1, n - 1)
+    return y.ravel()
+
+
+@pytest.mark.parametrize("n,stride", [(2, 1), (5, 1), (13, 1), (16, 2), (33, 1), (64, 2)])
+def test_operator_fp64_matches_element_assembly(M, n, stride):
+    S = 3
+    a_n = n * stride
+    af = rough_field(a_n, S, seed=n)
+    x = random_vectors(n, S, seed=n + 1)
+    y = torch.empty((S, (n + 1) ** 2), dtype=torch.float64, device=device())
+    M.mlmc_apply_operator(n, S, to_dev(af), M.MLMC_FP64, a_n, M.MLMC_FP64, to_dev(x), y, M.MLMC_FP64)
+    torch.cuda.synchronize()
+    got = y.cpu().numpy()
+    for s in range(S):
+        ac = af[s].reshape(a_n + 1, a_n + 1)[::stride, ::stride].ravel()
+        ref = _oracle_apply(n, ac, x[s])
+        assert np.max(np.abs(got[s] - ref)) <= 1e-14 * max(1.0, np.max(np.abs(ref)))
+
+
+@pytest.mark.parametrize("op", ["FP32", "BF16S", "FP16S"])
+def test_operator_storage_precisions(M, op):
+    prec = getattr(M, "MLMC_" + op)
+    n, S = 31, 2
+    af = smooth_lognormal_field(n, S, seed=2)
+    x = random_vectors(n, S, seed=3)
+    y = torch.empty((S, (n + 1) ** 2), dtype=torch.float32, device=device())
+    M.mlmc_apply_operator(n, S, to_dev(af, torch.float32), M.MLMC_FP32, n, prec, to_dev(x, torch.float32), y,
+                          M.MLMC_FP32)
+    torch.cuda.synchronize()
+    got = y.cpu().numpy().astype(np.float64)
+    for s in range(S):
+        ref = _oracle_apply(n, round_storage(af[s], prec, M), x[s])
+        assert np.max(np.abs(got[s] - ref)) <= 2e-6 * np.max(np.abs(ref))
+
+
+# ---------------------------------------------------------------- A5-A7: solves
+def _solve(M, h, n, a_np, a_prec, a_n, prec, delta, max_iters=200000, u=True):
+    S = a_np.shape[0]
+    dt = torch.float64 if a_prec == M.MLMC_FP64 else torch.float32
+    a = to_dev(a_np, dt)
+    U = torch.zeros((S, (n + 1) ** 2), dtype=torch.float64, device=device()) if u else None
+    Q = torch.empty(S, dtype=torch.float64, device=device())
+    it = torch.zeros(S, dtype=torch.int32, device=device())
+    rr = torch.zeros(S, dtype=torch.float64, device=device())
+    fl = torch.zeros(S, dtype=torch.int32, device=device())
+    M.mlmc_level_solve(h, n, S, a, a_prec, a_n, prec, M.MLMC_CG, delta, max_iters, U, Q, it, rr, fl)
+    torch.cuda.synchronize()
+    return (U.cpu().numpy() if u else None), Q.cpu().numpy(), it.cpu().numpy(), rr.cpu().numpy(), fl.cpu().numpy()
+
+
+def _interior(n, u):
+    return u.reshape(n + 1, n + 1)[1:n, 1:n].ravel()
+
+
+@pytest.mark.parametrize("n", [2, 3, 8, 13, 32, 64])
+def test_solve_fp64_matches_cholesky(M, n):
+    h = _ctx(M)
+    try:
+        S = 5
+        af = smooth_lognormal_field(n, S, seed=10 + n, log_sd=1.0)
+        U, Q, it, rr, fl = _solve(M, h, n, af, M.MLMC_FP64, n, M.MLMC_FP64, 1e-13)
+        for s in range(S):
+            x, Qo = o_fem.solve_sample(n, af[s])
+            assert abs(Q[s] - Qo) <= 1e-12 * abs(Qo)
+            assert np.max(np.abs(_interior(n, U[s]) - x)) <= 1e-11 * np.max(np.abs(x))
+            assert fl[s] == M.MLMC_F_CONVERGED and rr[s] < 1e-13
+            assert o_fem.relative_residual(n, af[s], _interior(n, U[s])) < 2e-13
+            # boundary of the returned solution is exactly zero
+            B = U[s].reshape(n + 1, n + 1)
+            assert not B[0].any() and not B[-1].any() and not B[:, 0].any() and not B[:, -1].any()
+    finally:
+        M.mlmc_destroy(h)
+
+
+@pytest.mark.parametrize("prec", ["FP32", "BF16S", "FP16S"])
+@pytest.mark.parametrize("delta", [3.5e-3, 1e-6, 1e-9])
+def test_solve_mixed_reaches_delta(M, prec, delta):
+    p = getattr(M, "MLMC_" + prec)
+    h = _ctx(M)
+    try:
+        n, S = 32, 6
+        af = smooth_lognormal_field(n, S, seed=77, log_sd=1.2)
+        U, Q, it, rr, fl = _solve(M, h, n, af, M.MLMC_FP32, n, p, delta)
+        assert np.all(fl == M.MLMC_F_CONVERGED), fl
+        for s in range(S):
+            x, Qo = o_fem.solve_sample(n, af[s])
+            res = o_fem.relative_residual(n, af[s], _interior(n, U[s]))
+            assert res < delta * (1 + 1e-6) and abs(res - rr[s]) <= 1e-6 * res + 1e-15
+            # rigorous QoI bound |dQ| <= ||g|| ||r|| / lambda_min(A)
+            A = o_fem.assemble(n, af[s])
+            lmin = spla.eigsh(A, k=1, sigma=0, which="LM", return_eigenvectors=False)[0]
+            b = o_fem.load_vector(n)
+            g = o_fem.qoi_weights(n)
+            bound = np.linalg.norm(g) * res * np.linalg.norm(b) / lmin
+            assert abs(Q[s] - Qo) <= bound * 1.01
+            if delta <= 1e-9:
+                assert abs(Q[s] - Qo) <= 1e-6 * abs(Qo)
+    finally:
+        M.mlmc_destroy(h)
+
+
+def test_coarse_view_solve(M):
+    h = _ctx(M)
+    try:
+        nf, S = 32, 4
+        af = smooth_lognormal_field(nf, S, seed=5)
+        _, Q, _, _, fl = _solve(M, h, nf // 2, af, M.MLMC_FP32, nf, M.MLMC_FP32, 1e-10, u=False)
+        for s in range(S):
+            _, Qo = o_fem.solve_sample(nf // 2, o_fem.coarse_view(af[s], nf))
+            assert abs(Q[s] - Qo) <= 1e-7 * abs(Qo)
+        assert np.all(fl == M.MLMC_F_CONVERGED)
+    finally:
+        M.mlmc_destroy(h)
+
+
+def test_box_qoi(M):
+    h = _ctx(M, qoi=1, box=(0.25, 0.75, 0.25, 0.75))
+    try:
+        n, S = 16, 3
+        af = smooth_lognormal_field(n, S, seed=9)
+        _, Q, _, _, _ = _solve(M, h, n, af, M.MLMC_FP64, n, M.MLMC_FP64, 1e-13, u=False)
+        for s in range(S):
+            _, Qo = o_fem.solve_sample(n, af[s], box=(0.25, 0.75, 0.25, 0.75))
+            assert abs(Q[s] - Qo) <= 1e-12 * abs(Qo)
+    finally:
+        M.mlmc_destroy(h)
+
+
+def test_solve_edge_cases(M):
+    h = _ctx(M)
+    try:
+        # S = 0 is a no-op
+        Q = torch.zeros(1, dtype=torch.float64, device=device())
+        M.mlmc_level_solve(h, 8, 0, Q, M.MLMC_FP64, 8, M.MLMC_FP64, M.MLMC_CG, 1e-8, 10, None, Q)
+        # max_iters = 1 stops early with MAXIT
+        af = smooth_lognormal_field(32, 2, seed=4)
+        _, _, it, rr, fl = _solve(M, h, 32, af, M.MLMC_FP64, 32, M.MLMC_FP64, 1e-12, max_iters=1, u=False)
+        assert np.all(fl == M.MLMC_F_MAXIT) and np.all(it <= 1) and np.all(rr > 1e-12)
+        # a NaN in the coefficient is reported, not propagated silently
+        bad = af.copy()
+        bad[1, 100] = np.nan
+        _, Qb, _, _, flb = _solve(M, h, 32, bad, M.MLMC_FP64, 32, M.MLMC_FP64, 1e-10, u=False)
+        assert flb[1] == M.MLMC_F_NONFINITE and flb[0] == M.MLMC_F_CONVERGED
+        # delta above 1: x = 0 already satisfies the criterion
+        _, Q0, it0, _, fl0 = _solve(M, h, 8, af[:, : 81], M.MLMC_FP64, 8, M.MLMC_FP64, 2.0, u=False)
+        assert np.all(Q0 == 0.0) and np.all(it0 == 0) and np.all(fl0 == M.MLMC_F_CONVERGED)
+        # argument errors
+        with pytest.raises(M.MlmcError):
+            M.mlmc_level_solve(h, 1, 1, Q, M.MLMC_FP64, 1, M.MLMC_FP64, M.MLMC_CG, 1e-8, 10, None, Q)
+        with pytest.raises(M.MlmcError):
+            M.mlmc_level_solve(h, 8, 1, Q, M.MLMC_FP64, 12, M.MLMC_FP64, M.MLMC_CG, 1e-8, 10, None, Q)
+    finally:
+        M.mlmc_destroy(h)
+
+
+def test_mixed_batch_many_sizes_one_launch(M):
+    # several grid sizes in one persistent launch through the estimate scheduler's path
+    h = _ctx(M, n0=6, L_max=3)
+    try:
+        for n in (6, 12, 24, 48):
+            af = smooth_lognormal_field(n, 3, seed=n)
+            _, Q, _, _, fl = _solve(M, h, n, af, M.MLMC_FP32, n, M.MLMC_FP16S, 1e-7, u=False)
+            assert np.all(fl == M.MLMC_F_CONVERGED)
+            for s in range(3):
+                assert abs(Q[s] - o_fem.solve_sample(n, af[s])[1]) <= 1e-5 * abs(Q[s])
+    finally:
+        M.mlmc_destroy(h)
+
+
+def test_barrier_timeout_is_reported_and_gpu_stays_usable(M):
+    h = _ctx(M)
+    try:
+        M.mlmc_set_wait_timeout(h, 0.2)
+        M.mlmc_debug_set_barrier_extra(h, 1)
+        af = smooth_lognormal_field(16, 2, seed=1)
+        with pytest.raises(M.MlmcError) as ei:
+            _solve(M, h, 16, af, M.MLMC_FP64, 16, M.MLMC_FP64, 1e-10, u=False)
+        assert ei.value.status == M.MLMC_E_TIMEOUT
+        M.mlmc_debug_set_barrier_extra(h, 0)
+        _, Q, _, _, fl = _solve(M, h, 16, af, M.MLMC_FP64, 16, M.MLMC_FP64, 1e-12, u=False)
+        assert np.all(fl == M.MLMC_F_CONVERGED)
+        assert abs(Q[0] - o_fem.solve_sample(16, af[0])[1]) <= 1e-11 * abs(Q[0])
+    finally:
+        M.mlmc_destroy(h)
+
+
+# ---------------------------------------------------------------- A8: statistics
+def test_level_stats(M):
+    h = _ctx(M)
+    try:
+        for S in (1, 2, 255, 1000, 4097):
+            g = np.random.default_rng(S)
+            Qf = g.standard_normal(S) * 1e-3 + 0.05
+            Qc = Qf - (g.standard_normal(S) * 1e-5 + 2e-4)
+            acc = M.mlmc_level_stats(h, S, to_dev(Qf), to_dev(Qc))
+            Y = Qf - Qc
+            m, v = o_mlmc.mean_var(Y)
+            assert acc.n == S
+            assert abs(acc.mean - m) <= 1e-13 * abs(m)
+            assert abs(acc.m2 / S - v) <= 1e-9 * v + 1e-30
+            assert abs((acc.sum + acc.sum_c) - np.sum(Y)) <= 1e-13 * abs(np.sum(Y))
+        acc0 = M.mlmc_level_stats(h, 3, to_dev(np.ones(3)), None)
+        assert acc0.n == 3 and acc0.mean == 1.0 and acc0.m2 == 0.0
+    finally:
+        M.mlmc_destroy(h)
+
+
+# ---------------------------------------------------------------- pipeline A1-A8
+def test_level_pipeline_matches_oracle_sampler(M):
+    seed = 21
+    h = _ctx(M, n0=8, L_max=2, K=16, seed=seed)
+    P = o_mlmc.Problem(n0=8, m=2, L_max=2, field_kind=0, K=16, sigma2=1.0, corr_len=0.3, seed=seed)
+    try:
+        for level in (0, 1, 2):
+            S, n = 40, 8 * 2 ** level
+            a = torch.empty((S, (n + 1) ** 2), dtype=torch.float64, device=device())
+            M.mlmc_sample_fields(h, level, 3, S, None, a, M.MLMC_FP64)
+            Qf = torch.empty(S, dtype=torch.float64, device=device())
+            M.mlmc_level_solve(h, n, S, a, M.MLMC_FP64, n, M.MLMC_FP64, M.MLMC_CG, 1e-13, 100000, None, Qf)
+            Qc = torch.zeros(S, dtype=torch.float64, device=device())
+            if level > 0:
+                M.mlmc_level_solve(h, n // 2, S, a, M.MLMC_FP64, n, M.MLMC_FP64, M.MLMC_CG, 1e-13, 100000, None, Qc)
+            acc = M.mlmc_level_stats(h, S, Qf, Qc if level > 0 else None)
+            qf_o, qc_o = P.level_samples(level, 3, S)
+            assert np.allclose(Qf.cpu().numpy(), qf_o, rtol=1e-11, atol=0)
+            assert np.allclose(Qc.cpu().numpy(), qc_o, rtol=1e-11, atol=0)
+            m, v = o_mlmc.mean_var(qf_o - qc_o)
+            assert abs(acc.mean - m) <= 1e-9 * abs(m) and abs(acc.m2 / S - v) <= 1e-6 * v
+    finally:
+        M.mlmc_destroy(h)
