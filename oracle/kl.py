@@ -19,7 +19,9 @@ sigma and the eigenvalues are folded into Phi_k.  Three kinds:
   for closed-form checks.
 
 Here the roots are bracketed by a sign scan and refined by Brent's method and
-the eigenfunctions are normalised by Gauss-Legendre quadrature.
+the eigenfunctions are normalised by composite Gauss-Legendre quadrature
+(64 panels of 24 points: exact to rounding for every oscillation frequency
+used here, unlike a single high-order rule whose weights lose ~1e-13).
 """
 import numpy as np
 from scipy.optimize import brentq
@@ -46,13 +48,22 @@ def expcov_roots(lam, count):
     return np.array(roots[:count])
 
 
-def expcov_1d(lam, count, quad_points=4000):
+def composite_gauss(panels=64, points=24):
+    """Nodes and weights of a composite Gauss-Legendre rule on [0, 1]."""
+    t, wt = np.polynomial.legendre.leggauss(points)
+    nodes, weights = [], []
+    for p in range(panels):
+        a, b = p / panels, (p + 1) / panels
+        nodes.append(a + (b - a) * 0.5 * (t + 1.0))
+        weights.append((b - a) * 0.5 * wt)
+    return np.concatenate(nodes), np.concatenate(weights)
+
+
+def expcov_1d(lam, count, panels=64):
     """(theta[count], w[count], norm[count]) with b_i(t) = (sin(w t) + lam w cos(w t)) / norm."""
     w = expcov_roots(lam, count)
     theta = 2.0 * lam / (1.0 + lam * lam * w * w)
-    t, wt = np.polynomial.legendre.leggauss(quad_points)
-    t = 0.5 * (t + 1.0)
-    wt = 0.5 * wt
+    t, wt = composite_gauss(panels)
     vals = np.sin(np.outer(w, t)) + (lam * w)[:, None] * np.cos(np.outer(w, t))
     norm = np.sqrt((vals * vals) @ wt)
     return theta, w, norm

@@ -34,10 +34,14 @@ def test_expcov_eigenpairs_satisfy_integral_equation(lam):
 
 @pytest.mark.parametrize("lam", [0.1, 0.3])
 def test_expcov_orthonormal_and_one_root_per_interval(lam):
+    # normalisation against the closed form of int_0^1 (sin wt + lam w cos wt)^2 dt
+    th, ww, nn = kl.expcov_1d(lam, 12)
+    closed = np.sqrt(0.5 - np.sin(2 * ww) / (4 * ww) + lam * np.sin(ww) ** 2 +
+                     lam ** 2 * ww ** 2 * (0.5 + np.sin(2 * ww) / (4 * ww)))
+    assert np.max(np.abs(nn - closed) / closed) < 2e-15
     M = 40
     theta, w, norm = kl.expcov_1d(lam, M)
-    t, wt = np.polynomial.legendre.leggauss(3000)
-    t, wt = 0.5 * (t + 1.0), 0.5 * wt
+    t, wt = kl.composite_gauss(128, 24)
     B = kl.expcov_1d_eval(lam, w, norm, t)
     assert np.max(np.abs((B * wt) @ B.T - np.eye(M))) < 1e-12
     # a missed or duplicated root breaks this: exactly one root in (i pi, (i+1) pi)
@@ -49,7 +53,7 @@ def test_expcov_trace():
     # sum of all 1D eigenvalues = int_0^1 C(t, t) dt = 1; the tail beyond M modes is
     # about sum 2 / (lam w^2) ~ 2 / (lam pi^2 M)
     lam, M = 0.3, 400
-    theta, w, _ = kl.expcov_1d(lam, M, quad_points=200)
+    theta, w, _ = kl.expcov_1d(lam, M, panels=4)
     s = theta.sum()
     assert s < 1.0
     assert 1.0 - s < 2.0 / (lam * np.pi ** 2 * (M - 1))
@@ -78,8 +82,7 @@ def test_basis_pointwise_variance_and_orthogonality():
     assert np.all((phi ** 2).sum(axis=0) <= sigma2 * (1 + 1e-12))
     # the constant-in-mean variance integral equals the sum of eigenvalues
     _, lam2d, _ = kl.expcov_modes(sigma2, lam, K)
-    t, wt = np.polynomial.legendre.leggauss(200)
-    t, wt = 0.5 * (t + 1.0), 0.5 * wt
+    t, wt = kl.composite_gauss(32, 24)
     modes, _, (theta, w, norm) = kl.expcov_modes(sigma2, lam, K)
     B = kl.expcov_1d_eval(lam, w, norm, t)
     gram = np.empty((K, K))
