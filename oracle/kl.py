@@ -75,17 +75,28 @@ def expcov_1d_eval(lam, w, norm, t):
     return (np.sin(np.outer(w, t)) + (lam * w)[:, None] * np.cos(np.outer(w, t))) / norm[:, None]
 
 
+TIE_RTOL = 1e-12
+
+
 def expcov_modes(sigma2, lam, K):
-    """The K leading 2D modes: list of (i, j) and their eigenvalues sigma^2 theta_i theta_j."""
+    """The K leading 2D modes: list of (i, j) and their eigenvalues sigma^2 theta_i theta_j.
+
+    Order: theta_i theta_j descending; values within TIE_RTOL (relative) of the
+    first value of a run count as tied -- (i, j) and (j, i) are exact ties of
+    the true eigenvalues -- and a run of ties is ordered by (i + j, i)."""
     m1 = max(K, 8)
     theta, w, norm = expcov_1d(lam, m1)
-    cand = []
-    for i in range(m1):
-        for j in range(m1):
-            cand.append((-(sigma2 * theta[i] * theta[j]), i + j, i, j))
-    cand.sort()
-    modes = [(c[2], c[3]) for c in cand[:K]]
-    lam2d = np.array([-c[0] for c in cand[:K]])
+    cand = sorted(((theta[i] * theta[j], i, j) for i in range(m1) for j in range(m1)), key=lambda c: -c[0])
+    ordered = []
+    start = 0
+    while start < len(cand):
+        end = start + 1
+        while end < len(cand) and cand[start][0] - cand[end][0] <= TIE_RTOL * cand[start][0]:
+            end += 1
+        ordered.extend(sorted(cand[start:end], key=lambda c: (c[1] + c[2], c[1])))
+        start = end
+    modes = [(c[1], c[2]) for c in ordered[:K]]
+    lam2d = np.array([sigma2 * c[0] for c in ordered[:K]])
     return modes, lam2d, (theta, w, norm)
 
 

@@ -11,14 +11,14 @@
 //     L^2(0,1) norm of b is the closed form
 //       1/2 - sin(2w)/(4w) + lam sin^2 w + lam^2 w^2 (1/2 + sin(2w)/(4w)).
 //     2D modes are products b_i(x1) b_j(x2) with eigenvalue sigma^2 theta_i theta_j,
-//     ordered by eigenvalue (descending), then i + j, then i (ascending).
+//     ordered by theta_i theta_j descending; values within a relative 1e-12 of a
+//     run's first value are ties, ordered by i + j, then i (ascending).
 //  1  Eq. (5.2): Phi_j = sigma j^-q sin(2 pi j x1) cos(2 pi j x2), j = 1..K.
 //  2  a single constant mode Phi_0 = sigma.
 // Every mode is separable, Phi_k(x_i, y_j) = c_k bx_k(x_i) by_k(y_j); the
 // tables (c, bx, by) are built here and expanded on the device.
 #include <algorithm>
 #include <cmath>
-#include <tuple>
 #include <vector>
 
 #include "internal.h"
@@ -82,18 +82,34 @@ void expcov_modes(double sigma2, double lam, int K, std::vector<int>& mi, std::v
                   std::vector<double>& eig, Basis1D& b1) {
     const int m1 = std::max(K, 8);
     b1 = expcov_1d(lam, m1);
-    std::vector<std::tuple<double, int, int, int>> cand;
+    struct Cand {
+        double v;
+        int i, j;
+    };
+    std::vector<Cand> cand;
     cand.reserve((size_t)m1 * m1);
     for (int i = 0; i < m1; ++i)
-        for (int j = 0; j < m1; ++j) cand.emplace_back(-(sigma2 * b1.theta[i] * b1.theta[j]), i + j, i, j);
-    std::partial_sort(cand.begin(), cand.begin() + K, cand.end());
+        for (int j = 0; j < m1; ++j) cand.push_back({b1.theta[i] * b1.theta[j], i, j});
+    std::stable_sort(cand.begin(), cand.end(), [](const Cand& a, const Cand& b) { return a.v > b.v; });
+    // Runs of values within kTieRtol of the run's first value are ties (theta_i theta_j and
+    // theta_j theta_i are equal eigenvalues); a run is ordered by (i + j, i).
+    const double kTieRtol = 1e-12;
+    size_t start = 0;
+    while (start < cand.size()) {
+        size_t end = start + 1;
+        while (end < cand.size() && cand[start].v - cand[end].v <= kTieRtol * cand[start].v) ++end;
+        std::sort(cand.begin() + start, cand.begin() + end, [](const Cand& a, const Cand& b) {
+            return (a.i + a.j != b.i + b.j) ? (a.i + a.j < b.i + b.j) : (a.i < b.i);
+        });
+        start = end;
+    }
     mi.resize(K);
     mj.resize(K);
     eig.resize(K);
     for (int k = 0; k < K; ++k) {
-        eig[k] = -std::get<0>(cand[k]);
-        mi[k] = std::get<2>(cand[k]);
-        mj[k] = std::get<3>(cand[k]);
+        eig[k] = sigma2 * cand[k].v;
+        mi[k] = cand[k].i;
+        mj[k] = cand[k].j;
     }
 }
 
