@@ -22,6 +22,14 @@ def to_dev(x, dtype=torch.float64):
     return torch.as_tensor(np.ascontiguousarray(x)).to(device=device(), dtype=dtype)
 
 
+def fp64_delta(n):
+    """Tightest relative residual to ask of an FP64 solve on an n x n grid.
+
+    Cor. 3.4 condition 2 needs c (1 + h^-2) u < delta: merely storing x in FP64
+    leaves a residual of order (1 + n^2) 2^-53, so delta must stay above it."""
+    return max(1e-13, 2.0 * (1.0 + n * n) * 2.0 ** -53)
+
+
 def round_storage(a, prec, M):
     """Round nodal values the way the operator's storage type does (inputs are FP32-exact)."""
     a = np.asarray(a, dtype=np.float64)

@@ -2,7 +2,7 @@
 import numpy as np
 import pytest
 
-from gpu_common import device, lib, to_dev, torch
+from gpu_common import device, fp64_delta, lib, to_dev, torch
 from oracle import adjoint as o_adj
 from oracle import kl as o_kl
 
@@ -32,7 +32,7 @@ def test_gradient_fp64_matches_cpu_adjoint(M, box):
     h = M.mlmc_create(M.make_problem(**kw), 0)
     try:
         xi = np.random.default_rng(5).standard_normal((3, 24))
-        Q, g = _grad(M, h, 0, xi, M.MLMC_FP64, 1e-14)
+        Q, g = _grad(M, h, 0, xi, M.MLMC_FP64, fp64_delta(16))
         phi = o_kl.basis(0, 24, 16, 1.0, 0.1)
         for s in range(3):
             Qo, go = o_adj.gradient(16, xi[s], phi, box)
@@ -46,7 +46,7 @@ def test_gradient_matches_central_differences_on_gpu(M):
     h = M.mlmc_create(M.make_problem(n0=32, m=2, L_max=0, kind=0, K=8, sigma2=1.0, corr_len=0.1, seed=0), 0)
     try:
         xi = np.random.default_rng(6).standard_normal((1, 8))
-        _, g = _grad(M, h, 0, xi, M.MLMC_FP64, 1e-14)
+        _, g = _grad(M, h, 0, xi, M.MLMC_FP64, fp64_delta(32))
         eps = 1e-6
         pert = np.repeat(xi, 16, axis=0)
         for k in range(8):
@@ -55,7 +55,7 @@ def test_gradient_matches_central_differences_on_gpu(M):
         a = torch.empty((16, 33 * 33), dtype=torch.float64, device=device())
         M.mlmc_synthesize_fields(h, 0, 16, to_dev(pert), a, M.MLMC_FP64)
         Q = torch.empty(16, dtype=torch.float64, device=device())
-        M.mlmc_level_solve(h, 32, 16, a, M.MLMC_FP64, 32, M.MLMC_FP64, M.MLMC_CG, 1e-14, 100000, None, Q)
+        M.mlmc_level_solve(h, 32, 16, a, M.MLMC_FP64, 32, M.MLMC_FP64, M.MLMC_CG, fp64_delta(32), 100000, None, Q)
         torch.cuda.synchronize()
         Qn = Q.cpu().numpy()
         fd = (Qn[0::2] - Qn[1::2]) / (2 * eps)
@@ -84,7 +84,7 @@ def test_autograd_function(M):
     try:
         xi_np = np.random.default_rng(9).standard_normal((5, 12))
         xi = to_dev(xi_np).requires_grad_(True)
-        Q = AG.qoi(xi, h, 0, 16, M.MLMC_FP64, 1e-14)
+        Q = AG.qoi(xi, h, 0, 16, M.MLMC_FP64, fp64_delta(16))
         w = torch.arange(1, 6, dtype=torch.float64, device=device())
         (Q * w).sum().backward()
         phi = o_kl.basis(0, 12, 16, 1.0, 0.2)

@@ -35,7 +35,7 @@ def test_fixed_sample_mlmc_config1_fp64(M):
     try:
         o = M.mlmc_default_options()
         o.form = M.MLMC_FORM_FP64_FIXED
-        o.fixed_delta = 1e-13
+        o.fixed_delta = 2e-13          # above the FP64 floor (1 + h^-2) u of the h = 1/32 level
         o.L_start = 2
         keep, o.fixed_N = _fixed(M, N)
         r = M.result_dict(M.mlmc_estimate(h, o))
