@@ -39,7 +39,9 @@ def test_tensor_core_field_matches_oracle(M, kind, K, n0, sigma2, corr, S):
         err = np.abs(np.log(got) - loga)
         assert np.all(np.isfinite(got))
         assert np.all(err <= 2e-6 * np.maximum(scale, 1.0)), err.max()
-        assert np.median(err) < 3e-7
+        # FP32 accumulation of K terms: typical error ~ sqrt(K) u_32 |log a|
+        rms = float(np.sqrt(np.mean(loga ** 2)))
+        assert np.median(err) < max(3e-7, 6e-8 * np.sqrt(K) * max(1.0, rms))
     finally:
         M.mlmc_destroy(h)
 
