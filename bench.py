@@ -180,6 +180,9 @@ def main():
     ap.add_argument("--impl", default="libmlmc", choices=["libmlmc", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-fp64", action="store_true")
+    ap.add_argument("--case", default="mlmc", choices=["mlmc", "solve-l4"],
+                    help="solve-l4: only the finest level's batch (100 samples, n = 256) of the workload: "
+                         "field synthesis and one persistent solve launch per step")
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)
@@ -211,6 +214,9 @@ def main():
 
     flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
     stream = torch.cuda.current_stream()
+
+    if args.case == "solve-l4":
+        return solve_l4_case(M, torch, dev, args, problem(1000), hbm_peak, peak_src, flush, stream)
 
     def timed_runs(form, steps, warmup, seed0, profile=False):
         h = M.mlmc_create(problem(seed0), local)
@@ -315,6 +321,46 @@ def main():
                                     "sample": sample + " (FP64 banded Cholesky, fine+coarse per sample), "
                                               "extrapolated to the estimate's N_l"}
         print(json.dumps(line))
+    return 0
+
+
+def solve_l4_case(M, torch, dev, args, prob, hbm_peak, peak_src, flush, stream):
+    """The dominant launch of the workload in isolation: the finest level's 100 fine systems
+    (n = 256) with the accuracy and inner precision the rule assigns to level 4."""
+    S, level, n = N_INIT, WORKLOAD["L_max"], WORKLOAD["n0"] * WORKLOAD["m"] ** WORKLOAD["L_max"]
+    hs = [1.0 / (WORKLOAD["n0"] * WORKLOAD["m"] ** l) for l in range(level + 1)]
+    deltas, precs = M.mlmc_adapt_precision(hs, 0.05)
+    h = M.mlmc_create(prob, dev.index or 0)
+    try:
+        M.mlmc_profile_enable(h, True)
+        a = torch.empty((S, (n + 1) ** 2), dtype=torch.float32, device=dev)
+        Q = torch.empty(S, dtype=torch.float64, device=dev)
+        it = torch.empty(S, dtype=torch.int32, device=dev)
+        ms = []
+        for s in range(args.warmup + args.steps):
+            if s == args.warmup:
+                M.mlmc_profile_reset(h)
+            flush.fill_(float(s))
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            M.mlmc_sample_fields(h, level, s * S, S, None, a, M.MLMC_FP32)
+            M.mlmc_level_solve(h, n, S, a, M.MLMC_FP32, n, precs[level], M.MLMC_CG, deltas[level], 200000,
+                               None, Q, it)
+            e1.record(stream)
+            e1.synchronize()
+            if s >= args.warmup:
+                ms.append(e0.elapsed_time(e1))
+        prof = M.mlmc_profile_get(h)
+    finally:
+        M.mlmc_destroy(h)
+    achieved = prof["solve_bytes"] / (prof["solve_ms"] * 1e-3) / 1e9
+    print(json.dumps({"case": "solve-l4", "ms_per_step": sum(ms) / len(ms), "systems": S, "n": n,
+                      "delta": deltas[level], "prec": precs[level],
+                      "inner_iters_per_system": prof["inner_iters"] / (S * args.steps),
+                      "solve_ms_per_launch": prof["solve_ms"] / prof["solve_launches"],
+                      "algorithmic_bytes_per_launch": prof["solve_bytes"] / prof["solve_launches"],
+                      "achieved_gbs": achieved, "peak_gbs": hbm_peak, "frac": achieved / hbm_peak,
+                      "peak_source": peak_src}))
     return 0
 
 
