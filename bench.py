@@ -180,9 +180,11 @@ def main():
     ap.add_argument("--impl", default="libmlmc", choices=["libmlmc", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-fp64", action="store_true")
-    ap.add_argument("--case", default="mlmc", choices=["mlmc", "solve-l4"],
+    ap.add_argument("--case", default="mlmc", choices=["mlmc", "solve-l4", "kl-synth"],
                     help="solve-l4: only the finest level's batch (100 samples, n = 256) of the workload: "
-                         "field synthesis and one persistent solve launch per step")
+                         "field synthesis and one persistent solve launch per step; kl-synth: tensor-core "
+                         "KL synthesis alone at the single-level sweep shapes (n = 512, K = 128, corr 0.1)")
+    ap.add_argument("--kl-samples", type=int, default=4096)
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)
@@ -217,6 +219,8 @@ def main():
 
     if args.case == "solve-l4":
         return solve_l4_case(M, torch, dev, args, problem(1000), hbm_peak, peak_src, flush, stream)
+    if args.case == "kl-synth":
+        return kl_synth_case(M, torch, dev, args, hbm_peak, peak_src, flush, stream)
 
     def timed_runs(form, steps, warmup, seed0, profile=False):
         h = M.mlmc_create(problem(seed0), local)
@@ -321,6 +325,33 @@ def main():
                                     "sample": sample + " (FP64 banded Cholesky, fine+coarse per sample), "
                                               "extrapolated to the estimate's N_l"}
         print(json.dumps(line))
+    return 0
+
+
+def kl_synth_case(M, torch, dev, args, hbm_peak, peak_src, flush, stream):
+    """Tensor-core KL synthesis alone: S samples on the 512 x 512 grid, K = 128, corr 0.1."""
+    S, n, K = args.kl_samples, 512, 128
+    prob = M.make_problem(n0=n, m=2, L_max=0, kind=0, K=K, sigma2=1.0, corr_len=0.1, seed=7)
+    h = M.mlmc_create(prob, dev.index or 0)
+    try:
+        M.mlmc_profile_enable(h, True)
+        a = torch.empty((S, (n + 1) ** 2), dtype=torch.float32, device=dev)
+        xi = torch.empty((S, K), dtype=torch.float64, device=dev)
+        M.mlmc_sample_fields(h, 0, 0, S, xi, a, M.MLMC_FP32)
+        for s in range(args.warmup + args.steps):
+            if s == args.warmup:
+                M.mlmc_profile_reset(h)
+            flush.fill_(float(s))
+            M.mlmc_synthesize_fields(h, 0, S, xi, a, M.MLMC_FP32)
+        prof = M.mlmc_profile_get(h)
+    finally:
+        M.mlmc_destroy(h)
+    ms = prof["kl_ms"] / prof["kl_launches"]
+    gbs = prof["kl_bytes"] / prof["kl_launches"] / (ms * 1e-3) / 1e9
+    tf = prof["kl_flops"] / prof["kl_launches"] / (ms * 1e-3) / 1e12
+    print(json.dumps({"case": "kl-synth", "samples": S, "n": n, "K": K, "ms_per_launch": ms,
+                      "algorithmic_bytes_per_launch": prof["kl_bytes"] / prof["kl_launches"], "achieved_gbs": gbs,
+                      "hbm_frac": gbs / hbm_peak, "executed_tensor_tflops": tf, "peak_source": peak_src}))
     return 0
 
 
