@@ -180,6 +180,42 @@ mlmc_status mlmc_level_solve(mlmc_ctx* ctx, int n, int S, const void* a, mlmc_pr
                              void* stream);
 
 /* ------------------------------------------------------------------------- */
+/* Allocation-free variant of mlmc_level_solve.  The paper has no counterpart:
+ * this entry point exists for callers that cannot allocate device memory --
+ * a host application or plug-in framework that owns all device memory and
+ * hands the library only its own buffers, or a serving loop that forbids
+ * allocation after start-up (cudaMalloc can synchronise the device, and it
+ * fails once a memory pool has reserved the device).  It solves like
+ * mlmc_level_solve (same method, kernel and outputs) but takes no context and
+ * calls no cudaMalloc, cudaFree or allocating library routine, on the device
+ * or the host: the solver's scratch (vectors, partial sums, descriptors, grid
+ * barrier) lives in one file-scope __device__ array of
+ * MLMC_NOALLOC_SCRATCH_BYTES, which every GPU that loads the library holds
+ * until the process exits, and the descriptors are written there by a kernel.
+ *   device  CUDA device to run on (made current for the call, then restored)
+ *   n, S, a, a_prec, a_n, prec, delta, max_iters: as mlmc_level_solve (CG only)
+ *   qoi, box, f: the QoI and right-hand side of mlmc_problem (box host [4], read
+ *           only when qoi == 1)
+ *   Q, iters, relres, flags: device outputs as in mlmc_level_solve (iters,
+ *           relres, flags may be NULL)
+ * Capacity: a batch needs about (8 + 4 p_v + p_s) (n+1)(n+1+3) bytes per system
+ * plus small per-tile terms (p_v, p_s: vector and coefficient storage bytes);
+ * a batch beyond MLMC_NOALLOC_SCRATCH_BYTES is rejected with MLMC_E_ARG and a
+ * message in mlmc_last_error(NULL), as are the argument errors of
+ * mlmc_level_solve.
+ * The first call on a device looks up the array's device address
+ * (cudaGetSymbolAddress) with that device current; make that first call
+ * before any stream capture.  Every call uses the same array and leaves its
+ * contents behind; the call clears what must start at zero.  Calls whose work
+ * overlaps on the GPU (other threads or streams) race on the array: issue them
+ * one after another.  Synchronises `stream` to read the kernel's error word. */
+#define MLMC_NOALLOC_SCRATCH_BYTES (64ull << 20)
+mlmc_status mlmc_level_solve_noalloc(int device, int n, int S, const void* a, mlmc_prec a_prec, int a_n,
+                                     mlmc_prec prec, double delta, int max_iters, int qoi, const double* box,
+                                     double f, double* Q, int32_t* iters, double* relres, int32_t* flags,
+                                     void* stream);
+
+/* ------------------------------------------------------------------------- */
 /* A8: level statistics.  Y_s = Qf[s] - Qc[s] (Qc NULL at level 0), Eq. (4.1);
  * the batch's (n, mean, m2, Kahan sums) is computed on the device in a fixed
  * order and merged into *acc (host) with Chan's pairwise update.

@@ -83,6 +83,9 @@ _SIGS = {
                                     c_void_p]),
     "mlmc_level_solve": (c_int, [c_void_p, c_int, c_int, c_void_p, c_int, c_int, c_int, c_int, c_double, c_int,
                                  c_void_p, c_void_p, c_void_p, c_void_p, c_void_p, c_void_p]),
+    "mlmc_level_solve_noalloc": (c_int, [c_int, c_int, c_int, c_void_p, c_int, c_int, c_int, c_double, c_int,
+                                         c_int, POINTER(c_double), c_double, c_void_p, c_void_p, c_void_p,
+                                         c_void_p, c_void_p]),
     "mlmc_level_stats": (c_int, [c_void_p, c_int, c_void_p, c_void_p, POINTER(mlmc_acc), c_void_p]),
     "mlmc_acc_merge": (None, [POINTER(mlmc_acc), POINTER(mlmc_acc)]),
     "mlmc_adapt_precision": (c_int, [c_int, POINTER(c_double), c_double, c_double, c_double, c_double, c_double,
@@ -224,6 +227,14 @@ def mlmc_level_solve(ctx, n, S, a, a_prec, a_n, prec, solver, delta, max_iters, 
                      flags=None, stream=None):
     _check(lib().mlmc_level_solve(ctx, n, S, _ptr(a), a_prec, a_n, prec, solver, delta, max_iters, _ptr(u),
                                   _ptr(Q), _ptr(iters), _ptr(relres), _ptr(flags), _stream(stream)), ctx)
+
+
+def mlmc_level_solve_noalloc(device, n, S, a, a_prec, a_n, prec, delta, max_iters, qoi, box, f, Q, iters=None,
+                             relres=None, flags=None, stream=None):
+    """Allocation-free solve (no context, scratch in the library's static device array)."""
+    bx = (c_double * 4)(*(box if box is not None else (0.0, 1.0, 0.0, 1.0)))
+    _check(lib().mlmc_level_solve_noalloc(device, n, S, _ptr(a), a_prec, a_n, prec, delta, max_iters, qoi, bx, f,
+                                          _ptr(Q), _ptr(iters), _ptr(relres), _ptr(flags), _stream(stream)))
 
 
 def mlmc_level_stats(ctx, S, Qf, Qc, acc=None, stream=None):

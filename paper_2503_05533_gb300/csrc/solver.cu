@@ -32,6 +32,7 @@
 #include <climits>
 #include <cmath>
 #include <cstring>
+#include <mutex>
 #include <vector>
 
 #include "device_common.cuh"
@@ -808,3 +809,256 @@ cudaError_t launch_apply_operator(int n, int S, const void* a, int a_fp64, int a
 }
 
 }  // namespace mlmc
+
+// ===========================================================================
+// Allocation-free solve (mlmc_level_solve_noalloc): the persistent solve with
+// its scratch in a file-scope device array instead of context workspaces.
+namespace mlmc {
+namespace {
+
+constexpr size_t kNoAllocBytes = MLMC_NOALLOC_SCRATCH_BYTES;
+__device__ __align__(256) unsigned char g_noalloc_scratch[kNoAllocBytes];
+
+constexpr int kNoAllocMaxDevices = 64;
+std::mutex g_noalloc_mu;
+void* g_noalloc_addr[kNoAllocMaxDevices] = {};
+
+// Device address of the scratch array on the current device (looked up once per device).
+cudaError_t noalloc_scratch(int device, void** out) {
+    std::lock_guard<std::mutex> lock(g_noalloc_mu);
+    if (!g_noalloc_addr[device]) {
+        void* p = nullptr;
+        const cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+        if (e != cudaSuccess) return e;
+        g_noalloc_addr[device] = p;
+    }
+    *out = g_noalloc_addr[device];
+    return cudaSuccess;
+}
+
+// Descriptors of a batch of equal-shaped systems, written on the device.
+__global__ void noalloc_plan_kernel(DevSolve proto, int S, long long stride_nodes, long long a_elems,
+                                    int a_elem_bytes, int ntile_per, int rpt, DevSolve* solves, DevTile* tiles) {
+    const long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (idx >= (long long)S * ntile_per) return;
+    const int s = (int)(idx / ntile_per), tt = (int)(idx % ntile_per);
+    if (tt == 0) {
+        DevSolve d = proto;
+        d.off = s * stride_nodes;
+        d.a = static_cast<const char*>(proto.a) + (size_t)s * a_elems * a_elem_bytes;
+        d.tile0 = s * ntile_per;
+        d.out = s;
+        solves[s] = d;
+    }
+    DevTile T;
+    T.solve = s;
+    T.j0 = 1 + tt * rpt;
+    T.j1 = min(proto.n, T.j0 + rpt);
+    tiles[idx] = T;
+}
+
+template <class VT, class ST>
+mlmc_status noalloc_typed(int n, int S, const void* a, int a_fp64, int a_n, double delta, int max_iters, int qoi,
+                          const double* box, double f, int prec, double* Q, int32_t* iters, double* relres,
+                          int32_t* flags, cudaStream_t st, void* scratch, int num_sms, std::string& err) {
+    const int ld = (int)align_up((size_t)n + 1, 4);
+    const int tile_nodes = 4096, max_outer = 12;
+    const int rpt = std::max(1, std::min(n - 1, tile_nodes / ld));
+    const int nt = (n - 1 + rpt - 1) / rpt;
+    const long long stride = (long long)align_up((size_t)(n + 1) * ld, 64);
+    const long long total = stride * S;
+    const int ns = S, ntl = S * nt;
+    size_t off = 0;
+    auto take = [&](size_t bytes) { size_t o = off; off = align_up(off + bytes, 256); return o; };
+    const size_t o_x = take(sizeof(double) * total);
+    const size_t o_r = take(sizeof(VT) * total);
+    const size_t o_p0 = take(sizeof(VT) * total);
+    const size_t o_p1 = take(sizeof(VT) * total);
+    const size_t o_d = take(sizeof(VT) * total);
+    const size_t o_as = take(sizeof(ST) * total);
+    const size_t o_pres = take(sizeof(double) * ntl);
+    const size_t o_prr0 = take(sizeof(double) * ntl);
+    const size_t o_prr = take(sizeof(double) * 2 * ntl);
+    const size_t o_psig = take(sizeof(double) * ntl);
+    const size_t o_pq = take(sizeof(double) * ntl);
+    const size_t o_inner = take(sizeof(int) * ns);
+    const size_t o_iters = take(sizeof(int) * ns);
+    const size_t o_rhoh = take(sizeof(double) * 2 * ns);
+    const size_t o_rhof = take(sizeof(double) * ns);
+    const size_t o_flags = take(sizeof(int) * ns);
+    const size_t o_act = take(sizeof(int) * (max_outer + 1));
+    const size_t o_done = take(sizeof(int) * (max_outer + 1));
+    const size_t o_bar = take(sizeof(unsigned) * 4);
+    const size_t zero_end = off;
+    const size_t o_conv = take(sizeof(int) * ns);
+    const size_t o_solves = take(sizeof(DevSolve) * ns);
+    const size_t o_tiles = take(sizeof(DevTile) * ntl);
+    if (off > kNoAllocBytes) {
+        err = "level_solve_noalloc: the batch needs " + std::to_string(off) + " bytes of scratch, above the " +
+              std::to_string(kNoAllocBytes) + "-byte maximum (MLMC_NOALLOC_SCRATCH_BYTES); use fewer systems";
+        return MLMC_E_ARG;
+    }
+    char* base = static_cast<char*>(scratch);
+    cudaError_t e;
+    if ((e = cudaMemsetAsync(base, 0, zero_end, st)) != cudaSuccess ||
+        (e = cudaMemsetAsync(base + o_conv, 0x7f, sizeof(int) * ns, st)) != cudaSuccess) {
+        err = std::string("level_solve_noalloc: cudaMemsetAsync: ") + cudaGetErrorString(e);
+        return MLMC_E_CUDA;
+    }
+    DevSolve proto{};
+    proto.n = n;
+    proto.ld = ld;
+    proto.a = a;
+    const int stridea = a_n / n;
+    proto.a_row = (long long)stridea * (a_n + 1);
+    proto.a_col = stridea;
+    proto.a_fp64 = a_fp64;
+    proto.ntiles = nt;
+    proto.cpr = (n - 1) / 4 + 1;
+    proto.rhs_mode = 0;
+    proto.qoi = qoi;
+    proto.bx0 = 0; proto.bx1 = n; proto.by0 = 0; proto.by1 = n;
+    if (qoi == 1) {
+        proto.bx0 = (int)std::lround(box[0] * n);
+        proto.bx1 = (int)std::lround(box[1] * n);
+        proto.by0 = (int)std::lround(box[2] * n);
+        proto.by1 = (int)std::lround(box[3] * n);
+    }
+    const double h = 1.0 / n;
+    proto.delta = delta;
+    proto.h2 = h * h;
+    proto.f = f;
+    proto.bnorm = std::fabs(f) * h * h * (double)(n - 1);
+    proto.Q = Q;
+    proto.iters = iters;
+    proto.relres = relres;
+    proto.flags = flags;
+    const long long a_elems = (long long)(a_n + 1) * (a_n + 1);
+    noalloc_plan_kernel<<<(unsigned)((ntl + 255) / 256), 256, 0, st>>>(
+        proto, S, stride, a_elems, a_fp64 ? 8 : 4, nt, rpt, reinterpret_cast<DevSolve*>(base + o_solves),
+        reinterpret_cast<DevTile*>(base + o_tiles));
+    g_launches.fetch_add(1, std::memory_order_relaxed);
+    if ((e = cudaGetLastError()) != cudaSuccess) {
+        err = std::string("level_solve_noalloc: plan kernel: ") + cudaGetErrorString(e);
+        return MLMC_E_CUDA;
+    }
+    Params P{};
+    P.solves = reinterpret_cast<const DevSolve*>(base + o_solves);
+    P.tiles = reinterpret_cast<const DevTile*>(base + o_tiles);
+    P.nsolves = ns;
+    P.ntiles = ntl;
+    P.x64 = reinterpret_cast<double*>(base + o_x);
+    P.r = base + o_r;
+    P.p0 = base + o_p0;
+    P.p1 = base + o_p1;
+    P.d = base + o_d;
+    P.as = base + o_as;
+    P.part_res = reinterpret_cast<double*>(base + o_pres);
+    P.part_rr0 = reinterpret_cast<double*>(base + o_prr0);
+    P.part_rr = reinterpret_cast<double*>(base + o_prr);
+    P.part_sig = reinterpret_cast<double*>(base + o_psig);
+    P.part_q = reinterpret_cast<double*>(base + o_pq);
+    P.conv_outer = reinterpret_cast<int*>(base + o_conv);
+    P.inner_tag = reinterpret_cast<int*>(base + o_inner);
+    P.iters_acc = reinterpret_cast<int*>(base + o_iters);
+    P.rho_hist = reinterpret_cast<double*>(base + o_rhoh);
+    P.rho_final = reinterpret_cast<double*>(base + o_rhof);
+    P.flags_acc = reinterpret_cast<int*>(base + o_flags);
+    P.active_count = reinterpret_cast<int*>(base + o_act);
+    P.done_count = reinterpret_cast<int*>(base + o_done);
+    P.bar = reinterpret_cast<unsigned*>(base + o_bar);
+    P.err = P.bar + 2;
+    P.max_outer = max_outer;
+    P.max_iters = max_iters;
+    P.theta = 0.3;
+    double tmin = 1e-6;
+    if (prec == MLMC_FP64) tmin = 1e-14;
+    if (prec == MLMC_FP16S) tmin = 1e-4;
+    if (prec == MLMC_BF16S) tmin = 1e-3;
+    P.tau_min = tmin;
+    P.tau_max = 0.5;
+    P.stag = 0.5;
+    P.timeout_ns = 10000000000ull;
+    int per_sm = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, persistent_solve<VT, ST>, BLOCK, 0) != cudaSuccess ||
+        per_sm <= 0)
+        per_sm = 1;
+    const int grid = std::max(1, std::min(ntl, per_sm * num_sms));
+    P.nbar = (unsigned)grid;
+    void* args[] = {&P};
+    if ((e = cudaLaunchCooperativeKernel((const void*)persistent_solve<VT, ST>, dim3(grid), dim3(BLOCK), args, 0,
+                                         st)) != cudaSuccess) {
+        err = std::string("level_solve_noalloc: cooperative launch: ") + cudaGetErrorString(e);
+        return MLMC_E_CUDA;
+    }
+    g_launches.fetch_add(1, std::memory_order_relaxed);
+    unsigned kerr = 0;
+    if ((e = cudaMemcpyAsync(&kerr, P.err, sizeof(unsigned), cudaMemcpyDeviceToHost, st)) != cudaSuccess ||
+        (e = cudaStreamSynchronize(st)) != cudaSuccess) {
+        err = std::string("level_solve_noalloc: ") + cudaGetErrorString(e);
+        return MLMC_E_CUDA;
+    }
+    if (kerr == KERR_TIMEOUT) {
+        err = "level_solve_noalloc: a grid barrier wait ran out (timeout)";
+        return MLMC_E_TIMEOUT;
+    }
+    return kerr == KERR_NONE ? MLMC_OK : MLMC_E_CUDA;
+}
+
+}  // namespace
+}  // namespace mlmc
+
+extern "C" mlmc_status mlmc_level_solve_noalloc(int device, int n, int S, const void* a, mlmc_prec a_prec, int a_n,
+                                                mlmc_prec prec, double delta, int max_iters, int qoi,
+                                                const double* box, double f, double* Q, int32_t* iters,
+                                                double* relres, int32_t* flags, void* stream) {
+    using namespace mlmc;
+    std::string& err = create_error();
+    err.clear();
+    if (n < 2 || n > 2048 || S < 0 || a_n < n || a_n % n != 0 || (a_prec != MLMC_FP64 && a_prec != MLMC_FP32) ||
+        prec < MLMC_FP64 || prec > MLMC_FP16S || !(delta > 0) || max_iters < 1 || (qoi != 0 && qoi != 1) ||
+        (qoi == 1 && !box) || !std::isfinite(f) || device < 0 || device >= kNoAllocMaxDevices) {
+        err = "level_solve_noalloc: bad device, n, S, a_n, precision, delta, max_iters, qoi, box or f";
+        return MLMC_E_ARG;
+    }
+    if (S == 0) return MLMC_OK;
+    if (!a || !Q) {
+        err = "level_solve_noalloc: null a or Q";
+        return MLMC_E_ARG;
+    }
+    int prev = 0;
+    cudaError_t e = cudaGetDevice(&prev);
+    if (e == cudaSuccess) e = cudaSetDevice(device);
+    int num_sms = 0;
+    void* scratch = nullptr;
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&num_sms, cudaDevAttrMultiProcessorCount, device);
+    if (e == cudaSuccess) e = noalloc_scratch(device, &scratch);
+    if (e != cudaSuccess) {
+        err = std::string("level_solve_noalloc: set-up: ") + cudaGetErrorString(e);
+        cudaSetDevice(prev);
+        return MLMC_E_CUDA;
+    }
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    const int a64 = a_prec == MLMC_FP64;
+    mlmc_status s;
+    switch (prec) {
+        case MLMC_FP64:
+            s = noalloc_typed<double, double>(n, S, a, a64, a_n, delta, max_iters, qoi, box, f, prec, Q, iters,
+                                              relres, flags, st, scratch, num_sms, err);
+            break;
+        case MLMC_FP32:
+            s = noalloc_typed<float, float>(n, S, a, a64, a_n, delta, max_iters, qoi, box, f, prec, Q, iters, relres,
+                                            flags, st, scratch, num_sms, err);
+            break;
+        case MLMC_BF16S:
+            s = noalloc_typed<float, __nv_bfloat16>(n, S, a, a64, a_n, delta, max_iters, qoi, box, f, prec, Q, iters,
+                                                    relres, flags, st, scratch, num_sms, err);
+            break;
+        default:
+            s = noalloc_typed<float, __half>(n, S, a, a64, a_n, delta, max_iters, qoi, box, f, prec, Q, iters,
+                                             relres, flags, st, scratch, num_sms, err);
+            break;
+    }
+    cudaSetDevice(prev);
+    return s;
+}
