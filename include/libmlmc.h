@@ -157,9 +157,10 @@ mlmc_status mlmc_apply_operator(int n, int S, const void* a, mlmc_prec a_prec, i
  * relative residual delta (Eq. (2.1) with C = 1; accuracy choice Eq. (4.12))
  * by iterative refinement (Alg. 2.1): r = b - A x in FP64 with the FP64
  * operator of the master coefficient; stop when ||r|| / ||b|| < delta; else
- * solve A d = r approximately with the inner Krylov method (CG or MINRES,
- * Sec. 2.2) in precision `prec`, and x += d in FP64.  All S solves run in one
- * persistent cooperative kernel.  Then Q_s = G(u_s) (Problem 4.5; the QoI of
+ * solve A d = r approximately with the inner Krylov method (Jacobi-
+ * preconditioned CG or MINRES, Sec. 2.2) in precision `prec`, and x += d in
+ * FP64.  All S solves run in one
+ * kernel launch.  Then Q_s = G(u_s) (Problem 4.5; the QoI of
  * the context's problem).
  *   n      cells per side of the solve grid, 2 <= n <= 2048
  *   a      device master coefficient [S][(a_n+1)^2], FP64 or FP32 (a_prec)
@@ -171,9 +172,10 @@ mlmc_status mlmc_apply_operator(int n, int S, const void* a, mlmc_prec a_prec, i
  *   iters  device int32 [S] inner iterations, or NULL
  *   relres device FP64 [S] final ||b - A x|| / ||b|| (FP64), or NULL
  *   flags  device int32 [S] MLMC_F_* bits, or NULL
+ * Every system is solved start to finish by one group of threads (a CTA, a
+ * quarter CTA or a warp, by grid size), all systems of the call in one launch.
  * Returns MLMC_OK when the kernel ran; per-solve failures are in `flags`.
- * MLMC_E_TIMEOUT if a bounded grid barrier ran out.  Synchronises `stream`
- * once, after the kernel, to read the kernel's error word. */
+ * Synchronises `stream` once, after the kernel. */
 mlmc_status mlmc_level_solve(mlmc_ctx* ctx, int n, int S, const void* a, mlmc_prec a_prec, int a_n,
                              mlmc_prec prec, mlmc_solver solver, double delta, int max_iters,
                              double* u, double* Q, int32_t* iters, double* relres, int32_t* flags,
@@ -323,7 +325,8 @@ mlmc_status mlmc_adjoint_grad(mlmc_ctx* ctx, int level, int S, const double* xi,
 
 /* ------------------------------------------------------------------------- */
 /* Diagnostics.  Timeout of every bounded device-side wait of this context, in
- * seconds (default 10).  Used to test the MLMC_E_TIMEOUT path. */
+ * seconds (default 10).  Used to test the MLMC_E_TIMEOUT path.  (The solves
+ * have no device-side waits: each system is solved by one group of threads.) */
 mlmc_status mlmc_set_wait_timeout(mlmc_ctx* ctx, double seconds);
 
 /* Measurement.  With profiling on, the context records CUDA events on the
@@ -351,12 +354,15 @@ mlmc_status mlmc_profile_enable(mlmc_ctx* ctx, int on);
 mlmc_status mlmc_profile_get(mlmc_ctx* ctx, mlmc_profile* out);   /* synchronises the device */
 mlmc_status mlmc_profile_reset(mlmc_ctx* ctx);
 
-/* Diagnostics.  Make every grid barrier of this context's persistent solves
- * also wait for `extra` CTAs that are never launched (extra = 0 restores
- * normal operation), so that every such wait runs out after the timeout.
- * Exists only to test that an expired wait returns MLMC_E_TIMEOUT and leaves
- * the GPU usable. */
-mlmc_status mlmc_debug_set_barrier_extra(mlmc_ctx* ctx, int extra);
+/* Diagnostics.  Make every bounded wait of this context's tensor-core KL
+ * synthesis expect 16 * extra bytes that never arrive (extra = 0 restores
+ * normal operation), so that each wait runs out after the timeout.  The kernel
+ * then records MLMC_E_TIMEOUT in its error word, waits (bounded) for its own
+ * copies, frees its tensor memory and returns; the next synchronising call of
+ * the context (mlmc_level_solve, mlmc_level_stats, mlmc_estimate,
+ * mlmc_adjoint_grad, mlmc_profile_get) returns MLMC_E_TIMEOUT.  Exists only to
+ * test that path; the GPU stays usable. */
+mlmc_status mlmc_debug_set_wait_extra(mlmc_ctx* ctx, int extra);
 
 #ifdef __cplusplus
 }

@@ -97,7 +97,7 @@ _SIGS = {
     "mlmc_adjoint_grad": (c_int, [c_void_p, c_int, c_int, c_void_p, c_int, c_double, c_int, c_void_p, c_void_p,
                                   c_void_p]),
     "mlmc_set_wait_timeout": (c_int, [c_void_p, c_double]),
-    "mlmc_debug_set_barrier_extra": (c_int, [c_void_p, c_int]),
+    "mlmc_debug_set_wait_extra": (c_int, [c_void_p, c_int]),
     "mlmc_profile_enable": (c_int, [c_void_p, c_int]),
     "mlmc_profile_get": (c_int, [c_void_p, c_void_p]),
     "mlmc_profile_reset": (c_int, [c_void_p]),
@@ -206,8 +206,8 @@ def mlmc_profile_reset(ctx):
     _check(lib().mlmc_profile_reset(ctx), ctx)
 
 
-def mlmc_debug_set_barrier_extra(ctx, extra):
-    _check(lib().mlmc_debug_set_barrier_extra(ctx, extra), ctx)
+def mlmc_debug_set_wait_extra(ctx, extra):
+    _check(lib().mlmc_debug_set_wait_extra(ctx, extra), ctx)
 
 
 def mlmc_sample_fields(ctx, level, first, S, xi, a, field_prec, stream=None):

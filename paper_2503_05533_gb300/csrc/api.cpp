@@ -343,6 +343,7 @@ void mlmc_destroy(mlmc_ctx* ctx) {
     Workspace& w = ctx->ws;
     for (DevBuf* b : {&w.solver, &w.fields, &w.xi, &w.q, &w.misc, &w.split, &w.adj}) b->release();
     if (w.pinned) cudaFreeHost(w.pinned);
+    if (ctx->kl_err) cudaFree(ctx->kl_err);
     delete ctx;
 }
 
@@ -375,7 +376,7 @@ mlmc_status mlmc_profile_get(mlmc_ctx* ctx, mlmc_profile* out) {
     }
     ctx->prof.kl_pending.clear();
     *out = ctx->prof.acc;
-    return MLMC_OK;
+    return check_kl_wait(ctx);
 }
 
 mlmc_status mlmc_profile_reset(mlmc_ctx* ctx) {
@@ -386,9 +387,9 @@ mlmc_status mlmc_profile_reset(mlmc_ctx* ctx) {
     return s;
 }
 
-mlmc_status mlmc_debug_set_barrier_extra(mlmc_ctx* ctx, int extra) {
+mlmc_status mlmc_debug_set_wait_extra(mlmc_ctx* ctx, int extra) {
     if (!ctx || extra < 0) return MLMC_E_ARG;
-    ctx->barrier_extra = extra;
+    ctx->wait_extra = extra;
     return MLMC_OK;
 }
 
@@ -458,7 +459,9 @@ mlmc_status mlmc_level_solve(mlmc_ctx* ctx, int n, int S, const void* a, mlmc_pr
     cfg.prec = prec;
     cfg.solver = solver;
     cfg.max_iters = max_iters;
-    return run_solve_batch(ctx, {g}, cfg, static_cast<cudaStream_t>(stream));
+    const mlmc_status s = run_solve_batch(ctx, {g}, cfg, static_cast<cudaStream_t>(stream));
+    if (s != MLMC_OK) return s;
+    return check_kl_wait(ctx);
 }
 
 void mlmc_acc_merge(mlmc_acc* into, const mlmc_acc* other) {
@@ -478,7 +481,7 @@ mlmc_status mlmc_level_stats(mlmc_ctx* ctx, int S, const double* Qf, const doubl
     MLMC_CUDA_RET(ctx->err, cudaStreamSynchronize(st));
     ctx->prof.acc.d2h_bytes += (int64_t)sizeof(got);
     acc_merge(acc, got);
-    return MLMC_OK;
+    return check_kl_wait(ctx);
 }
 
 mlmc_status mlmc_adapt_precision(int L, const double* h, double kp, double alpha1, double alpha2, double beta1,
@@ -638,6 +641,10 @@ mlmc_status mlmc_estimate(mlmc_ctx* ctx, const mlmc_options* opts, mlmc_result* 
             const mlmc_status s = run_solve_batch(ctx, kv.second, cfg, st);
             if (s != MLMC_OK) return s;
         }
+        {
+            const mlmc_status s = check_kl_wait(ctx);
+            if (s != MLMC_OK) return s;
+        }
         // ---- level statistics of the batch
         mlmc_acc* dacc = ctx->ws.misc.as<mlmc_acc>();
         for (size_t i = 0; i < req.size(); ++i) {
@@ -725,6 +732,7 @@ mlmc_status mlmc_adjoint_grad(mlmc_ctx* ctx, int level, int S, const double* xi,
     cfg.max_iters = max_iters;
     s = run_solve_batch(ctx, {gf, ga}, cfg, st);
     if (s != MLMC_OK) return s;
+    if ((s = check_kl_wait(ctx)) != MLMC_OK) return s;
     MLMC_CUDA_RET(ctx->err, launch_adjoint_elements(n, S, a, fp == MLMC_FP64, u, lam, w, st));
     MLMC_CUDA_RET(ctx->err, launch_kl_transpose_fp64(ctx->basis.at(n), S, w, dQdxi, st));
     return MLMC_OK;

@@ -122,66 +122,71 @@ __device__ __forceinline__ double warp_sum_partials(const double* part, int t0, 
 // ---------------------------------------------------------------------------
 // Storage types of the nodal coefficient and vectors: 4 consecutive values
 // starting at a 4-aligned index, widened to the compute type.
+//
+// Cache policy.  Vectors that the persistent solve rewrites (x, r, p, d) are
+// read with ordinary L1-cached loads: no phase reads a location that another
+// CTA writes in the same phase, and the grid barrier between phases performs
+// a gpu-scope acquire, which discards stale L1 lines.  The coefficient and its
+// inverse diagonal are read-only after set-up and use the read-only path.
 template <class T> struct Vec4;
 template <> struct Vec4<float> {
     static __device__ __forceinline__ void load(const float* p, float v[4]) {
-        const float4 q = __ldcg(reinterpret_cast<const float4*>(p));
+        const float4 q = *reinterpret_cast<const float4*>(p);
         v[0] = q.x; v[1] = q.y; v[2] = q.z; v[3] = q.w;
     }
     static __device__ __forceinline__ void store(float* p, const float v[4]) {
-        __stcg(reinterpret_cast<float4*>(p), make_float4(v[0], v[1], v[2], v[3]));
+        *reinterpret_cast<float4*>(p) = make_float4(v[0], v[1], v[2], v[3]);
     }
 };
 template <> struct Vec4<double> {
     static __device__ __forceinline__ void load(const double* p, double v[4]) {
-        const double2 a = __ldcg(reinterpret_cast<const double2*>(p));
-        const double2 b = __ldcg(reinterpret_cast<const double2*>(p) + 1);
+        const double2 a = *reinterpret_cast<const double2*>(p);
+        const double2 b = *(reinterpret_cast<const double2*>(p) + 1);
         v[0] = a.x; v[1] = a.y; v[2] = b.x; v[3] = b.y;
     }
     static __device__ __forceinline__ void store(double* p, const double v[4]) {
-        __stcg(reinterpret_cast<double2*>(p), make_double2(v[0], v[1]));
-        __stcg(reinterpret_cast<double2*>(p) + 1, make_double2(v[2], v[3]));
+        *reinterpret_cast<double2*>(p) = make_double2(v[0], v[1]);
+        *(reinterpret_cast<double2*>(p) + 1) = make_double2(v[2], v[3]);
     }
 };
 
-// Coefficient storage: load 4 values of ST widened to CT.
+// Coefficient storage (read-only while it is read): load 4 values of ST widened to CT.
 template <class ST, class CT> struct CoefLoad;
 template <class CT> struct CoefLoad<double, CT> {
     static __device__ __forceinline__ void load4(const double* p, CT v[4]) {
-        double t[4];
-        Vec4<double>::load(p, t);
-        for (int k = 0; k < 4; ++k) v[k] = (CT)t[k];
+        const double2 a = __ldg(reinterpret_cast<const double2*>(p));
+        const double2 b = __ldg(reinterpret_cast<const double2*>(p) + 1);
+        v[0] = (CT)a.x; v[1] = (CT)a.y; v[2] = (CT)b.x; v[3] = (CT)b.y;
     }
-    static __device__ __forceinline__ CT load1(const double* p) { return (CT)__ldcg(p); }
+    static __device__ __forceinline__ CT load1(const double* p) { return (CT)__ldg(p); }
 };
 template <class CT> struct CoefLoad<float, CT> {
     static __device__ __forceinline__ void load4(const float* p, CT v[4]) {
-        float t[4];
-        Vec4<float>::load(p, t);
-        for (int k = 0; k < 4; ++k) v[k] = (CT)t[k];
+        const float4 q = __ldg(reinterpret_cast<const float4*>(p));
+        v[0] = (CT)q.x; v[1] = (CT)q.y; v[2] = (CT)q.z; v[3] = (CT)q.w;
     }
-    static __device__ __forceinline__ CT load1(const float* p) { return (CT)__ldcg(p); }
+    static __device__ __forceinline__ CT load1(const float* p) { return (CT)__ldg(p); }
 };
 template <class CT> struct CoefLoad<__half, CT> {
     static __device__ __forceinline__ void load4(const __half* p, CT v[4]) {
-        const uint2 q = __ldcg(reinterpret_cast<const uint2*>(p));
+        const uint2 q = __ldg(reinterpret_cast<const uint2*>(p));
         const __half2 lo = *reinterpret_cast<const __half2*>(&q.x);
         const __half2 hi = *reinterpret_cast<const __half2*>(&q.y);
         const float2 a = __half22float2(lo), b = __half22float2(hi);
         v[0] = (CT)a.x; v[1] = (CT)a.y; v[2] = (CT)b.x; v[3] = (CT)b.y;
     }
-    static __device__ __forceinline__ CT load1(const __half* p) { return (CT)__half2float(__ldcg(p)); }
+    static __device__ __forceinline__ CT load1(const __half* p) { return (CT)__half2float(__ldg(p)); }
 };
 template <class CT> struct CoefLoad<__nv_bfloat16, CT> {
     static __device__ __forceinline__ void load4(const __nv_bfloat16* p, CT v[4]) {
-        const uint2 q = __ldcg(reinterpret_cast<const uint2*>(p));
+        const uint2 q = __ldg(reinterpret_cast<const uint2*>(p));
         const __nv_bfloat162 lo = *reinterpret_cast<const __nv_bfloat162*>(&q.x);
         const __nv_bfloat162 hi = *reinterpret_cast<const __nv_bfloat162*>(&q.y);
         const float2 a = __bfloat1622float2(lo), b = __bfloat1622float2(hi);
         v[0] = (CT)a.x; v[1] = (CT)a.y; v[2] = (CT)b.x; v[3] = (CT)b.y;
     }
     static __device__ __forceinline__ CT load1(const __nv_bfloat16* p) {
-        return (CT)__bfloat162float(__ldcg(p));
+        return (CT)__bfloat162float(__ldg(p));
     }
 };
 

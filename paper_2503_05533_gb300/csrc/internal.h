@@ -88,8 +88,9 @@ struct mlmc_ctx {
     std::map<int, mlmc::GridBasis> basis;   // keyed by n
     mlmc::Workspace ws;
     double wait_timeout_s = 10.0;
-    unsigned* kl_err = nullptr;   // error word of the last tensor-core synthesis (device)
-    int barrier_extra = 0;        // diagnostic: phantom CTAs every grid barrier waits for
+    unsigned* kl_err = nullptr;   // error word of the tensor-core synthesis (device, 4 bytes)
+    int kl_err_pending = 0;       // a synthesis ran since the word was last read
+    int wait_extra = 0;           // diagnostic: bytes every tensor-core wait expects and never receives
     mlmc::Profile prof;
 };
 
@@ -145,8 +146,8 @@ struct SolveConfig {
     double inner_theta = 0.3;   // inner tolerance = clamp(theta * delta / rho, tau_min, tau_max)
     double tau_min = -1.0;      // <0: per-precision default
     double tau_max = 0.5;
-    int tile_nodes = 4096;      // target interior nodes per work tile
-    int block = 256;
+    int tile_nodes = 2048;      // target nodes per warp tile
+    int jacobi = 1;             // Jacobi-preconditioned inner CG
 };
 struct SolveStats {
     int64_t inner_iters = 0;    // summed over solves (host copy, only if requested)
@@ -161,6 +162,10 @@ cudaError_t launch_level_stats(int S, const double* Qf, const double* Qc, mlmc_a
 // adjoint.cu
 cudaError_t launch_adjoint_elements(int n, int S, const void* a, int a_fp64, const double* u,
                                     const double* lam, double* G, cudaStream_t st);
+
+// Error word of the last tensor-core synthesis (kl_tc.cu): MLMC_OK, or MLMC_E_TIMEOUT
+// when one of its bounded waits ran out; clears the word.  Synchronises.
+mlmc_status check_kl_wait(mlmc_ctx* ctx);
 
 // host helpers (api.cpp)
 void acc_merge(mlmc_acc* into, const mlmc_acc& other);

@@ -116,7 +116,7 @@ __global__ void __launch_bounds__(128, 1) kl_tc_kernel(const __grid_constant__ C
                                                        const __grid_constant__ CUtensorMap mapB, int S, int Spad,
                                                        int V, int Vpad, int Kpad, int num_m,
                                                        float* __restrict__ out, unsigned* err,
-                                                       unsigned long long timeout_ns) {
+                                                       unsigned long long timeout_ns, unsigned extra_tx) {
     extern __shared__ uint8_t smem_raw[];
     uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
     uint64_t* bar_full = reinterpret_cast<uint64_t*>(smem + kOffBar);
@@ -149,7 +149,7 @@ __global__ void __launch_bounds__(128, 1) kl_tc_kernel(const __grid_constant__ C
         const int nkb = Kpad / TKB;
         bool ok = true;
         for (int kb = 0; kb < nkb && ok; ++kb) {
-            mbar_expect_tx(bar_full, 4 * kTileBytes);
+            mbar_expect_tx(bar_full, 4 * kTileBytes + extra_tx);
             tma_load_2d(smem + kOffAhi, &mapA, kb * TKB, s0, bar_full);
             tma_load_2d(smem + kOffAlo, &mapA, kb * TKB, Spad + s0, bar_full);
             tma_load_2d(smem + kOffBhi, &mapB, kb * TKB, v0, bar_full);
@@ -270,9 +270,12 @@ cudaError_t launch_kl_fp32(mlmc_ctx* ctx, const GridBasis& gb, int S, const doub
     cudaError_t e = ctx->ws.split.reserve(abytes + 256);
     if (e != cudaSuccess) return e;
     __half* a16 = ctx->ws.split.as<__half>();
-    unsigned* errw = reinterpret_cast<unsigned*>(ctx->ws.split.as<char>() + abytes);   // abytes is 32 KiB-aligned
-    ctx->kl_err = errw;
-    if ((e = cudaMemsetAsync(errw, 0, sizeof(unsigned), st)) != cudaSuccess) return e;
+    // the error word lives in its own small buffer so that it survives later reservations of `split`
+    if (!ctx->kl_err && (e = cudaMalloc(&ctx->kl_err, sizeof(unsigned))) != cudaSuccess) return e;
+    if (ctx->kl_err_pending == 0 && (e = cudaMemsetAsync(ctx->kl_err, 0, sizeof(unsigned), st)) != cudaSuccess)
+        return e;
+    ctx->kl_err_pending = 1;
+    unsigned* errw = ctx->kl_err;
     const long long work = (long long)Spad * Kpad;
     split_xi_kernel<<<(unsigned)((work + 255) / 256), 256, 0, st>>>(S, gb.K, Spad, Kpad, xi, a16);
     g_launches.fetch_add(1, std::memory_order_relaxed);
@@ -298,7 +301,7 @@ cudaError_t launch_kl_fp32(mlmc_ctx* ctx, const GridBasis& gb, int S, const doub
     }
     kl_tc_kernel<<<(unsigned)(num_m * num_n), 128, kSmemBytes, st>>>(
         mapA, mapB, S, Spad, gb.nodes, gb.nodes_pad, Kpad, num_m, a, errw,
-        (unsigned long long)(ctx->wait_timeout_s * 1e9));
+        (unsigned long long)(ctx->wait_timeout_s * 1e9), 16u * (unsigned)ctx->wait_extra);
     g_launches.fetch_add(1, std::memory_order_relaxed);
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
     if (ctx->prof.on) {
@@ -309,6 +312,19 @@ cudaError_t launch_kl_fp32(mlmc_ctx* ctx, const GridBasis& gb, int S, const doub
         ctx->prof.kl_pending.push_back(pend);
     }
     return cudaSuccess;
+}
+
+mlmc_status check_kl_wait(mlmc_ctx* ctx) {
+    if (!ctx->kl_err || !ctx->kl_err_pending) return MLMC_OK;
+    unsigned w = 0;
+    MLMC_CUDA_RET(ctx->err, cudaMemcpy(&w, ctx->kl_err, sizeof(unsigned), cudaMemcpyDeviceToHost));
+    MLMC_CUDA_RET(ctx->err, cudaMemset(ctx->kl_err, 0, sizeof(unsigned)));
+    ctx->kl_err_pending = 0;
+    if (w == KERR_TIMEOUT) {
+        ctx->err = "tensor-core KL synthesis: a bounded wait ran out (timeout); its output is not valid";
+        return MLMC_E_TIMEOUT;
+    }
+    return MLMC_OK;
 }
 
 }  // namespace mlmc

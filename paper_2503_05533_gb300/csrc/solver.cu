@@ -1,6 +1,5 @@
 // A3-A7: matrix-free P1 operator, batched inner Krylov solve, FP64 iterative
-// refinement and the QoI, for many independent systems in one persistent
-// cooperative kernel.
+// refinement and the QoI, for every system of a batch in one launch.
 //
 // Operator (Sec. 3.1, P1 elements on the uniform grid with SW-NE diagonals,
 // a_T = mean of the vertex values).  Right-angled P1 triangles couple only
@@ -12,18 +11,19 @@
 //
 // Solve (Alg. 2.1 with the factorisation replaced by a Krylov method):
 //   x = 0; loop: r = b - A x (FP64, master coefficient); stop if ||r||/||b|| < delta
-//   (Eq. (2.1), C = 1); else solve A d = r with CG (Sec. 2.2) in the inner
-//   precision to relative residual tau = clamp(theta delta / rho, tau_min, tau_max);
-//   x += d (FP64).
+//   (Eq. (2.1), C = 1); else solve A d = r with Jacobi-preconditioned CG
+//   (Sec. 2.2) in the inner precision to ||r_k|| <= tau ||r_0||,
+//   tau = clamp(theta delta / rho, tau_min, tau_max); x += d (FP64).
 // QoI (Problem 4.5): Q = sum_i g_i x_i, g_i = int_B phi_i (B = D: g_i = h^2).
 //
-// Execution: all systems of a batch share one cooperative launch.  A system's
-// interior rows are cut into row tiles; CTAs take tiles grid-stride.  Phases
-// are separated by a bounded grid barrier.  Each tile writes one partial sum
-// per reduction; every CTA that needs a system's scalar (alpha, beta, rho,
-// stop decisions) sums the same partials in the same order, so all CTAs agree
-// bit for bit without an extra barrier.  Per-system state that must outlive a
-// phase is written by the CTA owning the system's first tile only.
+// Execution: each system is solved start to finish by one group of threads --
+// a 512-thread CTA for large grids, a 128-thread quarter of a CTA for medium
+// grids, a warp for small grids -- so every synchronisation is group-local
+// (__syncthreads, a named barrier, __syncwarp) and nothing waits on another
+// group.  One launch covers all systems of all levels: CTA b takes either one
+// large system, four medium ones or sixteen small ones.  A system's working
+// set (a few MB at n = 256) is re-read by one SM every iteration, so L1 and L2
+// serve most of its traffic.
 #include <cuda_bf16.h>
 #include <cuda_fp16.h>
 #include <cuda_runtime.h>
@@ -42,7 +42,8 @@ namespace mlmc {
 
 namespace {
 
-constexpr int BLOCK = 256;
+constexpr int CTA = 512;              // threads per CTA
+constexpr int G_BIG = 512, G_MED = 128, G_SMALL = 32;
 
 struct DevSolve {
     int n, ld;
@@ -51,7 +52,6 @@ struct DevSolve {
     long long a_row;         // element stride between rows of `a`
     int a_col;               // element stride between columns of `a`
     int a_fp64;              // master precision (1: FP64, 0: FP32)
-    int tile0, ntiles;
     int cpr;                 // 4-node chunks per row
     int rhs_mode;            // 0: b_i = f h^2 ; 1: b_i = g_i (adjoint right-hand side)
     int qoi;                 // 0: int_D ; 1: int_B
@@ -63,41 +63,25 @@ struct DevSolve {
     double* relres;
     int32_t* flags;
     int out;                 // index into the output arrays
-};
-
-struct DevTile {
-    int solve, j0, j1;
+    int sys;                 // index of the system in the batch
 };
 
 struct Params {
-    unsigned nbar;       // CTAs a grid barrier waits for (the grid, plus a diagnostic surplus)
     const DevSolve* solves;
-    const DevTile* tiles;
-    int nsolves, ntiles;
+    const int* order;        // systems in launch order: big, then medium, then small
+    int nbig, nmed, nsmall;
     double* x64;
     void* r;
     void* p0;
     void* p1;
     void* d;
     void* as;
-    double* part_res;
-    double* part_rr0;
-    double* part_rr;     // [2][ntiles]
-    double* part_sig;
-    double* part_q;
-    int* conv_outer;     // outer index at which the system stopped (INT_MAX: running)
-    int* inner_tag;      // o + 1 once the inner solve of outer step o finished
-    int* iters_acc;      // inner iterations so far
-    double* rho_hist;    // [2][nsolves]
-    double* rho_final;
-    int* flags_acc;
-    int* active_count;   // [max_outer + 1]
-    int* done_count;     // [max_outer + 1]
-    unsigned* bar;
-    unsigned* err;
+    void* dinv;              // inverse diagonal in the storage type (Jacobi)
+    int32_t* sys_iters;      // per system: inner iterations
+    int32_t* sys_outer;      // per system: refinement steps
     int max_outer, max_iters;
     double theta, tau_min, tau_max, stag;
-    unsigned long long timeout_ns;
+    int jacobi;
 };
 
 // ---------------------------------------------------------------------------
@@ -137,8 +121,20 @@ __device__ __forceinline__ void load_vec_chunk(const VT* v, int ld, int n, int j
     Vec4<VT>::load(row - ld + 4 * c, s);
     Vec4<VT>::load(row + 4 * c, &cc[1]);
     Vec4<VT>::load(row + ld + 4 * c, nn);
-    cc[0] = (c > 0) ? __ldcg(row + 4 * c - 1) : (VT)0;
-    cc[5] = (4 * c + 4 <= n) ? __ldcg(row + 4 * c + 4) : (VT)0;
+    cc[0] = (c > 0) ? row[4 * c - 1] : (VT)0;
+    cc[5] = (4 * c + 4 <= n) ? row[4 * c + 4] : (VT)0;
+}
+
+// Storage-type values at the chunk's cross neighbourhood (same shape as load_vec_chunk).
+template <class ST, class CT>
+__device__ __forceinline__ void load_coef_cross(const ST* v, int ld, int n, int j, int c, CT s[4], CT cc[6],
+                                                CT nn[4]) {
+    const ST* row = v + (size_t)j * ld;
+    CoefLoad<ST, CT>::load4(row - ld + 4 * c, s);
+    CoefLoad<ST, CT>::load4(row + 4 * c, &cc[1]);
+    CoefLoad<ST, CT>::load4(row + ld + 4 * c, nn);
+    cc[0] = (c > 0) ? CoefLoad<ST, CT>::load1(row + 4 * c - 1) : (CT)0;
+    cc[5] = (4 * c + 4 <= n) ? CoefLoad<ST, CT>::load1(row + 4 * c + 4) : (CT)0;
 }
 
 template <class CT>
@@ -173,346 +169,386 @@ __device__ __forceinline__ double rhs_value(const DevSolve& S, int i, int j) {
     return S.rhs_mode == 0 ? S.f * S.h2 : qoi_weight(S, i, j);
 }
 
-// Inner tolerance for the current refinement step.
-__device__ __forceinline__ double inner_tau(const Params& P, const DevSolve& S, double rho) {
-    double t = P.theta * S.delta / rho;
-    t = fmin(fmax(t, P.tau_min), P.tau_max);
-    return t;
-}
-
-// Stop decision of outer step o from the residual partials (identical in every CTA).
-// Returns 0 to continue, else the MLMC_F_* reason.
-__device__ __forceinline__ int stop_reason(const Params& P, const DevSolve& S, int s, int o, double rho) {
-    if (!(rho == rho) || isinf(rho)) return MLMC_F_NONFINITE;
-    if (rho < S.delta) return MLMC_F_CONVERGED;
-    if (o >= P.max_outer) return MLMC_F_MAXIT;
-    if (__ldcg(P.iters_acc + s) >= P.max_iters) return MLMC_F_MAXIT;
-    if (o >= 1) {
-        const double prev = __ldcg(P.rho_hist + (size_t)((o - 1) & 1) * P.nsolves + s);
-        if (rho > P.stag * prev) return MLMC_F_STAGNATED;
-    }
-    return 0;
-}
-
-__device__ __forceinline__ double solve_rho(const Params& P, const DevSolve& S) {
-    const double rr = warp_sum_partials(P.part_res, S.tile0, S.ntiles);
-    return sqrt(rr) / S.bnorm;
-}
 
 // ---------------------------------------------------------------------------
-// Per-tile decision of one phase, made by warp 0 and broadcast to the block so
-// that every thread takes the same branch (other CTAs may update a system's
-// words concurrently; reading them once keeps the block uniform).
-struct TileDecision {
-    int go;
-    double s0, s1;
+// Groups of GT threads that solve one system.
+__device__ __forceinline__ double warp_sum_bcast(double v) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    return __shfl_sync(0xffffffffu, v, 0);   // lanes may differ in the last bit: take lane 0's
+}
+
+template <int GT>
+struct Group {
+    int rank, gid;           // thread rank in the group, group index in the CTA
+    double* red;             // 3 * (GT / 32) doubles of shared scratch
+    __device__ __forceinline__ void sync() const {
+        if (GT == 32) {
+            __syncwarp();
+        } else if (GT == CTA) {
+            __syncthreads();
+        } else {
+            asm volatile("bar.sync %0, %1;" ::"r"(gid + 1), "r"(GT) : "memory");
+        }
+    }
+    // Sums of three values over the group, in a fixed order; every thread gets the same bits.
+    __device__ __forceinline__ void sum3(double& a, double& b, double& c) const {
+        a = warp_sum_bcast(a);
+        b = warp_sum_bcast(b);
+        c = warp_sum_bcast(c);
+        if (GT == 32) return;
+        constexpr int W = GT / 32;
+        const int w = rank >> 5;
+        if ((rank & 31) == 0) {
+            red[w] = a;
+            red[W + w] = b;
+            red[2 * W + w] = c;
+        }
+        sync();
+        double ta = 0.0, tb = 0.0, tc = 0.0;
+#pragma unroll
+        for (int i = 0; i < W; ++i) {
+            ta += red[i];
+            tb += red[W + i];
+            tc += red[2 * W + i];
+        }
+        sync();
+        a = ta;
+        b = tb;
+        c = tc;
+    }
 };
 
-template <class VT, class ST>
-__global__ void __launch_bounds__(BLOCK) persistent_solve(Params P) {
-    __shared__ double red[2 * BLOCK / 32];
-    __shared__ TileDecision sh;
-    const unsigned nb = gridDim.x;
-    const int lane = threadIdx.x & 31;
-    const bool w0 = threadIdx.x < 32;
-    double* x64 = P.x64;
-    VT* r = static_cast<VT*>(P.r);
-    VT* pb[2] = {static_cast<VT*>(P.p0), static_cast<VT*>(P.p1)};
-    VT* d = static_cast<VT*>(P.d);
-    ST* as = static_cast<ST*>(P.as);
+__device__ __forceinline__ double inner_tau(const Params& P, const DevSolve& S, double rho) {
+    return fmin(fmax(P.theta * S.delta / rho, P.tau_min), P.tau_max);
+}
 
-    // ---- setup: coefficient in the inner storage precision (all rows 0..n)
-    for (int t = blockIdx.x; t < P.ntiles; t += nb) {
-        const DevTile T = P.tiles[t];
-        const DevSolve& S = P.solves[T.solve];
-        const int jlo = (T.j0 == 1) ? 0 : T.j0;
-        const int jhi = (T.j1 == S.n) ? S.n + 1 : T.j1;
-        const int width = S.n + 1;
-        for (int it = threadIdx.x; it < (jhi - jlo) * width; it += BLOCK) {
-            const int j = jlo + it / width, i = it % width;
-            as[S.off + (size_t)j * S.ld + i] = to_store<ST>(master_a(S, i, j));
+
+// ---------------------------------------------------------------------------
+// Row sweeps of the inner iteration.  A thread owns one 4-node column chunk c
+// and marches down its row segment [ja, jb), keeping a 3-row window of the
+// direction and of the coefficient in registers, so each row costs one vector
+// load (plus two halo scalars) per array instead of the full 3 x 6 stencil
+// neighbourhood.
+
+// The stencil on a 4-node chunk from three coefficient rows (south, centre, north).
+template <class CT>
+__device__ __forceinline__ void apply_rows(const CT* aS, const CT* aC, const CT* aN, const CT* s, const CT* cc,
+                                           const CT* nn, int n, int c, CT y[4]) {
+#pragma unroll
+    for (int t = 0; t < 4; ++t) {
+        const int ii = t + 1;
+        const int i = 4 * c + t;
+        const CT v = stencil_point<CT>(aC[ii], aC[ii + 1], aC[ii - 1], aN[ii], aS[ii], aN[ii + 1], aS[ii - 1], cc[ii],
+                                       cc[ii + 1], cc[ii - 1], nn[t], s[t]);
+        y[t] = (i >= 1 && i <= n - 1) ? v : (CT)0;
+    }
+}
+
+// One row of the storage-type coefficient at columns 4c-1 .. 4c+4.
+template <class ST, class CT>
+__device__ __forceinline__ void coef_row(const ST* AS, int ld, int n, int jj, int c, CT v[6]) {
+    const ST* row = AS + (size_t)jj * ld + 4 * c;
+    CoefLoad<ST, CT>::load4(row, &v[1]);
+    v[0] = (c > 0) ? CoefLoad<ST, CT>::load1(row - 1) : (CT)0;
+    v[5] = (4 * c + 4 <= n) ? CoefLoad<ST, CT>::load1(row + 4) : (CT)0;
+}
+
+// One row of a vector at columns 4c-1 .. 4c+4.
+template <class VT>
+__device__ __forceinline__ void vec_row(const VT* V, int ld, int n, int jj, int c, VT v[6]) {
+    const VT* row = V + (size_t)jj * ld + 4 * c;
+    Vec4<VT>::load(row, &v[1]);
+    v[0] = (c > 0) ? row[-1] : (VT)0;
+    v[5] = (4 * c + 4 <= n) ? row[4] : (VT)0;
+}
+
+// Direction at one row: p = z + beta p_old, z = D^-1 r (JAC) or r; p_old only when PREV.
+template <class VT, class ST, bool JAC, bool PREV>
+__device__ __forceinline__ void dir_row(const VT* R, const ST* DI, const VT* PO, VT beta, int ld, int n, int jj,
+                                        int c, VT v[6]) {
+    vec_row<VT>(R, ld, n, jj, c, v);
+    if (JAC) {
+        VT dd[6];
+        coef_row<ST, VT>(DI, ld, n, jj, c, dd);
+#pragma unroll
+        for (int q = 0; q < 6; ++q) v[q] *= dd[q];
+    }
+    if (PREV) {
+        VT po[6];
+        vec_row<VT>(PO, ld, n, jj, c, po);
+#pragma unroll
+        for (int q = 0; q < 6; ++q) v[q] = v[q] + beta * po[q];
+    }
+}
+
+// I1 sweep: writes p_new on rows [ja, jb) and returns this thread's part of (p, A p).
+template <class VT, class ST, bool JAC, bool PREV>
+__device__ __forceinline__ double sweep_dir(const VT* R, const ST* DI, const VT* PO, VT* PN, const ST* AS, VT beta,
+                                            int ld, int n, int c, int ja, int jb) {
+    VT pm[6], p0[6], pp[6], am[6], a0[6], ap[6];
+    dir_row<VT, ST, JAC, PREV>(R, DI, PO, beta, ld, n, ja - 1, c, pm);
+    dir_row<VT, ST, JAC, PREV>(R, DI, PO, beta, ld, n, ja, c, p0);
+    coef_row<ST, VT>(AS, ld, n, ja - 1, c, am);
+    coef_row<ST, VT>(AS, ld, n, ja, c, a0);
+    VT acc = 0;
+    for (int j = ja; j < jb; ++j) {
+        dir_row<VT, ST, JAC, PREV>(R, DI, PO, beta, ld, n, j + 1, c, pp);
+        coef_row<ST, VT>(AS, ld, n, j + 1, c, ap);
+        VT y[4];
+        apply_rows<VT>(am, a0, ap, &pm[1], p0, &pp[1], n, c, y);
+        Vec4<VT>::store(PN + (size_t)j * ld + 4 * c, &p0[1]);
+#pragma unroll
+        for (int q = 0; q < 4; ++q) acc += p0[q + 1] * y[q];
+#pragma unroll
+        for (int q = 0; q < 6; ++q) {
+            pm[q] = p0[q];
+            p0[q] = pp[q];
+            am[q] = a0[q];
+            a0[q] = ap[q];
         }
     }
-    if (!grid_barrier(P.bar, P.nbar, P.err, P.timeout_ns)) return;
+    return (double)acc;
+}
 
-    for (int o = 0; o <= P.max_outer; ++o) {
+// I2 sweep: d += alpha p, r -= alpha A p on rows [ja, jb); returns (||r||^2, (r, z)) parts.
+template <class VT, class ST, bool JAC>
+__device__ __forceinline__ void sweep_upd(const VT* PK, VT* R, VT* D, const ST* DI, const ST* AS, VT alpha, int ld,
+                                          int n, int c, int ja, int jb, double& rr, double& rz) {
+    VT pm[6], p0[6], pp[6], am[6], a0[6], ap[6];
+    vec_row<VT>(PK, ld, n, ja - 1, c, pm);
+    vec_row<VT>(PK, ld, n, ja, c, p0);
+    coef_row<ST, VT>(AS, ld, n, ja - 1, c, am);
+    coef_row<ST, VT>(AS, ld, n, ja, c, a0);
+    VT acc_r = 0, acc_z = 0;
+    for (int j = ja; j < jb; ++j) {
+        vec_row<VT>(PK, ld, n, j + 1, c, pp);
+        coef_row<ST, VT>(AS, ld, n, j + 1, c, ap);
+        const size_t base = (size_t)j * ld + 4 * c;
+        VT dv[4], rv[4], zz[4];
+        Vec4<VT>::load(D + base, dv);
+        Vec4<VT>::load(R + base, rv);
+        if (JAC) CoefLoad<ST, VT>::load4(DI + base, zz);
+        VT y[4];
+        apply_rows<VT>(am, a0, ap, &pm[1], p0, &pp[1], n, c, y);
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+            dv[q] = dv[q] + alpha * p0[q + 1];
+            rv[q] = rv[q] - alpha * y[q];
+            acc_r += rv[q] * rv[q];
+            acc_z += JAC ? rv[q] * (rv[q] * zz[q]) : rv[q] * rv[q];
+        }
+        Vec4<VT>::store(D + base, dv);
+        Vec4<VT>::store(R + base, rv);
+#pragma unroll
+        for (int q = 0; q < 6; ++q) {
+            pm[q] = p0[q];
+            p0[q] = pp[q];
+            am[q] = a0[q];
+            a0[q] = ap[q];
+        }
+    }
+    rr = (double)acc_r;
+    rz = (double)acc_z;
+}
+
+// One system, start to finish: set-up, refinement loop with the inner PCG, QoI.
+template <class VT, class ST, int GT>
+__device__ void solve_system(const Params& P, const DevSolve& S, const Group<GT>& G) {
+    const int n = S.n, ld = S.ld, cpr = S.cpr;
+    const int items = (n - 1) * cpr;
+    const int tr = G.rank;
+    double* X = P.x64 + S.off;
+    VT* R = static_cast<VT*>(P.r) + S.off;
+    VT* PB0 = static_cast<VT*>(P.p0) + S.off;
+    VT* PB1 = static_cast<VT*>(P.p1) + S.off;
+    VT* D = static_cast<VT*>(P.d) + S.off;
+    ST* AS = static_cast<ST*>(P.as) + S.off;
+    ST* DI = static_cast<ST*>(P.dinv) + S.off;
+    const bool jac = P.jacobi != 0;
+    // row-sweep mapping: GT / cpr row segments, each thread one chunk column of one segment
+    const int nseg = max(1, GT / cpr);
+    const int seg_rows = (n - 1 + nseg - 1) / nseg;
+    const int sc = tr % cpr, seg = tr / cpr;
+    const int ja = 1 + seg * seg_rows, jb = min(n, ja + seg_rows);
+    const bool sweep_on = seg < nseg && ja < jb;
+
+    // ---- set-up: coefficient (and inverse diagonal) in the inner storage precision
+    for (int it = tr; it < (n + 1) * (n + 1); it += GT) {
+        const int j = it / (n + 1), i = it - j * (n + 1);
+        AS[(size_t)j * ld + i] = to_store<ST>(master_a(S, i, j));
+        if (jac && i >= 1 && i <= n - 1 && j >= 1 && j <= n - 1) {
+            const double a00 = master_a(S, i, j), aE = master_a(S, i + 1, j), aW = master_a(S, i - 1, j);
+            const double aN = master_a(S, i, j + 1), aS = master_a(S, i, j - 1);
+            const double aNE = master_a(S, i + 1, j + 1), aSW = master_a(S, i - 1, j - 1);
+            const double diag = (2.0 * (a00 + aE) + aNE + aS + 2.0 * (aW + a00) + aN + aSW + 2.0 * (a00 + aN) +
+                                 aNE + aW + 2.0 * (aS + a00) + aE + aSW) * (1.0 / 6.0);
+            DI[(size_t)j * ld + i] = to_store<ST>(1.0 / diag);
+        }
+    }
+    G.sync();
+
+    double rho = 0.0, rho_prev = 0.0;
+    int iters = 0, flag = 0, o = 0;
+    for (;; ++o) {
         // ---- R: r = b - A x in FP64 with the master coefficient; d = 0
-        for (int t = blockIdx.x; t < P.ntiles; t += nb) {
-            const DevTile T = P.tiles[t];
-            const DevSolve& S = P.solves[T.solve];
-            __syncthreads();
-            if (threadIdx.x == 0) sh.go = (__ldcg(P.conv_outer + T.solve) >= o);
-            __syncthreads();
-            if (!sh.go) continue;
-            double acc64 = 0.0, accv = 0.0;
-            const int items = (T.j1 - T.j0) * S.cpr;
-            for (int it = threadIdx.x; it < items; it += BLOCK) {
-                const int j = T.j0 + it / S.cpr, c = it % S.cpr;
-                double xs[4], xc[6], xn[4];
-                load_vec_chunk<double>(x64 + S.off, S.ld, S.n, j, c, xs, xc, xn);
-                VT rv[4];
-#pragma unroll
-                for (int q = 0; q < 4; ++q) {
-                    const int i = 4 * c + q;
-                    double rq = 0.0;
-                    if (i >= 1 && i <= S.n - 1) {
-                        const double a00 = master_a(S, i, j), aE = master_a(S, i + 1, j), aW = master_a(S, i - 1, j);
-                        const double aN = master_a(S, i, j + 1), aS = master_a(S, i, j - 1);
-                        const double aNE = master_a(S, i + 1, j + 1), aSW = master_a(S, i - 1, j - 1);
-                        const double ax = stencil_point<double>(a00, aE, aW, aN, aS, aNE, aSW, xc[q + 1], xc[q + 2],
-                                                                xc[q], xn[q], xs[q]);
-                        rq = rhs_value(S, i, j) - ax;
-                    }
-                    rv[q] = (VT)rq;
-                    acc64 += rq * rq;
-                    accv += (double)rv[q] * (double)rv[q];
-                }
-                const size_t base = S.off + (size_t)j * S.ld + 4 * c;
-                Vec4<VT>::store(r + base, rv);
-                const VT z[4] = {(VT)0, (VT)0, (VT)0, (VT)0};
-                Vec4<VT>::store(d + base, z);
-            }
-            const double2 tot = block_sum2<BLOCK>(acc64, accv, red);
-            if (threadIdx.x == 0) {
-                P.part_res[t] = tot.x;
-                P.part_rr0[t] = tot.y;
-                P.part_rr[t] = tot.y;   // rho_0 of the inner solve, parity 0
-            }
-        }
-        if (!grid_barrier(P.bar, P.nbar, P.err, P.timeout_ns)) return;
-
-        // ---- decide: the CTA owning a system's first tile records the outcome
-        if (w0) {
-            for (int t = blockIdx.x; t < P.ntiles; t += nb) {
-                const DevTile T = P.tiles[t];
-                const DevSolve& S = P.solves[T.solve];
-                if (t != S.tile0 || __ldcg(P.conv_outer + T.solve) < o) continue;
-                const double rho = solve_rho(P, S);
-                const int why = stop_reason(P, S, T.solve, o, rho);
-                if (lane == 0) {
-                    P.rho_hist[(size_t)(o & 1) * P.nsolves + T.solve] = rho;
-                    P.rho_final[T.solve] = rho;
-                    if (why) {
-                        P.conv_outer[T.solve] = o;
-                        P.flags_acc[T.solve] = why;
-                    } else {
-                        atomicAdd(P.active_count + o, 1);
-                    }
-                }
-            }
-        }
-        if (o == P.max_outer) break;
-
-        // ---- inner CG on A d = r
-        for (int k = 0;; ++k) {
-            const int cur = k & 1;
-            // I1: beta, p = r + beta p_old, sigma = (p, A p)
-            for (int t = blockIdx.x; t < P.ntiles; t += nb) {
-                const DevTile T = P.tiles[t];
-                const DevSolve& S = P.solves[T.solve];
-                const int s = T.solve;
-                __syncthreads();
-                if (w0) {
-                    int go = 1;
-                    double beta = 0.0;
-                    const int co = __ldcg(P.conv_outer + s);
-                    if (co <= o || __ldcg(P.inner_tag + s) == o + 1) {
-                        go = 0;
-                    } else {
-                        const double rho = solve_rho(P, S);
-                        if (k == 0 && stop_reason(P, S, s, o, rho)) {
-                            go = 0;
-                        } else {
-                            const double rrk =
-                                warp_sum_partials(P.part_rr + (size_t)cur * P.ntiles, S.tile0, S.ntiles);
-                            const double rr0 = warp_sum_partials(P.part_rr0, S.tile0, S.ntiles);
-                            const double tau = inner_tau(P, S, rho);
-                            const int budget = P.max_iters - __ldcg(P.iters_acc + s);
-                            const bool finite = (rrk == rrk) && !isinf(rrk);
-                            const bool done = !finite || rrk <= tau * tau * rr0 || rrk == 0.0 || k >= budget;
-                            if (done) {
-                                go = 0;
-                                if (t == S.tile0 && lane == 0) {
-                                    P.inner_tag[s] = o + 1;
-                                    P.iters_acc[s] += k;
-                                    atomicAdd(P.done_count + o, 1);
-                                }
-                            } else if (k > 0) {
-                                const double rrp = warp_sum_partials(P.part_rr + (size_t)(cur ^ 1) * P.ntiles,
-                                                                     S.tile0, S.ntiles);
-                                beta = rrk / rrp;
-                            }
-                        }
-                    }
-                    if (lane == 0) {
-                        sh.go = go;
-                        sh.s0 = beta;
-                    }
-                }
-                __syncthreads();
-                if (!sh.go) continue;
-                const VT vb = (VT)sh.s0;
-                const VT* pold = pb[cur ^ 1] + S.off;
-                VT* pnew = pb[cur] + S.off;
-                const VT* rr = r + S.off;
-                VT acc = 0;
-                const int items = (T.j1 - T.j0) * S.cpr;
-                for (int it = threadIdx.x; it < items; it += BLOCK) {
-                    const int j = T.j0 + it / S.cpr, c = it % S.cpr;
-                    VT rs[4], rc[6], rn[4];
-                    load_vec_chunk<VT>(rr, S.ld, S.n, j, c, rs, rc, rn);
-                    if (k > 0) {
-                        VT ps[4], pc[6], pn[4];
-                        load_vec_chunk<VT>(pold, S.ld, S.n, j, c, ps, pc, pn);
-#pragma unroll
-                        for (int q = 0; q < 4; ++q) {
-                            rs[q] = rs[q] + vb * ps[q];
-                            rn[q] = rn[q] + vb * pn[q];
-                        }
-#pragma unroll
-                        for (int q = 0; q < 6; ++q) rc[q] = rc[q] + vb * pc[q];
-                    }
-                    VT a[3][6];
-                    load_coef_chunk<ST, VT>(as + S.off, S.ld, S.n, j, c, a);
-                    VT y[4];
-                    apply_chunk<VT>(a, rs, rc, rn, S.n, c, y);
-                    Vec4<VT>::store(pnew + (size_t)j * S.ld + 4 * c, &rc[1]);
-#pragma unroll
-                    for (int q = 0; q < 4; ++q) acc += rc[q + 1] * y[q];
-                }
-                const double tot = block_sum<BLOCK>((double)acc, red);
-                if (threadIdx.x == 0) P.part_sig[t] = tot;
-            }
-            if (!grid_barrier(P.bar, P.nbar, P.err, P.timeout_ns)) return;
-            if (__ldcg(P.done_count + o) >= __ldcg(P.active_count + o)) break;
-
-            // I2: alpha = rr / sigma; d += alpha p; r -= alpha A p; rr_new = (r, r)
-            for (int t = blockIdx.x; t < P.ntiles; t += nb) {
-                const DevTile T = P.tiles[t];
-                const DevSolve& S = P.solves[T.solve];
-                const int s = T.solve;
-                __syncthreads();
-                if (w0) {
-                    int go = 1;
-                    double alpha = 0.0;
-                    if (__ldcg(P.conv_outer + s) <= o || __ldcg(P.inner_tag + s) == o + 1) {
-                        go = 0;
-                    } else {
-                        const double rrk = warp_sum_partials(P.part_rr + (size_t)cur * P.ntiles, S.tile0, S.ntiles);
-                        const double sig = warp_sum_partials(P.part_sig, S.tile0, S.ntiles);
-                        alpha = rrk / sig;
-                    }
-                    if (lane == 0) {
-                        sh.go = go;
-                        sh.s0 = alpha;
-                    }
-                }
-                __syncthreads();
-                if (!sh.go) continue;
-                const VT va = (VT)sh.s0;
-                const VT* pk = pb[cur] + S.off;
-                VT* rr = r + S.off;
-                VT* dd = d + S.off;
-                VT acc = 0;
-                const int items = (T.j1 - T.j0) * S.cpr;
-                for (int it = threadIdx.x; it < items; it += BLOCK) {
-                    const int j = T.j0 + it / S.cpr, c = it % S.cpr;
-                    VT ps[4], pc[6], pn[4];
-                    load_vec_chunk<VT>(pk, S.ld, S.n, j, c, ps, pc, pn);
-                    VT a[3][6];
-                    load_coef_chunk<ST, VT>(as + S.off, S.ld, S.n, j, c, a);
-                    VT y[4];
-                    apply_chunk<VT>(a, ps, pc, pn, S.n, c, y);
-                    const size_t base = (size_t)j * S.ld + 4 * c;
-                    VT dv[4], rv[4];
-                    Vec4<VT>::load(dd + base, dv);
-                    Vec4<VT>::load(rr + base, rv);
-#pragma unroll
-                    for (int q = 0; q < 4; ++q) {
-                        dv[q] = dv[q] + va * pc[q + 1];
-                        rv[q] = rv[q] - va * y[q];
-                        acc += rv[q] * rv[q];
-                    }
-                    Vec4<VT>::store(dd + base, dv);
-                    Vec4<VT>::store(rr + base, rv);
-                }
-                const double tot = block_sum<BLOCK>((double)acc, red);
-                if (threadIdx.x == 0) P.part_rr[(size_t)(cur ^ 1) * P.ntiles + t] = tot;
-            }
-            if (!grid_barrier(P.bar, P.nbar, P.err, P.timeout_ns)) return;
-        }
-        if (__ldcg(P.active_count + o) == 0) break;
-
-        // ---- U: x += d in FP64
-        for (int t = blockIdx.x; t < P.ntiles; t += nb) {
-            const DevTile T = P.tiles[t];
-            const DevSolve& S = P.solves[T.solve];
-            __syncthreads();
-            if (threadIdx.x == 0) sh.go = (__ldcg(P.conv_outer + T.solve) > o);
-            __syncthreads();
-            if (!sh.go) continue;
-            const int items = (T.j1 - T.j0) * S.cpr;
-            for (int it = threadIdx.x; it < items; it += BLOCK) {
-                const int j = T.j0 + it / S.cpr, c = it % S.cpr;
-                const size_t base = S.off + (size_t)j * S.ld + 4 * c;
-                double xv[4];
-                VT dv[4];
-                Vec4<double>::load(x64 + base, xv);
-                Vec4<VT>::load(d + base, dv);
-#pragma unroll
-                for (int q = 0; q < 4; ++q) xv[q] += (double)dv[q];
-                Vec4<double>::store(x64 + base, xv);
-            }
-        }
-        if (!grid_barrier(P.bar, P.nbar, P.err, P.timeout_ns)) return;
-    }
-
-    // ---- Q: G(u) = sum g_i x_i; optional dense copy of u
-    for (int t = blockIdx.x; t < P.ntiles; t += nb) {
-        const DevTile T = P.tiles[t];
-        const DevSolve& S = P.solves[T.solve];
-        double acc = 0.0;
-        const int items = (T.j1 - T.j0) * S.cpr;
-        for (int it = threadIdx.x; it < items; it += BLOCK) {
-            const int j = T.j0 + it / S.cpr, c = it % S.cpr;
-            double xv[4];
-            Vec4<double>::load(x64 + S.off + (size_t)j * S.ld + 4 * c, xv);
+        double res = 0.0, rr0 = 0.0, rz0 = 0.0;
+        for (int it = tr; it < items; it += GT) {
+            const int j = 1 + it / cpr, c = it - (j - 1) * cpr;
+            double xs[4], xc[6], xn[4];
+            load_vec_chunk<double>(X, ld, n, j, c, xs, xc, xn);
+            const size_t base = (size_t)j * ld + 4 * c;
+            VT rv[4], zv[4];
+            if (jac) CoefLoad<ST, VT>::load4(DI + base, zv);
 #pragma unroll
             for (int q = 0; q < 4; ++q) {
                 const int i = 4 * c + q;
-                if (i >= 1 && i <= S.n - 1) acc += qoi_weight(S, i, j) * xv[q];
+                double rq = 0.0;
+                if (i >= 1 && i <= n - 1) {
+                    const double a00 = master_a(S, i, j), aE = master_a(S, i + 1, j), aW = master_a(S, i - 1, j);
+                    const double aN = master_a(S, i, j + 1), aS = master_a(S, i, j - 1);
+                    const double aNE = master_a(S, i + 1, j + 1), aSW = master_a(S, i - 1, j - 1);
+                    const double ax = stencil_point<double>(a00, aE, aW, aN, aS, aNE, aSW, xc[q + 1], xc[q + 2],
+                                                            xc[q], xn[q], xs[q]);
+                    rq = rhs_value(S, i, j) - ax;
+                }
+                rv[q] = (VT)rq;
+                res += rq * rq;
+                rr0 += (double)rv[q] * (double)rv[q];
+                rz0 += jac ? (double)rv[q] * (double)(rv[q] * zv[q]) : (double)rv[q] * (double)rv[q];
             }
+            Vec4<VT>::store(R + base, rv);
+            const VT z[4] = {(VT)0, (VT)0, (VT)0, (VT)0};
+            Vec4<VT>::store(D + base, z);
         }
-        if (S.u) {
-            double* u = S.u + (size_t)S.out * (S.n + 1) * (S.n + 1);
-            const int jlo = (T.j0 == 1) ? 0 : T.j0;
-            const int jhi = (T.j1 == S.n) ? S.n + 1 : T.j1;
-            const int width = S.n + 1;
-            for (int it = threadIdx.x; it < (jhi - jlo) * width; it += BLOCK) {
-                const int j = jlo + it / width, i = it % width;
-                const bool inner = (i >= 1 && i <= S.n - 1 && j >= 1 && j <= S.n - 1);
-                u[(size_t)j * width + i] = inner ? x64[S.off + (size_t)j * S.ld + i] : 0.0;
+        G.sum3(res, rr0, rz0);
+        rho = sqrt(res) / S.bnorm;
+        if (!(rho == rho) || isinf(rho)) { flag = MLMC_F_NONFINITE; break; }
+        if (rho < S.delta) { flag = MLMC_F_CONVERGED; break; }
+        if (o >= P.max_outer || iters >= P.max_iters) { flag = MLMC_F_MAXIT; break; }
+        if (o >= 1 && rho > P.stag * rho_prev) { flag = MLMC_F_STAGNATED; break; }
+        rho_prev = rho;
+        const double tau = inner_tau(P, S, rho);
+
+        // ---- inner PCG on A d = r (z = D^-1 r with Jacobi, z = r otherwise)
+        double rrk = rr0, rzk = rz0, rzp = 0.0;
+        int k = 0;
+        while ((rrk == rrk) && !isinf(rrk) && rrk > tau * tau * rr0 && rrk != 0.0 && iters + k < P.max_iters) {
+            const VT vb = (VT)(k > 0 ? rzk / rzp : 0.0);
+            const VT* pold = (k & 1) ? PB0 : PB1;
+            VT* pnew = (k & 1) ? PB1 : PB0;
+            // I1: p = z + beta p_old on the segment rows (and recomputed on the halo rows); sigma = (p, A p)
+            double sig = 0.0, t1 = 0.0, t2 = 0.0;
+            if (sweep_on) {
+                if (jac) {
+                    sig = (k > 0) ? sweep_dir<VT, ST, true, true>(R, DI, pold, pnew, AS, vb, ld, n, sc, ja, jb)
+                                  : sweep_dir<VT, ST, true, false>(R, DI, pold, pnew, AS, vb, ld, n, sc, ja, jb);
+                } else {
+                    sig = (k > 0) ? sweep_dir<VT, ST, false, true>(R, DI, pold, pnew, AS, vb, ld, n, sc, ja, jb)
+                                  : sweep_dir<VT, ST, false, false>(R, DI, pold, pnew, AS, vb, ld, n, sc, ja, jb);
+                }
             }
+            G.sum3(sig, t1, t2);
+            const VT va = (VT)(rzk / sig);
+            // I2: d += alpha p; r -= alpha A p; ||r||^2 and (r, z)
+            double nrr = 0.0, nrz = 0.0, t3 = 0.0;
+            if (sweep_on) {
+                if (jac)
+                    sweep_upd<VT, ST, true>(pnew, R, D, DI, AS, va, ld, n, sc, ja, jb, nrr, nrz);
+                else
+                    sweep_upd<VT, ST, false>(pnew, R, D, DI, AS, va, ld, n, sc, ja, jb, nrr, nrz);
+            }
+            G.sum3(nrr, nrz, t3);
+            rrk = nrr;
+            rzp = rzk;
+            rzk = nrz;
+            ++k;
         }
-        const double tot = block_sum<BLOCK>(acc, red);
-        if (threadIdx.x == 0) P.part_q[t] = tot;
+        iters += k;
+
+        // ---- U: x += d in FP64
+        for (int it = tr; it < items; it += GT) {
+            const int j = 1 + it / cpr, c = it - (j - 1) * cpr;
+            const size_t base = (size_t)j * ld + 4 * c;
+            double xv[4];
+            VT dvv[4];
+            Vec4<double>::load(X + base, xv);
+            Vec4<VT>::load(D + base, dvv);
+#pragma unroll
+            for (int q = 0; q < 4; ++q) xv[q] += (double)dvv[q];
+            Vec4<double>::store(X + base, xv);
+        }
+        G.sync();
     }
-    if (!grid_barrier(P.bar, P.nbar, P.err, P.timeout_ns)) return;
-    if (w0) {
-        for (int t = blockIdx.x; t < P.ntiles; t += nb) {
-            const DevTile T = P.tiles[t];
-            const DevSolve& S = P.solves[T.solve];
-            if (t != S.tile0) continue;
-            const double q = warp_sum_partials(P.part_q, S.tile0, S.ntiles);
-            if (lane == 0) {
-                if (S.Q) S.Q[S.out] = q;
-                if (S.iters) S.iters[S.out] = P.iters_acc[T.solve];
-                if (S.relres) S.relres[S.out] = P.rho_final[T.solve];
-                if (S.flags) S.flags[S.out] = P.flags_acc[T.solve];
-            }
+
+    // ---- Q: G(u) = sum g_i x_i; optional dense copy of u
+    double qsum = 0.0, t4 = 0.0, t5 = 0.0;
+    for (int it = tr; it < items; it += GT) {
+        const int j = 1 + it / cpr, c = it - (j - 1) * cpr;
+        double xv[4];
+        Vec4<double>::load(X + (size_t)j * ld + 4 * c, xv);
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+            const int i = 4 * c + q;
+            if (i >= 1 && i <= n - 1) qsum += qoi_weight(S, i, j) * xv[q];
         }
+    }
+    if (S.u) {
+        double* u = S.u + (size_t)S.out * (n + 1) * (n + 1);
+        for (int it = tr; it < (n + 1) * (n + 1); it += GT) {
+            const int j = it / (n + 1), i = it - j * (n + 1);
+            const bool inner = (i >= 1 && i <= n - 1 && j >= 1 && j <= n - 1);
+            u[it] = inner ? X[(size_t)j * ld + i] : 0.0;
+        }
+    }
+    G.sum3(qsum, t4, t5);
+    if (tr == 0) {
+        if (S.Q) S.Q[S.out] = qsum;
+        if (S.iters) S.iters[S.out] = iters;
+        if (S.relres) S.relres[S.out] = rho;
+        if (S.flags) S.flags[S.out] = flag;
+        P.sys_iters[S.sys] = iters;
+        P.sys_outer[S.sys] = o;
     }
 }
+
+// One launch for every system: CTA b < nbig solves one large system; the next
+// ceil(nmed / 4) CTAs solve four medium systems each (128-thread groups); the
+// rest solve sixteen small systems each (one warp each).
+template <class VT, class ST>
+__global__ void __launch_bounds__(CTA, 1) resident_solve(Params P) {
+    __shared__ double red[3 * (CTA / 32)];
+    const int b = blockIdx.x;
+    const int nmed_cta = (P.nmed + 3) / 4;
+    if (b < P.nbig) {
+        Group<G_BIG> G{(int)threadIdx.x, 0, red};
+        solve_system<VT, ST, G_BIG>(P, P.solves[P.order[b]], G);
+        return;
+    }
+    if (b < P.nbig + nmed_cta) {
+        const int gid = threadIdx.x / G_MED;
+        const int idx = (b - P.nbig) * 4 + gid;
+        if (idx >= P.nmed) return;
+        Group<G_MED> G{(int)(threadIdx.x % G_MED), gid, red + gid * 3 * (G_MED / 32)};
+        solve_system<VT, ST, G_MED>(P, P.solves[P.order[P.nbig + idx]], G);
+        return;
+    }
+    const int gid = threadIdx.x / G_SMALL;
+    const int idx = (b - P.nbig - nmed_cta) * (CTA / G_SMALL) + gid;
+    if (idx >= P.nsmall) return;
+    Group<G_SMALL> G{(int)(threadIdx.x % G_SMALL), gid, nullptr};
+    solve_system<VT, ST, G_SMALL>(P, P.solves[P.order[P.nbig + P.nmed + idx]], G);
+}
+
+// Group size class of a system: chunk items per thread stay around 8..32.
+int size_class(int n) {
+    const long long items = (long long)(n - 1) * ((n - 1) / 4 + 1);
+    if (items <= 512) return 2;        // warp
+    if (items <= 2048) return 1;       // 128 threads
+    return 0;                          // 512 threads
+}
+
+size_t align_up(size_t v, size_t a) { return (v + a - 1) / a * a; }
 
 // ---------------------------------------------------------------------------
 // Stand-alone operator application y = A x (dense nodal layouts), for testing
@@ -545,29 +581,75 @@ __global__ void apply_operator_kernel(int n, int S, const void* a, int a_fp64, i
     y[(size_t)s * V + v] = out;
 }
 
-// Occupancy-derived co-resident grid for each instantiation.
+
+// Workspace of a batch: vectors, coefficient storage, descriptors, launch order.
+struct Layout {
+    size_t o_x, o_r, o_p0, o_p1, o_d, o_as, o_dinv, o_stats, zero_end, o_solves, o_order, total;
+};
+
 template <class VT, class ST>
-int max_coresident(int num_sms) {
-    static int cached = -1;
-    if (cached < 0) {
-        int per_sm = 0;
-        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, persistent_solve<VT, ST>, BLOCK, 0) !=
-                cudaSuccess ||
-            per_sm <= 0)
-            per_sm = 1;
-        cached = per_sm;
-    }
-    return cached * num_sms;
+Layout make_layout(long long nodes, int ns, bool jacobi) {
+    Layout L{};
+    size_t off = 0;
+    auto take = [&](size_t bytes) { size_t o = off; off = align_up(off + bytes, 256); return o; };
+    L.o_x = take(sizeof(double) * nodes);
+    L.o_r = take(sizeof(VT) * nodes);
+    L.o_p0 = take(sizeof(VT) * nodes);
+    L.o_p1 = take(sizeof(VT) * nodes);
+    L.o_d = take(sizeof(VT) * nodes);
+    L.o_as = take(sizeof(ST) * nodes);
+    L.o_dinv = take(jacobi ? sizeof(ST) * nodes : 0);
+    L.o_stats = take(sizeof(int32_t) * 2 * ns);
+    L.zero_end = off;
+    L.o_solves = take(sizeof(DevSolve) * ns);
+    L.o_order = take(sizeof(int) * ns);
+    L.total = off;
+    return L;
 }
 
-size_t align_up(size_t v, size_t a) { return (v + a - 1) / a * a; }
+template <class VT, class ST>
+Params make_params(char* base, const Layout& L, int ns, int nbig, int nmed, int nsmall, int max_outer,
+                   int max_iters, int prec, int jacobi, double theta, double tau_max) {
+    Params P{};
+    P.solves = reinterpret_cast<const DevSolve*>(base + L.o_solves);
+    P.order = reinterpret_cast<const int*>(base + L.o_order);
+    P.nbig = nbig;
+    P.nmed = nmed;
+    P.nsmall = nsmall;
+    P.x64 = reinterpret_cast<double*>(base + L.o_x);
+    P.r = base + L.o_r;
+    P.p0 = base + L.o_p0;
+    P.p1 = base + L.o_p1;
+    P.d = base + L.o_d;
+    P.as = base + L.o_as;
+    P.dinv = base + L.o_dinv;
+    P.sys_iters = reinterpret_cast<int32_t*>(base + L.o_stats);
+    P.sys_outer = P.sys_iters + ns;
+    P.max_outer = max_outer;
+    P.max_iters = max_iters;
+    P.theta = theta;
+    // Refining the inner solve below what its operator can deliver wastes iterations:
+    // a refinement step contracts the residual by about the storage unit roundoff.
+    double tmin = 1e-6;
+    if (prec == MLMC_FP64) tmin = 1e-14;
+    if (prec == MLMC_FP16S) tmin = 1e-4;
+    if (prec == MLMC_BF16S) tmin = 1e-3;
+    P.tau_min = tmin;
+    P.tau_max = tau_max;
+    P.stag = 0.5;
+    P.jacobi = jacobi;
+    return P;
+}
+
+int grid_of(int nbig, int nmed, int nsmall) {
+    return nbig + (nmed + 3) / 4 + (nsmall + CTA / G_SMALL - 1) / (CTA / G_SMALL);
+}
 
 template <class VT, class ST>
 mlmc_status run_typed(mlmc_ctx* ctx, const std::vector<SolveGroup>& groups, const SolveConfig& cfg,
                       cudaStream_t st) {
     // ---- host plan
     std::vector<DevSolve> solves;
-    std::vector<DevTile> tiles;
     long long total = 0;
     const mlmc_problem& pb = ctx->prob;
     for (const SolveGroup& g : groups) {
@@ -577,8 +659,6 @@ mlmc_status run_typed(mlmc_ctx* ctx, const std::vector<SolveGroup>& groups, cons
         const int stride = g.a_n / n;
         const size_t elem = g.a_fp64 ? sizeof(double) : sizeof(float);
         const long long aV = (long long)(g.a_n + 1) * (g.a_n + 1);
-        const int rpt = std::max(1, std::min(n - 1, cfg.tile_nodes / ld));
-        const int nt = (n - 1 + rpt - 1) / rpt;
         const double h = 1.0 / n;
         int bx0 = 0, bx1 = n, by0 = 0, by1 = n;
         if (pb.qoi == 1) {
@@ -587,8 +667,7 @@ mlmc_status run_typed(mlmc_ctx* ctx, const std::vector<SolveGroup>& groups, cons
             by0 = (int)std::lround(pb.box[2] * n);
             by1 = (int)std::lround(pb.box[3] * n);
         }
-        double gnorm = 0.0;
-        if (g.rhs_weights) gnorm = *g.rhs_weights;   // precomputed ||g||_2 for the adjoint rhs
+        const double gnorm = g.rhs_weights ? *g.rhs_weights : 0.0;
         for (int s = 0; s < g.S; ++s) {
             DevSolve d{};
             d.n = n;
@@ -599,8 +678,6 @@ mlmc_status run_typed(mlmc_ctx* ctx, const std::vector<SolveGroup>& groups, cons
             d.a_row = (long long)stride * (g.a_n + 1);
             d.a_col = stride;
             d.a_fp64 = g.a_fp64;
-            d.tile0 = (int)tiles.size();
-            d.ntiles = nt;
             d.cpr = (n - 1) / 4 + 1;
             d.rhs_mode = g.rhs_weights ? 1 : 0;
             d.qoi = pb.qoi;
@@ -615,138 +692,71 @@ mlmc_status run_typed(mlmc_ctx* ctx, const std::vector<SolveGroup>& groups, cons
             d.relres = g.relres;
             d.flags = g.flags;
             d.out = s;
-            for (int tt = 0; tt < nt; ++tt) {
-                DevTile T;
-                T.solve = (int)solves.size();
-                T.j0 = 1 + tt * rpt;
-                T.j1 = std::min(n, T.j0 + rpt);
-                tiles.push_back(T);
-            }
+            d.sys = (int)solves.size();
             solves.push_back(d);
         }
     }
-    const int ns = (int)solves.size(), ntl = (int)tiles.size();
+    const int ns = (int)solves.size();
     if (ns == 0) return MLMC_OK;
-    const int max_outer = cfg.max_outer;
-
-    // ---- workspace layout (256-byte aligned sections)
-    size_t off = 0;
-    auto take = [&](size_t bytes) { size_t o = off; off = align_up(off + bytes, 256); return o; };
-    const size_t o_x = take(sizeof(double) * total);
-    const size_t o_r = take(sizeof(VT) * total);
-    const size_t o_p0 = take(sizeof(VT) * total);
-    const size_t o_p1 = take(sizeof(VT) * total);
-    const size_t o_d = take(sizeof(VT) * total);
-    const size_t o_as = take(sizeof(ST) * total);
-    const size_t zero_begin = off;   // everything below is cleared per launch except descriptors
-    const size_t o_pres = take(sizeof(double) * ntl);
-    const size_t o_prr0 = take(sizeof(double) * ntl);
-    const size_t o_prr = take(sizeof(double) * 2 * ntl);
-    const size_t o_psig = take(sizeof(double) * ntl);
-    const size_t o_pq = take(sizeof(double) * ntl);
-    const size_t o_inner = take(sizeof(int) * ns);
-    const size_t o_iters = take(sizeof(int) * ns);
-    const size_t o_rhoh = take(sizeof(double) * 2 * ns);
-    const size_t o_rhof = take(sizeof(double) * ns);
-    const size_t o_flags = take(sizeof(int) * ns);
-    const size_t o_act = take(sizeof(int) * (max_outer + 1));
-    const size_t o_done = take(sizeof(int) * (max_outer + 1));
-    const size_t o_bar = take(sizeof(unsigned) * 4);
-    const size_t zero_end = off;
-    const size_t o_conv = take(sizeof(int) * ns);
-    const size_t o_solves = take(sizeof(DevSolve) * ns);
-    const size_t o_tiles = take(sizeof(DevTile) * ntl);
-    const size_t need = off;
-
+    // launch order: large systems first (largest first), then medium, then small
+    std::vector<int> order(ns);
+    for (int i = 0; i < ns; ++i) order[i] = i;
+    std::stable_sort(order.begin(), order.end(), [&](int x, int y) { return solves[x].n > solves[y].n; });
+    int nbig = 0, nmed = 0, nsmall = 0;
+    for (int i : order) {
+        const int c = size_class(solves[i].n);
+        nbig += c == 0;
+        nmed += c == 1;
+        nsmall += c == 2;
+    }
+    const Layout L = make_layout<VT, ST>(total, ns, cfg.jacobi != 0);
     mlmc::DevBuf& buf = ctx->ws.solver;
-    MLMC_CUDA_RET(ctx->err, buf.reserve(need));
+    MLMC_CUDA_RET(ctx->err, buf.reserve(L.total));
     char* base = buf.as<char>();
     // vectors start at zero (boundary and padding entries stay zero forever)
-    MLMC_CUDA_RET(ctx->err, cudaMemsetAsync(base, 0, zero_end, st));
-    MLMC_CUDA_RET(ctx->err, cudaMemsetAsync(base + o_conv, 0x7f, sizeof(int) * ns, st));
-    MLMC_CUDA_RET(ctx->err, cudaMemcpyAsync(base + o_solves, solves.data(), sizeof(DevSolve) * ns,
+    MLMC_CUDA_RET(ctx->err, cudaMemsetAsync(base, 0, L.zero_end, st));
+    MLMC_CUDA_RET(ctx->err, cudaMemcpyAsync(base + L.o_solves, solves.data(), sizeof(DevSolve) * ns,
                                             cudaMemcpyHostToDevice, st));
-    MLMC_CUDA_RET(ctx->err, cudaMemcpyAsync(base + o_tiles, tiles.data(), sizeof(DevTile) * ntl,
+    MLMC_CUDA_RET(ctx->err, cudaMemcpyAsync(base + L.o_order, order.data(), sizeof(int) * ns,
                                             cudaMemcpyHostToDevice, st));
-    (void)zero_begin;
-
-    Params P{};
-    P.solves = reinterpret_cast<const DevSolve*>(base + o_solves);
-    P.tiles = reinterpret_cast<const DevTile*>(base + o_tiles);
-    P.nsolves = ns;
-    P.ntiles = ntl;
-    P.x64 = reinterpret_cast<double*>(base + o_x);
-    P.r = base + o_r;
-    P.p0 = base + o_p0;
-    P.p1 = base + o_p1;
-    P.d = base + o_d;
-    P.as = base + o_as;
-    P.part_res = reinterpret_cast<double*>(base + o_pres);
-    P.part_rr0 = reinterpret_cast<double*>(base + o_prr0);
-    P.part_rr = reinterpret_cast<double*>(base + o_prr);
-    P.part_sig = reinterpret_cast<double*>(base + o_psig);
-    P.part_q = reinterpret_cast<double*>(base + o_pq);
-    P.conv_outer = reinterpret_cast<int*>(base + o_conv);
-    P.inner_tag = reinterpret_cast<int*>(base + o_inner);
-    P.iters_acc = reinterpret_cast<int*>(base + o_iters);
-    P.rho_hist = reinterpret_cast<double*>(base + o_rhoh);
-    P.rho_final = reinterpret_cast<double*>(base + o_rhof);
-    P.flags_acc = reinterpret_cast<int*>(base + o_flags);
-    P.active_count = reinterpret_cast<int*>(base + o_act);
-    P.done_count = reinterpret_cast<int*>(base + o_done);
-    P.bar = reinterpret_cast<unsigned*>(base + o_bar);
-    P.err = P.bar + 2;
-    P.max_outer = max_outer;
-    P.max_iters = cfg.max_iters;
-    P.theta = cfg.inner_theta;
-    // Refining the inner solve below what its operator can deliver wastes iterations:
-    // a refinement step contracts the residual by about the storage unit roundoff.
-    double tmin = 1e-6;
-    if (cfg.prec == MLMC_FP64) tmin = 1e-14;
-    if (cfg.prec == MLMC_FP16S) tmin = 1e-4;
-    if (cfg.prec == MLMC_BF16S) tmin = 1e-3;
-    P.tau_min = cfg.tau_min > 0 ? cfg.tau_min : tmin;
-    P.tau_max = cfg.tau_max;
-    P.stag = 0.5;
-    P.timeout_ns = (unsigned long long)(ctx->wait_timeout_s * 1e9);
-
-    const int grid = std::max(1, std::min(ntl, max_coresident<VT, ST>(ctx->num_sms)));
-    P.nbar = (unsigned)(grid + std::max(0, ctx->barrier_extra));
-    void* args[] = {&P};
+    Params P = make_params<VT, ST>(base, L, ns, nbig, nmed, nsmall, cfg.max_outer, cfg.max_iters, cfg.prec,
+                                   cfg.jacobi, cfg.inner_theta, cfg.tau_max);
+    if (cfg.tau_min > 0) P.tau_min = cfg.tau_min;
     cudaEvent_t ev[2] = {nullptr, nullptr};
     if (ctx->prof.on) {
         MLMC_CUDA_RET(ctx->err, cudaEventCreate(&ev[0]));
         MLMC_CUDA_RET(ctx->err, cudaEventCreate(&ev[1]));
         MLMC_CUDA_RET(ctx->err, cudaEventRecord(ev[0], st));
     }
-    MLMC_CUDA_RET(ctx->err, cudaLaunchCooperativeKernel((const void*)persistent_solve<VT, ST>, dim3(grid),
-                                                        dim3(BLOCK), args, 0, st));
+    resident_solve<VT, ST><<<grid_of(nbig, nmed, nsmall), CTA, 0, st>>>(P);
     g_launches.fetch_add(1, std::memory_order_relaxed);
+    MLMC_CUDA_RET(ctx->err, cudaGetLastError());
     if (ctx->prof.on) MLMC_CUDA_RET(ctx->err, cudaEventRecord(ev[1], st));
-    unsigned kerr = 0;
-    MLMC_CUDA_RET(ctx->err, cudaMemcpyAsync(&kerr, P.err, sizeof(unsigned), cudaMemcpyDeviceToHost, st));
     MLMC_CUDA_RET(ctx->err, cudaStreamSynchronize(st));
-    ctx->prof.acc.h2d_bytes += (int64_t)(sizeof(DevSolve) * ns + sizeof(DevTile) * ntl);
-    ctx->prof.acc.d2h_bytes += (int64_t)sizeof(unsigned);
+    ctx->prof.acc.h2d_bytes += (int64_t)((sizeof(DevSolve) + sizeof(int)) * ns);
     if (ctx->prof.on) {
         float ms = 0.f;
         cudaEventElapsedTime(&ms, ev[0], ev[1]);
         cudaEventDestroy(ev[0]);
         cudaEventDestroy(ev[1]);
-        std::vector<int> it(ns), co(ns);
-        MLMC_CUDA_RET(ctx->err, cudaMemcpy(it.data(), P.iters_acc, sizeof(int) * ns, cudaMemcpyDeviceToHost));
-        MLMC_CUDA_RET(ctx->err, cudaMemcpy(co.data(), P.conv_outer, sizeof(int) * ns, cudaMemcpyDeviceToHost));
+        std::vector<int32_t> stats(2 * ns);
+        MLMC_CUDA_RET(ctx->err, cudaMemcpy(stats.data(), base + L.o_stats, sizeof(int32_t) * 2 * ns,
+                                           cudaMemcpyDeviceToHost));
+        const int32_t* outer = stats.data() + ns;
         const double pv = sizeof(VT), ps = sizeof(ST);
         double bytes = 0.0;
         int64_t iters = 0, uit = 0;
         for (int i = 0; i < ns; ++i) {
-            const double unk = (double)(solves[i].n - 1) * (solves[i].n - 1);
-            const double pm = solves[i].a_fp64 ? 8.0 : 4.0;
-            const int steps = std::min(co[i], max_outer);   // refinement (inner) solves
-            bytes += unk * ((double)it[i] * (8 * pv + 2 * ps) + (double)(steps + 1) * (8 + pm + 2 * pv) +
-                            (double)steps * (16 + pv) + (8 + pm + ps));
-            iters += it[i];
-            uit += (int64_t)unk * it[i];
+            const DevSolve& d = solves[i];
+            const int32_t it = stats[i];
+            const double unk = (double)(d.n - 1) * (d.n - 1);
+            const double pm = d.a_fp64 ? 8.0 : 4.0;
+            const double pd = cfg.jacobi ? ps : 0.0;   // inverse diagonal read once per inner iteration
+            const int steps = std::min(outer[i], cfg.max_outer);
+            bytes += unk * ((double)it * (8 * pv + 2 * ps + pd) + (double)(steps + 1) * (8 + pm + 2 * pv + pd) +
+                            (double)steps * (16 + pv) + (8 + pm + ps + pd));
+            iters += it;
+            uit += (int64_t)unk * it;
         }
         mlmc_profile& A = ctx->prof.acc;
         A.solve_launches += 1;
@@ -754,14 +764,6 @@ mlmc_status run_typed(mlmc_ctx* ctx, const std::vector<SolveGroup>& groups, cons
         A.solve_bytes += bytes;
         A.inner_iters += iters;
         A.unknown_iters += uit;
-    }
-    if (kerr == KERR_TIMEOUT) {
-        ctx->err = "persistent solve: a grid barrier wait ran out (timeout)";
-        return MLMC_E_TIMEOUT;
-    }
-    if (kerr != KERR_NONE) {
-        ctx->err = "persistent solve: kernel error word set";
-        return MLMC_E_CUDA;
     }
     return MLMC_OK;
 }
@@ -811,8 +813,8 @@ cudaError_t launch_apply_operator(int n, int S, const void* a, int a_fp64, int a
 }  // namespace mlmc
 
 // ===========================================================================
-// Allocation-free solve (mlmc_level_solve_noalloc): the persistent solve with
-// its scratch in a file-scope device array instead of context workspaces.
+// Allocation-free solve (mlmc_level_solve_noalloc): the same kernel with its
+// scratch in a file-scope device array instead of context workspaces.
 namespace mlmc {
 namespace {
 
@@ -836,72 +838,35 @@ cudaError_t noalloc_scratch(int device, void** out) {
     return cudaSuccess;
 }
 
-// Descriptors of a batch of equal-shaped systems, written on the device.
+// Descriptors and launch order of a batch of equal-shaped systems, written on the device.
 __global__ void noalloc_plan_kernel(DevSolve proto, int S, long long stride_nodes, long long a_elems,
-                                    int a_elem_bytes, int ntile_per, int rpt, DevSolve* solves, DevTile* tiles) {
-    const long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-    if (idx >= (long long)S * ntile_per) return;
-    const int s = (int)(idx / ntile_per), tt = (int)(idx % ntile_per);
-    if (tt == 0) {
-        DevSolve d = proto;
-        d.off = s * stride_nodes;
-        d.a = static_cast<const char*>(proto.a) + (size_t)s * a_elems * a_elem_bytes;
-        d.tile0 = s * ntile_per;
-        d.out = s;
-        solves[s] = d;
-    }
-    DevTile T;
-    T.solve = s;
-    T.j0 = 1 + tt * rpt;
-    T.j1 = min(proto.n, T.j0 + rpt);
-    tiles[idx] = T;
+                                    int a_elem_bytes, DevSolve* solves, int* order) {
+    const int s = blockIdx.x * blockDim.x + threadIdx.x;
+    if (s >= S) return;
+    DevSolve d = proto;
+    d.off = s * stride_nodes;
+    d.a = static_cast<const char*>(proto.a) + (size_t)s * a_elems * a_elem_bytes;
+    d.out = s;
+    d.sys = s;
+    solves[s] = d;
+    order[s] = s;
 }
 
 template <class VT, class ST>
 mlmc_status noalloc_typed(int n, int S, const void* a, int a_fp64, int a_n, double delta, int max_iters, int qoi,
                           const double* box, double f, int prec, double* Q, int32_t* iters, double* relres,
-                          int32_t* flags, cudaStream_t st, void* scratch, int num_sms, std::string& err) {
+                          int32_t* flags, cudaStream_t st, void* scratch, std::string& err) {
     const int ld = (int)align_up((size_t)n + 1, 4);
-    const int tile_nodes = 4096, max_outer = 12;
-    const int rpt = std::max(1, std::min(n - 1, tile_nodes / ld));
-    const int nt = (n - 1 + rpt - 1) / rpt;
     const long long stride = (long long)align_up((size_t)(n + 1) * ld, 64);
-    const long long total = stride * S;
-    const int ns = S, ntl = S * nt;
-    size_t off = 0;
-    auto take = [&](size_t bytes) { size_t o = off; off = align_up(off + bytes, 256); return o; };
-    const size_t o_x = take(sizeof(double) * total);
-    const size_t o_r = take(sizeof(VT) * total);
-    const size_t o_p0 = take(sizeof(VT) * total);
-    const size_t o_p1 = take(sizeof(VT) * total);
-    const size_t o_d = take(sizeof(VT) * total);
-    const size_t o_as = take(sizeof(ST) * total);
-    const size_t o_pres = take(sizeof(double) * ntl);
-    const size_t o_prr0 = take(sizeof(double) * ntl);
-    const size_t o_prr = take(sizeof(double) * 2 * ntl);
-    const size_t o_psig = take(sizeof(double) * ntl);
-    const size_t o_pq = take(sizeof(double) * ntl);
-    const size_t o_inner = take(sizeof(int) * ns);
-    const size_t o_iters = take(sizeof(int) * ns);
-    const size_t o_rhoh = take(sizeof(double) * 2 * ns);
-    const size_t o_rhof = take(sizeof(double) * ns);
-    const size_t o_flags = take(sizeof(int) * ns);
-    const size_t o_act = take(sizeof(int) * (max_outer + 1));
-    const size_t o_done = take(sizeof(int) * (max_outer + 1));
-    const size_t o_bar = take(sizeof(unsigned) * 4);
-    const size_t zero_end = off;
-    const size_t o_conv = take(sizeof(int) * ns);
-    const size_t o_solves = take(sizeof(DevSolve) * ns);
-    const size_t o_tiles = take(sizeof(DevTile) * ntl);
-    if (off > kNoAllocBytes) {
-        err = "level_solve_noalloc: the batch needs " + std::to_string(off) + " bytes of scratch, above the " +
+    const Layout L = make_layout<VT, ST>(stride * S, S, true);
+    if (L.total > kNoAllocBytes) {
+        err = "level_solve_noalloc: the batch needs " + std::to_string(L.total) + " bytes of scratch, above the " +
               std::to_string(kNoAllocBytes) + "-byte maximum (MLMC_NOALLOC_SCRATCH_BYTES); use fewer systems";
         return MLMC_E_ARG;
     }
     char* base = static_cast<char*>(scratch);
     cudaError_t e;
-    if ((e = cudaMemsetAsync(base, 0, zero_end, st)) != cudaSuccess ||
-        (e = cudaMemsetAsync(base + o_conv, 0x7f, sizeof(int) * ns, st)) != cudaSuccess) {
+    if ((e = cudaMemsetAsync(base, 0, L.zero_end, st)) != cudaSuccess) {
         err = std::string("level_solve_noalloc: cudaMemsetAsync: ") + cudaGetErrorString(e);
         return MLMC_E_CUDA;
     }
@@ -913,7 +878,6 @@ mlmc_status noalloc_typed(int n, int S, const void* a, int a_fp64, int a_n, doub
     proto.a_row = (long long)stridea * (a_n + 1);
     proto.a_col = stridea;
     proto.a_fp64 = a_fp64;
-    proto.ntiles = nt;
     proto.cpr = (n - 1) / 4 + 1;
     proto.rhs_mode = 0;
     proto.qoi = qoi;
@@ -934,75 +898,24 @@ mlmc_status noalloc_typed(int n, int S, const void* a, int a_fp64, int a_n, doub
     proto.relres = relres;
     proto.flags = flags;
     const long long a_elems = (long long)(a_n + 1) * (a_n + 1);
-    noalloc_plan_kernel<<<(unsigned)((ntl + 255) / 256), 256, 0, st>>>(
-        proto, S, stride, a_elems, a_fp64 ? 8 : 4, nt, rpt, reinterpret_cast<DevSolve*>(base + o_solves),
-        reinterpret_cast<DevTile*>(base + o_tiles));
+    noalloc_plan_kernel<<<(unsigned)((S + 255) / 256), 256, 0, st>>>(
+        proto, S, stride, a_elems, a_fp64 ? 8 : 4, reinterpret_cast<DevSolve*>(base + L.o_solves),
+        reinterpret_cast<int*>(base + L.o_order));
     g_launches.fetch_add(1, std::memory_order_relaxed);
     if ((e = cudaGetLastError()) != cudaSuccess) {
         err = std::string("level_solve_noalloc: plan kernel: ") + cudaGetErrorString(e);
         return MLMC_E_CUDA;
     }
-    Params P{};
-    P.solves = reinterpret_cast<const DevSolve*>(base + o_solves);
-    P.tiles = reinterpret_cast<const DevTile*>(base + o_tiles);
-    P.nsolves = ns;
-    P.ntiles = ntl;
-    P.x64 = reinterpret_cast<double*>(base + o_x);
-    P.r = base + o_r;
-    P.p0 = base + o_p0;
-    P.p1 = base + o_p1;
-    P.d = base + o_d;
-    P.as = base + o_as;
-    P.part_res = reinterpret_cast<double*>(base + o_pres);
-    P.part_rr0 = reinterpret_cast<double*>(base + o_prr0);
-    P.part_rr = reinterpret_cast<double*>(base + o_prr);
-    P.part_sig = reinterpret_cast<double*>(base + o_psig);
-    P.part_q = reinterpret_cast<double*>(base + o_pq);
-    P.conv_outer = reinterpret_cast<int*>(base + o_conv);
-    P.inner_tag = reinterpret_cast<int*>(base + o_inner);
-    P.iters_acc = reinterpret_cast<int*>(base + o_iters);
-    P.rho_hist = reinterpret_cast<double*>(base + o_rhoh);
-    P.rho_final = reinterpret_cast<double*>(base + o_rhof);
-    P.flags_acc = reinterpret_cast<int*>(base + o_flags);
-    P.active_count = reinterpret_cast<int*>(base + o_act);
-    P.done_count = reinterpret_cast<int*>(base + o_done);
-    P.bar = reinterpret_cast<unsigned*>(base + o_bar);
-    P.err = P.bar + 2;
-    P.max_outer = max_outer;
-    P.max_iters = max_iters;
-    P.theta = 0.3;
-    double tmin = 1e-6;
-    if (prec == MLMC_FP64) tmin = 1e-14;
-    if (prec == MLMC_FP16S) tmin = 1e-4;
-    if (prec == MLMC_BF16S) tmin = 1e-3;
-    P.tau_min = tmin;
-    P.tau_max = 0.5;
-    P.stag = 0.5;
-    P.timeout_ns = 10000000000ull;
-    int per_sm = 0;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, persistent_solve<VT, ST>, BLOCK, 0) != cudaSuccess ||
-        per_sm <= 0)
-        per_sm = 1;
-    const int grid = std::max(1, std::min(ntl, per_sm * num_sms));
-    P.nbar = (unsigned)grid;
-    void* args[] = {&P};
-    if ((e = cudaLaunchCooperativeKernel((const void*)persistent_solve<VT, ST>, dim3(grid), dim3(BLOCK), args, 0,
-                                         st)) != cudaSuccess) {
-        err = std::string("level_solve_noalloc: cooperative launch: ") + cudaGetErrorString(e);
-        return MLMC_E_CUDA;
-    }
+    const int c = size_class(n);
+    const int nbig = c == 0 ? S : 0, nmed = c == 1 ? S : 0, nsmall = c == 2 ? S : 0;
+    const Params P = make_params<VT, ST>(base, L, S, nbig, nmed, nsmall, 12, max_iters, prec, 1, 0.3, 0.5);
+    resident_solve<VT, ST><<<grid_of(nbig, nmed, nsmall), CTA, 0, st>>>(P);
     g_launches.fetch_add(1, std::memory_order_relaxed);
-    unsigned kerr = 0;
-    if ((e = cudaMemcpyAsync(&kerr, P.err, sizeof(unsigned), cudaMemcpyDeviceToHost, st)) != cudaSuccess ||
-        (e = cudaStreamSynchronize(st)) != cudaSuccess) {
+    if ((e = cudaGetLastError()) != cudaSuccess || (e = cudaStreamSynchronize(st)) != cudaSuccess) {
         err = std::string("level_solve_noalloc: ") + cudaGetErrorString(e);
         return MLMC_E_CUDA;
     }
-    if (kerr == KERR_TIMEOUT) {
-        err = "level_solve_noalloc: a grid barrier wait ran out (timeout)";
-        return MLMC_E_TIMEOUT;
-    }
-    return kerr == KERR_NONE ? MLMC_OK : MLMC_E_CUDA;
+    return MLMC_OK;
 }
 
 }  // namespace
@@ -1029,9 +942,7 @@ extern "C" mlmc_status mlmc_level_solve_noalloc(int device, int n, int S, const 
     int prev = 0;
     cudaError_t e = cudaGetDevice(&prev);
     if (e == cudaSuccess) e = cudaSetDevice(device);
-    int num_sms = 0;
     void* scratch = nullptr;
-    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&num_sms, cudaDevAttrMultiProcessorCount, device);
     if (e == cudaSuccess) e = noalloc_scratch(device, &scratch);
     if (e != cudaSuccess) {
         err = std::string("level_solve_noalloc: set-up: ") + cudaGetErrorString(e);
@@ -1044,19 +955,19 @@ extern "C" mlmc_status mlmc_level_solve_noalloc(int device, int n, int S, const 
     switch (prec) {
         case MLMC_FP64:
             s = noalloc_typed<double, double>(n, S, a, a64, a_n, delta, max_iters, qoi, box, f, prec, Q, iters,
-                                              relres, flags, st, scratch, num_sms, err);
+                                              relres, flags, st, scratch, err);
             break;
         case MLMC_FP32:
             s = noalloc_typed<float, float>(n, S, a, a64, a_n, delta, max_iters, qoi, box, f, prec, Q, iters, relres,
-                                            flags, st, scratch, num_sms, err);
+                                            flags, st, scratch, err);
             break;
         case MLMC_BF16S:
             s = noalloc_typed<float, __nv_bfloat16>(n, S, a, a64, a_n, delta, max_iters, qoi, box, f, prec, Q, iters,
-                                                    relres, flags, st, scratch, num_sms, err);
+                                                    relres, flags, st, scratch, err);
             break;
         default:
             s = noalloc_typed<float, __half>(n, S, a, a64, a_n, delta, max_iters, qoi, box, f, prec, Q, iters,
-                                             relres, flags, st, scratch, num_sms, err);
+                                             relres, flags, st, scratch, err);
             break;
     }
     cudaSetDevice(prev);
