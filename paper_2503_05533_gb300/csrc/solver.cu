@@ -77,6 +77,10 @@ struct Params {
     void* d;
     void* as;
     void* dinv;              // inverse diagonal in the storage type (Jacobi)
+    void* vb;                // MINRES: second Lanczos vector buffer
+    void* w0;                // MINRES: search directions (two buffers)
+    void* w1;
+    int solver;              // MLMC_CG or MLMC_MINRES
     int32_t* sys_iters;      // per system: inner iterations
     int32_t* sys_outer;      // per system: refinement steps
     int max_outer, max_iters;
@@ -352,8 +356,118 @@ __device__ __forceinline__ void sweep_upd(const VT* PK, VT* R, VT* D, const ST* 
     rz = (double)acc_z;
 }
 
+
+// ---------------------------------------------------------------------------
+// MINRES sweeps (preconditioned Lanczos with Givens rotations, Paige-Saunders).
+// zn_j = Z_j / gamma_j is the normalised preconditioned Lanczos vector.
+
+// Pending update of iteration j-1, elementwise at one chunk:
+// w_new = (zn_prev - a3 w_old - a2 w_new_prev) / a1 (stored over w_old), d += cst w_new.
+template <class VT>
+__device__ __forceinline__ void minres_update_chunk(const VT* ZP, VT gpi, VT* WO, const VT* WN, VT* D, VT a1i, VT a2,
+                                                    VT a3, VT cst, size_t base) {
+    VT zp[4], wo[4], wn[4], dv[4];
+    Vec4<VT>::load(ZP + base, zp);
+    Vec4<VT>::load(WO + base, wo);
+    Vec4<VT>::load(WN + base, wn);
+    Vec4<VT>::load(D + base, dv);
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+        const VT w = (zp[q] * gpi - a3 * wo[q] - a2 * wn[q]) * a1i;
+        wo[q] = w;
+        dv[q] = dv[q] + cst * w;
+    }
+    Vec4<VT>::store(WO + base, wo);
+    Vec4<VT>::store(D + base, dv);
+}
+
+// Sweep A: this thread's part of delta_j = (A zn_j, zn_j); with UPD, also the pending update.
+template <class VT, class ST, bool UPD>
+__device__ __forceinline__ double sweep_minres_a(const VT* ZC, VT gci, const ST* AS, int ld, int n, int c, int ja,
+                                                 int jb, const VT* ZP, VT gpi, VT* WO, const VT* WN, VT* D, VT a1i,
+                                                 VT a2, VT a3, VT cst) {
+    VT zm[6], z0[6], zp[6], am[6], a0[6], ap[6];
+    vec_row<VT>(ZC, ld, n, ja - 1, c, zm);
+    vec_row<VT>(ZC, ld, n, ja, c, z0);
+#pragma unroll
+    for (int q = 0; q < 6; ++q) {
+        zm[q] *= gci;
+        z0[q] *= gci;
+    }
+    coef_row<ST, VT>(AS, ld, n, ja - 1, c, am);
+    coef_row<ST, VT>(AS, ld, n, ja, c, a0);
+    VT acc = 0;
+    for (int j = ja; j < jb; ++j) {
+        vec_row<VT>(ZC, ld, n, j + 1, c, zp);
+#pragma unroll
+        for (int q = 0; q < 6; ++q) zp[q] *= gci;
+        coef_row<ST, VT>(AS, ld, n, j + 1, c, ap);
+        VT y[4];
+        apply_rows<VT>(am, a0, ap, &zm[1], z0, &zp[1], n, c, y);
+#pragma unroll
+        for (int q = 0; q < 4; ++q) acc += z0[q + 1] * y[q];
+        if (UPD) minres_update_chunk<VT>(ZP, gpi, WO, WN, D, a1i, a2, a3, cst, (size_t)j * ld + 4 * c);
+#pragma unroll
+        for (int q = 0; q < 6; ++q) {
+            zm[q] = z0[q];
+            z0[q] = zp[q];
+            am[q] = a0[q];
+            a0[q] = ap[q];
+        }
+    }
+    return (double)acc;
+}
+
+// Sweep B: v_{j+1} = A zn_j - cA v_j - cB v_{j-1} (over v_{j-1}), z_{j+1} = D^-1 v_{j+1} or v_{j+1};
+// returns this thread's part of (z_{j+1}, v_{j+1}).
+template <class VT, class ST, bool JAC>
+__device__ __forceinline__ double sweep_minres_b(const VT* ZC, VT gci, const ST* AS, VT* VP, const VT* VC,
+                                                 const ST* DI, VT* ZN, VT cA, VT cB, int ld, int n, int c, int ja,
+                                                 int jb) {
+    VT zm[6], z0[6], zp[6], am[6], a0[6], ap[6];
+    vec_row<VT>(ZC, ld, n, ja - 1, c, zm);
+    vec_row<VT>(ZC, ld, n, ja, c, z0);
+#pragma unroll
+    for (int q = 0; q < 6; ++q) {
+        zm[q] *= gci;
+        z0[q] *= gci;
+    }
+    coef_row<ST, VT>(AS, ld, n, ja - 1, c, am);
+    coef_row<ST, VT>(AS, ld, n, ja, c, a0);
+    VT acc = 0;
+    for (int j = ja; j < jb; ++j) {
+        vec_row<VT>(ZC, ld, n, j + 1, c, zp);
+#pragma unroll
+        for (int q = 0; q < 6; ++q) zp[q] *= gci;
+        coef_row<ST, VT>(AS, ld, n, j + 1, c, ap);
+        VT y[4];
+        apply_rows<VT>(am, a0, ap, &zm[1], z0, &zp[1], n, c, y);
+        const size_t base = (size_t)j * ld + 4 * c;
+        VT vp[4], vc[4], dd[4];
+        Vec4<VT>::load(VP + base, vp);
+        Vec4<VT>::load(VC + base, vc);
+        if (JAC) CoefLoad<ST, VT>::load4(DI + base, dd);
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+            vp[q] = y[q] - cA * vc[q] - cB * vp[q];
+            vc[q] = JAC ? dd[q] * vp[q] : vp[q];
+            acc += vc[q] * vp[q];
+        }
+        Vec4<VT>::store(VP + base, vp);
+        Vec4<VT>::store(ZN + base, vc);
+#pragma unroll
+        for (int q = 0; q < 6; ++q) {
+            zm[q] = z0[q];
+            z0[q] = zp[q];
+            am[q] = a0[q];
+            a0[q] = ap[q];
+        }
+    }
+    return (double)acc;
+}
+
 // One system, start to finish: set-up, refinement loop with the inner PCG, QoI.
-template <class VT, class ST, int GT>
+template <class VT, class ST, int SOLVER, int GT>
 __device__ void solve_system(const Params& P, const DevSolve& S, const Group<GT>& G) {
     const int n = S.n, ld = S.ld, cpr = S.cpr;
     const int items = (n - 1) * cpr;
@@ -366,6 +480,10 @@ __device__ void solve_system(const Params& P, const DevSolve& S, const Group<GT>
     ST* AS = static_cast<ST*>(P.as) + S.off;
     ST* DI = static_cast<ST*>(P.dinv) + S.off;
     const bool jac = P.jacobi != 0;
+    constexpr bool minres = SOLVER == MLMC_MINRES;
+    VT* VB = minres ? static_cast<VT*>(P.vb) + S.off : nullptr;
+    VT* W0 = minres ? static_cast<VT*>(P.w0) + S.off : nullptr;
+    VT* W1 = minres ? static_cast<VT*>(P.w1) + S.off : nullptr;
     // row-sweep mapping: GT / cpr row segments, each thread one chunk column of one segment
     const int nseg = max(1, GT / cpr);
     const int seg_rows = (n - 1 + nseg - 1) / nseg;
@@ -420,6 +538,16 @@ __device__ void solve_system(const Params& P, const DevSolve& S, const Group<GT>
             Vec4<VT>::store(R + base, rv);
             const VT z[4] = {(VT)0, (VT)0, (VT)0, (VT)0};
             Vec4<VT>::store(D + base, z);
+            if (minres) {
+                // v_1 = r (in R), z_1 = D^-1 v_1 (in PB0), v_0 = w_0 = w_1 = 0
+                VT z1[4];
+#pragma unroll
+                for (int q = 0; q < 4; ++q) z1[q] = jac ? rv[q] * zv[q] : rv[q];
+                Vec4<VT>::store(PB0 + base, z1);
+                Vec4<VT>::store(VB + base, z);
+                Vec4<VT>::store(W0 + base, z);
+                Vec4<VT>::store(W1 + base, z);
+            }
         }
         G.sum3(res, rr0, rz0);
         rho = sqrt(res) / S.bnorm;
@@ -430,10 +558,69 @@ __device__ void solve_system(const Params& P, const DevSolve& S, const Group<GT>
         rho_prev = rho;
         const double tau = inner_tau(P, S, rho);
 
+        int k = 0;
+        if (minres) {
+            // ---- inner preconditioned MINRES on A d = r; |eta| is ||r_k|| in the D^-1 norm
+            double g0 = 1.0, g1 = sqrt(rz0), c0 = 1.0, c1 = 1.0, s0 = 0.0, s1 = 0.0;
+            double eta = g1;
+            const double eta0 = g1;
+            VT *Vp = VB, *Vc = R, *Zc = PB0, *Zn = PB1, *Wo = W0, *Wn = W1;
+            bool pend = false;
+            VT pa1i = 0, pa2 = 0, pa3 = 0, pcst = 0, pgi = 0;
+            while ((eta == eta) && !isinf(eta) && fabs(eta) > tau * eta0 && eta0 > 0.0 && iters + k < P.max_iters) {
+                const VT gci = (VT)(1.0 / g1);
+                double dl = 0.0, t1 = 0.0, t2 = 0.0;
+                if (sweep_on)
+                    dl = pend ? sweep_minres_a<VT, ST, true>(Zc, gci, AS, ld, n, sc, ja, jb, Zn, pgi, Wo, Wn, D, pa1i,
+                                                             pa2, pa3, pcst)
+                              : sweep_minres_a<VT, ST, false>(Zc, gci, AS, ld, n, sc, ja, jb, Zn, pgi, Wo, Wn, D, pa1i,
+                                                              pa2, pa3, pcst);
+                G.sum3(dl, t1, t2);
+                if (pend) {
+                    VT* tw = Wo;
+                    Wo = Wn;
+                    Wn = tw;
+                }
+                double zv = 0.0, t3 = 0.0, t4 = 0.0;
+                const VT cA = (VT)(dl / g1), cB = (VT)(g1 / g0);
+                if (sweep_on) {
+                    if (jac)
+                        zv = sweep_minres_b<VT, ST, true>(Zc, gci, AS, Vp, Vc, DI, Zn, cA, cB, ld, n, sc, ja, jb);
+                    else
+                        zv = sweep_minres_b<VT, ST, false>(Zc, gci, AS, Vp, Vc, DI, Zn, cA, cB, ld, n, sc, ja, jb);
+                }
+                G.sum3(zv, t3, t4);
+                const double g2 = sqrt(fmax(zv, 0.0));
+                const double al0 = c1 * dl - c0 * s1 * g1;
+                const double al1 = sqrt(al0 * al0 + g2 * g2);
+                const double al2 = s1 * dl + c0 * c1 * g1;
+                const double al3 = s0 * g1;
+                const double c2 = al0 / al1, s2 = g2 / al1;
+                pend = true;
+                pa1i = (VT)(1.0 / al1);
+                pa2 = (VT)al2;
+                pa3 = (VT)al3;
+                pcst = (VT)(c2 * eta);
+                pgi = gci;
+                eta = -s2 * eta;
+                c0 = c1; c1 = c2; s0 = s1; s1 = s2; g0 = g1; g1 = g2;
+                VT* tv = Vp; Vp = Vc; Vc = tv;
+                VT* tz = Zc; Zc = Zn; Zn = tz;
+                ++k;
+                if (g2 == 0.0) break;
+            }
+            if (pend) {
+                for (int it = tr; it < items; it += GT) {
+                    const int j = 1 + it / cpr, c = it - (j - 1) * cpr;
+                    minres_update_chunk<VT>(Zn, pgi, Wo, Wn, D, pa1i, pa2, pa3, pcst, (size_t)j * ld + 4 * c);
+                }
+                G.sync();
+            }
+        }
         // ---- inner PCG on A d = r (z = D^-1 r with Jacobi, z = r otherwise)
         double rrk = rr0, rzk = rz0, rzp = 0.0;
-        int k = 0;
-        while ((rrk == rrk) && !isinf(rrk) && rrk > tau * tau * rr0 && rrk != 0.0 && iters + k < P.max_iters) {
+        while (!minres && (rrk == rrk) && !isinf(rrk) && rrk > tau * tau * rr0 && rrk != 0.0 &&
+               iters + k < P.max_iters) {
             const VT vb = (VT)(k > 0 ? rzk / rzp : 0.0);
             const VT* pold = (k & 1) ? PB0 : PB1;
             VT* pnew = (k & 1) ? PB1 : PB0;
@@ -515,14 +702,14 @@ __device__ void solve_system(const Params& P, const DevSolve& S, const Group<GT>
 // One launch for every system: CTA b < nbig solves one large system; the next
 // ceil(nmed / 4) CTAs solve four medium systems each (128-thread groups); the
 // rest solve sixteen small systems each (one warp each).
-template <class VT, class ST>
+template <class VT, class ST, int SOLVER>
 __global__ void __launch_bounds__(CTA, 1) resident_solve(Params P) {
     __shared__ double red[3 * (CTA / 32)];
     const int b = blockIdx.x;
     const int nmed_cta = (P.nmed + 3) / 4;
     if (b < P.nbig) {
         Group<G_BIG> G{(int)threadIdx.x, 0, red};
-        solve_system<VT, ST, G_BIG>(P, P.solves[P.order[b]], G);
+        solve_system<VT, ST, SOLVER, G_BIG>(P, P.solves[P.order[b]], G);
         return;
     }
     if (b < P.nbig + nmed_cta) {
@@ -530,14 +717,14 @@ __global__ void __launch_bounds__(CTA, 1) resident_solve(Params P) {
         const int idx = (b - P.nbig) * 4 + gid;
         if (idx >= P.nmed) return;
         Group<G_MED> G{(int)(threadIdx.x % G_MED), gid, red + gid * 3 * (G_MED / 32)};
-        solve_system<VT, ST, G_MED>(P, P.solves[P.order[P.nbig + idx]], G);
+        solve_system<VT, ST, SOLVER, G_MED>(P, P.solves[P.order[P.nbig + idx]], G);
         return;
     }
     const int gid = threadIdx.x / G_SMALL;
     const int idx = (b - P.nbig - nmed_cta) * (CTA / G_SMALL) + gid;
     if (idx >= P.nsmall) return;
     Group<G_SMALL> G{(int)(threadIdx.x % G_SMALL), gid, nullptr};
-    solve_system<VT, ST, G_SMALL>(P, P.solves[P.order[P.nbig + P.nmed + idx]], G);
+    solve_system<VT, ST, SOLVER, G_SMALL>(P, P.solves[P.order[P.nbig + P.nmed + idx]], G);
 }
 
 // Group size class of a system: chunk items per thread stay around 8..32.
@@ -584,11 +771,11 @@ __global__ void apply_operator_kernel(int n, int S, const void* a, int a_fp64, i
 
 // Workspace of a batch: vectors, coefficient storage, descriptors, launch order.
 struct Layout {
-    size_t o_x, o_r, o_p0, o_p1, o_d, o_as, o_dinv, o_stats, zero_end, o_solves, o_order, total;
+    size_t o_x, o_r, o_p0, o_p1, o_d, o_as, o_dinv, o_vb, o_w0, o_w1, o_stats, zero_end, o_solves, o_order, total;
 };
 
 template <class VT, class ST>
-Layout make_layout(long long nodes, int ns, bool jacobi) {
+Layout make_layout(long long nodes, int ns, bool jacobi, bool minres) {
     Layout L{};
     size_t off = 0;
     auto take = [&](size_t bytes) { size_t o = off; off = align_up(off + bytes, 256); return o; };
@@ -599,6 +786,9 @@ Layout make_layout(long long nodes, int ns, bool jacobi) {
     L.o_d = take(sizeof(VT) * nodes);
     L.o_as = take(sizeof(ST) * nodes);
     L.o_dinv = take(jacobi ? sizeof(ST) * nodes : 0);
+    L.o_vb = take(minres ? sizeof(VT) * nodes : 0);
+    L.o_w0 = take(minres ? sizeof(VT) * nodes : 0);
+    L.o_w1 = take(minres ? sizeof(VT) * nodes : 0);
     L.o_stats = take(sizeof(int32_t) * 2 * ns);
     L.zero_end = off;
     L.o_solves = take(sizeof(DevSolve) * ns);
@@ -609,7 +799,7 @@ Layout make_layout(long long nodes, int ns, bool jacobi) {
 
 template <class VT, class ST>
 Params make_params(char* base, const Layout& L, int ns, int nbig, int nmed, int nsmall, int max_outer,
-                   int max_iters, int prec, int jacobi, double theta, double tau_max) {
+                   int max_iters, int prec, int jacobi, int solver, double theta, double tau_max) {
     Params P{};
     P.solves = reinterpret_cast<const DevSolve*>(base + L.o_solves);
     P.order = reinterpret_cast<const int*>(base + L.o_order);
@@ -623,6 +813,10 @@ Params make_params(char* base, const Layout& L, int ns, int nbig, int nmed, int 
     P.d = base + L.o_d;
     P.as = base + L.o_as;
     P.dinv = base + L.o_dinv;
+    P.vb = base + L.o_vb;
+    P.w0 = base + L.o_w0;
+    P.w1 = base + L.o_w1;
+    P.solver = solver;
     P.sys_iters = reinterpret_cast<int32_t*>(base + L.o_stats);
     P.sys_outer = P.sys_iters + ns;
     P.max_outer = max_outer;
@@ -709,7 +903,7 @@ mlmc_status run_typed(mlmc_ctx* ctx, const std::vector<SolveGroup>& groups, cons
         nmed += c == 1;
         nsmall += c == 2;
     }
-    const Layout L = make_layout<VT, ST>(total, ns, cfg.jacobi != 0);
+    const Layout L = make_layout<VT, ST>(total, ns, cfg.jacobi != 0, cfg.solver == MLMC_MINRES);
     mlmc::DevBuf& buf = ctx->ws.solver;
     MLMC_CUDA_RET(ctx->err, buf.reserve(L.total));
     char* base = buf.as<char>();
@@ -720,7 +914,7 @@ mlmc_status run_typed(mlmc_ctx* ctx, const std::vector<SolveGroup>& groups, cons
     MLMC_CUDA_RET(ctx->err, cudaMemcpyAsync(base + L.o_order, order.data(), sizeof(int) * ns,
                                             cudaMemcpyHostToDevice, st));
     Params P = make_params<VT, ST>(base, L, ns, nbig, nmed, nsmall, cfg.max_outer, cfg.max_iters, cfg.prec,
-                                   cfg.jacobi, cfg.inner_theta, cfg.tau_max);
+                                   cfg.jacobi, cfg.solver, cfg.inner_theta, cfg.tau_max);
     if (cfg.tau_min > 0) P.tau_min = cfg.tau_min;
     cudaEvent_t ev[2] = {nullptr, nullptr};
     if (ctx->prof.on) {
@@ -728,7 +922,10 @@ mlmc_status run_typed(mlmc_ctx* ctx, const std::vector<SolveGroup>& groups, cons
         MLMC_CUDA_RET(ctx->err, cudaEventCreate(&ev[1]));
         MLMC_CUDA_RET(ctx->err, cudaEventRecord(ev[0], st));
     }
-    resident_solve<VT, ST><<<grid_of(nbig, nmed, nsmall), CTA, 0, st>>>(P);
+    if (cfg.solver == MLMC_MINRES)
+        resident_solve<VT, ST, MLMC_MINRES><<<grid_of(nbig, nmed, nsmall), CTA, 0, st>>>(P);
+    else
+        resident_solve<VT, ST, MLMC_CG><<<grid_of(nbig, nmed, nsmall), CTA, 0, st>>>(P);
     g_launches.fetch_add(1, std::memory_order_relaxed);
     MLMC_CUDA_RET(ctx->err, cudaGetLastError());
     if (ctx->prof.on) MLMC_CUDA_RET(ctx->err, cudaEventRecord(ev[1], st));
@@ -753,7 +950,8 @@ mlmc_status run_typed(mlmc_ctx* ctx, const std::vector<SolveGroup>& groups, cons
             const double pm = d.a_fp64 ? 8.0 : 4.0;
             const double pd = cfg.jacobi ? ps : 0.0;   // inverse diagonal read once per inner iteration
             const int steps = std::min(outer[i], cfg.max_outer);
-            bytes += unk * ((double)it * (8 * pv + 2 * ps + pd) + (double)(steps + 1) * (8 + pm + 2 * pv + pd) +
+            const double per_it = cfg.solver == MLMC_MINRES ? (14 * pv + 2 * ps + pd) : (8 * pv + 2 * ps + pd);
+            bytes += unk * ((double)it * per_it + (double)(steps + 1) * (8 + pm + 2 * pv + pd) +
                             (double)steps * (16 + pv) + (8 + pm + ps + pd));
             iters += it;
             uit += (int64_t)unk * it;
@@ -772,9 +970,9 @@ mlmc_status run_typed(mlmc_ctx* ctx, const std::vector<SolveGroup>& groups, cons
 
 mlmc_status run_solve_batch(mlmc_ctx* ctx, const std::vector<SolveGroup>& groups, const SolveConfig& cfg,
                             cudaStream_t st) {
-    if (cfg.solver != MLMC_CG) {
-        ctx->err = "solver not available in this build";
-        return MLMC_E_UNSUPPORTED;
+    if (cfg.solver != MLMC_CG && cfg.solver != MLMC_MINRES) {
+        ctx->err = "unknown solver";
+        return MLMC_E_ARG;
     }
     switch (cfg.prec) {
         case MLMC_FP64: return run_typed<double, double>(ctx, groups, cfg, st);
@@ -858,7 +1056,7 @@ mlmc_status noalloc_typed(int n, int S, const void* a, int a_fp64, int a_n, doub
                           int32_t* flags, cudaStream_t st, void* scratch, std::string& err) {
     const int ld = (int)align_up((size_t)n + 1, 4);
     const long long stride = (long long)align_up((size_t)(n + 1) * ld, 64);
-    const Layout L = make_layout<VT, ST>(stride * S, S, true);
+    const Layout L = make_layout<VT, ST>(stride * S, S, true, false);
     if (L.total > kNoAllocBytes) {
         err = "level_solve_noalloc: the batch needs " + std::to_string(L.total) + " bytes of scratch, above the " +
               std::to_string(kNoAllocBytes) + "-byte maximum (MLMC_NOALLOC_SCRATCH_BYTES); use fewer systems";
@@ -908,8 +1106,8 @@ mlmc_status noalloc_typed(int n, int S, const void* a, int a_fp64, int a_n, doub
     }
     const int c = size_class(n);
     const int nbig = c == 0 ? S : 0, nmed = c == 1 ? S : 0, nsmall = c == 2 ? S : 0;
-    const Params P = make_params<VT, ST>(base, L, S, nbig, nmed, nsmall, 12, max_iters, prec, 1, 0.3, 0.5);
-    resident_solve<VT, ST><<<grid_of(nbig, nmed, nsmall), CTA, 0, st>>>(P);
+    const Params P = make_params<VT, ST>(base, L, S, nbig, nmed, nsmall, 12, max_iters, prec, 1, MLMC_CG, 0.3, 0.5);
+    resident_solve<VT, ST, MLMC_CG><<<grid_of(nbig, nmed, nsmall), CTA, 0, st>>>(P);
     g_launches.fetch_add(1, std::memory_order_relaxed);
     if ((e = cudaGetLastError()) != cudaSuccess || (e = cudaStreamSynchronize(st)) != cudaSuccess) {
         err = std::string("level_solve_noalloc: ") + cudaGetErrorString(e);

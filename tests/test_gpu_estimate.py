@@ -145,3 +145,27 @@ def test_bench_configuration_estimate_runs_clean(M):
     # E[Q] of the unit-coefficient problem is 0.0351; a lognormal coefficient with
     # sigma^2 = 1 raises it (E[1/a] = e^{1/2} for a constant field)
     assert 0.035 < r["estimate"] < 0.1
+
+
+def test_paper_setting_minres_fp64(M):
+    # Sec. 5.1: f = 1, field of Eq. (5.2) with s = 4, q = 2, sigma = 2, h_0 = 1/8, m = 2,
+    # MINRES in double precision to the accuracy delta_l of Eq. (4.12), k_p = 0.05.
+    tol = 2e-3
+    kw = dict(n0=8, m=2, L_max=3, kind=1, K=4, sigma2=4.0, q=2.0, seed=3)
+    h = M.mlmc_create(M.make_problem(**kw), 0)
+    try:
+        o = M.mlmc_default_options()
+        o.form = M.MLMC_FORM_FP64_ADAPTIVE
+        o.solver = M.MLMC_MINRES
+        o.tol, o.N_init = tol, 40
+        r = M.result_dict(M.mlmc_estimate(h, o))
+        o.solver = M.MLMC_CG
+        rc = M.result_dict(M.mlmc_estimate(h, o))
+    finally:
+        M.mlmc_destroy(h)
+    P = o_mlmc.Problem(n0=8, m=2, L_max=3, field_kind=1, K=4, sigma2=4.0, q=2.0, seed=3)
+    ref = o_mlmc.estimate(P, tol, N_init=40)
+    assert r["L"] == ref["L"] and r["flags_or"] & ~M.MLMC_F_CONVERGED == 0
+    assert abs(r["estimate"] - ref["estimate"]) <= max(1e-3 * abs(ref["estimate"]), 0.5 * ref["rmse"])
+    # MINRES and CG reach the same accuracy per level: the estimates agree to the solver tolerances
+    assert abs(r["estimate"] - rc["estimate"]) <= 1e-3 * abs(rc["estimate"])

@@ -324,3 +324,55 @@ def test_level_pipeline_matches_oracle_sampler(M):
             assert abs(acc.mean - m) <= 1e-9 * abs(m) and abs(acc.m2 / S - v) <= 1e-6 * v
     finally:
         M.mlmc_destroy(h)
+
+
+# ---------------------------------------------------------------- A5: MINRES
+def _solve_minres(M, h, n, a_np, a_prec, prec, delta):
+    S = a_np.shape[0]
+    dt = torch.float64 if a_prec == M.MLMC_FP64 else torch.float32
+    U = torch.zeros((S, (n + 1) ** 2), dtype=torch.float64, device=device())
+    Q = torch.empty(S, dtype=torch.float64, device=device())
+    it = torch.zeros(S, dtype=torch.int32, device=device())
+    rr = torch.zeros(S, dtype=torch.float64, device=device())
+    fl = torch.zeros(S, dtype=torch.int32, device=device())
+    M.mlmc_level_solve(h, n, S, to_dev(a_np, dt), a_prec, n, prec, M.MLMC_MINRES, delta, 200000, U, Q, it, rr, fl)
+    torch.cuda.synchronize()
+    return U.cpu().numpy(), Q.cpu().numpy(), it.cpu().numpy(), rr.cpu().numpy(), fl.cpu().numpy()
+
+
+@pytest.mark.parametrize("n", [2, 8, 13, 32, 64])
+def test_minres_fp64_matches_cholesky(M, n):
+    h = _ctx(M)
+    try:
+        af = smooth_lognormal_field(n, 4, seed=200 + n, log_sd=1.0)
+        delta = fp64_delta(n)
+        U, Q, it, rr, fl = _solve_minres(M, h, n, af, M.MLMC_FP64, M.MLMC_FP64, delta)
+        for s in range(4):
+            x, Qo = o_fem.solve_sample(n, af[s])
+            assert fl[s] == M.MLMC_F_CONVERGED and rr[s] < delta
+            assert abs(Q[s] - Qo) <= 1e-12 * abs(Qo)
+            assert np.max(np.abs(_interior(n, U[s]) - x)) <= 1e-11 * np.max(np.abs(x))
+    finally:
+        M.mlmc_destroy(h)
+
+
+@pytest.mark.parametrize("prec", ["FP32", "FP16S"])
+@pytest.mark.parametrize("delta", [3.5e-3, 1e-7])
+def test_minres_mixed_reaches_delta(M, prec, delta):
+    p = getattr(M, "MLMC_" + prec)
+    h = _ctx(M)
+    try:
+        n, S = 48, 5
+        af = smooth_lognormal_field(n, S, seed=31, log_sd=1.2)
+        U, Q, it, rr, fl = _solve_minres(M, h, n, af, M.MLMC_FP32, p, delta)
+        assert np.all(fl == M.MLMC_F_CONVERGED), fl
+        for s in range(S):
+            x, Qo = o_fem.solve_sample(n, af[s])
+            res = o_fem.relative_residual(n, af[s], _interior(n, U[s]))
+            assert res < delta * (1 + 1e-6)
+            A = o_fem.assemble(n, af[s])
+            lmin = spla.eigsh(A, k=1, sigma=0, which="LM", return_eigenvectors=False)[0]
+            bound = np.linalg.norm(o_fem.qoi_weights(n)) * res * np.linalg.norm(o_fem.load_vector(n)) / lmin
+            assert abs(Q[s] - Qo) <= bound * 1.01
+    finally:
+        M.mlmc_destroy(h)
