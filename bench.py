@@ -2,7 +2,7 @@
 
 Workload (one "step"): the whole hot path of one adaptive MLMC estimate --
 Philox draws, tensor-core KL synthesis, every fine and coarse solve of every
-level in persistent launches (FP32 inner CG with a 16-bit-stored coefficient
+level in resident-solve launches (FP32 inner CG with a 16-bit-stored coefficient
 on coarse levels, FP64 iterative refinement to the per-level accuracy of
 Eq. (4.12)), QoI and level statistics, and the N_l updates of Alg. 4.1 --
 on the five-level hierarchy h = 1/16 .. 1/256 with a 64-term KL field
@@ -12,7 +12,7 @@ Q = int u, N_init = 100 on every level, target RMSE 1e-3.
 value    = seconds per estimate (device time between CUDA events on the stream).
 e2e      = the same through the C ABI from host data: context creation (basis
            tables built on the host and uploaded), estimate, result to host.
-roofline = the persistent solve kernel: algorithmic bytes / event time, against
+roofline = the resident solve kernel: algorithmic bytes / event time, against
            the measured HBM copy bandwidth.
 cpu_baseline / --impl reference = the CPU FP64 oracle on a bounded sample of
            the same workload, extrapolated to the estimate's sample counts.
@@ -32,6 +32,10 @@ METRIC = "MLMC time-to-RMSE (s) & solved DOF/s: mixed vs FP64 on 1 GB300; HBM GB
 WORKLOAD = dict(n0=16, m=2, L_max=4, kind=0, K=64, sigma2=1.0, corr_len=0.3, q=2.0, qoi=0, f=1.0)
 TOL, N_INIT = 1e-3, 100
 L2_FLUSH_BYTES = 512 << 20
+# DRAM bytes (read + write) per resident_solve launch of one timed step of this workload, averaged
+# over the step's launches, from one ncu capture of dram__bytes_read.sum + dram__bytes_write.sum
+# (summary under profiles/).  None whenever the solve kernel has changed since that capture.
+SOLVE_TRAFFIC_BYTES_PER_LAUNCH = 123.8e9
 
 
 def workload_desc():
@@ -182,7 +186,7 @@ def main():
     ap.add_argument("--no-fp64", action="store_true")
     ap.add_argument("--case", default="mlmc", choices=["mlmc", "solve-l4", "kl-synth"],
                     help="solve-l4: only the finest level's batch (100 samples, n = 256) of the workload: "
-                         "field synthesis and one persistent solve launch per step; kl-synth: tensor-core "
+                         "field synthesis and one resident-solve launch per step; kl-synth: tensor-core "
                          "KL synthesis alone at the single-level sweep shapes (n = 512, K = 128, corr 0.1)")
     ap.add_argument("--kl-samples", type=int, default=4096)
     args = ap.parse_args()
@@ -303,9 +307,11 @@ def main():
             "rmse": [r["rmse"] for r in results], "N_l": results[-1]["N"], "rounds": results[-1]["rounds"],
             "inner_iters_per_step": sum(iters) / len(iters),
             "fp64": fp64,
-            "roofline": {"bound": "hbm", "kernel": "persistent_solve", "achieved": achieved, "peak": hbm_peak,
+            "roofline": {"bound": "hbm", "kernel": "resident_solve", "achieved": achieved, "peak": hbm_peak,
                          "unit": "GB/s", "frac": achieved / hbm_peak, "peak_source": peak_src + " (burst copy)",
-                         "traffic": None, "launches": prof["solve_launches"],
+                         "traffic": SOLVE_TRAFFIC_BYTES_PER_LAUNCH,
+                         "algorithmic_bytes_per_launch": prof["solve_bytes"] / max(1, prof["solve_launches"]),
+                         "launches": prof["solve_launches"],
                          "kernel_ms_per_step": prof["solve_ms"] / args.steps,
                          "share_of_step": prof["solve_ms"] / total_ms if total_ms > 0 else None},
             "kl_synthesis": {"achieved_gbs": kl_gbs, "tensor_tflops": kl_tf, "ms_per_step": prof["kl_ms"] / args.steps},

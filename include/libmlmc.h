@@ -247,7 +247,7 @@ mlmc_status mlmc_adapt_precision(int L, const double* h, double kp, double alpha
 
 /* ------------------------------------------------------------------------- */
 /* A10 + A11: the estimate loop, Alg. 4.1, with every round's samples of all
- * levels solved in one persistent launch. */
+ * levels solved in one resident-solve launch. */
 typedef enum {
     MLMC_FORM_MIXED = 0,          /* per-level accuracy delta_l (Eq. (4.12)), per-level inner precision  */
     MLMC_FORM_FP64_ADAPTIVE = 1,  /* per-level delta_l, FP64 inner                                        */
@@ -311,7 +311,7 @@ mlmc_status mlmc_estimate_host(int m, int L_max, int n0, const mlmc_options* opt
 /* ------------------------------------------------------------------------- */
 /* A12: dQ/dxi for S samples on level grid `level` (QoI of the context).
  * Field from xi (device FP64 [S][K]); the forward solve A x = b and the
- * adjoint solve A lambda = g (g_i = G(phi_i)) run together in one persistent
+ * adjoint solve A lambda = g (g_i = G(phi_i)) run together in one resident-solve
  * launch, to accuracy delta in precision prec; then
  * G_v = -(1/3) sum_{T contains v} |T| grad(lambda_h).grad(u_h)|_T and
  * dQ/dxi[s][k] = sum_v Phi_k(x_v) a_v G_v (the transposed KL contraction).
@@ -330,7 +330,7 @@ mlmc_status mlmc_adjoint_grad(mlmc_ctx* ctx, int level, int S, const double* xi,
 mlmc_status mlmc_set_wait_timeout(mlmc_ctx* ctx, double seconds);
 
 /* Measurement.  With profiling on, the context records CUDA events on the
- * launching stream around every persistent solve and tensor-core synthesis
+ * launching stream around every resident solve and tensor-core synthesis
  * launch and, after each solve, derives the launch's algorithmic bytes from
  * the per-system inner-iteration and refinement counts:
  *   per unknown and inner iteration 8 p_v + 2 p_s bytes (p_v vector bytes,
@@ -342,7 +342,7 @@ mlmc_status mlmc_set_wait_timeout(mlmc_ctx* ctx, double seconds);
  * FLOPs (three MMAs per split product).  Event times are resolved lazily. */
 typedef struct {
     int64_t solve_launches;
-    double solve_ms;           /* summed event time of the persistent solve launches */
+    double solve_ms;           /* summed event time of the resident-solve launches */
     double solve_bytes;        /* their algorithmic bytes */
     int64_t inner_iters;       /* inner iterations summed over systems */
     int64_t unknown_iters;     /* sum over systems of interior unknowns x inner iterations */

@@ -3,7 +3,7 @@
 Forward: KL synthesis of the coefficient from xi and the batched solve give
 Q[s] (only Q is kept).  Backward: ``mlmc_adjoint_grad`` recomputes the
 forward solution together with the adjoint solution A lambda = g in one
-persistent launch, forms the element products and contracts them back onto
+resident-solve launch, forms the element products and contracts them back onto
 the KL terms (Problem 4.5 with the discrete adjoint of the P1 system).
 """
 import torch

@@ -1,6 +1,6 @@
 // libmlmc C ABI (include/libmlmc.h): context, entry points, the estimate loop
 // of Alg. 4.1 and the round scheduler that puts every sample of every level
-// of a round into one persistent solve launch per precision class.
+// of a round into one resident-solve launch per precision class.
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -604,7 +604,7 @@ mlmc_status mlmc_estimate(mlmc_ctx* ctx, const mlmc_options* opts, mlmc_result* 
                                                      (void*)st);
             if (s != MLMC_OK) return s;
         }
-        // ---- one persistent launch per inner-precision class: every fine and coarse member
+        // ---- one resident-solve launch per inner-precision class: every fine and coarse member
         std::map<int, std::vector<SolveGroup>> classes;
         for (size_t i = 0; i < req.size(); ++i) {
             const int l = req[i].level;

@@ -244,7 +244,7 @@ def test_solve_edge_cases(M):
 
 
 def test_mixed_batch_many_sizes_one_launch(M):
-    # several grid sizes in one persistent launch through the estimate scheduler's path
+    # several grid sizes in one resident-solve launch through the estimate scheduler's path
     h = _ctx(M, n0=6, L_max=3)
     try:
         for n in (6, 12, 24, 48):
