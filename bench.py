@@ -184,11 +184,17 @@ def main():
     ap.add_argument("--impl", default="libmlmc", choices=["libmlmc", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-fp64", action="store_true")
-    ap.add_argument("--case", default="mlmc", choices=["mlmc", "solve-l4", "kl-synth"],
+    ap.add_argument("--case", default="mlmc", choices=["mlmc", "solve-l4", "kl-synth", "sweep", "adjoint"],
                     help="solve-l4: only the finest level's batch (100 samples, n = 256) of the workload: "
                          "field synthesis and one resident-solve launch per step; kl-synth: tensor-core "
                          "KL synthesis alone at the single-level sweep shapes (n = 512, K = 128, corr 0.1)")
     ap.add_argument("--kl-samples", type=int, default=4096)
+    ap.add_argument("--sweep-samples", type=int, default=4096,
+                    help="sweep: systems per batch (n = 512, K = 128, corr 0.1, fixed delta 1e-6)")
+    ap.add_argument("--prec", default="FP32", choices=["FP64", "FP32", "BF16S", "FP16S"],
+                    help="sweep: inner precision (FP64 uses an FP64 field and FP64 vectors)")
+    ap.add_argument("--ring", type=int, default=-1,
+                    help="solve-l4: row-pipeline slots of the large CG solves (-1 automatic, 0 plain loads)")
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)
@@ -225,6 +231,10 @@ def main():
         return solve_l4_case(M, torch, dev, args, problem(1000), hbm_peak, peak_src, flush, stream)
     if args.case == "kl-synth":
         return kl_synth_case(M, torch, dev, args, hbm_peak, peak_src, flush, stream)
+    if args.case == "sweep":
+        return sweep_case(M, torch, dev, args, hbm_peak, peak_src, flush, stream)
+    if args.case == "adjoint":
+        return adjoint_case(M, torch, dev, args, hbm_peak, peak_src, flush, stream)
 
     def timed_runs(form, steps, warmup, seed0, profile=False):
         h = M.mlmc_create(problem(seed0), local)
@@ -370,6 +380,7 @@ def solve_l4_case(M, torch, dev, args, prob, hbm_peak, peak_src, flush, stream):
     h = M.mlmc_create(prob, dev.index or 0)
     try:
         M.mlmc_profile_enable(h, True)
+        M.mlmc_debug_set_solve_ring(h, args.ring)
         a = torch.empty((S, (n + 1) ** 2), dtype=torch.float32, device=dev)
         Q = torch.empty(S, dtype=torch.float64, device=dev)
         it = torch.empty(S, dtype=torch.int32, device=dev)
@@ -391,13 +402,97 @@ def solve_l4_case(M, torch, dev, args, prob, hbm_peak, peak_src, flush, stream):
     finally:
         M.mlmc_destroy(h)
     achieved = prof["solve_bytes"] / (prof["solve_ms"] * 1e-3) / 1e9
-    print(json.dumps({"case": "solve-l4", "ms_per_step": sum(ms) / len(ms), "systems": S, "n": n,
+    print(json.dumps({"case": "solve-l4", "ring": args.ring, "ms_per_step": sum(ms) / len(ms), "systems": S, "n": n,
                       "delta": deltas[level], "prec": precs[level],
                       "inner_iters_per_system": prof["inner_iters"] / (S * args.steps),
                       "solve_ms_per_launch": prof["solve_ms"] / prof["solve_launches"],
                       "algorithmic_bytes_per_launch": prof["solve_bytes"] / prof["solve_launches"],
                       "achieved_gbs": achieved, "peak_gbs": hbm_peak, "frac": achieved / hbm_peak,
                       "peak_source": peak_src}))
+    return 0
+
+
+def adjoint_case(M, torch, dev, args, hbm_peak, peak_src, flush, stream):
+    """Adjoint gradients dQ/dxi: 1024 samples on the 256 x 256 grid, K = 256, corr 0.1, QoI the
+    integral over [0.25, 0.75]^2; forward and adjoint solves (FP32 inner, FP64 refinement to
+    1e-8) in one launch, then the element products and the contraction onto the KL terms."""
+    S, n, K = 1024, 256, 256
+    prob = M.make_problem(n0=n, m=2, L_max=0, kind=0, K=K, sigma2=1.0, corr_len=0.1, seed=21, qoi=1,
+                          box=(0.25, 0.75, 0.25, 0.75))
+    h = M.mlmc_create(prob, dev.index or 0)
+    try:
+        M.mlmc_profile_enable(h, True)
+        xi = torch.empty((S, K), dtype=torch.float64, device=dev)
+        a = torch.empty((S, (n + 1) ** 2), dtype=torch.float32, device=dev)
+        M.mlmc_sample_fields(h, 0, 0, S, xi, a, M.MLMC_FP32)
+        Q = torch.empty(S, dtype=torch.float64, device=dev)
+        G = torch.empty((S, K), dtype=torch.float64, device=dev)
+        ms = []
+        for s in range(args.warmup + args.steps):
+            if s == args.warmup:
+                M.mlmc_profile_reset(h)
+            flush.fill_(float(s))
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            M.mlmc_adjoint_grad(h, 0, S, xi, M.MLMC_FP32, 1e-8, 200000, Q, G)
+            e1.record(stream)
+            e1.synchronize()
+            if s >= args.warmup:
+                ms.append(e0.elapsed_time(e1))
+        prof = M.mlmc_profile_get(h)
+    finally:
+        M.mlmc_destroy(h)
+    t = sum(ms) / len(ms) / 1e3
+    achieved = prof["solve_bytes"] / (prof["solve_ms"] * 1e-3) / 1e9 if prof["solve_ms"] > 0 else 0.0
+    print(json.dumps({"case": "adjoint", "samples": S, "n": n, "K": K, "seconds_per_batch": t,
+                      "grads_per_s": S / t, "solve_share": prof["solve_ms"] / (sum(ms)),
+                      "solve_achieved_gbs": achieved, "peak_gbs": hbm_peak, "solve_frac": achieved / hbm_peak,
+                      "peak_source": peak_src}))
+    return 0
+
+
+def sweep_case(M, torch, dev, args, hbm_peak, peak_src, flush, stream):
+    """Single-level batched solve: S systems on the 512 x 512 grid (261,121 unknowns each), KL field
+    with K = 128 terms and correlation length 0.1, fixed relative residual 1e-6; solved DOF/s and
+    the solve kernel's HBM rate."""
+    S, n, K, delta = args.sweep_samples, 512, 128, 1e-6
+    prec = getattr(M, "MLMC_" + args.prec)
+    fp64 = prec == M.MLMC_FP64
+    prob = M.make_problem(n0=n, m=2, L_max=0, kind=0, K=K, sigma2=1.0, corr_len=0.1, seed=11)
+    h = M.mlmc_create(prob, dev.index or 0)
+    try:
+        M.mlmc_profile_enable(h, True)
+        M.mlmc_debug_set_solve_ring(h, args.ring)
+        a = torch.empty((S, (n + 1) ** 2), dtype=torch.float64 if fp64 else torch.float32, device=dev)
+        Q = torch.empty(S, dtype=torch.float64, device=dev)
+        it = torch.empty(S, dtype=torch.int32, device=dev)
+        fl = torch.empty(S, dtype=torch.int32, device=dev)
+        fprec = M.MLMC_FP64 if fp64 else M.MLMC_FP32
+        M.mlmc_sample_fields(h, 0, 0, S, None, a, fprec)
+        ms = []
+        for s in range(args.warmup + args.steps):
+            if s == args.warmup:
+                M.mlmc_profile_reset(h)
+            flush.fill_(float(s))
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            M.mlmc_level_solve(h, n, S, a, fprec, n, prec, M.MLMC_CG, delta, 200000, None, Q, it, None, fl)
+            e1.record(stream)
+            e1.synchronize()
+            if s >= args.warmup:
+                ms.append(e0.elapsed_time(e1))
+        prof = M.mlmc_profile_get(h)
+        flags = fl.cpu()
+    finally:
+        M.mlmc_destroy(h)
+    t = sum(ms) / len(ms) / 1e3
+    achieved = prof["solve_bytes"] / (prof["solve_ms"] * 1e-3) / 1e9
+    print(json.dumps({"case": "sweep", "prec": args.prec, "ring": args.ring, "systems": S, "n": n, "delta": delta,
+                      "seconds_per_batch": t, "solved_dof_per_s": S * (n - 1) ** 2 / t,
+                      "inner_iters_per_system": prof["inner_iters"] / (S * args.steps),
+                      "algorithmic_bytes_per_launch": prof["solve_bytes"] / prof["solve_launches"],
+                      "achieved_gbs": achieved, "peak_gbs": hbm_peak, "frac": achieved / hbm_peak,
+                      "peak_source": peak_src, "all_converged": bool((flags == M.MLMC_F_CONVERGED).all())}))
     return 0
 
 

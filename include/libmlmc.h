@@ -66,6 +66,7 @@ typedef enum { MLMC_CG = 0, MLMC_MINRES = 1 } mlmc_solver;   /* Sec. 2.2 */
 #define MLMC_F_MAXIT     2   /* iteration budget exhausted before delta */
 #define MLMC_F_STAGNATED 4   /* an outer refinement step reduced the residual by less than 2x */
 #define MLMC_F_NONFINITE 8   /* NaN / Inf in the residual (e.g. coefficient overflow, Sec. 5.2) */
+#define MLMC_F_TIMEOUT   16  /* a bounded wait of the solve's row pipeline ran out; the solve stopped early */
 
 /* Random log-coefficient, log a(x) = sum_{k<K} xi_k Phi_k(x), xi_k ~ N(0,1). */
 typedef struct {
@@ -290,6 +291,9 @@ typedef struct {
     int64_t dofs[MLMC_MAX_LEVELS];   /* unknowns solved per level (fine + coarse members)         */
     mlmc_acc acc[MLMC_MAX_LEVELS];   /* final level accumulators                                  */
     double seconds;                  /* wall time of the call                                     */
+    int64_t fp64_retries[MLMC_MAX_LEVELS];  /* mixed form: solves re-run with FP64 inner arithmetic
+                                               after their low-precision refinement stagnated or ran
+                                               out of iterations (Cor. 3.4 conditions failed)     */
 } mlmc_result;
 
 /* Fill *opts with the paper's defaults: kp 0.05, (2,1,4,2), alpha 2, gamma 2,
@@ -325,8 +329,9 @@ mlmc_status mlmc_adjoint_grad(mlmc_ctx* ctx, int level, int S, const double* xi,
 
 /* ------------------------------------------------------------------------- */
 /* Diagnostics.  Timeout of every bounded device-side wait of this context, in
- * seconds (default 10).  Used to test the MLMC_E_TIMEOUT path.  (The solves
- * have no device-side waits: each system is solved by one group of threads.) */
+ * seconds (default 10): the tensor-core synthesis waits on its TMA copies and
+ * MMAs, and the large CG solves wait on the bulk row copies of their pipeline.
+ * Used to test the MLMC_E_TIMEOUT path. */
 mlmc_status mlmc_set_wait_timeout(mlmc_ctx* ctx, double seconds);
 
 /* Measurement.  With profiling on, the context records CUDA events on the
@@ -355,14 +360,27 @@ mlmc_status mlmc_profile_get(mlmc_ctx* ctx, mlmc_profile* out);   /* synchronise
 mlmc_status mlmc_profile_reset(mlmc_ctx* ctx);
 
 /* Diagnostics.  Make every bounded wait of this context's tensor-core KL
- * synthesis expect 16 * extra bytes that never arrive (extra = 0 restores
- * normal operation), so that each wait runs out after the timeout.  The kernel
- * then records MLMC_E_TIMEOUT in its error word, waits (bounded) for its own
- * copies, frees its tensor memory and returns; the next synchronising call of
- * the context (mlmc_level_solve, mlmc_level_stats, mlmc_estimate,
- * mlmc_adjoint_grad, mlmc_profile_get) returns MLMC_E_TIMEOUT.  Exists only to
- * test that path; the GPU stays usable. */
+ * synthesis, and the first row-copy wait of each team of a large CG solve,
+ * expect 16 * extra bytes that never arrive (extra = 0 restores normal
+ * operation), so that the wait runs out after the timeout.  The synthesis then
+ * records MLMC_E_TIMEOUT in its error word, waits (bounded) for its own copies,
+ * frees its tensor memory and returns; the next synchronising call of the
+ * context (mlmc_level_solve, mlmc_level_stats, mlmc_estimate,
+ * mlmc_adjoint_grad, mlmc_profile_get) returns MLMC_E_TIMEOUT.  The solve stops
+ * at its next reduction, flags the system MLMC_F_TIMEOUT, waits (bounded) for
+ * its copies in flight, and mlmc_level_solve returns MLMC_E_TIMEOUT.  Exists
+ * only to test those paths; the GPU stays usable. */
 mlmc_status mlmc_debug_set_wait_extra(mlmc_ctx* ctx, int extra);
+
+/* Diagnostics.  Slots per team of the row pipeline of this context's large CG
+ * solves (n >= 91, one 512-thread CTA per system; used for grids whose rows
+ * are a multiple of 128 cells wide).  -1 chooses automatically (default): the
+ * deepest of 4..2 that fits shared memory when the launch has at least one
+ * large system per SM, else none.  0 turns the pipeline off (rows are read with
+ * plain cached loads); 2..4 cap the depth.  The arithmetic is the same either
+ * way, so results are bit-identical; exists to measure the pipeline and to test
+ * that identity. */
+mlmc_status mlmc_debug_set_solve_ring(mlmc_ctx* ctx, int ring);
 
 #ifdef __cplusplus
 }

@@ -27,7 +27,7 @@ MLMC_CG, MLMC_MINRES = range(2)
 # mlmc_form
 MLMC_FORM_MIXED, MLMC_FORM_FP64_ADAPTIVE, MLMC_FORM_FP64_FIXED = range(3)
 # flags
-MLMC_F_CONVERGED, MLMC_F_MAXIT, MLMC_F_STAGNATED, MLMC_F_NONFINITE = 1, 2, 4, 8
+MLMC_F_CONVERGED, MLMC_F_MAXIT, MLMC_F_STAGNATED, MLMC_F_NONFINITE, MLMC_F_TIMEOUT = 1, 2, 4, 8, 16
 
 
 class mlmc_field(ctypes.Structure):
@@ -58,7 +58,8 @@ class mlmc_result(ctypes.Structure):
                 ("N", c_int64 * MLMC_MAX_LEVELS), ("Yhat", c_double * MLMC_MAX_LEVELS),
                 ("s2", c_double * MLMC_MAX_LEVELS), ("delta", c_double * MLMC_MAX_LEVELS),
                 ("prec", c_int32 * MLMC_MAX_LEVELS), ("inner_iters", c_int64 * MLMC_MAX_LEVELS),
-                ("dofs", c_int64 * MLMC_MAX_LEVELS), ("acc", mlmc_acc * MLMC_MAX_LEVELS), ("seconds", c_double)]
+                ("dofs", c_int64 * MLMC_MAX_LEVELS), ("acc", mlmc_acc * MLMC_MAX_LEVELS), ("seconds", c_double),
+                ("fp64_retries", c_int64 * MLMC_MAX_LEVELS)]
 
 
 class mlmc_profile(ctypes.Structure):
@@ -98,6 +99,7 @@ _SIGS = {
                                   c_void_p]),
     "mlmc_set_wait_timeout": (c_int, [c_void_p, c_double]),
     "mlmc_debug_set_wait_extra": (c_int, [c_void_p, c_int]),
+    "mlmc_debug_set_solve_ring": (c_int, [c_void_p, c_int]),
     "mlmc_profile_enable": (c_int, [c_void_p, c_int]),
     "mlmc_profile_get": (c_int, [c_void_p, c_void_p]),
     "mlmc_profile_reset": (c_int, [c_void_p]),
@@ -210,6 +212,10 @@ def mlmc_debug_set_wait_extra(ctx, extra):
     _check(lib().mlmc_debug_set_wait_extra(ctx, extra), ctx)
 
 
+def mlmc_debug_set_solve_ring(ctx, ring):
+    _check(lib().mlmc_debug_set_solve_ring(ctx, ring), ctx)
+
+
 def mlmc_sample_fields(ctx, level, first, S, xi, a, field_prec, stream=None):
     _check(lib().mlmc_sample_fields(ctx, level, first, S, _ptr(xi), _ptr(a), field_prec, _stream(stream)), ctx)
 
@@ -301,4 +307,5 @@ def result_dict(res):
         "N": list(res.N[:L + 1]), "Yhat": list(res.Yhat[:L + 1]), "s2": list(res.s2[:L + 1]),
         "delta": list(res.delta[:L + 1]), "prec": list(res.prec[:L + 1]),
         "inner_iters": list(res.inner_iters[:L + 1]), "dofs": list(res.dofs[:L + 1]), "seconds": res.seconds,
+        "fp64_retries": list(res.fp64_retries[:L + 1]),
     }

@@ -393,6 +393,12 @@ mlmc_status mlmc_debug_set_wait_extra(mlmc_ctx* ctx, int extra) {
     return MLMC_OK;
 }
 
+mlmc_status mlmc_debug_set_solve_ring(mlmc_ctx* ctx, int ring) {
+    if (!ctx || ring < -1 || ring == 1 || ring > 4) return MLMC_E_ARG;
+    ctx->solve_ring = ring;
+    return MLMC_OK;
+}
+
 mlmc_status mlmc_sample_fields(mlmc_ctx* ctx, int level, uint64_t first, int S, double* xi, void* a,
                                mlmc_prec field_prec, void* stream) {
     if (!ctx) return MLMC_E_ARG;
@@ -552,6 +558,7 @@ mlmc_status mlmc_estimate(mlmc_ctx* ctx, const mlmc_options* opts, mlmc_result* 
     int32_t flags_or = 0;
     std::vector<int64_t> iters_lvl(MLMC_MAX_LEVELS, 0), dofs_lvl(MLMC_MAX_LEVELS, 0);
     std::vector<int32_t> prec_lvl(MLMC_MAX_LEVELS, -1);
+    std::vector<int64_t> retries_lvl(MLMC_MAX_LEVELS, 0);
 
     RoundFn round = [&](const std::vector<Request>& req, const std::vector<double>& df, const std::vector<double>& dc,
                         std::vector<mlmc_acc>& out, mlmc_result*) -> mlmc_status {
@@ -606,6 +613,7 @@ mlmc_status mlmc_estimate(mlmc_ctx* ctx, const mlmc_options* opts, mlmc_result* 
         }
         // ---- one resident-solve launch per inner-precision class: every fine and coarse member
         std::map<int, std::vector<SolveGroup>> classes;
+        std::map<int, std::vector<int>> class_level;   // level of each group, for the counters
         for (size_t i = 0; i < req.size(); ++i) {
             const int l = req[i].level;
             const int n = level_n(p, l);
@@ -620,6 +628,7 @@ mlmc_status mlmc_estimate(mlmc_ctx* ctx, const mlmc_options* opts, mlmc_result* 
             gf.iters = itf + qoff[i];
             gf.flags = flf + qoff[i];
             classes[prec_of(l)].push_back(gf);
+            class_level[prec_of(l)].push_back(l);
             prec_lvl[l] = prec_of(l);
             dofs_lvl[l] += (int64_t)req[i].count * (n - 1) * (n - 1);
             if (l > 0) {
@@ -630,6 +639,7 @@ mlmc_status mlmc_estimate(mlmc_ctx* ctx, const mlmc_options* opts, mlmc_result* 
                 gc.iters = itc + qoff[i];
                 gc.flags = flc + qoff[i];
                 classes[prec_of(l - 1)].push_back(gc);
+                class_level[prec_of(l - 1)].push_back(l);
                 dofs_lvl[l] += (int64_t)req[i].count * (gc.n - 1) * (gc.n - 1);
             }
         }
@@ -640,6 +650,47 @@ mlmc_status mlmc_estimate(mlmc_ctx* ctx, const mlmc_options* opts, mlmc_result* 
             cfg.max_iters = o.max_iters;
             const mlmc_status s = run_solve_batch(ctx, kv.second, cfg, st);
             if (s != MLMC_OK) return s;
+        }
+        // ---- Cor. 3.4 safety net: the low-precision conditions can fail for a sample
+        // whose coefficient is rougher than the precision rule assumed; a refinement
+        // that stagnated or ran out of iterations is re-run with FP64 inner arithmetic
+        // to the same delta (Alg. 2.1 with u_f = u), in one more launch.
+        if (o.form == MLMC_FORM_MIXED && classes.size() > (classes.count(MLMC_FP64) ? 1u : 0u)) {
+            std::vector<int32_t> hfl(2 * qn), hit2(2 * qn);
+            MLMC_CUDA_RET(ctx->err, cudaMemcpy(hfl.data(), flf, 2 * qn * sizeof(int32_t), cudaMemcpyDeviceToHost));
+            MLMC_CUDA_RET(ctx->err, cudaMemcpy(hit2.data(), itf, 2 * qn * sizeof(int32_t), cudaMemcpyDeviceToHost));
+            ctx->prof.acc.d2h_bytes += (int64_t)(4 * qn * sizeof(int32_t));
+            std::vector<SolveGroup> retry;
+            for (auto& kv : classes) {
+                if (kv.first == MLMC_FP64) continue;
+                const std::vector<int>& lv = class_level[kv.first];
+                for (size_t gi = 0; gi < kv.second.size(); ++gi) {
+                    const SolveGroup& g = kv.second[gi];
+                    const size_t elem = g.a_fp64 ? sizeof(double) : sizeof(float);
+                    const size_t aV = (size_t)(g.a_n + 1) * (g.a_n + 1);
+                    for (int smp = 0; smp < g.S; ++smp) {
+                        const size_t q = (size_t)(g.flags - flf) + smp;
+                        if (!(hfl[q] & (MLMC_F_STAGNATED | MLMC_F_MAXIT))) continue;
+                        SolveGroup r = g;
+                        r.S = 1;
+                        r.a = static_cast<const char*>(g.a) + smp * aV * elem;
+                        r.Q = g.Q + smp;
+                        r.iters = g.iters + smp;
+                        r.flags = g.flags + smp;
+                        retry.push_back(r);
+                        iters_lvl[lv[gi]] += hit2[q];       // the abandoned attempt's iterations
+                        retries_lvl[lv[gi]] += 1;
+                    }
+                }
+            }
+            if (!retry.empty()) {
+                SolveConfig cfg;
+                cfg.prec = MLMC_FP64;
+                cfg.solver = o.solver;
+                cfg.max_iters = o.max_iters;
+                const mlmc_status s = run_solve_batch(ctx, retry, cfg, st);
+                if (s != MLMC_OK) return s;
+            }
         }
         {
             const mlmc_status s = check_kl_wait(ctx);
@@ -674,6 +725,7 @@ mlmc_status mlmc_estimate(mlmc_ctx* ctx, const mlmc_options* opts, mlmc_result* 
         res->prec[l] = prec_lvl[l];
         res->inner_iters[l] = iters_lvl[l];
         res->dofs[l] = dofs_lvl[l];
+        res->fp64_retries[l] = retries_lvl[l];
     }
     res->flags_or = flags_or;
     const int32_t bad = MLMC_F_MAXIT | MLMC_F_STAGNATED | MLMC_F_NONFINITE;

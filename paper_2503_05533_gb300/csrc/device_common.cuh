@@ -1,5 +1,6 @@
 // Device helpers shared by the libmlmc kernels: the global timer for bounded
-// waits and 4-wide loads of the storage types.
+// waits, mbarriers and bulk asynchronous copies, and 4-wide loads of the
+// storage types.
 #pragma once
 
 #include <cuda_bf16.h>
@@ -17,6 +18,52 @@ __device__ __forceinline__ uint64_t global_ns() {
     asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
     return t;
 }
+
+// ---------------------------------------------------------------------------
+// mbarriers and bulk asynchronous copies (the TMA engine).
+__device__ __forceinline__ uint32_t smem_u32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
+
+__device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
+}
+// One arrival that also raises the phase's expected transaction count by `bytes`.
+__device__ __forceinline__ void mbar_expect_tx(uint64_t* bar, uint32_t bytes) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes)
+                 : "memory");
+}
+__device__ __forceinline__ void mbar_arrive(uint64_t* bar) {
+    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
+}
+// True once the phase of parity `phase` has completed.
+__device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t phase) {
+    uint32_t ok;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}"
+        : "=r"(ok)
+        : "r"(smem_u32(bar)), "r"(phase)
+        : "memory");
+    return ok != 0;
+}
+// Bounded wait: false if the phase has not completed within timeout_ns of wall time.
+__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t phase, uint64_t timeout_ns) {
+    const uint64_t t0 = global_ns();
+    while (!mbar_try_wait(bar, phase))
+        if (global_ns() - t0 > timeout_ns) return false;
+    return true;
+}
+// Copy `bytes` (a multiple of 16; both addresses 16-byte aligned) from global
+// memory into this CTA's shared memory; completion is counted in bytes on `bar`.
+__device__ __forceinline__ void bulk_g2s(void* dst, const void* src, uint32_t bytes, uint64_t* bar) {
+    asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+                     smem_u32(dst)),
+                 "l"(src), "r"(bytes), "r"(smem_u32(bar))
+                 : "memory");
+}
+// Orders this thread's earlier global writes (generic proxy) before later bulk
+// copies (async proxy) that read them.
+__device__ __forceinline__ void fence_proxy_async_global() { asm volatile("fence.proxy.async.global;" ::: "memory"); }
 
 // ---------------------------------------------------------------------------
 // Storage types of the nodal coefficient and vectors: 4 consecutive values
@@ -88,6 +135,42 @@ template <class CT> struct CoefLoad<__nv_bfloat16, CT> {
     static __device__ __forceinline__ CT load1(const __nv_bfloat16* p) {
         return (CT)__bfloat162float(__ldg(p));
     }
+};
+
+// Storage-type values from shared memory (same conversions as CoefLoad).
+template <class ST, class CT> struct SmemLoad;
+template <class CT> struct SmemLoad<double, CT> {
+    static __device__ __forceinline__ void load4(const double* p, CT v[4]) {
+        const double2 a = *reinterpret_cast<const double2*>(p);
+        const double2 b = *(reinterpret_cast<const double2*>(p) + 1);
+        v[0] = (CT)a.x; v[1] = (CT)a.y; v[2] = (CT)b.x; v[3] = (CT)b.y;
+    }
+    static __device__ __forceinline__ CT load1(const double* p) { return (CT)*p; }
+};
+template <class CT> struct SmemLoad<float, CT> {
+    static __device__ __forceinline__ void load4(const float* p, CT v[4]) {
+        const float4 q = *reinterpret_cast<const float4*>(p);
+        v[0] = (CT)q.x; v[1] = (CT)q.y; v[2] = (CT)q.z; v[3] = (CT)q.w;
+    }
+    static __device__ __forceinline__ CT load1(const float* p) { return (CT)*p; }
+};
+template <class CT> struct SmemLoad<__half, CT> {
+    static __device__ __forceinline__ void load4(const __half* p, CT v[4]) {
+        const uint2 q = *reinterpret_cast<const uint2*>(p);
+        const float2 a = __half22float2(*reinterpret_cast<const __half2*>(&q.x));
+        const float2 b = __half22float2(*reinterpret_cast<const __half2*>(&q.y));
+        v[0] = (CT)a.x; v[1] = (CT)a.y; v[2] = (CT)b.x; v[3] = (CT)b.y;
+    }
+    static __device__ __forceinline__ CT load1(const __half* p) { return (CT)__half2float(*p); }
+};
+template <class CT> struct SmemLoad<__nv_bfloat16, CT> {
+    static __device__ __forceinline__ void load4(const __nv_bfloat16* p, CT v[4]) {
+        const uint2 q = *reinterpret_cast<const uint2*>(p);
+        const float2 a = __bfloat1622float2(*reinterpret_cast<const __nv_bfloat162*>(&q.x));
+        const float2 b = __bfloat1622float2(*reinterpret_cast<const __nv_bfloat162*>(&q.y));
+        v[0] = (CT)a.x; v[1] = (CT)a.y; v[2] = (CT)b.x; v[3] = (CT)b.y;
+    }
+    static __device__ __forceinline__ CT load1(const __nv_bfloat16* p) { return (CT)__bfloat162float(*p); }
 };
 
 // Widen one stored coefficient value (a register, not memory) to the compute type.

@@ -91,6 +91,7 @@ struct mlmc_ctx {
     unsigned* kl_err = nullptr;   // error word of the tensor-core synthesis (device, 4 bytes)
     int kl_err_pending = 0;       // a synthesis ran since the word was last read
     int wait_extra = 0;           // diagnostic: bytes every tensor-core wait expects and never receives
+    int solve_ring = -1;          // diagnostic: row-pipeline slots of large CG solves (-1 automatic, 0 off)
     mlmc::Profile prof;
 };
 

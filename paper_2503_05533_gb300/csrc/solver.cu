@@ -86,7 +86,22 @@ struct Params {
     int max_outer, max_iters;
     double theta, tau_min, tau_max, stag;
     int jacobi;
+    int ring;                // row-pipeline slots per team of a 512-thread CG group (0: no pipeline)
+    unsigned* err;           // error word of the launch (KERR_*)
+    unsigned long long timeout_ns;   // bound of every pipeline wait
+    unsigned extra_tx;       // diagnostic: bytes a team's first full barrier expects and never receives
 };
+
+// Shared memory of the row pipeline.  A system of n cells is swept by
+// nseg = 512 / cpr teams of cpr threads (cpr = 4-node chunks per row); each
+// team owns `ring` slots large enough for the five rows (three vectors, two
+// storage-type arrays) of one step of the update sweep.
+__host__ __device__ constexpr int pipe_nseg(int n) { return (512 / ((n - 1) / 4 + 1)) > 1 ? 512 / ((n - 1) / 4 + 1) : 1; }
+__host__ __device__ constexpr int pipe_slot_bytes(int ld, int pv, int ps) { return ((3 * pv + 2 * ps) * ld + 127) / 128 * 128; }
+__host__ __device__ constexpr int pipe_bar_bytes(int n, int ring) { return (16 * ring * pipe_nseg(n) + 127) / 128 * 128; }
+__host__ __device__ constexpr int pipe_smem_bytes(int n, int ld, int ring, int pv, int ps) {
+    return pipe_bar_bytes(n, ring) + pipe_nseg(n) * ring * pipe_slot_bytes(ld, pv, ps);
+}
 
 // ---------------------------------------------------------------------------
 // The 5-point P1 stencil at one node from its coefficient neighbourhood.
@@ -176,16 +191,18 @@ __device__ __forceinline__ double rhs_value(const DevSolve& S, int i, int j) {
 
 // ---------------------------------------------------------------------------
 // Groups of GT threads that solve one system.
-__device__ __forceinline__ double warp_sum_bcast(double v) {
+template <class T>
+__device__ __forceinline__ T warp_allsum(T v) {
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-    return __shfl_sync(0xffffffffu, v, 0);   // lanes may differ in the last bit: take lane 0's
+    return v;   // an xor butterfly leaves the same bits in every lane: addition commutes
 }
 
 template <int GT>
 struct Group {
     int rank, gid;           // thread rank in the group, group index in the CTA
     double* red;             // 3 * (GT / 32) doubles of shared scratch
+    double* bc;              // 4 doubles: results broadcast by the group's first thread
     __device__ __forceinline__ void sync() const {
         if (GT == 32) {
             __syncwarp();
@@ -195,31 +212,60 @@ struct Group {
             asm volatile("bar.sync %0, %1;" ::"r"(gid + 1), "r"(GT) : "memory");
         }
     }
-    // Sums of three values over the group, in a fixed order; every thread gets the same bits.
-    __device__ __forceinline__ void sum3(double& a, double& b, double& c) const {
-        a = warp_sum_bcast(a);
-        b = warp_sum_bcast(b);
-        c = warp_sum_bcast(c);
-        if (GT == 32) return;
-        constexpr int W = GT / 32;
-        const int w = rank >> 5;
-        if ((rank & 31) == 0) {
-            red[w] = a;
-            red[W + w] = b;
-            red[2 * W + w] = c;
-        }
-        sync();
-        double ta = 0.0, tb = 0.0, tc = 0.0;
+    // Sums over the group of three per-thread values of type T -- a butterfly
+    // in T within each warp, then the warp sums in FP64 in a fixed order by the
+    // first warp -- then fn(sum_a, sum_b, sum_c, r) evaluated once (by every
+    // lane of a one-warp group, by thread 0 otherwise).  Every thread returns
+    // the same r[0..3], converted to OT.
+    template <class T, class OT, class FN>
+    __device__ __forceinline__ void reduce(T a, T b, T c, FN fn, OT out[4]) const {
+        a = warp_allsum(a);
+        b = warp_allsum(b);
+        c = warp_allsum(c);
+        if (GT == 32) {
+            double r[4] = {0.0, 0.0, 0.0, 0.0};
+            fn((double)a, (double)b, (double)c, r);
 #pragma unroll
-        for (int i = 0; i < W; ++i) {
-            ta += red[i];
-            tb += red[W + i];
-            tc += red[2 * W + i];
+            for (int i = 0; i < 4; ++i) out[i] = (OT)r[i];
+            return;
+        }
+        constexpr int W = GT / 32;
+        const int w = rank >> 5, lane = rank & 31;
+        if (lane == 0) {
+            red[w] = (double)a;
+            red[W + w] = (double)b;
+            red[2 * W + w] = (double)c;
         }
         sync();
-        a = ta;
-        b = tb;
-        c = tc;
+        if (w == 0) {
+            double ta = lane < W ? red[lane] : 0.0;
+            double tb = lane < W ? red[W + lane] : 0.0;
+            double tc = lane < W ? red[2 * W + lane] : 0.0;
+            ta = warp_allsum(ta);
+            tb = warp_allsum(tb);
+            tc = warp_allsum(tc);
+            if (lane == 0) {
+                double r[4] = {0.0, 0.0, 0.0, 0.0};
+                fn(ta, tb, tc, r);
+                OT* o = reinterpret_cast<OT*>(bc);
+#pragma unroll
+                for (int i = 0; i < 4; ++i) o[i] = (OT)r[i];
+            }
+        }
+        sync();
+        const OT* o = reinterpret_cast<const OT*>(bc);
+#pragma unroll
+        for (int i = 0; i < 4; ++i) out[i] = o[i];
+    }
+    // Plain group sums, the same bits in every thread.
+    template <class T>
+    __device__ __forceinline__ void sum3(T a, T b, T c, double& sa, double& sb, double& sc) const {
+        double o[4];
+        reduce<T, double>(a, b, c, [](double x, double y, double z, double* r) { r[0] = x; r[1] = y; r[2] = z; },
+                          o);
+        sa = o[0];
+        sb = o[1];
+        sc = o[2];
     }
 };
 
@@ -249,46 +295,69 @@ __device__ __forceinline__ void apply_rows(const CT* aS, const CT* aC, const CT*
     }
 }
 
+// Halo columns 4c-1 and 4c+4 of a chunk row: every lane loads its own, in the
+// same batch as the row's four values (columns outside 0..n give 0).  Loading
+// them beats fetching them from the neighbouring lanes by shuffles here: the
+// sweeps are latency-bound, the loads overlap with the row's own loads and hit
+// L1, whereas a shuffle adds a dependent step after them.
+template <class T, class F>
+__device__ __forceinline__ void halo_edges(int n, int c, F edge, T v[6]) {
+    v[0] = (c > 0) ? edge(4 * c - 1) : (T)0;
+    v[5] = (4 * c + 4 <= n) ? edge(4 * c + 4) : (T)0;
+}
+
+// Rounded-to-nearest products and FMAs, so that a value is formed with the same
+// roundings wherever it is formed (its owner lane or a neighbour's halo).
+__device__ __forceinline__ float mul_rn(float a, float b) { return __fmul_rn(a, b); }
+__device__ __forceinline__ double mul_rn(double a, double b) { return __dmul_rn(a, b); }
+__device__ __forceinline__ float fma_rn(float a, float b, float c) { return __fmaf_rn(a, b, c); }
+__device__ __forceinline__ double fma_rn(double a, double b, double c) { return __fma_rn(a, b, c); }
+
+// p = z + beta p_old with z = D^-1 r (JAC) or r, and p_old only when PREV.
+template <class VT, bool JAC, bool PREV>
+__device__ __forceinline__ VT dir_value(VT r, VT dinv, VT po, VT beta) {
+    VT z = JAC ? mul_rn(r, dinv) : r;
+    return PREV ? fma_rn(beta, po, z) : z;
+}
+
 // One row of the storage-type coefficient at columns 4c-1 .. 4c+4.
 template <class ST, class CT>
 __device__ __forceinline__ void coef_row(const ST* AS, int ld, int n, int jj, int c, CT v[6]) {
-    const ST* row = AS + (size_t)jj * ld + 4 * c;
-    CoefLoad<ST, CT>::load4(row, &v[1]);
-    v[0] = (c > 0) ? CoefLoad<ST, CT>::load1(row - 1) : (CT)0;
-    v[5] = (4 * c + 4 <= n) ? CoefLoad<ST, CT>::load1(row + 4) : (CT)0;
+    const ST* rowb = AS + (size_t)jj * ld;
+    CoefLoad<ST, CT>::load4(rowb + 4 * c, &v[1]);
+    halo_edges<CT>(n, c, [&](int col) -> CT { return CoefLoad<ST, CT>::load1(rowb + col); }, v);
 }
 
 // One row of a vector at columns 4c-1 .. 4c+4.
 template <class VT>
 __device__ __forceinline__ void vec_row(const VT* V, int ld, int n, int jj, int c, VT v[6]) {
-    const VT* row = V + (size_t)jj * ld + 4 * c;
-    Vec4<VT>::load(row, &v[1]);
-    v[0] = (c > 0) ? row[-1] : (VT)0;
-    v[5] = (4 * c + 4 <= n) ? row[4] : (VT)0;
+    const VT* rowb = V + (size_t)jj * ld;
+    Vec4<VT>::load(rowb + 4 * c, &v[1]);
+    halo_edges<VT>(n, c, [&](int col) -> VT { return rowb[col]; }, v);
 }
 
-// Direction at one row: p = z + beta p_old, z = D^-1 r (JAC) or r; p_old only when PREV.
+// Direction at one row (columns 4c-1 .. 4c+4).
 template <class VT, class ST, bool JAC, bool PREV>
 __device__ __forceinline__ void dir_row(const VT* R, const ST* DI, const VT* PO, VT beta, int ld, int n, int jj,
                                         int c, VT v[6]) {
-    vec_row<VT>(R, ld, n, jj, c, v);
-    if (JAC) {
-        VT dd[6];
-        coef_row<ST, VT>(DI, ld, n, jj, c, dd);
+    const size_t rb = (size_t)jj * ld;
+    VT r4[4], d4[4] = {(VT)0, (VT)0, (VT)0, (VT)0}, o4[4] = {(VT)0, (VT)0, (VT)0, (VT)0};
+    Vec4<VT>::load(R + rb + 4 * c, r4);
+    if (JAC) CoefLoad<ST, VT>::load4(DI + rb + 4 * c, d4);
+    if (PREV) Vec4<VT>::load(PO + rb + 4 * c, o4);
+    halo_edges<VT>(n, c,
+                   [&](int col) -> VT {
+                       return dir_value<VT, JAC, PREV>(R[rb + col], JAC ? CoefLoad<ST, VT>::load1(DI + rb + col) : (VT)0,
+                                                       PREV ? PO[rb + col] : (VT)0, beta);
+                   },
+                   v);
 #pragma unroll
-        for (int q = 0; q < 6; ++q) v[q] *= dd[q];
-    }
-    if (PREV) {
-        VT po[6];
-        vec_row<VT>(PO, ld, n, jj, c, po);
-#pragma unroll
-        for (int q = 0; q < 6; ++q) v[q] = v[q] + beta * po[q];
-    }
+    for (int q = 0; q < 4; ++q) v[q + 1] = dir_value<VT, JAC, PREV>(r4[q], d4[q], o4[q], beta);
 }
 
 // I1 sweep: writes p_new on rows [ja, jb) and returns this thread's part of (p, A p).
 template <class VT, class ST, bool JAC, bool PREV>
-__device__ __forceinline__ double sweep_dir(const VT* R, const ST* DI, const VT* PO, VT* PN, const ST* AS, VT beta,
+__device__ __forceinline__ VT sweep_dir(const VT* R, const ST* DI, const VT* PO, VT* PN, const ST* AS, VT beta,
                                             int ld, int n, int c, int ja, int jb) {
     VT pm[6], p0[6], pp[6], am[6], a0[6], ap[6];
     dir_row<VT, ST, JAC, PREV>(R, DI, PO, beta, ld, n, ja - 1, c, pm);
@@ -312,13 +381,13 @@ __device__ __forceinline__ double sweep_dir(const VT* R, const ST* DI, const VT*
             a0[q] = ap[q];
         }
     }
-    return (double)acc;
+    return acc;
 }
 
 // I2 sweep: d += alpha p, r -= alpha A p on rows [ja, jb); returns (||r||^2, (r, z)) parts.
 template <class VT, class ST, bool JAC>
 __device__ __forceinline__ void sweep_upd(const VT* PK, VT* R, VT* D, const ST* DI, const ST* AS, VT alpha, int ld,
-                                          int n, int c, int ja, int jb, double& rr, double& rz) {
+                                          int n, int c, int ja, int jb, VT& rr, VT& rz) {
     VT pm[6], p0[6], pp[6], am[6], a0[6], ap[6];
     vec_row<VT>(PK, ld, n, ja - 1, c, pm);
     vec_row<VT>(PK, ld, n, ja, c, p0);
@@ -352,8 +421,286 @@ __device__ __forceinline__ void sweep_upd(const VT* PK, VT* R, VT* D, const ST* 
             a0[q] = ap[q];
         }
     }
-    rr = (double)acc_r;
-    rz = (double)acc_z;
+    rr = acc_r;
+    rz = acc_z;
+}
+
+
+// ---------------------------------------------------------------------------
+// Row pipeline of the 512-thread CG groups.  The row segments of a system are
+// teams of cpr threads.  A team streams the rows its sweep needs through a ring
+// of shared-memory slots: its first thread issues bulk asynchronous copies of
+// whole rows (the TMA engine) ring - 1 steps ahead of the row being computed,
+// so loads never wait on HBM latency.  Slot s has a `full` mbarrier (one
+// arrival plus the copied bytes) and an `empty` mbarrier (one arrival per team
+// thread, when it has read the slot).  Every wait is bounded in wall time; on
+// expiry the CTA raises its abort flag and the launch's error word, every
+// later wait returns at once, the sweeps run to their ends on whatever the
+// slots hold, and the solve stops at its next reduction.
+struct Pipe {
+    uint8_t* slots = nullptr;    // this team's ring
+    uint64_t* full = nullptr;
+    uint64_t* empty = nullptr;
+    int ring = 0, slot_bytes = 0;
+    // consumer position (the same in every team thread): slot and parity of the next step
+    int cslot = 0;
+    unsigned cphase = 0;
+    // producer position (team leader): slot, parity and count of the next step to issue
+    int pslot = 0;
+    unsigned pphase = 0;
+    unsigned issued = 0;
+    bool leader = false;         // lane 0 of the leader warp: owns the producer position
+    bool lead_warp = false;      // the team's first warp issues the copies
+    int* abort = nullptr;        // CTA abort flag (shared memory)
+    unsigned* err = nullptr;
+    unsigned long long timeout_ns = 0;
+    unsigned extra_tx = 0;
+};
+
+__device__ __forceinline__ bool pipe_aborted(const Pipe& p) { return *(volatile int*)p.abort != 0; }
+
+__device__ __forceinline__ bool pipe_wait(Pipe& p, uint64_t* bar, uint32_t parity) {
+    if (mbar_try_wait(bar, parity)) return true;
+    const uint64_t t0 = global_ns();
+    while (!mbar_try_wait(bar, parity)) {
+        if (pipe_aborted(p)) return false;
+        if (global_ns() - t0 > p.timeout_ns) {
+            *(volatile int*)p.abort = 1;
+            atomicCAS(p.err, KERR_NONE, KERR_TIMEOUT);
+            return false;
+        }
+    }
+    return true;
+}
+
+// Leader: claim the slot of the next step once every team thread has read its
+// previous contents (the empty phase one lap earlier), and announce `bytes` on
+// its full barrier.  nullptr after an abort.
+__device__ __forceinline__ uint8_t* pipe_produce(Pipe& p, uint32_t bytes, uint64_t*& bar) {
+    const int s = p.pslot;
+    if (p.issued >= (unsigned)p.ring && !pipe_wait(p, p.empty + s, p.pphase ^ 1u)) return nullptr;
+    if (pipe_aborted(p)) return nullptr;
+    bar = p.full + s;
+    mbar_expect_tx(bar, bytes + (p.issued == 0 ? p.extra_tx : 0u));
+    ++p.issued;
+    if (++p.pslot == p.ring) {
+        p.pslot = 0;
+        p.pphase ^= 1u;
+    }
+    return p.slots + (size_t)s * p.slot_bytes;
+}
+
+// Every team thread: wait for the next step's rows, then release the slot once read.
+__device__ __forceinline__ const uint8_t* pipe_acquire(Pipe& p) {
+    pipe_wait(p, p.full + p.cslot, p.cphase);
+    return p.slots + (size_t)p.cslot * p.slot_bytes;
+}
+__device__ __forceinline__ void pipe_release(Pipe& p) {
+    mbar_arrive(p.empty + p.cslot);
+    if (++p.cslot == p.ring) {
+        p.cslot = 0;
+        p.cphase ^= 1u;
+    }
+}
+
+// Leader, after an abort: wait (bounded) for the copies of each slot's last issued step.
+__device__ __forceinline__ void pipe_drain(Pipe& p) {
+    for (int s = 0; s < p.ring; ++s) {
+        if (p.issued <= (unsigned)s) continue;
+        const unsigned g = p.issued - 1u - ((p.issued - 1u - (unsigned)s) % (unsigned)p.ring);
+        mbar_wait(p.full + s, (g / (unsigned)p.ring) & 1u, p.timeout_ns);
+    }
+}
+
+// Leader warp: issue one pipeline step -- lane 0 claims the slot and posts the
+// step's `total` bytes, then every lane holding a copy (src != nullptr) issues
+// it into slot + off.  Returns false after an abort.
+__device__ __forceinline__ bool pipe_issue_step(Pipe& p, uint32_t total, const void* src, uint32_t off,
+                                                uint32_t bytes) {
+    const int lane = threadIdx.x & 31;
+    uint8_t* dst = nullptr;
+    uint64_t* bar = nullptr;
+    if (lane == 0) dst = pipe_produce(p, total, bar);
+    dst = reinterpret_cast<uint8_t*>(__shfl_sync(0xffffffffu, reinterpret_cast<unsigned long long>(dst), 0));
+    bar = reinterpret_cast<uint64_t*>(__shfl_sync(0xffffffffu, reinterpret_cast<unsigned long long>(bar), 0));
+    if (!dst) return false;
+    if (src) bulk_g2s(dst + off, src, bytes, bar);
+    return true;
+}
+
+// A row of a vector (columns 4c-1 .. 4c+4) from a shared-memory slot.
+template <class VT>
+__device__ __forceinline__ void srow_vec(const VT* row, int n, int c, VT v[6]) {
+    Vec4<VT>::load(row + 4 * c, &v[1]);
+    halo_edges<VT>(n, c, [&](int col) -> VT { return row[col]; }, v);
+}
+// A row of a storage-type array (columns 4c-1 .. 4c+4) from a shared-memory slot.
+template <class ST, class CT>
+__device__ __forceinline__ void srow_coef(const ST* row, int n, int c, CT v[6]) {
+    SmemLoad<ST, CT>::load4(row + 4 * c, &v[1]);
+    halo_edges<CT>(n, c, [&](int col) -> CT { return SmemLoad<ST, CT>::load1(row + col); }, v);
+}
+
+// I1 sweep through the pipeline: the same arithmetic as sweep_dir.  Step t
+// carries row ja - 1 + t of r, D^-1, p_old and the coefficient.
+template <class VT, class ST, bool JAC, bool PREV>
+__device__ __forceinline__ VT sweep_dir_staged(Pipe& p, const VT* R, const ST* DI, const VT* PO, VT* PN,
+                                               const ST* AS, VT beta, int ld, int n, int c, int ja, int jb) {
+    const uint32_t rv = (uint32_t)ld * sizeof(VT), rs = (uint32_t)ld * sizeof(ST);
+    const uint32_t o_di = rv, o_po = o_di + (JAC ? rs : 0u), o_as = o_po + (PREV ? rv : 0u);
+    const uint32_t total = o_as + rs;
+    const int nsteps = jb - ja + 2;                 // rows ja-1 .. jb
+    int next = 0;                                   // leader warp: next step of this sweep to issue
+    auto issue_to = [&](int upto) {
+        for (; next < upto && next < nsteps; ++next) {
+            const size_t row = (size_t)(ja - 1 + next) * ld;
+            // lane 0: r; lane 1: D^-1 (JAC); next lane: p_old (PREV); next lane: coefficient
+            constexpr int l_di = JAC ? 1 : -1, l_po = PREV ? (JAC ? 2 : 1) : -1, l_as = 1 + JAC + PREV;
+            const int lane = threadIdx.x & 31;
+            const void* src = nullptr;
+            uint32_t off = 0, by = 0;
+            if (lane == 0) { src = R + row; off = 0; by = rv; }
+            if (lane == l_di) { src = DI + row; off = o_di; by = rs; }
+            if (lane == l_po) { src = PO + row; off = o_po; by = rv; }
+            if (lane == l_as) { src = AS + row; off = o_as; by = rs; }
+            if (!pipe_issue_step(p, total, src, off, by)) {
+                next = nsteps;
+                break;
+            }
+        }
+    };
+    const int depth = p.ring - 1;
+    int taken = 0;
+    auto take = [&](VT* pv, VT* av) {
+        const uint8_t* sl = pipe_acquire(p);
+        const VT* rrow = reinterpret_cast<const VT*>(sl);
+        const ST* drow = reinterpret_cast<const ST*>(sl + o_di);
+        const VT* prow = reinterpret_cast<const VT*>(sl + o_po);
+        VT r4[4], d4[4] = {(VT)0, (VT)0, (VT)0, (VT)0}, o4[4] = {(VT)0, (VT)0, (VT)0, (VT)0};
+        Vec4<VT>::load(rrow + 4 * c, r4);
+        if (JAC) SmemLoad<ST, VT>::load4(drow + 4 * c, d4);
+        if (PREV) Vec4<VT>::load(prow + 4 * c, o4);
+        halo_edges<VT>(n, c,
+                       [&](int col) -> VT {
+                           return dir_value<VT, JAC, PREV>(rrow[col], JAC ? SmemLoad<ST, VT>::load1(drow + col) : (VT)0,
+                                                           PREV ? prow[col] : (VT)0, beta);
+                       },
+                       pv);
+#pragma unroll
+        for (int q = 0; q < 4; ++q) pv[q + 1] = dir_value<VT, JAC, PREV>(r4[q], d4[q], o4[q], beta);
+        srow_coef<ST, VT>(reinterpret_cast<const ST*>(sl + o_as), n, c, av);
+        pipe_release(p);
+        ++taken;
+        if (p.lead_warp) issue_to(taken + depth);
+    };
+    if (p.lead_warp) issue_to(depth);
+    VT pm[6], p0[6], pp[6], am[6], a0[6], ap[6];
+    take(pm, am);
+    take(p0, a0);
+    VT acc = 0;
+    for (int j = ja; j < jb; ++j) {
+        take(pp, ap);
+        VT y[4];
+        apply_rows<VT>(am, a0, ap, &pm[1], p0, &pp[1], n, c, y);
+        Vec4<VT>::store(PN + (size_t)j * ld + 4 * c, &p0[1]);
+#pragma unroll
+        for (int q = 0; q < 4; ++q) acc += p0[q + 1] * y[q];
+#pragma unroll
+        for (int q = 0; q < 6; ++q) {
+            pm[q] = p0[q];
+            p0[q] = pp[q];
+            am[q] = a0[q];
+            a0[q] = ap[q];
+        }
+    }
+    fence_proxy_async_global();
+    return acc;
+}
+
+// I2 sweep through the pipeline: the same arithmetic as sweep_upd.  Steps 0
+// and 1 carry rows ja-1 and ja of p and the coefficient; step 2+q carries row
+// ja+q+1 of p and the coefficient and row ja+q of d, r and D^-1.
+template <class VT, class ST, bool JAC>
+__device__ __forceinline__ void sweep_upd_staged(Pipe& p, const VT* PK, VT* R, VT* D, const ST* DI, const ST* AS,
+                                                 VT alpha, int ld, int n, int c, int ja, int jb, VT& rr, VT& rz) {
+    const uint32_t rv = (uint32_t)ld * sizeof(VT), rs = (uint32_t)ld * sizeof(ST);
+    const uint32_t o_as = rv, o_d = o_as + rs, o_r = o_d + rv, o_di = o_r + rv;
+    const int nsteps = jb - ja + 2;
+    int next = 0;
+    auto issue_to = [&](int upto) {
+        for (; next < upto && next < nsteps; ++next) {
+            const size_t rowk = (size_t)(ja - 1 + next) * ld;
+            const size_t rowo = (size_t)(ja - 2 + next) * ld;
+            // lanes 0, 1: p and coefficient at row ja-1+next; lanes 2, 3, 4: d, r, D^-1 at row ja-2+next
+            const int lane = threadIdx.x & 31;
+            const bool own = next >= 2;
+            const void* src = nullptr;
+            uint32_t off = 0, by = 0;
+            if (lane == 0) { src = PK + rowk; off = 0; by = rv; }
+            if (lane == 1) { src = AS + rowk; off = o_as; by = rs; }
+            if (own && lane == 2) { src = D + rowo; off = o_d; by = rv; }
+            if (own && lane == 3) { src = R + rowo; off = o_r; by = rv; }
+            if (own && JAC && lane == 4) { src = DI + rowo; off = o_di; by = rs; }
+            const uint32_t total = own ? o_di + (JAC ? rs : 0u) : o_d;
+            if (!pipe_issue_step(p, total, src, off, by)) {
+                next = nsteps;
+                break;
+            }
+        }
+    };
+    const int depth = p.ring - 1;
+    int taken = 0;
+    if (p.lead_warp) issue_to(depth);
+    VT pm[6], p0[6], pp[6], am[6], a0[6], ap[6];
+    {
+        const uint8_t* sl = pipe_acquire(p);
+        srow_vec<VT>(reinterpret_cast<const VT*>(sl), n, c, pm);
+        srow_coef<ST, VT>(reinterpret_cast<const ST*>(sl + o_as), n, c, am);
+        pipe_release(p);
+        ++taken;
+        if (p.lead_warp) issue_to(taken + depth);
+        sl = pipe_acquire(p);
+        srow_vec<VT>(reinterpret_cast<const VT*>(sl), n, c, p0);
+        srow_coef<ST, VT>(reinterpret_cast<const ST*>(sl + o_as), n, c, a0);
+        pipe_release(p);
+        ++taken;
+        if (p.lead_warp) issue_to(taken + depth);
+    }
+    VT acc_r = 0, acc_z = 0;
+    for (int j = ja; j < jb; ++j) {
+        const uint8_t* sl = pipe_acquire(p);
+        srow_vec<VT>(reinterpret_cast<const VT*>(sl), n, c, pp);
+        srow_coef<ST, VT>(reinterpret_cast<const ST*>(sl + o_as), n, c, ap);
+        VT dv[4], rv4[4], zz[4];
+        Vec4<VT>::load(reinterpret_cast<const VT*>(sl + o_d) + 4 * c, dv);
+        Vec4<VT>::load(reinterpret_cast<const VT*>(sl + o_r) + 4 * c, rv4);
+        if (JAC) SmemLoad<ST, VT>::load4(reinterpret_cast<const ST*>(sl + o_di) + 4 * c, zz);
+        pipe_release(p);
+        ++taken;
+        if (p.lead_warp) issue_to(taken + depth);
+        VT y[4];
+        apply_rows<VT>(am, a0, ap, &pm[1], p0, &pp[1], n, c, y);
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+            dv[q] = dv[q] + alpha * p0[q + 1];
+            rv4[q] = rv4[q] - alpha * y[q];
+            acc_r += rv4[q] * rv4[q];
+            acc_z += JAC ? rv4[q] * (rv4[q] * zz[q]) : rv4[q] * rv4[q];
+        }
+        const size_t base = (size_t)j * ld + 4 * c;
+        Vec4<VT>::store(D + base, dv);
+        Vec4<VT>::store(R + base, rv4);
+#pragma unroll
+        for (int q = 0; q < 6; ++q) {
+            pm[q] = p0[q];
+            p0[q] = pp[q];
+            am[q] = a0[q];
+            a0[q] = ap[q];
+        }
+    }
+    fence_proxy_async_global();
+    rr = acc_r;
+    rz = acc_z;
 }
 
 
@@ -383,7 +730,7 @@ __device__ __forceinline__ void minres_update_chunk(const VT* ZP, VT gpi, VT* WO
 
 // Sweep A: this thread's part of delta_j = (A zn_j, zn_j); with UPD, also the pending update.
 template <class VT, class ST, bool UPD>
-__device__ __forceinline__ double sweep_minres_a(const VT* ZC, VT gci, const ST* AS, int ld, int n, int c, int ja,
+__device__ __forceinline__ VT sweep_minres_a(const VT* ZC, VT gci, const ST* AS, int ld, int n, int c, int ja,
                                                  int jb, const VT* ZP, VT gpi, VT* WO, const VT* WN, VT* D, VT a1i,
                                                  VT a2, VT a3, VT cst) {
     VT zm[6], z0[6], zp[6], am[6], a0[6], ap[6];
@@ -415,13 +762,13 @@ __device__ __forceinline__ double sweep_minres_a(const VT* ZC, VT gci, const ST*
             a0[q] = ap[q];
         }
     }
-    return (double)acc;
+    return acc;
 }
 
 // Sweep B: v_{j+1} = A zn_j - cA v_j - cB v_{j-1} (over v_{j-1}), z_{j+1} = D^-1 v_{j+1} or v_{j+1};
 // returns this thread's part of (z_{j+1}, v_{j+1}).
 template <class VT, class ST, bool JAC>
-__device__ __forceinline__ double sweep_minres_b(const VT* ZC, VT gci, const ST* AS, VT* VP, const VT* VC,
+__device__ __forceinline__ VT sweep_minres_b(const VT* ZC, VT gci, const ST* AS, VT* VP, const VT* VC,
                                                  const ST* DI, VT* ZN, VT cA, VT cB, int ld, int n, int c, int ja,
                                                  int jb) {
     VT zm[6], z0[6], zp[6], am[6], a0[6], ap[6];
@@ -463,12 +810,14 @@ __device__ __forceinline__ double sweep_minres_b(const VT* ZC, VT gci, const ST*
             a0[q] = ap[q];
         }
     }
-    return (double)acc;
+    return acc;
 }
 
 // One system, start to finish: set-up, refinement loop with the inner PCG, QoI.
+// `pipe` is non-null for a 512-thread CG group whose sweeps stream rows
+// through shared memory.
 template <class VT, class ST, int SOLVER, int GT>
-__device__ void solve_system(const Params& P, const DevSolve& S, const Group<GT>& G) {
+__device__ void solve_system(const Params& P, const DevSolve& S, const Group<GT>& G, Pipe* pipe) {
     const int n = S.n, ld = S.ld, cpr = S.cpr;
     const int items = (n - 1) * cpr;
     const int tr = G.rank;
@@ -481,6 +830,7 @@ __device__ void solve_system(const Params& P, const DevSolve& S, const Group<GT>
     ST* DI = static_cast<ST*>(P.dinv) + S.off;
     const bool jac = P.jacobi != 0;
     constexpr bool minres = SOLVER == MLMC_MINRES;
+    const bool pipe_on = pipe != nullptr;
     VT* VB = minres ? static_cast<VT*>(P.vb) + S.off : nullptr;
     VT* W0 = minres ? static_cast<VT*>(P.w0) + S.off : nullptr;
     VT* W1 = minres ? static_cast<VT*>(P.w1) + S.off : nullptr;
@@ -504,6 +854,7 @@ __device__ void solve_system(const Params& P, const DevSolve& S, const Group<GT>
             DI[(size_t)j * ld + i] = to_store<ST>(1.0 / diag);
         }
     }
+    if (pipe_on) fence_proxy_async_global();
     G.sync();
 
     double rho = 0.0, rho_prev = 0.0;
@@ -549,8 +900,10 @@ __device__ void solve_system(const Params& P, const DevSolve& S, const Group<GT>
                 Vec4<VT>::store(W1 + base, z);
             }
         }
-        G.sum3(res, rr0, rz0);
+        if (pipe_on) fence_proxy_async_global();
+        G.template sum3<double>(res, rr0, rz0, res, rr0, rz0);
         rho = sqrt(res) / S.bnorm;
+        if (pipe_on && pipe_aborted(*pipe)) { flag = MLMC_F_TIMEOUT; break; }
         if (!(rho == rho) || isinf(rho)) { flag = MLMC_F_NONFINITE; break; }
         if (rho < S.delta) { flag = MLMC_F_CONVERGED; break; }
         if (o >= P.max_outer || iters >= P.max_iters) { flag = MLMC_F_MAXIT; break; }
@@ -569,27 +922,29 @@ __device__ void solve_system(const Params& P, const DevSolve& S, const Group<GT>
             VT pa1i = 0, pa2 = 0, pa3 = 0, pcst = 0, pgi = 0;
             while ((eta == eta) && !isinf(eta) && fabs(eta) > tau * eta0 && eta0 > 0.0 && iters + k < P.max_iters) {
                 const VT gci = (VT)(1.0 / g1);
-                double dl = 0.0, t1 = 0.0, t2 = 0.0;
+                VT dlp = 0;
                 if (sweep_on)
-                    dl = pend ? sweep_minres_a<VT, ST, true>(Zc, gci, AS, ld, n, sc, ja, jb, Zn, pgi, Wo, Wn, D, pa1i,
-                                                             pa2, pa3, pcst)
-                              : sweep_minres_a<VT, ST, false>(Zc, gci, AS, ld, n, sc, ja, jb, Zn, pgi, Wo, Wn, D, pa1i,
-                                                              pa2, pa3, pcst);
-                G.sum3(dl, t1, t2);
+                    dlp = pend ? sweep_minres_a<VT, ST, true>(Zc, gci, AS, ld, n, sc, ja, jb, Zn, pgi, Wo, Wn, D, pa1i,
+                                                              pa2, pa3, pcst)
+                               : sweep_minres_a<VT, ST, false>(Zc, gci, AS, ld, n, sc, ja, jb, Zn, pgi, Wo, Wn, D,
+                                                               pa1i, pa2, pa3, pcst);
+                double dl, t1, t2;
+                G.template sum3<VT>(dlp, (VT)0, (VT)0, dl, t1, t2);
                 if (pend) {
                     VT* tw = Wo;
                     Wo = Wn;
                     Wn = tw;
                 }
-                double zv = 0.0, t3 = 0.0, t4 = 0.0;
+                VT zvp = 0;
                 const VT cA = (VT)(dl / g1), cB = (VT)(g1 / g0);
                 if (sweep_on) {
                     if (jac)
-                        zv = sweep_minres_b<VT, ST, true>(Zc, gci, AS, Vp, Vc, DI, Zn, cA, cB, ld, n, sc, ja, jb);
+                        zvp = sweep_minres_b<VT, ST, true>(Zc, gci, AS, Vp, Vc, DI, Zn, cA, cB, ld, n, sc, ja, jb);
                     else
-                        zv = sweep_minres_b<VT, ST, false>(Zc, gci, AS, Vp, Vc, DI, Zn, cA, cB, ld, n, sc, ja, jb);
+                        zvp = sweep_minres_b<VT, ST, false>(Zc, gci, AS, Vp, Vc, DI, Zn, cA, cB, ld, n, sc, ja, jb);
                 }
-                G.sum3(zv, t3, t4);
+                double zv, t3, t4;
+                G.template sum3<VT>(zvp, (VT)0, (VT)0, zv, t3, t4);
                 const double g2 = sqrt(fmax(zv, 0.0));
                 const double al0 = c1 * dl - c0 * s1 * g1;
                 const double al1 = sqrt(al0 * al0 + g2 * g2);
@@ -616,40 +971,78 @@ __device__ void solve_system(const Params& P, const DevSolve& S, const Group<GT>
                 }
                 G.sync();
             }
-        }
-        // ---- inner PCG on A d = r (z = D^-1 r with Jacobi, z = r otherwise)
-        double rrk = rr0, rzk = rz0, rzp = 0.0;
-        while (!minres && (rrk == rrk) && !isinf(rrk) && rrk > tau * tau * rr0 && rrk != 0.0 &&
-               iters + k < P.max_iters) {
-            const VT vb = (VT)(k > 0 ? rzk / rzp : 0.0);
-            const VT* pold = (k & 1) ? PB0 : PB1;
-            VT* pnew = (k & 1) ? PB1 : PB0;
-            // I1: p = z + beta p_old on the segment rows (and recomputed on the halo rows); sigma = (p, A p)
-            double sig = 0.0, t1 = 0.0, t2 = 0.0;
-            if (sweep_on) {
-                if (jac) {
-                    sig = (k > 0) ? sweep_dir<VT, ST, true, true>(R, DI, pold, pnew, AS, vb, ld, n, sc, ja, jb)
-                                  : sweep_dir<VT, ST, true, false>(R, DI, pold, pnew, AS, vb, ld, n, sc, ja, jb);
-                } else {
-                    sig = (k > 0) ? sweep_dir<VT, ST, false, true>(R, DI, pold, pnew, AS, vb, ld, n, sc, ja, jb)
-                                  : sweep_dir<VT, ST, false, false>(R, DI, pold, pnew, AS, vb, ld, n, sc, ja, jb);
+        } else {
+            // ---- inner PCG on A d = r (z = D^-1 r with Jacobi, z = r otherwise).  The
+            // scalars are formed once per reduction from the FP64 group sums and broadcast.
+            const double tau2rr0 = tau * tau * rr0;
+            double rzk = rz0;              // (r, z) of the current residual, kept where the scalars are formed
+            VT beta = 0;
+            bool cont = (rr0 == rr0) && !isinf(rr0) && rr0 > tau2rr0 && rr0 != 0.0 && iters < P.max_iters;
+            while (cont) {
+                const VT* pold = (k & 1) ? PB0 : PB1;
+                VT* pnew = (k & 1) ? PB1 : PB0;
+                // I1: p = z + beta p_old on the segment rows (recomputed on the halo rows); sigma = (p, A p)
+                VT sig = 0;
+                if (sweep_on) {
+                    if (pipe_on) {
+                        if (jac)
+                            sig = (k > 0) ? sweep_dir_staged<VT, ST, true, true>(*pipe, R, DI, pold, pnew, AS, beta, ld,
+                                                                                 n, sc, ja, jb)
+                                          : sweep_dir_staged<VT, ST, true, false>(*pipe, R, DI, pold, pnew, AS, beta,
+                                                                                  ld, n, sc, ja, jb);
+                        else
+                            sig = (k > 0) ? sweep_dir_staged<VT, ST, false, true>(*pipe, R, DI, pold, pnew, AS, beta,
+                                                                                  ld, n, sc, ja, jb)
+                                          : sweep_dir_staged<VT, ST, false, false>(*pipe, R, DI, pold, pnew, AS,
+                                                                                   beta, ld, n, sc, ja, jb);
+                    } else {
+                        if (jac)
+                            sig = (k > 0) ? sweep_dir<VT, ST, true, true>(R, DI, pold, pnew, AS, beta, ld, n, sc, ja, jb)
+                                          : sweep_dir<VT, ST, true, false>(R, DI, pold, pnew, AS, beta, ld, n, sc, ja,
+                                                                           jb);
+                        else
+                            sig = (k > 0) ? sweep_dir<VT, ST, false, true>(R, DI, pold, pnew, AS, beta, ld, n, sc, ja,
+                                                                           jb)
+                                          : sweep_dir<VT, ST, false, false>(R, DI, pold, pnew, AS, beta, ld, n, sc, ja,
+                                                                            jb);
+                    }
                 }
+                VT sc1[4];
+                G.template reduce<VT, VT>(sig, (VT)0, (VT)0,
+                                          [&](double sg, double, double, double* r) { r[0] = rzk / sg; }, sc1);
+                const VT alpha = sc1[0];
+                // I2: d += alpha p; r -= alpha A p; ||r||^2 and (r, z)
+                VT nrr = 0, nrz = 0;
+                if (sweep_on) {
+                    if (pipe_on) {
+                        if (jac)
+                            sweep_upd_staged<VT, ST, true>(*pipe, pnew, R, D, DI, AS, alpha, ld, n, sc, ja, jb, nrr, nrz);
+                        else
+                            sweep_upd_staged<VT, ST, false>(*pipe, pnew, R, D, DI, AS, alpha, ld, n, sc, ja, jb, nrr,
+                                                            nrz);
+                    } else {
+                        if (jac)
+                            sweep_upd<VT, ST, true>(pnew, R, D, DI, AS, alpha, ld, n, sc, ja, jb, nrr, nrz);
+                        else
+                            sweep_upd<VT, ST, false>(pnew, R, D, DI, AS, alpha, ld, n, sc, ja, jb, nrr, nrz);
+                    }
+                }
+                VT sc2[4];
+                const int kk = k;
+                G.template reduce<VT, VT>(nrr, nrz, (VT)0,
+                                          [&](double rr, double rz, double, double* r) {
+                                              const bool ab = pipe_on && pipe_aborted(*pipe);
+                                              const bool go = (rr == rr) && !isinf(rr) && rr > tau2rr0 && rr != 0.0 &&
+                                                              iters + kk + 1 < P.max_iters && !ab;
+                                              r[0] = rz / rzk;
+                                              r[1] = go ? 1.0 : 0.0;
+                                              rzk = rz;
+                                          },
+                                          sc2);
+                beta = sc2[0];
+                cont = sc2[1] != (VT)0;
+                ++k;
             }
-            G.sum3(sig, t1, t2);
-            const VT va = (VT)(rzk / sig);
-            // I2: d += alpha p; r -= alpha A p; ||r||^2 and (r, z)
-            double nrr = 0.0, nrz = 0.0, t3 = 0.0;
-            if (sweep_on) {
-                if (jac)
-                    sweep_upd<VT, ST, true>(pnew, R, D, DI, AS, va, ld, n, sc, ja, jb, nrr, nrz);
-                else
-                    sweep_upd<VT, ST, false>(pnew, R, D, DI, AS, va, ld, n, sc, ja, jb, nrr, nrz);
-            }
-            G.sum3(nrr, nrz, t3);
-            rrk = nrr;
-            rzp = rzk;
-            rzk = nrz;
-            ++k;
         }
         iters += k;
 
@@ -669,7 +1062,7 @@ __device__ void solve_system(const Params& P, const DevSolve& S, const Group<GT>
     }
 
     // ---- Q: G(u) = sum g_i x_i; optional dense copy of u
-    double qsum = 0.0, t4 = 0.0, t5 = 0.0;
+    double qsum = 0.0;
     for (int it = tr; it < items; it += GT) {
         const int j = 1 + it / cpr, c = it - (j - 1) * cpr;
         double xv[4];
@@ -688,9 +1081,10 @@ __device__ void solve_system(const Params& P, const DevSolve& S, const Group<GT>
             u[it] = inner ? X[(size_t)j * ld + i] : 0.0;
         }
     }
-    G.sum3(qsum, t4, t5);
+    double qs, t4, t5;
+    G.template sum3<double>(qsum, 0.0, 0.0, qs, t4, t5);
     if (tr == 0) {
-        if (S.Q) S.Q[S.out] = qsum;
+        if (S.Q) S.Q[S.out] = qs;
         if (S.iters) S.iters[S.out] = iters;
         if (S.relres) S.relres[S.out] = rho;
         if (S.flags) S.flags[S.out] = flag;
@@ -701,30 +1095,67 @@ __device__ void solve_system(const Params& P, const DevSolve& S, const Group<GT>
 
 // One launch for every system: CTA b < nbig solves one large system; the next
 // ceil(nmed / 4) CTAs solve four medium systems each (128-thread groups); the
-// rest solve sixteen small systems each (one warp each).
+// rest solve sixteen small systems each (one warp each).  A large CG system
+// streams its sweeps through the row pipeline when P.ring >= 2 (dynamic
+// shared memory of pipe_smem_bytes).
 template <class VT, class ST, int SOLVER>
 __global__ void __launch_bounds__(CTA, 1) resident_solve(Params P) {
+    extern __shared__ __align__(128) uint8_t dsm[];
     __shared__ double red[3 * (CTA / 32)];
+    __shared__ double bcast[4 * (CTA / G_MED)];
+    __shared__ int s_abort;
     const int b = blockIdx.x;
     const int nmed_cta = (P.nmed + 3) / 4;
     if (b < P.nbig) {
-        Group<G_BIG> G{(int)threadIdx.x, 0, red};
-        solve_system<VT, ST, SOLVER, G_BIG>(P, P.solves[P.order[b]], G);
+        const DevSolve& S = P.solves[P.order[b]];
+        Group<G_BIG> G{(int)threadIdx.x, 0, red, bcast};
+        if (SOLVER == MLMC_CG && P.ring >= 2 && S.cpr % 32 == 0) {
+            const int cpr = S.cpr, nseg = pipe_nseg(S.n), ring = P.ring;
+            uint64_t* bars = reinterpret_cast<uint64_t*>(dsm);
+            if (threadIdx.x == 0) {
+                s_abort = 0;
+                for (int i = 0; i < ring * nseg; ++i) {
+                    mbar_init(bars + i, 1);
+                    mbar_init(bars + ring * nseg + i, (uint32_t)cpr);
+                }
+                asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+            }
+            __syncthreads();
+            Pipe pipe;
+            pipe.ring = ring;
+            pipe.abort = &s_abort;
+            pipe.err = P.err;
+            pipe.timeout_ns = P.timeout_ns;
+            pipe.extra_tx = P.extra_tx;
+            const int seg = (int)threadIdx.x / cpr;
+            if (seg < nseg) {
+                pipe.slot_bytes = pipe_slot_bytes(S.ld, (int)sizeof(VT), (int)sizeof(ST));
+                pipe.slots = dsm + pipe_bar_bytes(S.n, ring) + (size_t)seg * ring * pipe.slot_bytes;
+                pipe.full = bars + seg * ring;
+                pipe.empty = bars + ring * nseg + seg * ring;
+                pipe.leader = ((int)threadIdx.x % cpr) == 0;
+                pipe.lead_warp = ((int)threadIdx.x % cpr) < 32;
+            }
+            solve_system<VT, ST, SOLVER, G_BIG>(P, S, G, &pipe);
+            if (pipe.leader && pipe_aborted(pipe)) pipe_drain(pipe);
+            return;
+        }
+        solve_system<VT, ST, SOLVER, G_BIG>(P, S, G, nullptr);
         return;
     }
     if (b < P.nbig + nmed_cta) {
         const int gid = threadIdx.x / G_MED;
         const int idx = (b - P.nbig) * 4 + gid;
         if (idx >= P.nmed) return;
-        Group<G_MED> G{(int)(threadIdx.x % G_MED), gid, red + gid * 3 * (G_MED / 32)};
-        solve_system<VT, ST, SOLVER, G_MED>(P, P.solves[P.order[P.nbig + idx]], G);
+        Group<G_MED> G{(int)(threadIdx.x % G_MED), gid, red + gid * 3 * (G_MED / 32), bcast + 4 * gid};
+        solve_system<VT, ST, SOLVER, G_MED>(P, P.solves[P.order[P.nbig + idx]], G, nullptr);
         return;
     }
     const int gid = threadIdx.x / G_SMALL;
     const int idx = (b - P.nbig - nmed_cta) * (CTA / G_SMALL) + gid;
     if (idx >= P.nsmall) return;
-    Group<G_SMALL> G{(int)(threadIdx.x % G_SMALL), gid, nullptr};
-    solve_system<VT, ST, SOLVER, G_SMALL>(P, P.solves[P.order[P.nbig + P.nmed + idx]], G);
+    Group<G_SMALL> G{(int)(threadIdx.x % G_SMALL), gid, nullptr, nullptr};
+    solve_system<VT, ST, SOLVER, G_SMALL>(P, P.solves[P.order[P.nbig + P.nmed + idx]], G, nullptr);
 }
 
 // Group size class of a system: chunk items per thread stay around 8..32.
@@ -771,7 +1202,8 @@ __global__ void apply_operator_kernel(int n, int S, const void* a, int a_fp64, i
 
 // Workspace of a batch: vectors, coefficient storage, descriptors, launch order.
 struct Layout {
-    size_t o_x, o_r, o_p0, o_p1, o_d, o_as, o_dinv, o_vb, o_w0, o_w1, o_stats, zero_end, o_solves, o_order, total;
+    size_t o_x, o_r, o_p0, o_p1, o_d, o_as, o_dinv, o_vb, o_w0, o_w1, o_stats, o_err, zero_end, o_solves, o_order,
+        total;
 };
 
 template <class VT, class ST>
@@ -790,6 +1222,7 @@ Layout make_layout(long long nodes, int ns, bool jacobi, bool minres) {
     L.o_w0 = take(minres ? sizeof(VT) * nodes : 0);
     L.o_w1 = take(minres ? sizeof(VT) * nodes : 0);
     L.o_stats = take(sizeof(int32_t) * 2 * ns);
+    L.o_err = take(sizeof(unsigned));
     L.zero_end = off;
     L.o_solves = take(sizeof(DevSolve) * ns);
     L.o_order = take(sizeof(int) * ns);
@@ -832,7 +1265,60 @@ Params make_params(char* base, const Layout& L, int ns, int nbig, int nmed, int 
     P.tau_max = tau_max;
     P.stag = 0.5;
     P.jacobi = jacobi;
+    P.ring = 0;
+    P.err = reinterpret_cast<unsigned*>(base + L.o_err);
+    P.timeout_ns = 10000000000ull;
+    P.extra_tx = 0;
     return P;
+}
+
+// Workspace row pitch: a multiple of 8 elements, so that every row of every
+// array (8- to 2-byte elements) starts on a 16-byte boundary for bulk copies.
+int row_pitch(int n) { return (int)align_up((size_t)n + 1, 8); }
+
+constexpr int kPipeSmemMax = 220 * 1024;   // dynamic shared memory budget of the row pipeline
+
+// Slots per team for the large systems of a CG launch: the deepest ring
+// (max_ring, or 4 when max_ring < 0, down to 2) whose shared memory fits every
+// large system; 0 (no pipeline) if none does, if max_ring == 0, or if
+// max_ring < 0 and there are fewer large systems than SMs.  Only systems with
+// warp-aligned teams (chunks per row a multiple of 32) use the pipeline.
+// `smem` receives the dynamic shared memory of the launch.
+template <class VT, class ST>
+int choose_ring(const std::vector<int>& big_n, size_t& smem, int max_ring, int num_sms) {
+    smem = 0;
+    if (big_n.empty() || max_ring == 0) return 0;
+    // Automatic: the pipeline pays when the large systems occupy every SM (DRAM
+    // latency under full load is what it hides; on a partly filled GPU the
+    // L1-cached plain loads keep up and cost fewer issue slots).
+    if (max_ring < 0 && (int)big_n.size() < num_sms) return 0;
+    for (int ring = max_ring < 0 ? 4 : max_ring; ring >= 2; --ring) {
+        size_t need = 0;
+        for (int n : big_n)
+            need = std::max(need, (size_t)pipe_smem_bytes(n, row_pitch(n), ring, (int)sizeof(VT), (int)sizeof(ST)));
+        if (need <= (size_t)kPipeSmemMax) {
+            smem = need;
+            return ring;
+        }
+    }
+    return 0;
+}
+
+// Launch the CG or MINRES kernel (the row pipeline is CG-only).
+template <class VT, class ST>
+cudaError_t launch_resident(const Params& P, int solver, int grid, size_t smem, cudaStream_t st) {
+    if (solver == MLMC_MINRES) {
+        resident_solve<VT, ST, MLMC_MINRES><<<grid, CTA, 0, st>>>(P);
+    } else {
+        if (smem > 0) {
+            const cudaError_t e = cudaFuncSetAttribute(resident_solve<VT, ST, MLMC_CG>,
+                                                       cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+            if (e != cudaSuccess) return e;
+        }
+        resident_solve<VT, ST, MLMC_CG><<<grid, CTA, smem, st>>>(P);
+    }
+    g_launches.fetch_add(1, std::memory_order_relaxed);
+    return cudaGetLastError();
 }
 
 int grid_of(int nbig, int nmed, int nsmall) {
@@ -849,7 +1335,7 @@ mlmc_status run_typed(mlmc_ctx* ctx, const std::vector<SolveGroup>& groups, cons
     for (const SolveGroup& g : groups) {
         if (g.S <= 0) continue;
         const int n = g.n;
-        const int ld = (int)align_up((size_t)n + 1, 4);
+        const int ld = row_pitch(n);
         const int stride = g.a_n / n;
         const size_t elem = g.a_fp64 ? sizeof(double) : sizeof(float);
         const long long aV = (long long)(g.a_n + 1) * (g.a_n + 1);
@@ -916,21 +1402,35 @@ mlmc_status run_typed(mlmc_ctx* ctx, const std::vector<SolveGroup>& groups, cons
     Params P = make_params<VT, ST>(base, L, ns, nbig, nmed, nsmall, cfg.max_outer, cfg.max_iters, cfg.prec,
                                    cfg.jacobi, cfg.solver, cfg.inner_theta, cfg.tau_max);
     if (cfg.tau_min > 0) P.tau_min = cfg.tau_min;
+    size_t smem = 0;
+    if (cfg.solver == MLMC_CG) {
+        std::vector<int> big_n;
+        for (int i : order)
+            if (size_class(solves[i].n) == 0) big_n.push_back(solves[i].n);
+        P.ring = choose_ring<VT, ST>(big_n, smem, ctx->solve_ring, ctx->num_sms);
+    }
+    P.timeout_ns = (unsigned long long)(ctx->wait_timeout_s * 1e9);
+    P.extra_tx = 16u * (unsigned)ctx->wait_extra;
     cudaEvent_t ev[2] = {nullptr, nullptr};
     if (ctx->prof.on) {
         MLMC_CUDA_RET(ctx->err, cudaEventCreate(&ev[0]));
         MLMC_CUDA_RET(ctx->err, cudaEventCreate(&ev[1]));
         MLMC_CUDA_RET(ctx->err, cudaEventRecord(ev[0], st));
     }
-    if (cfg.solver == MLMC_MINRES)
-        resident_solve<VT, ST, MLMC_MINRES><<<grid_of(nbig, nmed, nsmall), CTA, 0, st>>>(P);
-    else
-        resident_solve<VT, ST, MLMC_CG><<<grid_of(nbig, nmed, nsmall), CTA, 0, st>>>(P);
-    g_launches.fetch_add(1, std::memory_order_relaxed);
-    MLMC_CUDA_RET(ctx->err, cudaGetLastError());
+    MLMC_CUDA_RET(ctx->err, (launch_resident<VT, ST>(P, cfg.solver, grid_of(nbig, nmed, nsmall), smem, st)));
     if (ctx->prof.on) MLMC_CUDA_RET(ctx->err, cudaEventRecord(ev[1], st));
     MLMC_CUDA_RET(ctx->err, cudaStreamSynchronize(st));
     ctx->prof.acc.h2d_bytes += (int64_t)((sizeof(DevSolve) + sizeof(int)) * ns);
+    unsigned kerr = 0;
+    MLMC_CUDA_RET(ctx->err, cudaMemcpy(&kerr, base + L.o_err, sizeof(unsigned), cudaMemcpyDeviceToHost));
+    ctx->prof.acc.d2h_bytes += (int64_t)sizeof(unsigned);
+    if (kerr != KERR_NONE) {
+        if (ev[0]) cudaEventDestroy(ev[0]);
+        if (ev[1]) cudaEventDestroy(ev[1]);
+        ctx->err = "resident solve: a bounded wait of the row pipeline ran out after " +
+                   std::to_string(ctx->wait_timeout_s) + " s; the affected systems carry MLMC_F_TIMEOUT";
+        return MLMC_E_TIMEOUT;
+    }
     if (ctx->prof.on) {
         float ms = 0.f;
         cudaEventElapsedTime(&ms, ev[0], ev[1]);
@@ -1054,7 +1554,7 @@ template <class VT, class ST>
 mlmc_status noalloc_typed(int n, int S, const void* a, int a_fp64, int a_n, double delta, int max_iters, int qoi,
                           const double* box, double f, int prec, double* Q, int32_t* iters, double* relres,
                           int32_t* flags, cudaStream_t st, void* scratch, std::string& err) {
-    const int ld = (int)align_up((size_t)n + 1, 4);
+    const int ld = row_pitch(n);
     const long long stride = (long long)align_up((size_t)(n + 1) * ld, 64);
     const Layout L = make_layout<VT, ST>(stride * S, S, true, false);
     if (L.total > kNoAllocBytes) {
@@ -1106,12 +1606,29 @@ mlmc_status noalloc_typed(int n, int S, const void* a, int a_fp64, int a_n, doub
     }
     const int c = size_class(n);
     const int nbig = c == 0 ? S : 0, nmed = c == 1 ? S : 0, nsmall = c == 2 ? S : 0;
-    const Params P = make_params<VT, ST>(base, L, S, nbig, nmed, nsmall, 12, max_iters, prec, 1, MLMC_CG, 0.3, 0.5);
-    resident_solve<VT, ST, MLMC_CG><<<grid_of(nbig, nmed, nsmall), CTA, 0, st>>>(P);
-    g_launches.fetch_add(1, std::memory_order_relaxed);
-    if ((e = cudaGetLastError()) != cudaSuccess || (e = cudaStreamSynchronize(st)) != cudaSuccess) {
+    Params P = make_params<VT, ST>(base, L, S, nbig, nmed, nsmall, 12, max_iters, prec, 1, MLMC_CG, 0.3, 0.5);
+    size_t smem = 0;
+    int sms = 0, cur = 0;
+    if ((e = cudaGetDevice(&cur)) != cudaSuccess ||
+        (e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, cur)) != cudaSuccess) {
         err = std::string("level_solve_noalloc: ") + cudaGetErrorString(e);
         return MLMC_E_CUDA;
+    }
+    P.ring = nbig > 0 ? choose_ring<VT, ST>(std::vector<int>((size_t)nbig, n), smem, -1, sms) : 0;
+    if ((e = launch_resident<VT, ST>(P, MLMC_CG, grid_of(nbig, nmed, nsmall), smem, st)) != cudaSuccess ||
+        (e = cudaStreamSynchronize(st)) != cudaSuccess) {
+        err = std::string("level_solve_noalloc: ") + cudaGetErrorString(e);
+        return MLMC_E_CUDA;
+    }
+    unsigned kerr = 0;
+    if ((e = cudaMemcpy(&kerr, base + L.o_err, sizeof(unsigned), cudaMemcpyDeviceToHost)) != cudaSuccess) {
+        err = std::string("level_solve_noalloc: ") + cudaGetErrorString(e);
+        return MLMC_E_CUDA;
+    }
+    if (kerr != KERR_NONE) {
+        err = "level_solve_noalloc: a bounded wait of the row pipeline ran out; the affected systems carry "
+              "MLMC_F_TIMEOUT";
+        return MLMC_E_TIMEOUT;
     }
     return MLMC_OK;
 }

@@ -189,6 +189,91 @@ def test_solve_mixed_reaches_delta(M, prec, delta):
         M.mlmc_destroy(h)
 
 
+@pytest.mark.parametrize("prec", ["FP64", "FP32", "FP16S"])
+@pytest.mark.parametrize("n", [100, 128, 160])
+def test_solve_large_systems_row_pipeline(M, prec, n):
+    # n >= 91 puts a system on a 512-thread CTA whose CG sweeps stream rows through
+    # shared memory; n = 100 and 160 give teams that straddle warps (25 and 40 chunks per row)
+    p = getattr(M, "MLMC_" + prec)
+    h = _ctx(M)
+    try:
+        S = 3
+        af = smooth_lognormal_field(n, S, seed=300 + n, log_sd=1.0)
+        delta = fp64_delta(n) if prec == "FP64" else 1e-7
+        ap = M.MLMC_FP64 if prec == "FP64" else M.MLMC_FP32
+        U, Q, it, rr, fl = _solve(M, h, n, af, ap, n, p, delta)
+        assert np.all(fl == M.MLMC_F_CONVERGED), fl
+        b = o_fem.load_vector(n)
+        g = o_fem.qoi_weights(n)
+        for s in range(S):
+            x, Qo = o_fem.solve_sample(n, af[s])
+            res = o_fem.relative_residual(n, af[s], _interior(n, U[s]))
+            assert res < (2 * delta if prec == "FP64" else delta * (1 + 1e-6))
+            A = o_fem.assemble(n, af[s])
+            lmin = spla.eigsh(A, k=1, sigma=0, which="LM", return_eigenvectors=False)[0]
+            assert abs(Q[s] - Qo) <= np.linalg.norm(g) * res * np.linalg.norm(b) / lmin * 1.01 + 1e-15 * abs(Qo)
+            if prec == "FP64":
+                assert abs(Q[s] - Qo) <= 1e-10 * abs(Qo)
+            B = U[s].reshape(n + 1, n + 1)
+            assert not B[0].any() and not B[-1].any() and not B[:, 0].any() and not B[:, -1].any()
+    finally:
+        M.mlmc_destroy(h)
+
+
+@pytest.mark.parametrize("prec", ["FP64", "FP32", "FP16S"])
+def test_row_pipeline_is_bit_identical_to_plain_loads(M, prec):
+    # the pipeline changes where rows come from, not the arithmetic: every ring depth and
+    # the plain-load sweeps must give the same bits
+    p = getattr(M, "MLMC_" + prec)
+    ap = M.MLMC_FP64 if prec == "FP64" else M.MLMC_FP32
+    h = _ctx(M)
+    try:
+        outs = []
+        for ring in (0, 2, 3, 4, -1):
+            M.mlmc_debug_set_solve_ring(h, ring)
+            for n in (100, 128):
+                af = smooth_lognormal_field(n, 2, seed=500 + n, log_sd=1.0)
+                U, Q, it, rr, fl = _solve(M, h, n, af, ap, n, p, 1e-9 if prec != "FP64" else fp64_delta(n))
+                outs.append((ring, n, U, Q, it, rr, fl))
+        ref = {o[1]: o for o in outs if o[0] == 0}
+        for ring, n, U, Q, it, rr, fl in outs:
+            r = ref[n]
+            assert np.array_equal(U, r[2]) and np.array_equal(Q, r[3]) and np.array_equal(it, r[4])
+            assert np.array_equal(rr, r[5]) and np.array_equal(fl, r[6]) and np.all(fl == M.MLMC_F_CONVERGED)
+        with pytest.raises(M.MlmcError):
+            M.mlmc_debug_set_solve_ring(h, 1)
+    finally:
+        M.mlmc_destroy(h)
+
+
+def test_large_solve_pipeline_timeout_is_reported_and_gpu_stays_usable(M):
+    # the row pipeline's first wait of every team expects bytes that never arrive:
+    # the solve stops, flags its systems, and the context keeps working afterwards
+    h = _ctx(M)
+    try:
+        n, S = 128, 2
+        af = smooth_lognormal_field(n, S, seed=41, log_sd=1.0)
+        a = to_dev(af, torch.float32)
+        Q = torch.empty(S, dtype=torch.float64, device=device())
+        fl = torch.zeros(S, dtype=torch.int32, device=device())
+        M.mlmc_set_wait_timeout(h, 0.2)
+        M.mlmc_debug_set_wait_extra(h, 1)
+        M.mlmc_debug_set_solve_ring(h, 4)     # two systems would not turn the pipeline on by themselves
+        with pytest.raises(M.MlmcError) as ei:
+            M.mlmc_level_solve(h, n, S, a, M.MLMC_FP32, n, M.MLMC_FP32, M.MLMC_CG, 1e-7, 100000, None, Q, None,
+                               None, fl)
+        assert ei.value.status == M.MLMC_E_TIMEOUT
+        torch.cuda.synchronize()
+        assert np.all(fl.cpu().numpy() == M.MLMC_F_TIMEOUT)
+        M.mlmc_debug_set_wait_extra(h, 0)
+        _, Q2, _, _, fl2 = _solve(M, h, n, af, M.MLMC_FP32, n, M.MLMC_FP32, 1e-9, u=False)
+        assert np.all(fl2 == M.MLMC_F_CONVERGED)
+        for s in range(S):
+            assert abs(Q2[s] - o_fem.solve_sample(n, af[s])[1]) <= 1e-6 * abs(Q2[s])
+    finally:
+        M.mlmc_destroy(h)
+
+
 def test_coarse_view_solve(M):
     h = _ctx(M)
     try:
