@@ -191,6 +191,8 @@ def main():
     ap.add_argument("--kl-samples", type=int, default=4096)
     ap.add_argument("--sweep-samples", type=int, default=4096,
                     help="sweep: systems per batch (n = 512, K = 128, corr 0.1, fixed delta 1e-6)")
+    ap.add_argument("--sweep-delta", type=float, default=1e-6,
+                    help="sweep: relative residual (1e-6 for the measurement; larger for short profiles)")
     ap.add_argument("--prec", default="FP32", choices=["FP64", "FP32", "BF16S", "FP16S"],
                     help="sweep: inner precision (FP64 uses an FP64 field and FP64 vectors)")
     ap.add_argument("--ring", type=int, default=-1,
@@ -455,7 +457,7 @@ def sweep_case(M, torch, dev, args, hbm_peak, peak_src, flush, stream):
     """Single-level batched solve: S systems on the 512 x 512 grid (261,121 unknowns each), KL field
     with K = 128 terms and correlation length 0.1, fixed relative residual 1e-6; solved DOF/s and
     the solve kernel's HBM rate."""
-    S, n, K, delta = args.sweep_samples, 512, 128, 1e-6
+    S, n, K, delta = args.sweep_samples, 512, 128, args.sweep_delta
     prec = getattr(M, "MLMC_" + args.prec)
     fp64 = prec == M.MLMC_FP64
     prob = M.make_problem(n0=n, m=2, L_max=0, kind=0, K=K, sigma2=1.0, corr_len=0.1, seed=11)

@@ -1281,17 +1281,21 @@ constexpr int kPipeSmemMax = 220 * 1024;   // dynamic shared memory budget of th
 // Slots per team for the large systems of a CG launch: the deepest ring
 // (max_ring, or 4 when max_ring < 0, down to 2) whose shared memory fits every
 // large system; 0 (no pipeline) if none does, if max_ring == 0, or if
-// max_ring < 0 and there are fewer large systems than SMs.  Only systems with
+// max_ring < 0 and fewer systems of the largest size than SMs.  Only systems with
 // warp-aligned teams (chunks per row a multiple of 32) use the pipeline.
 // `smem` receives the dynamic shared memory of the launch.
 template <class VT, class ST>
 int choose_ring(const std::vector<int>& big_n, size_t& smem, int max_ring, int num_sms) {
     smem = 0;
     if (big_n.empty() || max_ring == 0) return 0;
-    // Automatic: the pipeline pays when the large systems occupy every SM (DRAM
-    // latency under full load is what it hides; on a partly filled GPU the
-    // L1-cached plain loads keep up and cost fewer issue slots).
-    if (max_ring < 0 && (int)big_n.size() < num_sms) return 0;
+    // Automatic: the pipeline pays when the largest systems -- the launch's
+    // critical path -- occupy every SM (DRAM latency under full load is what it
+    // hides; on a partly filled GPU the L1-cached plain loads keep up and cost
+    // fewer issue slots).
+    if (max_ring < 0) {
+        const int nmax = *std::max_element(big_n.begin(), big_n.end());
+        if ((int)std::count(big_n.begin(), big_n.end(), nmax) < num_sms) return 0;
+    }
     for (int ring = max_ring < 0 ? 4 : max_ring; ring >= 2; --ring) {
         size_t need = 0;
         for (int n : big_n)
