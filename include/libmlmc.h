@@ -59,7 +59,9 @@ typedef enum {
     MLMC_FP16S = 3    /* inner FP32, coefficient stored IEEE half                */
 } mlmc_prec;
 
-typedef enum { MLMC_CG = 0, MLMC_MINRES = 1 } mlmc_solver;   /* Sec. 2.2 */
+typedef enum { MLMC_CG = 0, MLMC_MINRES = 1 } mlmc_solver;
+/* Preconditioner of the CG inner solves (MINRES always uses Jacobi). */
+typedef enum { MLMC_PC_JACOBI = 0, MLMC_PC_MG = 1 } mlmc_precond;   /* Sec. 2.2 */
 
 /* per-solve flag bits (int32 arrays returned by the solves) */
 #define MLMC_F_CONVERGED 1   /* ||b - A x||_2 / ||b||_2 < delta reached (Eq. (2.1), C = 1) */
@@ -189,10 +191,10 @@ mlmc_status mlmc_level_solve(mlmc_ctx* ctx, int n, int S, const void* a, mlmc_pr
  * hands the library only its own buffers, or a serving loop that forbids
  * allocation after start-up (cudaMalloc can synchronise the device, and it
  * fails once a memory pool has reserved the device).  It solves like
- * mlmc_level_solve (same method, kernel and outputs) but takes no context and
- * calls no cudaMalloc, cudaFree or allocating library routine, on the device
- * or the host: the solver's scratch (vectors, partial sums, descriptors, grid
- * barrier) lives in one file-scope __device__ array of
+ * mlmc_level_solve with the Jacobi preconditioner (same kernel and outputs)
+ * but takes no context and calls no cudaMalloc, cudaFree or allocating library
+ * routine, on the device or the host: the solver's scratch (vectors,
+ * descriptors, error word) lives in one file-scope __device__ array of
  * MLMC_NOALLOC_SCRATCH_BYTES, which every GPU that loads the library holds
  * until the process exits, and the descriptors are written there by a kernel.
  *   device  CUDA device to run on (made current for the call, then restored)
@@ -201,8 +203,8 @@ mlmc_status mlmc_level_solve(mlmc_ctx* ctx, int n, int S, const void* a, mlmc_pr
  *           only when qoi == 1)
  *   Q, iters, relres, flags: device outputs as in mlmc_level_solve (iters,
  *           relres, flags may be NULL)
- * Capacity: a batch needs about (8 + 4 p_v + p_s) (n+1)(n+1+3) bytes per system
- * plus small per-tile terms (p_v, p_s: vector and coefficient storage bytes);
+ * Capacity: a batch needs about (8 + 4 p_v + 2 p_s) (n+1)(n+8) bytes per system
+ * (p_v, p_s: vector and coefficient storage bytes) plus a few words;
  * a batch beyond MLMC_NOALLOC_SCRATCH_BYTES is rejected with MLMC_E_ARG and a
  * message in mlmc_last_error(NULL), as are the argument errors of
  * mlmc_level_solve.
@@ -328,6 +330,22 @@ mlmc_status mlmc_adjoint_grad(mlmc_ctx* ctx, int level, int S, const double* xi,
                               double delta, int max_iters, double* Q, double* dQdxi, void* stream);
 
 /* ------------------------------------------------------------------------- */
+/* Preconditioner of this context's CG inner solves (mlmc_level_solve,
+ * mlmc_estimate, mlmc_adjoint_grad).
+ *  - MLMC_PC_JACOBI: z = D^-1 r.
+ *  - MLMC_PC_MG (default): one geometric multigrid V-cycle, the optimal solver
+ *    that the cost model of Sec. 4 assumes (cost per sample proportional to the
+ *    unknowns).  Coarse grids n/2, n/4, ... while even and at least 4 cells, the
+ *    nodal coefficient injected at the coarse nodes and the P1 operator
+ *    re-discretised on it; P1 interpolation on the SW-NE triangulation and its
+ *    transpose; nu damped-Jacobi sweeps (damping omega) before and after the
+ *    coarse correction; coarse_sweeps Jacobi sweeps on the coarsest grid.  The
+ *    V-cycle is a fixed symmetric linear map, so CG stays CG.
+ * nu in {1, 2}, coarse_sweeps even and >= 2, 0 < omega < 1; 0 keeps the current
+ * value (defaults nu = 2, coarse_sweeps = 8, omega = 0.8).  Stopping is still
+ * on the FP64 residual of the refinement (Alg. 2.1). */
+mlmc_status mlmc_set_precond(mlmc_ctx* ctx, mlmc_precond pc, int nu, int coarse_sweeps, double omega);
+
 /* Diagnostics.  Timeout of every bounded device-side wait of this context, in
  * seconds (default 10): the tensor-core synthesis waits on its TMA copies and
  * MMAs, and the large CG solves wait on the bulk row copies of their pipeline.

@@ -24,6 +24,7 @@ STATUS_NAMES = ["MLMC_OK", "MLMC_E_ARG", "MLMC_E_NOMEM", "MLMC_E_CUDA", "MLMC_E_
 MLMC_FP64, MLMC_FP32, MLMC_BF16S, MLMC_FP16S = range(4)
 # mlmc_solver
 MLMC_CG, MLMC_MINRES = range(2)
+MLMC_PC_JACOBI, MLMC_PC_MG = range(2)
 # mlmc_form
 MLMC_FORM_MIXED, MLMC_FORM_FP64_ADAPTIVE, MLMC_FORM_FP64_FIXED = range(3)
 # flags
@@ -100,6 +101,7 @@ _SIGS = {
     "mlmc_set_wait_timeout": (c_int, [c_void_p, c_double]),
     "mlmc_debug_set_wait_extra": (c_int, [c_void_p, c_int]),
     "mlmc_debug_set_solve_ring": (c_int, [c_void_p, c_int]),
+    "mlmc_set_precond": (c_int, [c_void_p, c_int, c_int, c_int, c_double]),
     "mlmc_profile_enable": (c_int, [c_void_p, c_int]),
     "mlmc_profile_get": (c_int, [c_void_p, c_void_p]),
     "mlmc_profile_reset": (c_int, [c_void_p]),
@@ -210,6 +212,10 @@ def mlmc_profile_reset(ctx):
 
 def mlmc_debug_set_wait_extra(ctx, extra):
     _check(lib().mlmc_debug_set_wait_extra(ctx, extra), ctx)
+
+
+def mlmc_set_precond(ctx, pc, nu=0, coarse_sweeps=0, omega=0.0):
+    _check(lib().mlmc_set_precond(ctx, pc, nu, coarse_sweeps, omega), ctx)
 
 
 def mlmc_debug_set_solve_ring(ctx, ring):

@@ -393,6 +393,18 @@ mlmc_status mlmc_debug_set_wait_extra(mlmc_ctx* ctx, int extra) {
     return MLMC_OK;
 }
 
+mlmc_status mlmc_set_precond(mlmc_ctx* ctx, mlmc_precond pc, int nu, int coarse_sweeps, double omega) {
+    if (!ctx) return MLMC_E_ARG;
+    if ((pc != MLMC_PC_JACOBI && pc != MLMC_PC_MG) || nu < 0 || nu > 2 || coarse_sweeps < 0 ||
+        (coarse_sweeps > 0 && (coarse_sweeps % 2 != 0 || coarse_sweeps < 2)) || !(omega >= 0.0 && omega < 1.0))
+        return fail(ctx, MLMC_E_ARG, "set_precond: bad preconditioner, nu (1..2), coarse sweeps (even) or omega");
+    ctx->precond = pc;
+    if (nu > 0) ctx->mg_nu = nu;
+    if (coarse_sweeps > 0) ctx->mg_coarse = coarse_sweeps;
+    if (omega > 0.0) ctx->mg_omega = omega;
+    return MLMC_OK;
+}
+
 mlmc_status mlmc_debug_set_solve_ring(mlmc_ctx* ctx, int ring) {
     if (!ctx || ring < -1 || ring == 1 || ring > 4) return MLMC_E_ARG;
     ctx->solve_ring = ring;

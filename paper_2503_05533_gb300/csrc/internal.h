@@ -92,6 +92,10 @@ struct mlmc_ctx {
     int kl_err_pending = 0;       // a synthesis ran since the word was last read
     int wait_extra = 0;           // diagnostic: bytes every tensor-core wait expects and never receives
     int solve_ring = -1;          // diagnostic: row-pipeline slots of large CG solves (-1 automatic, 0 off)
+    int precond = MLMC_PC_MG;     // preconditioner of the CG inner solves
+    int mg_nu = 2;                // multigrid: smoothing sweeps before and after the coarse correction
+    int mg_coarse = 8;            // multigrid: Jacobi sweeps on the coarsest grid
+    double mg_omega = 0.8;        // multigrid: Jacobi damping
     mlmc::Profile prof;
 };
 
@@ -149,6 +153,7 @@ struct SolveConfig {
     double tau_max = 0.5;
     int tile_nodes = 2048;      // target nodes per warp tile
     int jacobi = 1;             // Jacobi-preconditioned inner CG
+    int precond = -1;           // MLMC_PC_*, or -1: the context's choice (mlmc_set_precond)
 };
 struct SolveStats {
     int64_t inner_iters = 0;    // summed over solves (host copy, only if requested)

@@ -64,6 +64,8 @@ struct DevSolve {
     int32_t* flags;
     int out;                 // index into the output arrays
     int sys;                 // index of the system in the batch
+    int mg_levels;           // multigrid: coarse levels below this grid (0: none)
+    long long mg_off;        // multigrid: node offset of this system's coarse levels
 };
 
 struct Params {
@@ -87,6 +89,17 @@ struct Params {
     double theta, tau_min, tau_max, stag;
     int jacobi;
     int ring;                // row-pipeline slots per team of a 512-thread CG group (0: no pipeline)
+    int mg;                  // CG preconditioner: 0 Jacobi, 1 geometric multigrid V-cycle
+    int mg_nu;               // multigrid: damped-Jacobi sweeps before and after the coarse correction
+    int mg_coarse;           // multigrid: Jacobi sweeps on the coarsest grid (even)
+    double mg_omega;         // multigrid: Jacobi damping
+    void* mz;                // multigrid: preconditioned residual z (fine grid)
+    void* mt;                // multigrid: fine-grid scratch
+    void* cx;                // multigrid: coarse-level iterate, scratch and right-hand side
+    void* ct;
+    void* cb;
+    void* cas;               // multigrid: coarse-level coefficient and inverse diagonal (storage type)
+    void* cdi;
     unsigned* err;           // error word of the launch (KERR_*)
     unsigned long long timeout_ns;   // bound of every pipeline wait
     unsigned extra_tx;       // diagnostic: bytes a team's first full barrier expects and never receives
@@ -101,6 +114,31 @@ __host__ __device__ constexpr int pipe_slot_bytes(int ld, int pv, int ps) { retu
 __host__ __device__ constexpr int pipe_bar_bytes(int n, int ring) { return (16 * ring * pipe_nseg(n) + 127) / 128 * 128; }
 __host__ __device__ constexpr int pipe_smem_bytes(int n, int ld, int ring, int pv, int ps) {
     return pipe_bar_bytes(n, ring) + pipe_nseg(n) * ring * pipe_slot_bytes(ld, pv, ps);
+}
+
+// Workspace row pitch: a multiple of 8 elements, so that every row of every
+// array (8- to 2-byte elements) starts on a 16-byte boundary for bulk copies.
+__host__ __device__ constexpr int row_pitch(int n) { return (n + 1 + 7) / 8 * 8; }
+
+// Multigrid hierarchy of an n-cell grid: halve while the grid is even and the
+// half has at least 4 cells.  Level k >= 1 (n >> k cells) occupies
+// mg_level_nodes(n >> k) nodes of the coarse-level arrays, levels in order.
+constexpr int kMgMinN = 4;
+__host__ __device__ constexpr int mg_level_count(int n) {
+    int l = 0;
+    while (n % 2 == 0 && n / 2 >= kMgMinN) {
+        n /= 2;
+        ++l;
+    }
+    return l;
+}
+__host__ __device__ constexpr long long mg_level_nodes(int nk) {
+    return ((long long)(nk + 1) * row_pitch(nk) + 63) / 64 * 64;
+}
+__host__ __device__ constexpr long long mg_coarse_nodes(int n, int nl) {
+    long long t = 0;
+    for (int k = 1; k <= nl; ++k) t += mg_level_nodes(n >> k);
+    return t;
 }
 
 // ---------------------------------------------------------------------------
@@ -182,6 +220,17 @@ __device__ __forceinline__ double qoi_weight(const DevSolve& S, int i, int j) {
     };
     const int cnt = 2 * in(i, j) + in(i - 1, j) + 2 * in(i - 1, j - 1) + in(i, j - 1);
     return S.h2 * (double)cnt * (1.0 / 6.0);
+}
+
+// Diagonal of the P1 operator at fine-grid node (i, j) of the grid whose nodes are 2^k fine nodes
+// apart (k = 0: the grid itself), from the master coefficient, in FP64.
+__device__ __forceinline__ double stencil_diag(const DevSolve& S, int i, int j, int k) {
+    const int d = 1 << k;
+    const double a00 = master_a(S, i, j), aE = master_a(S, i + d, j), aW = master_a(S, i - d, j);
+    const double aN = master_a(S, i, j + d), aS = master_a(S, i, j - d);
+    const double aNE = master_a(S, i + d, j + d), aSW = master_a(S, i - d, j - d);
+    return (2.0 * (a00 + aE) + aNE + aS + 2.0 * (aW + a00) + aN + aSW + 2.0 * (a00 + aN) + aNE + aW +
+            2.0 * (aS + a00) + aE + aSW) * (1.0 / 6.0);
 }
 
 __device__ __forceinline__ double rhs_value(const DevSolve& S, int i, int j) {
@@ -813,6 +862,231 @@ __device__ __forceinline__ VT sweep_minres_b(const VT* ZC, VT gci, const ST* AS,
     return acc;
 }
 
+// ---------------------------------------------------------------------------
+// Geometric multigrid V-cycle: the CG preconditioner when P.mg != 0 (the
+// optimal solver the cost model of Sec. 4 assumes, cost per sample ~ unknowns).
+//  - Level k >= 1 is the grid of n >> k cells.  Its nodal coefficient is the
+//    master coefficient injected at the coarse nodes, a_k(I, J) = a(2^k I, 2^k J),
+//    and its operator is the P1 operator of Sec. 3.1 re-discretised on it.
+//  - Prolongation P is P1 interpolation on the SW-NE triangulation: even nodes
+//    copy the coarse value, edge midpoints (horizontal, vertical and the SW-NE
+//    diagonal) average its two ends.  Restriction is P^T.
+//  - Smoothing: nu damped-Jacobi sweeps before and nu after the coarse
+//    correction; the coarsest grid takes mg_coarse sweeps from zero.
+// Every step is a fixed linear map and the post-smoother is the adjoint of the
+// pre-smoother, so z = B r is symmetric in r, as CG needs.  Each pass is one
+// group-strided loop over 4-node chunks followed by a group barrier.
+template <class VT, class ST>
+struct MGLevel {
+    int n, ld, cpr;
+    VT* x;          // iterate (level 0: z)
+    VT* t;          // scratch
+    VT* b;          // right-hand side (level 0: r, read only)
+    const ST* a;    // coefficient in the storage type
+    const ST* di;   // inverse diagonal in the storage type (zero off the interior)
+};
+
+template <class VT, class ST>
+__device__ __forceinline__ MGLevel<VT, ST> mg_level(const Params& P, const DevSolve& S, int k, VT* Z, VT* T,
+                                                   const VT* R, const ST* AS, const ST* DI) {
+    MGLevel<VT, ST> L;
+    if (k == 0) {
+        L.n = S.n;
+        L.ld = S.ld;
+        L.x = Z;
+        L.t = T;
+        L.b = const_cast<VT*>(R);
+        L.a = AS;
+        L.di = DI;
+    } else {
+        L.n = S.n >> k;
+        L.ld = row_pitch(L.n);
+        const long long off = S.mg_off + mg_coarse_nodes(S.n, k - 1);
+        L.x = static_cast<VT*>(P.cx) + off;
+        L.t = static_cast<VT*>(P.ct) + off;
+        L.b = static_cast<VT*>(P.cb) + off;
+        L.a = static_cast<const ST*>(P.cas) + off;
+        L.di = static_cast<const ST*>(P.cdi) + off;
+    }
+    L.cpr = (L.n - 1) / 4 + 1;
+    return L;
+}
+
+// out = in + w D^-1 (b - A in) (in == nullptr: out = w D^-1 b); returns this
+// thread's part of (b, out) when RZ.
+template <class VT, class ST, int GT, bool RZ>
+__device__ __forceinline__ VT mg_smooth(const Group<GT>& G, const MGLevel<VT, ST>& L, const VT* in, VT* out, VT w) {
+    const int n = L.n, ld = L.ld, cpr = L.cpr, items = (n - 1) * cpr;
+    VT acc = 0;
+    for (int it = G.rank; it < items; it += GT) {
+        const int j = 1 + it / cpr, c = it - (j - 1) * cpr;
+        const size_t base = (size_t)j * ld + 4 * c;
+        VT b4[4], d4[4], y[4] = {(VT)0, (VT)0, (VT)0, (VT)0}, x4[4] = {(VT)0, (VT)0, (VT)0, (VT)0};
+        Vec4<VT>::load(L.b + base, b4);
+        CoefLoad<ST, VT>::load4(L.di + base, d4);
+        if (in) {
+            VT a3[3][6], xs[4], xc[6], xn[4];
+            load_coef_chunk<ST, VT>(L.a, ld, n, j, c, a3);
+            load_vec_chunk<VT>(in, ld, n, j, c, xs, xc, xn);
+            apply_chunk<VT>(a3, xs, xc, xn, n, c, y);
+#pragma unroll
+            for (int q = 0; q < 4; ++q) x4[q] = xc[q + 1];
+        }
+        VT o4[4];
+#pragma unroll
+        for (int q = 0; q < 4; ++q) o4[q] = fma_rn(mul_rn(w, d4[q]), b4[q] - y[q], x4[q]);
+        Vec4<VT>::store(out + base, o4);
+        if (RZ) {
+#pragma unroll
+            for (int q = 0; q < 4; ++q) acc += b4[q] * o4[q];
+        }
+    }
+    G.sync();
+    return acc;
+}
+
+// t = b - A x on level L.
+template <class VT, class ST, int GT>
+__device__ __forceinline__ void mg_residual(const Group<GT>& G, const MGLevel<VT, ST>& L) {
+    const int n = L.n, ld = L.ld, cpr = L.cpr, items = (n - 1) * cpr;
+    for (int it = G.rank; it < items; it += GT) {
+        const int j = 1 + it / cpr, c = it - (j - 1) * cpr;
+        const size_t base = (size_t)j * ld + 4 * c;
+        VT b4[4], y[4], a3[3][6], xs[4], xc[6], xn[4];
+        Vec4<VT>::load(L.b + base, b4);
+        load_coef_chunk<ST, VT>(L.a, ld, n, j, c, a3);
+        load_vec_chunk<VT>(L.x, ld, n, j, c, xs, xc, xn);
+        apply_chunk<VT>(a3, xs, xc, xn, n, c, y);
+#pragma unroll
+        for (int q = 0; q < 4; ++q) b4[q] -= y[q];
+        Vec4<VT>::store(L.t + base, b4);
+    }
+    G.sync();
+}
+
+// Coarse right-hand side C.b = P^T F.t: each interior coarse node gathers its
+// fine node and half of its six P1 neighbours (E, W, N, S, NE, SW).
+template <class VT, class ST, int GT>
+__device__ __forceinline__ void mg_restrict(const Group<GT>& G, const MGLevel<VT, ST>& F, const MGLevel<VT, ST>& C) {
+    const int nc = C.n, items = (nc - 1) * C.cpr;
+    const VT half = (VT)0.5;
+    for (int it = G.rank; it < items; it += GT) {
+        const int J = 1 + it / C.cpr, Cc = it - (J - 1) * C.cpr;
+        VT v[3][9];     // fine rows 2J-1 .. 2J+1, columns 8Cc-1 .. 8Cc+7
+#pragma unroll
+        for (int r = 0; r < 3; ++r) {
+            const VT* row = F.t + (size_t)(2 * J - 1 + r) * F.ld;
+#pragma unroll
+            for (int m = 0; m < 9; ++m) {
+                const int col = 8 * Cc - 1 + m;
+                v[r][m] = (col >= 0 && col <= F.n) ? row[col] : (VT)0;
+            }
+        }
+        VT o4[4];
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+            const int I = 4 * Cc + q, m = 2 * q + 1;
+            const VT nb = v[1][m + 1] + v[1][m - 1] + v[2][m] + v[0][m] + v[2][m + 1] + v[0][m - 1];
+            o4[q] = (I >= 1 && I <= nc - 1) ? fma_rn(half, nb, v[1][m]) : (VT)0;
+        }
+        Vec4<VT>::store(C.b + (size_t)J * C.ld + 4 * Cc, o4);
+    }
+    G.sync();
+}
+
+// out = F.x + P C.x on the interior of level F (out may be F.x).
+template <class VT, class ST, int GT>
+__device__ __forceinline__ void mg_prolong(const Group<GT>& G, const MGLevel<VT, ST>& C, const MGLevel<VT, ST>& F,
+                                           VT* out) {
+    const int n = F.n, cpr = F.cpr, items = (n - 1) * cpr;
+    const VT half = (VT)0.5;
+    for (int it = G.rank; it < items; it += GT) {
+        const int j = 1 + it / cpr, c = it - (j - 1) * cpr;
+        const size_t base = (size_t)j * F.ld + 4 * c;
+        const int Ja = j >> 1, Jb = (j + 1) >> 1;      // equal for even j
+        VT ca[3], cb[3];                               // coarse columns 2c .. 2c+2 of rows Ja and Jb
+#pragma unroll
+        for (int m = 0; m < 3; ++m) {
+            const int col = 2 * c + m;
+            ca[m] = col <= C.n ? C.x[(size_t)Ja * C.ld + col] : (VT)0;
+            cb[m] = col <= C.n ? C.x[(size_t)Jb * C.ld + col] : (VT)0;
+        }
+        const bool odd = (j & 1) != 0;
+        VT pv[4];
+        // even columns 4c, 4c+2 take (2c, 2c+1); odd columns take their SW and NE (odd row) or W and E ends
+        pv[0] = odd ? half * (ca[0] + cb[0]) : ca[0];
+        pv[1] = odd ? half * (ca[0] + cb[1]) : half * (ca[0] + ca[1]);
+        pv[2] = odd ? half * (ca[1] + cb[1]) : ca[1];
+        pv[3] = odd ? half * (ca[1] + cb[2]) : half * (ca[1] + ca[2]);
+        VT x4[4];
+        Vec4<VT>::load(F.x + base, x4);
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+            const int i = 4 * c + q;
+            x4[q] = (i >= 1 && i <= n - 1) ? x4[q] + pv[q] : x4[q];
+        }
+        Vec4<VT>::store(out + base, x4);
+    }
+    G.sync();
+}
+
+// nu sweeps from zero, alternating t and x so that the last lands in x.
+template <class VT, class ST, int GT>
+__device__ __forceinline__ void mg_sweeps_from_zero(const Group<GT>& G, const MGLevel<VT, ST>& L, int nu, VT w) {
+    const VT* in = nullptr;
+    for (int s = 1; s <= nu; ++s) {
+        VT* out = ((nu - s) % 2 == 0) ? L.x : L.t;
+        mg_smooth<VT, ST, GT, false>(G, L, in, out, w);
+        in = out;
+    }
+}
+
+// z = B r; returns this thread's part of (r, z).
+template <class VT, class ST, int GT>
+__device__ VT mg_vcycle(const Params& P, const DevSolve& S, const Group<GT>& G, VT* Z, VT* T, const VT* R,
+                        const ST* AS, const ST* DI) {
+    const int nl = S.mg_levels, nu = P.mg_nu;
+    const VT w = (VT)P.mg_omega;
+    for (int k = 0; k < nl; ++k) {
+        const MGLevel<VT, ST> L = mg_level<VT, ST>(P, S, k, Z, T, R, AS, DI);
+        mg_sweeps_from_zero<VT, ST, GT>(G, L, nu, w);
+        mg_residual<VT, ST, GT>(G, L);
+        mg_restrict<VT, ST, GT>(G, L, mg_level<VT, ST>(P, S, k + 1, Z, T, R, AS, DI));
+    }
+    mg_sweeps_from_zero<VT, ST, GT>(G, mg_level<VT, ST>(P, S, nl, Z, T, R, AS, DI), P.mg_coarse, w);
+    VT rz = 0;
+    for (int k = nl - 1; k >= 0; --k) {
+        const MGLevel<VT, ST> L = mg_level<VT, ST>(P, S, k, Z, T, R, AS, DI);
+        // corrected iterate into t for odd nu, in place for even nu, so that nu sweeps end in x
+        VT* corr = (nu % 2) ? L.t : L.x;
+        mg_prolong<VT, ST, GT>(G, mg_level<VT, ST>(P, S, k + 1, Z, T, R, AS, DI), L, corr);
+        const VT* in = corr;
+        for (int s = 1; s <= nu; ++s) {
+            VT* out = ((nu - s) % 2 == 0) ? L.x : L.t;
+            if (k == 0 && s == nu)
+                rz = mg_smooth<VT, ST, GT, true>(G, L, in, out, w);
+            else
+                mg_smooth<VT, ST, GT, false>(G, L, in, out, w);
+            in = out;
+        }
+    }
+    if (nl == 0) {
+        // no coarse grid: the coarsest sweeps ran on the fine grid itself; (r, z) separately
+        const MGLevel<VT, ST> L = mg_level<VT, ST>(P, S, 0, Z, T, R, AS, DI);
+        const int n = L.n, ld = L.ld, cpr = L.cpr, items = (n - 1) * cpr;
+        for (int it = G.rank; it < items; it += GT) {
+            const int j = 1 + it / cpr, c = it - (j - 1) * cpr;
+            const size_t base = (size_t)j * ld + 4 * c;
+            VT b4[4], z4[4];
+            Vec4<VT>::load(R + base, b4);
+            Vec4<VT>::load(Z + base, z4);
+#pragma unroll
+            for (int q = 0; q < 4; ++q) rz += b4[q] * z4[q];
+        }
+    }
+    return rz;
+}
+
 // One system, start to finish: set-up, refinement loop with the inner PCG, QoI.
 // `pipe` is non-null for a 512-thread CG group whose sweeps stream rows
 // through shared memory.
@@ -834,6 +1108,8 @@ __device__ void solve_system(const Params& P, const DevSolve& S, const Group<GT>
     VT* VB = minres ? static_cast<VT*>(P.vb) + S.off : nullptr;
     VT* W0 = minres ? static_cast<VT*>(P.w0) + S.off : nullptr;
     VT* W1 = minres ? static_cast<VT*>(P.w1) + S.off : nullptr;
+    VT* MZ = P.mg ? static_cast<VT*>(P.mz) + S.off : nullptr;
+    VT* MT = P.mg ? static_cast<VT*>(P.mt) + S.off : nullptr;
     // row-sweep mapping: GT / cpr row segments, each thread one chunk column of one segment
     const int nseg = max(1, GT / cpr);
     const int seg_rows = (n - 1 + nseg - 1) / nseg;
@@ -841,17 +1117,28 @@ __device__ void solve_system(const Params& P, const DevSolve& S, const Group<GT>
     const int ja = 1 + seg * seg_rows, jb = min(n, ja + seg_rows);
     const bool sweep_on = seg < nseg && ja < jb;
 
-    // ---- set-up: coefficient (and inverse diagonal) in the inner storage precision
+    // ---- set-up: coefficient (and inverse diagonal) in the inner storage precision, on the
+    // grid and, with multigrid, on every coarse level (coefficient injected at the coarse nodes)
+    const bool mg = P.mg != 0 && !minres;
+    const bool need_di = jac || mg;
     for (int it = tr; it < (n + 1) * (n + 1); it += GT) {
         const int j = it / (n + 1), i = it - j * (n + 1);
         AS[(size_t)j * ld + i] = to_store<ST>(master_a(S, i, j));
-        if (jac && i >= 1 && i <= n - 1 && j >= 1 && j <= n - 1) {
-            const double a00 = master_a(S, i, j), aE = master_a(S, i + 1, j), aW = master_a(S, i - 1, j);
-            const double aN = master_a(S, i, j + 1), aS = master_a(S, i, j - 1);
-            const double aNE = master_a(S, i + 1, j + 1), aSW = master_a(S, i - 1, j - 1);
-            const double diag = (2.0 * (a00 + aE) + aNE + aS + 2.0 * (aW + a00) + aN + aSW + 2.0 * (a00 + aN) +
-                                 aNE + aW + 2.0 * (aS + a00) + aE + aSW) * (1.0 / 6.0);
-            DI[(size_t)j * ld + i] = to_store<ST>(1.0 / diag);
+        if (need_di && i >= 1 && i <= n - 1 && j >= 1 && j <= n - 1)
+            DI[(size_t)j * ld + i] = to_store<ST>(1.0 / stencil_diag(S, i, j, 0));
+    }
+    if (mg) {
+        for (int k = 1; k <= S.mg_levels; ++k) {
+            const int nk = n >> k, ldk = row_pitch(nk);
+            const long long off = S.mg_off + mg_coarse_nodes(n, k - 1);
+            ST* ca = static_cast<ST*>(P.cas) + off;
+            ST* cd = static_cast<ST*>(P.cdi) + off;
+            for (int it = tr; it < (nk + 1) * (nk + 1); it += GT) {
+                const int J = it / (nk + 1), I = it - J * (nk + 1);
+                ca[(size_t)J * ldk + I] = to_store<ST>(master_a(S, I << k, J << k));
+                if (I >= 1 && I <= nk - 1 && J >= 1 && J <= nk - 1)
+                    cd[(size_t)J * ldk + I] = to_store<ST>(1.0 / stencil_diag(S, I << k, J << k, k));
+            }
         }
     }
     if (pipe_on) fence_proxy_async_global();
@@ -972,56 +1259,72 @@ __device__ void solve_system(const Params& P, const DevSolve& S, const Group<GT>
                 G.sync();
             }
         } else {
-            // ---- inner PCG on A d = r (z = D^-1 r with Jacobi, z = r otherwise).  The
-            // scalars are formed once per reduction from the FP64 group sums and broadcast.
+            // ---- inner PCG on A d = r: z = D^-1 r (Jacobi), z = B r (multigrid V-cycle) or z = r.
+            // The scalars are formed once per reduction from the FP64 group sums and broadcast.
             const double tau2rr0 = tau * tau * rr0;
             double rzk = rz0;              // (r, z) of the current residual, kept where the scalars are formed
             VT beta = 0;
+            const bool dj = jac && !mg;    // the sweeps form z = D^-1 r themselves
+            const VT* zsrc = mg ? MZ : R;
             bool cont = (rr0 == rr0) && !isinf(rr0) && rr0 > tau2rr0 && rr0 != 0.0 && iters < P.max_iters;
             while (cont) {
                 const VT* pold = (k & 1) ? PB0 : PB1;
                 VT* pnew = (k & 1) ? PB1 : PB0;
+                if (mg) {
+                    // z = B r and (r, z); beta = (r, z) / (r, z)_previous
+                    const VT rzp = mg_vcycle<VT, ST, GT>(P, S, G, MZ, MT, R, AS, DI);
+                    VT sc0[4];
+                    const int k0 = k;
+                    G.template reduce<VT, VT>(rzp, (VT)0, (VT)0,
+                                              [&](double rz, double, double, double* r) {
+                                                  r[0] = k0 > 0 ? rz / rzk : 0.0;
+                                                  rzk = rz;
+                                              },
+                                              sc0);
+                    beta = sc0[0];
+                }
                 // I1: p = z + beta p_old on the segment rows (recomputed on the halo rows); sigma = (p, A p)
                 VT sig = 0;
                 if (sweep_on) {
                     if (pipe_on) {
-                        if (jac)
-                            sig = (k > 0) ? sweep_dir_staged<VT, ST, true, true>(*pipe, R, DI, pold, pnew, AS, beta, ld,
-                                                                                 n, sc, ja, jb)
-                                          : sweep_dir_staged<VT, ST, true, false>(*pipe, R, DI, pold, pnew, AS, beta,
-                                                                                  ld, n, sc, ja, jb);
+                        if (dj)
+                            sig = (k > 0) ? sweep_dir_staged<VT, ST, true, true>(*pipe, zsrc, DI, pold, pnew, AS, beta,
+                                                                                 ld, n, sc, ja, jb)
+                                          : sweep_dir_staged<VT, ST, true, false>(*pipe, zsrc, DI, pold, pnew, AS,
+                                                                                  beta, ld, n, sc, ja, jb);
                         else
-                            sig = (k > 0) ? sweep_dir_staged<VT, ST, false, true>(*pipe, R, DI, pold, pnew, AS, beta,
-                                                                                  ld, n, sc, ja, jb)
-                                          : sweep_dir_staged<VT, ST, false, false>(*pipe, R, DI, pold, pnew, AS,
+                            sig = (k > 0) ? sweep_dir_staged<VT, ST, false, true>(*pipe, zsrc, DI, pold, pnew, AS,
+                                                                                  beta, ld, n, sc, ja, jb)
+                                          : sweep_dir_staged<VT, ST, false, false>(*pipe, zsrc, DI, pold, pnew, AS,
                                                                                    beta, ld, n, sc, ja, jb);
                     } else {
-                        if (jac)
-                            sig = (k > 0) ? sweep_dir<VT, ST, true, true>(R, DI, pold, pnew, AS, beta, ld, n, sc, ja, jb)
-                                          : sweep_dir<VT, ST, true, false>(R, DI, pold, pnew, AS, beta, ld, n, sc, ja,
-                                                                           jb);
+                        if (dj)
+                            sig = (k > 0) ? sweep_dir<VT, ST, true, true>(zsrc, DI, pold, pnew, AS, beta, ld, n, sc,
+                                                                          ja, jb)
+                                          : sweep_dir<VT, ST, true, false>(zsrc, DI, pold, pnew, AS, beta, ld, n, sc,
+                                                                           ja, jb);
                         else
-                            sig = (k > 0) ? sweep_dir<VT, ST, false, true>(R, DI, pold, pnew, AS, beta, ld, n, sc, ja,
-                                                                           jb)
-                                          : sweep_dir<VT, ST, false, false>(R, DI, pold, pnew, AS, beta, ld, n, sc, ja,
-                                                                            jb);
+                            sig = (k > 0) ? sweep_dir<VT, ST, false, true>(zsrc, DI, pold, pnew, AS, beta, ld, n, sc,
+                                                                           ja, jb)
+                                          : sweep_dir<VT, ST, false, false>(zsrc, DI, pold, pnew, AS, beta, ld, n,
+                                                                            sc, ja, jb);
                     }
                 }
                 VT sc1[4];
                 G.template reduce<VT, VT>(sig, (VT)0, (VT)0,
                                           [&](double sg, double, double, double* r) { r[0] = rzk / sg; }, sc1);
                 const VT alpha = sc1[0];
-                // I2: d += alpha p; r -= alpha A p; ||r||^2 and (r, z)
+                // I2: d += alpha p; r -= alpha A p; ||r||^2 and, with Jacobi, (r, D^-1 r)
                 VT nrr = 0, nrz = 0;
                 if (sweep_on) {
                     if (pipe_on) {
-                        if (jac)
+                        if (dj)
                             sweep_upd_staged<VT, ST, true>(*pipe, pnew, R, D, DI, AS, alpha, ld, n, sc, ja, jb, nrr, nrz);
                         else
                             sweep_upd_staged<VT, ST, false>(*pipe, pnew, R, D, DI, AS, alpha, ld, n, sc, ja, jb, nrr,
                                                             nrz);
                     } else {
-                        if (jac)
+                        if (dj)
                             sweep_upd<VT, ST, true>(pnew, R, D, DI, AS, alpha, ld, n, sc, ja, jb, nrr, nrz);
                         else
                             sweep_upd<VT, ST, false>(pnew, R, D, DI, AS, alpha, ld, n, sc, ja, jb, nrr, nrz);
@@ -1034,12 +1337,14 @@ __device__ void solve_system(const Params& P, const DevSolve& S, const Group<GT>
                                               const bool ab = pipe_on && pipe_aborted(*pipe);
                                               const bool go = (rr == rr) && !isinf(rr) && rr > tau2rr0 && rr != 0.0 &&
                                                               iters + kk + 1 < P.max_iters && !ab;
-                                              r[0] = rz / rzk;
+                                              if (!mg) {
+                                                  r[0] = rz / rzk;
+                                                  rzk = rz;
+                                              }
                                               r[1] = go ? 1.0 : 0.0;
-                                              rzk = rz;
                                           },
                                           sc2);
-                beta = sc2[0];
+                if (!mg) beta = sc2[0];
                 cont = sc2[1] != (VT)0;
                 ++k;
             }
@@ -1200,14 +1505,34 @@ __global__ void apply_operator_kernel(int n, int S, const void* a, int a_fp64, i
 }
 
 
+// Algorithmic bytes of one V-cycle summed over the unknowns of every level:
+// per unknown, a sweep from zero reads b and D^-1 and writes x (2 p_v + p_s),
+// a sweep reads x, b, a, D^-1 and writes x (3 p_v + 2 p_s), the residual reads
+// x, b, a and writes t (3 p_v + p_s), restriction reads t and writes the coarse
+// b, prolongation reads the coarse x and x and writes x.
+double mg_iter_bytes(int n, int nl, int nu, int ncs, double pv, double ps) {
+    double bytes = 0.0;
+    for (int k = 0; k <= nl; ++k) {
+        const double u = (double)((n >> k) - 1) * ((n >> k) - 1);
+        if (k < nl) {
+            const double pre = (2 * pv + ps) + (nu - 1) * (3 * pv + 2 * ps), post = nu * (3 * pv + 2 * ps);
+            const double uc = (double)((n >> (k + 1)) - 1) * ((n >> (k + 1)) - 1);
+            bytes += u * (pre + (3 * pv + ps) + pv + 2 * pv + post) + uc * (2 * pv);
+        } else {
+            bytes += u * ((2 * pv + ps) + (ncs - 1) * (3 * pv + 2 * ps));
+        }
+    }
+    return bytes;
+}
+
 // Workspace of a batch: vectors, coefficient storage, descriptors, launch order.
 struct Layout {
-    size_t o_x, o_r, o_p0, o_p1, o_d, o_as, o_dinv, o_vb, o_w0, o_w1, o_stats, o_err, zero_end, o_solves, o_order,
-        total;
+    size_t o_x, o_r, o_p0, o_p1, o_d, o_as, o_dinv, o_vb, o_w0, o_w1, o_mz, o_mt, o_cx, o_ct, o_cb, o_cas, o_cdi,
+        o_stats, o_err, zero_end, o_solves, o_order, total;
 };
 
 template <class VT, class ST>
-Layout make_layout(long long nodes, int ns, bool jacobi, bool minres) {
+Layout make_layout(long long nodes, int ns, bool jacobi, bool minres, bool mg = false, long long cnodes = 0) {
     Layout L{};
     size_t off = 0;
     auto take = [&](size_t bytes) { size_t o = off; off = align_up(off + bytes, 256); return o; };
@@ -1217,10 +1542,17 @@ Layout make_layout(long long nodes, int ns, bool jacobi, bool minres) {
     L.o_p1 = take(sizeof(VT) * nodes);
     L.o_d = take(sizeof(VT) * nodes);
     L.o_as = take(sizeof(ST) * nodes);
-    L.o_dinv = take(jacobi ? sizeof(ST) * nodes : 0);
+    L.o_dinv = take(jacobi || mg ? sizeof(ST) * nodes : 0);
     L.o_vb = take(minres ? sizeof(VT) * nodes : 0);
     L.o_w0 = take(minres ? sizeof(VT) * nodes : 0);
     L.o_w1 = take(minres ? sizeof(VT) * nodes : 0);
+    L.o_mz = take(mg ? sizeof(VT) * nodes : 0);
+    L.o_mt = take(mg ? sizeof(VT) * nodes : 0);
+    L.o_cx = take(mg ? sizeof(VT) * cnodes : 0);
+    L.o_ct = take(mg ? sizeof(VT) * cnodes : 0);
+    L.o_cb = take(mg ? sizeof(VT) * cnodes : 0);
+    L.o_cas = take(mg ? sizeof(ST) * cnodes : 0);
+    L.o_cdi = take(mg ? sizeof(ST) * cnodes : 0);
     L.o_stats = take(sizeof(int32_t) * 2 * ns);
     L.o_err = take(sizeof(unsigned));
     L.zero_end = off;
@@ -1249,6 +1581,17 @@ Params make_params(char* base, const Layout& L, int ns, int nbig, int nmed, int 
     P.vb = base + L.o_vb;
     P.w0 = base + L.o_w0;
     P.w1 = base + L.o_w1;
+    P.mz = base + L.o_mz;
+    P.mt = base + L.o_mt;
+    P.cx = base + L.o_cx;
+    P.ct = base + L.o_ct;
+    P.cb = base + L.o_cb;
+    P.cas = base + L.o_cas;
+    P.cdi = base + L.o_cdi;
+    P.mg = 0;
+    P.mg_nu = 2;
+    P.mg_coarse = 8;
+    P.mg_omega = 0.8;
     P.solver = solver;
     P.sys_iters = reinterpret_cast<int32_t*>(base + L.o_stats);
     P.sys_outer = P.sys_iters + ns;
@@ -1274,7 +1617,6 @@ Params make_params(char* base, const Layout& L, int ns, int nbig, int nmed, int 
 
 // Workspace row pitch: a multiple of 8 elements, so that every row of every
 // array (8- to 2-byte elements) starts on a 16-byte boundary for bulk copies.
-int row_pitch(int n) { return (int)align_up((size_t)n + 1, 8); }
 
 constexpr int kPipeSmemMax = 220 * 1024;   // dynamic shared memory budget of the row pipeline
 
@@ -1334,8 +1676,10 @@ mlmc_status run_typed(mlmc_ctx* ctx, const std::vector<SolveGroup>& groups, cons
                       cudaStream_t st) {
     // ---- host plan
     std::vector<DevSolve> solves;
-    long long total = 0;
+    long long total = 0, ctotal = 0;
     const mlmc_problem& pb = ctx->prob;
+    const int precond = cfg.precond >= 0 ? cfg.precond : ctx->precond;
+    const bool mg = precond == MLMC_PC_MG && cfg.solver == MLMC_CG;
     for (const SolveGroup& g : groups) {
         if (g.S <= 0) continue;
         const int n = g.n;
@@ -1377,6 +1721,9 @@ mlmc_status run_typed(mlmc_ctx* ctx, const std::vector<SolveGroup>& groups, cons
             d.flags = g.flags;
             d.out = s;
             d.sys = (int)solves.size();
+            d.mg_levels = mg ? mg_level_count(n) : 0;
+            d.mg_off = ctotal;
+            ctotal += mg ? mg_coarse_nodes(n, d.mg_levels) : 0;
             solves.push_back(d);
         }
     }
@@ -1393,7 +1740,7 @@ mlmc_status run_typed(mlmc_ctx* ctx, const std::vector<SolveGroup>& groups, cons
         nmed += c == 1;
         nsmall += c == 2;
     }
-    const Layout L = make_layout<VT, ST>(total, ns, cfg.jacobi != 0, cfg.solver == MLMC_MINRES);
+    const Layout L = make_layout<VT, ST>(total, ns, cfg.jacobi != 0, cfg.solver == MLMC_MINRES, mg, ctotal);
     mlmc::DevBuf& buf = ctx->ws.solver;
     MLMC_CUDA_RET(ctx->err, buf.reserve(L.total));
     char* base = buf.as<char>();
@@ -1406,6 +1753,12 @@ mlmc_status run_typed(mlmc_ctx* ctx, const std::vector<SolveGroup>& groups, cons
     Params P = make_params<VT, ST>(base, L, ns, nbig, nmed, nsmall, cfg.max_outer, cfg.max_iters, cfg.prec,
                                    cfg.jacobi, cfg.solver, cfg.inner_theta, cfg.tau_max);
     if (cfg.tau_min > 0) P.tau_min = cfg.tau_min;
+    if (mg) {
+        P.mg = 1;
+        P.mg_nu = ctx->mg_nu;
+        P.mg_coarse = ctx->mg_coarse;
+        P.mg_omega = ctx->mg_omega;
+    }
     size_t smem = 0;
     if (cfg.solver == MLMC_CG) {
         std::vector<int> big_n;
@@ -1454,7 +1807,11 @@ mlmc_status run_typed(mlmc_ctx* ctx, const std::vector<SolveGroup>& groups, cons
             const double pm = d.a_fp64 ? 8.0 : 4.0;
             const double pd = cfg.jacobi ? ps : 0.0;   // inverse diagonal read once per inner iteration
             const int steps = std::min(outer[i], cfg.max_outer);
-            const double per_it = cfg.solver == MLMC_MINRES ? (14 * pv + 2 * ps + pd) : (8 * pv + 2 * ps + pd);
+            const double per_it = cfg.solver == MLMC_MINRES
+                                      ? (14 * pv + 2 * ps + pd)
+                                      : mg ? mg_iter_bytes(d.n, d.mg_levels, P.mg_nu, P.mg_coarse, pv, ps) / unk +
+                                                 8 * pv + 2 * ps
+                                           : (8 * pv + 2 * ps + pd);
             bytes += unk * ((double)it * per_it + (double)(steps + 1) * (8 + pm + 2 * pv + pd) +
                             (double)steps * (16 + pv) + (8 + pm + ps + pd));
             iters += it;

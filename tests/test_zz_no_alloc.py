@@ -29,6 +29,7 @@ def _reference(M, n, af, a_prec, prec, delta, qoi, box):
         kw["box"] = box
     h = M.mlmc_create(M.make_problem(**kw), 0)
     try:
+        M.mlmc_set_precond(h, M.MLMC_PC_JACOBI)    # the allocation-free entry point runs Jacobi-PCG
         S = af.shape[0]
         dt = torch.float64 if a_prec == M.MLMC_FP64 else torch.float32
         Q = torch.empty(S, dtype=torch.float64, device=device())
