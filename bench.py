@@ -38,11 +38,22 @@ L2_FLUSH_BYTES = 512 << 20
 SOLVE_TRAFFIC_BYTES_PER_LAUNCH = None
 
 
+DESC = ("mixed-precision batched MLMC: 5 levels h=1/16..1/256, KL 64 terms (exp. covariance sigma^2=1, "
+        "corr length 0.3), f=1, Q=int u; FP32 inner CG preconditioned by a geometric multigrid V-cycle "
+        "(FP16-stored coefficient while delta_l>=1e-4) with FP64 iterative refinement to delta_l of Eq. (4.12), "
+        "k_p=0.05; N_init=100 per level, N_l from the optimal formula for RMSE 1e-3")
+# The 7-level hierarchy (bench.py --case mlmc7): h = 1/16 .. 1/1024, K = 256, sigma^2 = 1.5, corr 0.1.
+WORKLOAD7 = dict(n0=16, m=2, L_max=6, kind=0, K=256, sigma2=1.5, corr_len=0.1, q=2.0, qoi=0, f=1.0)
+TOL7 = 2e-4
+DESC7 = ("mixed-precision batched MLMC: 7 levels h=1/16..1/1024, KL 256 terms (exp. covariance sigma^2=1.5, "
+         "corr length 0.1), f=1, Q=int u; FP32 inner CG preconditioned by a geometric multigrid V-cycle "
+         "(FP16-stored coefficient while delta_l>=1e-4) with FP64 iterative refinement to delta_l of Eq. (4.12), "
+         "k_p=0.05, FP64 re-runs of refinements that stagnate; N_init=100 per level, N_l from the optimal formula "
+         "for RMSE 2e-4")
+
+
 def workload_desc():
-    return ("mixed-precision batched MLMC: 5 levels h=1/16..1/256, KL 64 terms (exp. covariance sigma^2=1, "
-            "corr length 0.3), f=1, Q=int u; FP32 inner CG (FP16-stored coefficient while delta_l>=1e-4) with "
-            "FP64 iterative refinement to delta_l of Eq. (4.12), k_p=0.05; N_init=100 per level, N_l from the "
-            "optimal formula for RMSE 1e-3")
+    return DESC
 
 
 def peaks():
@@ -184,7 +195,7 @@ def main():
     ap.add_argument("--impl", default="libmlmc", choices=["libmlmc", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-fp64", action="store_true")
-    ap.add_argument("--case", default="mlmc", choices=["mlmc", "solve-l4", "kl-synth", "sweep", "adjoint"],
+    ap.add_argument("--case", default="mlmc", choices=["mlmc", "mlmc7", "solve-l4", "kl-synth", "sweep", "adjoint"],
                     help="solve-l4: only the finest level's batch (100 samples, n = 256) of the workload: "
                          "field synthesis and one resident-solve launch per step; kl-synth: tensor-core "
                          "KL synthesis alone at the single-level sweep shapes (n = 512, K = 128, corr 0.1)")
@@ -198,6 +209,10 @@ def main():
     ap.add_argument("--ring", type=int, default=-1,
                     help="solve-l4: row-pipeline slots of the large CG solves (-1 automatic, 0 plain loads)")
     args = ap.parse_args()
+    if args.case == "mlmc7":
+        global WORKLOAD, TOL, DESC
+        WORKLOAD, TOL, DESC = WORKLOAD7, TOL7, DESC7
+        args.no_cpu_baseline = True     # the oracle's banded solves at h = 1/1024 take minutes per sample
     if args.impl == "reference":
         return run_reference(args)
 
@@ -288,7 +303,7 @@ def main():
         for name, form in (("fp64_fixed_1e-10", M.MLMC_FORM_FP64_FIXED), ("fp64_adaptive", M.MLMC_FORM_FP64_ADAPTIVE)):
             fms, fres, _, _ = timed_runs(form, 1, 1, 1000 + rank)
             fp64[name] = {"seconds": fms[0] / 1e3, "N_l": fres[0]["N"], "inner_iters": sum(fres[0]["inner_iters"]),
-                          "estimate": fres[0]["estimate"]}
+                          "estimate": fres[0]["estimate"], "rmse": fres[0]["rmse"]}
 
     # e2e through the C ABI from host data
     e2e_s, h2d, d2h = [], 0, 0
@@ -313,10 +328,12 @@ def main():
             "metric": METRIC, "value": step_s, "unit": "s", "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": False, "scaling": "weak",
             "vs_baseline": None, "dtype": "f32+f64", "data": "synthetic",
+            **({"case": "mlmc7"} if args.case == "mlmc7" else {}),
             "config": {"workload": workload_desc(), "l2": "flushed between timed steps (512 MiB write)",
                        "seed": "1000 + rank", "parallelism": "replicas" if world > 1 else "single GPU"},
             "solved_dof_per_s": dofs / step_s,
             "rmse": [r["rmse"] for r in results], "N_l": results[-1]["N"], "rounds": results[-1]["rounds"],
+            "prec_l": results[-1]["prec"], "fp64_retries_l": results[-1]["fp64_retries"],
             "inner_iters_per_step": sum(iters) / len(iters),
             "fp64": fp64,
             "roofline": {"bound": "hbm", "kernel": "resident_solve", "achieved": achieved, "peak": hbm_peak,

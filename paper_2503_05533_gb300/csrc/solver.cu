@@ -222,15 +222,37 @@ __device__ __forceinline__ double qoi_weight(const DevSolve& S, int i, int j) {
     return S.h2 * (double)cnt * (1.0 / 6.0);
 }
 
-// Diagonal of the P1 operator at fine-grid node (i, j) of the grid whose nodes are 2^k fine nodes
-// apart (k = 0: the grid itself), from the master coefficient, in FP64.
-__device__ __forceinline__ double stencil_diag(const DevSolve& S, int i, int j, int k) {
+// The master coefficient at node (i, j) in the compute type CT: FP32 masters are read as FP32
+// (no FP64 conversion when CT is float).
+template <class CT>
+__device__ __forceinline__ CT master_a_as(const DevSolve& S, int i, int j) {
+    const long long idx = (long long)j * S.a_row + (long long)i * S.a_col;
+    return S.a_fp64 ? (CT)__ldg(static_cast<const double*>(S.a) + idx)
+                    : (CT)__ldg(static_cast<const float*>(S.a) + idx);
+}
+
+// Inverse diagonal of the P1 operator at fine-grid node (i, j) of the grid whose nodes are 2^k
+// fine nodes apart (k = 0: the grid itself), from the master coefficient, in the compute type
+// of the inner solve (it only enters the preconditioner).
+template <class CT>
+__device__ __forceinline__ CT stencil_inv_diag(const DevSolve& S, int i, int j, int k) {
     const int d = 1 << k;
-    const double a00 = master_a(S, i, j), aE = master_a(S, i + d, j), aW = master_a(S, i - d, j);
-    const double aN = master_a(S, i, j + d), aS = master_a(S, i, j - d);
-    const double aNE = master_a(S, i + d, j + d), aSW = master_a(S, i - d, j - d);
-    return (2.0 * (a00 + aE) + aNE + aS + 2.0 * (aW + a00) + aN + aSW + 2.0 * (a00 + aN) + aNE + aW +
-            2.0 * (aS + a00) + aE + aSW) * (1.0 / 6.0);
+    const CT a00 = master_a_as<CT>(S, i, j), aE = master_a_as<CT>(S, i + d, j), aW = master_a_as<CT>(S, i - d, j);
+    const CT aN = master_a_as<CT>(S, i, j + d), aS = master_a_as<CT>(S, i, j - d);
+    const CT aNE = master_a_as<CT>(S, i + d, j + d), aSW = master_a_as<CT>(S, i - d, j - d);
+    const CT two = (CT)2;
+    const CT diag = (two * (a00 + aE) + aNE + aS + two * (aW + a00) + aN + aSW + two * (a00 + aN) + aNE + aW +
+                     two * (aS + a00) + aE + aSW) * (CT)(1.0 / 6.0);
+    return (CT)1 / diag;
+}
+
+// A master value in the storage type, converted from the compute type.
+template <class ST, class CT> __device__ __forceinline__ ST store_from(CT v);
+template <> __device__ __forceinline__ double store_from<double, double>(double v) { return v; }
+template <> __device__ __forceinline__ float store_from<float, float>(float v) { return v; }
+template <> __device__ __forceinline__ __half store_from<__half, float>(float v) { return __float2half_rn(v); }
+template <> __device__ __forceinline__ __nv_bfloat16 store_from<__nv_bfloat16, float>(float v) {
+    return __float2bfloat16_rn(v);
 }
 
 __device__ __forceinline__ double rhs_value(const DevSolve& S, int i, int j) {
@@ -972,15 +994,15 @@ __device__ __forceinline__ void mg_restrict(const Group<GT>& G, const MGLevel<VT
     const VT half = (VT)0.5;
     for (int it = G.rank; it < items; it += GT) {
         const int J = 1 + it / C.cpr, Cc = it - (J - 1) * C.cpr;
-        VT v[3][9];     // fine rows 2J-1 .. 2J+1, columns 8Cc-1 .. 8Cc+7
+        // fine rows 2J-1 .. 2J+1, columns 8Cc-1 .. 8Cc+7: two aligned 4-wide loads and one halo
+        // value per row (columns past n are padding, which stays zero, and lie within the row pitch)
+        VT v[3][9];
 #pragma unroll
         for (int r = 0; r < 3; ++r) {
-            const VT* row = F.t + (size_t)(2 * J - 1 + r) * F.ld;
-#pragma unroll
-            for (int m = 0; m < 9; ++m) {
-                const int col = 8 * Cc - 1 + m;
-                v[r][m] = (col >= 0 && col <= F.n) ? row[col] : (VT)0;
-            }
+            const VT* row = F.t + (size_t)(2 * J - 1 + r) * F.ld + 8 * Cc;
+            Vec4<VT>::load(row, &v[r][1]);
+            Vec4<VT>::load(row + 4, &v[r][5]);
+            v[r][0] = Cc > 0 ? row[-1] : (VT)0;
         }
         VT o4[4];
 #pragma unroll
@@ -1123,9 +1145,9 @@ __device__ void solve_system(const Params& P, const DevSolve& S, const Group<GT>
     const bool need_di = jac || mg;
     for (int it = tr; it < (n + 1) * (n + 1); it += GT) {
         const int j = it / (n + 1), i = it - j * (n + 1);
-        AS[(size_t)j * ld + i] = to_store<ST>(master_a(S, i, j));
+        AS[(size_t)j * ld + i] = store_from<ST, VT>(master_a_as<VT>(S, i, j));
         if (need_di && i >= 1 && i <= n - 1 && j >= 1 && j <= n - 1)
-            DI[(size_t)j * ld + i] = to_store<ST>(1.0 / stencil_diag(S, i, j, 0));
+            DI[(size_t)j * ld + i] = store_from<ST, VT>(stencil_inv_diag<VT>(S, i, j, 0));
     }
     if (mg) {
         for (int k = 1; k <= S.mg_levels; ++k) {
@@ -1135,9 +1157,9 @@ __device__ void solve_system(const Params& P, const DevSolve& S, const Group<GT>
             ST* cd = static_cast<ST*>(P.cdi) + off;
             for (int it = tr; it < (nk + 1) * (nk + 1); it += GT) {
                 const int J = it / (nk + 1), I = it - J * (nk + 1);
-                ca[(size_t)J * ldk + I] = to_store<ST>(master_a(S, I << k, J << k));
+                ca[(size_t)J * ldk + I] = store_from<ST, VT>(master_a_as<VT>(S, I << k, J << k));
                 if (I >= 1 && I <= nk - 1 && J >= 1 && J <= nk - 1)
-                    cd[(size_t)J * ldk + I] = to_store<ST>(1.0 / stencil_diag(S, I << k, J << k, k));
+                    cd[(size_t)J * ldk + I] = store_from<ST, VT>(stencil_inv_diag<VT>(S, I << k, J << k, k));
             }
         }
     }
