@@ -206,6 +206,12 @@ def main():
                     help="sweep: relative residual (1e-6 for the measurement; larger for short profiles)")
     ap.add_argument("--prec", default="FP32", choices=["FP64", "FP32", "BF16S", "FP16S"],
                     help="sweep: inner precision (FP64 uses an FP64 field and FP64 vectors)")
+    ap.add_argument("--pc", default="mg", choices=["mg", "jacobi"],
+                    help="solve-l4 and sweep: preconditioner of the CG inner solves")
+    ap.add_argument("--mg-nu", type=int, default=0, help="solve-l4 and sweep: smoothing sweeps (0: default)")
+    ap.add_argument("--mg-coarse", type=int, default=0, help="solve-l4 and sweep: coarsest-grid sweeps (0: default)")
+    ap.add_argument("--tau-min", type=float, default=0.0,
+                    help="solve-l4 and sweep: floor of the inner tolerance (0: per-precision default)")
     ap.add_argument("--ring", type=int, default=-1,
                     help="solve-l4: row-pipeline slots of the large CG solves (-1 automatic, 0 plain loads)")
     args = ap.parse_args()
@@ -400,6 +406,8 @@ def solve_l4_case(M, torch, dev, args, prob, hbm_peak, peak_src, flush, stream):
     try:
         M.mlmc_profile_enable(h, True)
         M.mlmc_debug_set_solve_ring(h, args.ring)
+        M.mlmc_set_precond(h, M.MLMC_PC_MG if args.pc == "mg" else M.MLMC_PC_JACOBI, args.mg_nu, args.mg_coarse)
+        M.mlmc_set_inner_tolerance(h, 0.0, args.tau_min)
         a = torch.empty((S, (n + 1) ** 2), dtype=torch.float32, device=dev)
         Q = torch.empty(S, dtype=torch.float64, device=dev)
         it = torch.empty(S, dtype=torch.int32, device=dev)
@@ -421,7 +429,8 @@ def solve_l4_case(M, torch, dev, args, prob, hbm_peak, peak_src, flush, stream):
     finally:
         M.mlmc_destroy(h)
     achieved = prof["solve_bytes"] / (prof["solve_ms"] * 1e-3) / 1e9
-    print(json.dumps({"case": "solve-l4", "ring": args.ring, "ms_per_step": sum(ms) / len(ms), "systems": S, "n": n,
+    print(json.dumps({"case": "solve-l4", "ring": args.ring, "pc": args.pc, "mg_nu": args.mg_nu, "tau_min": args.tau_min,
+                      "mg_coarse": args.mg_coarse, "ms_per_step": sum(ms) / len(ms), "systems": S, "n": n,
                       "delta": deltas[level], "prec": precs[level],
                       "inner_iters_per_system": prof["inner_iters"] / (S * args.steps),
                       "solve_ms_per_launch": prof["solve_ms"] / prof["solve_launches"],
@@ -482,6 +491,7 @@ def sweep_case(M, torch, dev, args, hbm_peak, peak_src, flush, stream):
     try:
         M.mlmc_profile_enable(h, True)
         M.mlmc_debug_set_solve_ring(h, args.ring)
+        M.mlmc_set_precond(h, M.MLMC_PC_MG if args.pc == "mg" else M.MLMC_PC_JACOBI, args.mg_nu, args.mg_coarse)
         a = torch.empty((S, (n + 1) ** 2), dtype=torch.float64 if fp64 else torch.float32, device=dev)
         Q = torch.empty(S, dtype=torch.float64, device=dev)
         it = torch.empty(S, dtype=torch.int32, device=dev)

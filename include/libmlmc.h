@@ -346,6 +346,15 @@ mlmc_status mlmc_adjoint_grad(mlmc_ctx* ctx, int level, int S, const double* xi,
  * on the FP64 residual of the refinement (Alg. 2.1). */
 mlmc_status mlmc_set_precond(mlmc_ctx* ctx, mlmc_precond pc, int nu, int coarse_sweeps, double omega);
 
+/* Inner tolerance of the refinement (Alg. 2.1) for this context's solves: each
+ * inner solve stops at ||r_k|| <= tau ||r_0|| with tau = clamp(theta delta /
+ * rho, tau_min, 0.5), rho the current relative residual.  theta = 0 keeps the
+ * current value (default 0.3); tau_min <= 0 restores the per-precision floor
+ * (1e-14 FP64, 1e-6 FP32, 1e-3 BF16 storage, 1e-4 FP16 storage), the accuracy
+ * an inner solve in that precision can be relied on to reach.  Stopping and
+ * the result are always judged on the FP64 residual. */
+mlmc_status mlmc_set_inner_tolerance(mlmc_ctx* ctx, double theta, double tau_min);
+
 /* Diagnostics.  Timeout of every bounded device-side wait of this context, in
  * seconds (default 10): the tensor-core synthesis waits on its TMA copies and
  * MMAs, and the large CG solves wait on the bulk row copies of their pipeline.

@@ -102,6 +102,7 @@ _SIGS = {
     "mlmc_debug_set_wait_extra": (c_int, [c_void_p, c_int]),
     "mlmc_debug_set_solve_ring": (c_int, [c_void_p, c_int]),
     "mlmc_set_precond": (c_int, [c_void_p, c_int, c_int, c_int, c_double]),
+    "mlmc_set_inner_tolerance": (c_int, [c_void_p, c_double, c_double]),
     "mlmc_profile_enable": (c_int, [c_void_p, c_int]),
     "mlmc_profile_get": (c_int, [c_void_p, c_void_p]),
     "mlmc_profile_reset": (c_int, [c_void_p]),
@@ -216,6 +217,10 @@ def mlmc_debug_set_wait_extra(ctx, extra):
 
 def mlmc_set_precond(ctx, pc, nu=0, coarse_sweeps=0, omega=0.0):
     _check(lib().mlmc_set_precond(ctx, pc, nu, coarse_sweeps, omega), ctx)
+
+
+def mlmc_set_inner_tolerance(ctx, theta=0.0, tau_min=0.0):
+    _check(lib().mlmc_set_inner_tolerance(ctx, theta, tau_min), ctx)
 
 
 def mlmc_debug_set_solve_ring(ctx, ring):

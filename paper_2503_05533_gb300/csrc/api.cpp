@@ -405,6 +405,15 @@ mlmc_status mlmc_set_precond(mlmc_ctx* ctx, mlmc_precond pc, int nu, int coarse_
     return MLMC_OK;
 }
 
+mlmc_status mlmc_set_inner_tolerance(mlmc_ctx* ctx, double theta, double tau_min) {
+    if (!ctx) return MLMC_E_ARG;
+    if (!(theta >= 0.0 && theta < 1.0) || !(tau_min < 0.5))
+        return fail(ctx, MLMC_E_ARG, "set_inner_tolerance: theta in [0, 1), tau_min < 0.5");
+    if (theta > 0.0) ctx->inner_theta = theta;
+    ctx->inner_tau_min = tau_min > 0.0 ? tau_min : -1.0;
+    return MLMC_OK;
+}
+
 mlmc_status mlmc_debug_set_solve_ring(mlmc_ctx* ctx, int ring) {
     if (!ctx || ring < -1 || ring == 1 || ring > 4) return MLMC_E_ARG;
     ctx->solve_ring = ring;

@@ -96,6 +96,8 @@ struct mlmc_ctx {
     int mg_nu = 2;                // multigrid: smoothing sweeps before and after the coarse correction
     int mg_coarse = 8;            // multigrid: Jacobi sweeps on the coarsest grid
     double mg_omega = 0.8;        // multigrid: Jacobi damping
+    double inner_theta = 0.3;     // inner tolerance tau = clamp(theta delta / rho, tau_min, 0.5)
+    double inner_tau_min = -1.0;  // < 0: per-precision default
     mlmc::Profile prof;
 };
 

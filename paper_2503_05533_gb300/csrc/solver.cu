@@ -934,33 +934,68 @@ __device__ __forceinline__ MGLevel<VT, ST> mg_level(const Params& P, const DevSo
     return L;
 }
 
+// The loads of one 4-node chunk of a smoothing or residual pass.  Passes handle
+// two chunks per step, loading both before using either, so that each thread
+// keeps two chunks' loads in flight.
+template <class VT>
+struct MGChunk {
+    VT b4[4], d4[4], a3[3][6], xs[4], xc[6], xn[4];
+};
+
+template <class VT, class ST, bool IN, bool DI>
+__device__ __forceinline__ void mg_load(const MGLevel<VT, ST>& L, const VT* in, int it, MGChunk<VT>& C) {
+    const int j = 1 + it / L.cpr, c = it - (j - 1) * L.cpr;
+    const size_t base = (size_t)j * L.ld + 4 * c;
+    Vec4<VT>::load(L.b + base, C.b4);
+    if (DI) CoefLoad<ST, VT>::load4(L.di + base, C.d4);
+    if (IN) {
+        load_coef_chunk<ST, VT>(L.a, L.ld, L.n, j, c, C.a3);
+        load_vec_chunk<VT>(in, L.ld, L.n, j, c, C.xs, C.xc, C.xn);
+    }
+}
+
+// Smoothing step on one loaded chunk: out = in + w D^-1 (b - A in); returns (b, out) when RZ.
+template <class VT, class ST, bool IN, bool RZ>
+__device__ __forceinline__ VT mg_smooth_store(const MGLevel<VT, ST>& L, VT* out, int it, const MGChunk<VT>& C,
+                                              VT w) {
+    const int j = 1 + it / L.cpr, c = it - (j - 1) * L.cpr;
+    VT y[4] = {(VT)0, (VT)0, (VT)0, (VT)0}, x4[4] = {(VT)0, (VT)0, (VT)0, (VT)0};
+    if (IN) {
+        apply_chunk<VT>(C.a3, C.xs, C.xc, C.xn, L.n, c, y);
+#pragma unroll
+        for (int q = 0; q < 4; ++q) x4[q] = C.xc[q + 1];
+    }
+    VT o4[4], acc = 0;
+#pragma unroll
+    for (int q = 0; q < 4; ++q) o4[q] = fma_rn(mul_rn(w, C.d4[q]), C.b4[q] - y[q], x4[q]);
+    Vec4<VT>::store(out + (size_t)j * L.ld + 4 * c, o4);
+    if (RZ) {
+#pragma unroll
+        for (int q = 0; q < 4; ++q) acc += C.b4[q] * o4[q];
+    }
+    return acc;
+}
+
 // out = in + w D^-1 (b - A in) (in == nullptr: out = w D^-1 b); returns this
 // thread's part of (b, out) when RZ.
 template <class VT, class ST, int GT, bool RZ>
 __device__ __forceinline__ VT mg_smooth(const Group<GT>& G, const MGLevel<VT, ST>& L, const VT* in, VT* out, VT w) {
-    const int n = L.n, ld = L.ld, cpr = L.cpr, items = (n - 1) * cpr;
+    const int items = (L.n - 1) * L.cpr;
     VT acc = 0;
-    for (int it = G.rank; it < items; it += GT) {
-        const int j = 1 + it / cpr, c = it - (j - 1) * cpr;
-        const size_t base = (size_t)j * ld + 4 * c;
-        VT b4[4], d4[4], y[4] = {(VT)0, (VT)0, (VT)0, (VT)0}, x4[4] = {(VT)0, (VT)0, (VT)0, (VT)0};
-        Vec4<VT>::load(L.b + base, b4);
-        CoefLoad<ST, VT>::load4(L.di + base, d4);
+    for (int it0 = G.rank; it0 < items; it0 += 2 * GT) {
+        const bool two = it0 + GT < items;
+        const int it1 = two ? it0 + GT : it0;     // a second valid chunk, or a repeat that is not stored
+        MGChunk<VT> c0, c1;
         if (in) {
-            VT a3[3][6], xs[4], xc[6], xn[4];
-            load_coef_chunk<ST, VT>(L.a, ld, n, j, c, a3);
-            load_vec_chunk<VT>(in, ld, n, j, c, xs, xc, xn);
-            apply_chunk<VT>(a3, xs, xc, xn, n, c, y);
-#pragma unroll
-            for (int q = 0; q < 4; ++q) x4[q] = xc[q + 1];
-        }
-        VT o4[4];
-#pragma unroll
-        for (int q = 0; q < 4; ++q) o4[q] = fma_rn(mul_rn(w, d4[q]), b4[q] - y[q], x4[q]);
-        Vec4<VT>::store(out + base, o4);
-        if (RZ) {
-#pragma unroll
-            for (int q = 0; q < 4; ++q) acc += b4[q] * o4[q];
+            mg_load<VT, ST, true, true>(L, in, it0, c0);
+            mg_load<VT, ST, true, true>(L, in, it1, c1);
+            acc += mg_smooth_store<VT, ST, true, RZ>(L, out, it0, c0, w);
+            if (two) acc += mg_smooth_store<VT, ST, true, RZ>(L, out, it1, c1, w);
+        } else {
+            mg_load<VT, ST, false, true>(L, in, it0, c0);
+            mg_load<VT, ST, false, true>(L, in, it1, c1);
+            acc += mg_smooth_store<VT, ST, false, RZ>(L, out, it0, c0, w);
+            if (two) acc += mg_smooth_store<VT, ST, false, RZ>(L, out, it1, c1, w);
         }
     }
     G.sync();
@@ -970,18 +1005,23 @@ __device__ __forceinline__ VT mg_smooth(const Group<GT>& G, const MGLevel<VT, ST
 // t = b - A x on level L.
 template <class VT, class ST, int GT>
 __device__ __forceinline__ void mg_residual(const Group<GT>& G, const MGLevel<VT, ST>& L) {
-    const int n = L.n, ld = L.ld, cpr = L.cpr, items = (n - 1) * cpr;
-    for (int it = G.rank; it < items; it += GT) {
-        const int j = 1 + it / cpr, c = it - (j - 1) * cpr;
-        const size_t base = (size_t)j * ld + 4 * c;
-        VT b4[4], y[4], a3[3][6], xs[4], xc[6], xn[4];
-        Vec4<VT>::load(L.b + base, b4);
-        load_coef_chunk<ST, VT>(L.a, ld, n, j, c, a3);
-        load_vec_chunk<VT>(L.x, ld, n, j, c, xs, xc, xn);
-        apply_chunk<VT>(a3, xs, xc, xn, n, c, y);
+    const int items = (L.n - 1) * L.cpr;
+    auto finish = [&](int it, const MGChunk<VT>& C) {
+        const int j = 1 + it / L.cpr, c = it - (j - 1) * L.cpr;
+        VT y[4], r4[4];
+        apply_chunk<VT>(C.a3, C.xs, C.xc, C.xn, L.n, c, y);
 #pragma unroll
-        for (int q = 0; q < 4; ++q) b4[q] -= y[q];
-        Vec4<VT>::store(L.t + base, b4);
+        for (int q = 0; q < 4; ++q) r4[q] = C.b4[q] - y[q];
+        Vec4<VT>::store(L.t + (size_t)j * L.ld + 4 * c, r4);
+    };
+    for (int it0 = G.rank; it0 < items; it0 += 2 * GT) {
+        const bool two = it0 + GT < items;
+        const int it1 = two ? it0 + GT : it0;
+        MGChunk<VT> c0, c1;
+        mg_load<VT, ST, true, false>(L, L.x, it0, c0);
+        mg_load<VT, ST, true, false>(L, L.x, it1, c1);
+        finish(it0, c0);
+        if (two) finish(it1, c1);
     }
     G.sync();
 }
@@ -1169,27 +1209,41 @@ __device__ void solve_system(const Params& P, const DevSolve& S, const Group<GT>
     double rho = 0.0, rho_prev = 0.0;
     int iters = 0, flag = 0, o = 0;
     for (;; ++o) {
-        // ---- R: r = b - A x in FP64 with the master coefficient; d = 0
+        // ---- R: r = b - A x in FP64 with the master coefficient (r = b while x = 0); d = 0
         double res = 0.0, rr0 = 0.0, rz0 = 0.0;
         for (int it = tr; it < items; it += GT) {
             const int j = 1 + it / cpr, c = it - (j - 1) * cpr;
-            double xs[4], xc[6], xn[4];
-            load_vec_chunk<double>(X, ld, n, j, c, xs, xc, xn);
             const size_t base = (size_t)j * ld + 4 * c;
             VT rv[4], zv[4];
             if (jac) CoefLoad<ST, VT>::load4(DI + base, zv);
+            double r4[4];
+            if (o == 0) {
+#pragma unroll
+                for (int q = 0; q < 4; ++q) {
+                    const int i = 4 * c + q;
+                    r4[q] = (i >= 1 && i <= n - 1) ? rhs_value(S, i, j) : 0.0;
+                }
+            } else {
+                double xs[4], xc[6], xn[4];
+                load_vec_chunk<double>(X, ld, n, j, c, xs, xc, xn);
+#pragma unroll
+                for (int q = 0; q < 4; ++q) {
+                    const int i = 4 * c + q;
+                    double rq = 0.0;
+                    if (i >= 1 && i <= n - 1) {
+                        const double a00 = master_a(S, i, j), aE = master_a(S, i + 1, j), aW = master_a(S, i - 1, j);
+                        const double aN = master_a(S, i, j + 1), aS = master_a(S, i, j - 1);
+                        const double aNE = master_a(S, i + 1, j + 1), aSW = master_a(S, i - 1, j - 1);
+                        const double ax = stencil_point<double>(a00, aE, aW, aN, aS, aNE, aSW, xc[q + 1], xc[q + 2],
+                                                                xc[q], xn[q], xs[q]);
+                        rq = rhs_value(S, i, j) - ax;
+                    }
+                    r4[q] = rq;
+                }
+            }
 #pragma unroll
             for (int q = 0; q < 4; ++q) {
-                const int i = 4 * c + q;
-                double rq = 0.0;
-                if (i >= 1 && i <= n - 1) {
-                    const double a00 = master_a(S, i, j), aE = master_a(S, i + 1, j), aW = master_a(S, i - 1, j);
-                    const double aN = master_a(S, i, j + 1), aS = master_a(S, i, j - 1);
-                    const double aNE = master_a(S, i + 1, j + 1), aSW = master_a(S, i - 1, j - 1);
-                    const double ax = stencil_point<double>(a00, aE, aW, aN, aS, aNE, aSW, xc[q + 1], xc[q + 2],
-                                                            xc[q], xn[q], xs[q]);
-                    rq = rhs_value(S, i, j) - ax;
-                }
+                const double rq = r4[q];
                 rv[q] = (VT)rq;
                 res += rq * rq;
                 rr0 += (double)rv[q] * (double)rv[q];
@@ -1773,7 +1827,8 @@ mlmc_status run_typed(mlmc_ctx* ctx, const std::vector<SolveGroup>& groups, cons
     MLMC_CUDA_RET(ctx->err, cudaMemcpyAsync(base + L.o_order, order.data(), sizeof(int) * ns,
                                             cudaMemcpyHostToDevice, st));
     Params P = make_params<VT, ST>(base, L, ns, nbig, nmed, nsmall, cfg.max_outer, cfg.max_iters, cfg.prec,
-                                   cfg.jacobi, cfg.solver, cfg.inner_theta, cfg.tau_max);
+                                   cfg.jacobi, cfg.solver, ctx->inner_theta, cfg.tau_max);
+    if (ctx->inner_tau_min > 0) P.tau_min = ctx->inner_tau_min;
     if (cfg.tau_min > 0) P.tau_min = cfg.tau_min;
     if (mg) {
         P.mg = 1;
