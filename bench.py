@@ -296,9 +296,8 @@ def main():
         ms, results, launches, prof = timed_runs(M.MLMC_FORM_MIXED, args.steps, args.warmup, 1000 + rank, True)
     total_ms = sum(ms)
     if dist:
-        t = torch.tensor([total_ms], dtype=torch.float64, device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        total_ms = t.item()
+        from paper_2503_05533_gb300 import replicas
+        total_ms = replicas.max_over_ranks(dist, total_ms, device=dev)
     ms_per_step = total_ms / args.steps
     dofs = sum(sum(r["dofs"]) for r in results) / len(results)
     iters = [sum(r["inner_iters"]) for r in results]
