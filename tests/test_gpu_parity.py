@@ -461,3 +461,78 @@ def test_minres_mixed_reaches_delta(M, prec, delta):
             assert abs(Q[s] - Qo) <= bound * 1.01
     finally:
         M.mlmc_destroy(h)
+
+
+# ---------------------------------------------------------------- A5: multigrid preconditioner
+def _solve_pc(M, h, n, af, a_prec, prec, delta, pc, nu=0, coarse=0, omega=0.0):
+    M.mlmc_set_precond(h, pc, nu, coarse, omega)
+    try:
+        return _solve(M, h, n, af, a_prec, n, prec, delta)
+    finally:
+        M.mlmc_set_precond(h, M.MLMC_PC_MG, 2, 8, 0.8)
+
+
+@pytest.mark.parametrize("prec", ["FP64", "FP32", "FP16S"])
+def test_multigrid_and_jacobi_reach_the_same_solution(M, prec):
+    p = getattr(M, "MLMC_" + prec)
+    ap = M.MLMC_FP64 if prec == "FP64" else M.MLMC_FP32
+    h = _ctx(M)
+    try:
+        n, S = 128, 3
+        af = smooth_lognormal_field(n, S, seed=640, log_sd=1.2)
+        delta = fp64_delta(n) if prec == "FP64" else 1e-7
+        Um, Qm, itm, rrm, flm = _solve_pc(M, h, n, af, ap, p, delta, M.MLMC_PC_MG)
+        Uj, Qj, itj, rrj, flj = _solve_pc(M, h, n, af, ap, p, delta, M.MLMC_PC_JACOBI)
+        assert np.all(flm == M.MLMC_F_CONVERGED) and np.all(flj == M.MLMC_F_CONVERGED)
+        # a V-cycle per iteration: iterations no longer grow like h^-1
+        assert np.all(itm * 10 < itj), (itm, itj)
+        b = o_fem.load_vector(n)
+        g = o_fem.qoi_weights(n)
+        for s in range(S):
+            A = o_fem.assemble(n, af[s])
+            lmin = spla.eigsh(A, k=1, sigma=0, which="LM", return_eigenvectors=False)[0]
+            _, Qo = o_fem.solve_sample(n, af[s])
+            for U, Q, rr in ((Um, Qm, rrm), (Uj, Qj, rrj)):
+                res = o_fem.relative_residual(n, af[s], _interior(n, U[s]))
+                assert res < (2 * delta if prec == "FP64" else delta * (1 + 1e-6))
+                assert abs(Q[s] - Qo) <= np.linalg.norm(g) * res * np.linalg.norm(b) / lmin * 1.01 + 1e-15 * abs(Qo)
+    finally:
+        M.mlmc_destroy(h)
+
+
+@pytest.mark.parametrize("n", [6, 24, 60, 100, 192])
+def test_multigrid_hierarchies_that_stop_early(M, n):
+    # coarsening halves while the grid is even and the half has >= 4 cells:
+    # 6 has no coarse grid, 24 -> 12 -> 6, 60 -> 30 -> 15, 100 -> 50 -> 25, 192 -> ... -> 6
+    h = _ctx(M)
+    try:
+        af = smooth_lognormal_field(n, 2, seed=700 + n, log_sd=1.0)
+        delta = fp64_delta(n)
+        U, Q, it, rr, fl = _solve_pc(M, h, n, af, M.MLMC_FP64, M.MLMC_FP64, delta, M.MLMC_PC_MG)
+        assert np.all(fl == M.MLMC_F_CONVERGED)
+        for s in range(2):
+            x, Qo = o_fem.solve_sample(n, af[s])
+            assert abs(Q[s] - Qo) <= 1e-11 * abs(Qo)
+            assert np.max(np.abs(_interior(n, U[s]) - x)) <= 1e-10 * np.max(np.abs(x))
+    finally:
+        M.mlmc_destroy(h)
+
+
+@pytest.mark.parametrize("nu,coarse,omega", [(1, 2, 0.8), (2, 16, 0.6), (1, 8, 0.9)])
+def test_multigrid_parameters(M, nu, coarse, omega):
+    h = _ctx(M)
+    try:
+        n = 64
+        af = smooth_lognormal_field(n, 3, seed=77, log_sd=1.0)
+        U, Q, it, rr, fl = _solve_pc(M, h, n, af, M.MLMC_FP32, M.MLMC_FP32, 1e-8, M.MLMC_PC_MG, nu, coarse, omega)
+        assert np.all(fl == M.MLMC_F_CONVERGED) and np.all(rr < 1e-8)
+        for s in range(3):
+            assert o_fem.relative_residual(n, af[s], _interior(n, U[s])) < 1e-8 * (1 + 1e-6)
+        with pytest.raises(M.MlmcError):
+            M.mlmc_set_precond(h, M.MLMC_PC_MG, 3, 0, 0.0)     # nu is 1 or 2
+        with pytest.raises(M.MlmcError):
+            M.mlmc_set_precond(h, M.MLMC_PC_MG, 0, 3, 0.0)     # coarse sweeps even
+        with pytest.raises(M.MlmcError):
+            M.mlmc_set_inner_tolerance(h, 1.5, 0.0)
+    finally:
+        M.mlmc_destroy(h)
