@@ -340,8 +340,15 @@ void mlmc_destroy(mlmc_ctx* ctx) {
         cudaEventDestroy(p.a);
         cudaEventDestroy(p.b);
     }
+    for (cudaStream_t& a : ctx->aux)
+        if (a) {
+            cudaStreamSynchronize(a);
+            cudaStreamDestroy(a);
+            a = nullptr;
+        }
     Workspace& w = ctx->ws;
-    for (DevBuf* b : {&w.solver, &w.fields, &w.xi, &w.q, &w.misc, &w.split, &w.adj}) b->release();
+    for (DevBuf& b : w.solver_slot) b.release();
+    for (DevBuf* b : {&w.fields, &w.xi, &w.q, &w.misc, &w.split, &w.adj}) b->release();
     if (w.pinned) cudaFreeHost(w.pinned);
     if (ctx->kl_err) cudaFree(ctx->kl_err);
     delete ctx;
@@ -664,12 +671,19 @@ mlmc_status mlmc_estimate(mlmc_ctx* ctx, const mlmc_options* opts, mlmc_result* 
                 dofs_lvl[l] += (int64_t)req[i].count * (gc.n - 1) * (gc.n - 1);
             }
         }
+        // the classes share no data: their launches run concurrently (the smaller ones fill the
+        // SMs that the finest level's few large systems leave idle)
+        std::vector<SolveBatch> batches;
         for (auto& kv : classes) {
-            SolveConfig cfg;
-            cfg.prec = kv.first;
-            cfg.solver = o.solver;
-            cfg.max_iters = o.max_iters;
-            const mlmc_status s = run_solve_batch(ctx, kv.second, cfg, st);
+            SolveBatch b;
+            b.groups = kv.second;
+            b.cfg.prec = kv.first;
+            b.cfg.solver = o.solver;
+            b.cfg.max_iters = o.max_iters;
+            batches.push_back(std::move(b));
+        }
+        {
+            const mlmc_status s = run_solve_batches(ctx, batches, st);
             if (s != MLMC_OK) return s;
         }
         // ---- Cor. 3.4 safety net: the low-precision conditions can fail for a sample

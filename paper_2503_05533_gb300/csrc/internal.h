@@ -55,8 +55,10 @@ struct GridBasis {
     DevBuf phi16;          // FP16 [2][nodes_pad][Kpad]: hi rows then lo rows, Phi = hi + lo 2^-11 (K-major)
 };
 
+constexpr int kSolveSlots = 4;   // solve batches that may run concurrently (one per precision class)
+
 struct Workspace {
-    DevBuf solver;         // solver scratch (vectors, partials, descriptors)
+    DevBuf solver_slot[kSolveSlots];   // solver scratch (vectors, descriptors), one per concurrent batch
     DevBuf fields;         // coefficient fields of the estimate loop
     DevBuf xi;             // KL coefficients of the estimate loop
     DevBuf q;              // QoI values of the estimate loop
@@ -99,6 +101,7 @@ struct mlmc_ctx {
     double inner_theta = 0.3;     // inner tolerance tau = clamp(theta delta / rho, tau_min, 0.5)
     double inner_tau_min = -1.0;  // < 0: per-precision default
     mlmc::Profile prof;
+    cudaStream_t aux[mlmc::kSolveSlots - 1] = {};   // streams of concurrent solve batches (created on demand)
 };
 
 namespace mlmc {
@@ -162,6 +165,14 @@ struct SolveStats {
 };
 mlmc_status run_solve_batch(mlmc_ctx* ctx, const std::vector<SolveGroup>& groups, const SolveConfig& cfg,
                             cudaStream_t st);
+// Independent batches (e.g. one per precision class) launched concurrently: the first on st,
+// the others on the context's auxiliary streams after st's prior work; returns once all are
+// done (st synchronised).  At most kSolveSlots batches.
+struct SolveBatch {
+    std::vector<SolveGroup> groups;
+    SolveConfig cfg;
+};
+mlmc_status run_solve_batches(mlmc_ctx* ctx, const std::vector<SolveBatch>& batches, cudaStream_t st);
 cudaError_t launch_apply_operator(int n, int S, const void* a, int a_fp64, int a_n, int op_prec,
                                   const void* x, void* y, int vec_fp64, cudaStream_t st);
 // stats.cu

@@ -1747,9 +1747,25 @@ int grid_of(int nbig, int nmed, int nsmall) {
     return nbig + (nmed + 3) / 4 + (nsmall + CTA / G_SMALL - 1) / (CTA / G_SMALL);
 }
 
+// A launched batch whose completion the host has not yet checked.
+struct PendingSolve {
+    bool active = false;
+    char* base = nullptr;
+    Layout L{};
+    std::vector<DevSolve> solves;
+    SolveConfig cfg;
+    bool mg = false;
+    int mg_nu = 0, mg_coarse = 0;
+    double pv = 0, ps = 0;
+    cudaEvent_t ev[2] = {nullptr, nullptr};
+};
+
+// Plan, upload and launch one batch on stream st using workspace slot `slot`; the host
+// checks it later with finish_solve (after st has been synchronised).
 template <class VT, class ST>
-mlmc_status run_typed(mlmc_ctx* ctx, const std::vector<SolveGroup>& groups, const SolveConfig& cfg,
-                      cudaStream_t st) {
+mlmc_status launch_typed(mlmc_ctx* ctx, const std::vector<SolveGroup>& groups, const SolveConfig& cfg,
+                         cudaStream_t st, int slot, PendingSolve& out) {
+    out = PendingSolve();
     // ---- host plan
     std::vector<DevSolve> solves;
     long long total = 0, ctotal = 0;
@@ -1817,7 +1833,7 @@ mlmc_status run_typed(mlmc_ctx* ctx, const std::vector<SolveGroup>& groups, cons
         nsmall += c == 2;
     }
     const Layout L = make_layout<VT, ST>(total, ns, cfg.jacobi != 0, cfg.solver == MLMC_MINRES, mg, ctotal);
-    mlmc::DevBuf& buf = ctx->ws.solver;
+    mlmc::DevBuf& buf = ctx->ws.solver_slot[slot];
     MLMC_CUDA_RET(ctx->err, buf.reserve(L.total));
     char* base = buf.as<char>();
     // vectors start at zero (boundary and padding entries stay zero forever)
@@ -1853,10 +1869,31 @@ mlmc_status run_typed(mlmc_ctx* ctx, const std::vector<SolveGroup>& groups, cons
     }
     MLMC_CUDA_RET(ctx->err, (launch_resident<VT, ST>(P, cfg.solver, grid_of(nbig, nmed, nsmall), smem, st)));
     if (ctx->prof.on) MLMC_CUDA_RET(ctx->err, cudaEventRecord(ev[1], st));
-    MLMC_CUDA_RET(ctx->err, cudaStreamSynchronize(st));
     ctx->prof.acc.h2d_bytes += (int64_t)((sizeof(DevSolve) + sizeof(int)) * ns);
+    out.active = true;
+    out.base = base;
+    out.L = L;
+    out.solves = std::move(solves);
+    out.cfg = cfg;
+    out.mg = mg;
+    out.mg_nu = P.mg_nu;
+    out.mg_coarse = P.mg_coarse;
+    out.pv = sizeof(VT);
+    out.ps = sizeof(ST);
+    out.ev[0] = ev[0];
+    out.ev[1] = ev[1];
+    return MLMC_OK;
+}
+
+// Error word and profile of a launched batch; its stream must have been synchronised.
+mlmc_status finish_solve(mlmc_ctx* ctx, PendingSolve& ps_) {
+    if (!ps_.active) return MLMC_OK;
+    ps_.active = false;
+    const int ns = (int)ps_.solves.size();
+    const SolveConfig& cfg = ps_.cfg;
+    cudaEvent_t* ev = ps_.ev;
     unsigned kerr = 0;
-    MLMC_CUDA_RET(ctx->err, cudaMemcpy(&kerr, base + L.o_err, sizeof(unsigned), cudaMemcpyDeviceToHost));
+    MLMC_CUDA_RET(ctx->err, cudaMemcpy(&kerr, ps_.base + ps_.L.o_err, sizeof(unsigned), cudaMemcpyDeviceToHost));
     ctx->prof.acc.d2h_bytes += (int64_t)sizeof(unsigned);
     if (kerr != KERR_NONE) {
         if (ev[0]) cudaEventDestroy(ev[0]);
@@ -1865,20 +1902,20 @@ mlmc_status run_typed(mlmc_ctx* ctx, const std::vector<SolveGroup>& groups, cons
                    std::to_string(ctx->wait_timeout_s) + " s; the affected systems carry MLMC_F_TIMEOUT";
         return MLMC_E_TIMEOUT;
     }
-    if (ctx->prof.on) {
+    if (ev[0]) {
         float ms = 0.f;
         cudaEventElapsedTime(&ms, ev[0], ev[1]);
         cudaEventDestroy(ev[0]);
         cudaEventDestroy(ev[1]);
         std::vector<int32_t> stats(2 * ns);
-        MLMC_CUDA_RET(ctx->err, cudaMemcpy(stats.data(), base + L.o_stats, sizeof(int32_t) * 2 * ns,
+        MLMC_CUDA_RET(ctx->err, cudaMemcpy(stats.data(), ps_.base + ps_.L.o_stats, sizeof(int32_t) * 2 * ns,
                                            cudaMemcpyDeviceToHost));
         const int32_t* outer = stats.data() + ns;
-        const double pv = sizeof(VT), ps = sizeof(ST);
+        const double pv = ps_.pv, ps = ps_.ps;
         double bytes = 0.0;
         int64_t iters = 0, uit = 0;
         for (int i = 0; i < ns; ++i) {
-            const DevSolve& d = solves[i];
+            const DevSolve& d = ps_.solves[i];
             const int32_t it = stats[i];
             const double unk = (double)(d.n - 1) * (d.n - 1);
             const double pm = d.a_fp64 ? 8.0 : 4.0;
@@ -1886,9 +1923,10 @@ mlmc_status run_typed(mlmc_ctx* ctx, const std::vector<SolveGroup>& groups, cons
             const int steps = std::min(outer[i], cfg.max_outer);
             const double per_it = cfg.solver == MLMC_MINRES
                                       ? (14 * pv + 2 * ps + pd)
-                                      : mg ? mg_iter_bytes(d.n, d.mg_levels, P.mg_nu, P.mg_coarse, pv, ps) / unk +
-                                                 8 * pv + 2 * ps
-                                           : (8 * pv + 2 * ps + pd);
+                                      : ps_.mg ? mg_iter_bytes(d.n, d.mg_levels, ps_.mg_nu, ps_.mg_coarse, pv, ps) /
+                                                         unk +
+                                                     8 * pv + 2 * ps
+                                               : (8 * pv + 2 * ps + pd);
             bytes += unk * ((double)it * per_it + (double)(steps + 1) * (8 + pm + 2 * pv + pd) +
                             (double)steps * (16 + pv) + (8 + pm + ps + pd));
             iters += it;
@@ -1904,21 +1942,87 @@ mlmc_status run_typed(mlmc_ctx* ctx, const std::vector<SolveGroup>& groups, cons
     return MLMC_OK;
 }
 
-}  // namespace
-
-mlmc_status run_solve_batch(mlmc_ctx* ctx, const std::vector<SolveGroup>& groups, const SolveConfig& cfg,
-                            cudaStream_t st) {
+mlmc_status launch_batch(mlmc_ctx* ctx, const std::vector<SolveGroup>& groups, const SolveConfig& cfg,
+                         cudaStream_t st, int slot, PendingSolve& out) {
     if (cfg.solver != MLMC_CG && cfg.solver != MLMC_MINRES) {
         ctx->err = "unknown solver";
         return MLMC_E_ARG;
     }
     switch (cfg.prec) {
-        case MLMC_FP64: return run_typed<double, double>(ctx, groups, cfg, st);
-        case MLMC_FP32: return run_typed<float, float>(ctx, groups, cfg, st);
-        case MLMC_BF16S: return run_typed<float, __nv_bfloat16>(ctx, groups, cfg, st);
-        case MLMC_FP16S: return run_typed<float, __half>(ctx, groups, cfg, st);
+        case MLMC_FP64: return launch_typed<double, double>(ctx, groups, cfg, st, slot, out);
+        case MLMC_FP32: return launch_typed<float, float>(ctx, groups, cfg, st, slot, out);
+        case MLMC_BF16S: return launch_typed<float, __nv_bfloat16>(ctx, groups, cfg, st, slot, out);
+        case MLMC_FP16S: return launch_typed<float, __half>(ctx, groups, cfg, st, slot, out);
         default: ctx->err = "bad precision"; return MLMC_E_ARG;
     }
+}
+
+}  // namespace
+
+mlmc_status run_solve_batch(mlmc_ctx* ctx, const std::vector<SolveGroup>& groups, const SolveConfig& cfg,
+                            cudaStream_t st) {
+    PendingSolve p;
+    mlmc_status s = launch_batch(ctx, groups, cfg, st, 0, p);
+    if (s != MLMC_OK) return s;
+    MLMC_CUDA_RET(ctx->err, cudaStreamSynchronize(st));
+    return finish_solve(ctx, p);
+}
+
+mlmc_status run_solve_batches(mlmc_ctx* ctx, const std::vector<SolveBatch>& batches, cudaStream_t st) {
+    if (batches.size() <= 1) return batches.empty() ? MLMC_OK : run_solve_batch(ctx, batches[0].groups,
+                                                                                 batches[0].cfg, st);
+    if (batches.size() > (size_t)kSolveSlots) {
+        ctx->err = "run_solve_batches: too many concurrent batches";
+        return MLMC_E_ARG;
+    }
+    // fork: batch 0 on st, batch i > 0 on the context's auxiliary stream i - 1, all after st's prior work
+    cudaEvent_t fork = nullptr;
+    MLMC_CUDA_RET(ctx->err, cudaEventCreateWithFlags(&fork, cudaEventDisableTiming));
+    MLMC_CUDA_RET(ctx->err, cudaEventRecord(fork, st));
+    std::vector<PendingSolve> pend(batches.size());
+    std::vector<cudaEvent_t> done(batches.size(), nullptr);
+    mlmc_status status = MLMC_OK;
+    for (size_t i = 0; i < batches.size() && status == MLMC_OK; ++i) {
+        cudaStream_t si = st;
+        if (i > 0) {
+            if (!ctx->aux[i - 1] && cudaStreamCreateWithFlags(&ctx->aux[i - 1], cudaStreamNonBlocking) != cudaSuccess) {
+                ctx->err = "run_solve_batches: cannot create a stream";
+                status = MLMC_E_CUDA;
+                break;
+            }
+            si = ctx->aux[i - 1];
+            if (cudaStreamWaitEvent(si, fork, 0) != cudaSuccess) {
+                ctx->err = "run_solve_batches: cudaStreamWaitEvent failed";
+                status = MLMC_E_CUDA;
+                break;
+            }
+        }
+        status = launch_batch(ctx, batches[i].groups, batches[i].cfg, si, (int)i, pend[i]);
+        if (status == MLMC_OK && i > 0) {
+            // join: st waits for batch i
+            if (cudaEventCreateWithFlags(&done[i], cudaEventDisableTiming) != cudaSuccess ||
+                cudaEventRecord(done[i], si) != cudaSuccess || cudaStreamWaitEvent(st, done[i], 0) != cudaSuccess) {
+                ctx->err = "run_solve_batches: joining the streams failed";
+                status = MLMC_E_CUDA;
+            }
+        }
+    }
+    // every launched batch is waited for, whatever failed
+    for (size_t i = 1; i < batches.size(); ++i)
+        if (ctx->aux[i - 1]) cudaStreamSynchronize(ctx->aux[i - 1]);
+    const cudaError_t se = cudaStreamSynchronize(st);
+    cudaEventDestroy(fork);
+    for (cudaEvent_t e : done)
+        if (e) cudaEventDestroy(e);
+    if (status == MLMC_OK && se != cudaSuccess) {
+        ctx->err = std::string("run_solve_batches: ") + cudaGetErrorString(se);
+        status = MLMC_E_CUDA;
+    }
+    for (PendingSolve& p : pend) {
+        const mlmc_status f = finish_solve(ctx, p);
+        if (status == MLMC_OK) status = f;
+    }
+    return status;
 }
 
 cudaError_t launch_apply_operator(int n, int S, const void* a, int a_fp64, int a_n, int op_prec, const void* x,
