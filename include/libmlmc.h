@@ -203,7 +203,7 @@ mlmc_status mlmc_level_solve(mlmc_ctx* ctx, int n, int S, const void* a, mlmc_pr
  *           only when qoi == 1)
  *   Q, iters, relres, flags: device outputs as in mlmc_level_solve (iters,
  *           relres, flags may be NULL)
- * Capacity: a batch needs about (8 + 4 p_v + 2 p_s) (n+1)(n+8) bytes per system
+ * Capacity: a batch needs about (24 + 4 p_v + 2 p_s) (n+1)(n+8) bytes per system
  * (p_v, p_s: vector and coefficient storage bytes) plus a few words;
  * a batch beyond MLMC_NOALLOC_SCRATCH_BYTES is rejected with MLMC_E_ARG and a
  * message in mlmc_last_error(NULL), as are the argument errors of
@@ -365,10 +365,12 @@ mlmc_status mlmc_set_wait_timeout(mlmc_ctx* ctx, double seconds);
  * launching stream around every resident solve and tensor-core synthesis
  * launch and, after each solve, derives the launch's algorithmic bytes from
  * the per-system inner-iteration and refinement counts:
- *   per unknown and inner iteration 8 p_v + 2 p_s bytes (p_v vector bytes,
- *   p_s coefficient storage bytes), per unknown and refinement step
- *   (residual + update) 44 + 3 p_v + p_m bytes (p_m master coefficient bytes),
- *   plus 8 + p_m + p_s bytes per unknown for set-up and the QoI.
+ *   per unknown and inner iteration 8 p_v + 2 p_s bytes with Jacobi (plus p_s
+ *   for its inverse diagonal; p_v vector bytes, p_s coefficient storage bytes),
+ *   or that plus the V-cycle's bytes with multigrid; per unknown and
+ *   refinement step (residual from x and the FP64 edge weights, update)
+ *   40 + 3 p_v bytes; plus 24 + p_m + p_s bytes per unknown for set-up and
+ *   the QoI (p_m master coefficient bytes).
  * The synthesis counts its FP32 output (4 bytes per node and sample) plus one
  * read of both split operands, and 3 x 2 S_pad K_pad N_pad executed tensor
  * FLOPs (three MMAs per split product).  Event times are resolved lazily. */

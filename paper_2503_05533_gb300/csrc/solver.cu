@@ -100,6 +100,8 @@ struct Params {
     void* cb;
     void* cas;               // multigrid: coarse-level coefficient and inverse diagonal (storage type)
     void* cdi;
+    double* we;              // FP64 edge weights of the master operator, 6 wE and 6 wN (refinement residual)
+    double* wn;
     unsigned* err;           // error word of the launch (KERR_*)
     unsigned long long timeout_ns;   // bound of every pipeline wait
     unsigned extra_tx;       // diagnostic: bytes a team's first full barrier expects and never receives
@@ -1189,6 +1191,25 @@ __device__ void solve_system(const Params& P, const DevSolve& S, const Group<GT>
         if (need_di && i >= 1 && i <= n - 1 && j >= 1 && j <= n - 1)
             DI[(size_t)j * ld + i] = store_from<ST, VT>(stencil_inv_diag<VT>(S, i, j, 0));
     }
+    // FP64 edge weights of the master operator (6 wE, 6 wN), formed once and reused by every
+    // refinement residual: WE(i,j) = 2 (a(i,j) + a(i+1,j)) + a(i+1,j+1) + a(i,j-1) on the edge
+    // (i,j)-(i+1,j), WN(i,j) = 2 (a(i,j) + a(i,j+1)) + a(i+1,j+1) + a(i-1,j) on (i,j)-(i,j+1).
+    {
+        double* WE = P.we + S.off;
+        double* WN = P.wn + S.off;
+        for (int it = tr; it < (n + 1) * (n + 1); it += GT) {
+            const int j = it / (n + 1), i = it - j * (n + 1);
+            double we = 0.0, wn = 0.0;
+            if (i <= n - 1 && j >= 1 && j <= n - 1)
+                we = 2.0 * (master_a(S, i, j) + master_a(S, i + 1, j)) + master_a(S, i + 1, j + 1) +
+                     master_a(S, i, j - 1);
+            if (j <= n - 1 && i >= 1 && i <= n - 1)
+                wn = 2.0 * (master_a(S, i, j) + master_a(S, i, j + 1)) + master_a(S, i + 1, j + 1) +
+                     master_a(S, i - 1, j);
+            WE[(size_t)j * ld + i] = we;
+            WN[(size_t)j * ld + i] = wn;
+        }
+    }
     if (mg) {
         for (int k = 1; k <= S.mg_levels; ++k) {
             const int nk = n >> k, ldk = row_pitch(nk);
@@ -1224,21 +1245,22 @@ __device__ void solve_system(const Params& P, const DevSolve& S, const Group<GT>
                     r4[q] = (i >= 1 && i <= n - 1) ? rhs_value(S, i, j) : 0.0;
                 }
             } else {
-                double xs[4], xc[6], xn[4];
+                // (A x)_ij = (WE(i,j)(x - x_E) + WE(i-1,j)(x - x_W) + WN(i,j)(x - x_N) + WN(i,j-1)(x - x_S)) / 6
+                const double* WE = P.we + S.off;
+                const double* WN = P.wn + S.off;
+                double xs[4], xc[6], xn[4], we[5], wn[4], ws[4];
                 load_vec_chunk<double>(X, ld, n, j, c, xs, xc, xn);
+                Vec4<double>::load(WE + base, &we[1]);
+                we[0] = c > 0 ? WE[base - 1] : 0.0;
+                Vec4<double>::load(WN + base, wn);
+                Vec4<double>::load(WN + base - ld, ws);
 #pragma unroll
                 for (int q = 0; q < 4; ++q) {
                     const int i = 4 * c + q;
-                    double rq = 0.0;
-                    if (i >= 1 && i <= n - 1) {
-                        const double a00 = master_a(S, i, j), aE = master_a(S, i + 1, j), aW = master_a(S, i - 1, j);
-                        const double aN = master_a(S, i, j + 1), aS = master_a(S, i, j - 1);
-                        const double aNE = master_a(S, i + 1, j + 1), aSW = master_a(S, i - 1, j - 1);
-                        const double ax = stencil_point<double>(a00, aE, aW, aN, aS, aNE, aSW, xc[q + 1], xc[q + 2],
-                                                                xc[q], xn[q], xs[q]);
-                        rq = rhs_value(S, i, j) - ax;
-                    }
-                    r4[q] = rq;
+                    const double x0 = xc[q + 1];
+                    const double ax = (we[q + 1] * (x0 - xc[q + 2]) + we[q] * (x0 - xc[q]) + wn[q] * (x0 - xn[q]) +
+                                       ws[q] * (x0 - xs[q])) * (1.0 / 6.0);
+                    r4[q] = (i >= 1 && i <= n - 1) ? rhs_value(S, i, j) - ax : 0.0;
                 }
             }
 #pragma unroll
@@ -1604,7 +1626,7 @@ double mg_iter_bytes(int n, int nl, int nu, int ncs, double pv, double ps) {
 // Workspace of a batch: vectors, coefficient storage, descriptors, launch order.
 struct Layout {
     size_t o_x, o_r, o_p0, o_p1, o_d, o_as, o_dinv, o_vb, o_w0, o_w1, o_mz, o_mt, o_cx, o_ct, o_cb, o_cas, o_cdi,
-        o_stats, o_err, zero_end, o_solves, o_order, total;
+        o_we, o_wn, o_stats, o_err, zero_end, o_solves, o_order, total;
 };
 
 template <class VT, class ST>
@@ -1629,6 +1651,8 @@ Layout make_layout(long long nodes, int ns, bool jacobi, bool minres, bool mg = 
     L.o_cb = take(mg ? sizeof(VT) * cnodes : 0);
     L.o_cas = take(mg ? sizeof(ST) * cnodes : 0);
     L.o_cdi = take(mg ? sizeof(ST) * cnodes : 0);
+    L.o_we = take(sizeof(double) * nodes);
+    L.o_wn = take(sizeof(double) * nodes);
     L.o_stats = take(sizeof(int32_t) * 2 * ns);
     L.o_err = take(sizeof(unsigned));
     L.zero_end = off;
@@ -1664,6 +1688,8 @@ Params make_params(char* base, const Layout& L, int ns, int nbig, int nmed, int 
     P.cb = base + L.o_cb;
     P.cas = base + L.o_cas;
     P.cdi = base + L.o_cdi;
+    P.we = reinterpret_cast<double*>(base + L.o_we);
+    P.wn = reinterpret_cast<double*>(base + L.o_wn);
     P.mg = 0;
     P.mg_nu = 2;
     P.mg_coarse = 8;
@@ -1927,8 +1953,10 @@ mlmc_status finish_solve(mlmc_ctx* ctx, PendingSolve& ps_) {
                                                          unk +
                                                      8 * pv + 2 * ps
                                                : (8 * pv + 2 * ps + pd);
-            bytes += unk * ((double)it * per_it + (double)(steps + 1) * (8 + pm + 2 * pv + pd) +
-                            (double)steps * (16 + pv) + (8 + pm + ps + pd));
+            // refinement residual: x, the two FP64 edge weights, r and d (and D^-1); set-up: the master
+            // coefficient read for the storage copy and the weights, the copy, D^-1 and the weights written
+            bytes += unk * ((double)it * per_it + (double)(steps + 1) * (8 + 16 + 2 * pv + pd) +
+                            (double)steps * (16 + pv) + (8 + pm + ps + pd + 16));
             iters += it;
             uit += (int64_t)unk * it;
         }
