@@ -207,9 +207,9 @@ def main():
     ap.add_argument("--prec", default="FP32", choices=["FP64", "FP32", "BF16S", "FP16S"],
                     help="sweep: inner precision (FP64 uses an FP64 field and FP64 vectors)")
     ap.add_argument("--pc", default="mg", choices=["mg", "jacobi"],
-                    help="solve-l4 and sweep: preconditioner of the CG inner solves")
-    ap.add_argument("--mg-nu", type=int, default=0, help="solve-l4 and sweep: smoothing sweeps (0: default)")
-    ap.add_argument("--mg-coarse", type=int, default=0, help="solve-l4 and sweep: coarsest-grid sweeps (0: default)")
+                    help="preconditioner of the CG inner solves")
+    ap.add_argument("--mg-nu", type=int, default=0, help="multigrid smoothing sweeps (0: default)")
+    ap.add_argument("--mg-coarse", type=int, default=0, help="multigrid coarsest-grid sweeps (0: default)")
     ap.add_argument("--tau-min", type=float, default=0.0,
                     help="solve-l4 and sweep: floor of the inner tolerance (0: per-precision default)")
     ap.add_argument("--ring", type=int, default=-1,
@@ -262,6 +262,9 @@ def main():
     def timed_runs(form, steps, warmup, seed0, profile=False):
         h = M.mlmc_create(problem(seed0), local)
         try:
+            if args.mg_nu or args.mg_coarse or args.pc != "mg":
+                M.mlmc_set_precond(h, M.MLMC_PC_MG if args.pc == "mg" else M.MLMC_PC_JACOBI, args.mg_nu,
+                                   args.mg_coarse)
             if profile:
                 M.mlmc_profile_enable(h, True)
             for w in range(warmup):

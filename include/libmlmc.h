@@ -342,7 +342,7 @@ mlmc_status mlmc_adjoint_grad(mlmc_ctx* ctx, int level, int S, const double* xi,
  *    coarse correction; coarse_sweeps Jacobi sweeps on the coarsest grid.  The
  *    V-cycle is a fixed symmetric linear map, so CG stays CG.
  * nu in {1, 2}, coarse_sweeps even and >= 2, 0 < omega < 1; 0 keeps the current
- * value (defaults nu = 2, coarse_sweeps = 8, omega = 0.8).  Stopping is still
+ * value (defaults nu = 1, coarse_sweeps = 8, omega = 0.8).  Stopping is still
  * on the FP64 residual of the refinement (Alg. 2.1). */
 mlmc_status mlmc_set_precond(mlmc_ctx* ctx, mlmc_precond pc, int nu, int coarse_sweeps, double omega);
 

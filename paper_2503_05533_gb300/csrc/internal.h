@@ -95,7 +95,7 @@ struct mlmc_ctx {
     int wait_extra = 0;           // diagnostic: bytes every tensor-core wait expects and never receives
     int solve_ring = -1;          // diagnostic: row-pipeline slots of large CG solves (-1 automatic, 0 off)
     int precond = MLMC_PC_MG;     // preconditioner of the CG inner solves
-    int mg_nu = 2;                // multigrid: smoothing sweeps before and after the coarse correction
+    int mg_nu = 1;                // multigrid: smoothing sweeps before and after the coarse correction
     int mg_coarse = 8;            // multigrid: Jacobi sweeps on the coarsest grid
     double mg_omega = 0.8;        // multigrid: Jacobi damping
     double inner_theta = 0.3;     // inner tolerance tau = clamp(theta delta / rho, tau_min, 0.5)

@@ -1691,7 +1691,7 @@ Params make_params(char* base, const Layout& L, int ns, int nbig, int nmed, int 
     P.we = reinterpret_cast<double*>(base + L.o_we);
     P.wn = reinterpret_cast<double*>(base + L.o_wn);
     P.mg = 0;
-    P.mg_nu = 2;
+    P.mg_nu = 1;
     P.mg_coarse = 8;
     P.mg_omega = 0.8;
     P.solver = solver;

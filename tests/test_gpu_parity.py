@@ -469,7 +469,7 @@ def _solve_pc(M, h, n, af, a_prec, prec, delta, pc, nu=0, coarse=0, omega=0.0):
     try:
         return _solve(M, h, n, af, a_prec, n, prec, delta)
     finally:
-        M.mlmc_set_precond(h, M.MLMC_PC_MG, 2, 8, 0.8)
+        M.mlmc_set_precond(h, M.MLMC_PC_MG, 1, 8, 0.8)
 
 
 @pytest.mark.parametrize("prec", ["FP64", "FP32", "FP16S"])
