@@ -127,8 +127,12 @@ def _oracle_level_job(args):
 
 
 def oracle_throughput(per_level, procs):
-    """Samples/s per level of the oracle with `procs` worker processes (spawn)."""
+    """Samples/s per level of the oracle with `procs` worker processes (spawn), one thread each."""
     import multiprocessing as mp
+    # one BLAS/OpenMP thread per worker: `procs` workers use `procs` cores (the children read this
+    # environment when they import numpy)
+    for var in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS", "BLIS_NUM_THREADS"):
+        os.environ[var] = "1"
     ctx = mp.get_context("spawn")
     out = {}
     with ctx.Pool(procs) as pool:
