@@ -199,7 +199,8 @@ def main():
     ap.add_argument("--impl", default="libmlmc", choices=["libmlmc", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-fp64", action="store_true")
-    ap.add_argument("--case", default="mlmc", choices=["mlmc", "mlmc7", "solve-l4", "kl-synth", "sweep", "adjoint"],
+    ap.add_argument("--case", default="mlmc",
+                    choices=["mlmc", "mlmc7", "paper", "solve-l4", "kl-synth", "sweep", "adjoint"],
                     help="solve-l4: only the finest level's batch (100 samples, n = 256) of the workload: "
                          "field synthesis and one resident-solve launch per step; kl-synth: tensor-core "
                          "KL synthesis alone at the single-level sweep shapes (n = 512, K = 128, corr 0.1)")
@@ -262,6 +263,8 @@ def main():
         return sweep_case(M, torch, dev, args, hbm_peak, peak_src, flush, stream)
     if args.case == "adjoint":
         return adjoint_case(M, torch, dev, args, hbm_peak, peak_src, flush, stream)
+    if args.case == "paper":
+        return paper_case(M, torch, dev, args, flush, stream)
 
     def timed_runs(form, steps, warmup, seed0, profile=False):
         h = M.mlmc_create(problem(seed0), local)
@@ -443,6 +446,52 @@ def solve_l4_case(M, torch, dev, args, prob, hbm_peak, peak_src, flush, stream):
                       "algorithmic_bytes_per_launch": prof["solve_bytes"] / prof["solve_launches"],
                       "achieved_gbs": achieved, "peak_gbs": hbm_peak, "frac": achieved / hbm_peak,
                       "peak_source": peak_src}))
+    return 0
+
+
+def paper_case(M, torch, dev, args, flush, stream):
+    """The paper's own setting (Sec. 5.1): f = 1, the field of Eq. (5.2) with s = 4 terms, q = 2,
+    sigma = 2, h_0 = 1/8, m = 2, Q = int u, Alg. 4.1 with adaptive L (at most 6 levels), MINRES as the
+    paper uses it.  Forms: the adaptive-accuracy mixed-precision method (MPML), FP64 with the
+    adaptive delta_l, and FP64 at the fixed tolerances 1e-6 and 1e-10 of the paper's comparison.
+    Reports time to RMSE, inner iterations and the unknowns x iterations per form, at two TOLs."""
+    prob = M.make_problem(n0=8, m=2, L_max=5, kind=1, K=4, sigma2=4.0, q=2.0, corr_len=0.3, seed=2025)
+    forms = [("mpml_mixed", M.MLMC_FORM_MIXED, 0.0), ("fp64_adaptive", M.MLMC_FORM_FP64_ADAPTIVE, 0.0),
+             ("fp64_fixed_1e-6", M.MLMC_FORM_FP64_FIXED, 1e-6), ("fp64_fixed_1e-10", M.MLMC_FORM_FP64_FIXED, 1e-10)]
+    out = {"case": "paper", "solver": "MINRES (Jacobi)", "results": {}}
+    for tol in (2e-3, 1e-3):
+        per = {}
+        for name, form, fd in forms:
+            h = M.mlmc_create(prob, dev.index or 0)
+            try:
+                M.mlmc_profile_enable(h, True)
+                o = M.mlmc_default_options()
+                o.tol, o.form, o.solver = tol, form, M.MLMC_MINRES
+                if fd > 0:
+                    o.fixed_delta = fd
+                ms = []
+                for s in range(args.warmup + args.steps):
+                    if s == args.warmup:
+                        M.mlmc_profile_reset(h)
+                    flush.fill_(float(s))
+                    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                    e0.record(stream)
+                    r = M.result_dict(M.mlmc_estimate(h, o))
+                    e1.record(stream)
+                    e1.synchronize()
+                    if s >= args.warmup:
+                        ms.append(e0.elapsed_time(e1))
+                prof = M.mlmc_profile_get(h)
+            finally:
+                M.mlmc_destroy(h)
+            per[name] = {"seconds": sum(ms) / len(ms) / 1e3, "estimate": r["estimate"], "rmse": r["rmse"],
+                         "L": r["L"], "N_l": r["N"], "prec_l": r["prec"],
+                         "unknown_iters": prof["unknown_iters"] / max(1, args.steps)}
+        base = per["fp64_fixed_1e-6"]
+        for name in per:
+            per[name]["time_vs_fp64_fixed_1e-6"] = base["seconds"] / per[name]["seconds"]
+        out["results"]["tol=%g" % tol] = per
+    print(json.dumps(out))
     return 0
 
 

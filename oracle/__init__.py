@@ -23,6 +23,9 @@ and Other Sampling Methods") that it follows:
                   accuracy rule (Eqs. (4.7), (4.12)), adaptive MPML
                   (Algorithm 4.1), cost model (Sec. 4.2, Cor. 4.4).
 * ``adjoint``  -- dQ/domega by the discrete adjoint of the P1 system.
-* ``ir``       -- iterative refinement (Algorithm 2.1) with a CG correction
-                  solve, used to check the refinement loop's behaviour.
+
+The refinement of Algorithm 2.1 has no separate oracle: its result is the
+solution of the P1 system, which ``fem`` computes directly, and every GPU
+solve is checked through the FP64 residual of its returned solution against
+``fem``'s own assembly.
 """
