@@ -200,7 +200,7 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-fp64", action="store_true")
     ap.add_argument("--case", default="mlmc",
-                    choices=["mlmc", "mlmc7", "paper", "solve-l4", "kl-synth", "sweep", "adjoint"],
+                    choices=["mlmc", "mlmc7", "paper", "fixed3", "solve-l4", "kl-synth", "sweep", "adjoint"],
                     help="solve-l4: only the finest level's batch (100 samples, n = 256) of the workload: "
                          "field synthesis and one resident-solve launch per step; kl-synth: tensor-core "
                          "KL synthesis alone at the single-level sweep shapes (n = 512, K = 128, corr 0.1)")
@@ -265,6 +265,8 @@ def main():
         return adjoint_case(M, torch, dev, args, hbm_peak, peak_src, flush, stream)
     if args.case == "paper":
         return paper_case(M, torch, dev, args, flush, stream)
+    if args.case == "fixed3":
+        return fixed3_case(M, torch, dev, args, flush, stream)
 
     def timed_runs(form, steps, warmup, seed0, profile=False):
         h = M.mlmc_create(problem(seed0), local)
@@ -446,6 +448,35 @@ def solve_l4_case(M, torch, dev, args, prob, hbm_peak, peak_src, flush, stream):
                       "algorithmic_bytes_per_launch": prof["solve_bytes"] / prof["solve_launches"],
                       "achieved_gbs": achieved, "peak_gbs": hbm_peak, "frac": achieved / hbm_peak,
                       "peak_source": peak_src}))
+    return 0
+
+
+def fixed3_case(M, torch, dev, args, flush, stream):
+    """Fixed-sample FP64 MLMC on 3 levels (h = 1/8, 1/16, 1/32), K = 16, sigma^2 = 1, corr 0.3,
+    N_l = 1000 / 500 / 250 solved to a relative residual of 1e-10: the small parity configuration,
+    timed."""
+    import ctypes
+    prob = M.make_problem(n0=8, m=2, L_max=2, kind=0, K=16, sigma2=1.0, corr_len=0.3, seed=0)
+    N = (ctypes.c_int64 * 3)(1000, 500, 250)
+    h = M.mlmc_create(prob, dev.index or 0)
+    try:
+        o = M.mlmc_default_options()
+        o.form, o.fixed_delta, o.L_start = M.MLMC_FORM_FP64_FIXED, 1e-10, 2
+        o.fixed_N = ctypes.cast(N, ctypes.POINTER(ctypes.c_int64))
+        ms = []
+        for s in range(args.warmup + args.steps):
+            flush.fill_(float(s))
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            r = M.result_dict(M.mlmc_estimate(h, o))
+            e1.record(stream)
+            e1.synchronize()
+            if s >= args.warmup:
+                ms.append(e0.elapsed_time(e1))
+    finally:
+        M.mlmc_destroy(h)
+    print(json.dumps({"case": "fixed3", "seconds": sum(ms) / len(ms) / 1e3, "N_l": r["N"],
+                      "estimate": r["estimate"], "rmse": r["rmse"], "inner_iters": r["inner_iters"]}))
     return 0
 
 

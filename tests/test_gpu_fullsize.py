@@ -70,9 +70,15 @@ def test_sweep_4096_systems_n512(M, prec):
         _, Q, it, rr, fl = _solve(M, h, n, a, M.MLMC_FP32, p, delta)
         assert np.all(fl == M.MLMC_F_CONVERGED), np.unique(fl)
         assert np.all(rr < delta) and np.all(np.isfinite(Q)) and np.all(Q > 0) and np.all(it > 0)
-        # the inputs are the method's own draws
+        # the inputs are the method's own draws, and the tensor-core field matches the FP64 field
         pick = [0, 2047, 4095]
-        assert np.array_equal(xi[pick].cpu().numpy(), o_rng.draw_xi(11, 0, 0, S, K)[pick])
+        xi_o = o_rng.draw_xi(11, 0, 0, S, K)[pick]
+        assert np.array_equal(xi[pick].cpu().numpy(), xi_o)
+        phi = o_kl.basis(0, K, n, 1.0, 0.1)
+        loga = o_kl.log_coefficient(xi_o, phi)
+        scale = np.abs(xi_o) @ np.abs(phi)
+        got = a[pick].cpu().numpy().astype(np.float64)
+        assert np.all(np.abs(np.log(got) - loga) <= 2e-6 * np.maximum(scale, 1.0))
         # sampled systems again, alone and with the solution: a system's result does not
         # depend on the batch it is solved in
         sub = a[pick].contiguous()
