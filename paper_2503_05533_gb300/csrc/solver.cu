@@ -33,6 +33,7 @@
 #include <cmath>
 #include <cstring>
 #include <mutex>
+#include <type_traits>
 #include <vector>
 
 #include "device_common.cuh"
@@ -500,6 +501,105 @@ __device__ __forceinline__ void sweep_upd(const VT* PK, VT* R, VT* D, const ST* 
 
 
 // ---------------------------------------------------------------------------
+// Stencil from the stored FP64 edge weights (the FP64 inner solve, whose storage
+// type is FP64 too): (A x)_ij = (WE(i,j)(x - x_E) + WE(i-1,j)(x - x_W)
+//   + WN(i,j)(x - x_N) + WN(i,j-1)(x - x_S)) / 6, about 9 FP64 operations per
+// node instead of about 21 for rebuilding the weights from the nodal coefficient.
+__device__ __forceinline__ void we_row(const double* WE, int ld, int j, int c, double w[5]) {
+    const double* row = WE + (size_t)j * ld + 4 * c;
+    Vec4<double>::load(row, &w[1]);
+    w[0] = c > 0 ? row[-1] : 0.0;
+}
+__device__ __forceinline__ void wn_row(const double* WN, int ld, int j, int c, double w[4]) {
+    Vec4<double>::load(WN + (size_t)j * ld + 4 * c, w);
+}
+template <class VT>
+__device__ __forceinline__ void apply_rows_w(const double we[5], const double ws[4], const double wn[4], const VT* s,
+                                             const VT* cc, const VT* nn, int n, int c, VT y[4]) {
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+        const int i = 4 * c + q;
+        const VT x0 = cc[q + 1];
+        const VT v = (we[q + 1] * (x0 - cc[q + 2]) + we[q] * (x0 - cc[q]) + wn[q] * (x0 - nn[q]) + ws[q] * (x0 - s[q])) *
+                     (VT)(1.0 / 6.0);
+        y[q] = (i >= 1 && i <= n - 1) ? v : (VT)0;
+    }
+}
+
+// I1 sweep with stored weights (same recurrences as sweep_dir).
+template <class VT, class ST, bool JAC, bool PREV>
+__device__ __forceinline__ VT sweep_dir_w(const VT* R, const ST* DI, const VT* PO, VT* PN, const double* WE,
+                                          const double* WN, VT beta, int ld, int n, int c, int ja, int jb) {
+    VT pm[6], p0[6], pp[6];
+    double ws[4], we[5], wn[4];
+    dir_row<VT, ST, JAC, PREV>(R, DI, PO, beta, ld, n, ja - 1, c, pm);
+    dir_row<VT, ST, JAC, PREV>(R, DI, PO, beta, ld, n, ja, c, p0);
+    wn_row(WN, ld, ja - 1, c, ws);
+    VT acc = 0;
+    for (int j = ja; j < jb; ++j) {
+        dir_row<VT, ST, JAC, PREV>(R, DI, PO, beta, ld, n, j + 1, c, pp);
+        we_row(WE, ld, j, c, we);
+        wn_row(WN, ld, j, c, wn);
+        VT y[4];
+        apply_rows_w<VT>(we, ws, wn, &pm[1], p0, &pp[1], n, c, y);
+        Vec4<VT>::store(PN + (size_t)j * ld + 4 * c, &p0[1]);
+#pragma unroll
+        for (int q = 0; q < 4; ++q) acc += p0[q + 1] * y[q];
+#pragma unroll
+        for (int q = 0; q < 6; ++q) {
+            pm[q] = p0[q];
+            p0[q] = pp[q];
+        }
+#pragma unroll
+        for (int q = 0; q < 4; ++q) ws[q] = wn[q];
+    }
+    return acc;
+}
+
+// I2 sweep with stored weights (same recurrences as sweep_upd).
+template <class VT, class ST, bool JAC>
+__device__ __forceinline__ void sweep_upd_w(const VT* PK, VT* R, VT* D, const ST* DI, const double* WE,
+                                            const double* WN, VT alpha, int ld, int n, int c, int ja, int jb, VT& rr,
+                                            VT& rz) {
+    VT pm[6], p0[6], pp[6];
+    double ws[4], we[5], wn[4];
+    vec_row<VT>(PK, ld, n, ja - 1, c, pm);
+    vec_row<VT>(PK, ld, n, ja, c, p0);
+    wn_row(WN, ld, ja - 1, c, ws);
+    VT acc_r = 0, acc_z = 0;
+    for (int j = ja; j < jb; ++j) {
+        vec_row<VT>(PK, ld, n, j + 1, c, pp);
+        we_row(WE, ld, j, c, we);
+        wn_row(WN, ld, j, c, wn);
+        const size_t base = (size_t)j * ld + 4 * c;
+        VT dv[4], rv[4], zz[4];
+        Vec4<VT>::load(D + base, dv);
+        Vec4<VT>::load(R + base, rv);
+        if (JAC) CoefLoad<ST, VT>::load4(DI + base, zz);
+        VT y[4];
+        apply_rows_w<VT>(we, ws, wn, &pm[1], p0, &pp[1], n, c, y);
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+            dv[q] = dv[q] + alpha * p0[q + 1];
+            rv[q] = rv[q] - alpha * y[q];
+            acc_r += rv[q] * rv[q];
+            acc_z += JAC ? rv[q] * (rv[q] * zz[q]) : rv[q] * rv[q];
+        }
+        Vec4<VT>::store(D + base, dv);
+        Vec4<VT>::store(R + base, rv);
+#pragma unroll
+        for (int q = 0; q < 6; ++q) {
+            pm[q] = p0[q];
+            p0[q] = pp[q];
+        }
+#pragma unroll
+        for (int q = 0; q < 4; ++q) ws[q] = wn[q];
+    }
+    rr = acc_r;
+    rz = acc_z;
+}
+
+// ---------------------------------------------------------------------------
 // Row pipeline of the 512-thread CG groups.  The row segments of a system are
 // teams of cpr threads.  A team streams the rows its sweep needs through a ring
 // of shared-memory slots: its first thread issues bulk asynchronous copies of
@@ -908,6 +1008,8 @@ struct MGLevel {
     VT* b;          // right-hand side (level 0: r, read only)
     const ST* a;    // coefficient in the storage type
     const ST* di;   // inverse diagonal in the storage type (zero off the interior)
+    const double* we;   // FP64 inner solve, grid level: stored edge weights (else nullptr)
+    const double* wn;
 };
 
 template <class VT, class ST>
@@ -922,7 +1024,13 @@ __device__ __forceinline__ MGLevel<VT, ST> mg_level(const Params& P, const DevSo
         L.b = const_cast<VT*>(R);
         L.a = AS;
         L.di = DI;
+        // the FP64 inner solve applies its grid operator from the stored FP64 edge weights
+        const bool w64 = sizeof(VT) == 8 && sizeof(ST) == 8;
+        L.we = w64 ? P.we + S.off : nullptr;
+        L.wn = w64 ? P.wn + S.off : nullptr;
     } else {
+        L.we = nullptr;
+        L.wn = nullptr;
         L.n = S.n >> k;
         L.ld = row_pitch(L.n);
         const long long off = S.mg_off + mg_coarse_nodes(S.n, k - 1);
@@ -943,27 +1051,49 @@ template <class VT>
 struct MGChunk {
     VT b4[4], d4[4], a3[3][6], xs[4], xc[6], xn[4];
 };
+// Stored-weight form (FP64 inner solve, grid level): the edge weights replace the coefficient.
+template <class VT>
+struct MGChunkW {
+    VT b4[4], d4[4], xs[4], xc[6], xn[4];
+    double we[5], ws[4], wn[4];
+};
+template <class VT, bool W> using MGChunkT = typename std::conditional<W, MGChunkW<VT>, MGChunk<VT>>::type;
 
-template <class VT, class ST, bool IN, bool DI>
-__device__ __forceinline__ void mg_load(const MGLevel<VT, ST>& L, const VT* in, int it, MGChunk<VT>& C) {
+template <class VT, class ST, bool IN, bool DI, bool W = false>
+__device__ __forceinline__ void mg_load(const MGLevel<VT, ST>& L, const VT* in, int it, MGChunkT<VT, W>& C) {
     const int j = 1 + it / L.cpr, c = it - (j - 1) * L.cpr;
     const size_t base = (size_t)j * L.ld + 4 * c;
     Vec4<VT>::load(L.b + base, C.b4);
     if (DI) CoefLoad<ST, VT>::load4(L.di + base, C.d4);
     if (IN) {
-        load_coef_chunk<ST, VT>(L.a, L.ld, L.n, j, c, C.a3);
+        if constexpr (W) {
+            we_row(L.we, L.ld, j, c, C.we);
+            wn_row(L.wn, L.ld, j - 1, c, C.ws);
+            wn_row(L.wn, L.ld, j, c, C.wn);
+        } else {
+            load_coef_chunk<ST, VT>(L.a, L.ld, L.n, j, c, C.a3);
+        }
         load_vec_chunk<VT>(in, L.ld, L.n, j, c, C.xs, C.xc, C.xn);
     }
 }
 
+template <class VT>
+__device__ __forceinline__ void mg_apply(const MGChunk<VT>& C, int n, int c, VT y[4]) {
+    apply_chunk<VT>(C.a3, C.xs, C.xc, C.xn, n, c, y);
+}
+template <class VT>
+__device__ __forceinline__ void mg_apply(const MGChunkW<VT>& C, int n, int c, VT y[4]) {
+    apply_rows_w<VT>(C.we, C.ws, C.wn, C.xs, C.xc, C.xn, n, c, y);
+}
+
 // Smoothing step on one loaded chunk: out = in + w D^-1 (b - A in); returns (b, out) when RZ.
-template <class VT, class ST, bool IN, bool RZ>
-__device__ __forceinline__ VT mg_smooth_store(const MGLevel<VT, ST>& L, VT* out, int it, const MGChunk<VT>& C,
+template <class VT, class ST, bool IN, bool RZ, bool W = false>
+__device__ __forceinline__ VT mg_smooth_store(const MGLevel<VT, ST>& L, VT* out, int it, const MGChunkT<VT, W>& C,
                                               VT w) {
     const int j = 1 + it / L.cpr, c = it - (j - 1) * L.cpr;
     VT y[4] = {(VT)0, (VT)0, (VT)0, (VT)0}, x4[4] = {(VT)0, (VT)0, (VT)0, (VT)0};
     if (IN) {
-        apply_chunk<VT>(C.a3, C.xs, C.xc, C.xn, L.n, c, y);
+        mg_apply<VT>(C, L.n, c, y);
 #pragma unroll
         for (int q = 0; q < 4; ++q) x4[q] = C.xc[q + 1];
     }
@@ -980,10 +1110,33 @@ __device__ __forceinline__ VT mg_smooth_store(const MGLevel<VT, ST>& L, VT* out,
 
 // out = in + w D^-1 (b - A in) (in == nullptr: out = w D^-1 b); returns this
 // thread's part of (b, out) when RZ.
+template <class VT, class ST, int GT, bool RZ, bool W>
+__device__ __forceinline__ VT mg_smooth_in(const Group<GT>& G, const MGLevel<VT, ST>& L, const VT* in, VT* out,
+                                           VT w, int items) {
+    VT acc = 0;
+    for (int it0 = G.rank; it0 < items; it0 += 2 * GT) {
+        const bool two = it0 + GT < items;
+        const int it1 = two ? it0 + GT : it0;     // a second valid chunk, or a repeat that is not stored
+        MGChunkT<VT, W> c0, c1;
+        mg_load<VT, ST, true, true, W>(L, in, it0, c0);
+        mg_load<VT, ST, true, true, W>(L, in, it1, c1);
+        acc += mg_smooth_store<VT, ST, true, RZ, W>(L, out, it0, c0, w);
+        if (two) acc += mg_smooth_store<VT, ST, true, RZ, W>(L, out, it1, c1, w);
+    }
+    return acc;
+}
+
 template <class VT, class ST, int GT, bool RZ>
 __device__ __forceinline__ VT mg_smooth(const Group<GT>& G, const MGLevel<VT, ST>& L, const VT* in, VT* out, VT w) {
     const int items = (L.n - 1) * L.cpr;
     VT acc = 0;
+    if constexpr (sizeof(VT) == 8 && sizeof(ST) == 8) {
+        if (in && L.we) {
+            acc = mg_smooth_in<VT, ST, GT, RZ, true>(G, L, in, out, w, items);
+            G.sync();
+            return acc;
+        }
+    }
     for (int it0 = G.rank; it0 < items; it0 += 2 * GT) {
         const bool two = it0 + GT < items;
         const int it1 = two ? it0 + GT : it0;     // a second valid chunk, or a repeat that is not stored
@@ -1005,13 +1158,13 @@ __device__ __forceinline__ VT mg_smooth(const Group<GT>& G, const MGLevel<VT, ST
 }
 
 // t = b - A x on level L.
-template <class VT, class ST, int GT>
-__device__ __forceinline__ void mg_residual(const Group<GT>& G, const MGLevel<VT, ST>& L) {
+template <class VT, class ST, int GT, bool W>
+__device__ __forceinline__ void mg_residual_pass(const Group<GT>& G, const MGLevel<VT, ST>& L) {
     const int items = (L.n - 1) * L.cpr;
-    auto finish = [&](int it, const MGChunk<VT>& C) {
+    auto finish = [&](int it, const MGChunkT<VT, W>& C) {
         const int j = 1 + it / L.cpr, c = it - (j - 1) * L.cpr;
         VT y[4], r4[4];
-        apply_chunk<VT>(C.a3, C.xs, C.xc, C.xn, L.n, c, y);
+        mg_apply<VT>(C, L.n, c, y);
 #pragma unroll
         for (int q = 0; q < 4; ++q) r4[q] = C.b4[q] - y[q];
         Vec4<VT>::store(L.t + (size_t)j * L.ld + 4 * c, r4);
@@ -1019,11 +1172,21 @@ __device__ __forceinline__ void mg_residual(const Group<GT>& G, const MGLevel<VT
     for (int it0 = G.rank; it0 < items; it0 += 2 * GT) {
         const bool two = it0 + GT < items;
         const int it1 = two ? it0 + GT : it0;
-        MGChunk<VT> c0, c1;
-        mg_load<VT, ST, true, false>(L, L.x, it0, c0);
-        mg_load<VT, ST, true, false>(L, L.x, it1, c1);
+        MGChunkT<VT, W> c0, c1;
+        mg_load<VT, ST, true, false, W>(L, L.x, it0, c0);
+        mg_load<VT, ST, true, false, W>(L, L.x, it1, c1);
         finish(it0, c0);
         if (two) finish(it1, c1);
+    }
+}
+
+template <class VT, class ST, int GT>
+__device__ __forceinline__ void mg_residual(const Group<GT>& G, const MGLevel<VT, ST>& L) {
+    if constexpr (sizeof(VT) == 8 && sizeof(ST) == 8) {
+        if (L.we) mg_residual_pass<VT, ST, GT, true>(G, L);
+        else mg_residual_pass<VT, ST, GT, false>(G, L);
+    } else {
+        mg_residual_pass<VT, ST, GT, false>(G, L);
     }
     G.sync();
 }
@@ -1168,6 +1331,8 @@ __device__ void solve_system(const Params& P, const DevSolve& S, const Group<GT>
     ST* DI = static_cast<ST*>(P.dinv) + S.off;
     const bool jac = P.jacobi != 0;
     constexpr bool minres = SOLVER == MLMC_MINRES;
+    // the FP64 inner solve applies its grid operator from the stored FP64 edge weights
+    constexpr bool W64 = sizeof(VT) == 8 && sizeof(ST) == 8;
     const bool pipe_on = pipe != nullptr;
     VT* VB = minres ? static_cast<VT*>(P.vb) + S.off : nullptr;
     VT* W0 = minres ? static_cast<VT*>(P.w0) + S.off : nullptr;
@@ -1395,6 +1560,19 @@ __device__ void solve_system(const Params& P, const DevSolve& S, const Group<GT>
                                                                                   beta, ld, n, sc, ja, jb)
                                           : sweep_dir_staged<VT, ST, false, false>(*pipe, zsrc, DI, pold, pnew, AS,
                                                                                    beta, ld, n, sc, ja, jb);
+                    } else if constexpr (W64) {
+                        const double* WE = P.we + S.off;
+                        const double* WN = P.wn + S.off;
+                        if (dj)
+                            sig = (k > 0) ? sweep_dir_w<VT, ST, true, true>(zsrc, DI, pold, pnew, WE, WN, beta, ld, n,
+                                                                            sc, ja, jb)
+                                          : sweep_dir_w<VT, ST, true, false>(zsrc, DI, pold, pnew, WE, WN, beta, ld,
+                                                                             n, sc, ja, jb);
+                        else
+                            sig = (k > 0) ? sweep_dir_w<VT, ST, false, true>(zsrc, DI, pold, pnew, WE, WN, beta, ld,
+                                                                             n, sc, ja, jb)
+                                          : sweep_dir_w<VT, ST, false, false>(zsrc, DI, pold, pnew, WE, WN, beta, ld,
+                                                                              n, sc, ja, jb);
                     } else {
                         if (dj)
                             sig = (k > 0) ? sweep_dir<VT, ST, true, true>(zsrc, DI, pold, pnew, AS, beta, ld, n, sc,
@@ -1421,6 +1599,13 @@ __device__ void solve_system(const Params& P, const DevSolve& S, const Group<GT>
                         else
                             sweep_upd_staged<VT, ST, false>(*pipe, pnew, R, D, DI, AS, alpha, ld, n, sc, ja, jb, nrr,
                                                             nrz);
+                    } else if constexpr (W64) {
+                        const double* WE = P.we + S.off;
+                        const double* WN = P.wn + S.off;
+                        if (dj)
+                            sweep_upd_w<VT, ST, true>(pnew, R, D, DI, WE, WN, alpha, ld, n, sc, ja, jb, nrr, nrz);
+                        else
+                            sweep_upd_w<VT, ST, false>(pnew, R, D, DI, WE, WN, alpha, ld, n, sc, ja, jb, nrr, nrz);
                     } else {
                         if (dj)
                             sweep_upd<VT, ST, true>(pnew, R, D, DI, AS, alpha, ld, n, sc, ja, jb, nrr, nrz);
@@ -1732,6 +1917,9 @@ template <class VT, class ST>
 int choose_ring(const std::vector<int>& big_n, size_t& smem, int max_ring, int num_sms) {
     smem = 0;
     if (big_n.empty() || max_ring == 0) return 0;
+    // The FP64 inner solve streams stored FP64 edge weights, not the coefficient rows the
+    // pipeline carries; it runs on plain loads.
+    if (sizeof(VT) == 8) return 0;
     // Automatic: the pipeline pays when the largest systems -- the launch's
     // critical path -- occupy every SM (DRAM latency under full load is what it
     // hides; on a partly filled GPU the L1-cached plain loads keep up and cost
