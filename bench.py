@@ -482,14 +482,14 @@ def fixed3_case(M, torch, dev, args, flush, stream):
 
 def paper_case(M, torch, dev, args, flush, stream):
     """The paper's own setting (Sec. 5.1): f = 1, the field of Eq. (5.2) with s = 4 terms, q = 2,
-    sigma = 2, h_0 = 1/8, m = 2, Q = int u, Alg. 4.1 with adaptive L (at most 6 levels), MINRES as the
-    paper uses it.  Forms: the adaptive-accuracy mixed-precision method (MPML), FP64 with the
+    sigma = 2, h_0 = 1/8, m = 2, Q = int u, Alg. 4.1 with adaptive L (at most 6 levels), MINRES (the
+    paper's solver) preconditioned by the multigrid V-cycle.  Forms: the adaptive-accuracy mixed-precision method (MPML), FP64 with the
     adaptive delta_l, and FP64 at the fixed tolerances 1e-6 and 1e-10 of the paper's comparison.
     Reports time to RMSE, inner iterations and the unknowns x iterations per form, at two TOLs."""
     prob = M.make_problem(n0=8, m=2, L_max=5, kind=1, K=4, sigma2=4.0, q=2.0, corr_len=0.3, seed=2025)
     forms = [("mpml_mixed", M.MLMC_FORM_MIXED, 0.0), ("fp64_adaptive", M.MLMC_FORM_FP64_ADAPTIVE, 0.0),
              ("fp64_fixed_1e-6", M.MLMC_FORM_FP64_FIXED, 1e-6), ("fp64_fixed_1e-10", M.MLMC_FORM_FP64_FIXED, 1e-10)]
-    out = {"case": "paper", "solver": "MINRES (Jacobi)", "results": {}}
+    out = {"case": "paper", "solver": "MINRES preconditioned by the multigrid V-cycle", "results": {}}
     for tol in (2e-3, 1e-3):
         per = {}
         for name, form, fd in forms:

@@ -60,7 +60,7 @@ typedef enum {
 } mlmc_prec;
 
 typedef enum { MLMC_CG = 0, MLMC_MINRES = 1 } mlmc_solver;
-/* Preconditioner of the CG inner solves (MINRES always uses Jacobi). */
+/* Preconditioner of the inner solves (CG and MINRES). */
 typedef enum { MLMC_PC_JACOBI = 0, MLMC_PC_MG = 1 } mlmc_precond;   /* Sec. 2.2 */
 
 /* per-solve flag bits (int32 arrays returned by the solves) */
@@ -330,7 +330,7 @@ mlmc_status mlmc_adjoint_grad(mlmc_ctx* ctx, int level, int S, const double* xi,
                               double delta, int max_iters, double* Q, double* dQdxi, void* stream);
 
 /* ------------------------------------------------------------------------- */
-/* Preconditioner of this context's CG inner solves (mlmc_level_solve,
+/* Preconditioner of this context's inner solves, CG and MINRES (mlmc_level_solve,
  * mlmc_estimate, mlmc_adjoint_grad).
  *  - MLMC_PC_JACOBI: z = D^-1 r.
  *  - MLMC_PC_MG (default): one geometric multigrid V-cycle, the optimal solver
@@ -340,7 +340,8 @@ mlmc_status mlmc_adjoint_grad(mlmc_ctx* ctx, int level, int S, const double* xi,
  *    re-discretised on it; P1 interpolation on the SW-NE triangulation and its
  *    transpose; nu damped-Jacobi sweeps (damping omega) before and after the
  *    coarse correction; coarse_sweeps Jacobi sweeps on the coarsest grid.  The
- *    V-cycle is a fixed symmetric linear map, so CG stays CG.
+ *    V-cycle is a fixed symmetric positive definite linear map, so CG stays
+ *    CG and MINRES stays preconditioned MINRES.
  * nu in {1, 2}, coarse_sweeps even and >= 2, 0 < omega < 1; 0 keeps the current
  * value (defaults nu = 1, coarse_sweeps = 8, omega = 0.8).  Stopping is still
  * on the FP64 residual of the refinement (Alg. 2.1). */

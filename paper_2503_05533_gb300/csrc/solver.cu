@@ -1348,7 +1348,7 @@ __device__ void solve_system(const Params& P, const DevSolve& S, const Group<GT>
 
     // ---- set-up: coefficient (and inverse diagonal) in the inner storage precision, on the
     // grid and, with multigrid, on every coarse level (coefficient injected at the coarse nodes)
-    const bool mg = P.mg != 0 && !minres;
+    const bool mg = P.mg != 0;
     const bool need_di = jac || mg;
     for (int it = tr; it < (n + 1) * (n + 1); it += GT) {
         const int j = it / (n + 1), i = it - j * (n + 1);
@@ -1463,7 +1463,15 @@ __device__ void solve_system(const Params& P, const DevSolve& S, const Group<GT>
 
         int k = 0;
         if (minres) {
-            // ---- inner preconditioned MINRES on A d = r; |eta| is ||r_k|| in the D^-1 norm
+            // ---- inner preconditioned MINRES on A d = r; |eta| is ||r_k|| in the M^-1 norm, with
+            // M^-1 = D^-1 (Jacobi) or the V-cycle B (multigrid, z_1 = B v_1 here and z_j+1 = B v_j+1
+            // after sweep B); the V-cycle is symmetric positive definite, as MINRES needs
+            if (mg) {
+                const VT zp = mg_vcycle<VT, ST, GT>(P, S, G, PB0, MT, R, AS, DI);
+                double zz, u1, u2;
+                G.template sum3<VT>(zp, (VT)0, (VT)0, zz, u1, u2);
+                rz0 = zz;
+            }
             double g0 = 1.0, g1 = sqrt(rz0), c0 = 1.0, c1 = 1.0, s0 = 0.0, s1 = 0.0;
             double eta = g1;
             const double eta0 = g1;
@@ -1488,10 +1496,15 @@ __device__ void solve_system(const Params& P, const DevSolve& S, const Group<GT>
                 VT zvp = 0;
                 const VT cA = (VT)(dl / g1), cB = (VT)(g1 / g0);
                 if (sweep_on) {
-                    if (jac)
+                    if (jac && !mg)
                         zvp = sweep_minres_b<VT, ST, true>(Zc, gci, AS, Vp, Vc, DI, Zn, cA, cB, ld, n, sc, ja, jb);
                     else
                         zvp = sweep_minres_b<VT, ST, false>(Zc, gci, AS, Vp, Vc, DI, Zn, cA, cB, ld, n, sc, ja, jb);
+                }
+                if (mg) {
+                    // z_j+1 = B v_j+1 and (v_j+1, z_j+1)
+                    G.sync();
+                    zvp = mg_vcycle<VT, ST, GT>(P, S, G, Zn, MT, Vp, AS, DI);
                 }
                 double zv, t3, t4;
                 G.template sum3<VT>(zvp, (VT)0, (VT)0, zv, t3, t4);
@@ -1985,7 +1998,7 @@ mlmc_status launch_typed(mlmc_ctx* ctx, const std::vector<SolveGroup>& groups, c
     long long total = 0, ctotal = 0;
     const mlmc_problem& pb = ctx->prob;
     const int precond = cfg.precond >= 0 ? cfg.precond : ctx->precond;
-    const bool mg = precond == MLMC_PC_MG && cfg.solver == MLMC_CG;
+    const bool mg = precond == MLMC_PC_MG;
     for (const SolveGroup& g : groups) {
         if (g.S <= 0) continue;
         const int n = g.n;
@@ -2136,7 +2149,10 @@ mlmc_status finish_solve(mlmc_ctx* ctx, PendingSolve& ps_) {
             const double pd = cfg.jacobi ? ps : 0.0;   // inverse diagonal read once per inner iteration
             const int steps = std::min(outer[i], cfg.max_outer);
             const double per_it = cfg.solver == MLMC_MINRES
-                                      ? (14 * pv + 2 * ps + pd)
+                                      ? (ps_.mg ? mg_iter_bytes(d.n, d.mg_levels, ps_.mg_nu, ps_.mg_coarse, pv, ps) /
+                                                          unk +
+                                                      14 * pv + 2 * ps
+                                                : 14 * pv + 2 * ps + pd)
                                       : ps_.mg ? mg_iter_bytes(d.n, d.mg_levels, ps_.mg_nu, ps_.mg_coarse, pv, ps) /
                                                          unk +
                                                      8 * pv + 2 * ps

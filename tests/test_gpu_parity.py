@@ -536,3 +536,29 @@ def test_multigrid_parameters(M, nu, coarse, omega):
             M.mlmc_set_inner_tolerance(h, 1.5, 0.0)
     finally:
         M.mlmc_destroy(h)
+
+
+@pytest.mark.parametrize("prec", ["FP64", "FP32"])
+def test_minres_with_multigrid_and_jacobi(M, prec):
+    p = getattr(M, "MLMC_" + prec)
+    ap = M.MLMC_FP64 if prec == "FP64" else M.MLMC_FP32
+    h = _ctx(M)
+    try:
+        n, S = 128, 2
+        af = smooth_lognormal_field(n, S, seed=810, log_sd=1.0)
+        delta = fp64_delta(n) if prec == "FP64" else 1e-7
+        out = {}
+        for pc in (M.MLMC_PC_MG, M.MLMC_PC_JACOBI):
+            M.mlmc_set_precond(h, pc, 0, 0, 0.0)
+            out[pc] = _solve_minres(M, h, n, af, ap, p, delta)
+        M.mlmc_set_precond(h, M.MLMC_PC_MG, 0, 0, 0.0)
+        Um, Qm, itm, rrm, flm = out[M.MLMC_PC_MG]
+        Uj, Qj, itj, rrj, flj = out[M.MLMC_PC_JACOBI]
+        assert np.all(flm == M.MLMC_F_CONVERGED) and np.all(flj == M.MLMC_F_CONVERGED)
+        assert np.all(itm * 10 < itj), (itm, itj)
+        for s in range(S):
+            for U in (Um, Uj):
+                res = o_fem.relative_residual(n, af[s], _interior(n, U[s]))
+                assert res < (2 * delta if prec == "FP64" else delta * (1 + 1e-6))
+    finally:
+        M.mlmc_destroy(h)
