@@ -94,6 +94,8 @@ struct Params {
     int mg_nu;               // multigrid: damped-Jacobi sweeps before and after the coarse correction
     int mg_coarse;           // multigrid: Jacobi sweeps on the coarsest grid (even)
     double mg_omega;         // multigrid: Jacobi damping
+    int mg_smem_nmax;        // multigrid: coarse levels of at most this many cells sit in shared memory
+    int mg_smem_off;         // ... at this offset of the dynamic shared memory (512-thread groups)
     void* mz;                // multigrid: preconditioned residual z (fine grid)
     void* mt;                // multigrid: fine-grid scratch
     void* cx;                // multigrid: coarse-level iterate, scratch and right-hand side
@@ -143,6 +145,21 @@ __host__ __device__ constexpr long long mg_coarse_nodes(int n, int nl) {
     for (int k = 1; k <= nl; ++k) t += mg_level_nodes(n >> k);
     return t;
 }
+// Coarse levels of at most `nmax` cells of a 512-thread group live in its shared memory:
+// per level x, scratch and b (p_v bytes each) and the coefficient and inverse diagonal
+// (p_s bytes each) over the level's padded grid, 16-byte aligned, deepest levels last.
+__host__ __device__ constexpr int mg_smem_array(int nk, int p) { return ((nk + 1) * row_pitch(nk) * p + 15) / 16 * 16; }
+__host__ __device__ constexpr int mg_smem_level_bytes(int nk, int pv, int ps) {
+    return 3 * mg_smem_array(nk, pv) + 2 * mg_smem_array(nk, ps);
+}
+// Bytes of the shared-memory levels of an n-cell grid with nl coarse levels, from level 1 up to
+// (not including) level `upto`.
+__host__ __device__ constexpr int mg_smem_bytes(int n, int nl, int nmax, int pv, int ps, int upto) {
+    int t = 0;
+    for (int k = 1; k <= nl && k < upto; ++k)
+        if ((n >> k) <= nmax) t += mg_smem_level_bytes(n >> k, pv, ps);
+    return t;
+}
 
 // ---------------------------------------------------------------------------
 // The 5-point P1 stencil at one node from its coefficient neighbourhood.
@@ -169,6 +186,18 @@ __device__ __forceinline__ void load_coef_chunk(const ST* as, int ld, int n, int
         CoefLoad<ST, CT>::load4(row + 4 * c, &a[r][1]);
         a[r][0] = (c > 0) ? CoefLoad<ST, CT>::load1(row + 4 * c - 1) : (CT)0;
         a[r][5] = (4 * c + 4 <= n) ? CoefLoad<ST, CT>::load1(row + 4 * c + 4) : (CT)0;
+    }
+}
+
+// The same from memory that may be shared or global (plain generic loads).
+template <class ST, class CT>
+__device__ __forceinline__ void load_coef_chunk_any(const ST* as, int ld, int n, int j, int c, CT a[3][6]) {
+#pragma unroll
+    for (int r = 0; r < 3; ++r) {
+        const ST* row = as + (size_t)(j - 1 + r) * ld;
+        SmemLoad<ST, CT>::load4(row + 4 * c, &a[r][1]);
+        a[r][0] = (c > 0) ? SmemLoad<ST, CT>::load1(row + 4 * c - 1) : (CT)0;
+        a[r][5] = (4 * c + 4 <= n) ? SmemLoad<ST, CT>::load1(row + 4 * c + 4) : (CT)0;
     }
 }
 
@@ -1014,7 +1043,7 @@ struct MGLevel {
 
 template <class VT, class ST>
 __device__ __forceinline__ MGLevel<VT, ST> mg_level(const Params& P, const DevSolve& S, int k, VT* Z, VT* T,
-                                                   const VT* R, const ST* AS, const ST* DI) {
+                                                   const VT* R, const ST* AS, const ST* DI, uint8_t* cs) {
     MGLevel<VT, ST> L;
     if (k == 0) {
         L.n = S.n;
@@ -1033,12 +1062,22 @@ __device__ __forceinline__ MGLevel<VT, ST> mg_level(const Params& P, const DevSo
         L.wn = nullptr;
         L.n = S.n >> k;
         L.ld = row_pitch(L.n);
-        const long long off = S.mg_off + mg_coarse_nodes(S.n, k - 1);
-        L.x = static_cast<VT*>(P.cx) + off;
-        L.t = static_cast<VT*>(P.ct) + off;
-        L.b = static_cast<VT*>(P.cb) + off;
-        L.a = static_cast<const ST*>(P.cas) + off;
-        L.di = static_cast<const ST*>(P.cdi) + off;
+        if (cs && L.n <= P.mg_smem_nmax) {
+            uint8_t* q = cs + mg_smem_bytes(S.n, S.mg_levels, P.mg_smem_nmax, (int)sizeof(VT), (int)sizeof(ST), k);
+            const int av = mg_smem_array(L.n, (int)sizeof(VT)), as = mg_smem_array(L.n, (int)sizeof(ST));
+            L.x = reinterpret_cast<VT*>(q);
+            L.t = reinterpret_cast<VT*>(q + av);
+            L.b = reinterpret_cast<VT*>(q + 2 * av);
+            L.a = reinterpret_cast<const ST*>(q + 3 * av);
+            L.di = reinterpret_cast<const ST*>(q + 3 * av + as);
+        } else {
+            const long long off = S.mg_off + mg_coarse_nodes(S.n, k - 1);
+            L.x = static_cast<VT*>(P.cx) + off;
+            L.t = static_cast<VT*>(P.ct) + off;
+            L.b = static_cast<VT*>(P.cb) + off;
+            L.a = static_cast<const ST*>(P.cas) + off;
+            L.di = static_cast<const ST*>(P.cdi) + off;
+        }
     }
     L.cpr = (L.n - 1) / 4 + 1;
     return L;
@@ -1064,14 +1103,14 @@ __device__ __forceinline__ void mg_load(const MGLevel<VT, ST>& L, const VT* in, 
     const int j = 1 + it / L.cpr, c = it - (j - 1) * L.cpr;
     const size_t base = (size_t)j * L.ld + 4 * c;
     Vec4<VT>::load(L.b + base, C.b4);
-    if (DI) CoefLoad<ST, VT>::load4(L.di + base, C.d4);
+    if (DI) SmemLoad<ST, VT>::load4(L.di + base, C.d4);    // levels may live in shared memory
     if (IN) {
         if constexpr (W) {
             we_row(L.we, L.ld, j, c, C.we);
             wn_row(L.wn, L.ld, j - 1, c, C.ws);
             wn_row(L.wn, L.ld, j, c, C.wn);
         } else {
-            load_coef_chunk<ST, VT>(L.a, L.ld, L.n, j, c, C.a3);
+            load_coef_chunk_any<ST, VT>(L.a, L.ld, L.n, j, c, C.a3);
         }
         load_vec_chunk<VT>(in, L.ld, L.n, j, c, C.xs, C.xc, C.xn);
     }
@@ -1271,22 +1310,22 @@ __device__ __forceinline__ void mg_sweeps_from_zero(const Group<GT>& G, const MG
 // z = B r; returns this thread's part of (r, z).
 template <class VT, class ST, int GT>
 __device__ VT mg_vcycle(const Params& P, const DevSolve& S, const Group<GT>& G, VT* Z, VT* T, const VT* R,
-                        const ST* AS, const ST* DI) {
+                        const ST* AS, const ST* DI, uint8_t* cs) {
     const int nl = S.mg_levels, nu = P.mg_nu;
     const VT w = (VT)P.mg_omega;
     for (int k = 0; k < nl; ++k) {
-        const MGLevel<VT, ST> L = mg_level<VT, ST>(P, S, k, Z, T, R, AS, DI);
+        const MGLevel<VT, ST> L = mg_level<VT, ST>(P, S, k, Z, T, R, AS, DI, cs);
         mg_sweeps_from_zero<VT, ST, GT>(G, L, nu, w);
         mg_residual<VT, ST, GT>(G, L);
-        mg_restrict<VT, ST, GT>(G, L, mg_level<VT, ST>(P, S, k + 1, Z, T, R, AS, DI));
+        mg_restrict<VT, ST, GT>(G, L, mg_level<VT, ST>(P, S, k + 1, Z, T, R, AS, DI, cs));
     }
-    mg_sweeps_from_zero<VT, ST, GT>(G, mg_level<VT, ST>(P, S, nl, Z, T, R, AS, DI), P.mg_coarse, w);
+    mg_sweeps_from_zero<VT, ST, GT>(G, mg_level<VT, ST>(P, S, nl, Z, T, R, AS, DI, cs), P.mg_coarse, w);
     VT rz = 0;
     for (int k = nl - 1; k >= 0; --k) {
-        const MGLevel<VT, ST> L = mg_level<VT, ST>(P, S, k, Z, T, R, AS, DI);
+        const MGLevel<VT, ST> L = mg_level<VT, ST>(P, S, k, Z, T, R, AS, DI, cs);
         // corrected iterate into t for odd nu, in place for even nu, so that nu sweeps end in x
         VT* corr = (nu % 2) ? L.t : L.x;
-        mg_prolong<VT, ST, GT>(G, mg_level<VT, ST>(P, S, k + 1, Z, T, R, AS, DI), L, corr);
+        mg_prolong<VT, ST, GT>(G, mg_level<VT, ST>(P, S, k + 1, Z, T, R, AS, DI, cs), L, corr);
         const VT* in = corr;
         for (int s = 1; s <= nu; ++s) {
             VT* out = ((nu - s) % 2 == 0) ? L.x : L.t;
@@ -1299,7 +1338,7 @@ __device__ VT mg_vcycle(const Params& P, const DevSolve& S, const Group<GT>& G, 
     }
     if (nl == 0) {
         // no coarse grid: the coarsest sweeps ran on the fine grid itself; (r, z) separately
-        const MGLevel<VT, ST> L = mg_level<VT, ST>(P, S, 0, Z, T, R, AS, DI);
+        const MGLevel<VT, ST> L = mg_level<VT, ST>(P, S, 0, Z, T, R, AS, DI, cs);
         const int n = L.n, ld = L.ld, cpr = L.cpr, items = (n - 1) * cpr;
         for (int it = G.rank; it < items; it += GT) {
             const int j = 1 + it / cpr, c = it - (j - 1) * cpr;
@@ -1318,7 +1357,7 @@ __device__ VT mg_vcycle(const Params& P, const DevSolve& S, const Group<GT>& G, 
 // `pipe` is non-null for a 512-thread CG group whose sweeps stream rows
 // through shared memory.
 template <class VT, class ST, int SOLVER, int GT>
-__device__ void solve_system(const Params& P, const DevSolve& S, const Group<GT>& G, Pipe* pipe) {
+__device__ void solve_system(const Params& P, const DevSolve& S, const Group<GT>& G, Pipe* pipe, uint8_t* cs) {
     const int n = S.n, ld = S.ld, cpr = S.cpr;
     const int items = (n - 1) * cpr;
     const int tr = G.rank;
@@ -1376,11 +1415,18 @@ __device__ void solve_system(const Params& P, const DevSolve& S, const Group<GT>
         }
     }
     if (mg) {
+        if (cs) {
+            // shared-memory levels start at zero (boundary and padding entries stay zero)
+            const int bytes = mg_smem_bytes(n, S.mg_levels, P.mg_smem_nmax, (int)sizeof(VT), (int)sizeof(ST),
+                                            S.mg_levels + 1);
+            for (int i = tr; i < bytes / 16; i += GT) reinterpret_cast<uint4*>(cs)[i] = make_uint4(0, 0, 0, 0);
+            G.sync();
+        }
         for (int k = 1; k <= S.mg_levels; ++k) {
             const int nk = n >> k, ldk = row_pitch(nk);
-            const long long off = S.mg_off + mg_coarse_nodes(n, k - 1);
-            ST* ca = static_cast<ST*>(P.cas) + off;
-            ST* cd = static_cast<ST*>(P.cdi) + off;
+            const MGLevel<VT, ST> Lk = mg_level<VT, ST>(P, S, k, nullptr, nullptr, nullptr, AS, DI, cs);
+            ST* ca = const_cast<ST*>(Lk.a);
+            ST* cd = const_cast<ST*>(Lk.di);
             for (int it = tr; it < (nk + 1) * (nk + 1); it += GT) {
                 const int J = it / (nk + 1), I = it - J * (nk + 1);
                 ca[(size_t)J * ldk + I] = store_from<ST, VT>(master_a_as<VT>(S, I << k, J << k));
@@ -1467,7 +1513,7 @@ __device__ void solve_system(const Params& P, const DevSolve& S, const Group<GT>
             // M^-1 = D^-1 (Jacobi) or the V-cycle B (multigrid, z_1 = B v_1 here and z_j+1 = B v_j+1
             // after sweep B); the V-cycle is symmetric positive definite, as MINRES needs
             if (mg) {
-                const VT zp = mg_vcycle<VT, ST, GT>(P, S, G, PB0, MT, R, AS, DI);
+                const VT zp = mg_vcycle<VT, ST, GT>(P, S, G, PB0, MT, R, AS, DI, cs);
                 double zz, u1, u2;
                 G.template sum3<VT>(zp, (VT)0, (VT)0, zz, u1, u2);
                 rz0 = zz;
@@ -1504,7 +1550,7 @@ __device__ void solve_system(const Params& P, const DevSolve& S, const Group<GT>
                 if (mg) {
                     // z_j+1 = B v_j+1 and (v_j+1, z_j+1)
                     G.sync();
-                    zvp = mg_vcycle<VT, ST, GT>(P, S, G, Zn, MT, Vp, AS, DI);
+                    zvp = mg_vcycle<VT, ST, GT>(P, S, G, Zn, MT, Vp, AS, DI, cs);
                 }
                 double zv, t3, t4;
                 G.template sum3<VT>(zvp, (VT)0, (VT)0, zv, t3, t4);
@@ -1548,7 +1594,7 @@ __device__ void solve_system(const Params& P, const DevSolve& S, const Group<GT>
                 VT* pnew = (k & 1) ? PB1 : PB0;
                 if (mg) {
                     // z = B r and (r, z); beta = (r, z) / (r, z)_previous
-                    const VT rzp = mg_vcycle<VT, ST, GT>(P, S, G, MZ, MT, R, AS, DI);
+                    const VT rzp = mg_vcycle<VT, ST, GT>(P, S, G, MZ, MT, R, AS, DI, cs);
                     VT sc0[4];
                     const int k0 = k;
                     G.template reduce<VT, VT>(rzp, (VT)0, (VT)0,
@@ -1737,11 +1783,11 @@ __global__ void __launch_bounds__(CTA, 1) resident_solve(Params P) {
                 pipe.leader = ((int)threadIdx.x % cpr) == 0;
                 pipe.lead_warp = ((int)threadIdx.x % cpr) < 32;
             }
-            solve_system<VT, ST, SOLVER, G_BIG>(P, S, G, &pipe);
+            solve_system<VT, ST, SOLVER, G_BIG>(P, S, G, &pipe, P.mg_smem_nmax > 0 ? dsm + P.mg_smem_off : nullptr);
             if (pipe.leader && pipe_aborted(pipe)) pipe_drain(pipe);
             return;
         }
-        solve_system<VT, ST, SOLVER, G_BIG>(P, S, G, nullptr);
+        solve_system<VT, ST, SOLVER, G_BIG>(P, S, G, nullptr, P.mg_smem_nmax > 0 ? dsm + P.mg_smem_off : nullptr);
         return;
     }
     if (b < P.nbig + nmed_cta) {
@@ -1749,14 +1795,14 @@ __global__ void __launch_bounds__(CTA, 1) resident_solve(Params P) {
         const int idx = (b - P.nbig) * 4 + gid;
         if (idx >= P.nmed) return;
         Group<G_MED> G{(int)(threadIdx.x % G_MED), gid, red + gid * 3 * (G_MED / 32), bcast + 4 * gid};
-        solve_system<VT, ST, SOLVER, G_MED>(P, P.solves[P.order[P.nbig + idx]], G, nullptr);
+        solve_system<VT, ST, SOLVER, G_MED>(P, P.solves[P.order[P.nbig + idx]], G, nullptr, nullptr);
         return;
     }
     const int gid = threadIdx.x / G_SMALL;
     const int idx = (b - P.nbig - nmed_cta) * (CTA / G_SMALL) + gid;
     if (idx >= P.nsmall) return;
     Group<G_SMALL> G{(int)(threadIdx.x % G_SMALL), gid, nullptr, nullptr};
-    solve_system<VT, ST, SOLVER, G_SMALL>(P, P.solves[P.order[P.nbig + P.nmed + idx]], G, nullptr);
+    solve_system<VT, ST, SOLVER, G_SMALL>(P, P.solves[P.order[P.nbig + P.nmed + idx]], G, nullptr, nullptr);
 }
 
 // Group size class of a system: chunk items per thread stay around 8..32.
@@ -1892,6 +1938,8 @@ Params make_params(char* base, const Layout& L, int ns, int nbig, int nmed, int 
     P.mg_nu = 1;
     P.mg_coarse = 8;
     P.mg_omega = 0.8;
+    P.mg_smem_nmax = 0;
+    P.mg_smem_off = 0;
     P.solver = solver;
     P.sys_iters = reinterpret_cast<int32_t*>(base + L.o_stats);
     P.sys_outer = P.sys_iters + ns;
@@ -1957,7 +2005,12 @@ int choose_ring(const std::vector<int>& big_n, size_t& smem, int max_ring, int n
 template <class VT, class ST>
 cudaError_t launch_resident(const Params& P, int solver, int grid, size_t smem, cudaStream_t st) {
     if (solver == MLMC_MINRES) {
-        resident_solve<VT, ST, MLMC_MINRES><<<grid, CTA, 0, st>>>(P);
+        if (smem > 0) {
+            const cudaError_t e = cudaFuncSetAttribute(resident_solve<VT, ST, MLMC_MINRES>,
+                                                       cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+            if (e != cudaSuccess) return e;
+        }
+        resident_solve<VT, ST, MLMC_MINRES><<<grid, CTA, smem, st>>>(P);
     } else {
         if (smem > 0) {
             const cudaError_t e = cudaFuncSetAttribute(resident_solve<VT, ST, MLMC_CG>,
@@ -2085,6 +2138,27 @@ mlmc_status launch_typed(mlmc_ctx* ctx, const std::vector<SolveGroup>& groups, c
         for (int i : order)
             if (size_class(solves[i].n) == 0) big_n.push_back(solves[i].n);
         P.ring = choose_ring<VT, ST>(big_n, smem, ctx->solve_ring, ctx->num_sms);
+    }
+    // multigrid: the deepest coarse levels of the 512-thread groups in shared memory, as deep a cut
+    // (coarse grids of at most 64, 32 or 16 cells) as fits beside the row pipeline
+    if (mg && nbig > 0) {
+        const size_t pipe_end = smem ? (smem + 127) / 128 * 128 : 0;
+        for (int nmax : {64, 32, 16}) {
+            // every large system's shared-memory levels must fit (halving chains differ by grid)
+            size_t need = 0;
+            for (int i : order) {
+                const int ni = solves[i].n;
+                if (size_class(ni) != 0) continue;
+                need = std::max(need, (size_t)mg_smem_bytes(ni, solves[i].mg_levels, nmax, (int)sizeof(VT),
+                                                            (int)sizeof(ST), solves[i].mg_levels + 1));
+            }
+            if (need > 0 && pipe_end + need <= (size_t)kPipeSmemMax) {
+                P.mg_smem_nmax = nmax;
+                P.mg_smem_off = (int)pipe_end;
+                smem = pipe_end + need;
+                break;
+            }
+        }
     }
     P.timeout_ns = (unsigned long long)(ctx->wait_timeout_s * 1e9);
     P.extra_tx = 16u * (unsigned)ctx->wait_extra;
