@@ -406,7 +406,9 @@ mlmc_status mlmc_debug_set_wait_extra(mlmc_ctx* ctx, int extra);
  * solves (n >= 91, one 512-thread CTA per system; used for grids whose rows
  * are a multiple of 128 cells wide).  -1 chooses automatically (default): the
  * deepest of 4..2 that fits shared memory when the launch has at least one
- * system of its largest size per SM, else none.  0 turns the pipeline off (rows are read with
+ * system of its largest size per SM and the solve is Jacobi-preconditioned,
+ * else none (the multigrid V-cycle uses that shared memory for its coarse
+ * levels).  0 turns the pipeline off (rows are read with
  * plain cached loads); 2..4 cap the depth.  The arithmetic is the same either
  * way, so results are bit-identical; exists to measure the pipeline and to test
  * that identity. */
