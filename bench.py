@@ -350,7 +350,8 @@ def main():
                        "seed": "1000 + rank", "parallelism": "replicas" if world > 1 else "single GPU"},
             "solved_dof_per_s": dofs / step_s,
             "rmse": [r["rmse"] for r in results], "N_l": results[-1]["N"], "rounds": results[-1]["rounds"],
-            "prec_l": results[-1]["prec"], "fp64_retries_l": results[-1]["fp64_retries"],
+            "delta_l": results[-1]["delta"], "prec_l": results[-1]["prec"],
+            "fp64_retries_l": results[-1]["fp64_retries"],
             "inner_iters_per_step": sum(iters) / len(iters),
             "fp64": fp64,
             "roofline": {"bound": "hbm", "kernel": "resident_solve", "achieved": achieved, "peak": hbm_peak,
