@@ -10,20 +10,19 @@
 // and b_i = f h^2 (six triangles of area h^2/2, one third each).
 //
 // Solve (Alg. 2.1 with the factorisation replaced by a Krylov method):
-//   x = 0; loop: r = b - A x (FP64, master coefficient); stop if ||r||/||b|| < delta
-//   (Eq. (2.1), C = 1); else solve A d = r with Jacobi-preconditioned CG
-//   (Sec. 2.2) in the inner precision to ||r_k|| <= tau ||r_0||,
-//   tau = clamp(theta delta / rho, tau_min, tau_max); x += d (FP64).
+//   x = 0; loop: r = b - A x (FP64, master coefficient; r = b while x = 0); stop if
+//   ||r||/||b|| < delta (Eq. (2.1), C = 1); else solve A d = r with CG or MINRES
+//   (Sec. 2.2), preconditioned by a geometric multigrid V-cycle or by Jacobi, in the
+//   inner precision to ||r_k|| <= tau ||r_0||, tau = clamp(theta delta / rho,
+//   tau_min, tau_max); x += d (FP64).
 // QoI (Problem 4.5): Q = sum_i g_i x_i, g_i = int_B phi_i (B = D: g_i = h^2).
 //
 // Execution: each system is solved start to finish by one group of threads --
 // a 512-thread CTA for large grids, a 128-thread quarter of a CTA for medium
 // grids, a warp for small grids -- so every synchronisation is group-local
 // (__syncthreads, a named barrier, __syncwarp) and nothing waits on another
-// group.  One launch covers all systems of all levels: CTA b takes either one
-// large system, four medium ones or sixteen small ones.  A system's working
-// set (a few MB at n = 256) is re-read by one SM every iteration, so L1 and L2
-// serve most of its traffic.
+// group.  One launch covers all systems of a precision class: CTA b takes either
+// one large system, four medium ones or sixteen small ones.
 #include <cuda_bf16.h>
 #include <cuda_fp16.h>
 #include <cuda_runtime.h>
