@@ -217,6 +217,8 @@ def main():
     ap.add_argument("--mg-coarse", type=int, default=0, help="multigrid coarsest-grid sweeps (0: default)")
     ap.add_argument("--tau-min", type=float, default=0.0,
                     help="solve-l4 and sweep: floor of the inner tolerance (0: per-precision default)")
+    ap.add_argument("--med-items", type=int, default=0,
+                    help="mlmc cases: most chunks of a system solved by a 128-thread group (0: the library's per-launch choice)")
     ap.add_argument("--ring", type=int, default=-1,
                     help="solve-l4: row-pipeline slots of the large CG solves (-1 automatic, 0 plain loads)")
     args = ap.parse_args()
@@ -274,6 +276,8 @@ def main():
             if args.mg_nu or args.mg_coarse or args.pc != "mg":
                 M.mlmc_set_precond(h, M.MLMC_PC_MG if args.pc == "mg" else M.MLMC_PC_JACOBI, args.mg_nu,
                                    args.mg_coarse)
+            if args.med_items:
+                M.mlmc_debug_set_medium_items(h, args.med_items)
             if profile:
                 M.mlmc_profile_enable(h, True)
             for w in range(warmup):

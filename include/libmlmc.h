@@ -414,6 +414,18 @@ mlmc_status mlmc_debug_set_wait_extra(mlmc_ctx* ctx, int extra);
  * that identity. */
 mlmc_status mlmc_debug_set_solve_ring(mlmc_ctx* ctx, int ring);
 
+/* Diagnostics.  Group size of this context's solves: a system of n cells has
+ * (n - 1) ((n - 1)/4 + 1) four-node chunks; up to 512 chunks it is solved by
+ * one warp, up to `items` chunks by a 128-thread quarter of a CTA (four
+ * systems per CTA), above that by a whole 512-thread CTA.  -1 (default)
+ * chooses per launch: 4096 (n = 91..128 in quarters) when the launch also
+ * holds systems at least twice their size and those systems plus the
+ * mid-size quarters need no more CTAs than the GPU has SMs, else 2048
+ * (n <= 90 in quarters).  Reduction orders follow the group size, so results
+ * agree to the solve tolerance, not bit for bit.
+ * Errors: MLMC_E_ARG unless items is -1 or 512 <= items <= 16384 (n <= 256). */
+mlmc_status mlmc_debug_set_medium_items(mlmc_ctx* ctx, int items);
+
 #ifdef __cplusplus
 }
 #endif

@@ -101,6 +101,7 @@ _SIGS = {
     "mlmc_set_wait_timeout": (c_int, [c_void_p, c_double]),
     "mlmc_debug_set_wait_extra": (c_int, [c_void_p, c_int]),
     "mlmc_debug_set_solve_ring": (c_int, [c_void_p, c_int]),
+    "mlmc_debug_set_medium_items": (c_int, [c_void_p, c_int]),
     "mlmc_set_precond": (c_int, [c_void_p, c_int, c_int, c_int, c_double]),
     "mlmc_set_inner_tolerance": (c_int, [c_void_p, c_double, c_double]),
     "mlmc_profile_enable": (c_int, [c_void_p, c_int]),
@@ -225,6 +226,10 @@ def mlmc_set_inner_tolerance(ctx, theta=0.0, tau_min=0.0):
 
 def mlmc_debug_set_solve_ring(ctx, ring):
     _check(lib().mlmc_debug_set_solve_ring(ctx, ring), ctx)
+
+
+def mlmc_debug_set_medium_items(ctx, items):
+    _check(lib().mlmc_debug_set_medium_items(ctx, items), ctx)
 
 
 def mlmc_sample_fields(ctx, level, first, S, xi, a, field_prec, stream=None):

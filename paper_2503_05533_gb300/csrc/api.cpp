@@ -421,6 +421,13 @@ mlmc_status mlmc_set_inner_tolerance(mlmc_ctx* ctx, double theta, double tau_min
     return MLMC_OK;
 }
 
+mlmc_status mlmc_debug_set_medium_items(mlmc_ctx* ctx, int items) {
+    // a quarter's sweeps need a row's chunks (n/4 + 1) to fit its 128 threads: n <= 256 is far inside
+    if (!ctx || (items != -1 && (items < 512 || items > 16384))) return MLMC_E_ARG;
+    ctx->med_items = items;
+    return MLMC_OK;
+}
+
 mlmc_status mlmc_debug_set_solve_ring(mlmc_ctx* ctx, int ring) {
     if (!ctx || ring < -1 || ring == 1 || ring > 4) return MLMC_E_ARG;
     ctx->solve_ring = ring;

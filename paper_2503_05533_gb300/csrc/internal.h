@@ -94,6 +94,7 @@ struct mlmc_ctx {
     int kl_err_pending = 0;       // a synthesis ran since the word was last read
     int wait_extra = 0;           // diagnostic: bytes every tensor-core wait expects and never receives
     int solve_ring = -1;          // diagnostic: row-pipeline slots of large CG solves (-1 automatic, 0 off)
+    int med_items = -1;           // diagnostic: most chunks of a system solved by a 128-thread group (-1 automatic)
     int precond = MLMC_PC_MG;     // preconditioner of the CG inner solves
     int mg_nu = 1;                // multigrid: smoothing sweeps before and after the coarse correction
     int mg_coarse = 8;            // multigrid: Jacobi sweeps on the coarsest grid

@@ -1805,10 +1805,11 @@ __global__ void __launch_bounds__(CTA, 1) resident_solve(Params P) {
 }
 
 // Group size class of a system: chunk items per thread stay around 8..32.
-int size_class(int n) {
+constexpr int kMedItems = 2048, kMedItemsWide = 4096;
+int size_class(int n, int med_items = kMedItems) {
     const long long items = (long long)(n - 1) * ((n - 1) / 4 + 1);
     if (items <= 512) return 2;        // warp
-    if (items <= 2048) return 1;       // 128 threads
+    if (items <= med_items) return 1;  // 128 threads
     return 0;                          // 512 threads
 }
 
@@ -2104,9 +2105,28 @@ mlmc_status launch_typed(mlmc_ctx* ctx, const std::vector<SolveGroup>& groups, c
     std::vector<int> order(ns);
     for (int i = 0; i < ns; ++i) order[i] = i;
     std::stable_sort(order.begin(), order.end(), [&](int x, int y) { return solves[x].n > solves[y].n; });
+    // Mid-size systems (2048 < chunks <= 4096, n = 91..128) go four to a CTA when the launch also holds
+    // systems at least twice their size and the CTAs of those and of the mid-size quarters fit one wave:
+    // a quarter then takes about as long as one of the largest systems on a whole CTA, every long CTA
+    // starts at once, and the small systems' CTAs fill in behind them.  Otherwise a whole CTA each.
+    int med_items = ctx->med_items;
+    if (med_items < 0) {
+        int nmax = 0, mid_nmax = 0, nmid = 0, nlarge = 0;
+        for (const DevSolve& d : solves) {
+            nmax = std::max(nmax, d.n);
+            if (size_class(d.n, kMedItemsWide) == 0) {
+                ++nlarge;
+            } else if (size_class(d.n, kMedItems) == 0) {
+                ++nmid;
+                mid_nmax = std::max(mid_nmax, d.n);
+            }
+        }
+        const bool wide = nmid > 0 && nlarge > 0 && 2 * mid_nmax <= nmax && nlarge + (nmid + 3) / 4 <= ctx->num_sms;
+        med_items = wide ? kMedItemsWide : kMedItems;
+    }
     int nbig = 0, nmed = 0, nsmall = 0;
     for (int i : order) {
-        const int c = size_class(solves[i].n);
+        const int c = size_class(solves[i].n, med_items);
         nbig += c == 0;
         nmed += c == 1;
         nsmall += c == 2;
@@ -2135,7 +2155,7 @@ mlmc_status launch_typed(mlmc_ctx* ctx, const std::vector<SolveGroup>& groups, c
     if (cfg.solver == MLMC_CG) {
         std::vector<int> big_n;
         for (int i : order)
-            if (size_class(solves[i].n) == 0) big_n.push_back(solves[i].n);
+            if (size_class(solves[i].n, med_items) == 0) big_n.push_back(solves[i].n);
         // automatic choice with multigrid: no pipeline.  Its ring would take the shared memory that
         // the coarse levels and L1 serve the V-cycle passes from (measured: 4096 x n = 512 sweep
         // 0.593 s without, 0.700 s with), and it only speeds up the CG sweeps.
@@ -2151,7 +2171,7 @@ mlmc_status launch_typed(mlmc_ctx* ctx, const std::vector<SolveGroup>& groups, c
             size_t need = 0;
             for (int i : order) {
                 const int ni = solves[i].n;
-                if (size_class(ni) != 0) continue;
+                if (size_class(ni, med_items) != 0) continue;
                 need = std::max(need, (size_t)mg_smem_bytes(ni, solves[i].mg_levels, nmax, (int)sizeof(VT),
                                                             (int)sizeof(ST), solves[i].mg_levels + 1));
             }

@@ -147,6 +147,30 @@ def test_bench_configuration_estimate_runs_clean(M):
     assert 0.035 < r["estimate"] < 0.1
 
 
+def test_group_size_choice_changes_the_estimate_only_within_the_solve_tolerance(M):
+    # the bench configuration's FP32 launch (levels 2-4) puts its n = 128 systems four to a CTA, a
+    # choice made per launch; a whole CTA each must give the same level means up to delta_l
+    N = [200, 100, 100, 100, 100]
+    out = {}
+    for items in (-1, 2048):
+        h = M.mlmc_create(M.make_problem(n0=16, m=2, L_max=4, kind=0, K=64, sigma2=1.0, corr_len=0.3, seed=0), 0)
+        try:
+            M.mlmc_debug_set_medium_items(h, items)
+            o = M.mlmc_default_options()
+            o.form = M.MLMC_FORM_MIXED
+            o.L_start = 4
+            keep, o.fixed_N = _fixed(M, N)
+            out[items] = M.result_dict(M.mlmc_estimate(h, o))
+        finally:
+            M.mlmc_destroy(h)
+    a, b = out[-1], out[2048]
+    assert a["N"] == N and b["N"] == N and a["prec"] == b["prec"]
+    assert a["flags_or"] & ~M.MLMC_F_CONVERGED == 0 and b["flags_or"] & ~M.MLMC_F_CONVERGED == 0
+    deltas = np.array(a["delta"])
+    for l in range(5):
+        assert abs(a["Yhat"][l] - b["Yhat"][l]) <= 50 * deltas[l] * 0.05 + 1e-9
+
+
 def test_paper_setting_minres_fp64(M):
     # Sec. 5.1: f = 1, field of Eq. (5.2) with s = 4, q = 2, sigma = 2, h_0 = 1/8, m = 2,
     # MINRES in double precision to the accuracy delta_l of Eq. (4.12), k_p = 0.05.

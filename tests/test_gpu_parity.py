@@ -246,6 +246,43 @@ def test_row_pipeline_is_bit_identical_to_plain_loads(M, prec):
         M.mlmc_destroy(h)
 
 
+@pytest.mark.parametrize("prec", ["FP64", "FP32"])
+@pytest.mark.parametrize("n", [100, 128])
+def test_mid_size_systems_in_quarter_groups(M, prec, n):
+    # n = 91..128 on 128-thread quarters (four systems per CTA, the last CTA partly filled), as the
+    # estimate's mixed launches place them, and on whole CTAs: both reach delta and the oracle's Q
+    p = getattr(M, "MLMC_" + prec)
+    ap = M.MLMC_FP64 if prec == "FP64" else M.MLMC_FP32
+    h = _ctx(M)
+    try:
+        S = 5
+        af = smooth_lognormal_field(n, S, seed=900 + n, log_sd=1.0)
+        delta = fp64_delta(n) if prec == "FP64" else 1e-8
+        out = {}
+        for items in (4096, 2048):
+            M.mlmc_debug_set_medium_items(h, items)
+            for pc in (M.MLMC_PC_MG, M.MLMC_PC_JACOBI):
+                out[(items, pc)] = _solve_pc(M, h, n, af, ap, p, delta, pc)
+        M.mlmc_debug_set_medium_items(h, -1)
+        b = o_fem.load_vector(n)
+        g = o_fem.qoi_weights(n)
+        for s in range(S):
+            _, Qo = o_fem.solve_sample(n, af[s])
+            A = o_fem.assemble(n, af[s])
+            lmin = spla.eigsh(A, k=1, sigma=0, which="LM", return_eigenvectors=False)[0]
+            for key, (U, Q, it, rr, fl) in out.items():
+                assert fl[s] == M.MLMC_F_CONVERGED, key
+                res = o_fem.relative_residual(n, af[s], _interior(n, U[s]))
+                assert res < (2 * delta if prec == "FP64" else delta * (1 + 1e-6)), key
+                bound = np.linalg.norm(g) * res * np.linalg.norm(b) / lmin
+                assert abs(Q[s] - Qo) <= bound * 1.01 + 1e-15 * abs(Qo), key
+        for bad in (0, 511, 16385, -2):
+            with pytest.raises(M.MlmcError):
+                M.mlmc_debug_set_medium_items(h, bad)
+    finally:
+        M.mlmc_destroy(h)
+
+
 def test_large_solve_pipeline_timeout_is_reported_and_gpu_stays_usable(M):
     # the row pipeline's first wait of every team expects bytes that never arrive:
     # the solve stops, flags its systems, and the context keeps working afterwards
