@@ -171,6 +171,29 @@ def test_group_size_choice_changes_the_estimate_only_within_the_solve_tolerance(
         assert abs(a["Yhat"][l] - b["Yhat"][l]) <= 50 * deltas[l] * 0.05 + 1e-9
 
 
+def test_mixed_estimate_with_quarter_groups_matches_oracle(M):
+    # the bench hierarchy with 8 samples per level: the FP32 launch of levels 2-4 holds the n = 256
+    # systems on whole CTAs and the n = 128 and n = 64 ones four to a CTA, whose coarsest grids sit
+    # in shared memory beside each other; every level mean must match the oracle's FP64 solves
+    N = [8] * 5
+    h = M.mlmc_create(M.make_problem(n0=16, m=2, L_max=4, kind=0, K=64, sigma2=1.0, corr_len=0.3, seed=3), 0)
+    try:
+        o = M.mlmc_default_options()
+        o.form = M.MLMC_FORM_MIXED
+        o.L_start = 4
+        keep, o.fixed_N = _fixed(M, N)
+        r = M.result_dict(M.mlmc_estimate(h, o))
+    finally:
+        M.mlmc_destroy(h)
+    P = o_mlmc.Problem(n0=16, m=2, L_max=4, field_kind=0, K=64, sigma2=1.0, corr_len=0.3, seed=3)
+    ref = o_mlmc.estimate_fixed(P, N)
+    assert r["N"] == N and r["flags_or"] & ~M.MLMC_F_CONVERGED == 0
+    deltas = np.array(r["delta"])
+    for l in range(5):
+        # solve error c delta_l |Q| plus the FP32 tensor-core field's (about 1e-6 relative)
+        assert abs(r["Yhat"][l] - ref["Yhat"][l]) <= 50 * deltas[l] * 0.05 + 1e-7, l
+
+
 def test_paper_setting_minres_fp64(M):
     # Sec. 5.1: f = 1, field of Eq. (5.2) with s = 4, q = 2, sigma = 2, h_0 = 1/8, m = 2,
     # MINRES in double precision to the accuracy delta_l of Eq. (4.12), k_p = 0.05.
