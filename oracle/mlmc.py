@@ -69,6 +69,17 @@ def bias_threshold(m, alpha, tol, r=1.0):
     return (r * m ** alpha - 1.0) * tol / math.sqrt(2.0)
 
 
+def rmse(Yhat, s2, N, m, alpha):
+    """Root-mean-square error estimate of the MLMC estimator (Sec. 4.1): the
+    squared bias, estimated by Richardson extrapolation from the finest level
+    mean as |Y_hat_L| / (m^alpha - 1), plus the estimator variance
+    sum_l s_l^2 / N_l of Eq. (4.2)."""
+    Yhat = np.asarray(Yhat, dtype=np.float64)
+    bias = abs(float(Yhat[-1])) / (m ** alpha - 1.0)
+    var = float(np.sum(np.asarray(s2, dtype=np.float64) / np.asarray(N, dtype=np.float64)))
+    return math.sqrt(bias ** 2 + var)
+
+
 def cost_ratio_bound(q, m, beta, gamma, L=None):
     """Sec. 4.2: bound on C^MPML / C^ML.  L None gives the L -> infinity limit
     q + m^((gamma-beta)/2) (1 - q) of Cor. 4.4; otherwise the finite-L form
@@ -165,7 +176,6 @@ def estimate(problem, tol, N_init=100, kp=0.05, alpha=2.0, gamma=2.0, L_start=1,
     Yhat = np.array([s[0] for s in stats])
     s2 = np.array([s[1] for s in stats])
     Nl = np.array([len(y) for y in Y])
-    bias = abs(Yhat[-1]) / (m ** alpha - 1.0)
     return {
         "estimate": float(np.sum(Yhat)),
         "L": L,
@@ -173,7 +183,7 @@ def estimate(problem, tol, N_init=100, kp=0.05, alpha=2.0, gamma=2.0, L_start=1,
         "Yhat": Yhat,
         "s2": s2,
         "delta": delta_rule_fem([problem.h(l) for l in range(L + 1)], kp),
-        "rmse": math.sqrt(bias ** 2 + float(np.sum(s2 / Nl))),
+        "rmse": rmse(Yhat, s2, Nl, m, alpha),
         "bias_failed": bool(bias_failed),
         "rounds": rounds,
         "Y": Y,

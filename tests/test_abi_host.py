@@ -147,3 +147,37 @@ def test_host_loop_rejects_bad_options(L):
     o.tol = -1.0
     with pytest.raises(L.MlmcError):
         L.mlmc_estimate_host(2, 2, 4, o, _Mock([0, 0, 0], [1, 1, 1], 0))
+
+
+class _Alternating:
+    """Y_l = mu_l + sd_l (-1)^k for sample k: mean mu_l and 1/N variance sd_l^2 for even counts."""
+
+    def __init__(self, mu, sd):
+        self.mu, self.sd = mu, sd
+
+    def __call__(self, l, first, count, deltas):
+        k = np.arange(first, first + count)
+        return self.mu[l] + self.sd[l] * np.where(k % 2 == 0, 1.0, -1.0)
+
+
+@pytest.mark.parametrize("yl, grows", [(2.1220e-3, True), (2.1205e-3, False)])
+def test_host_loop_bias_test_constant(L, yl, grows):
+    # m = 2, alpha = 2, r = 1, TOL = 1e-3: the bias test passes iff |Y_hat_L| <= 2.1213203435596424e-3
+    o = L.mlmc_default_options()
+    o.tol, o.N_init, o.L_start = 1e-3, 10, 1
+    r = L.result_dict(L.mlmc_estimate_host(2, 2, 4, o, _Alternating([0.05, yl, 0.0], [1e-4, 1e-5, 1e-6])))
+    assert r["L"] == (2 if grows else 1)
+
+
+def test_host_loop_rmse_hand_computed(L):
+    # fixed N = 100/10/2, means 0.03/0.003/9e-4, variances 1e-5/5e-7/2e-8: bias 9e-4/3 = 3e-4,
+    # variance of the estimator 1.6e-7, RMSE sqrt(9e-8 + 1.6e-7) = 5e-4; estimate 0.0339
+    o = L.mlmc_default_options()
+    o.L_start = 2
+    N = (ctypes.c_int64 * 3)(100, 10, 2)
+    o.fixed_N = ctypes.cast(N, ctypes.POINTER(ctypes.c_int64))
+    sampler = _Alternating([0.03, 0.003, 9e-4], [math.sqrt(1e-5), math.sqrt(5e-7), math.sqrt(2e-8)])
+    r = L.result_dict(L.mlmc_estimate_host(2, 2, 4, o, sampler))
+    assert r["rmse"] == pytest.approx(5e-4, rel=1e-12)
+    assert r["estimate"] == pytest.approx(0.0339, rel=1e-13)
+    assert r["var_est"] == pytest.approx(1.6e-7, rel=1e-12)

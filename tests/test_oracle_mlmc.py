@@ -148,3 +148,23 @@ def test_fixed_sample_mlmc_telescopes():
     assert np.isclose(out["estimate"], np.sum(out["Yhat"]))
     Qf0, _ = P.level_samples(0, 0, 40)
     assert np.isclose(out["Yhat"][0], Qf0.mean())
+
+
+def test_bias_threshold_literal_values():
+    # Alg. 4.1 bias test |Y_hat_L| <= (r m^alpha - 1) TOL / sqrt(2): with m = 2, alpha = 2, r = 1 the
+    # constant is 3 / sqrt(2) = 2.1213203435596424; with r = 1.5 it is 5 / sqrt(2) = 3.5355339059327373
+    assert mlmc.bias_threshold(2, 2.0, 1e-3) == pytest.approx(2.1213203435596424e-3, rel=1e-15)
+    assert mlmc.bias_threshold(2, 2.0, 1e-3, r=1.5) == pytest.approx(3.5355339059327373e-3, rel=1e-15)
+    # m = 4, alpha = 1: (4 - 1) TOL / sqrt(2) again
+    assert mlmc.bias_threshold(4, 1.0, 2e-4) == pytest.approx(4.242640687119285e-4, rel=1e-15)
+
+
+def test_rmse_hand_computed():
+    # bias = 9e-4 / (2^2 - 1) = 3e-4; variance 1e-5/100 + 5e-7/10 + 2e-8/2 = 1.6e-7;
+    # sqrt(9e-8 + 1.6e-7) = sqrt(2.5e-7) = 5e-4 exactly
+    r = mlmc.rmse([0.03, 0.003, 9e-4], [1e-5, 5e-7, 2e-8], [100, 10, 2], 2, 2.0)
+    assert r == pytest.approx(5e-4, rel=1e-13)
+    # the sign of the finest mean does not matter: one level with mean -0.02 has bias 0.02 / 3 and
+    # variance 0.04 / 100 = 4e-4, so the RMSE is sqrt(4/9 1e-4 + 4e-4) = 0.0210818510677891...
+    r1 = mlmc.rmse([-0.02], [0.04], [100], 2, 2.0)
+    assert r1 == pytest.approx(0.021081851067789197, rel=1e-14)
