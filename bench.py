@@ -2,20 +2,30 @@
 
 Workload (one "step"): the whole hot path of one adaptive MLMC estimate --
 Philox draws, tensor-core KL synthesis, every fine and coarse solve of every
-level in resident-solve launches (FP32 inner CG with a 16-bit-stored coefficient
-on coarse levels, FP64 iterative refinement to the per-level accuracy of
-Eq. (4.12)), QoI and level statistics, and the N_l updates of Alg. 4.1 --
-on the five-level hierarchy h = 1/16 .. 1/256 with a 64-term KL field
-(exponential covariance, sigma^2 = 1, correlation length 0.3), f = 1,
-Q = int u, N_init = 100 on every level, target RMSE 1e-3.
+level in resident-solve launches (FP32 inner CG preconditioned by a multigrid
+V-cycle, a 16-bit-stored coefficient on coarse levels, FP64 iterative
+refinement to the per-level accuracy of Eq. (4.12)), QoI and level statistics,
+and the N_l updates of Alg. 4.1 -- on the five-level hierarchy h = 1/16 .. 1/256
+with a 64-term KL field (exponential covariance, sigma^2 = 1, correlation
+length 0.3), f = 1, Q = int u, N_init = 100 on every level, target RMSE 1e-3.
 
 value    = seconds per estimate (device time between CUDA events on the stream).
 e2e      = the same through the C ABI from host data: context creation (basis
            tables built on the host and uploaded), estimate, result to host.
-roofline = the resident solve kernel: algorithmic bytes / event time, against
-           the measured HBM copy bandwidth.
-cpu_baseline / --impl reference = the CPU FP64 oracle on a bounded sample of
-           the same workload, extrapolated to the estimate's sample counts.
+roofline = the resident solve kernel: algorithmic bytes / event time of its
+           launches (each on its own stream), against the measured HBM copy
+           bandwidth; share_of_step = union of those launches on the device
+           timeline / step time.
+fp64     = the two FP64 forms (fixed 1e-10 and adaptive delta_l) on the same
+           workload, seeds, --steps and --warmup.
+cfg3_sweep / cfg4_adjoint / cfg5_7level = the other configurations, each on
+           the same --steps and --warmup: the single-level sweep (4096 systems
+           at n = 512, K = 128, four inner precisions), the adjoint gradients
+           (1024 samples at n = 256, K = 256, box QoI) and the seven-level
+           estimate (h = 1/16 .. 1/1024, K = 256, sigma^2 = 1.5, RMSE 2e-4).
+cpu_baseline / --impl reference = the CPU FP64 oracle (banded Cholesky per
+           solve) running the same Alg. 4.1 estimate in full, on the same seed,
+           with one worker process per host core.
 """
 import argparse
 import json
@@ -31,6 +41,7 @@ sys.path.insert(0, ROOT)
 METRIC = "MLMC time-to-RMSE (s) & solved DOF/s: mixed vs FP64 on 1 GB300; HBM GB/s"
 WORKLOAD = dict(n0=16, m=2, L_max=4, kind=0, K=64, sigma2=1.0, corr_len=0.3, q=2.0, qoi=0, f=1.0)
 TOL, N_INIT = 1e-3, 100
+SEED = 1000          # Philox key of the timed estimate (rank r uses SEED + r)
 L2_FLUSH_BYTES = 512 << 20
 # DRAM bytes (read + write) per resident_solve launch of one timed step of this workload, averaged
 # over the step's launches, from one ncu capture of dram__bytes_read.sum + dram__bytes_write.sum
@@ -115,45 +126,55 @@ class ClockSampler:
 
 
 # ---------------------------------------------------------------------------
-# CPU oracle on a bounded sample (only the cpu_baseline leg and --impl reference run this)
-def _oracle_level_job(args):
-    level, first, count = args
-    sys.path.insert(0, ROOT)
-    from oracle import mlmc as o_mlmc
-    P = o_mlmc.Problem(n0=WORKLOAD["n0"], m=WORKLOAD["m"], L_max=WORKLOAD["L_max"], field_kind=WORKLOAD["kind"],
-                       K=WORKLOAD["K"], sigma2=WORKLOAD["sigma2"], corr_len=WORKLOAD["corr_len"], seed=0)
-    t0 = time.perf_counter()
-    Qf, Qc = P.level_samples(level, first, count)
-    return level, time.perf_counter() - t0, list(Qf - Qc)
+# CPU oracle (only the cpu_baseline leg and --impl reference run this)
+_ORACLE = {}
 
 
-def oracle_throughput(per_level, procs):
-    """Samples/s per level of the oracle with `procs` worker processes (spawn), one thread each."""
+def _oracle_chunk(args):
+    """Y = Q_l - Q_{l-1} of samples [first, first + count) of one level, by the oracle's FP64 solves."""
+    wl, seed, level, first, count = args
+    key = (tuple(sorted(wl.items())), seed)
+    if key not in _ORACLE:
+        sys.path.insert(0, ROOT)
+        from oracle import mlmc as o_mlmc
+        _ORACLE[key] = o_mlmc.Problem(n0=wl["n0"], m=wl["m"], L_max=wl["L_max"], field_kind=wl["kind"], K=wl["K"],
+                                      sigma2=wl["sigma2"], corr_len=wl["corr_len"], q=wl["q"], seed=seed)
+    Qf, Qc = _ORACLE[key].level_samples(level, first, count)
+    return list(Qf - Qc)
+
+
+def oracle_pool(procs):
     import multiprocessing as mp
     # one BLAS/OpenMP thread per worker: `procs` workers use `procs` cores (the children read this
     # environment when they import numpy)
     for var in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS", "BLIS_NUM_THREADS"):
         os.environ[var] = "1"
-    ctx = mp.get_context("spawn")
-    out = {}
-    with ctx.Pool(procs) as pool:
-        pool.map(_oracle_level_job, [(0, 0, 1)] * procs)   # warm the workers (imports, basis tables)
-        for level, count in per_level.items():
-            jobs = [(level, 10_000 + i * count, count) for i in range(procs)]
-            t0 = time.perf_counter()
-            res = pool.map(_oracle_level_job, jobs)
-            wall = time.perf_counter() - t0
-            Y = [y for r in res for y in r[2]]
-            out[level] = {"samples_per_s": procs * count / wall, "Y": Y}
-    return out
+    return mp.get_context("spawn").Pool(procs)
 
 
-def cpu_extrapolated_seconds(N, procs, per_level=None):
-    per_level = per_level or {0: 8, 1: 4, 2: 2, 3: 1, 4: 1}
-    thr = oracle_throughput(per_level, procs)
-    secs = sum(N[l] / thr[l]["samples_per_s"] for l in range(len(N)))
-    sample = "; ".join("level %d: %d samples" % (l, procs * per_level[l]) for l in sorted(per_level))
-    return secs, sample, thr
+def oracle_estimate(pool, procs, wl, tol, seed):
+    """Alg. 4.1 of the oracle on the bench hierarchy (L fixed at L_max, N_init per level), its level
+    samples evaluated in parallel chunks; returns (wall seconds, result dict)."""
+    import numpy as np
+    sys.path.insert(0, ROOT)
+    from oracle import mlmc as o_mlmc
+    P = o_mlmc.Problem(n0=wl["n0"], m=wl["m"], L_max=wl["L_max"], field_kind=wl["kind"], K=wl["K"],
+                       sigma2=wl["sigma2"], corr_len=wl["corr_len"], q=wl["q"], seed=seed)
+
+    def sampler(level, first, count, deltas):
+        nchunk = max(1, min(count, 4 * procs))
+        bounds = [first + (count * c) // nchunk for c in range(nchunk + 1)]
+        jobs = [(wl, seed, level, bounds[c], bounds[c + 1] - bounds[c]) for c in range(nchunk)
+                if bounds[c + 1] > bounds[c]]
+        return np.concatenate([np.asarray(y) for y in pool.map(_oracle_chunk, jobs)])
+
+    t0 = time.perf_counter()
+    res = o_mlmc.estimate(P, tol, N_init=N_INIT, L_start=wl["L_max"], sampler=sampler)
+    return time.perf_counter() - t0, res
+
+
+def oracle_warm(pool, procs, wl, seed):
+    pool.map(_oracle_chunk, [(wl, seed, wl["L_max"], 10_000_000 + i, 1) for i in range(procs)])
 
 
 # ---------------------------------------------------------------------------
@@ -161,31 +182,29 @@ def run_reference(args):
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
         return 0
-    import math
-    procs = min(16, os.cpu_count() or 1)
-    # pilot of the oracle itself: variances for the N_l formula (fixed 5-level hierarchy)
-    pilot = oracle_throughput({0: 8, 1: 4, 2: 2, 3: 1, 4: 1}, procs)
-    V = []
-    for l in range(5):
-        Y = pilot[l]["Y"]
-        mu = sum(Y) / len(Y)
-        V.append(sum((y - mu) ** 2 for y in Y) / len(Y))
-    C = [4.0 ** l for l in range(5)]
-    s = sum(math.sqrt(v * c) for v, c in zip(V, C))
-    N = [max(N_INIT, int(math.ceil(math.sqrt(v / c) * 2.0 / TOL ** 2 * s))) for v, c in zip(V, C)]
-    times = []
-    for it in range(args.warmup + args.steps):
-        secs, sample, _ = cpu_extrapolated_seconds(N, procs)
-        if it >= args.warmup:
-            times.append(secs)
+    procs = min(64, os.cpu_count() or 1)
+    pool = oracle_pool(procs)
+    try:
+        oracle_warm(pool, procs, WORKLOAD, SEED)
+        times, res = [], None
+        for it in range(args.warmup + args.steps):
+            secs, res = oracle_estimate(pool, procs, WORKLOAD, TOL, SEED)
+            if it >= args.warmup:
+                times.append(secs)
+    finally:
+        pool.close()
+        pool.join()
     val = sum(times) / len(times)
+    N = [int(x) for x in res["N"]]
     line = {"metric": METRIC, "value": val, "unit": "s", "n_gpus": args.gpus, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": val * 1e3, "higher_is_better": False, "scaling": "weak",
             "vs_baseline": None, "dtype": "f64", "data": "synthetic", "impl": "reference",
-            "config": {"workload": workload_desc(), "N_l": N},
+            "config": {"workload": workload_desc(), "seed": SEED},
+            "N_l": N, "estimate": float(res["estimate"]), "rmse": float(res["rmse"]),
             "cpu_baseline": {"value": val, "unit": "s", "cores": procs, "kind": "oracle",
-                             "sample": "per step: " + sample + " (banded-Cholesky FP64 solves, fine+coarse), "
-                                       "extrapolated to N_l from an oracle pilot"},
+                             "sample": "the whole estimate per step (Alg. 4.1 on the fixed 5-level hierarchy, "
+                                       "N_l = %s, every fine and coarse solve by FP64 banded Cholesky), "
+                                       "%d worker processes" % (N, procs)},
             "e2e": {"value": val, "unit": "s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line))
     return 0
@@ -200,6 +219,8 @@ def main():
     ap.add_argument("--impl", default="libmlmc", choices=["libmlmc", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-fp64", action="store_true")
+    ap.add_argument("--no-extras", action="store_true",
+                    help="time the headline workload only (no 7-level, sweep and adjoint keys)")
     ap.add_argument("--case", default="mlmc",
                     choices=["mlmc", "mlmc7", "paper", "fixed3", "solve-l4", "kl-synth", "sweep", "adjoint"],
                     help="solve-l4: only the finest level's batch (100 samples, n = 256) of the workload: "
@@ -246,9 +267,10 @@ def main():
     dev = torch.device("cuda", local)
     hbm_peak, _, peak_src = peaks()
 
-    def opts(form=M.MLMC_FORM_MIXED):
+    def opts(wl=None, tol=None, form=M.MLMC_FORM_MIXED):
+        wl, tol = wl or WORKLOAD, tol or TOL
         o = M.mlmc_default_options()
-        o.tol, o.L_start, o.N_init, o.form = TOL, WORKLOAD["L_max"], N_INIT, form
+        o.tol, o.L_start, o.N_init, o.form = tol, wl["L_max"], N_INIT, form
         o.fixed_delta = 1e-10
         return o
 
@@ -259,20 +281,22 @@ def main():
     stream = torch.cuda.current_stream()
 
     if args.case == "solve-l4":
-        return solve_l4_case(M, torch, dev, args, problem(1000), hbm_peak, peak_src, flush, stream)
+        return solve_l4_case(M, torch, dev, args, problem(SEED), hbm_peak, peak_src, flush, stream)
     if args.case == "kl-synth":
         return kl_synth_case(M, torch, dev, args, hbm_peak, peak_src, flush, stream)
     if args.case == "sweep":
-        return sweep_case(M, torch, dev, args, hbm_peak, peak_src, flush, stream)
+        print(json.dumps(sweep_case(M, torch, dev, args, hbm_peak, peak_src, flush, stream)))
+        return 0
     if args.case == "adjoint":
-        return adjoint_case(M, torch, dev, args, hbm_peak, peak_src, flush, stream)
+        print(json.dumps(adjoint_case(M, torch, dev, args, hbm_peak, peak_src, flush, stream)))
+        return 0
     if args.case == "paper":
         return paper_case(M, torch, dev, args, flush, stream)
     if args.case == "fixed3":
         return fixed3_case(M, torch, dev, args, flush, stream)
 
-    def timed_runs(form, steps, warmup, seed0, profile=False):
-        h = M.mlmc_create(problem(seed0), local)
+    def timed_runs(wl, tol, form, steps, warmup, seed0, profile=False):
+        h = M.mlmc_create(M.make_problem(seed=seed0, **wl), local)
         try:
             if args.mg_nu or args.mg_coarse or args.pc != "mg":
                 M.mlmc_set_precond(h, M.MLMC_PC_MG if args.pc == "mg" else M.MLMC_PC_JACOBI, args.mg_nu,
@@ -282,10 +306,10 @@ def main():
             if profile:
                 M.mlmc_profile_enable(h, True)
             for w in range(warmup):
-                M.mlmc_estimate(h, opts(form))
+                M.mlmc_estimate(h, opts(wl, tol, form))
+            torch.cuda.synchronize()
             if profile:
                 M.mlmc_profile_reset(h)
-            torch.cuda.synchronize()
             if dist:
                 dist.barrier()
             torch.cuda.synchronize()
@@ -295,7 +319,7 @@ def main():
                 flush.fill_(float(s))                      # L2 flush between timed steps (outside the events)
                 e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
                 e0.record(stream)
-                res = M.mlmc_estimate(h, opts(form))
+                res = M.mlmc_estimate(h, opts(wl, tol, form))
                 e1.record(stream)
                 e1.synchronize()
                 ms.append(e0.elapsed_time(e1))
@@ -309,8 +333,20 @@ def main():
             M.mlmc_destroy(h)
         return ms, results, launches, prof
 
+    def fp64_forms(wl, tol):
+        """The plain FP64 MLMC (fixed 1e-10) and FP64 with the adaptive delta_l, same workload, seeds,
+        steps and warm-up as the mixed form."""
+        out = {}
+        for name, form in (("fp64_fixed_1e-10", M.MLMC_FORM_FP64_FIXED), ("fp64_adaptive", M.MLMC_FORM_FP64_ADAPTIVE)):
+            fms, fres, _, _ = timed_runs(wl, tol, form, args.steps, args.warmup, SEED + rank)
+            out[name] = {"seconds": sum(fms) / len(fms) / 1e3, "steps": len(fms), "N_l": fres[-1]["N"],
+                         "inner_iters": sum(fres[-1]["inner_iters"]), "estimate": fres[-1]["estimate"],
+                         "rmse": fres[-1]["rmse"]}
+        return out
+
     with ClockSampler(local) as clk:
-        ms, results, launches, prof = timed_runs(M.MLMC_FORM_MIXED, args.steps, args.warmup, 1000 + rank, True)
+        ms, results, launches, prof = timed_runs(WORKLOAD, TOL, M.MLMC_FORM_MIXED, args.steps, args.warmup,
+                                                 SEED + rank, True)
     total_ms = sum(ms)
     if dist:
         from paper_2503_05533_gb300 import replicas
@@ -319,15 +355,9 @@ def main():
     dofs = sum(sum(r["dofs"]) for r in results) / len(results)
     iters = [sum(r["inner_iters"]) for r in results]
 
-    # FP64 forms on the same workload and seeds (plain FP64 MLMC and FP64 with the adaptive delta_l)
-    fp64 = {}
-    if not args.no_fp64:
-        for name, form in (("fp64_fixed_1e-10", M.MLMC_FORM_FP64_FIXED), ("fp64_adaptive", M.MLMC_FORM_FP64_ADAPTIVE)):
-            fms, fres, _, _ = timed_runs(form, 1, 1, 1000 + rank)
-            fp64[name] = {"seconds": fms[0] / 1e3, "N_l": fres[0]["N"], "inner_iters": sum(fres[0]["inner_iters"]),
-                          "estimate": fres[0]["estimate"], "rmse": fres[0]["rmse"]}
+    fp64 = {} if args.no_fp64 else fp64_forms(WORKLOAD, TOL)
 
-    # e2e through the C ABI from host data
+    # e2e through the C ABI from host data: a new context (new seed) per estimate
     e2e_s, h2d, d2h = [], 0, 0
     for s in range(args.steps):
         torch.cuda.synchronize()
@@ -339,6 +369,28 @@ def main():
         torch.cuda.synchronize()
         e2e_s.append(time.perf_counter() - t0)
         h2d, d2h = p["h2d_bytes"], p["d2h_bytes"]
+
+    # the other configurations (one GPU only: the scaling runs time the headline workload alone)
+    extras = {}
+    if world == 1 and not args.no_extras and args.case == "mlmc":
+        with ClockSampler(local) as clk_x:
+            m7, r7, _, p7 = timed_runs(WORKLOAD7, TOL7, M.MLMC_FORM_MIXED, args.steps, args.warmup, SEED, True)
+            f7 = {} if args.no_fp64 else fp64_forms(WORKLOAD7, TOL7)
+            t7 = sum(m7) / len(m7) / 1e3
+            extras["cfg5_7level"] = {
+                "workload": DESC7, "seconds": t7, "steps": len(m7), "rmse": r7[-1]["rmse"], "N_l": r7[-1]["N"],
+                "delta_l": r7[-1]["delta"], "prec_l": r7[-1]["prec"], "fp64_retries_l": r7[-1]["fp64_retries"],
+                "solved_dof_per_s": sum(r7[-1]["dofs"]) / t7,
+                "solve_gbs": p7["solve_bytes"] / (p7["solve_ms"] * 1e-3) / 1e9 if p7["solve_ms"] > 0 else None,
+                "fp64": f7,
+                "speedup_vs_fp64_fixed": (f7["fp64_fixed_1e-10"]["seconds"] / t7) if f7 else None,
+                "speedup_vs_fp64_adaptive": (f7["fp64_adaptive"]["seconds"] / t7) if f7 else None}
+            sw = {}
+            for prec in ("FP32", "FP16S", "BF16S", "FP64"):
+                sw[prec] = sweep_case(M, torch, dev, args, hbm_peak, peak_src, flush, stream, prec=prec)
+            extras["cfg3_sweep"] = sw
+            extras["cfg4_adjoint"] = adjoint_case(M, torch, dev, args, hbm_peak, peak_src, flush, stream)
+        extras["clocks"] = clk_x.summary()
 
     line = None
     if rank == 0:
@@ -352,36 +404,47 @@ def main():
             "vs_baseline": None, "dtype": "f32+f64", "data": "synthetic",
             **({"case": "mlmc7"} if args.case == "mlmc7" else {}),
             "config": {"workload": workload_desc(), "l2": "flushed between timed steps (512 MiB write)",
-                       "seed": "1000 + rank", "parallelism": "replicas" if world > 1 else "single GPU"},
+                       "seed": "%d + rank" % SEED, "parallelism": "replicas" if world > 1 else "single GPU"},
             "solved_dof_per_s": dofs / step_s,
             "rmse": [r["rmse"] for r in results], "N_l": results[-1]["N"], "rounds": results[-1]["rounds"],
             "delta_l": results[-1]["delta"], "prec_l": results[-1]["prec"],
             "fp64_retries_l": results[-1]["fp64_retries"],
             "inner_iters_per_step": sum(iters) / len(iters),
             "fp64": fp64,
+            "speedup_vs_fp64_fixed": (fp64["fp64_fixed_1e-10"]["seconds"] / step_s) if fp64 else None,
+            "speedup_vs_fp64_adaptive": (fp64["fp64_adaptive"]["seconds"] / step_s) if fp64 else None,
             "roofline": {"bound": "hbm", "kernel": "resident_solve", "achieved": achieved, "peak": hbm_peak,
                          "unit": "GB/s", "frac": achieved / hbm_peak, "peak_source": peak_src + " (burst copy)",
                          "traffic": SOLVE_TRAFFIC_BYTES_PER_LAUNCH,
                          "algorithmic_bytes_per_launch": prof["solve_bytes"] / max(1, prof["solve_launches"]),
                          "launches": prof["solve_launches"],
-                         "kernel_ms_per_step": prof["solve_ms"] / args.steps,
-                         "share_of_step": prof["solve_ms"] / total_ms if total_ms > 0 else None},
+                         "launch_ms_summed_per_step": prof["solve_ms"] / args.steps,
+                         "busy_ms_per_step": prof["solve_busy_ms"] / args.steps,
+                         "share_of_step": prof["solve_busy_ms"] / sum(ms) if sum(ms) > 0 else None},
             "kl_synthesis": {"achieved_gbs": kl_gbs, "tensor_tflops": kl_tf, "ms_per_step": prof["kl_ms"] / args.steps},
             "e2e": {"value": sum(e2e_s) / len(e2e_s), "unit": "s", "h2d_bytes_per_step": h2d,
                     "d2h_bytes_per_step": d2h},
             "gpu_launches": launches,
             "clocks": clk.summary(),
+            **extras,
         }
     if dist:
         dist.barrier()
         dist.destroy_process_group()
     if rank == 0:
         if world == 1 and not args.no_cpu_baseline:
-            procs = min(16, os.cpu_count() or 1)
-            secs, sample, _ = cpu_extrapolated_seconds(results[-1]["N"], procs)
+            procs = min(64, os.cpu_count() or 1)
+            pool = oracle_pool(procs)
+            try:
+                oracle_warm(pool, procs, WORKLOAD, SEED)
+                secs, ores = oracle_estimate(pool, procs, WORKLOAD, TOL, SEED)
+            finally:
+                pool.close()
+                pool.join()
             line["cpu_baseline"] = {"value": secs, "unit": "s", "cores": procs, "kind": "oracle",
-                                    "sample": sample + " (FP64 banded Cholesky, fine+coarse per sample), "
-                                              "extrapolated to the estimate's N_l"}
+                                    "sample": "one whole estimate: Alg. 4.1 on the same hierarchy and seed "
+                                              "(N_l = %s), every fine and coarse solve by FP64 banded Cholesky"
+                                              % [int(x) for x in ores["N"]]}
         print(json.dumps(line))
     return 0
 
@@ -564,19 +627,19 @@ def adjoint_case(M, torch, dev, args, hbm_peak, peak_src, flush, stream):
         M.mlmc_destroy(h)
     t = sum(ms) / len(ms) / 1e3
     achieved = prof["solve_bytes"] / (prof["solve_ms"] * 1e-3) / 1e9 if prof["solve_ms"] > 0 else 0.0
-    print(json.dumps({"case": "adjoint", "samples": S, "n": n, "K": K, "seconds_per_batch": t,
-                      "grads_per_s": S / t, "solve_share": prof["solve_ms"] / (sum(ms)),
-                      "solve_achieved_gbs": achieved, "peak_gbs": hbm_peak, "solve_frac": achieved / hbm_peak,
-                      "peak_source": peak_src}))
-    return 0
+    return {"case": "adjoint", "samples": S, "n": n, "K": K, "seconds_per_batch": t, "steps": len(ms),
+            "grads_per_s": S / t, "solve_share": prof["solve_busy_ms"] / (sum(ms)),
+            "solve_achieved_gbs": achieved, "peak_gbs": hbm_peak, "solve_frac": achieved / hbm_peak,
+            "peak_source": peak_src}
 
 
-def sweep_case(M, torch, dev, args, hbm_peak, peak_src, flush, stream):
+def sweep_case(M, torch, dev, args, hbm_peak, peak_src, flush, stream, prec=None):
     """Single-level batched solve: S systems on the 512 x 512 grid (261,121 unknowns each), KL field
     with K = 128 terms and correlation length 0.1, fixed relative residual 1e-6; solved DOF/s and
     the solve kernel's HBM rate."""
     S, n, K, delta = args.sweep_samples, 512, 128, args.sweep_delta
-    prec = getattr(M, "MLMC_" + args.prec)
+    pname = prec or args.prec
+    prec = getattr(M, "MLMC_" + pname)
     fp64 = prec == M.MLMC_FP64
     prob = M.make_problem(n0=n, m=2, L_max=0, kind=0, K=K, sigma2=1.0, corr_len=0.1, seed=11)
     h = M.mlmc_create(prob, dev.index or 0)
@@ -606,15 +669,16 @@ def sweep_case(M, torch, dev, args, hbm_peak, peak_src, flush, stream):
         flags = fl.cpu()
     finally:
         M.mlmc_destroy(h)
+        del a
+        torch.cuda.empty_cache()
     t = sum(ms) / len(ms) / 1e3
     achieved = prof["solve_bytes"] / (prof["solve_ms"] * 1e-3) / 1e9
-    print(json.dumps({"case": "sweep", "prec": args.prec, "ring": args.ring, "systems": S, "n": n, "delta": delta,
-                      "seconds_per_batch": t, "solved_dof_per_s": S * (n - 1) ** 2 / t,
-                      "inner_iters_per_system": prof["inner_iters"] / (S * args.steps),
-                      "algorithmic_bytes_per_launch": prof["solve_bytes"] / prof["solve_launches"],
-                      "achieved_gbs": achieved, "peak_gbs": hbm_peak, "frac": achieved / hbm_peak,
-                      "peak_source": peak_src, "all_converged": bool((flags == M.MLMC_F_CONVERGED).all())}))
-    return 0
+    return {"case": "sweep", "prec": pname, "ring": args.ring, "systems": S, "n": n, "delta": delta,
+            "seconds_per_batch": t, "steps": len(ms), "solved_dof_per_s": S * (n - 1) ** 2 / t,
+            "inner_iters_per_system": prof["inner_iters"] / (S * args.steps),
+            "algorithmic_bytes_per_launch": prof["solve_bytes"] / prof["solve_launches"],
+            "achieved_gbs": achieved, "peak_gbs": hbm_peak, "frac": achieved / hbm_peak,
+            "peak_source": peak_src, "all_converged": bool((flags == M.MLMC_F_CONVERGED).all())}
 
 
 if __name__ == "__main__":

@@ -160,10 +160,10 @@ mlmc_status mlmc_apply_operator(int n, int S, const void* a, mlmc_prec a_prec, i
  * relative residual delta (Eq. (2.1) with C = 1; accuracy choice Eq. (4.12))
  * by iterative refinement (Alg. 2.1): r = b - A x in FP64 with the FP64
  * operator of the master coefficient; stop when ||r|| / ||b|| < delta; else
- * solve A d = r approximately with the inner Krylov method (Jacobi-
- * preconditioned CG or MINRES, Sec. 2.2) in precision `prec`, and x += d in
- * FP64.  All S solves run in one
- * kernel launch.  Then Q_s = G(u_s) (Problem 4.5; the QoI of
+ * solve A d = r approximately with the inner Krylov method (CG or MINRES,
+ * Sec. 2.2, preconditioned by the context's choice: a geometric multigrid
+ * V-cycle by default, or Jacobi; mlmc_set_precond) in precision `prec`, and
+ * x += d in FP64.  All S solves run in one kernel launch.  Then Q_s = G(u_s) (Problem 4.5; the QoI of
  * the context's problem).
  *   n      cells per side of the solve grid, 2 <= n <= 2048
  *   a      device master coefficient [S][(a_n+1)^2], FP64 or FP32 (a_prec)
@@ -177,12 +177,24 @@ mlmc_status mlmc_apply_operator(int n, int S, const void* a, mlmc_prec a_prec, i
  *   flags  device int32 [S] MLMC_F_* bits, or NULL
  * Every system is solved start to finish by one group of threads (a CTA, a
  * quarter CTA or a warp, by grid size), all systems of the call in one launch.
- * Returns MLMC_OK when the kernel ran; per-solve failures are in `flags`.
- * Synchronises `stream` once, after the kernel. */
+ * Asynchronous: the call enqueues the solve on `stream` and returns; Q, u,
+ * iters, relres and flags are valid once `stream` has been synchronised.
+ * Per-solve failures are in `flags`; a bounded wait that ran out is reported
+ * by the context's next synchronising call (mlmc_sync, mlmc_level_stats,
+ * mlmc_estimate, mlmc_profile_get) as MLMC_E_TIMEOUT.  With profiling on
+ * (mlmc_profile_enable) the call synchronises to read the launch's counters. */
 mlmc_status mlmc_level_solve(mlmc_ctx* ctx, int n, int S, const void* a, mlmc_prec a_prec, int a_n,
                              mlmc_prec prec, mlmc_solver solver, double delta, int max_iters,
                              double* u, double* Q, int32_t* iters, double* relres, int32_t* flags,
                              void* stream);
+
+/* Wait for the work this context enqueued on `stream` and report what the
+ * asynchronous calls could not: MLMC_E_TIMEOUT when a bounded device-side wait
+ * of a synthesis or a solve ran out since the last synchronising call.
+ * The calls of one context share its workspaces, so the work each call
+ * enqueues starts on the device after the work of the context's previous call,
+ * whatever stream either used. */
+mlmc_status mlmc_sync(mlmc_ctx* ctx, void* stream);
 
 /* ------------------------------------------------------------------------- */
 /* Allocation-free variant of mlmc_level_solve.  The paper has no counterpart:
@@ -207,13 +219,15 @@ mlmc_status mlmc_level_solve(mlmc_ctx* ctx, int n, int S, const void* a, mlmc_pr
  * (p_v, p_s: vector and coefficient storage bytes) plus a few words;
  * a batch beyond MLMC_NOALLOC_SCRATCH_BYTES is rejected with MLMC_E_ARG and a
  * message in mlmc_last_error(NULL), as are the argument errors of
- * mlmc_level_solve.
+ * mlmc_level_solve and a QoI box that is not finite, ordered, inside the unit
+ * square and on grid lines of the n-cell grid.
  * The first call on a device looks up the array's device address
- * (cudaGetSymbolAddress) with that device current; make that first call
- * before any stream capture.  Every call uses the same array and leaves its
- * contents behind; the call clears what must start at zero.  Calls whose work
- * overlaps on the GPU (other threads or streams) race on the array: issue them
- * one after another.  Synchronises `stream` to read the kernel's error word. */
+ * (cudaGetSymbolAddress) with that device current.  Every call uses the same
+ * array and leaves its contents behind; the call clears what must start at
+ * zero.  Calls whose work overlaps on the GPU (other threads or streams) race
+ * on the array: issue them one after another.  Every call synchronises
+ * `stream` and copies the kernel's error word to the host, so it cannot be
+ * called while a stream is being captured. */
 #define MLMC_NOALLOC_SCRATCH_BYTES (64ull << 20)
 mlmc_status mlmc_level_solve_noalloc(int device, int n, int S, const void* a, mlmc_prec a_prec, int a_n,
                                      mlmc_prec prec, double delta, int max_iters, int qoi, const double* box,
@@ -325,7 +339,8 @@ mlmc_status mlmc_estimate_host(int m, int L_max, int n0, const mlmc_options* opt
  * autograd wrapper's forward stores only Q).  The field is FP64 when
  * prec == MLMC_FP64, else FP32 from the tensor-core synthesis.
  *   Q      device FP64 [S] out;  dQdxi  device FP64 [S][K] out
- * Synchronises `stream` (inside the solve). */
+ * Asynchronous like mlmc_level_solve: results are valid once `stream` has been
+ * synchronised. */
 mlmc_status mlmc_adjoint_grad(mlmc_ctx* ctx, int level, int S, const double* xi, mlmc_prec prec,
                               double delta, int max_iters, double* Q, double* dQdxi, void* stream);
 
@@ -384,6 +399,9 @@ typedef struct {
     int64_t kl_launches;
     double kl_ms, kl_bytes, kl_flops;
     int64_t h2d_bytes, d2h_bytes;  /* host<->device bytes moved by this context's calls */
+    double solve_busy_ms;      /* union of the resident-solve launches' intervals on the device timeline
+                                  (launches on concurrent streams counted once), since profiling was
+                                  switched on or reset */
 } mlmc_profile;
 mlmc_status mlmc_profile_enable(mlmc_ctx* ctx, int on);
 mlmc_status mlmc_profile_get(mlmc_ctx* ctx, mlmc_profile* out);   /* synchronises the device */

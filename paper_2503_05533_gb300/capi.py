@@ -67,7 +67,7 @@ class mlmc_profile(ctypes.Structure):
     _fields_ = [("solve_launches", c_int64), ("solve_ms", c_double), ("solve_bytes", c_double),
                 ("inner_iters", c_int64), ("unknown_iters", c_int64), ("kl_launches", c_int64),
                 ("kl_ms", c_double), ("kl_bytes", c_double), ("kl_flops", c_double),
-                ("h2d_bytes", c_int64), ("d2h_bytes", c_int64)]
+                ("h2d_bytes", c_int64), ("d2h_bytes", c_int64), ("solve_busy_ms", c_double)]
 
 
 SAMPLER_FN = ctypes.CFUNCTYPE(c_int, c_void_p, c_int, c_int64, c_int, POINTER(c_double), POINTER(c_double))
@@ -85,6 +85,7 @@ _SIGS = {
                                     c_void_p]),
     "mlmc_level_solve": (c_int, [c_void_p, c_int, c_int, c_void_p, c_int, c_int, c_int, c_int, c_double, c_int,
                                  c_void_p, c_void_p, c_void_p, c_void_p, c_void_p, c_void_p]),
+    "mlmc_sync": (c_int, [c_void_p, c_void_p]),
     "mlmc_level_solve_noalloc": (c_int, [c_int, c_int, c_int, c_void_p, c_int, c_int, c_int, c_double, c_int,
                                          c_int, POINTER(c_double), c_double, c_void_p, c_void_p, c_void_p,
                                          c_void_p, c_void_p]),
@@ -249,6 +250,11 @@ def mlmc_level_solve(ctx, n, S, a, a_prec, a_n, prec, solver, delta, max_iters, 
                      flags=None, stream=None):
     _check(lib().mlmc_level_solve(ctx, n, S, _ptr(a), a_prec, a_n, prec, solver, delta, max_iters, _ptr(u),
                                   _ptr(Q), _ptr(iters), _ptr(relres), _ptr(flags), _stream(stream)), ctx)
+
+
+def mlmc_sync(ctx, stream=None):
+    """Wait for the context's work on `stream`; raises on a bounded wait that ran out."""
+    _check(lib().mlmc_sync(ctx, _stream(stream)), ctx)
 
 
 def mlmc_level_solve_noalloc(device, n, S, a, a_prec, a_n, prec, delta, max_iters, qoi, box, f, Q, iters=None,

@@ -26,6 +26,11 @@ std::string& create_error() {
 
 cudaError_t DevBuf::reserve(size_t want) {
     if (want <= bytes && ptr) return cudaSuccess;
+    // calls return before their kernels finish: work still in flight may use the old buffer
+    if (ptr) {
+        const cudaError_t e = cudaDeviceSynchronize();
+        if (e != cudaSuccess) return e;
+    }
     release();
     const size_t grow = std::max(want, bytes + bytes / 4);
     cudaError_t e = cudaMalloc(&ptr, grow);
@@ -83,6 +88,35 @@ static void acc_push(mlmc_acc* a, double y) {
     a->m2 += d * (y - a->mean);
     two_sum_add(a->sum, a->sum_c, y);
     two_sum_add(a->sumsq, a->sumsq_c, y * y);
+}
+
+cudaError_t ctx_order_begin(mlmc_ctx* ctx, cudaStream_t st) {
+    return ctx->order_recorded ? cudaStreamWaitEvent(st, ctx->order_ev, 0) : cudaSuccess;
+}
+
+cudaError_t ctx_order_end(mlmc_ctx* ctx, cudaStream_t st) {
+    if (!ctx->order_ev) {
+        const cudaError_t e = cudaEventCreateWithFlags(&ctx->order_ev, cudaEventDisableTiming);
+        if (e != cudaSuccess) return e;
+    }
+    const cudaError_t e = cudaEventRecord(ctx->order_ev, st);
+    if (e == cudaSuccess) ctx->order_recorded = true;
+    return e;
+}
+
+mlmc_status check_device_errors(mlmc_ctx* ctx, cudaStream_t st) {
+    unsigned w[2] = {0u, 0u};
+    MLMC_CUDA_RET(ctx->err, cudaMemcpyAsync(w, ctx->kl_err, sizeof(w), cudaMemcpyDeviceToHost, st));
+    MLMC_CUDA_RET(ctx->err, cudaStreamSynchronize(st));
+    if (w[0] == 0u && w[1] == 0u) return MLMC_OK;   // KERR_NONE
+    MLMC_CUDA_RET(ctx->err, cudaMemsetAsync(ctx->kl_err, 0, sizeof(w), st));
+    MLMC_CUDA_RET(ctx->err, cudaStreamSynchronize(st));
+    if (w[0] != 0u)
+        ctx->err = "tensor-core KL synthesis: a bounded wait ran out (timeout); its output is not valid";
+    else
+        ctx->err = "resident solve: a bounded wait of the row pipeline ran out after " +
+                   std::to_string(ctx->wait_timeout_s) + " s; the affected systems carry MLMC_F_TIMEOUT";
+    return MLMC_E_TIMEOUT;
 }
 
 double qoi_weight_node(const mlmc_problem& p, int n, int i, int j) {
@@ -312,6 +346,15 @@ mlmc_status mlmc_create(const mlmc_problem* prob, int device, mlmc_ctx** out) {
     ctx->prob = *prob;
     ctx->device = device;
     cudaDeviceGetAttribute(&ctx->num_sms, cudaDevAttrMultiProcessorCount, device);
+    // the device error words of the synthesis and the solves, zero until a bounded wait runs out
+    if ((e = cudaMalloc(&ctx->kl_err, 2 * sizeof(unsigned))) != cudaSuccess ||
+        (e = cudaMemset(ctx->kl_err, 0, 2 * sizeof(unsigned))) != cudaSuccess) {
+        create_error() = std::string("error words: ") + cudaGetErrorString(e);
+        ctx->kl_err = nullptr;
+        mlmc_destroy(ctx);
+        return e == cudaErrorMemoryAllocation ? MLMC_E_NOMEM : MLMC_E_CUDA;
+    }
+    ctx->solve_err = ctx->kl_err + 1;
     for (int l = 0; l <= prob->L_max; ++l) {
         const int n = level_n(*prob, l);
         std::string err;
@@ -351,6 +394,8 @@ void mlmc_destroy(mlmc_ctx* ctx) {
     for (DevBuf* b : {&w.fields, &w.xi, &w.q, &w.misc, &w.split, &w.adj}) b->release();
     if (w.pinned) cudaFreeHost(w.pinned);
     if (ctx->kl_err) cudaFree(ctx->kl_err);
+    if (ctx->order_ev) cudaEventDestroy(ctx->order_ev);
+    if (ctx->prof.t0) cudaEventDestroy(ctx->prof.t0);
     delete ctx;
 }
 
@@ -360,9 +405,20 @@ mlmc_status mlmc_set_wait_timeout(mlmc_ctx* ctx, double seconds) {
     return MLMC_OK;
 }
 
+// Reference event of the profile's launch intervals, recorded on the legacy stream.
+static mlmc_status profile_mark_t0(mlmc_ctx* ctx) {
+    if (!ctx->prof.t0) MLMC_CUDA_RET(ctx->err, cudaEventCreate(&ctx->prof.t0));
+    MLMC_CUDA_RET(ctx->err, cudaEventRecord(ctx->prof.t0, nullptr));
+    ctx->prof.solve_iv.clear();
+    return MLMC_OK;
+}
+
 mlmc_status mlmc_profile_enable(mlmc_ctx* ctx, int on) {
     if (!ctx) return MLMC_E_ARG;
+    cudaSetDevice(ctx->device);
+    const bool was = ctx->prof.on;
     ctx->prof.on = on != 0;
+    if (ctx->prof.on && !was) return profile_mark_t0(ctx);
     return MLMC_OK;
 }
 
@@ -382,8 +438,23 @@ mlmc_status mlmc_profile_get(mlmc_ctx* ctx, mlmc_profile* out) {
         cudaEventDestroy(p.b);
     }
     ctx->prof.kl_pending.clear();
+    // union of the solve launches' intervals
+    std::vector<std::pair<double, double>> iv = ctx->prof.solve_iv;
+    std::sort(iv.begin(), iv.end());
+    double busy = 0.0, cs = 0.0, ce = -1.0;
+    for (const auto& x : iv) {
+        if (x.first > ce) {
+            if (ce > cs) busy += ce - cs;
+            cs = x.first;
+            ce = x.second;
+        } else {
+            ce = std::max(ce, x.second);
+        }
+    }
+    if (ce > cs) busy += ce - cs;
+    ctx->prof.acc.solve_busy_ms = busy;
     *out = ctx->prof.acc;
-    return check_kl_wait(ctx);
+    return check_device_errors(ctx, nullptr);
 }
 
 mlmc_status mlmc_profile_reset(mlmc_ctx* ctx) {
@@ -391,7 +462,8 @@ mlmc_status mlmc_profile_reset(mlmc_ctx* ctx) {
     mlmc_profile tmp;
     mlmc_status s = mlmc_profile_get(ctx, &tmp);
     std::memset(&ctx->prof.acc, 0, sizeof(ctx->prof.acc));
-    return s;
+    const mlmc_status t = profile_mark_t0(ctx);
+    return s != MLMC_OK ? s : t;
 }
 
 mlmc_status mlmc_debug_set_wait_extra(mlmc_ctx* ctx, int extra) {
@@ -447,8 +519,12 @@ mlmc_status mlmc_sample_fields(mlmc_ctx* ctx, int level, uint64_t first, int S, 
         MLMC_CUDA_RET(ctx->err, ctx->ws.xi.reserve(sizeof(double) * (size_t)S * ctx->prob.field.K));
         xbuf = ctx->ws.xi.as<double>();
     }
+    MLMC_CUDA_RET(ctx->err, ctx_order_begin(ctx, st));
     MLMC_CUDA_RET(ctx->err, launch_philox_normals(ctx->prob.seed, level, first, S, ctx->prob.field.K, xbuf, st));
-    return synth(ctx, level, S, xbuf, a, field_prec, st);
+    const mlmc_status s = synth(ctx, level, S, xbuf, a, field_prec, st);
+    if (s != MLMC_OK) return s;
+    MLMC_CUDA_RET(ctx->err, ctx_order_end(ctx, st));
+    return MLMC_OK;
 }
 
 mlmc_status mlmc_synthesize_fields(mlmc_ctx* ctx, int level, int S, const double* xi, void* a,
@@ -458,7 +534,12 @@ mlmc_status mlmc_synthesize_fields(mlmc_ctx* ctx, int level, int S, const double
         return fail(ctx, MLMC_E_ARG, "synthesize_fields: bad level, S, pointers or field precision");
     if (S == 0) return MLMC_OK;
     cudaSetDevice(ctx->device);
-    return synth(ctx, level, S, xi, a, field_prec, static_cast<cudaStream_t>(stream));
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    MLMC_CUDA_RET(ctx->err, ctx_order_begin(ctx, st));
+    const mlmc_status s = synth(ctx, level, S, xi, a, field_prec, st);
+    if (s != MLMC_OK) return s;
+    MLMC_CUDA_RET(ctx->err, ctx_order_end(ctx, st));
+    return MLMC_OK;
 }
 
 mlmc_status mlmc_apply_operator(int n, int S, const void* a, mlmc_prec a_prec, int a_n, mlmc_prec op_prec,
@@ -500,9 +581,18 @@ mlmc_status mlmc_level_solve(mlmc_ctx* ctx, int n, int S, const void* a, mlmc_pr
     cfg.prec = prec;
     cfg.solver = solver;
     cfg.max_iters = max_iters;
-    const mlmc_status s = run_solve_batch(ctx, {g}, cfg, static_cast<cudaStream_t>(stream));
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    MLMC_CUDA_RET(ctx->err, ctx_order_begin(ctx, st));
+    const mlmc_status s = launch_solve_async(ctx, {g}, cfg, st);
     if (s != MLMC_OK) return s;
-    return check_kl_wait(ctx);
+    MLMC_CUDA_RET(ctx->err, ctx_order_end(ctx, st));
+    return MLMC_OK;
+}
+
+mlmc_status mlmc_sync(mlmc_ctx* ctx, void* stream) {
+    if (!ctx) return MLMC_E_ARG;
+    cudaSetDevice(ctx->device);
+    return check_device_errors(ctx, static_cast<cudaStream_t>(stream));
 }
 
 void mlmc_acc_merge(mlmc_acc* into, const mlmc_acc* other) {
@@ -516,13 +606,17 @@ mlmc_status mlmc_level_stats(mlmc_ctx* ctx, int S, const double* Qf, const doubl
     cudaSetDevice(ctx->device);
     cudaStream_t st = static_cast<cudaStream_t>(stream);
     MLMC_CUDA_RET(ctx->err, ctx->ws.misc.reserve(sizeof(mlmc_acc)));
+    MLMC_CUDA_RET(ctx->err, ctx_order_begin(ctx, st));
     MLMC_CUDA_RET(ctx->err, launch_level_stats(S, Qf, Qc, ctx->ws.misc.as<mlmc_acc>(), st));
     mlmc_acc got;
     MLMC_CUDA_RET(ctx->err, cudaMemcpyAsync(&got, ctx->ws.misc.ptr, sizeof(got), cudaMemcpyDeviceToHost, st));
+    MLMC_CUDA_RET(ctx->err, ctx_order_end(ctx, st));
     MLMC_CUDA_RET(ctx->err, cudaStreamSynchronize(st));
     ctx->prof.acc.d2h_bytes += (int64_t)sizeof(got);
+    const mlmc_status s = check_device_errors(ctx, st);
+    if (s != MLMC_OK) return s;
     acc_merge(acc, got);
-    return check_kl_wait(ctx);
+    return MLMC_OK;
 }
 
 mlmc_status mlmc_adapt_precision(int L, const double* h, double kp, double alpha1, double alpha2, double beta1,
@@ -588,6 +682,7 @@ mlmc_status mlmc_estimate(mlmc_ctx* ctx, const mlmc_options* opts, mlmc_result* 
     const mlmc_problem& p = ctx->prob;
     const int K = p.field.K;
     const cudaStream_t st = nullptr;
+    MLMC_CUDA_RET(ctx->err, ctx_order_begin(ctx, st));
     const mlmc_prec field_prec = (o.form == MLMC_FORM_MIXED) ? MLMC_FP32 : MLMC_FP64;
     const size_t felem = field_prec == MLMC_FP64 ? sizeof(double) : sizeof(float);
     int32_t flags_or = 0;
@@ -735,7 +830,7 @@ mlmc_status mlmc_estimate(mlmc_ctx* ctx, const mlmc_options* opts, mlmc_result* 
             }
         }
         {
-            const mlmc_status s = check_kl_wait(ctx);
+            const mlmc_status s = check_device_errors(ctx, st);
             if (s != MLMC_OK) return s;
         }
         // ---- level statistics of the batch
@@ -762,6 +857,7 @@ mlmc_status mlmc_estimate(mlmc_ctx* ctx, const mlmc_options* opts, mlmc_result* 
         return MLMC_OK;
     };
     const mlmc_status s = alg41(p.m, p.L_max, p.n0, o, round, res);
+    MLMC_CUDA_RET(ctx->err, ctx_order_end(ctx, st));
     if (s != MLMC_OK) return s;
     for (int l = 0; l <= res->L; ++l) {
         res->prec[l] = prec_lvl[l];
@@ -785,6 +881,7 @@ mlmc_status mlmc_adjoint_grad(mlmc_ctx* ctx, int level, int S, const double* xi,
     if (!xi || !Q || !dQdxi) return fail(ctx, MLMC_E_ARG, "adjoint_grad: null pointer");
     cudaSetDevice(ctx->device);
     cudaStream_t st = static_cast<cudaStream_t>(stream);
+    MLMC_CUDA_RET(ctx->err, ctx_order_begin(ctx, st));
     const int n = level_n(ctx->prob, level);
     const size_t V = (size_t)(n + 1) * (n + 1);
     const mlmc_prec fp = (prec == MLMC_FP64) ? MLMC_FP64 : MLMC_FP32;
@@ -824,11 +921,11 @@ mlmc_status mlmc_adjoint_grad(mlmc_ctx* ctx, int level, int S, const double* xi,
     SolveConfig cfg;
     cfg.prec = prec;
     cfg.max_iters = max_iters;
-    s = run_solve_batch(ctx, {gf, ga}, cfg, st);
+    s = launch_solve_async(ctx, {gf, ga}, cfg, st);
     if (s != MLMC_OK) return s;
-    if ((s = check_kl_wait(ctx)) != MLMC_OK) return s;
     MLMC_CUDA_RET(ctx->err, launch_adjoint_elements(n, S, a, fp == MLMC_FP64, u, lam, w, st));
     MLMC_CUDA_RET(ctx->err, launch_kl_transpose_fp64(ctx->basis.at(n), S, w, dQdxi, st));
+    MLMC_CUDA_RET(ctx->err, ctx_order_end(ctx, st));
     return MLMC_OK;
 }
 

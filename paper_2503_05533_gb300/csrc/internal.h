@@ -7,6 +7,7 @@
 #include <atomic>
 #include <cstdint>
 #include <map>
+#include <utility>
 #include <string>
 #include <vector>
 
@@ -78,6 +79,10 @@ struct Profile {
         double bytes = 0, flops = 0;
     };
     std::vector<Pending> kl_pending;
+    // resident-solve launch intervals [start, end) in ms after the reference event t0 (recorded when
+    // profiling is switched on or reset), for the union of busy time across concurrent streams
+    cudaEvent_t t0 = nullptr;
+    std::vector<std::pair<double, double>> solve_iv;
 };
 
 }  // namespace mlmc
@@ -90,8 +95,10 @@ struct mlmc_ctx {
     std::map<int, mlmc::GridBasis> basis;   // keyed by n
     mlmc::Workspace ws;
     double wait_timeout_s = 10.0;
-    unsigned* kl_err = nullptr;   // error word of the tensor-core synthesis (device, 4 bytes)
-    int kl_err_pending = 0;       // a synthesis ran since the word was last read
+    unsigned* kl_err = nullptr;   // device error words, cleared when the host reads them:
+    unsigned* solve_err = nullptr;    // [0] tensor-core synthesis, [1] resident solves (KERR_*)
+    cudaEvent_t order_ev = nullptr;   // end of the context's last call: later calls on any stream wait for it
+    bool order_recorded = false;
     int wait_extra = 0;           // diagnostic: bytes every tensor-core wait expects and never receives
     int solve_ring = -1;          // diagnostic: row-pipeline slots of large CG solves (-1 automatic, 0 off)
     int med_items = -1;           // diagnostic: most chunks of a system solved by a 128-thread group (-1 automatic)
@@ -164,8 +171,40 @@ struct SolveConfig {
 struct SolveStats {
     int64_t inner_iters = 0;    // summed over solves (host copy, only if requested)
 };
+// A launched batch whose completion the host has not yet checked, with what its profile needs.
+struct PendingSolve {
+    bool active = false;
+    const int32_t* stats = nullptr;   // device int32 [2][ns]: inner iterations, refinement steps per system
+    int ns = 0;
+    int max_outer = 0;
+    // algorithmic bytes of system i: it_i c_it[i] + (steps_i + 1) c_res[i] + steps_i c_upd[i] + c_set[i]
+    // (filled only while profiling)
+    std::vector<double> unk, c_it, c_res, c_upd, c_set;
+    cudaEvent_t ev[2] = {nullptr, nullptr};
+};
+// solver_<precision>.cu (solver_impl.cuh): one inner precision's batch launcher (plan, upload and
+// launch on st with workspace slot `slot`), stand-alone operator apply and allocation-free solve.
+#define MLMC_DECLARE_SOLVER_PRECISION(P)                                                                       \
+    mlmc_status solve_launch_##P(mlmc_ctx* ctx, const std::vector<SolveGroup>& groups, const SolveConfig& cfg, \
+                                 cudaStream_t st, int slot, PendingSolve& out);                                \
+    cudaError_t apply_operator_##P(int n, int S, const void* a, int a_fp64, int a_n, const void* x, void* y,  \
+                                   cudaStream_t st);                                                           \
+    mlmc_status noalloc_solve_##P(int n, int S, const void* a, int a_fp64, int a_n, double delta, int max_iters, \
+                                  int qoi, const double* box, double f, double* Q, int32_t* iters,             \
+                                  double* relres, int32_t* flags, cudaStream_t st, void* scratch,              \
+                                  std::string& err);
+MLMC_DECLARE_SOLVER_PRECISION(fp64)
+MLMC_DECLARE_SOLVER_PRECISION(fp32)
+MLMC_DECLARE_SOLVER_PRECISION(bf16s)
+MLMC_DECLARE_SOLVER_PRECISION(fp16s)
+#undef MLMC_DECLARE_SOLVER_PRECISION
+
 mlmc_status run_solve_batch(mlmc_ctx* ctx, const std::vector<SolveGroup>& groups, const SolveConfig& cfg,
                             cudaStream_t st);
+// The same batch enqueued on st without waiting for it (errors surface at the context's next
+// synchronising call); with profiling on it synchronises to read the launch's counters.
+mlmc_status launch_solve_async(mlmc_ctx* ctx, const std::vector<SolveGroup>& groups, const SolveConfig& cfg,
+                               cudaStream_t st);
 // Independent batches (e.g. one per precision class) launched concurrently: the first on st,
 // the others on the context's auxiliary streams after st's prior work; returns once all are
 // done (st synchronised).  At most kSolveSlots batches.
@@ -183,9 +222,15 @@ cudaError_t launch_level_stats(int S, const double* Qf, const double* Qc, mlmc_a
 cudaError_t launch_adjoint_elements(int n, int S, const void* a, int a_fp64, const double* u,
                                     const double* lam, double* G, cudaStream_t st);
 
-// Error word of the last tensor-core synthesis (kl_tc.cu): MLMC_OK, or MLMC_E_TIMEOUT
-// when one of its bounded waits ran out; clears the word.  Synchronises.
-mlmc_status check_kl_wait(mlmc_ctx* ctx);
+// The context's device error words (api.cpp): synchronises `st`, reads and clears
+// them; MLMC_OK, or MLMC_E_TIMEOUT when a bounded wait of a synthesis or a solve ran out
+// since they were last read.
+mlmc_status check_device_errors(mlmc_ctx* ctx, cudaStream_t st);
+// Device-side ordering of a context's calls: work that a call enqueues on `st` starts after
+// the work of the context's previous call, whatever stream that call used (the calls share
+// the context's workspaces).  begin() before a call's first enqueue, end() after its last.
+cudaError_t ctx_order_begin(mlmc_ctx* ctx, cudaStream_t st);
+cudaError_t ctx_order_end(mlmc_ctx* ctx, cudaStream_t st);
 
 // host helpers (api.cpp)
 void acc_merge(mlmc_acc* into, const mlmc_acc& other);

@@ -244,11 +244,7 @@ cudaError_t launch_kl_fp32(mlmc_ctx* ctx, const GridBasis& gb, int S, const doub
     cudaError_t e = ctx->ws.split.reserve(abytes + 256);
     if (e != cudaSuccess) return e;
     __half* a16 = ctx->ws.split.as<__half>();
-    // the error word lives in its own small buffer so that it survives later reservations of `split`
-    if (!ctx->kl_err && (e = cudaMalloc(&ctx->kl_err, sizeof(unsigned))) != cudaSuccess) return e;
-    if (ctx->kl_err_pending == 0 && (e = cudaMemsetAsync(ctx->kl_err, 0, sizeof(unsigned), st)) != cudaSuccess)
-        return e;
-    ctx->kl_err_pending = 1;
+    // the error word is the context's (cleared when the host reads it)
     unsigned* errw = ctx->kl_err;
     const long long work = (long long)Spad * Kpad;
     split_xi_kernel<<<(unsigned)((work + 255) / 256), 256, 0, st>>>(S, gb.K, Spad, Kpad, xi, a16);
@@ -286,19 +282,6 @@ cudaError_t launch_kl_fp32(mlmc_ctx* ctx, const GridBasis& gb, int S, const doub
         ctx->prof.kl_pending.push_back(pend);
     }
     return cudaSuccess;
-}
-
-mlmc_status check_kl_wait(mlmc_ctx* ctx) {
-    if (!ctx->kl_err || !ctx->kl_err_pending) return MLMC_OK;
-    unsigned w = 0;
-    MLMC_CUDA_RET(ctx->err, cudaMemcpy(&w, ctx->kl_err, sizeof(unsigned), cudaMemcpyDeviceToHost));
-    MLMC_CUDA_RET(ctx->err, cudaMemset(ctx->kl_err, 0, sizeof(unsigned)));
-    ctx->kl_err_pending = 0;
-    if (w == KERR_TIMEOUT) {
-        ctx->err = "tensor-core KL synthesis: a bounded wait ran out (timeout); its output is not valid";
-        return MLMC_E_TIMEOUT;
-    }
-    return MLMC_OK;
 }
 
 }  // namespace mlmc

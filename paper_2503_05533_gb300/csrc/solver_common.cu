@@ -1,0 +1,257 @@
+// A3-A7 host side shared by the four inner precisions: dispatch of a batch to
+// its precision's launcher (solver_<precision>.cu), the launch profile, the
+// synchronous and concurrent batch runners, the operator-apply dispatch and the
+// allocation-free entry point with its static scratch array.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <mutex>
+#include <string>
+#include <vector>
+
+#include "internal.h"
+
+namespace mlmc {
+
+namespace {
+
+// Profile of a launched batch; its stream must have been synchronised.  (Its error word is
+// the context's, read by check_device_errors.)
+mlmc_status finish_solve(mlmc_ctx* ctx, PendingSolve& ps_) {
+    if (!ps_.active) return MLMC_OK;
+    ps_.active = false;
+    const int ns = ps_.ns;
+    cudaEvent_t* ev = ps_.ev;
+    if (ev[0]) {
+        float ms = 0.f, a0 = 0.f, a1 = 0.f;
+        cudaEventElapsedTime(&ms, ev[0], ev[1]);
+        if (ctx->prof.t0 && cudaEventElapsedTime(&a0, ctx->prof.t0, ev[0]) == cudaSuccess &&
+            cudaEventElapsedTime(&a1, ctx->prof.t0, ev[1]) == cudaSuccess)
+            ctx->prof.solve_iv.emplace_back((double)a0, (double)a1);
+        cudaEventDestroy(ev[0]);
+        cudaEventDestroy(ev[1]);
+        ev[0] = ev[1] = nullptr;
+        std::vector<int32_t> stats(2 * ns);
+        MLMC_CUDA_RET(ctx->err, cudaMemcpy(stats.data(), ps_.stats, sizeof(int32_t) * 2 * ns, cudaMemcpyDeviceToHost));
+        const int32_t* outer = stats.data() + ns;
+        double bytes = 0.0;
+        int64_t iters = 0, uit = 0;
+        for (int i = 0; i < ns && i < (int)ps_.unk.size(); ++i) {
+            const int32_t it = stats[i];
+            const int steps = std::min(outer[i], ps_.max_outer);
+            bytes += (double)it * ps_.c_it[i] + (double)(steps + 1) * ps_.c_res[i] + (double)steps * ps_.c_upd[i] +
+                     ps_.c_set[i];
+            iters += it;
+            uit += (int64_t)ps_.unk[i] * it;
+        }
+        mlmc_profile& A = ctx->prof.acc;
+        A.solve_launches += 1;
+        A.solve_ms += ms;
+        A.solve_bytes += bytes;
+        A.inner_iters += iters;
+        A.unknown_iters += uit;
+    }
+    return MLMC_OK;
+}
+
+mlmc_status launch_batch(mlmc_ctx* ctx, const std::vector<SolveGroup>& groups, const SolveConfig& cfg,
+                         cudaStream_t st, int slot, PendingSolve& out) {
+    if (cfg.solver != MLMC_CG && cfg.solver != MLMC_MINRES) {
+        ctx->err = "unknown solver";
+        return MLMC_E_ARG;
+    }
+    switch (cfg.prec) {
+        case MLMC_FP64: return solve_launch_fp64(ctx, groups, cfg, st, slot, out);
+        case MLMC_FP32: return solve_launch_fp32(ctx, groups, cfg, st, slot, out);
+        case MLMC_BF16S: return solve_launch_bf16s(ctx, groups, cfg, st, slot, out);
+        case MLMC_FP16S: return solve_launch_fp16s(ctx, groups, cfg, st, slot, out);
+        default: ctx->err = "bad precision"; return MLMC_E_ARG;
+    }
+}
+
+}  // namespace
+
+mlmc_status run_solve_batch(mlmc_ctx* ctx, const std::vector<SolveGroup>& groups, const SolveConfig& cfg,
+                            cudaStream_t st) {
+    PendingSolve p;
+    mlmc_status s = launch_batch(ctx, groups, cfg, st, 0, p);
+    if (s != MLMC_OK) return s;
+    MLMC_CUDA_RET(ctx->err, cudaStreamSynchronize(st));
+    s = finish_solve(ctx, p);
+    const mlmc_status e = check_device_errors(ctx, st);
+    return s != MLMC_OK ? s : e;
+}
+
+mlmc_status launch_solve_async(mlmc_ctx* ctx, const std::vector<SolveGroup>& groups, const SolveConfig& cfg,
+                               cudaStream_t st) {
+    // profiling reads the launch's per-system counters from its workspace, which the next call reuses
+    if (ctx->prof.on) return run_solve_batch(ctx, groups, cfg, st);
+    PendingSolve p;
+    return launch_batch(ctx, groups, cfg, st, 0, p);
+}
+
+mlmc_status run_solve_batches(mlmc_ctx* ctx, const std::vector<SolveBatch>& batches, cudaStream_t st) {
+    if (batches.size() <= 1) return batches.empty() ? MLMC_OK : run_solve_batch(ctx, batches[0].groups,
+                                                                                 batches[0].cfg, st);
+    if (batches.size() > (size_t)kSolveSlots) {
+        ctx->err = "run_solve_batches: too many concurrent batches";
+        return MLMC_E_ARG;
+    }
+    // fork: batch 0 on st, batch i > 0 on the context's auxiliary stream i - 1, all after st's prior work
+    cudaEvent_t fork = nullptr;
+    MLMC_CUDA_RET(ctx->err, cudaEventCreateWithFlags(&fork, cudaEventDisableTiming));
+    MLMC_CUDA_RET(ctx->err, cudaEventRecord(fork, st));
+    std::vector<PendingSolve> pend(batches.size());
+    std::vector<cudaEvent_t> done(batches.size(), nullptr);
+    mlmc_status status = MLMC_OK;
+    for (size_t i = 0; i < batches.size() && status == MLMC_OK; ++i) {
+        cudaStream_t si = st;
+        if (i > 0) {
+            if (!ctx->aux[i - 1] && cudaStreamCreateWithFlags(&ctx->aux[i - 1], cudaStreamNonBlocking) != cudaSuccess) {
+                ctx->err = "run_solve_batches: cannot create a stream";
+                status = MLMC_E_CUDA;
+                break;
+            }
+            si = ctx->aux[i - 1];
+            if (cudaStreamWaitEvent(si, fork, 0) != cudaSuccess) {
+                ctx->err = "run_solve_batches: cudaStreamWaitEvent failed";
+                status = MLMC_E_CUDA;
+                break;
+            }
+        }
+        status = launch_batch(ctx, batches[i].groups, batches[i].cfg, si, (int)i, pend[i]);
+        if (status == MLMC_OK && i > 0) {
+            // join: st waits for batch i
+            if (cudaEventCreateWithFlags(&done[i], cudaEventDisableTiming) != cudaSuccess ||
+                cudaEventRecord(done[i], si) != cudaSuccess || cudaStreamWaitEvent(st, done[i], 0) != cudaSuccess) {
+                ctx->err = "run_solve_batches: joining the streams failed";
+                status = MLMC_E_CUDA;
+            }
+        }
+    }
+    // every launched batch is waited for, whatever failed
+    for (size_t i = 1; i < batches.size(); ++i)
+        if (ctx->aux[i - 1]) cudaStreamSynchronize(ctx->aux[i - 1]);
+    const cudaError_t se = cudaStreamSynchronize(st);
+    cudaEventDestroy(fork);
+    for (cudaEvent_t e : done)
+        if (e) cudaEventDestroy(e);
+    if (status == MLMC_OK && se != cudaSuccess) {
+        ctx->err = std::string("run_solve_batches: ") + cudaGetErrorString(se);
+        status = MLMC_E_CUDA;
+    }
+    for (PendingSolve& p : pend) {
+        const mlmc_status f = finish_solve(ctx, p);
+        if (status == MLMC_OK) status = f;
+    }
+    if (status == MLMC_OK) status = check_device_errors(ctx, st);
+    return status;
+}
+
+cudaError_t launch_apply_operator(int n, int S, const void* a, int a_fp64, int a_n, int op_prec, const void* x,
+                                  void* y, int vec_fp64, cudaStream_t st) {
+    if (S <= 0) return cudaSuccess;
+    if (vec_fp64) return apply_operator_fp64(n, S, a, a_fp64, a_n, x, y, st);
+    switch (op_prec) {
+        case MLMC_FP32: return apply_operator_fp32(n, S, a, a_fp64, a_n, x, y, st);
+        case MLMC_BF16S: return apply_operator_bf16s(n, S, a, a_fp64, a_n, x, y, st);
+        case MLMC_FP16S: return apply_operator_fp16s(n, S, a, a_fp64, a_n, x, y, st);
+        default: return cudaErrorInvalidValue;
+    }
+}
+
+}  // namespace mlmc
+
+// ===========================================================================
+// Allocation-free solve (mlmc_level_solve_noalloc): the resident solve with its
+// scratch in a file-scope device array instead of context workspaces.
+namespace mlmc {
+namespace {
+
+constexpr size_t kNoAllocBytes = MLMC_NOALLOC_SCRATCH_BYTES;
+__device__ __align__(256) unsigned char g_noalloc_scratch[kNoAllocBytes];
+
+constexpr int kNoAllocMaxDevices = 64;
+std::mutex g_noalloc_mu;
+void* g_noalloc_addr[kNoAllocMaxDevices] = {};
+
+// Device address of the scratch array on the current device (looked up once per device).
+cudaError_t noalloc_scratch(int device, void** out) {
+    std::lock_guard<std::mutex> lock(g_noalloc_mu);
+    if (!g_noalloc_addr[device]) {
+        void* p = nullptr;
+        const cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+        if (e != cudaSuccess) return e;
+        g_noalloc_addr[device] = p;
+    }
+    *out = g_noalloc_addr[device];
+    return cudaSuccess;
+}
+
+}  // namespace
+}  // namespace mlmc
+
+extern "C" mlmc_status mlmc_level_solve_noalloc(int device, int n, int S, const void* a, mlmc_prec a_prec, int a_n,
+                                                mlmc_prec prec, double delta, int max_iters, int qoi,
+                                                const double* box, double f, double* Q, int32_t* iters,
+                                                double* relres, int32_t* flags, void* stream) {
+    using namespace mlmc;
+    std::string& err = create_error();
+    err.clear();
+    if (n < 2 || n > 2048 || S < 0 || a_n < n || a_n % n != 0 || (a_prec != MLMC_FP64 && a_prec != MLMC_FP32) ||
+        prec < MLMC_FP64 || prec > MLMC_FP16S || !(delta > 0) || max_iters < 1 || (qoi != 0 && qoi != 1) ||
+        (qoi == 1 && !box) || !std::isfinite(f) || device < 0 || device >= kNoAllocMaxDevices) {
+        err = "level_solve_noalloc: bad device, n, S, a_n, precision, delta, max_iters, qoi, box or f";
+        return MLMC_E_ARG;
+    }
+    if (qoi == 1) {
+        // the box must be finite, ordered, inside the unit square and on grid lines of the n-cell grid
+        bool ok = std::isfinite(box[0]) && std::isfinite(box[1]) && std::isfinite(box[2]) && std::isfinite(box[3]) &&
+                  box[0] >= 0.0 && box[0] < box[1] && box[1] <= 1.0 && box[2] >= 0.0 && box[2] < box[3] &&
+                  box[3] <= 1.0;
+        for (int k = 0; k < 4 && ok; ++k) {
+            const double v = box[k] * n;
+            ok = std::fabs(v - std::round(v)) <= 1e-9;
+        }
+        if (!ok) {
+            err = "level_solve_noalloc: the QoI box must satisfy 0 <= x0 < x1 <= 1, 0 <= y0 < y1 <= 1, "
+                  "with every side on a grid line of the n-cell grid";
+            return MLMC_E_ARG;
+        }
+    }
+    if (S == 0) return MLMC_OK;
+    if (!a || !Q) {
+        err = "level_solve_noalloc: null a or Q";
+        return MLMC_E_ARG;
+    }
+    int prev = 0;
+    cudaError_t e = cudaGetDevice(&prev);
+    if (e == cudaSuccess) e = cudaSetDevice(device);
+    void* scratch = nullptr;
+    if (e == cudaSuccess) e = noalloc_scratch(device, &scratch);
+    if (e != cudaSuccess) {
+        err = std::string("level_solve_noalloc: set-up: ") + cudaGetErrorString(e);
+        cudaSetDevice(prev);
+        return MLMC_E_CUDA;
+    }
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    const int a64 = a_prec == MLMC_FP64;
+    mlmc_status s;
+    switch (prec) {
+        case MLMC_FP64:
+            s = noalloc_solve_fp64(n, S, a, a64, a_n, delta, max_iters, qoi, box, f, Q, iters, relres, flags, st, scratch, err);
+            break;
+        case MLMC_FP32:
+            s = noalloc_solve_fp32(n, S, a, a64, a_n, delta, max_iters, qoi, box, f, Q, iters, relres, flags, st, scratch, err);
+            break;
+        case MLMC_BF16S:
+            s = noalloc_solve_bf16s(n, S, a, a64, a_n, delta, max_iters, qoi, box, f, Q, iters, relres, flags, st, scratch, err);
+            break;
+        default:
+            s = noalloc_solve_fp16s(n, S, a, a64, a_n, delta, max_iters, qoi, box, f, Q, iters, relres, flags, st, scratch, err);
+            break;
+    }
+    cudaSetDevice(prev);
+    return s;
+}

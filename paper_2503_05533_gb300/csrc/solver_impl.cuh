@@ -1,6 +1,11 @@
 // A3-A7: matrix-free P1 operator, batched inner Krylov solve, FP64 iterative
 // refinement and the QoI, for every system of a batch in one launch.
 //
+// This file holds the kernels and launchers of one inner precision; each
+// solver_<precision>.cu defines MLMC_SOLVER_PREC (an mlmc_prec value) and
+// includes it, so the four precisions compile as separate translation units.
+// solver_common.cu dispatches to them.
+//
 // Operator (Sec. 3.1, P1 elements on the uniform grid with SW-NE diagonals,
 // a_T = mean of the vertex values).  Right-angled P1 triangles couple only
 // along their legs, so A is 5-point with edge weights
@@ -2027,19 +2032,6 @@ int grid_of(int nbig, int nmed, int nsmall) {
     return nbig + (nmed + 3) / 4 + (nsmall + CTA / G_SMALL - 1) / (CTA / G_SMALL);
 }
 
-// A launched batch whose completion the host has not yet checked.
-struct PendingSolve {
-    bool active = false;
-    char* base = nullptr;
-    Layout L{};
-    std::vector<DevSolve> solves;
-    SolveConfig cfg;
-    bool mg = false;
-    int mg_nu = 0, mg_coarse = 0;
-    double pv = 0, ps = 0;
-    cudaEvent_t ev[2] = {nullptr, nullptr};
-};
-
 // Plan, upload and launch one batch on stream st using workspace slot `slot`; the host
 // checks it later with finish_solve (after st has been synchronised).
 template <class VT, class ST>
@@ -2185,6 +2177,7 @@ mlmc_status launch_typed(mlmc_ctx* ctx, const std::vector<SolveGroup>& groups, c
     }
     P.timeout_ns = (unsigned long long)(ctx->wait_timeout_s * 1e9);
     P.extra_tx = 16u * (unsigned)ctx->wait_extra;
+    P.err = ctx->solve_err;   // the context's word: it outlives the workspace, read at the next synchronising call
     cudaEvent_t ev[2] = {nullptr, nullptr};
     if (ctx->prof.on) {
         MLMC_CUDA_RET(ctx->err, cudaEventCreate(&ev[0]));
@@ -2195,216 +2188,32 @@ mlmc_status launch_typed(mlmc_ctx* ctx, const std::vector<SolveGroup>& groups, c
     if (ctx->prof.on) MLMC_CUDA_RET(ctx->err, cudaEventRecord(ev[1], st));
     ctx->prof.acc.h2d_bytes += (int64_t)((sizeof(DevSolve) + sizeof(int)) * ns);
     out.active = true;
-    out.base = base;
-    out.L = L;
-    out.solves = std::move(solves);
-    out.cfg = cfg;
-    out.mg = mg;
-    out.mg_nu = P.mg_nu;
-    out.mg_coarse = P.mg_coarse;
-    out.pv = sizeof(VT);
-    out.ps = sizeof(ST);
+    out.stats = reinterpret_cast<const int32_t*>(base + L.o_stats);
+    out.ns = ns;
+    out.max_outer = cfg.max_outer;
     out.ev[0] = ev[0];
     out.ev[1] = ev[1];
-    return MLMC_OK;
-}
-
-// Error word and profile of a launched batch; its stream must have been synchronised.
-mlmc_status finish_solve(mlmc_ctx* ctx, PendingSolve& ps_) {
-    if (!ps_.active) return MLMC_OK;
-    ps_.active = false;
-    const int ns = (int)ps_.solves.size();
-    const SolveConfig& cfg = ps_.cfg;
-    cudaEvent_t* ev = ps_.ev;
-    unsigned kerr = 0;
-    MLMC_CUDA_RET(ctx->err, cudaMemcpy(&kerr, ps_.base + ps_.L.o_err, sizeof(unsigned), cudaMemcpyDeviceToHost));
-    ctx->prof.acc.d2h_bytes += (int64_t)sizeof(unsigned);
-    if (kerr != KERR_NONE) {
-        if (ev[0]) cudaEventDestroy(ev[0]);
-        if (ev[1]) cudaEventDestroy(ev[1]);
-        ctx->err = "resident solve: a bounded wait of the row pipeline ran out after " +
-                   std::to_string(ctx->wait_timeout_s) + " s; the affected systems carry MLMC_F_TIMEOUT";
-        return MLMC_E_TIMEOUT;
-    }
-    if (ev[0]) {
-        float ms = 0.f;
-        cudaEventElapsedTime(&ms, ev[0], ev[1]);
-        cudaEventDestroy(ev[0]);
-        cudaEventDestroy(ev[1]);
-        std::vector<int32_t> stats(2 * ns);
-        MLMC_CUDA_RET(ctx->err, cudaMemcpy(stats.data(), ps_.base + ps_.L.o_stats, sizeof(int32_t) * 2 * ns,
-                                           cudaMemcpyDeviceToHost));
-        const int32_t* outer = stats.data() + ns;
-        const double pv = ps_.pv, ps = ps_.ps;
-        double bytes = 0.0;
-        int64_t iters = 0, uit = 0;
-        for (int i = 0; i < ns; ++i) {
-            const DevSolve& d = ps_.solves[i];
-            const int32_t it = stats[i];
+    if (ctx->prof.on) {
+        // algorithmic bytes of each system, per unit of its counters (inner iterations, refinement steps)
+        const double pv = sizeof(VT), ps = sizeof(ST);
+        const double pd = cfg.jacobi ? ps : 0.0;   // inverse diagonal read once per inner iteration
+        for (const DevSolve& d : solves) {
             const double unk = (double)(d.n - 1) * (d.n - 1);
             const double pm = d.a_fp64 ? 8.0 : 4.0;
-            const double pd = cfg.jacobi ? ps : 0.0;   // inverse diagonal read once per inner iteration
-            const int steps = std::min(outer[i], cfg.max_outer);
-            const double per_it = cfg.solver == MLMC_MINRES
-                                      ? (ps_.mg ? mg_iter_bytes(d.n, d.mg_levels, ps_.mg_nu, ps_.mg_coarse, pv, ps) /
-                                                          unk +
-                                                      14 * pv + 2 * ps
-                                                : 14 * pv + 2 * ps + pd)
-                                      : ps_.mg ? mg_iter_bytes(d.n, d.mg_levels, ps_.mg_nu, ps_.mg_coarse, pv, ps) /
-                                                         unk +
-                                                     8 * pv + 2 * ps
-                                               : (8 * pv + 2 * ps + pd);
-            // refinement residual: x, the two FP64 edge weights, r and d (and D^-1); set-up: the master
-            // coefficient read for the storage copy and the weights, the copy, D^-1 and the weights written
-            bytes += unk * ((double)it * per_it + (double)(steps + 1) * (8 + 16 + 2 * pv + pd) +
-                            (double)steps * (16 + pv) + (8 + pm + ps + pd + 16));
-            iters += it;
-            uit += (int64_t)unk * it;
+            const double vcyc = mg ? mg_iter_bytes(d.n, d.mg_levels, P.mg_nu, P.mg_coarse, pv, ps) / unk : 0.0;
+            const double per_it = cfg.solver == MLMC_MINRES ? (mg ? vcyc + 14 * pv + 2 * ps : 14 * pv + 2 * ps + pd)
+                                                            : (mg ? vcyc + 8 * pv + 2 * ps : 8 * pv + 2 * ps + pd);
+            out.unk.push_back(unk);
+            out.c_it.push_back(unk * per_it);
+            // refinement residual: x, the two FP64 edge weights, r and d (and D^-1); update: x and d;
+            // set-up: the master coefficient read for the storage copy and the weights, the copy, D^-1 and
+            // the weights written
+            out.c_res.push_back(unk * (8 + 16 + 2 * pv + pd));
+            out.c_upd.push_back(unk * (16 + pv));
+            out.c_set.push_back(unk * (8 + pm + ps + pd + 16));
         }
-        mlmc_profile& A = ctx->prof.acc;
-        A.solve_launches += 1;
-        A.solve_ms += ms;
-        A.solve_bytes += bytes;
-        A.inner_iters += iters;
-        A.unknown_iters += uit;
     }
     return MLMC_OK;
-}
-
-mlmc_status launch_batch(mlmc_ctx* ctx, const std::vector<SolveGroup>& groups, const SolveConfig& cfg,
-                         cudaStream_t st, int slot, PendingSolve& out) {
-    if (cfg.solver != MLMC_CG && cfg.solver != MLMC_MINRES) {
-        ctx->err = "unknown solver";
-        return MLMC_E_ARG;
-    }
-    switch (cfg.prec) {
-        case MLMC_FP64: return launch_typed<double, double>(ctx, groups, cfg, st, slot, out);
-        case MLMC_FP32: return launch_typed<float, float>(ctx, groups, cfg, st, slot, out);
-        case MLMC_BF16S: return launch_typed<float, __nv_bfloat16>(ctx, groups, cfg, st, slot, out);
-        case MLMC_FP16S: return launch_typed<float, __half>(ctx, groups, cfg, st, slot, out);
-        default: ctx->err = "bad precision"; return MLMC_E_ARG;
-    }
-}
-
-}  // namespace
-
-mlmc_status run_solve_batch(mlmc_ctx* ctx, const std::vector<SolveGroup>& groups, const SolveConfig& cfg,
-                            cudaStream_t st) {
-    PendingSolve p;
-    mlmc_status s = launch_batch(ctx, groups, cfg, st, 0, p);
-    if (s != MLMC_OK) return s;
-    MLMC_CUDA_RET(ctx->err, cudaStreamSynchronize(st));
-    return finish_solve(ctx, p);
-}
-
-mlmc_status run_solve_batches(mlmc_ctx* ctx, const std::vector<SolveBatch>& batches, cudaStream_t st) {
-    if (batches.size() <= 1) return batches.empty() ? MLMC_OK : run_solve_batch(ctx, batches[0].groups,
-                                                                                 batches[0].cfg, st);
-    if (batches.size() > (size_t)kSolveSlots) {
-        ctx->err = "run_solve_batches: too many concurrent batches";
-        return MLMC_E_ARG;
-    }
-    // fork: batch 0 on st, batch i > 0 on the context's auxiliary stream i - 1, all after st's prior work
-    cudaEvent_t fork = nullptr;
-    MLMC_CUDA_RET(ctx->err, cudaEventCreateWithFlags(&fork, cudaEventDisableTiming));
-    MLMC_CUDA_RET(ctx->err, cudaEventRecord(fork, st));
-    std::vector<PendingSolve> pend(batches.size());
-    std::vector<cudaEvent_t> done(batches.size(), nullptr);
-    mlmc_status status = MLMC_OK;
-    for (size_t i = 0; i < batches.size() && status == MLMC_OK; ++i) {
-        cudaStream_t si = st;
-        if (i > 0) {
-            if (!ctx->aux[i - 1] && cudaStreamCreateWithFlags(&ctx->aux[i - 1], cudaStreamNonBlocking) != cudaSuccess) {
-                ctx->err = "run_solve_batches: cannot create a stream";
-                status = MLMC_E_CUDA;
-                break;
-            }
-            si = ctx->aux[i - 1];
-            if (cudaStreamWaitEvent(si, fork, 0) != cudaSuccess) {
-                ctx->err = "run_solve_batches: cudaStreamWaitEvent failed";
-                status = MLMC_E_CUDA;
-                break;
-            }
-        }
-        status = launch_batch(ctx, batches[i].groups, batches[i].cfg, si, (int)i, pend[i]);
-        if (status == MLMC_OK && i > 0) {
-            // join: st waits for batch i
-            if (cudaEventCreateWithFlags(&done[i], cudaEventDisableTiming) != cudaSuccess ||
-                cudaEventRecord(done[i], si) != cudaSuccess || cudaStreamWaitEvent(st, done[i], 0) != cudaSuccess) {
-                ctx->err = "run_solve_batches: joining the streams failed";
-                status = MLMC_E_CUDA;
-            }
-        }
-    }
-    // every launched batch is waited for, whatever failed
-    for (size_t i = 1; i < batches.size(); ++i)
-        if (ctx->aux[i - 1]) cudaStreamSynchronize(ctx->aux[i - 1]);
-    const cudaError_t se = cudaStreamSynchronize(st);
-    cudaEventDestroy(fork);
-    for (cudaEvent_t e : done)
-        if (e) cudaEventDestroy(e);
-    if (status == MLMC_OK && se != cudaSuccess) {
-        ctx->err = std::string("run_solve_batches: ") + cudaGetErrorString(se);
-        status = MLMC_E_CUDA;
-    }
-    for (PendingSolve& p : pend) {
-        const mlmc_status f = finish_solve(ctx, p);
-        if (status == MLMC_OK) status = f;
-    }
-    return status;
-}
-
-cudaError_t launch_apply_operator(int n, int S, const void* a, int a_fp64, int a_n, int op_prec, const void* x,
-                                  void* y, int vec_fp64, cudaStream_t st) {
-    if (S <= 0) return cudaSuccess;
-    const long long work = (long long)S * (n + 1) * (n + 1);
-    const unsigned grid = (unsigned)((work + 255) / 256);
-    if (vec_fp64) {
-        apply_operator_kernel<double, double><<<grid, 256, 0, st>>>(n, S, a, a_fp64, a_n,
-                                                                    static_cast<const double*>(x),
-                                                                    static_cast<double*>(y));
-    } else {
-        const float* xf = static_cast<const float*>(x);
-        float* yf = static_cast<float*>(y);
-        switch (op_prec) {
-            case MLMC_FP32: apply_operator_kernel<float, float><<<grid, 256, 0, st>>>(n, S, a, a_fp64, a_n, xf, yf); break;
-            case MLMC_BF16S:
-                apply_operator_kernel<float, __nv_bfloat16><<<grid, 256, 0, st>>>(n, S, a, a_fp64, a_n, xf, yf);
-                break;
-            case MLMC_FP16S: apply_operator_kernel<float, __half><<<grid, 256, 0, st>>>(n, S, a, a_fp64, a_n, xf, yf); break;
-            default: return cudaErrorInvalidValue;
-        }
-    }
-    g_launches.fetch_add(1, std::memory_order_relaxed);
-    return cudaGetLastError();
-}
-
-}  // namespace mlmc
-
-// ===========================================================================
-// Allocation-free solve (mlmc_level_solve_noalloc): the same kernel with its
-// scratch in a file-scope device array instead of context workspaces.
-namespace mlmc {
-namespace {
-
-constexpr size_t kNoAllocBytes = MLMC_NOALLOC_SCRATCH_BYTES;
-__device__ __align__(256) unsigned char g_noalloc_scratch[kNoAllocBytes];
-
-constexpr int kNoAllocMaxDevices = 64;
-std::mutex g_noalloc_mu;
-void* g_noalloc_addr[kNoAllocMaxDevices] = {};
-
-// Device address of the scratch array on the current device (looked up once per device).
-cudaError_t noalloc_scratch(int device, void** out) {
-    std::lock_guard<std::mutex> lock(g_noalloc_mu);
-    if (!g_noalloc_addr[device]) {
-        void* p = nullptr;
-        const cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
-        if (e != cudaSuccess) return e;
-        g_noalloc_addr[device] = p;
-    }
-    *out = g_noalloc_addr[device];
-    return cudaSuccess;
 }
 
 // Descriptors and launch order of a batch of equal-shaped systems, written on the device.
@@ -2428,9 +2237,9 @@ mlmc_status noalloc_typed(int n, int S, const void* a, int a_fp64, int a_n, doub
     const int ld = row_pitch(n);
     const long long stride = (long long)align_up((size_t)(n + 1) * ld, 64);
     const Layout L = make_layout<VT, ST>(stride * S, S, true, false);
-    if (L.total > kNoAllocBytes) {
+    if (L.total > (size_t)MLMC_NOALLOC_SCRATCH_BYTES) {
         err = "level_solve_noalloc: the batch needs " + std::to_string(L.total) + " bytes of scratch, above the " +
-              std::to_string(kNoAllocBytes) + "-byte maximum (MLMC_NOALLOC_SCRATCH_BYTES); use fewer systems";
+              std::to_string((size_t)MLMC_NOALLOC_SCRATCH_BYTES) + "-byte maximum (MLMC_NOALLOC_SCRATCH_BYTES); use fewer systems";
         return MLMC_E_ARG;
     }
     char* base = static_cast<char*>(scratch);
@@ -2505,57 +2314,51 @@ mlmc_status noalloc_typed(int n, int S, const void* a, int a_fp64, int a_n, doub
 }
 
 }  // namespace
-}  // namespace mlmc
 
-extern "C" mlmc_status mlmc_level_solve_noalloc(int device, int n, int S, const void* a, mlmc_prec a_prec, int a_n,
-                                                mlmc_prec prec, double delta, int max_iters, int qoi,
-                                                const double* box, double f, double* Q, int32_t* iters,
-                                                double* relres, int32_t* flags, void* stream) {
-    using namespace mlmc;
-    std::string& err = create_error();
-    err.clear();
-    if (n < 2 || n > 2048 || S < 0 || a_n < n || a_n % n != 0 || (a_prec != MLMC_FP64 && a_prec != MLMC_FP32) ||
-        prec < MLMC_FP64 || prec > MLMC_FP16S || !(delta > 0) || max_iters < 1 || (qoi != 0 && qoi != 1) ||
-        (qoi == 1 && !box) || !std::isfinite(f) || device < 0 || device >= kNoAllocMaxDevices) {
-        err = "level_solve_noalloc: bad device, n, S, a_n, precision, delta, max_iters, qoi, box or f";
-        return MLMC_E_ARG;
-    }
-    if (S == 0) return MLMC_OK;
-    if (!a || !Q) {
-        err = "level_solve_noalloc: null a or Q";
-        return MLMC_E_ARG;
-    }
-    int prev = 0;
-    cudaError_t e = cudaGetDevice(&prev);
-    if (e == cudaSuccess) e = cudaSetDevice(device);
-    void* scratch = nullptr;
-    if (e == cudaSuccess) e = noalloc_scratch(device, &scratch);
-    if (e != cudaSuccess) {
-        err = std::string("level_solve_noalloc: set-up: ") + cudaGetErrorString(e);
-        cudaSetDevice(prev);
-        return MLMC_E_CUDA;
-    }
-    cudaStream_t st = static_cast<cudaStream_t>(stream);
-    const int a64 = a_prec == MLMC_FP64;
-    mlmc_status s;
-    switch (prec) {
-        case MLMC_FP64:
-            s = noalloc_typed<double, double>(n, S, a, a64, a_n, delta, max_iters, qoi, box, f, prec, Q, iters,
-                                              relres, flags, st, scratch, err);
-            break;
-        case MLMC_FP32:
-            s = noalloc_typed<float, float>(n, S, a, a64, a_n, delta, max_iters, qoi, box, f, prec, Q, iters, relres,
-                                            flags, st, scratch, err);
-            break;
-        case MLMC_BF16S:
-            s = noalloc_typed<float, __nv_bfloat16>(n, S, a, a64, a_n, delta, max_iters, qoi, box, f, prec, Q, iters,
-                                                    relres, flags, st, scratch, err);
-            break;
-        default:
-            s = noalloc_typed<float, __half>(n, S, a, a64, a_n, delta, max_iters, qoi, box, f, prec, Q, iters,
-                                             relres, flags, st, scratch, err);
-            break;
-    }
-    cudaSetDevice(prev);
-    return s;
+// ---------------------------------------------------------------------------
+// The entry points of this precision (declared in internal.h).
+#if MLMC_SOLVER_PREC == 0
+#define MLMC_SOLVER_NAME(x) x##_fp64
+using SolverVT = double;
+using SolverST = double;
+#elif MLMC_SOLVER_PREC == 1
+#define MLMC_SOLVER_NAME(x) x##_fp32
+using SolverVT = float;
+using SolverST = float;
+#elif MLMC_SOLVER_PREC == 2
+#define MLMC_SOLVER_NAME(x) x##_bf16s
+using SolverVT = float;
+using SolverST = __nv_bfloat16;
+#elif MLMC_SOLVER_PREC == 3
+#define MLMC_SOLVER_NAME(x) x##_fp16s
+using SolverVT = float;
+using SolverST = __half;
+#else
+#error "MLMC_SOLVER_PREC must be an mlmc_prec value"
+#endif
+
+mlmc_status MLMC_SOLVER_NAME(solve_launch)(mlmc_ctx* ctx, const std::vector<SolveGroup>& groups,
+                                           const SolveConfig& cfg, cudaStream_t st, int slot, PendingSolve& out) {
+    return launch_typed<SolverVT, SolverST>(ctx, groups, cfg, st, slot, out);
 }
+
+cudaError_t MLMC_SOLVER_NAME(apply_operator)(int n, int S, const void* a, int a_fp64, int a_n, const void* x, void* y,
+                                             cudaStream_t st) {
+    const long long work = (long long)S * (n + 1) * (n + 1);
+    const unsigned grid = (unsigned)((work + 255) / 256);
+    apply_operator_kernel<SolverVT, SolverST><<<grid, 256, 0, st>>>(n, S, a, a_fp64, a_n,
+                                                                     static_cast<const SolverVT*>(x),
+                                                                     static_cast<SolverVT*>(y));
+    g_launches.fetch_add(1, std::memory_order_relaxed);
+    return cudaGetLastError();
+}
+
+mlmc_status MLMC_SOLVER_NAME(noalloc_solve)(int n, int S, const void* a, int a_fp64, int a_n, double delta,
+                                            int max_iters, int qoi, const double* box, double f, double* Q,
+                                            int32_t* iters, double* relres, int32_t* flags, cudaStream_t st,
+                                            void* scratch, std::string& err) {
+    return noalloc_typed<SolverVT, SolverST>(n, S, a, a_fp64, a_n, delta, max_iters, qoi, box, f, MLMC_SOLVER_PREC, Q,
+                                             iters, relres, flags, st, scratch, err);
+}
+
+}  // namespace mlmc

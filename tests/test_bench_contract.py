@@ -1,5 +1,6 @@
 """The benchmark's reference arm on the host: `bench.py --impl reference` times the
-CPU oracle on a bounded sample and prints one JSON line with the keys the
+CPU oracle running the whole benchmark estimate (Alg. 4.1 on the 5-level
+hierarchy, same seed as the GPU arm) and prints one JSON line with the keys the
 benchmark contract names; a rank other than 0 prints nothing and exits 0."""
 import json
 import os
@@ -28,10 +29,13 @@ def test_reference_arm_prints_one_contract_line():
     cb = d["cpu_baseline"]
     assert cb["kind"] == "oracle" and cb["value"] == d["value"] and cb["cores"] >= 1 and cb["sample"]
     assert d["e2e"] == {"value": d["value"], "unit": "s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}
-    # N_l from the oracle's own pilot variances: at least the initial 100 samples per level, and
-    # decreasing with the level as the variances of the corrections do
-    N = d["config"]["N_l"]
+    # the GPU arm's workload and seed; N_l from Alg. 4.1's own variance estimates: at least the initial
+    # 100 samples per level, and decreasing with the level as the variances of the corrections do
+    import bench
+    assert d["config"] == {"workload": bench.workload_desc(), "seed": bench.SEED}
+    N = d["N_l"]
     assert len(N) == 5 and all(n >= 100 for n in N) and N[0] >= N[-1]
+    assert d["rmse"] <= bench.TOL * 1.01 and 0.035 < d["estimate"] < 0.1
 
 
 def test_reference_arm_other_ranks_exit_quietly():

@@ -296,10 +296,13 @@ def test_large_solve_pipeline_timeout_is_reported_and_gpu_stays_usable(M):
         M.mlmc_set_wait_timeout(h, 0.2)
         M.mlmc_debug_set_wait_extra(h, 1)
         M.mlmc_debug_set_solve_ring(h, 4)     # two systems would not turn the pipeline on by themselves
+        # the solve is asynchronous: the wait that ran out is reported by the next synchronising call
+        M.mlmc_level_solve(h, n, S, a, M.MLMC_FP32, n, M.MLMC_FP32, M.MLMC_CG, 1e-7, 100000, None, Q, None,
+                           None, fl)
         with pytest.raises(M.MlmcError) as ei:
-            M.mlmc_level_solve(h, n, S, a, M.MLMC_FP32, n, M.MLMC_FP32, M.MLMC_CG, 1e-7, 100000, None, Q, None,
-                               None, fl)
+            M.mlmc_sync(h)
         assert ei.value.status == M.MLMC_E_TIMEOUT
+        M.mlmc_sync(h)          # the error words were cleared by the read
         torch.cuda.synchronize()
         assert np.all(fl.cpu().numpy() == M.MLMC_F_TIMEOUT)
         M.mlmc_debug_set_wait_extra(h, 0)
@@ -597,5 +600,34 @@ def test_minres_with_multigrid_and_jacobi(M, prec):
             for U in (Um, Uj):
                 res = o_fem.relative_residual(n, af[s], _interior(n, U[s]))
                 assert res < (2 * delta if prec == "FP64" else delta * (1 + 1e-6))
+    finally:
+        M.mlmc_destroy(h)
+
+
+def test_two_asynchronous_solves_on_a_user_stream(M):
+    # mlmc_level_solve enqueues its launch and returns: two calls on a stream of the caller's, with no
+    # host synchronisation between them, share the context's workspace in call order on the device
+    h = _ctx(M)
+    try:
+        st = torch.cuda.Stream()
+        S, cases = 4, [(32, 71, M.MLMC_FP64, M.MLMC_FP64), (64, 72, M.MLMC_FP32, M.MLMC_FP32)]
+        outs = []
+        with torch.cuda.stream(st):
+            for n, seed, ap, prec in cases:
+                af = smooth_lognormal_field(n, S, seed=seed, log_sd=1.0)
+                a = to_dev(af, torch.float64 if ap == M.MLMC_FP64 else torch.float32)
+                Q = torch.empty(S, dtype=torch.float64, device=device())
+                fl = torch.zeros(S, dtype=torch.int32, device=device())
+                delta = fp64_delta(n) if prec == M.MLMC_FP64 else 1e-9
+                M.mlmc_level_solve(h, n, S, a, ap, n, prec, M.MLMC_CG, delta, 100000, None, Q, None, None, fl,
+                                   stream=st)
+                outs.append((n, af, a, Q, fl, prec))
+        M.mlmc_sync(h, st)
+        for n, af, a, Q, fl, prec in outs:
+            assert np.all(fl.cpu().numpy() == M.MLMC_F_CONVERGED)
+            tol = 1e-11 if prec == M.MLMC_FP64 else 1e-7
+            for s in range(S):
+                Qo = o_fem.solve_sample(n, af[s])[1]
+                assert abs(Q[s].item() - Qo) <= tol * abs(Qo)
     finally:
         M.mlmc_destroy(h)

@@ -60,6 +60,8 @@ def test_noalloc_matches_level_solve_on_two_calls_in_a_row(M):
         # n, S, master precision, inner precision, delta, qoi, box
         (64, 7, M.MLMC_FP64, M.MLMC_FP64, 1e-11, 0, None),
         (32, 13, M.MLMC_FP32, M.MLMC_FP16S, 1e-6, 1, (0.25, 0.75, 0.25, 0.75)),
+        # n = 128: one 512-thread CTA per system (the large-system class), BF16-stored coefficient
+        (128, 8, M.MLMC_FP32, M.MLMC_BF16S, 1e-6, 0, None),
     ]
     for i, (n, S, ap, prec, delta, qoi, box) in enumerate(cases):
         af = smooth_lognormal_field(n, S, seed=100 + i, log_sd=1.0)
@@ -80,3 +82,16 @@ def test_noalloc_rejects_batches_beyond_its_scratch(M):
         M.mlmc_level_solve_noalloc(0, n, S, a, M.MLMC_FP64, n, M.MLMC_FP64, 1e-8, 1000, 0, None, 1.0, Q)
     assert ei.value.status == M.MLMC_E_ARG
     assert "MLMC_NOALLOC_SCRATCH_BYTES" in M.mlmc_last_error(None)
+
+
+@pytest.mark.parametrize("box", [(0.25, 0.2, 0.25, 0.75), (0.25, 0.75, -0.25, 0.75), (0.25, 0.75, 0.25, 1.5),
+                                 (0.25, float("nan"), 0.25, 0.75), (0.3, 0.75, 0.25, 0.75)])
+def test_noalloc_rejects_bad_qoi_boxes(M, box):
+    # inverted, outside the unit square, not finite, or off the grid lines of n = 16 (0.3 * 16 = 4.8)
+    n, S = 16, 2
+    a = torch.ones((S, (n + 1) ** 2), dtype=torch.float64, device=device())
+    Q = torch.empty(S, dtype=torch.float64, device=device())
+    with pytest.raises(M.MlmcError) as ei:
+        M.mlmc_level_solve_noalloc(0, n, S, a, M.MLMC_FP64, n, M.MLMC_FP64, 1e-8, 1000, 1, box, 1.0, Q)
+    assert ei.value.status == M.MLMC_E_ARG
+    assert "box" in M.mlmc_last_error(None)
