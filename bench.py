@@ -227,6 +227,8 @@ def main():
                          "field synthesis and one resident-solve launch per step; kl-synth: tensor-core "
                          "KL synthesis alone at the single-level sweep shapes (n = 512, K = 128, corr 0.1)")
     ap.add_argument("--kl-samples", type=int, default=4096)
+    ap.add_argument("--kl-prec", default="FP32", choices=["FP32", "FP64TC"],
+                    help="kl-synth: output of the tensor-core synthesis")
     ap.add_argument("--sweep-samples", type=int, default=4096,
                     help="sweep: systems per batch (n = 512, K = 128, corr 0.1, fixed delta 1e-6)")
     ap.add_argument("--sweep-delta", type=float, default=1e-6,
@@ -450,27 +452,30 @@ def main():
 
 
 def kl_synth_case(M, torch, dev, args, hbm_peak, peak_src, flush, stream):
-    """Tensor-core KL synthesis alone: S samples on the 512 x 512 grid, K = 128, corr 0.1."""
+    """Tensor-core KL synthesis alone: S samples on the 512 x 512 grid, K = 128, corr 0.1, FP32 output
+    (--kl-prec FP32) or the FP64 output of the exact-lead form (--kl-prec FP64TC)."""
     S, n, K = args.kl_samples, 512, 128
+    fprec = getattr(M, "MLMC_" + args.kl_prec)
     prob = M.make_problem(n0=n, m=2, L_max=0, kind=0, K=K, sigma2=1.0, corr_len=0.1, seed=7)
     h = M.mlmc_create(prob, dev.index or 0)
     try:
         M.mlmc_profile_enable(h, True)
-        a = torch.empty((S, (n + 1) ** 2), dtype=torch.float32, device=dev)
+        a = torch.empty((S, (n + 1) ** 2), dtype=torch.float32 if fprec == M.MLMC_FP32 else torch.float64,
+                        device=dev)
         xi = torch.empty((S, K), dtype=torch.float64, device=dev)
-        M.mlmc_sample_fields(h, 0, 0, S, xi, a, M.MLMC_FP32)
+        M.mlmc_sample_fields(h, 0, 0, S, xi, a, fprec)
         for s in range(args.warmup + args.steps):
             if s == args.warmup:
                 M.mlmc_profile_reset(h)
             flush.fill_(float(s))
-            M.mlmc_synthesize_fields(h, 0, S, xi, a, M.MLMC_FP32)
+            M.mlmc_synthesize_fields(h, 0, S, xi, a, fprec)
         prof = M.mlmc_profile_get(h)
     finally:
         M.mlmc_destroy(h)
     ms = prof["kl_ms"] / prof["kl_launches"]
     gbs = prof["kl_bytes"] / prof["kl_launches"] / (ms * 1e-3) / 1e9
     tf = prof["kl_flops"] / prof["kl_launches"] / (ms * 1e-3) / 1e12
-    print(json.dumps({"case": "kl-synth", "samples": S, "n": n, "K": K, "ms_per_launch": ms,
+    print(json.dumps({"case": "kl-synth", "prec": args.kl_prec, "samples": S, "n": n, "K": K, "ms_per_launch": ms,
                       "algorithmic_bytes_per_launch": prof["kl_bytes"] / prof["kl_launches"], "achieved_gbs": gbs,
                       "hbm_frac": gbs / hbm_peak, "executed_tensor_tflops": tf, "peak_source": peak_src}))
     return 0

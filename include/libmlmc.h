@@ -56,7 +56,9 @@ typedef enum {
     MLMC_FP64 = 0,    /* inner FP64, coefficient FP64 (plain double solve)       */
     MLMC_FP32 = 1,    /* inner FP32, coefficient stored FP32                     */
     MLMC_BF16S = 2,   /* inner FP32, coefficient stored bfloat16                 */
-    MLMC_FP16S = 3    /* inner FP32, coefficient stored IEEE half                */
+    MLMC_FP16S = 3,   /* inner FP32, coefficient stored IEEE half                */
+    MLMC_FP64TC = 4   /* fields only: FP64 field from the tensor-core contraction
+                         (see mlmc_sample_fields); not an inner precision        */
 } mlmc_prec;
 
 typedef enum { MLMC_CG = 0, MLMC_MINRES = 1 } mlmc_solver;
@@ -126,11 +128,19 @@ int64_t mlmc_launch_count(void);                  /* kernels launched by this li
  * Wichura's AS241 inverse normal; sample indices are first .. first+S-1.
  * a[s][v] = exp(sum_k xi[s][k] Phi_k(x_v)) on the (n_l+1)^2 nodes of level l.
  *   xi    device FP64 [S][K], out (may be NULL when not wanted)
- *   a     device [S][(n_l+1)^2] dense nodal layout, out; FP64 if field_prec ==
- *         MLMC_FP64 (FP64 contraction and exp), else FP32 (tensor-core
- *         contraction with split FP16 operands and FP32 accumulation, then exp)
+ *   a     device [S][(n_l+1)^2] dense nodal layout, out, by field_prec:
+ *         MLMC_FP64   FP64; contraction and exp on the FP64 pipe (plain FP64 form);
+ *         MLMC_FP32   FP32; tensor-core contraction with split FP16 operands
+ *                     (hi + 2^-11 lo) and FP32 accumulation, then expf: about
+ *                     1e-6 relative error;
+ *         MLMC_FP64TC FP64; tensor-core contraction with an exactly accumulated
+ *                     integer lead slice and two FP16 correction slices per
+ *                     operand, log a as a float-float pair, exp in float-float
+ *                     (Tang's table-driven method): log a within about 1e-9
+ *                     (a bound in terms of sum |xi_k| and sum |Phi_k| is given
+ *                     in kl_tc.cu), the master coefficient of the mixed form.
  * S = 0 is a no-op.  Errors: MLMC_E_ARG for level outside [0, L_max], S < 0,
- * null a with S > 0, field_prec not FP64/FP32. */
+ * null a with S > 0, field_prec not FP64/FP32/FP64TC. */
 mlmc_status mlmc_sample_fields(mlmc_ctx* ctx, int level, uint64_t first, int S,
                                double* xi, void* a, mlmc_prec field_prec, void* stream);
 
@@ -288,6 +298,9 @@ typedef struct {
     int max_rounds;        /* safety cap on Alg. 4.1 rounds                                          */
     const int64_t* fixed_N;/* non-NULL: no adaptivity, exactly fixed_N[l] samples on levels 0..L_start */
     double contrast;       /* contrast estimate for the precision rule (<= 0: 1)                     */
+    int mixed_field;       /* master coefficient of the mixed form: MLMC_FP64TC (default; FP64 from
+                              the tensor cores, as the FP64 refinement residual of Alg. 2.1 needs) or
+                              MLMC_FP32 (the FP32 tensor-core field, about 1e-6 relative)            */
 } mlmc_options;
 
 typedef struct {
@@ -313,7 +326,8 @@ typedef struct {
 } mlmc_result;
 
 /* Fill *opts with the paper's defaults: kp 0.05, (2,1,4,2), alpha 2, gamma 2,
- * r 1, N_init 100, L_start 1, mixed form, CG, fixed_delta 1e-10. */
+ * r 1, N_init 100, L_start 1, mixed form with an MLMC_FP64TC master field, CG,
+ * fixed_delta 1e-10. */
 void mlmc_default_options(mlmc_options* opts);
 
 /* Run Alg. 4.1 on the GPU; synchronises; results in *res (host). */
@@ -336,8 +350,9 @@ mlmc_status mlmc_estimate_host(int m, int L_max, int n0, const mlmc_options* opt
  * G_v = -(1/3) sum_{T contains v} |T| grad(lambda_h).grad(u_h)|_T and
  * dQ/dxi[s][k] = sum_v Phi_k(x_v) a_v G_v (the transposed KL contraction).
  * u is recomputed here rather than kept from an earlier forward pass (the
- * autograd wrapper's forward stores only Q).  The field is FP64 when
- * prec == MLMC_FP64, else FP32 from the tensor-core synthesis.
+ * autograd wrapper's forward stores only Q).  The field is FP64: from the FP64
+ * contraction when prec == MLMC_FP64, else from the tensor-core contraction
+ * (MLMC_FP64TC of mlmc_sample_fields).
  *   Q      device FP64 [S] out;  dQdxi  device FP64 [S][K] out
  * Asynchronous like mlmc_level_solve: results are valid once `stream` has been
  * synchronised. */

@@ -20,12 +20,13 @@ class MlmcQoI(torch.autograd.Function):
             raise ValueError("xi must be a CUDA tensor")
         xi = xi.detach().to(torch.float64).contiguous()
         S = xi.shape[0]
-        field_prec = L.MLMC_FP64 if prec == L.MLMC_FP64 else L.MLMC_FP32
-        dt = torch.float64 if field_prec == L.MLMC_FP64 else torch.float32
-        a = torch.empty((S, (n + 1) * (n + 1)), dtype=dt, device=xi.device)
+        # the same FP64 master field as the backward pass: FP64 contraction for the FP64 solve, the
+        # tensor-core FP64 field for the mixed-precision solves
+        field_prec = L.MLMC_FP64 if prec == L.MLMC_FP64 else L.MLMC_FP64TC
+        a = torch.empty((S, (n + 1) * (n + 1)), dtype=torch.float64, device=xi.device)
         L.mlmc_synthesize_fields(handle, level, S, xi, a, field_prec)
         Q = torch.empty(S, dtype=torch.float64, device=xi.device)
-        L.mlmc_level_solve(handle, n, S, a, field_prec, n, prec, L.MLMC_CG, delta, max_iters, None, Q)
+        L.mlmc_level_solve(handle, n, S, a, L.MLMC_FP64, n, prec, L.MLMC_CG, delta, max_iters, None, Q)
         fctx.save_for_backward(xi)
         fctx.cfg = (handle, level, prec, delta, max_iters)
         return Q

@@ -141,7 +141,8 @@ int level_n(const mlmc_problem& p, int l) {
     return (int)n;
 }
 
-bool is_field_prec(mlmc_prec p) { return p == MLMC_FP64 || p == MLMC_FP32; }
+bool is_field_prec(mlmc_prec p) { return p == MLMC_FP64 || p == MLMC_FP32 || p == MLMC_FP64TC; }
+bool is_master_prec(mlmc_prec p) { return p == MLMC_FP64 || p == MLMC_FP32; }   // element type of a stored field
 bool is_prec(int p) { return p >= MLMC_FP64 && p <= MLMC_FP16S; }
 
 mlmc_status fail(mlmc_ctx* ctx, mlmc_status code, const std::string& msg) {
@@ -186,8 +187,9 @@ mlmc_status synth(mlmc_ctx* ctx, int level, int S, const double* xi, void* a, ml
                   cudaStream_t st) {
     const int n = level_n(ctx->prob, level);
     GridBasis& gb = ctx->basis.at(n);
-    cudaError_t e = (field_prec == MLMC_FP64) ? launch_kl_fp64(gb, S, xi, static_cast<double*>(a), st)
-                                              : launch_kl_fp32(ctx, gb, S, xi, static_cast<float*>(a), st);
+    cudaError_t e = (field_prec == MLMC_FP64)     ? launch_kl_fp64(gb, S, xi, static_cast<double*>(a), st)
+                    : (field_prec == MLMC_FP64TC) ? launch_kl_tc64(ctx, gb, S, xi, static_cast<double*>(a), st)
+                                                  : launch_kl_fp32(ctx, gb, S, xi, static_cast<float*>(a), st);
     if (e != cudaSuccess) return fail(ctx, MLMC_E_CUDA, std::string("KL synthesis: ") + cudaGetErrorString(e));
     return MLMC_OK;
 }
@@ -306,6 +308,10 @@ mlmc_status check_options(const mlmc_options* o, int L_max, std::string& err) {
         err = "options: bad form, precision, solver or max_iters";
         return MLMC_E_ARG;
     }
+    if (o->mixed_field != MLMC_FP64TC && o->mixed_field != MLMC_FP32) {
+        err = "options: mixed_field must be MLMC_FP64TC or MLMC_FP32";
+        return MLMC_E_ARG;
+    }
     if (o->fixed_N)
         for (int l = 0; l <= o->L_start; ++l)
             if (o->fixed_N[l] < 1) { err = "fixed_N entries must be >= 1"; return MLMC_E_ARG; }
@@ -378,6 +384,8 @@ void mlmc_destroy(mlmc_ctx* ctx) {
     for (auto& kv : ctx->basis) {
         kv.second.phi64.release();
         kv.second.phi16.release();
+        kv.second.phix.release();
+        kv.second.ev.release();
     }
     for (auto& p : ctx->prof.kl_pending) {
         cudaEventDestroy(p.a);
@@ -544,8 +552,8 @@ mlmc_status mlmc_synthesize_fields(mlmc_ctx* ctx, int level, int S, const double
 
 mlmc_status mlmc_apply_operator(int n, int S, const void* a, mlmc_prec a_prec, int a_n, mlmc_prec op_prec,
                                 const void* x, void* y, mlmc_prec vec_prec, void* stream) {
-    if (n < 2 || S < 0 || a_n < n || a_n % n != 0 || !is_field_prec(a_prec) || !is_prec(op_prec) ||
-        !is_field_prec(vec_prec))
+    if (n < 2 || S < 0 || a_n < n || a_n % n != 0 || !is_master_prec(a_prec) || !is_prec(op_prec) ||
+        !is_master_prec(vec_prec))
         return MLMC_E_ARG;
     if ((op_prec == MLMC_FP64) != (vec_prec == MLMC_FP64)) return MLMC_E_ARG;
     if (S == 0) return MLMC_OK;
@@ -559,7 +567,7 @@ mlmc_status mlmc_level_solve(mlmc_ctx* ctx, int n, int S, const void* a, mlmc_pr
                              mlmc_prec prec, mlmc_solver solver, double delta, int max_iters, double* u,
                              double* Q, int32_t* iters, double* relres, int32_t* flags, void* stream) {
     if (!ctx) return MLMC_E_ARG;
-    if (n < 2 || n > 2048 || S < 0 || a_n < n || a_n % n != 0 || !is_field_prec(a_prec) || !is_prec(prec) ||
+    if (n < 2 || n > 2048 || S < 0 || a_n < n || a_n % n != 0 || !is_master_prec(a_prec) || !is_prec(prec) ||
         (solver != MLMC_CG && solver != MLMC_MINRES) || !(delta > 0) || max_iters < 1)
         return fail(ctx, MLMC_E_ARG, "level_solve: bad n, S, a_n, precision, solver, delta or max_iters");
     if (S == 0) return MLMC_OK;
@@ -654,6 +662,7 @@ void mlmc_default_options(mlmc_options* o) {
     o->max_rounds = 100;
     o->fixed_N = nullptr;
     o->contrast = 1.0;
+    o->mixed_field = MLMC_FP64TC;
 }
 
 mlmc_status mlmc_estimate_host(int m, int L_max, int n0, const mlmc_options* opts, mlmc_sampler_fn sampler,
@@ -683,8 +692,10 @@ mlmc_status mlmc_estimate(mlmc_ctx* ctx, const mlmc_options* opts, mlmc_result* 
     const int K = p.field.K;
     const cudaStream_t st = nullptr;
     MLMC_CUDA_RET(ctx->err, ctx_order_begin(ctx, st));
-    const mlmc_prec field_prec = (o.form == MLMC_FORM_MIXED) ? MLMC_FP32 : MLMC_FP64;
-    const size_t felem = field_prec == MLMC_FP64 ? sizeof(double) : sizeof(float);
+    // the master coefficient: FP64 on the FP64 pipe for the FP64 forms; for the mixed form the option's
+    // tensor-core field (FP64 to about 1e-9 in log a by default, or FP32)
+    const mlmc_prec field_prec = (o.form == MLMC_FORM_MIXED) ? (mlmc_prec)o.mixed_field : MLMC_FP64;
+    const size_t felem = field_prec == MLMC_FP32 ? sizeof(float) : sizeof(double);
     int32_t flags_or = 0;
     std::vector<int64_t> iters_lvl(MLMC_MAX_LEVELS, 0), dofs_lvl(MLMC_MAX_LEVELS, 0);
     std::vector<int32_t> prec_lvl(MLMC_MAX_LEVELS, -1);
@@ -751,7 +762,7 @@ mlmc_status mlmc_estimate(mlmc_ctx* ctx, const mlmc_options* opts, mlmc_result* 
             gf.n = n;
             gf.S = req[i].count;
             gf.a = fb + foff[i];
-            gf.a_fp64 = field_prec == MLMC_FP64;
+            gf.a_fp64 = field_prec != MLMC_FP32;
             gf.a_n = n;
             gf.delta = df[l];
             gf.Q = Qf + qoff[i];
@@ -884,8 +895,10 @@ mlmc_status mlmc_adjoint_grad(mlmc_ctx* ctx, int level, int S, const double* xi,
     MLMC_CUDA_RET(ctx->err, ctx_order_begin(ctx, st));
     const int n = level_n(ctx->prob, level);
     const size_t V = (size_t)(n + 1) * (n + 1);
-    const mlmc_prec fp = (prec == MLMC_FP64) ? MLMC_FP64 : MLMC_FP32;
-    const size_t felem = fp == MLMC_FP64 ? sizeof(double) : sizeof(float);
+    // the master coefficient is FP64: on the FP64 pipe for the FP64 solve, from the tensor cores
+    // (exact lead slice, about 1e-9 in log a) for the mixed-precision solves
+    const mlmc_prec fp = (prec == MLMC_FP64) ? MLMC_FP64 : MLMC_FP64TC;
+    const size_t felem = sizeof(double);
     // layout: a [S][V] (field precision) | u [S][V] | lam [S][V] | w [S][V] (FP64)
     const size_t abytes = (S * V * felem + 255) / 256 * 256;
     MLMC_CUDA_RET(ctx->err, ctx->ws.adj.reserve(abytes + 3 * S * V * sizeof(double)));
@@ -909,7 +922,7 @@ mlmc_status mlmc_adjoint_grad(mlmc_ctx* ctx, int level, int S, const double* xi,
     gf.n = n;
     gf.S = S;
     gf.a = a;
-    gf.a_fp64 = fp == MLMC_FP64;
+    gf.a_fp64 = 1;
     gf.a_n = n;
     gf.delta = delta;
     gf.Q = Q;
@@ -923,7 +936,7 @@ mlmc_status mlmc_adjoint_grad(mlmc_ctx* ctx, int level, int S, const double* xi,
     cfg.max_iters = max_iters;
     s = launch_solve_async(ctx, {gf, ga}, cfg, st);
     if (s != MLMC_OK) return s;
-    MLMC_CUDA_RET(ctx->err, launch_adjoint_elements(n, S, a, fp == MLMC_FP64, u, lam, w, st));
+    MLMC_CUDA_RET(ctx->err, launch_adjoint_elements(n, S, a, 1, u, lam, w, st));
     MLMC_CUDA_RET(ctx->err, launch_kl_transpose_fp64(ctx->basis.at(n), S, w, dQdxi, st));
     MLMC_CUDA_RET(ctx->err, ctx_order_end(ctx, st));
     return MLMC_OK;

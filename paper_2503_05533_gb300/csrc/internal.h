@@ -54,6 +54,8 @@ struct GridBasis {
     int Kpad = 0;          // K rounded up to 64 (16-bit K-major rows of 128 B)
     DevBuf phi64;          // FP64 [K][nodes_pad]
     DevBuf phi16;          // FP16 [2][nodes_pad][Kpad]: hi rows then lo rows, Phi = hi + lo 2^-11 (K-major)
+    DevBuf phix;           // FP16 [3][nodes_pad][Kpad]: exact-lead slices of the FP64-output synthesis (lazy)
+    DevBuf ev;             // int [nodes_pad]: their per-node power-of-two exponents
 };
 
 constexpr int kSolveSlots = 4;   // solve batches that may run concurrently (one per precision class)
@@ -139,6 +141,9 @@ cudaError_t launch_kl_fp64(const GridBasis& gb, int S, const double* xi, double*
 // kl_tc.cu: tensor-core synthesis into FP32
 cudaError_t launch_kl_fp32(mlmc_ctx* ctx, const GridBasis& gb, int S, const double* xi, float* a,
                            cudaStream_t st);
+// kl_tc.cu: tensor-core synthesis into FP64 (exact integer lead slice, float-float exp); builds the
+// grid's exact-lead basis slices on first use
+cudaError_t launch_kl_tc64(mlmc_ctx* ctx, GridBasis& gb, int S, const double* xi, double* a, cudaStream_t st);
 cudaError_t launch_kl_transpose_fp64(const GridBasis& gb, int S, const double* w, double* out,
                                      cudaStream_t st);
 // stencil / solver (solver.cu)

@@ -1,27 +1,58 @@
-// A2 on the tensor cores: a[s][v] = exp(sum_k xi[s][k] Phi[k][v]) in FP32.
+// A2 on the tensor cores: a[s][v] = exp(sum_k xi[s][k] Phi[k][v]) (Sec. 5.1,
+// Eq. (5.2); the KL field of the configurations) as a (samples x KL terms) x
+// (KL terms x nodes) contraction on tcgen05 with FP16 operands and FP32
+// accumulation in tensor memory, in two forms:
 //
-// The contraction (samples x KL terms) x (KL terms x nodes) runs on tcgen05
-// with FP16 operands and FP32 accumulation.  FP16 alone would give ~1e-3
-// relative error in log a, so both operands are split, x = hi + lo 2^-11
-// (hi = fp16(x), lo = fp16((x - hi) 2^11), which keeps lo in FP16's normal
-// range), and two TMEM accumulators hold
-//   D1 = xi_hi Phi_hi^T,   D2 = xi_hi Phi_lo^T + xi_lo Phi_hi^T,
-// so log a = D1 + 2^-11 D2 with the lo*lo term (2^-22 relative) dropped.
+// FP32 output.  Both operands are split x = hi + lo 2^-11 (hi = fp16(x),
+// lo = fp16((x - hi) 2^11), which keeps lo in FP16's normal range) and two
+// accumulators hold D0 = xi_hi Phi_hi^T and D1 = xi_hi Phi_lo^T + xi_lo Phi_hi^T
+// over all K; log a = D0 + 2^-11 D1 (the lo*lo term, 2^-22 relative, dropped)
+// and a = expf(log a).  About 1e-6 relative error in a.
 //
-// One CTA computes a 128-sample x 128-node tile.  Thread 0 streams 64-term K
-// blocks of the four operand tiles with TMA (128-byte swizzle) into shared
-// memory and issues the MMAs (M = 128, N = 128, K = 16); tcgen05.commit
-// signals completion through an mbarrier.  The four warps then read their 32
-// TMEM lanes (one sample each), form exp(D1 + 2^-11 D2), and write the tile
-// through a shared-memory transpose so that stores are row-contiguous.
-// Every mbarrier wait is bounded in wall time; on expiry the CTA records an
-// error word, waits (bounded) for its own copies in flight, frees its TMEM
-// and returns.
+// FP64 output (the master coefficient of the mixed-precision solves, where the
+// refinement residual of Alg. 2.1 is FP64).  Each sample row of xi is scaled by
+// a power of two 2^-e_s so that its largest entry lies in [1/2, 1), and each
+// node's column of Phi likewise by 2^-e_v; the scaled values times 2^9 are
+// split into an integer lead slice (|lead| <= 512, exact in FP16) and two FP16
+// slices h and l of the remainder (X = lead + h + 2^-11 l up to 2^-23 for
+// |X| <= 512).  Three accumulators hold, per 64-term K block,
+//   E0 = lead_x lead_y^T                                  (integers below 2^24:
+//        exact in FP32, whatever order the tensor core adds them in),
+//   E1 = lead_x h_y^T + h_x lead_y^T + h_x h_y^T,
+//   E2 = lead_x l_y^T + l_x lead_y^T + h_x l_y^T + l_x h_y^T,
+// and the epilogue adds the K blocks: E0 as exact 32-bit integers, E1 + 2^-11 E2
+// in FP32, then log a = 2^(e_s + e_v - 18) (sum E0 + sum (E1 + 2^-11 E2)) as a
+// float-float pair.  The slices represent each operand to 2^-23 of |X| <= 512,
+// which bounds the log-a error by 2^-32 (2^e_v sum_k |xi_k| + 2^e_s sum_k
+// |Phi_k(x_v)|) + K 2^(e_s + e_v - 42); the FP32 accumulation of E1 (terms at
+// most 2^-9 of the E0 scale, at most 12 additions per K block) adds at most
+// about six times that; E0 adds nothing.  Rounding errors of opposite signs
+// cancel, and the error is typically near 1e-10.
+// a = exp(log a) is formed in float-float arithmetic by the table-driven method
+// of P. T. P. Tang (ACM TOMS 15(2), 1989): N = round(32 log a / ln 2),
+// r = log a - N ln 2 / 32 with ln 2 / 32 split into three parts so that the
+// reduction is exact to float-float precision, exp(r) - 1 by its Taylor
+// polynomial to r^5 (|r| <= ln 2 / 64), times the table value 2^(j/32) stored as
+// a float-float pair and 2^((N - j) / 32); the pair is written as one FP64
+// value.  The FP32 pipe does all of this work: GB300's FP64 pipe is narrow.
+//
+// Execution: a persistent kernel, one CTA per SM walking output tiles of 128
+// samples x TN nodes.  Warp 0 streams the operand slices of every 64-term K
+// block by TMA (128-byte swizzle) through a ring of shared-memory stages;
+// warp 1 issues the MMAs (M = 128, N = TN, K = 16) into one of two tensor-
+// memory buffers and signals through mbarriers; warps 2-5 drain the other
+// buffer (each warp its 32 TMEM lanes, one sample per lane), form the output
+// and write it through a shared-memory transpose so that stores are
+// row-contiguous.  Loads of tile t+1 and the epilogue of tile t overlap its
+// MMAs.  Every mbarrier wait is bounded in wall time; on expiry the CTA records
+// the context's error word, every role leaves its loop, the producer waits
+// (bounded) for its copies in flight, and the TMEM is freed.
 #include <cuda.h>
 #include <cuda_fp16.h>
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <cmath>
 #include <cstring>
 
 #include "device_common.cuh"
@@ -31,15 +62,44 @@ namespace mlmc {
 namespace {
 
 constexpr int TM = 128;              // samples per tile (MMA M, TMEM lanes)
-constexpr int TN = 128;              // nodes per tile (MMA N)
 constexpr int TKB = 64;              // terms per K block: 64 FP16 = one 128-byte swizzle row
-constexpr int kTmemCols = 256;       // D1 in columns [0, 128), D2 in [128, 256)
-constexpr uint32_t kTileBytes = TM * TKB * 2;                  // 16 KiB (A tile; B tile is the same size)
-constexpr uint32_t kOffAhi = 0, kOffAlo = kTileBytes, kOffBhi = 2 * kTileBytes, kOffBlo = 3 * kTileBytes;
-constexpr uint32_t kOffStage = 4 * kTileBytes;                 // 4 warps x 32 x 33 floats
-constexpr uint32_t kStageBytes = 4 * 32 * 33 * 4;
-constexpr uint32_t kOffBar = kOffStage + kStageBytes;          // 2 mbarriers + TMEM slot + status
-constexpr uint32_t kSmemBytes = kOffBar + 64 + 1024;           // + 1 KiB for 1024-byte alignment
+constexpr int kThreads = 192;        // warp 0: TMA, warp 1: MMA, warps 2-5: epilogue
+constexpr uint32_t kATile = TM * TKB * 2;   // 16 KiB: one slice of 128 sample rows
+
+// MODE 0: FP32 output (2 slices per operand); MODE 1: FP64 output (3 slices, exact lead).
+template <int MODE> struct KLCfg;
+template <> struct KLCfg<0> {
+    static constexpr int NA = 2, NB = 2, TN = 128, NACC = 2, NSTAGE = 3;
+    static constexpr bool DRAIN = false;   // accumulate the whole K range in TMEM
+    using Out = float;
+};
+template <> struct KLCfg<1> {
+    static constexpr int NA = 3, NB = 3, TN = 64, NACC = 3, NSTAGE = 2;
+    static constexpr bool DRAIN = true;    // the epilogue drains every K block
+    using Out = double;
+};
+
+template <int MODE> struct KLLayout {
+    using C = KLCfg<MODE>;
+    static constexpr uint32_t kBTile = C::TN * TKB * 2;
+    static constexpr uint32_t kStage = C::NA * kATile + C::NB * kBTile;   // multiple of 1024
+    static constexpr uint32_t kOffStg = C::NSTAGE * kStage;               // epilogue transpose staging
+    static constexpr uint32_t kStgBytes = 4 * 32 * 33 * sizeof(typename C::Out);
+    static constexpr uint32_t kOffBar = (kOffStg + kStgBytes + 15) / 16 * 16;
+    // full[NSTAGE], empty[NSTAGE], tfull[2], tempty[2], then the TMEM address and the abort flag
+    static constexpr uint32_t kBarBytes = 8 * (2 * C::NSTAGE + 4) + 16;
+    static constexpr uint32_t kSmem = kOffBar + kBarBytes + 1024;          // + 1 KiB for 1024-byte alignment
+    static constexpr uint32_t kTmemCols = 512;                             // 2 buffers x NACC x TN <= 512
+    static_assert(2 * C::NACC * C::TN <= 512, "tensor memory");
+    static_assert(kSmem <= 227 * 1024, "shared memory");
+};
+
+// Float-float exponential tables (host-computed): 2^(j/32) = th[j] + tl[j]; ln 2 / 32 = l1 + l2 + l3
+// with l1 of at most 12 significant bits; inv = 32 / ln 2.
+struct FFExp {
+    float th[32], tl[32];
+    float l1, l2, l3, inv;
+};
 
 __device__ __forceinline__ void tma_load_2d(void* dst, const CUtensorMap* map, int c0, int c1, uint64_t* bar) {
     asm volatile(
@@ -59,16 +119,19 @@ __device__ __forceinline__ uint64_t desc_sw128(uint32_t saddr) {
     d |= (uint64_t)2 << 61;
     return d;
 }
-// Instruction descriptor, kind::f16: D FP32, A and B FP16, both K-major, N = 128, M = 128.
-constexpr uint32_t kIdesc = (1u << 4) | (0u << 7) | (0u << 10) | ((uint32_t)(TN >> 3) << 17) |
-                            ((uint32_t)(TM >> 4) << 24);
+// Instruction descriptor, kind::f16: D FP32, A and B FP16, both K-major, M = 128, N = TN.
+template <int TN>
+constexpr uint32_t idesc() {
+    return (1u << 4) | (0u << 7) | (0u << 10) | ((uint32_t)(TN >> 3) << 17) | ((uint32_t)(TM >> 4) << 24);
+}
 
+template <int TN>
 __device__ __forceinline__ void mma_f16(uint32_t tmem_d, uint64_t adesc, uint64_t bdesc, uint32_t accum) {
     asm volatile(
         "{\n\t.reg .pred p;\n\t"
         "setp.ne.b32 p, %4, 0;\n\t"
         "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}" ::"r"(tmem_d),
-        "l"(adesc), "l"(bdesc), "r"(kIdesc), "r"(accum));
+        "l"(adesc), "l"(bdesc), "r"(idesc<TN>()), "r"(accum));
 }
 __device__ __forceinline__ void mma_commit(uint64_t* bar) {
     asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(smem_u32(bar))
@@ -85,109 +148,367 @@ __device__ __forceinline__ void tmem_ld_x32(uint32_t taddr, uint32_t (&r)[32]) {
           "=r"(r[24]), "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
         : "r"(taddr));
 }
+__device__ __forceinline__ void tmem_wait_ld() { asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory"); }
+__device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
+__device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
 
-__global__ void __launch_bounds__(128, 1) kl_tc_kernel(const __grid_constant__ CUtensorMap mapA,
-                                                       const __grid_constant__ CUtensorMap mapB, int S, int Spad,
-                                                       int V, int Vpad, int Kpad, int num_m,
-                                                       float* __restrict__ out, unsigned* err,
-                                                       unsigned long long timeout_ns, unsigned extra_tx) {
+// Bounded wait that also gives up once another role has aborted the CTA.
+__device__ __forceinline__ bool kl_wait(uint64_t* bar, uint32_t parity, volatile int* abort, unsigned* err,
+                                        uint64_t timeout_ns) {
+    if (mbar_try_wait(bar, parity)) return true;
+    const uint64_t t0 = global_ns();
+    while (!mbar_try_wait(bar, parity)) {
+        if (*abort) return false;
+        if (global_ns() - t0 > timeout_ns) {
+            *abort = 1;
+            atomicCAS(err, KERR_NONE, KERR_TIMEOUT);
+            return false;
+        }
+    }
+    return true;
+}
+
+// The same wait for a whole warp: lane 0 waits (bounded), the warp agrees on the outcome, and on
+// success every lane observes the completed phase itself (at once: it has completed), so that the
+// warp's later .sync.aligned tensor-memory loads are never split by a timeout.
+__device__ __forceinline__ bool kl_warp_wait(uint64_t* bar, uint32_t parity, volatile int* abort, unsigned* err,
+                                             uint64_t timeout_ns) {
+    bool ok = false;
+    if ((threadIdx.x & 31) == 0) ok = kl_wait(bar, parity, abort, err, timeout_ns);
+    ok = __shfl_sync(0xffffffffu, ok ? 1 : 0, 0) != 0;
+    if (ok) mbar_wait(bar, parity, timeout_ns);
+    return ok;
+}
+
+// ---- float-float arithmetic (explicit round-to-nearest operations: never contracted)
+__device__ __forceinline__ void two_sum(float a, float b, float& s, float& e) {
+    s = __fadd_rn(a, b);
+    const float bb = __fsub_rn(s, a);
+    e = __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb));
+}
+__device__ __forceinline__ void fast_two_sum(float a, float b, float& s, float& e) {   // |a| >= |b|
+    s = __fadd_rn(a, b);
+    e = __fsub_rn(b, __fsub_rn(s, a));
+}
+__device__ __forceinline__ void two_prod(float a, float b, float& p, float& e) {
+    p = __fmul_rn(a, b);
+    e = __fmaf_rn(a, b, -p);
+}
+
+// exp(xh + xl) as a float-float pair (Tang's table-driven method, see the file comment).
+__device__ __forceinline__ void ff_exp(float xh, float xl, const FFExp& T, float& rh, float& rl) {
+    const int N = __float2int_rn(__fmul_rn(xh, T.inv));
+    const float nf = (float)N;
+    const int j = N & 31;
+    const int m = (N - j) / 32;
+    // r = x - N ln2/32: xh - N l1 is exact (N l1 has at most 24 bits and is within a factor 2 of xh)
+    const float t = __fsub_rn(xh, __fmul_rn(nf, T.l1));
+    float p, pe, s, se;
+    two_prod(nf, T.l2, p, pe);
+    two_sum(t, -p, s, se);
+    const float lo = __fsub_rn(__fadd_rn(se, xl), __fmaf_rn(nf, T.l3, pe));
+    float r, rlo;
+    fast_two_sum(s, lo, r, rlo);
+    // exp(r) - 1 = r + r^2/2 + r^3 (1/6 + r (1/24 + r/120))
+    float sq, sqe;
+    two_prod(r, r, sq, sqe);
+    const float r3 = __fmul_rn(__fmul_rn(sq, r),
+                               __fmaf_rn(r, __fmaf_rn(r, 1.0f / 120.0f, 1.0f / 24.0f), 1.0f / 6.0f));
+    float qh, qe;
+    two_sum(r, __fmul_rn(0.5f, sq), qh, qe);
+    const float ql0 = __fadd_rn(__fadd_rn(qe, rlo), __fadd_rn(__fmaf_rn(0.5f, sqe, __fmul_rn(r, rlo)), r3));
+    float q, ql;
+    fast_two_sum(qh, ql0, q, ql);
+    // 2^(j/32) (1 + q)
+    const float th = T.th[j], tl = T.tl[j];
+    float ph, phe, s1, s1e;
+    two_prod(th, q, ph, phe);
+    two_sum(th, ph, s1, s1e);
+    const float lo2 = __fadd_rn(__fadd_rn(s1e, phe), __fmaf_rn(th, ql, __fmaf_rn(tl, q, tl)));
+    float h, l;
+    fast_two_sum(s1, lo2, h, l);
+    rh = ldexpf(h, m);
+    rl = ldexpf(l, m);
+}
+
+template <int MODE>
+__global__ void __launch_bounds__(kThreads, 1)
+    kl_tc_kernel(const __grid_constant__ CUtensorMap mapA, const __grid_constant__ CUtensorMap mapB, int S, int Spad,
+                 int V, int Vpad, int Kpad, int num_m, int num_tiles, const int* __restrict__ es,
+                 const int* __restrict__ ev, const __grid_constant__ FFExp ffx, typename KLCfg<MODE>::Out* __restrict__ out,
+                 unsigned* err, unsigned long long timeout_ns, unsigned extra_tx) {
+    using C = KLCfg<MODE>;
+    using Lay = KLLayout<MODE>;
+    using Out = typename C::Out;
+    constexpr int TN = C::TN;
     extern __shared__ uint8_t smem_raw[];
     uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
-    uint64_t* bar_full = reinterpret_cast<uint64_t*>(smem + kOffBar);
-    uint64_t* bar_done = bar_full + 1;
-    uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(bar_full + 2);
-    uint32_t* status = tmem_slot + 1;
-    float* stage = reinterpret_cast<float*>(smem + kOffStage);
+    uint64_t* full = reinterpret_cast<uint64_t*>(smem + Lay::kOffBar);
+    uint64_t* empty = full + C::NSTAGE;
+    uint64_t* tfull = empty + C::NSTAGE;
+    uint64_t* tempty = tfull + 2;
+    uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(tempty + 2);
+    volatile int* abort = reinterpret_cast<volatile int*>(tmem_slot + 1);
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int m_tile = blockIdx.x % num_m, n_tile = blockIdx.x / num_m;
-    const int s0 = m_tile * TM, v0 = n_tile * TN;
+    const int nkb = Kpad / TKB;
 
     if (threadIdx.x == 0) {
-        mbar_init(bar_full, 1);
-        mbar_init(bar_done, 1);
+        for (int i = 0; i < C::NSTAGE; ++i) {
+            mbar_init(full + i, 1);
+            mbar_init(empty + i, 1);
+        }
+        for (int i = 0; i < 2; ++i) {
+            mbar_init(tfull + i, 1);
+            mbar_init(tempty + i, 4);   // one arrival per epilogue warp
+        }
+        *abort = 0;
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
-        *status = 1;
     }
-    if (warp == 0) {
+    if (warp == 1) {
         asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(tmem_slot)),
-                     "r"(kTmemCols)
+                     "r"(Lay::kTmemCols)
                      : "memory");
         asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
     }
-    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    tc_fence_before();
     __syncthreads();
-    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    tc_fence_after();
     const uint32_t tmem = *tmem_slot;
 
-    if (threadIdx.x == 0) {
-        const int nkb = Kpad / TKB;
-        bool ok = true;
-        for (int kb = 0; kb < nkb && ok; ++kb) {
-            mbar_expect_tx(bar_full, 4 * kTileBytes + extra_tx);
-            tma_load_2d(smem + kOffAhi, &mapA, kb * TKB, s0, bar_full);
-            tma_load_2d(smem + kOffAlo, &mapA, kb * TKB, Spad + s0, bar_full);
-            tma_load_2d(smem + kOffBhi, &mapB, kb * TKB, v0, bar_full);
-            tma_load_2d(smem + kOffBlo, &mapB, kb * TKB, Vpad + v0, bar_full);
-            if (!mbar_wait(bar_full, (uint32_t)(kb & 1), timeout_ns)) {
-                atomicCAS(err, KERR_NONE, KERR_TIMEOUT);
-                mbar_wait(bar_full, (uint32_t)(kb & 1), timeout_ns);   // let in-flight copies land
-                ok = false;
-                break;
-            }
-            asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-            const uint32_t aH = smem_u32(smem + kOffAhi), aL = smem_u32(smem + kOffAlo);
-            const uint32_t bH = smem_u32(smem + kOffBhi), bL = smem_u32(smem + kOffBlo);
-#pragma unroll
-            for (int k = 0; k < TKB / 16; ++k) {
-                const uint32_t koff = (uint32_t)k * 32u;   // 16 FP16 = 32 bytes along the swizzled row
-                const uint64_t dAH = desc_sw128(aH + koff), dAL = desc_sw128(aL + koff);
-                const uint64_t dBH = desc_sw128(bH + koff), dBL = desc_sw128(bL + koff);
-                const uint32_t acc = (kb > 0 || k > 0) ? 1u : 0u;
-                mma_f16(tmem + 0, dAH, dBH, acc);
-                mma_f16(tmem + TN, dAH, dBL, acc);
-                mma_f16(tmem + TN, dAL, dBH, 1u);
-            }
-            mma_commit(bar_done);
-            if (!mbar_wait(bar_done, (uint32_t)(kb & 1), timeout_ns)) {
-                atomicCAS(err, KERR_NONE, KERR_TIMEOUT);
-                mbar_wait(bar_done, (uint32_t)(kb & 1), timeout_ns);
-                ok = false;
-                break;
-            }
-        }
-        *status = ok ? 1u : 0u;
-    }
-    __syncthreads();
-    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-
-    if (*status) {
-        float* stg = stage + warp * 32 * 33;
-        const uint32_t lane_base = (uint32_t)(warp * 32) << 16;
-#pragma unroll 1
-        for (int c = 0; c < TN / 32; ++c) {
-            uint32_t r1[32], r2[32];
-            tmem_ld_x32(tmem + lane_base + (uint32_t)(c * 32), r1);
-            tmem_ld_x32(tmem + lane_base + (uint32_t)(TN + c * 32), r2);
-            asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
-#pragma unroll
-            for (int j = 0; j < 32; ++j) {
-                const float lg = __uint_as_float(r1[j]) + __uint_as_float(r2[j]) * (1.0f / 2048.0f);
-                stg[lane * 33 + j] = expf(lg);
-            }
-            __syncwarp();
-            const int v = v0 + c * 32 + lane;
-#pragma unroll 4
-            for (int rr = 0; rr < 32; ++rr) {
-                const int s = s0 + warp * 32 + rr;
-                if (s < S && v < V) out[(size_t)s * V + v] = stg[rr * 33 + lane];
-            }
-            __syncwarp();
-        }
-    }
-    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
-    __syncthreads();
     if (warp == 0) {
-        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(kTmemCols) : "memory");
+        // ---- TMA producer
+        if (lane == 0) {
+            int stage = 0;
+            uint32_t phase = 0;
+            unsigned issued = 0;
+            bool ok = true;
+            for (int t = blockIdx.x; t < num_tiles && ok; t += gridDim.x) {
+                const int s0 = (t % num_m) * TM, v0 = (t / num_m) * TN;
+                for (int kb = 0; kb < nkb; ++kb) {
+                    if (!kl_wait(empty + stage, phase ^ 1u, abort, err, timeout_ns)) {
+                        ok = false;
+                        break;
+                    }
+                    uint8_t* st = smem + (size_t)stage * Lay::kStage;
+                    mbar_expect_tx(full + stage, Lay::kStage + (issued == 0 ? extra_tx : 0u));
+                    ++issued;
+#pragma unroll
+                    for (int q = 0; q < C::NA; ++q) tma_load_2d(st + q * kATile, &mapA, kb * TKB, q * Spad + s0, full + stage);
+#pragma unroll
+                    for (int q = 0; q < C::NB; ++q)
+                        tma_load_2d(st + C::NA * kATile + q * Lay::kBTile, &mapB, kb * TKB, q * Vpad + v0, full + stage);
+                    if (++stage == C::NSTAGE) {
+                        stage = 0;
+                        phase ^= 1u;
+                    }
+                }
+            }
+            if (!ok) {
+                // let the copies in flight land before the CTA's shared memory goes away: the last
+                // NSTAGE issues, each on its own stage (bounded; a copy that never completes its
+                // barrier is waited for only until the timeout)
+                const unsigned n = issued < (unsigned)C::NSTAGE ? issued : (unsigned)C::NSTAGE;
+                for (unsigned i = 0; i < n; ++i) {
+                    const unsigned g = issued - 1u - i;
+                    mbar_wait(full + (g % C::NSTAGE), (g / C::NSTAGE) & 1u, timeout_ns);
+                }
+            }
+        }
+    } else if (warp == 1) {
+        // ---- MMA issuer
+        if (lane == 0) {
+            int stage = 0, tb = 0;
+            uint32_t phase = 0, tphase = 0;
+            bool ok = true;
+            uint64_t* last_bar = nullptr;   // barrier and parity of the last commit, for a clean abort
+            uint32_t last_par = 0;
+            for (int t = blockIdx.x; t < num_tiles && ok; t += gridDim.x) {
+                if (!C::DRAIN && !kl_wait(tempty + tb, tphase ^ 1u, abort, err, timeout_ns)) break;
+                for (int kb = 0; kb < nkb; ++kb) {
+                    if (C::DRAIN && !kl_wait(tempty + tb, tphase ^ 1u, abort, err, timeout_ns)) {
+                        ok = false;
+                        break;
+                    }
+                    if (!kl_wait(full + stage, phase, abort, err, timeout_ns)) {
+                        ok = false;
+                        break;
+                    }
+                    tc_fence_after();
+                    const uint32_t sa = smem_u32(smem + (size_t)stage * Lay::kStage);
+                    const uint32_t sb = sa + C::NA * kATile;
+                    const uint32_t d0 = tmem + (uint32_t)(tb * C::NACC * TN);
+#pragma unroll
+                    for (int k = 0; k < TKB / 16; ++k) {
+                        const uint32_t koff = (uint32_t)k * 32u;   // 16 FP16 = 32 bytes along the swizzled row
+                        const bool first = C::DRAIN ? (k == 0) : (kb == 0 && k == 0);
+                        const uint64_t a0 = desc_sw128(sa + koff), b0 = desc_sw128(sb + koff);
+                        const uint64_t a1 = desc_sw128(sa + kATile + koff), b1 = desc_sw128(sb + Lay::kBTile + koff);
+                        mma_f16<TN>(d0, a0, b0, first ? 0u : 1u);
+                        mma_f16<TN>(d0 + TN, a0, b1, first ? 0u : 1u);
+                        mma_f16<TN>(d0 + TN, a1, b0, 1u);
+                        if (MODE == 1) {
+                            const uint64_t a2 = desc_sw128(sa + 2 * kATile + koff);
+                            const uint64_t b2 = desc_sw128(sb + 2 * Lay::kBTile + koff);
+                            mma_f16<TN>(d0 + TN, a1, b1, 1u);
+                            mma_f16<TN>(d0 + 2 * TN, a0, b2, first ? 0u : 1u);
+                            mma_f16<TN>(d0 + 2 * TN, a2, b0, 1u);
+                            mma_f16<TN>(d0 + 2 * TN, a1, b2, 1u);
+                            mma_f16<TN>(d0 + 2 * TN, a2, b1, 1u);
+                        }
+                    }
+                    mma_commit(empty + stage);   // the stage is free once these MMAs have read it
+                    last_bar = empty + stage;
+                    last_par = phase;
+                    if (++stage == C::NSTAGE) {
+                        stage = 0;
+                        phase ^= 1u;
+                    }
+                    if (C::DRAIN) {
+                        mma_commit(tfull + tb);
+                        if (++tb == 2) {
+                            tb = 0;
+                            tphase ^= 1u;
+                        }
+                    }
+                }
+                if (!ok) break;
+                if (!C::DRAIN) {
+                    mma_commit(tfull + tb);
+                    if (++tb == 2) {
+                        tb = 0;
+                        tphase ^= 1u;
+                    }
+                }
+            }
+            // after an abort, the MMAs already issued finish before the tensor memory is freed
+            if (*abort && last_bar) mbar_wait(last_bar, last_par, timeout_ns);
+        }
+    } else {
+        // ---- epilogue: warps 2-5, TMEM lanes 32 (warp % 4) .. + 31 (one sample per lane)
+        const int q4 = warp & 3;
+        const uint32_t lane_base = (uint32_t)(q4 * 32) << 16;
+        Out* stg = reinterpret_cast<Out*>(smem + Lay::kOffStg) + (warp - 2) * 32 * 33;
+        int tb = 0;
+        uint32_t tphase = 0;
+        for (int t = blockIdx.x; t < num_tiles; t += gridDim.x) {
+            const int s0 = (t % num_m) * TM, v0 = (t / num_m) * TN;
+            const int srow = s0 + q4 * 32 + lane;   // this lane's sample
+            if (MODE == 0) {
+                if (!kl_warp_wait(tfull + tb, tphase, abort, err, timeout_ns)) break;
+                tc_fence_after();
+                const uint32_t base = tmem + lane_base + (uint32_t)(tb * C::NACC * TN);
+#pragma unroll 1
+                for (int c = 0; c < TN / 32; ++c) {
+                    uint32_t r0[32], r1[32];
+                    tmem_ld_x32(base + (uint32_t)(c * 32), r0);
+                    tmem_ld_x32(base + (uint32_t)(TN + c * 32), r1);
+                    tmem_wait_ld();
+                    if (c == TN / 32 - 1) {
+                        // every value of this buffer is in registers: hand it back to the MMA warp
+                        tc_fence_before();
+                        __syncwarp();
+                        if (lane == 0) mbar_arrive(tempty + tb);
+                    }
+#pragma unroll
+                    for (int j = 0; j < 32; ++j) {
+                        const float lg = __uint_as_float(r0[j]) + __uint_as_float(r1[j]) * (1.0f / 2048.0f);
+                        stg[lane * 33 + j] = (Out)expf(lg);
+                    }
+                    __syncwarp();
+                    const int v = v0 + c * 32 + lane;
+#pragma unroll 4
+                    for (int rr = 0; rr < 32; ++rr) {
+                        const int s = s0 + q4 * 32 + rr;
+                        if (s < S && v < V) out[(size_t)s * V + v] = stg[rr * 33 + lane];
+                    }
+                    __syncwarp();
+                }
+                if (++tb == 2) {
+                    tb = 0;
+                    tphase ^= 1u;
+                }
+            } else {
+                int s0i[TN];        // sum over K blocks of E0 (exact integers)
+                float s1f[TN];      // sum over K blocks of E1 + 2^-11 E2
+#pragma unroll
+                for (int j = 0; j < TN; ++j) {
+                    s0i[j] = 0;
+                    s1f[j] = 0.0f;
+                }
+                bool ok = true;
+                for (int kb = 0; kb < nkb; ++kb) {
+                    if (!kl_warp_wait(tfull + tb, tphase, abort, err, timeout_ns)) {
+                        ok = false;
+                        break;
+                    }
+                    tc_fence_after();
+                    const uint32_t base = tmem + lane_base + (uint32_t)(tb * C::NACC * TN);
+#pragma unroll
+                    for (int c = 0; c < TN / 32; ++c) {
+                        uint32_t r[32];
+                        tmem_ld_x32(base + (uint32_t)(c * 32), r);
+                        tmem_wait_ld();
+#pragma unroll
+                        for (int j = 0; j < 32; ++j) s0i[c * 32 + j] += __float2int_rn(__uint_as_float(r[j]));
+                        tmem_ld_x32(base + (uint32_t)(TN + c * 32), r);
+                        tmem_wait_ld();
+#pragma unroll
+                        for (int j = 0; j < 32; ++j) s1f[c * 32 + j] = __fadd_rn(s1f[c * 32 + j], __uint_as_float(r[j]));
+                        tmem_ld_x32(base + (uint32_t)(2 * TN + c * 32), r);
+                        tmem_wait_ld();
+#pragma unroll
+                        for (int j = 0; j < 32; ++j)
+                            s1f[c * 32 + j] = __fmaf_rn(__uint_as_float(r[j]), 1.0f / 2048.0f, s1f[c * 32 + j]);
+                    }
+                    tc_fence_before();
+                    __syncwarp();
+                    if (lane == 0) mbar_arrive(tempty + tb);
+                    if (++tb == 2) {
+                        tb = 0;
+                        tphase ^= 1u;
+                    }
+                }
+                if (!ok) break;
+                const int esv = srow < Spad ? es[srow] : 0;
+                // (fully unrolled: the per-column sums stay in registers)
+#pragma unroll
+                for (int c = 0; c < TN / 32; ++c) {
+#pragma unroll
+                    for (int j = 0; j < 32; ++j) {
+                        const int v = v0 + c * 32 + j;
+                        const int sc = esv + ev[v < Vpad ? v : Vpad - 1] - 18;
+                        // float-float of the integer sum (up to 2^26) plus the FP32 correction sum
+                        const int ii = s0i[c * 32 + j];
+                        const float ih = (float)ii;
+                        const float il = (float)(ii - (int)ih);
+                        float h, e;
+                        two_sum(ih, s1f[c * 32 + j], h, e);
+                        float lh, ll;
+                        fast_two_sum(h, __fadd_rn(e, il), lh, ll);
+                        lh = ldexpf(lh, sc);
+                        ll = ldexpf(ll, sc);
+                        float ah, al;
+                        ff_exp(lh, ll, ffx, ah, al);
+                        stg[lane * 33 + j] = (double)ah + (double)al;
+                    }
+                    __syncwarp();
+                    const int v = v0 + c * 32 + lane;
+#pragma unroll 4
+                    for (int rr = 0; rr < 32; ++rr) {
+                        const int s = s0 + q4 * 32 + rr;
+                        if (s < S && v < V) out[(size_t)s * V + v] = stg[rr * 33 + lane];
+                    }
+                    __syncwarp();
+                }
+            }
+        }
+    }
+    tc_fence_before();
+    __syncthreads();
+    if (warp == 1) {
+        tc_fence_after();
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(Lay::kTmemCols)
+                     : "memory");
     }
 }
 
@@ -201,6 +522,61 @@ __global__ void split_xi_kernel(int S, int K, int Spad, int Kpad, const double* 
     const __half hi = __double2half(x);
     a16[idx] = hi;
     a16[(size_t)Spad * Kpad + idx] = __double2half((x - (double)__half2float(hi)) * 2048.0);
+}
+
+// Exact-lead slices of a row x[0..K) (FP64, read with stride `stride`): scale 2^-e with
+// max |x_k| 2^-e in [1/2, 1) (e = 0 for an all-zero row), X = x 2^(9 - e), lead = rint(X),
+// h = fp16(X - lead), l = fp16((X - lead - h) 2^11); written to out[q * slice + k], q = 0, 1, 2.
+// One warp per row.
+__device__ __forceinline__ void exact_slices_row(const double* x, long long stride, int K, int Kpad, __half* out,
+                                                 size_t slice, int* e_out) {
+    const int lane = threadIdx.x & 31;
+    double mx = 0.0;
+    for (int k = lane; k < K; k += 32) mx = fmax(mx, fabs(x[(long long)k * stride]));
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) mx = fmax(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+    int e = 0;
+    if (mx > 0.0) frexp(mx, &e);   // mx = f 2^e, f in [1/2, 1)
+    const double sc = ldexp(1.0, 9 - e);
+    for (int k = lane; k < Kpad; k += 32) {
+        const double X = k < K ? x[(long long)k * stride] * sc : 0.0;
+        const double lead = rint(X);
+        const double rem = X - lead;                      // exact: |rem| <= 1/2
+        const __half h = __double2half(rem);
+        const __half l = __double2half((rem - (double)__half2float(h)) * 2048.0);
+        out[k] = __double2half(lead);                    // |lead| <= 512: exact
+        out[slice + k] = h;
+        out[2 * slice + k] = l;
+    }
+    if (lane == 0) *e_out = e;
+}
+
+// xi (FP64 [S][K]) -> exact-lead operand [3][Spad][Kpad] and row exponents es[Spad].
+__global__ void split_xi_exact_kernel(int S, int K, int Spad, int Kpad, const double* __restrict__ xi,
+                                      __half* __restrict__ a16, int* __restrict__ es) {
+    const int s = (int)(((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5);
+    if (s >= Spad) return;
+    const size_t slice = (size_t)Spad * Kpad;
+    if (s < S) {
+        exact_slices_row(xi + (size_t)s * K, 1, K, Kpad, a16 + (size_t)s * Kpad, slice, es + s);
+    } else {
+        const int lane = threadIdx.x & 31;
+        for (int k = lane; k < Kpad; k += 32) {
+            a16[(size_t)s * Kpad + k] = __float2half(0.0f);
+            a16[slice + (size_t)s * Kpad + k] = __float2half(0.0f);
+            a16[2 * slice + (size_t)s * Kpad + k] = __float2half(0.0f);
+        }
+        if (lane == 0) es[s] = 0;
+    }
+}
+
+// Basis columns Phi[.][v] (FP64 [K][ld64]) -> exact-lead operand [3][Vpad][Kpad] and node exponents ev[Vpad].
+__global__ void split_basis_exact_kernel(int K, int Kpad, int V, int Vpad, int ld64, const double* __restrict__ phi64,
+                                         __half* __restrict__ b16, int* __restrict__ ev) {
+    const int v = (int)(((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5);
+    if (v >= Vpad) return;
+    // padding nodes (v >= V) are zero columns of phi64
+    exact_slices_row(phi64 + v, ld64, K, Kpad, b16 + (size_t)v * Kpad, (size_t)Vpad * Kpad, ev + v);
 }
 
 typedef CUresult (*EncodeTiledFn)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*, const cuuint64_t*,
@@ -220,17 +596,82 @@ EncodeTiledFn encode_fn() {
     return fn;
 }
 
-// 2D FP16 tensor [rows][cols] (cols contiguous), box {64, 128}, 128-byte swizzle.
-bool make_map(CUtensorMap* map, const void* base, uint64_t rows, uint64_t cols) {
+// 2D FP16 tensor [rows][cols] (cols contiguous), box {64, box_rows}, 128-byte swizzle.
+bool make_map(CUtensorMap* map, const void* base, uint64_t rows, uint64_t cols, uint32_t box_rows) {
     EncodeTiledFn fn = encode_fn();
     if (!fn) return false;
     const cuuint64_t dims[2] = {cols, rows};
     const cuuint64_t strides[1] = {cols * sizeof(__half)};
-    const cuuint32_t box[2] = {TKB, 128};
+    const cuuint32_t box[2] = {TKB, box_rows};
     const cuuint32_t estr[2] = {1, 1};
     return fn(map, CU_TENSOR_MAP_DATA_TYPE_FLOAT16, 2, const_cast<void*>(base), dims, strides, box, estr,
               CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
               CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+
+// Tang's tables in float-float, from long-double host arithmetic.
+FFExp make_ffexp() {
+    FFExp T;
+    for (int j = 0; j < 32; ++j) {
+        const long double t = std::exp2((long double)j / 32.0L);
+        T.th[j] = (float)t;
+        T.tl[j] = (float)(t - (long double)T.th[j]);
+    }
+    const long double L = std::log(2.0L) / 32.0L;
+    // l1: L rounded to 12 significant bits (so that N l1 is exact for |N| < 2^12)
+    int e = 0;
+    const long double f = std::frexp(L, &e);               // L = f 2^e, f in [1/2, 1)
+    const long double l1 = std::ldexp(std::round(std::ldexp(f, 12)), e - 12);
+    T.l1 = (float)l1;
+    T.l2 = (float)(L - l1);
+    T.l3 = (float)(L - l1 - (long double)T.l2);
+    T.inv = (float)(1.0L / L);
+    return T;
+}
+
+template <int MODE>
+cudaError_t kl_launch(mlmc_ctx* ctx, int S, int Spad, int Kpad, int nodes, int nodes_pad, const void* aops,
+                      const void* bops, const int* es, const int* ev, void* out, cudaStream_t st) {
+    using C = KLCfg<MODE>;
+    using Lay = KLLayout<MODE>;
+    CUtensorMap mapA, mapB;
+    if (!make_map(&mapA, aops, (uint64_t)C::NA * Spad, (uint64_t)Kpad, TM) ||
+        !make_map(&mapB, bops, (uint64_t)C::NB * nodes_pad, (uint64_t)Kpad, C::TN))
+        return cudaErrorInvalidValue;
+    static bool attr = false;
+    cudaError_t e;
+    if (!attr) {
+        if ((e = cudaFuncSetAttribute(kl_tc_kernel<MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                      (int)Lay::kSmem)) != cudaSuccess)
+            return e;
+        attr = true;
+    }
+    static const FFExp ffx = make_ffexp();
+    const int num_m = Spad / TM;
+    const int num_tiles = num_m * (nodes_pad / C::TN);
+    const int grid = num_tiles < ctx->num_sms ? num_tiles : ctx->num_sms;
+    Profile::Pending pend;
+    if (ctx->prof.on) {
+        if ((e = cudaEventCreate(&pend.a)) != cudaSuccess) return e;
+        if ((e = cudaEventCreate(&pend.b)) != cudaSuccess) return e;
+        if ((e = cudaEventRecord(pend.a, st)) != cudaSuccess) return e;
+    }
+    kl_tc_kernel<MODE><<<(unsigned)grid, kThreads, Lay::kSmem, st>>>(
+        mapA, mapB, S, Spad, nodes, nodes_pad, Kpad, num_m, num_tiles, es, ev, ffx,
+        static_cast<typename C::Out*>(out), ctx->kl_err, (unsigned long long)(ctx->wait_timeout_s * 1e9),
+        16u * (unsigned)ctx->wait_extra);
+    g_launches.fetch_add(1, std::memory_order_relaxed);
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    if (ctx->prof.on) {
+        if ((e = cudaEventRecord(pend.b, st)) != cudaSuccess) return e;
+        // written output, one read of both operands' slices (and the exponents)
+        pend.bytes = (double)S * nodes * sizeof(typename C::Out) + (double)C::NA * Spad * Kpad * 2.0 +
+                     (double)C::NB * nodes_pad * Kpad * 2.0 + (MODE == 1 ? 4.0 * (Spad + nodes_pad) : 0.0);
+        const int mmas = MODE == 0 ? 3 : 8;   // MMAs per 16-term step
+        pend.flops = 2.0 * mmas * Spad * (double)Kpad * nodes_pad;
+        ctx->prof.kl_pending.push_back(pend);
+    }
+    return cudaSuccess;
 }
 
 }  // namespace
@@ -239,49 +680,44 @@ cudaError_t launch_kl_fp32(mlmc_ctx* ctx, const GridBasis& gb, int S, const doub
     if (S <= 0) return cudaSuccess;
     const int Spad = (S + TM - 1) / TM * TM;
     const int Kpad = gb.Kpad;
-    // split operand + error word
-    const size_t abytes = (size_t)2 * Spad * Kpad * sizeof(__half);
-    cudaError_t e = ctx->ws.split.reserve(abytes + 256);
+    cudaError_t e = ctx->ws.split.reserve((size_t)2 * Spad * Kpad * sizeof(__half));
     if (e != cudaSuccess) return e;
     __half* a16 = ctx->ws.split.as<__half>();
-    // the error word is the context's (cleared when the host reads it)
-    unsigned* errw = ctx->kl_err;
     const long long work = (long long)Spad * Kpad;
     split_xi_kernel<<<(unsigned)((work + 255) / 256), 256, 0, st>>>(S, gb.K, Spad, Kpad, xi, a16);
     g_launches.fetch_add(1, std::memory_order_relaxed);
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
-    CUtensorMap mapA, mapB;
-    if (!make_map(&mapA, a16, (uint64_t)2 * Spad, (uint64_t)Kpad) ||
-        !make_map(&mapB, gb.phi16.ptr, (uint64_t)2 * gb.nodes_pad, (uint64_t)Kpad))
-        return cudaErrorInvalidValue;
-    static bool attr = false;
-    if (!attr) {
-        if ((e = cudaFuncSetAttribute(kl_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmemBytes)) !=
-            cudaSuccess)
+    return kl_launch<0>(ctx, S, Spad, Kpad, gb.nodes, gb.nodes_pad, a16, gb.phi16.ptr, nullptr, nullptr, a, st);
+}
+
+cudaError_t launch_kl_tc64(mlmc_ctx* ctx, GridBasis& gb, int S, const double* xi, double* a, cudaStream_t st) {
+    if (S <= 0) return cudaSuccess;
+    cudaError_t e;
+    if (!gb.phix.ptr) {
+        // exact-lead basis slices and node exponents, built once per grid from the FP64 basis
+        if ((e = gb.phix.reserve((size_t)3 * gb.nodes_pad * gb.Kpad * sizeof(__half))) != cudaSuccess) return e;
+        if ((e = gb.ev.reserve((size_t)gb.nodes_pad * sizeof(int))) != cudaSuccess) {
+            gb.phix.release();
             return e;
-        attr = true;
+        }
+        const long long threads = (long long)gb.nodes_pad * 32;
+        split_basis_exact_kernel<<<(unsigned)((threads + 255) / 256), 256, 0, st>>>(
+            gb.K, gb.Kpad, gb.nodes, gb.nodes_pad, gb.nodes_pad, gb.phi64.as<double>(), gb.phix.as<__half>(),
+            gb.ev.as<int>());
+        g_launches.fetch_add(1, std::memory_order_relaxed);
+        if ((e = cudaGetLastError()) != cudaSuccess) return e;
     }
-    const int num_m = Spad / TM;
-    const int num_n = (gb.nodes + TN - 1) / TN;
-    Profile::Pending pend;
-    if (ctx->prof.on) {
-        if ((e = cudaEventCreate(&pend.a)) != cudaSuccess) return e;
-        if ((e = cudaEventCreate(&pend.b)) != cudaSuccess) return e;
-        if ((e = cudaEventRecord(pend.a, st)) != cudaSuccess) return e;
-    }
-    kl_tc_kernel<<<(unsigned)(num_m * num_n), 128, kSmemBytes, st>>>(
-        mapA, mapB, S, Spad, gb.nodes, gb.nodes_pad, Kpad, num_m, a, errw,
-        (unsigned long long)(ctx->wait_timeout_s * 1e9), 16u * (unsigned)ctx->wait_extra);
+    const int Spad = (S + TM - 1) / TM * TM;
+    const int Kpad = gb.Kpad;
+    const size_t abytes = ((size_t)3 * Spad * Kpad * sizeof(__half) + 255) / 256 * 256;
+    if ((e = ctx->ws.split.reserve(abytes + (size_t)Spad * sizeof(int))) != cudaSuccess) return e;
+    __half* a16 = ctx->ws.split.as<__half>();
+    int* es = reinterpret_cast<int*>(ctx->ws.split.as<char>() + abytes);
+    const long long threads = (long long)Spad * 32;
+    split_xi_exact_kernel<<<(unsigned)((threads + 255) / 256), 256, 0, st>>>(S, gb.K, Spad, Kpad, xi, a16, es);
     g_launches.fetch_add(1, std::memory_order_relaxed);
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
-    if (ctx->prof.on) {
-        if ((e = cudaEventRecord(pend.b, st)) != cudaSuccess) return e;
-        const double npad = (double)num_n * TN;
-        pend.bytes = (double)S * gb.nodes * 4.0 + 2.0 * Spad * Kpad * 2.0 + 2.0 * (double)gb.nodes_pad * Kpad * 2.0;
-        pend.flops = 6.0 * Spad * (double)Kpad * npad;
-        ctx->prof.kl_pending.push_back(pend);
-    }
-    return cudaSuccess;
+    return kl_launch<1>(ctx, S, Spad, Kpad, gb.nodes, gb.nodes_pad, a16, gb.phix.ptr, es, gb.ev.as<int>(), a, st);
 }
 
 }  // namespace mlmc
