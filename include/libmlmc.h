@@ -417,6 +417,12 @@ typedef struct {
     double solve_busy_ms;      /* union of the resident-solve launches' intervals on the device timeline
                                   (launches on concurrent streams counted once), since profiling was
                                   switched on or reset */
+    double solve_flops;        /* arithmetic operations of the resident solves, counted per unknown as
+                                  the kernels execute them: a stencil point 28 (nodal coefficient) or 12
+                                  (stored FP64 edge weights); per inner iteration two stencil sweeps with
+                                  their recurrences and dots, plus the V-cycle with multigrid; per
+                                  refinement step the FP64 residual and its dots (20) and the update;
+                                  set-up (edge weights, inverse diagonal) and the QoI */
 } mlmc_profile;
 mlmc_status mlmc_profile_enable(mlmc_ctx* ctx, int on);
 mlmc_status mlmc_profile_get(mlmc_ctx* ctx, mlmc_profile* out);   /* synchronises the device */

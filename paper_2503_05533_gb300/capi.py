@@ -68,7 +68,8 @@ class mlmc_profile(ctypes.Structure):
     _fields_ = [("solve_launches", c_int64), ("solve_ms", c_double), ("solve_bytes", c_double),
                 ("inner_iters", c_int64), ("unknown_iters", c_int64), ("kl_launches", c_int64),
                 ("kl_ms", c_double), ("kl_bytes", c_double), ("kl_flops", c_double),
-                ("h2d_bytes", c_int64), ("d2h_bytes", c_int64), ("solve_busy_ms", c_double)]
+                ("h2d_bytes", c_int64), ("d2h_bytes", c_int64), ("solve_busy_ms", c_double),
+                ("solve_flops", c_double)]
 
 
 SAMPLER_FN = ctypes.CFUNCTYPE(c_int, c_void_p, c_int, c_int64, c_int, POINTER(c_double), POINTER(c_double))

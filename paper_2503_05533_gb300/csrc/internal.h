@@ -185,6 +185,7 @@ struct PendingSolve {
     // algorithmic bytes of system i: it_i c_it[i] + (steps_i + 1) c_res[i] + steps_i c_upd[i] + c_set[i]
     // (filled only while profiling)
     std::vector<double> unk, c_it, c_res, c_upd, c_set;
+    std::vector<double> f_it, f_res, f_upd, f_set;   // the same for arithmetic operations
     cudaEvent_t ev[2] = {nullptr, nullptr};
 };
 // solver_<precision>.cu (solver_impl.cuh): one inner precision's batch launcher (plan, upload and

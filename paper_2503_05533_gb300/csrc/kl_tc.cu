@@ -40,10 +40,10 @@
 // samples x TN nodes.  Warp 0 streams the operand slices of every 64-term K
 // block by TMA (128-byte swizzle) through a ring of shared-memory stages;
 // warp 1 issues the MMAs (M = 128, N = TN, K = 16) into one of two tensor-
-// memory buffers and signals through mbarriers; warps 2-5 drain the other
-// buffer (each warp its 32 TMEM lanes, one sample per lane), form the output
-// and write it through a shared-memory transpose so that stores are
-// row-contiguous.  Loads of tile t+1 and the epilogue of tile t overlap its
+// memory buffers and signals through mbarriers; TN / 8 epilogue warps drain
+// the other buffer (each warp 32 columns of one TMEM lane quarter, one sample
+// per lane), form the output and write it through a shared-memory transpose so
+// that stores are row-contiguous.  Loads of tile t+1 and the epilogue of tile t overlap its
 // MMAs.  Every mbarrier wait is bounded in wall time; on expiry the CTA records
 // the context's error word, every role leaves its loop, the producer waits
 // (bounded) for its copies in flight, and the TMEM is freed.
@@ -63,18 +63,19 @@ namespace {
 
 constexpr int TM = 128;              // samples per tile (MMA M, TMEM lanes)
 constexpr int TKB = 64;              // terms per K block: 64 FP16 = one 128-byte swizzle row
-constexpr int kThreads = 192;        // warp 0: TMA, warp 1: MMA, warps 2-5: epilogue
 constexpr uint32_t kATile = TM * TKB * 2;   // 16 KiB: one slice of 128 sample rows
 
 // MODE 0: FP32 output (2 slices per operand); MODE 1: FP64 output (3 slices, exact lead).
 template <int MODE> struct KLCfg;
+// Warp 0 issues the TMA copies, warp 1 the MMAs; EW = TN / 8 epilogue warps follow, each draining one
+// 32-column chunk of one TMEM lane quarter (its warp index mod 4).
 template <> struct KLCfg<0> {
-    static constexpr int NA = 2, NB = 2, TN = 128, NACC = 2, NSTAGE = 3;
+    static constexpr int NA = 2, NB = 2, TN = 128, NACC = 2, NSTAGE = 2, EW = TN / 8;
     static constexpr bool DRAIN = false;   // accumulate the whole K range in TMEM
     using Out = float;
 };
 template <> struct KLCfg<1> {
-    static constexpr int NA = 3, NB = 3, TN = 64, NACC = 3, NSTAGE = 2;
+    static constexpr int NA = 3, NB = 3, TN = 64, NACC = 3, NSTAGE = 2, EW = TN / 8;
     static constexpr bool DRAIN = true;    // the epilogue drains every K block
     using Out = double;
 };
@@ -84,7 +85,8 @@ template <int MODE> struct KLLayout {
     static constexpr uint32_t kBTile = C::TN * TKB * 2;
     static constexpr uint32_t kStage = C::NA * kATile + C::NB * kBTile;   // multiple of 1024
     static constexpr uint32_t kOffStg = C::NSTAGE * kStage;               // epilogue transpose staging
-    static constexpr uint32_t kStgBytes = 4 * 32 * 33 * sizeof(typename C::Out);
+    static constexpr uint32_t kStgBytes = C::EW * 32 * 33 * sizeof(typename C::Out);
+    static constexpr int kThreads = 64 + 32 * C::EW;
     static constexpr uint32_t kOffBar = (kOffStg + kStgBytes + 15) / 16 * 16;
     // full[NSTAGE], empty[NSTAGE], tfull[2], tempty[2], then the TMEM address and the abort flag
     static constexpr uint32_t kBarBytes = 8 * (2 * C::NSTAGE + 4) + 16;
@@ -232,7 +234,7 @@ __device__ __forceinline__ void ff_exp(float xh, float xl, const FFExp& T, float
 }
 
 template <int MODE>
-__global__ void __launch_bounds__(kThreads, 1)
+__global__ void __launch_bounds__(KLLayout<MODE>::kThreads, 1)
     kl_tc_kernel(const __grid_constant__ CUtensorMap mapA, const __grid_constant__ CUtensorMap mapB, int S, int Spad,
                  int V, int Vpad, int Kpad, int num_m, int num_tiles, const int* __restrict__ es,
                  const int* __restrict__ ev, const __grid_constant__ FFExp ffx, typename KLCfg<MODE>::Out* __restrict__ out,
@@ -259,7 +261,7 @@ __global__ void __launch_bounds__(kThreads, 1)
         }
         for (int i = 0; i < 2; ++i) {
             mbar_init(tfull + i, 1);
-            mbar_init(tempty + i, 4);   // one arrival per epilogue warp
+            mbar_init(tempty + i, C::EW);   // one arrival per epilogue warp
         }
         *abort = 0;
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
@@ -384,10 +386,13 @@ __global__ void __launch_bounds__(kThreads, 1)
             if (*abort && last_bar) mbar_wait(last_bar, last_par, timeout_ns);
         }
     } else {
-        // ---- epilogue: warps 2-5, TMEM lanes 32 (warp % 4) .. + 31 (one sample per lane)
+        // ---- epilogue: warp 2 + e drains TMEM lanes 32 (warp % 4) .. + 31 (one sample per lane) of the
+        // tile's column chunk e / 4 (32 columns) and writes them
+        const int e = warp - 2;
         const int q4 = warp & 3;
+        const int c = e >> 2;
         const uint32_t lane_base = (uint32_t)(q4 * 32) << 16;
-        Out* stg = reinterpret_cast<Out*>(smem + Lay::kOffStg) + (warp - 2) * 32 * 33;
+        Out* stg = reinterpret_cast<Out*>(smem + Lay::kOffStg) + e * 32 * 33;
         int tb = 0;
         uint32_t tphase = 0;
         for (int t = blockIdx.x; t < num_tiles; t += gridDim.x) {
@@ -396,42 +401,29 @@ __global__ void __launch_bounds__(kThreads, 1)
             if (MODE == 0) {
                 if (!kl_warp_wait(tfull + tb, tphase, abort, err, timeout_ns)) break;
                 tc_fence_after();
-                const uint32_t base = tmem + lane_base + (uint32_t)(tb * C::NACC * TN);
-#pragma unroll 1
-                for (int c = 0; c < TN / 32; ++c) {
-                    uint32_t r0[32], r1[32];
-                    tmem_ld_x32(base + (uint32_t)(c * 32), r0);
-                    tmem_ld_x32(base + (uint32_t)(TN + c * 32), r1);
-                    tmem_wait_ld();
-                    if (c == TN / 32 - 1) {
-                        // every value of this buffer is in registers: hand it back to the MMA warp
-                        tc_fence_before();
-                        __syncwarp();
-                        if (lane == 0) mbar_arrive(tempty + tb);
-                    }
-#pragma unroll
-                    for (int j = 0; j < 32; ++j) {
-                        const float lg = __uint_as_float(r0[j]) + __uint_as_float(r1[j]) * (1.0f / 2048.0f);
-                        stg[lane * 33 + j] = (Out)expf(lg);
-                    }
-                    __syncwarp();
-                    const int v = v0 + c * 32 + lane;
-#pragma unroll 4
-                    for (int rr = 0; rr < 32; ++rr) {
-                        const int s = s0 + q4 * 32 + rr;
-                        if (s < S && v < V) out[(size_t)s * V + v] = stg[rr * 33 + lane];
-                    }
-                    __syncwarp();
-                }
+                const uint32_t base = tmem + lane_base + (uint32_t)(tb * C::NACC * TN + c * 32);
+                uint32_t r0[32], r1[32];
+                tmem_ld_x32(base, r0);
+                tmem_ld_x32(base + (uint32_t)TN, r1);
+                tmem_wait_ld();
+                // this warp's values are in registers: its share of the buffer goes back to the MMA warp
+                tc_fence_before();
+                __syncwarp();
+                if (lane == 0) mbar_arrive(tempty + tb);
                 if (++tb == 2) {
                     tb = 0;
                     tphase ^= 1u;
                 }
-            } else {
-                int s0i[TN];        // sum over K blocks of E0 (exact integers)
-                float s1f[TN];      // sum over K blocks of E1 + 2^-11 E2
 #pragma unroll
-                for (int j = 0; j < TN; ++j) {
+                for (int j = 0; j < 32; ++j) {
+                    const float lg = __uint_as_float(r0[j]) + __uint_as_float(r1[j]) * (1.0f / 2048.0f);
+                    stg[lane * 33 + j] = (Out)expf(lg);
+                }
+            } else {
+                int s0i[32];        // sum over K blocks of E0 (exact integers)
+                float s1f[32];      // sum over K blocks of E1 + 2^-11 E2
+#pragma unroll
+                for (int j = 0; j < 32; ++j) {
                     s0i[j] = 0;
                     s1f[j] = 0.0f;
                 }
@@ -442,24 +434,12 @@ __global__ void __launch_bounds__(kThreads, 1)
                         break;
                     }
                     tc_fence_after();
-                    const uint32_t base = tmem + lane_base + (uint32_t)(tb * C::NACC * TN);
-#pragma unroll
-                    for (int c = 0; c < TN / 32; ++c) {
-                        uint32_t r[32];
-                        tmem_ld_x32(base + (uint32_t)(c * 32), r);
-                        tmem_wait_ld();
-#pragma unroll
-                        for (int j = 0; j < 32; ++j) s0i[c * 32 + j] += __float2int_rn(__uint_as_float(r[j]));
-                        tmem_ld_x32(base + (uint32_t)(TN + c * 32), r);
-                        tmem_wait_ld();
-#pragma unroll
-                        for (int j = 0; j < 32; ++j) s1f[c * 32 + j] = __fadd_rn(s1f[c * 32 + j], __uint_as_float(r[j]));
-                        tmem_ld_x32(base + (uint32_t)(2 * TN + c * 32), r);
-                        tmem_wait_ld();
-#pragma unroll
-                        for (int j = 0; j < 32; ++j)
-                            s1f[c * 32 + j] = __fmaf_rn(__uint_as_float(r[j]), 1.0f / 2048.0f, s1f[c * 32 + j]);
-                    }
+                    const uint32_t base = tmem + lane_base + (uint32_t)(tb * C::NACC * TN + c * 32);
+                    uint32_t r0[32], r1[32], r2[32];
+                    tmem_ld_x32(base, r0);
+                    tmem_ld_x32(base + (uint32_t)TN, r1);
+                    tmem_ld_x32(base + (uint32_t)(2 * TN), r2);
+                    tmem_wait_ld();
                     tc_fence_before();
                     __syncwarp();
                     if (lane == 0) mbar_arrive(tempty + tb);
@@ -467,40 +447,42 @@ __global__ void __launch_bounds__(kThreads, 1)
                         tb = 0;
                         tphase ^= 1u;
                     }
+#pragma unroll
+                    for (int j = 0; j < 32; ++j) {
+                        s0i[j] += __float2int_rn(__uint_as_float(r0[j]));
+                        s1f[j] = __fmaf_rn(__uint_as_float(r2[j]), 1.0f / 2048.0f,
+                                           __fadd_rn(s1f[j], __uint_as_float(r1[j])));
+                    }
                 }
                 if (!ok) break;
                 const int esv = srow < Spad ? es[srow] : 0;
-                // (fully unrolled: the per-column sums stay in registers)
 #pragma unroll
-                for (int c = 0; c < TN / 32; ++c) {
-#pragma unroll
-                    for (int j = 0; j < 32; ++j) {
-                        const int v = v0 + c * 32 + j;
-                        const int sc = esv + ev[v < Vpad ? v : Vpad - 1] - 18;
-                        // float-float of the integer sum (up to 2^26) plus the FP32 correction sum
-                        const int ii = s0i[c * 32 + j];
-                        const float ih = (float)ii;
-                        const float il = (float)(ii - (int)ih);
-                        float h, e;
-                        two_sum(ih, s1f[c * 32 + j], h, e);
-                        float lh, ll;
-                        fast_two_sum(h, __fadd_rn(e, il), lh, ll);
-                        lh = ldexpf(lh, sc);
-                        ll = ldexpf(ll, sc);
-                        float ah, al;
-                        ff_exp(lh, ll, ffx, ah, al);
-                        stg[lane * 33 + j] = (double)ah + (double)al;
-                    }
-                    __syncwarp();
-                    const int v = v0 + c * 32 + lane;
-#pragma unroll 4
-                    for (int rr = 0; rr < 32; ++rr) {
-                        const int s = s0 + q4 * 32 + rr;
-                        if (s < S && v < V) out[(size_t)s * V + v] = stg[rr * 33 + lane];
-                    }
-                    __syncwarp();
+                for (int j = 0; j < 32; ++j) {
+                    const int v = v0 + c * 32 + j;
+                    const int sc = esv + ev[v < Vpad ? v : Vpad - 1] - 18;
+                    // float-float of the integer sum (up to 2^26) plus the FP32 correction sum
+                    const int ii = s0i[j];
+                    const float ih = (float)ii;
+                    const float il = (float)(ii - (int)ih);
+                    float h, e2;
+                    two_sum(ih, s1f[j], h, e2);
+                    float lh, ll;
+                    fast_two_sum(h, __fadd_rn(e2, il), lh, ll);
+                    lh = ldexpf(lh, sc);
+                    ll = ldexpf(ll, sc);
+                    float ah, al;
+                    ff_exp(lh, ll, ffx, ah, al);
+                    stg[lane * 33 + j] = (double)ah + (double)al;
                 }
             }
+            __syncwarp();
+            const int v = v0 + c * 32 + lane;
+#pragma unroll 4
+            for (int rr = 0; rr < 32; ++rr) {
+                const int s = s0 + q4 * 32 + rr;
+                if (s < S && v < V) out[(size_t)s * V + v] = stg[rr * 33 + lane];
+            }
+            __syncwarp();
         }
     }
     tc_fence_before();
@@ -656,7 +638,7 @@ cudaError_t kl_launch(mlmc_ctx* ctx, int S, int Spad, int Kpad, int nodes, int n
         if ((e = cudaEventCreate(&pend.b)) != cudaSuccess) return e;
         if ((e = cudaEventRecord(pend.a, st)) != cudaSuccess) return e;
     }
-    kl_tc_kernel<MODE><<<(unsigned)grid, kThreads, Lay::kSmem, st>>>(
+    kl_tc_kernel<MODE><<<(unsigned)grid, Lay::kThreads, Lay::kSmem, st>>>(
         mapA, mapB, S, Spad, nodes, nodes_pad, Kpad, num_m, num_tiles, es, ev, ffx,
         static_cast<typename C::Out*>(out), ctx->kl_err, (unsigned long long)(ctx->wait_timeout_s * 1e9),
         16u * (unsigned)ctx->wait_extra);

@@ -35,13 +35,16 @@ mlmc_status finish_solve(mlmc_ctx* ctx, PendingSolve& ps_) {
         std::vector<int32_t> stats(2 * ns);
         MLMC_CUDA_RET(ctx->err, cudaMemcpy(stats.data(), ps_.stats, sizeof(int32_t) * 2 * ns, cudaMemcpyDeviceToHost));
         const int32_t* outer = stats.data() + ns;
-        double bytes = 0.0;
+        double bytes = 0.0, flops = 0.0;
         int64_t iters = 0, uit = 0;
         for (int i = 0; i < ns && i < (int)ps_.unk.size(); ++i) {
             const int32_t it = stats[i];
             const int steps = std::min(outer[i], ps_.max_outer);
             bytes += (double)it * ps_.c_it[i] + (double)(steps + 1) * ps_.c_res[i] + (double)steps * ps_.c_upd[i] +
                      ps_.c_set[i];
+            // the first refinement residual is r = b (x = 0): its dots only
+            flops += (double)it * ps_.f_it[i] + (double)steps * ps_.f_res[i] + ps_.f_res[i] * (7.0 / 20.0) +
+                     (double)steps * ps_.f_upd[i] + ps_.f_set[i];
             iters += it;
             uit += (int64_t)ps_.unk[i] * it;
         }
@@ -49,6 +52,7 @@ mlmc_status finish_solve(mlmc_ctx* ctx, PendingSolve& ps_) {
         A.solve_launches += 1;
         A.solve_ms += ms;
         A.solve_bytes += bytes;
+        A.solve_flops += flops;
         A.inner_iters += iters;
         A.unknown_iters += uit;
     }

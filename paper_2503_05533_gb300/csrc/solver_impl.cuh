@@ -1872,6 +1872,30 @@ double mg_iter_bytes(int n, int nl, int nu, int ncs, double pv, double ps) {
     return bytes;
 }
 
+// Arithmetic operations per interior unknown, as the kernels execute them: a stencil point from
+// the nodal coefficient (four edge weights of 4 operations each, then 4 differences, 4 products,
+// 3 sums and the 1/6 scaling) or from stored FP64 edge weights (the FP64 inner solve's grid level).
+constexpr double kFlopStencil = 28.0, kFlopStencilW = 12.0;
+
+// Operations of one V-cycle summed over the unknowns of every level: a smoothing sweep from zero
+// 2 (omega D^-1 b), a later sweep a stencil plus 4 (b - A x, D^-1, omega, update), the residual a
+// stencil plus 1, restriction 8 per coarse unknown (the fine node and half of six neighbours),
+// prolongation 3 per fine unknown, and (r, z) on the grid 2.  The grid level uses stencil `s0`.
+double mg_iter_flops(int n, int nl, int nu, int ncs, double s0) {
+    double fl = 0.0;
+    for (int k = 0; k <= nl; ++k) {
+        const double u = (double)((n >> k) - 1) * ((n >> k) - 1);
+        const double st = k == 0 ? s0 : kFlopStencil;
+        if (k < nl) {
+            const double uc = (double)((n >> (k + 1)) - 1) * ((n >> (k + 1)) - 1);
+            fl += u * (2.0 + (nu - 1) * (st + 4.0) + (st + 1.0) + 3.0 + nu * (st + 4.0)) + uc * 8.0;
+        } else {
+            fl += u * (2.0 + (ncs - 1) * (st + 4.0));
+        }
+    }
+    return fl + 2.0 * (double)(n - 1) * (n - 1);
+}
+
 // Workspace of a batch: vectors, coefficient storage, descriptors, launch order.
 struct Layout {
     size_t o_x, o_r, o_p0, o_p1, o_d, o_as, o_dinv, o_vb, o_w0, o_w1, o_mz, o_mt, o_cx, o_ct, o_cb, o_cas, o_cdi,
@@ -2211,6 +2235,19 @@ mlmc_status launch_typed(mlmc_ctx* ctx, const std::vector<SolveGroup>& groups, c
             out.c_res.push_back(unk * (8 + 16 + 2 * pv + pd));
             out.c_upd.push_back(unk * (16 + pv));
             out.c_set.push_back(unk * (8 + pm + ps + pd + 16));
+            // operations: per inner iteration two stencil sweeps with their recurrences and dots, plus
+            // the V-cycle (CG: 12 + 2 S with Jacobi, 10 + 2 S with multigrid; MINRES: 18 + 2 S and
+            // 17 + 2 S); per refinement step the FP64 residual from the stored weights with its three
+            // dots (20) and the update (1); set-up: the edge weights (8), the inverse diagonal (21;
+            // 7 more for the coarse levels) and the QoI (2)
+            const double S_ = (sizeof(VT) == 8 && sizeof(ST) == 8) ? kFlopStencilW : kFlopStencil;
+            const double vf = mg ? mg_iter_flops(d.n, d.mg_levels, P.mg_nu, P.mg_coarse, S_) / unk : 0.0;
+            const double fit = cfg.solver == MLMC_MINRES ? (mg ? 17.0 : 18.0) + 2.0 * S_ + vf
+                                                         : (mg ? 10.0 : 12.0) + 2.0 * S_ + vf;
+            out.f_it.push_back(unk * fit);
+            out.f_res.push_back(unk * 20.0);
+            out.f_upd.push_back(unk * 1.0);
+            out.f_set.push_back(unk * (8.0 + 21.0 + (mg ? 7.0 : 0.0) + 2.0));
         }
     }
     return MLMC_OK;
