@@ -219,6 +219,8 @@ def main():
     ap.add_argument("--impl", default="libmlmc", choices=["libmlmc", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-fp64", action="store_true")
+    ap.add_argument("--no-autotune", action="store_true",
+                    help="use the library's fixed launch rules instead of the autotuner's choices")
     ap.add_argument("--no-extras", action="store_true",
                     help="time the headline workload only (no 7-level, sweep and adjoint keys)")
     ap.add_argument("--case", default="mlmc",
@@ -307,10 +309,13 @@ def main():
                                    args.mg_coarse)
             if args.med_items:
                 M.mlmc_debug_set_medium_items(h, args.med_items)
+            # launch settings: the autotuner times candidates on the warm-up estimates' launches
+            M.mlmc_set_autotune(h, not args.no_autotune)
             if profile:
                 M.mlmc_profile_enable(h, True)
             for w in range(warmup):
                 M.mlmc_estimate(h, opts(wl, tol, form))
+            tune = [M.mlmc_autotune_entry(h, i) for i in range(M.mlmc_autotune_count(h))]
             torch.cuda.synchronize()
             if profile:
                 M.mlmc_profile_reset(h)
@@ -333,6 +338,9 @@ def main():
                 dist.barrier()
             launches = M.mlmc_launch_count() - l0
             prof = M.mlmc_profile_get(h) if profile else None
+            if prof is not None:
+                prof["autotune"] = [{k: e[k] for k in ("shape", "med_items", "ring", "nu", "theta", "best_ms",
+                                                        "default_ms", "trials")} for e in tune]
         finally:
             M.mlmc_destroy(h)
         return ms, results, launches, prof
@@ -426,6 +434,7 @@ def main():
                          "busy_ms_per_step": prof["solve_busy_ms"] / args.steps,
                          "share_of_step": prof["solve_busy_ms"] / sum(ms) if sum(ms) > 0 else None},
             "kl_synthesis": {"achieved_gbs": kl_gbs, "tensor_tflops": kl_tf, "ms_per_step": prof["kl_ms"] / args.steps},
+            "autotune": prof["autotune"],
             "e2e": {"value": sum(e2e_s) / len(e2e_s), "unit": "s", "h2d_bytes_per_step": h2d,
                     "d2h_bytes_per_step": d2h},
             "gpu_launches": launches,
@@ -625,6 +634,7 @@ def adjoint_case(M, torch, dev, args, hbm_peak, peak_src, flush, stream):
     h = M.mlmc_create(prob, dev.index or 0)
     try:
         M.mlmc_profile_enable(h, True)
+        M.mlmc_set_autotune(h, not args.no_autotune)
         xi = torch.empty((S, K), dtype=torch.float64, device=dev)
         a = torch.empty((S, (n + 1) ** 2), dtype=torch.float32, device=dev)
         M.mlmc_sample_fields(h, 0, 0, S, xi, a, M.MLMC_FP32)
@@ -667,6 +677,7 @@ def sweep_case(M, torch, dev, args, hbm_peak, peak_src, flush, stream, prec=None
         M.mlmc_profile_enable(h, True)
         M.mlmc_debug_set_solve_ring(h, args.ring)
         M.mlmc_set_precond(h, M.MLMC_PC_MG if args.pc == "mg" else M.MLMC_PC_JACOBI, args.mg_nu, args.mg_coarse)
+        M.mlmc_set_autotune(h, not args.no_autotune)
         a = torch.empty((S, (n + 1) ** 2), dtype=torch.float64 if fp64 else torch.float32, device=dev)
         Q = torch.empty(S, dtype=torch.float64, device=dev)
         it = torch.empty(S, dtype=torch.int32, device=dev)

@@ -386,6 +386,31 @@ mlmc_status mlmc_set_precond(mlmc_ctx* ctx, mlmc_precond pc, int nu, int coarse_
  * the result are always judged on the FP64 residual. */
 mlmc_status mlmc_set_inner_tolerance(mlmc_ctx* ctx, double theta, double tau_min);
 
+/* A11: launch-setting autotuner of this context's resident solves (off by
+ * default).  When on, the first launch of each new launch shape -- inner
+ * precision, solver, preconditioner, and the batch's grid sizes with their
+ * system counts rounded down to powers of two -- is solved once per candidate
+ * setting, changing one setting at a time from the library's own rules: the
+ * group size of n = 91..128 systems (mlmc_debug_set_medium_items), the row-
+ * pipeline depth of Jacobi-preconditioned CG (0, 2, 4 slots), the V-cycle's
+ * smoothing sweeps (1, 2) and the inner tolerance factor theta (0.1, 0.3, 0.6;
+ * mlmc_set_inner_tolerance).  Each candidate is timed twice with CUDA events;
+ * a change is kept when at least 1% faster, and the fastest setting is cached
+ * in the context for the shape.  Every candidate solves the same systems to
+ * the same delta, so results agree to the solve tolerance whatever is chosen.
+ * A launch that tunes synchronises its stream (mlmc_level_solve included). */
+mlmc_status mlmc_set_autotune(mlmc_ctx* ctx, int on);
+typedef struct {
+    char shape[192];       /* the launch shape, as text                                        */
+    int prec, solver, precond;
+    int med_items, ring, nu;   /* chosen settings; -3 (and nu 0) means the context's own rule    */
+    double theta;          /* chosen inner tolerance factor; 0 means the context's (0.3)       */
+    double best_ms, default_ms;   /* launch time with the chosen and with the default settings */
+    int trials;            /* timed trial launches                                              */
+} mlmc_tune_entry;
+int mlmc_autotune_count(const mlmc_ctx* ctx);                  /* shapes tuned so far */
+mlmc_status mlmc_autotune_entry(const mlmc_ctx* ctx, int i, mlmc_tune_entry* out);   /* in tuning order */
+
 /* Diagnostics.  Timeout of every bounded device-side wait of this context, in
  * seconds (default 10): the tensor-core synthesis waits on its TMA copies and
  * MMAs, and the large CG solves wait on the bulk row copies of their pipeline.

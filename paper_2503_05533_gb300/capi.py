@@ -72,6 +72,12 @@ class mlmc_profile(ctypes.Structure):
                 ("solve_flops", c_double)]
 
 
+class mlmc_tune_entry(ctypes.Structure):
+    _fields_ = [("shape", ctypes.c_char * 192), ("prec", c_int), ("solver", c_int), ("precond", c_int),
+                ("med_items", c_int), ("ring", c_int), ("nu", c_int), ("theta", c_double),
+                ("best_ms", c_double), ("default_ms", c_double), ("trials", c_int)]
+
+
 SAMPLER_FN = ctypes.CFUNCTYPE(c_int, c_void_p, c_int, c_int64, c_int, POINTER(c_double), POINTER(c_double))
 
 # name -> (restype, argtypes)
@@ -102,6 +108,9 @@ _SIGS = {
     "mlmc_adjoint_grad": (c_int, [c_void_p, c_int, c_int, c_void_p, c_int, c_double, c_int, c_void_p, c_void_p,
                                   c_void_p]),
     "mlmc_set_wait_timeout": (c_int, [c_void_p, c_double]),
+    "mlmc_set_autotune": (c_int, [c_void_p, c_int]),
+    "mlmc_autotune_count": (c_int, [c_void_p]),
+    "mlmc_autotune_entry": (c_int, [c_void_p, c_int, c_void_p]),
     "mlmc_debug_set_wait_extra": (c_int, [c_void_p, c_int]),
     "mlmc_debug_set_solve_ring": (c_int, [c_void_p, c_int]),
     "mlmc_debug_set_medium_items": (c_int, [c_void_p, c_int]),
@@ -195,6 +204,22 @@ def mlmc_version():
 
 def mlmc_launch_count():
     return lib().mlmc_launch_count()
+
+
+def mlmc_set_autotune(ctx, on=True):
+    _check(lib().mlmc_set_autotune(ctx, 1 if on else 0), ctx)
+
+
+def mlmc_autotune_count(ctx):
+    return lib().mlmc_autotune_count(ctx)
+
+
+def mlmc_autotune_entry(ctx, i):
+    e = mlmc_tune_entry()
+    _check(lib().mlmc_autotune_entry(ctx, i, byref(e)), ctx)
+    d = {name: getattr(e, name) for name, _ in mlmc_tune_entry._fields_}
+    d["shape"] = e.shape.decode()
+    return d
 
 
 def mlmc_set_wait_timeout(ctx, seconds):

@@ -501,6 +501,33 @@ mlmc_status mlmc_set_inner_tolerance(mlmc_ctx* ctx, double theta, double tau_min
     return MLMC_OK;
 }
 
+mlmc_status mlmc_set_autotune(mlmc_ctx* ctx, int on) {
+    if (!ctx) return MLMC_E_ARG;
+    ctx->autotune = on != 0;
+    return MLMC_OK;
+}
+
+int mlmc_autotune_count(const mlmc_ctx* ctx) { return ctx ? (int)ctx->tune_order.size() : 0; }
+
+mlmc_status mlmc_autotune_entry(const mlmc_ctx* ctx, int i, mlmc_tune_entry* out) {
+    if (!ctx || !out || i < 0 || i >= (int)ctx->tune_order.size()) return MLMC_E_ARG;
+    const std::string& key = ctx->tune_order[(size_t)i];
+    const TuneChoice& t = ctx->tune.at(key);
+    std::memset(out, 0, sizeof(*out));
+    std::strncpy(out->shape, key.c_str(), sizeof(out->shape) - 1);
+    out->prec = t.prec;
+    out->solver = t.solver;
+    out->precond = t.precond;
+    out->med_items = t.med_items;
+    out->ring = t.ring;
+    out->nu = t.nu;
+    out->theta = t.theta;
+    out->best_ms = t.best_ms;
+    out->default_ms = t.default_ms;
+    out->trials = t.trials;
+    return MLMC_OK;
+}
+
 mlmc_status mlmc_debug_set_medium_items(mlmc_ctx* ctx, int items) {
     // a quarter's sweeps need a row's chunks (n/4 + 1) to fit its 128 threads: n <= 256 is far inside
     if (!ctx || (items != -1 && (items < 512 || items > 16384))) return MLMC_E_ARG;

@@ -173,6 +173,55 @@ template <class CT> struct SmemLoad<__nv_bfloat16, CT> {
     static __device__ __forceinline__ CT load1(const __nv_bfloat16* p) { return (CT)__bfloat162float(*p); }
 };
 
+// ---------------------------------------------------------------------------
+// Float-float arithmetic: a value h + l with |l| <= ulp(h) / 2 (about 48 significant bits) on
+// the FP32 pipe, GB300's FP64 pipe being narrow.  Error-free transformations (Knuth's TwoSum,
+// Dekker's FastTwoSum, the FMA product error) with explicit round-to-nearest operations, which
+// the compiler never contracts.
+struct __align__(8) ff2 {
+    float h, l;
+};
+__device__ __forceinline__ void ff_two_sum(float a, float b, float& s, float& e) {
+    s = __fadd_rn(a, b);
+    const float bb = __fsub_rn(s, a);
+    e = __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb));
+}
+__device__ __forceinline__ void ff_fast_two_sum(float a, float b, float& s, float& e) {   // |a| >= |b| or a = 0
+    s = __fadd_rn(a, b);
+    e = __fsub_rn(b, __fsub_rn(s, a));
+}
+__device__ __forceinline__ void ff_two_prod(float a, float b, float& p, float& e) {
+    p = __fmul_rn(a, b);
+    e = __fmaf_rn(a, b, -p);
+}
+__device__ __forceinline__ ff2 ff_add(ff2 a, ff2 b) {
+    float s, e, h, l;
+    ff_two_sum(a.h, b.h, s, e);
+    ff_fast_two_sum(s, __fadd_rn(e, __fadd_rn(a.l, b.l)), h, l);
+    return {h, l};
+}
+__device__ __forceinline__ ff2 ff_neg(ff2 a) { return {-a.h, -a.l}; }
+__device__ __forceinline__ ff2 ff_sub(ff2 a, ff2 b) { return ff_add(a, ff_neg(b)); }
+__device__ __forceinline__ ff2 ff_mul(ff2 a, ff2 b) {
+    float p, e, h, l;
+    ff_two_prod(a.h, b.h, p, e);
+    e = __fmaf_rn(a.h, b.l, __fmaf_rn(a.l, b.h, e));
+    ff_fast_two_sum(p, e, h, l);
+    return {h, l};
+}
+__device__ __forceinline__ ff2 ff_add_f(ff2 a, float b) {
+    float s, e, h, l;
+    ff_two_sum(a.h, b, s, e);
+    ff_fast_two_sum(s, __fadd_rn(e, a.l), h, l);
+    return {h, l};
+}
+// Nearest float-float of a double (two conversions and a subtraction on the FP64 pipe).
+__device__ __forceinline__ ff2 ff_from_d(double x) {
+    const float h = __double2float_rn(x);
+    return {h, __double2float_rn(x - (double)h)};
+}
+__device__ __forceinline__ double ff_to_d(ff2 a) { return (double)a.h + (double)a.l; }
+
 // Widen one stored coefficient value (a register, not memory) to the compute type.
 template <class CT> __device__ __forceinline__ CT widen(double v) { return (CT)v; }
 template <class CT> __device__ __forceinline__ CT widen(float v) { return (CT)v; }

@@ -59,6 +59,17 @@ struct GridBasis {
 };
 
 constexpr int kSolveSlots = 4;   // solve batches that may run concurrently (one per precision class)
+constexpr int kTuneUnset = -3;   // a SolveConfig launch setting left to the context
+
+// The autotuner's choice for one launch shape (see solver_common.cu): SolveConfig launch settings
+// (kTuneUnset / 0: the context's own) and the timings that chose them.
+struct TuneChoice {
+    int prec = 0, solver = 0, precond = 0;
+    int med_items = kTuneUnset, ring = kTuneUnset, nu = 0;
+    double theta = 0.0;
+    float best_ms = 0.f, default_ms = 0.f;
+    int trials = 0;
+};
 
 struct Workspace {
     DevBuf solver_slot[kSolveSlots];   // solver scratch (vectors, descriptors), one per concurrent batch
@@ -112,6 +123,9 @@ struct mlmc_ctx {
     double inner_tau_min = -1.0;  // < 0: per-precision default
     mlmc::Profile prof;
     cudaStream_t aux[mlmc::kSolveSlots - 1] = {};   // streams of concurrent solve batches (created on demand)
+    bool autotune = false;        // time candidate launch settings for every new launch shape
+    std::map<std::string, mlmc::TuneChoice> tune;   // launch shape -> chosen settings
+    std::vector<std::string> tune_order;            // keys in the order they were tuned
 };
 
 namespace mlmc {
@@ -172,6 +186,11 @@ struct SolveConfig {
     int tile_nodes = 2048;      // target nodes per warp tile
     int jacobi = 1;             // Jacobi-preconditioned inner CG
     int precond = -1;           // MLMC_PC_*, or -1: the context's choice (mlmc_set_precond)
+    // launch settings of the autotuner, overriding the context's (kTuneUnset / 0: the context's)
+    int med_items = kTuneUnset;
+    int ring = kTuneUnset;
+    int nu = 0;
+    double theta = 0.0;
 };
 struct SolveStats {
     int64_t inner_iters = 0;    // summed over solves (host copy, only if requested)

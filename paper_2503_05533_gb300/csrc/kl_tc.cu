@@ -182,21 +182,6 @@ __device__ __forceinline__ bool kl_warp_wait(uint64_t* bar, uint32_t parity, vol
     return ok;
 }
 
-// ---- float-float arithmetic (explicit round-to-nearest operations: never contracted)
-__device__ __forceinline__ void two_sum(float a, float b, float& s, float& e) {
-    s = __fadd_rn(a, b);
-    const float bb = __fsub_rn(s, a);
-    e = __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb));
-}
-__device__ __forceinline__ void fast_two_sum(float a, float b, float& s, float& e) {   // |a| >= |b|
-    s = __fadd_rn(a, b);
-    e = __fsub_rn(b, __fsub_rn(s, a));
-}
-__device__ __forceinline__ void two_prod(float a, float b, float& p, float& e) {
-    p = __fmul_rn(a, b);
-    e = __fmaf_rn(a, b, -p);
-}
-
 // exp(xh + xl) as a float-float pair (Tang's table-driven method, see the file comment).
 __device__ __forceinline__ void ff_exp(float xh, float xl, const FFExp& T, float& rh, float& rl) {
     const int N = __float2int_rn(__fmul_rn(xh, T.inv));
@@ -206,29 +191,29 @@ __device__ __forceinline__ void ff_exp(float xh, float xl, const FFExp& T, float
     // r = x - N ln2/32: xh - N l1 is exact (N l1 has at most 24 bits and is within a factor 2 of xh)
     const float t = __fsub_rn(xh, __fmul_rn(nf, T.l1));
     float p, pe, s, se;
-    two_prod(nf, T.l2, p, pe);
-    two_sum(t, -p, s, se);
+    ff_two_prod(nf, T.l2, p, pe);
+    ff_two_sum(t, -p, s, se);
     const float lo = __fsub_rn(__fadd_rn(se, xl), __fmaf_rn(nf, T.l3, pe));
     float r, rlo;
-    fast_two_sum(s, lo, r, rlo);
+    ff_fast_two_sum(s, lo, r, rlo);
     // exp(r) - 1 = r + r^2/2 + r^3 (1/6 + r (1/24 + r/120))
     float sq, sqe;
-    two_prod(r, r, sq, sqe);
+    ff_two_prod(r, r, sq, sqe);
     const float r3 = __fmul_rn(__fmul_rn(sq, r),
                                __fmaf_rn(r, __fmaf_rn(r, 1.0f / 120.0f, 1.0f / 24.0f), 1.0f / 6.0f));
     float qh, qe;
-    two_sum(r, __fmul_rn(0.5f, sq), qh, qe);
+    ff_two_sum(r, __fmul_rn(0.5f, sq), qh, qe);
     const float ql0 = __fadd_rn(__fadd_rn(qe, rlo), __fadd_rn(__fmaf_rn(0.5f, sqe, __fmul_rn(r, rlo)), r3));
     float q, ql;
-    fast_two_sum(qh, ql0, q, ql);
+    ff_fast_two_sum(qh, ql0, q, ql);
     // 2^(j/32) (1 + q)
     const float th = T.th[j], tl = T.tl[j];
     float ph, phe, s1, s1e;
-    two_prod(th, q, ph, phe);
-    two_sum(th, ph, s1, s1e);
+    ff_two_prod(th, q, ph, phe);
+    ff_two_sum(th, ph, s1, s1e);
     const float lo2 = __fadd_rn(__fadd_rn(s1e, phe), __fmaf_rn(th, ql, __fmaf_rn(tl, q, tl)));
     float h, l;
-    fast_two_sum(s1, lo2, h, l);
+    ff_fast_two_sum(s1, lo2, h, l);
     rh = ldexpf(h, m);
     rl = ldexpf(l, m);
 }
@@ -465,9 +450,9 @@ __global__ void __launch_bounds__(KLLayout<MODE>::kThreads, 1)
                     const float ih = (float)ii;
                     const float il = (float)(ii - (int)ih);
                     float h, e2;
-                    two_sum(ih, s1f[j], h, e2);
+                    ff_two_sum(ih, s1f[j], h, e2);
                     float lh, ll;
-                    fast_two_sum(h, __fadd_rn(e2, il), lh, ll);
+                    ff_fast_two_sum(h, __fadd_rn(e2, il), lh, ll);
                     lh = ldexpf(lh, sc);
                     ll = ldexpf(ll, sc);
                     float ah, al;

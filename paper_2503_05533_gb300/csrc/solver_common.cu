@@ -6,6 +6,7 @@
 
 #include <algorithm>
 #include <cmath>
+#include <map>
 #include <mutex>
 #include <string>
 #include <vector>
@@ -74,10 +75,145 @@ mlmc_status launch_batch(mlmc_ctx* ctx, const std::vector<SolveGroup>& groups, c
     }
 }
 
+// ---------------------------------------------------------------------------
+// Autotuner (mlmc_set_autotune).  A launch shape -- inner precision, solver, preconditioner, and the
+// batch's grids with their system counts rounded down to powers of two -- that has not been seen is
+// solved once per candidate setting, starting from the library's own rules and changing one setting
+// at a time (coordinate descent): the group size of n = 91..128 systems (2048 or 4096 chunks per
+// 128-thread group), the row-pipeline depth of Jacobi-preconditioned CG (0, 2, 4 slots), the
+// V-cycle's smoothing sweeps (1, 2) and the inner tolerance factor theta (0.1, 0.3, 0.6).  Each
+// candidate is timed twice with CUDA events on the stream (the minimum counts); a change is kept if
+// it is at least 1% faster.  Every trial solves the same systems to the same accuracy, so the
+// outputs of the last trial are valid results.
+std::string tune_key(const std::vector<SolveGroup>& groups, const SolveConfig& cfg, int precond) {
+    std::map<int, long long> cnt;
+    for (const SolveGroup& g : groups)
+        if (g.S > 0) cnt[g.n] += g.S;
+    std::string k = "prec " + std::to_string(cfg.prec) + " solver " + std::to_string(cfg.solver) + " pc " +
+                    std::to_string(precond) + ":";
+    for (const auto& kv : cnt) {
+        int c = 0;
+        while ((2LL << c) <= kv.second) ++c;
+        k += " " + std::to_string(kv.first) + "x2^" + std::to_string(c);
+    }
+    return k;
+}
+
+void tune_apply(const TuneChoice& t, SolveConfig& cfg) {
+    cfg.med_items = t.med_items;
+    cfg.ring = t.ring;
+    cfg.nu = t.nu;
+    cfg.theta = t.theta;
+}
+
+// One timed solve of the batch (minimum of `reps` runs) with the settings of t.
+mlmc_status tune_time(mlmc_ctx* ctx, const std::vector<SolveGroup>& groups, SolveConfig cfg, const TuneChoice& t,
+                      cudaStream_t st, int reps, float* ms) {
+    tune_apply(t, cfg);
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    MLMC_CUDA_RET(ctx->err, cudaEventCreate(&e0));
+    MLMC_CUDA_RET(ctx->err, cudaEventCreate(&e1));
+    *ms = 1e30f;
+    mlmc_status s = MLMC_OK;
+    for (int r = 0; r < reps && s == MLMC_OK; ++r) {
+        PendingSolve p;
+        cudaEventRecord(e0, st);
+        s = launch_batch(ctx, groups, cfg, st, 0, p);
+        cudaEventRecord(e1, st);
+        const cudaError_t e = cudaStreamSynchronize(st);
+        if (s == MLMC_OK && e != cudaSuccess) {
+            ctx->err = std::string("autotune: ") + cudaGetErrorString(e);
+            s = MLMC_E_CUDA;
+        }
+        float x = 0.f;
+        if (s == MLMC_OK && cudaEventElapsedTime(&x, e0, e1) == cudaSuccess) *ms = std::min(*ms, x);
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    return s;
+}
+
+mlmc_status autotune_batch(mlmc_ctx* ctx, const std::vector<SolveGroup>& groups, SolveConfig& cfg, cudaStream_t st) {
+    const int precond = cfg.precond >= 0 ? cfg.precond : ctx->precond;
+    const std::string key = tune_key(groups, cfg, precond);
+    auto it = ctx->tune.find(key);
+    if (it != ctx->tune.end()) {
+        tune_apply(it->second, cfg);
+        return MLMC_OK;
+    }
+    // which settings can matter for this shape
+    bool has_mid = false, pipe_sizes = false;
+    for (const SolveGroup& g : groups) {
+        if (g.S <= 0) continue;
+        const long long items = (long long)(g.n - 1) * ((g.n - 1) / 4 + 1);
+        if (items > 2048 && items <= 4096) has_mid = true;
+        if (items > 2048 && ((g.n - 1) / 4 + 1) % 32 == 0) pipe_sizes = true;
+    }
+    const bool mg = precond == MLMC_PC_MG;
+    const bool ring_matters = cfg.solver == MLMC_CG && !mg && cfg.prec != MLMC_FP64 && pipe_sizes;
+    const bool prof = ctx->prof.on;
+    ctx->prof.on = false;   // trials are not part of the profile
+    TuneChoice cur;
+    cur.prec = cfg.prec;
+    cur.solver = cfg.solver;
+    cur.precond = precond;
+    float best = 0.f;
+    mlmc_status s = tune_time(ctx, groups, cfg, cur, st, 2, &best);
+    cur.default_ms = best;
+    int trials = 2;
+    auto consider = [&](TuneChoice cand) {
+        if (s != MLMC_OK) return;
+        float ms = 0.f;
+        s = tune_time(ctx, groups, cfg, cand, st, 2, &ms);
+        trials += 2;
+        if (s == MLMC_OK && ms < 0.99f * best) {
+            best = ms;
+            cur = cand;
+        }
+    };
+    if (has_mid)
+        for (int m : {2048, 4096}) {
+            TuneChoice c = cur;
+            c.med_items = m;
+            consider(c);
+        }
+    if (ring_matters)
+        for (int r : {0, 2, 4}) {
+            TuneChoice c = cur;
+            c.ring = r;
+            consider(c);
+        }
+    if (mg)
+        for (int nu : {1, 2}) {
+            if (nu == ctx->mg_nu) continue;
+            TuneChoice c = cur;
+            c.nu = nu;
+            consider(c);
+        }
+    for (double th : {0.1, 0.6}) {
+        TuneChoice c = cur;
+        c.theta = th;
+        consider(c);
+    }
+    ctx->prof.on = prof;
+    if (s != MLMC_OK) return s;
+    cur.best_ms = best;
+    cur.trials = trials;
+    ctx->tune[key] = cur;
+    ctx->tune_order.push_back(key);
+    tune_apply(cur, cfg);
+    return MLMC_OK;
+}
+
 }  // namespace
 
-mlmc_status run_solve_batch(mlmc_ctx* ctx, const std::vector<SolveGroup>& groups, const SolveConfig& cfg,
+mlmc_status run_solve_batch(mlmc_ctx* ctx, const std::vector<SolveGroup>& groups, const SolveConfig& cfg_in,
                             cudaStream_t st) {
+    SolveConfig cfg = cfg_in;
+    if (ctx->autotune) {
+        const mlmc_status t = autotune_batch(ctx, groups, cfg, st);
+        if (t != MLMC_OK) return t;
+    }
     PendingSolve p;
     mlmc_status s = launch_batch(ctx, groups, cfg, st, 0, p);
     if (s != MLMC_OK) return s;
@@ -89,8 +225,9 @@ mlmc_status run_solve_batch(mlmc_ctx* ctx, const std::vector<SolveGroup>& groups
 
 mlmc_status launch_solve_async(mlmc_ctx* ctx, const std::vector<SolveGroup>& groups, const SolveConfig& cfg,
                                cudaStream_t st) {
-    // profiling reads the launch's per-system counters from its workspace, which the next call reuses
-    if (ctx->prof.on) return run_solve_batch(ctx, groups, cfg, st);
+    // profiling reads the launch's per-system counters from its workspace, which the next call reuses;
+    // tuning a new launch shape times its candidates
+    if (ctx->prof.on || ctx->autotune) return run_solve_batch(ctx, groups, cfg, st);
     PendingSolve p;
     return launch_batch(ctx, groups, cfg, st, 0, p);
 }
@@ -101,6 +238,15 @@ mlmc_status run_solve_batches(mlmc_ctx* ctx, const std::vector<SolveBatch>& batc
     if (batches.size() > (size_t)kSolveSlots) {
         ctx->err = "run_solve_batches: too many concurrent batches";
         return MLMC_E_ARG;
+    }
+    // settings of each batch (the autotuner times a new shape alone, on st, before the concurrent launch)
+    std::vector<SolveConfig> cfgs;
+    for (const SolveBatch& b : batches) {
+        cfgs.push_back(b.cfg);
+        if (ctx->autotune) {
+            const mlmc_status t = autotune_batch(ctx, b.groups, cfgs.back(), st);
+            if (t != MLMC_OK) return t;
+        }
     }
     // fork: batch 0 on st, batch i > 0 on the context's auxiliary stream i - 1, all after st's prior work
     cudaEvent_t fork = nullptr;
@@ -124,7 +270,7 @@ mlmc_status run_solve_batches(mlmc_ctx* ctx, const std::vector<SolveBatch>& batc
                 break;
             }
         }
-        status = launch_batch(ctx, batches[i].groups, batches[i].cfg, si, (int)i, pend[i]);
+        status = launch_batch(ctx, batches[i].groups, cfgs[i], si, (int)i, pend[i]);
         if (status == MLMC_OK && i > 0) {
             // join: st waits for batch i
             if (cudaEventCreateWithFlags(&done[i], cudaEventDisableTiming) != cudaSuccess ||
