@@ -621,6 +621,59 @@ def paper_case(M, torch, dev, args, flush, stream):
             per[name]["flop_gain_vs_mlmc_1e-6"] = base["flops"] / per[name]["flops"]
             per[name]["time_gain_vs_mlmc_1e-6"] = base["seconds"] / per[name]["seconds"]
         out["results"]["TOL2=%g" % tol2] = per
+    out["cholesky"] = paper_cholesky(M, torch, dev, args, flush, stream, prob_kw)
+    return out
+
+
+def paper_cholesky(M, torch, dev, args, flush, stream, prob_kw):
+    """The paper's direct-solver experiment (Sec. 5.2): the same field and hierarchy, MPML solving with a
+    banded Cholesky factor in low precision and iterative refinement (Table 1, right: hhss on level 0,
+    ssss on level 1, ssdd above) against standard MLMC with an FP64 factor (dddd), both on the sample
+    counts of an adaptive standard-MLMC run and the same seeds.  Cost: the memory model of Sec. 5.2
+    (bits of every factor and vector entry computed and stored; the paper reports about 2x) beside the
+    measured time."""
+    import ctypes
+    import math
+    out = {"paper_memory_gain": 2.0, "results": {}}
+    for tol2 in (8e-6, 4e-6, 2e-6, 1e-6):
+        tol = math.sqrt(tol2)
+        bits = {"mpml": [], "mlmc": []}
+        secs = {"mpml": [], "mlmc": []}
+        for run in range(args.paper_runs):
+            kw = dict(prob_kw, L_max=3, seed=2025 + run)
+            h = M.mlmc_create(M.make_problem(**kw), dev.index or 0)
+            try:
+                o = M.mlmc_default_options()
+                o.tol, o.form, o.solver, o.fixed_delta = tol, M.MLMC_FORM_FP64_FIXED, M.MLMC_CHOLESKY, 1e-10
+                r0 = M.result_dict(M.mlmc_estimate(h, o))        # sample counts of the adaptive MLMC run
+            finally:
+                M.mlmc_destroy(h)
+            Nl = [int(x) for x in r0["N"][: r0["L"] + 1]]
+            arr = (ctypes.c_int64 * len(Nl))(*Nl)
+            for name, form in (("mpml", M.MLMC_FORM_MIXED), ("mlmc", M.MLMC_FORM_FP64_FIXED)):
+                h = M.mlmc_create(M.make_problem(**kw), dev.index or 0)
+                try:
+                    o = M.mlmc_default_options()
+                    o.form, o.solver, o.fixed_delta, o.L_start = form, M.MLMC_CHOLESKY, 1e-10, len(Nl) - 1
+                    o.fixed_N = ctypes.cast(arr, ctypes.POINTER(ctypes.c_int64))
+                    M.mlmc_estimate(h, o)
+                    M.mlmc_profile_enable(h, True)
+                    M.mlmc_profile_reset(h)
+                    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                    e0.record(stream)
+                    M.mlmc_estimate(h, o)
+                    e1.record(stream)
+                    e1.synchronize()
+                    prof = M.mlmc_profile_get(h)
+                finally:
+                    M.mlmc_destroy(h)
+                bits[name].append(prof["chol_bits"])
+                secs[name].append(e0.elapsed_time(e1) / 1e3)
+        out["results"]["TOL2=%g" % tol2] = {
+            "memory_gain": sum(bits["mlmc"]) / sum(bits["mpml"]),
+            "time_gain": sum(secs["mlmc"]) / sum(secs["mpml"]),
+            "mpml_seconds": sum(secs["mpml"]) / len(secs["mpml"]),
+            "mlmc_seconds": sum(secs["mlmc"]) / len(secs["mlmc"])}
     return out
 
 

@@ -61,7 +61,12 @@ typedef enum {
                          (see mlmc_sample_fields); not an inner precision        */
 } mlmc_prec;
 
-typedef enum { MLMC_CG = 0, MLMC_MINRES = 1 } mlmc_solver;
+/* Solvers of the correction equation in the refinement (Alg. 2.1): the Krylov
+ * methods of Sec. 2.2, and the banded Cholesky factorisation of Sec. 5.2,
+ * computed once per system in the precision `prec` (IEEE half, bfloat16,
+ * single or double storage; FP32 arithmetic below double) and reused by every
+ * correction solve.  The Cholesky solver takes grids of 2 to 128 cells. */
+typedef enum { MLMC_CG = 0, MLMC_MINRES = 1, MLMC_CHOLESKY = 2 } mlmc_solver;
 /* Preconditioner of the inner solves (CG and MINRES). */
 typedef enum { MLMC_PC_JACOBI = 0, MLMC_PC_MG = 1 } mlmc_precond;   /* Sec. 2.2 */
 
@@ -377,6 +382,14 @@ mlmc_status mlmc_adjoint_grad(mlmc_ctx* ctx, int level, int S, const double* xi,
  * on the FP64 residual of the refinement (Alg. 2.1). */
 mlmc_status mlmc_set_precond(mlmc_ctx* ctx, mlmc_precond pc, int nu, int coarse_sweeps, double omega);
 
+/* Working precision u (of the iterate x) and residual precision u_r of the
+ * refinement of this context's Cholesky solves (MLMC_CHOLESKY), each MLMC_FP32
+ * or MLMC_FP64 (default FP64, FP64); with the factor precision `prec` of
+ * mlmc_level_solve they form the quadruple (u_f, u_s = u_f, u, u_r) of Sec. 5.2,
+ * e.g. (half, half, single, single) for `hhss`.  mlmc_estimate with the
+ * Cholesky solver sets these per level itself (Table 1, right). */
+mlmc_status mlmc_set_cholesky_precision(mlmc_ctx* ctx, mlmc_prec u, mlmc_prec u_r);
+
 /* Inner tolerance of the refinement (Alg. 2.1) for this context's solves: each
  * inner solve stops at ||r_k|| <= tau ||r_0|| with tau = clamp(theta delta /
  * rho, tau_min, 0.5), rho the current relative residual.  theta = 0 keeps the
@@ -448,6 +461,10 @@ typedef struct {
                                   their recurrences and dots, plus the V-cycle with multigrid; per
                                   refinement step the FP64 residual and its dots (20) and the update;
                                   set-up (edge weights, inverse diagonal) and the QoI */
+    double chol_bits;          /* Cholesky solves: the memory cost model of Sec. 5.2 -- bits of every
+                                  entry computed and stored while solving: the factor's nonzeros
+                                  (N (bw+1) - bw (bw+1)/2, bw = n - 1) in u_f, x_0 in u, each residual in
+                                  u_r, each correction and update in u */
 } mlmc_profile;
 mlmc_status mlmc_profile_enable(mlmc_ctx* ctx, int on);
 mlmc_status mlmc_profile_get(mlmc_ctx* ctx, mlmc_profile* out);   /* synchronises the device */

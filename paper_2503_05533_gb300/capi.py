@@ -23,7 +23,7 @@ STATUS_NAMES = ["MLMC_OK", "MLMC_E_ARG", "MLMC_E_NOMEM", "MLMC_E_CUDA", "MLMC_E_
 # mlmc_prec
 MLMC_FP64, MLMC_FP32, MLMC_BF16S, MLMC_FP16S, MLMC_FP64TC = range(5)
 # mlmc_solver
-MLMC_CG, MLMC_MINRES = range(2)
+MLMC_CG, MLMC_MINRES, MLMC_CHOLESKY = range(3)
 MLMC_PC_JACOBI, MLMC_PC_MG = range(2)
 # mlmc_form
 MLMC_FORM_MIXED, MLMC_FORM_FP64_ADAPTIVE, MLMC_FORM_FP64_FIXED = range(3)
@@ -69,7 +69,7 @@ class mlmc_profile(ctypes.Structure):
                 ("inner_iters", c_int64), ("unknown_iters", c_int64), ("kl_launches", c_int64),
                 ("kl_ms", c_double), ("kl_bytes", c_double), ("kl_flops", c_double),
                 ("h2d_bytes", c_int64), ("d2h_bytes", c_int64), ("solve_busy_ms", c_double),
-                ("solve_flops", c_double)]
+                ("solve_flops", c_double), ("chol_bits", c_double)]
 
 
 class mlmc_tune_entry(ctypes.Structure):
@@ -109,6 +109,7 @@ _SIGS = {
                                   c_void_p]),
     "mlmc_set_wait_timeout": (c_int, [c_void_p, c_double]),
     "mlmc_set_autotune": (c_int, [c_void_p, c_int]),
+    "mlmc_set_cholesky_precision": (c_int, [c_void_p, c_int, c_int]),
     "mlmc_autotune_count": (c_int, [c_void_p]),
     "mlmc_autotune_entry": (c_int, [c_void_p, c_int, c_void_p]),
     "mlmc_debug_set_wait_extra": (c_int, [c_void_p, c_int]),
@@ -204,6 +205,10 @@ def mlmc_version():
 
 def mlmc_launch_count():
     return lib().mlmc_launch_count()
+
+
+def mlmc_set_cholesky_precision(ctx, u, u_r):
+    _check(lib().mlmc_set_cholesky_precision(ctx, u, u_r), ctx)
 
 
 def mlmc_set_autotune(ctx, on=True):

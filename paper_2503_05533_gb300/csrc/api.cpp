@@ -304,7 +304,7 @@ mlmc_status check_options(const mlmc_options* o, int L_max, std::string& err) {
         return MLMC_E_ARG;
     }
     if (o->form < 0 || o->form > 2 || (o->force_prec >= 0 && !is_prec(o->force_prec)) ||
-        (o->solver != MLMC_CG && o->solver != MLMC_MINRES) || o->max_iters < 1) {
+        (o->solver != MLMC_CG && o->solver != MLMC_MINRES && o->solver != MLMC_CHOLESKY) || o->max_iters < 1) {
         err = "options: bad form, precision, solver or max_iters";
         return MLMC_E_ARG;
     }
@@ -501,6 +501,15 @@ mlmc_status mlmc_set_inner_tolerance(mlmc_ctx* ctx, double theta, double tau_min
     return MLMC_OK;
 }
 
+mlmc_status mlmc_set_cholesky_precision(mlmc_ctx* ctx, mlmc_prec u, mlmc_prec u_r) {
+    if (!ctx) return MLMC_E_ARG;
+    if ((u != MLMC_FP32 && u != MLMC_FP64) || (u_r != MLMC_FP32 && u_r != MLMC_FP64))
+        return fail(ctx, MLMC_E_ARG, "set_cholesky_precision: u and u_r must be MLMC_FP32 or MLMC_FP64");
+    ctx->chol_u = u;
+    ctx->chol_ur = u_r;
+    return MLMC_OK;
+}
+
 mlmc_status mlmc_set_autotune(mlmc_ctx* ctx, int on) {
     if (!ctx) return MLMC_E_ARG;
     ctx->autotune = on != 0;
@@ -595,7 +604,7 @@ mlmc_status mlmc_level_solve(mlmc_ctx* ctx, int n, int S, const void* a, mlmc_pr
                              double* Q, int32_t* iters, double* relres, int32_t* flags, void* stream) {
     if (!ctx) return MLMC_E_ARG;
     if (n < 2 || n > 2048 || S < 0 || a_n < n || a_n % n != 0 || !is_master_prec(a_prec) || !is_prec(prec) ||
-        (solver != MLMC_CG && solver != MLMC_MINRES) || !(delta > 0) || max_iters < 1)
+        (solver != MLMC_CG && solver != MLMC_MINRES && solver != MLMC_CHOLESKY) || !(delta > 0) || max_iters < 1)
         return fail(ctx, MLMC_E_ARG, "level_solve: bad n, S, a_n, precision, solver, delta or max_iters");
     if (S == 0) return MLMC_OK;
     if (!a || !Q) return fail(ctx, MLMC_E_ARG, "level_solve: null a or Q");
@@ -616,6 +625,8 @@ mlmc_status mlmc_level_solve(mlmc_ctx* ctx, int n, int S, const void* a, mlmc_pr
     cfg.prec = prec;
     cfg.solver = solver;
     cfg.max_iters = max_iters;
+    cfg.chol_u = ctx->chol_u;
+    cfg.chol_ur = ctx->chol_ur;
     cudaStream_t st = static_cast<cudaStream_t>(stream);
     MLMC_CUDA_RET(ctx->err, ctx_order_begin(ctx, st));
     const mlmc_status s = launch_solve_async(ctx, {g}, cfg, st);
@@ -741,7 +752,18 @@ mlmc_status mlmc_estimate(mlmc_ctx* ctx, const mlmc_options* opts, mlmc_result* 
         auto prec_of = [&](int l) -> mlmc_prec {
             if (o.form != MLMC_FORM_MIXED) return MLMC_FP64;
             if (o.force_prec >= 0) return (mlmc_prec)o.force_prec;
+            // the Cholesky solver of Sec. 5.2 takes Table 1 (right): a half factor on level 0, single above
+            if (o.solver == MLMC_CHOLESKY) return l == 0 ? MLMC_FP16S : MLMC_FP32;
             return prec_rule[l];
+        };
+        // launch class of a solve: the factor / inner precision, plus for the Cholesky solver the working
+        // and residual precisions of Table 1 (right): single on levels 0 and 1 (hhss, ssss), double above
+        // (ssdd); double throughout for the FP64 forms (dddd)
+        auto class_of = [&](int l) -> int {
+            const int p = prec_of(l);
+            if (o.solver != MLMC_CHOLESKY) return p;
+            const bool dbl = o.form != MLMC_FORM_MIXED || l >= 2;
+            return p | (dbl ? 0 : 16);
         };
         size_t fbytes = 0, xbytes = 0, qn = 0;
         std::vector<size_t> foff(req.size()), xoff(req.size()), qoff(req.size());
@@ -795,8 +817,8 @@ mlmc_status mlmc_estimate(mlmc_ctx* ctx, const mlmc_options* opts, mlmc_result* 
             gf.Q = Qf + qoff[i];
             gf.iters = itf + qoff[i];
             gf.flags = flf + qoff[i];
-            classes[prec_of(l)].push_back(gf);
-            class_level[prec_of(l)].push_back(l);
+            classes[class_of(l)].push_back(gf);
+            class_level[class_of(l)].push_back(l);
             prec_lvl[l] = prec_of(l);
             dofs_lvl[l] += (int64_t)req[i].count * (n - 1) * (n - 1);
             if (l > 0) {
@@ -806,8 +828,8 @@ mlmc_status mlmc_estimate(mlmc_ctx* ctx, const mlmc_options* opts, mlmc_result* 
                 gc.Q = Qc + qoff[i];
                 gc.iters = itc + qoff[i];
                 gc.flags = flc + qoff[i];
-                classes[prec_of(l - 1)].push_back(gc);
-                class_level[prec_of(l - 1)].push_back(l);
+                classes[class_of(l - 1)].push_back(gc);
+                class_level[class_of(l - 1)].push_back(l);
                 dofs_lvl[l] += (int64_t)req[i].count * (gc.n - 1) * (gc.n - 1);
             }
         }
@@ -817,9 +839,11 @@ mlmc_status mlmc_estimate(mlmc_ctx* ctx, const mlmc_options* opts, mlmc_result* 
         for (auto& kv : classes) {
             SolveBatch b;
             b.groups = kv.second;
-            b.cfg.prec = kv.first;
+            b.cfg.prec = kv.first & 15;
             b.cfg.solver = o.solver;
             b.cfg.max_iters = o.max_iters;
+            b.cfg.chol_u = (kv.first & 16) ? MLMC_FP32 : MLMC_FP64;
+            b.cfg.chol_ur = b.cfg.chol_u;
             batches.push_back(std::move(b));
         }
         {
@@ -837,7 +861,7 @@ mlmc_status mlmc_estimate(mlmc_ctx* ctx, const mlmc_options* opts, mlmc_result* 
             ctx->prof.acc.d2h_bytes += (int64_t)(4 * qn * sizeof(int32_t));
             std::vector<SolveGroup> retry;
             for (auto& kv : classes) {
-                if (kv.first == MLMC_FP64) continue;
+                if (kv.first == MLMC_FP64) continue;   // FP64 inner (or the dddd Cholesky)
                 const std::vector<int>& lv = class_level[kv.first];
                 for (size_t gi = 0; gi < kv.second.size(); ++gi) {
                     const SolveGroup& g = kv.second[gi];

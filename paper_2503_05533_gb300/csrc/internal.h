@@ -79,6 +79,7 @@ struct Workspace {
     DevBuf misc;           // small per-call scratch (flags, iteration counts)
     DevBuf split;          // split FP16 operands of the tensor-core synthesis
     DevBuf adj;            // adjoint path scratch
+    DevBuf chol;           // Cholesky solver: band factors, iterates, descriptors
     void* pinned = nullptr;    // pinned host staging
     size_t pinned_bytes = 0;
 };
@@ -116,6 +117,8 @@ struct mlmc_ctx {
     int solve_ring = -1;          // diagnostic: row-pipeline slots of large CG solves (-1 automatic, 0 off)
     int med_items = -1;           // diagnostic: most chunks of a system solved by a 128-thread group (-1 automatic)
     int precond = MLMC_PC_MG;     // preconditioner of the CG inner solves
+    int chol_u = MLMC_FP64;       // Cholesky solves: working precision of x (mlmc_set_cholesky_precision)
+    int chol_ur = MLMC_FP64;      // ... and precision of the refinement residual
     int mg_nu = 1;                // multigrid: smoothing sweeps before and after the coarse correction
     int mg_coarse = 8;            // multigrid: Jacobi sweeps on the coarsest grid
     double mg_omega = 0.8;        // multigrid: Jacobi damping
@@ -191,6 +194,9 @@ struct SolveConfig {
     int ring = kTuneUnset;
     int nu = 0;
     double theta = 0.0;
+    // Cholesky solver (MLMC_CHOLESKY): working precision u of x and residual precision u_r of Alg. 2.1
+    int chol_u = MLMC_FP64;
+    int chol_ur = MLMC_FP64;
 };
 struct SolveStats {
     int64_t inner_iters = 0;    // summed over solves (host copy, only if requested)
@@ -226,6 +232,11 @@ MLMC_DECLARE_SOLVER_PRECISION(fp16s)
 
 mlmc_status run_solve_batch(mlmc_ctx* ctx, const std::vector<SolveGroup>& groups, const SolveConfig& cfg,
                             cudaStream_t st);
+// cholesky.cu: the batch solved by the banded Cholesky factorisation in precision cfg.prec with
+// iterative refinement (working precision cfg.chol_u, residual cfg.chol_ur).  With sync, waits for
+// the launch and reads its profile and error words; without, enqueues it (no profile).
+mlmc_status run_cholesky_batch(mlmc_ctx* ctx, const std::vector<SolveGroup>& groups, const SolveConfig& cfg,
+                               cudaStream_t st, bool sync);
 // The same batch enqueued on st without waiting for it (errors surface at the context's next
 // synchronising call); with profiling on it synchronises to read the launch's counters.
 mlmc_status launch_solve_async(mlmc_ctx* ctx, const std::vector<SolveGroup>& groups, const SolveConfig& cfg,

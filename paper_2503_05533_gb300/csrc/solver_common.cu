@@ -209,6 +209,7 @@ mlmc_status autotune_batch(mlmc_ctx* ctx, const std::vector<SolveGroup>& groups,
 
 mlmc_status run_solve_batch(mlmc_ctx* ctx, const std::vector<SolveGroup>& groups, const SolveConfig& cfg_in,
                             cudaStream_t st) {
+    if (cfg_in.solver == MLMC_CHOLESKY) return run_cholesky_batch(ctx, groups, cfg_in, st, true);
     SolveConfig cfg = cfg_in;
     if (ctx->autotune) {
         const mlmc_status t = autotune_batch(ctx, groups, cfg, st);
@@ -227,6 +228,7 @@ mlmc_status launch_solve_async(mlmc_ctx* ctx, const std::vector<SolveGroup>& gro
                                cudaStream_t st) {
     // profiling reads the launch's per-system counters from its workspace, which the next call reuses;
     // tuning a new launch shape times its candidates
+    if (cfg.solver == MLMC_CHOLESKY) return run_cholesky_batch(ctx, groups, cfg, st, false);
     if (ctx->prof.on || ctx->autotune) return run_solve_batch(ctx, groups, cfg, st);
     PendingSolve p;
     return launch_batch(ctx, groups, cfg, st, 0, p);
@@ -235,6 +237,14 @@ mlmc_status launch_solve_async(mlmc_ctx* ctx, const std::vector<SolveGroup>& gro
 mlmc_status run_solve_batches(mlmc_ctx* ctx, const std::vector<SolveBatch>& batches, cudaStream_t st) {
     if (batches.size() <= 1) return batches.empty() ? MLMC_OK : run_solve_batch(ctx, batches[0].groups,
                                                                                  batches[0].cfg, st);
+    if (batches[0].cfg.solver == MLMC_CHOLESKY) {
+        // the Cholesky launches of a round run one after another
+        for (const SolveBatch& b : batches) {
+            const mlmc_status s = run_cholesky_batch(ctx, b.groups, b.cfg, st, true);
+            if (s != MLMC_OK) return s;
+        }
+        return MLMC_OK;
+    }
     if (batches.size() > (size_t)kSolveSlots) {
         ctx->err = "run_solve_batches: too many concurrent batches";
         return MLMC_E_ARG;

@@ -1376,11 +1376,6 @@ __device__ void solve_system(const Params& P, const DevSolve& S, const Group<GT>
     constexpr bool minres = SOLVER == MLMC_MINRES;
     // the FP64 inner solve applies its grid operator from the stored FP64 edge weights
     constexpr bool W64 = sizeof(VT) == 8 && sizeof(ST) == 8;
-    // Solves with FP32 inner arithmetic keep the refinement's FP64 quantities -- the iterate x and the
-    // edge weights of the master operator -- as float-float pairs in the same 8 bytes, and form the
-    // residual b - A x, the update x += d and the QoI in float-float on the FP32 pipe (about 48
-    // significant bits, far below any accuracy asked of a solve); the FP64 inner solve keeps FP64.
-    constexpr bool FF = sizeof(VT) == 4;
     const bool pipe_on = pipe != nullptr;
     VT* VB = minres ? static_cast<VT*>(P.vb) + S.off : nullptr;
     VT* W0 = minres ? static_cast<VT*>(P.w0) + S.off : nullptr;
@@ -1419,13 +1414,8 @@ __device__ void solve_system(const Params& P, const DevSolve& S, const Group<GT>
             if (j <= n - 1 && i >= 1 && i <= n - 1)
                 wn = 2.0 * (master_a(S, i, j) + master_a(S, i, j + 1)) + master_a(S, i + 1, j + 1) +
                      master_a(S, i - 1, j);
-            if constexpr (FF) {
-                reinterpret_cast<ff2*>(WE)[(size_t)j * ld + i] = ff_from_d(we);
-                reinterpret_cast<ff2*>(WN)[(size_t)j * ld + i] = ff_from_d(wn);
-            } else {
-                WE[(size_t)j * ld + i] = we;
-                WN[(size_t)j * ld + i] = wn;
-            }
+            WE[(size_t)j * ld + i] = we;
+            WN[(size_t)j * ld + i] = wn;
         }
     }
     if (mg) {
@@ -1454,71 +1444,14 @@ __device__ void solve_system(const Params& P, const DevSolve& S, const Group<GT>
 
     double rho = 0.0, rho_prev = 0.0;
     int iters = 0, flag = 0, o = 0;
-    // float-float refinement: the right-hand side f h^2, and a power of two rsc with rms(b) rsc in [1, 2)
-    [[maybe_unused]] const ff2 bff = ff_from_d(S.f * S.h2);
-    [[maybe_unused]] float rsc = 1.0f;
-    if constexpr (FF) {
-        int e2 = 0;
-        frexp(S.bnorm / (double)(n - 1), &e2);
-        rsc = ldexpf(1.0f, 1 - e2);
-    }
     for (;; ++o) {
         // ---- R: r = b - A x in FP64 with the master coefficient (r = b while x = 0); d = 0
         double res = 0.0, rr0 = 0.0, rz0 = 0.0;
-        [[maybe_unused]] float resf = 0.0f, rz0f = 0.0f;
         for (int it = tr; it < items; it += GT) {
             const int j = 1 + it / cpr, c = it - (j - 1) * cpr;
             const size_t base = (size_t)j * ld + 4 * c;
             VT rv[4], zv[4];
             if (jac) CoefLoad<ST, VT>::load4(DI + base, zv);
-            if constexpr (FF) {
-                // r = b - A x in float-float; the inner solve takes its leading part, and the norms
-                // are summed in FP32 after scaling by a power of two near 1 / rms(b)
-                if (o == 0) {
-#pragma unroll
-                    for (int q = 0; q < 4; ++q) {
-                        const int i = 4 * c + q;
-                        rv[q] = (i >= 1 && i <= n - 1) ? __double2float_rn(rhs_value(S, i, j)) : (VT)0;
-                    }
-                } else {
-                    const ff2* XF = reinterpret_cast<const ff2*>(X);
-                    const ff2* WEf = reinterpret_cast<const ff2*>(P.we + S.off);
-                    const ff2* WNf = reinterpret_cast<const ff2*>(P.wn + S.off);
-                    const ff2 z2 = {0.0f, 0.0f};
-                    ff2 xs[4], xc[6], xn[4], we[5], wn[4], ws[4];
-#pragma unroll
-                    for (int q = 0; q < 4; ++q) {
-                        xs[q] = XF[base - ld + q];
-                        xc[q + 1] = XF[base + q];
-                        xn[q] = XF[base + ld + q];
-                        we[q + 1] = WEf[base + q];
-                        wn[q] = WNf[base + q];
-                        ws[q] = WNf[base - ld + q];
-                    }
-                    xc[0] = c > 0 ? XF[base - 1] : z2;
-                    xc[5] = (4 * c + 4 <= n) ? XF[base + 4] : z2;
-                    we[0] = c > 0 ? WEf[base - 1] : z2;
-                    const ff2 sixth = {(float)(1.0 / 6.0), (float)(1.0 / 6.0 - (double)(float)(1.0 / 6.0))};
-#pragma unroll
-                    for (int q = 0; q < 4; ++q) {
-                        const int i = 4 * c + q;
-                        const ff2 x0 = xc[q + 1];
-                        ff2 ax = ff_mul(we[q + 1], ff_sub(x0, xc[q + 2]));
-                        ax = ff_add(ax, ff_mul(we[q], ff_sub(x0, xc[q])));
-                        ax = ff_add(ax, ff_mul(wn[q], ff_sub(x0, xn[q])));
-                        ax = ff_add(ax, ff_mul(ws[q], ff_sub(x0, xs[q])));
-                        const ff2 b = S.rhs_mode == 0 ? bff : ff_from_d(rhs_value(S, i, j));
-                        const ff2 r = ff_sub(b, ff_mul(ax, sixth));
-                        rv[q] = (i >= 1 && i <= n - 1) ? r.h : (VT)0;
-                    }
-                }
-#pragma unroll
-                for (int q = 0; q < 4; ++q) {
-                    const float rq = rv[q] * rsc;
-                    resf += rq * rq;
-                    rz0f += jac ? rq * (rq * (float)zv[q]) : rq * rq;
-                }
-            } else {
             double r4[4];
             if (o == 0) {
 #pragma unroll
@@ -1553,7 +1486,6 @@ __device__ void solve_system(const Params& P, const DevSolve& S, const Group<GT>
                 rr0 += (double)rv[q] * (double)rv[q];
                 rz0 += jac ? (double)rv[q] * (double)(rv[q] * zv[q]) : (double)rv[q] * (double)rv[q];
             }
-            }
             Vec4<VT>::store(R + base, rv);
             const VT z[4] = {(VT)0, (VT)0, (VT)0, (VT)0};
             Vec4<VT>::store(D + base, z);
@@ -1569,17 +1501,7 @@ __device__ void solve_system(const Params& P, const DevSolve& S, const Group<GT>
             }
         }
         if (pipe_on) fence_proxy_async_global();
-        if constexpr (FF) {
-            // the leading part of r is what the inner solve sees: ||r||^2 and (r, r) agree here
-            double unused;
-            G.template sum3<float>(resf, rz0f, 0.0f, res, rz0, unused);
-            const double us = 1.0 / ((double)rsc * (double)rsc);
-            res *= us;
-            rz0 *= us;
-            rr0 = res;
-        } else {
-            G.template sum3<double>(res, rr0, rz0, res, rr0, rz0);
-        }
+        G.template sum3<double>(res, rr0, rz0, res, rr0, rz0);
         rho = sqrt(res) / S.bnorm;
         if (pipe_on && pipe_aborted(*pipe)) { flag = MLMC_F_TIMEOUT; break; }
         if (!(rho == rho) || isinf(rho)) { flag = MLMC_F_NONFINITE; break; }
@@ -1775,23 +1697,17 @@ __device__ void solve_system(const Params& P, const DevSolve& S, const Group<GT>
         }
         iters += k;
 
-        // ---- U: x += d in FP64 (float-float for FP32 inner solves)
+        // ---- U: x += d in FP64
         for (int it = tr; it < items; it += GT) {
             const int j = 1 + it / cpr, c = it - (j - 1) * cpr;
             const size_t base = (size_t)j * ld + 4 * c;
+            double xv[4];
             VT dvv[4];
+            Vec4<double>::load(X + base, xv);
             Vec4<VT>::load(D + base, dvv);
-            if constexpr (FF) {
-                ff2* XF = reinterpret_cast<ff2*>(X);
 #pragma unroll
-                for (int q = 0; q < 4; ++q) XF[base + q] = ff_add_f(XF[base + q], (float)dvv[q]);
-            } else {
-                double xv[4];
-                Vec4<double>::load(X + base, xv);
-#pragma unroll
-                for (int q = 0; q < 4; ++q) xv[q] += (double)dvv[q];
-                Vec4<double>::store(X + base, xv);
-            }
+            for (int q = 0; q < 4; ++q) xv[q] += (double)dvv[q];
+            Vec4<double>::store(X + base, xv);
         }
         G.sync();
     }
@@ -1801,12 +1717,7 @@ __device__ void solve_system(const Params& P, const DevSolve& S, const Group<GT>
     for (int it = tr; it < items; it += GT) {
         const int j = 1 + it / cpr, c = it - (j - 1) * cpr;
         double xv[4];
-        if constexpr (FF) {
-#pragma unroll
-            for (int q = 0; q < 4; ++q) xv[q] = ff_to_d(reinterpret_cast<const ff2*>(X)[(size_t)j * ld + 4 * c + q]);
-        } else {
-            Vec4<double>::load(X + (size_t)j * ld + 4 * c, xv);
-        }
+        Vec4<double>::load(X + (size_t)j * ld + 4 * c, xv);
 #pragma unroll
         for (int q = 0; q < 4; ++q) {
             const int i = 4 * c + q;
@@ -1818,14 +1729,7 @@ __device__ void solve_system(const Params& P, const DevSolve& S, const Group<GT>
         for (int it = tr; it < (n + 1) * (n + 1); it += GT) {
             const int j = it / (n + 1), i = it - j * (n + 1);
             const bool inner = (i >= 1 && i <= n - 1 && j >= 1 && j <= n - 1);
-            double xv = 0.0;
-            if (inner) {
-                if constexpr (FF)
-                    xv = ff_to_d(reinterpret_cast<const ff2*>(X)[(size_t)j * ld + i]);
-                else
-                    xv = X[(size_t)j * ld + i];
-            }
-            u[it] = xv;
+            u[it] = inner ? X[(size_t)j * ld + i] : 0.0;
         }
     }
     double qs, t4, t5;
