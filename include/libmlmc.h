@@ -306,6 +306,13 @@ typedef struct {
     int mixed_field;       /* master coefficient of the mixed form: MLMC_FP64TC (default; FP64 from
                               the tensor cores, as the FP64 refinement residual of Alg. 2.1 needs) or
                               MLMC_FP32 (the FP32 tensor-core field, about 1e-6 relative)            */
+    int prec_rule;         /* inner precision of the mixed form's Krylov solves: 0 (default) the rule of
+                              mlmc_adapt_precision with `contrast`; 1 calibrated: each level's contrast
+                              is measured on its own fields (max over samples of max(a) / min(a),
+                              which bounds kappa(A) / kappa(Laplacian), Lemma 3.3), FP64 where Cor. 3.4's
+                              condition contrast h^-2 u_single <= 0.5 fails, and a 16-bit stored
+                              coefficient IEEE half where a and D^-1 fit its normal range
+                              (min a >= 6.2e-5, max a <= 4e3), else bfloat16                        */
 } mlmc_options;
 
 typedef struct {
@@ -328,6 +335,7 @@ typedef struct {
     int64_t fp64_retries[MLMC_MAX_LEVELS];  /* mixed form: solves re-run with FP64 inner arithmetic
                                                after their low-precision refinement stagnated or ran
                                                out of iterations (Cor. 3.4 conditions failed)     */
+    double contrast[MLMC_MAX_LEVELS];       /* calibrated rule: measured contrast per level (else 0) */
 } mlmc_result;
 
 /* Fill *opts with the paper's defaults: kp 0.05, (2,1,4,2), alpha 2, gamma 2,

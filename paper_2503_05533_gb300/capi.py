@@ -51,7 +51,7 @@ class mlmc_options(ctypes.Structure):
                 ("alpha", c_double), ("gamma", c_double), ("r", c_double), ("form", c_int),
                 ("fixed_delta", c_double), ("force_prec", c_int), ("solver", c_int), ("max_iters", c_int),
                 ("max_rounds", c_int), ("fixed_N", POINTER(c_int64)), ("contrast", c_double),
-                ("mixed_field", c_int)]
+                ("mixed_field", c_int), ("prec_rule", c_int)]
 
 
 class mlmc_result(ctypes.Structure):
@@ -61,7 +61,7 @@ class mlmc_result(ctypes.Structure):
                 ("s2", c_double * MLMC_MAX_LEVELS), ("delta", c_double * MLMC_MAX_LEVELS),
                 ("prec", c_int32 * MLMC_MAX_LEVELS), ("inner_iters", c_int64 * MLMC_MAX_LEVELS),
                 ("dofs", c_int64 * MLMC_MAX_LEVELS), ("acc", mlmc_acc * MLMC_MAX_LEVELS), ("seconds", c_double),
-                ("fp64_retries", c_int64 * MLMC_MAX_LEVELS)]
+                ("fp64_retries", c_int64 * MLMC_MAX_LEVELS), ("contrast", c_double * MLMC_MAX_LEVELS)]
 
 
 class mlmc_profile(ctypes.Structure):
@@ -361,5 +361,5 @@ def result_dict(res):
         "N": list(res.N[:L + 1]), "Yhat": list(res.Yhat[:L + 1]), "s2": list(res.s2[:L + 1]),
         "delta": list(res.delta[:L + 1]), "prec": list(res.prec[:L + 1]),
         "inner_iters": list(res.inner_iters[:L + 1]), "dofs": list(res.dofs[:L + 1]), "seconds": res.seconds,
-        "fp64_retries": list(res.fp64_retries[:L + 1]),
+        "fp64_retries": list(res.fp64_retries[:L + 1]), "contrast": list(res.contrast[:L + 1]),
     }

@@ -203,6 +203,16 @@ mlmc_prec pick_prec(double h, double delta, double contrast) {
     return MLMC_FP32;
 }
 
+// The calibrated rule (mlmc_options.prec_rule = 1): the level's measured contrast in Cor. 3.4's
+// condition, and IEEE half storage only where the coefficient and its inverse diagonal 1 / (4 a) stay
+// in half's normal range.
+mlmc_prec pick_prec_calibrated(double h, double delta, double contrast, double amin, double amax) {
+    const double u_single = 0x1p-24;
+    if (contrast / (h * h) * u_single > 0.5) return MLMC_FP64;
+    if (delta >= 1e-4) return (amin >= 6.2e-5 && amax <= 4.0e3) ? MLMC_FP16S : MLMC_BF16S;
+    return MLMC_FP32;
+}
+
 // ---------------------------------------------------------------------------
 // Alg. 4.1 host loop, shared by the GPU estimate and the host-sampler variant.
 struct Request {
@@ -306,6 +316,10 @@ mlmc_status check_options(const mlmc_options* o, int L_max, std::string& err) {
     if (o->form < 0 || o->form > 2 || (o->force_prec >= 0 && !is_prec(o->force_prec)) ||
         (o->solver != MLMC_CG && o->solver != MLMC_MINRES && o->solver != MLMC_CHOLESKY) || o->max_iters < 1) {
         err = "options: bad form, precision, solver or max_iters";
+        return MLMC_E_ARG;
+    }
+    if (o->prec_rule != 0 && o->prec_rule != 1) {
+        err = "options: prec_rule must be 0 or 1";
         return MLMC_E_ARG;
     }
     if (o->mixed_field != MLMC_FP64TC && o->mixed_field != MLMC_FP32) {
@@ -738,6 +752,11 @@ mlmc_status mlmc_estimate(mlmc_ctx* ctx, const mlmc_options* opts, mlmc_result* 
     std::vector<int64_t> iters_lvl(MLMC_MAX_LEVELS, 0), dofs_lvl(MLMC_MAX_LEVELS, 0);
     std::vector<int32_t> prec_lvl(MLMC_MAX_LEVELS, -1);
     std::vector<int64_t> retries_lvl(MLMC_MAX_LEVELS, 0);
+    // calibrated precision rule: per level, the largest contrast max(a) / min(a) of its samples so far
+    std::vector<double> cal_contrast(MLMC_MAX_LEVELS, 0.0), cal_amin(MLMC_MAX_LEVELS, 1e300),
+        cal_amax(MLMC_MAX_LEVELS, 0.0);
+    const bool calibrate = o.prec_rule == 1 && o.form == MLMC_FORM_MIXED && o.solver != MLMC_CHOLESKY &&
+                           o.force_prec < 0;
 
     RoundFn round = [&](const std::vector<Request>& req, const std::vector<double>& df, const std::vector<double>& dc,
                         std::vector<mlmc_acc>& out, mlmc_result*) -> mlmc_status {
@@ -749,20 +768,24 @@ mlmc_status mlmc_estimate(mlmc_ctx* ctx, const mlmc_options* opts, mlmc_result* 
         std::vector<double> dtmp(L + 1);
         mlmc_adapt_precision(L, h.data(), o.kp, o.alpha1, o.alpha2, o.beta1, o.beta2, o.contrast, dtmp.data(),
                              prec_rule.data());
-        auto prec_of = [&](int l) -> mlmc_prec {
+        // precision of a solve on the grid of level g with a field of level fl (fl = g + 1 for the coarse
+        // member of a level pair)
+        auto prec_for = [&](int g, int fl) -> mlmc_prec {
             if (o.form != MLMC_FORM_MIXED) return MLMC_FP64;
             if (o.force_prec >= 0) return (mlmc_prec)o.force_prec;
             // the Cholesky solver of Sec. 5.2 takes Table 1 (right): a half factor on level 0, single above
-            if (o.solver == MLMC_CHOLESKY) return l == 0 ? MLMC_FP16S : MLMC_FP32;
-            return prec_rule[l];
+            if (o.solver == MLMC_CHOLESKY) return g == 0 ? MLMC_FP16S : MLMC_FP32;
+            if (calibrate) return pick_prec_calibrated(h[g], df[g], cal_contrast[fl], cal_amin[fl], cal_amax[fl]);
+            return prec_rule[g];
         };
+        auto prec_of = [&](int l) -> mlmc_prec { return prec_for(l, l); };
         // launch class of a solve: the factor / inner precision, plus for the Cholesky solver the working
         // and residual precisions of Table 1 (right): single on levels 0 and 1 (hhss, ssss), double above
         // (ssdd); double throughout for the FP64 forms (dddd)
-        auto class_of = [&](int l) -> int {
-            const int p = prec_of(l);
+        auto class_of = [&](int g, int fl) -> int {
+            const int p = prec_for(g, fl);
             if (o.solver != MLMC_CHOLESKY) return p;
-            const bool dbl = o.form != MLMC_FORM_MIXED || l >= 2;
+            const bool dbl = o.form != MLMC_FORM_MIXED || g >= 2;
             return p | (dbl ? 0 : 16);
         };
         size_t fbytes = 0, xbytes = 0, qn = 0;
@@ -782,7 +805,8 @@ mlmc_status mlmc_estimate(mlmc_ctx* ctx, const mlmc_options* opts, mlmc_result* 
         // Qf, Qc (doubles), iters and flags for fine and coarse (int32)
         const size_t qbytes = qn * (2 * sizeof(double) + 4 * sizeof(int32_t));
         MLMC_CUDA_RET(ctx->err, ctx->ws.q.reserve(qbytes));
-        MLMC_CUDA_RET(ctx->err, ctx->ws.misc.reserve(sizeof(mlmc_acc) * req.size()));
+        MLMC_CUDA_RET(ctx->err, ctx->ws.misc.reserve(std::max(sizeof(mlmc_acc) * req.size(),
+                                                               calibrate ? 2 * qn * sizeof(double) : 0)));
         char* fb = ctx->ws.fields.as<char>();
         double* xb = ctx->ws.xi.as<double>();
         double* Qf = ctx->ws.q.as<double>();
@@ -801,6 +825,28 @@ mlmc_status mlmc_estimate(mlmc_ctx* ctx, const mlmc_options* opts, mlmc_result* 
                                                      (void*)st);
             if (s != MLMC_OK) return s;
         }
+        // ---- calibrated rule: the contrast of every new field, per level
+        if (calibrate) {
+            double* rng = ctx->ws.misc.as<double>();
+            for (size_t i = 0; i < req.size(); ++i) {
+                const int n = level_n(p, req[i].level);
+                MLMC_CUDA_RET(ctx->err, launch_field_range(req[i].count, (n + 1) * (n + 1), fb + foff[i],
+                                                           field_prec != MLMC_FP32, rng + 2 * qoff[i], st));
+            }
+            std::vector<double> hr(2 * qn);
+            MLMC_CUDA_RET(ctx->err, cudaMemcpyAsync(hr.data(), rng, 2 * qn * sizeof(double), cudaMemcpyDeviceToHost, st));
+            MLMC_CUDA_RET(ctx->err, cudaStreamSynchronize(st));
+            ctx->prof.acc.d2h_bytes += (int64_t)(2 * qn * sizeof(double));
+            for (size_t i = 0; i < req.size(); ++i) {
+                const int l = req[i].level;
+                for (int k = 0; k < req[i].count; ++k) {
+                    const double lo = hr[2 * (qoff[i] + k)], hi = hr[2 * (qoff[i] + k) + 1];
+                    cal_amin[l] = std::min(cal_amin[l], lo);
+                    cal_amax[l] = std::max(cal_amax[l], hi);
+                    if (lo > 0) cal_contrast[l] = std::max(cal_contrast[l], hi / lo);
+                }
+            }
+        }
         // ---- one resident-solve launch per inner-precision class: every fine and coarse member
         std::map<int, std::vector<SolveGroup>> classes;
         std::map<int, std::vector<int>> class_level;   // level of each group, for the counters
@@ -817,8 +863,8 @@ mlmc_status mlmc_estimate(mlmc_ctx* ctx, const mlmc_options* opts, mlmc_result* 
             gf.Q = Qf + qoff[i];
             gf.iters = itf + qoff[i];
             gf.flags = flf + qoff[i];
-            classes[class_of(l)].push_back(gf);
-            class_level[class_of(l)].push_back(l);
+            classes[class_of(l, l)].push_back(gf);
+            class_level[class_of(l, l)].push_back(l);
             prec_lvl[l] = prec_of(l);
             dofs_lvl[l] += (int64_t)req[i].count * (n - 1) * (n - 1);
             if (l > 0) {
@@ -828,8 +874,8 @@ mlmc_status mlmc_estimate(mlmc_ctx* ctx, const mlmc_options* opts, mlmc_result* 
                 gc.Q = Qc + qoff[i];
                 gc.iters = itc + qoff[i];
                 gc.flags = flc + qoff[i];
-                classes[class_of(l - 1)].push_back(gc);
-                class_level[class_of(l - 1)].push_back(l);
+                classes[class_of(l - 1, l)].push_back(gc);
+                class_level[class_of(l - 1, l)].push_back(l);
                 dofs_lvl[l] += (int64_t)req[i].count * (gc.n - 1) * (gc.n - 1);
             }
         }
@@ -926,6 +972,7 @@ mlmc_status mlmc_estimate(mlmc_ctx* ctx, const mlmc_options* opts, mlmc_result* 
         res->inner_iters[l] = iters_lvl[l];
         res->dofs[l] = dofs_lvl[l];
         res->fp64_retries[l] = retries_lvl[l];
+        res->contrast[l] = calibrate ? cal_contrast[l] : 0.0;
     }
     res->flags_or = flags_or;
     const int32_t bad = MLMC_F_MAXIT | MLMC_F_STAGNATED | MLMC_F_NONFINITE;

@@ -154,7 +154,9 @@ __global__ void __launch_bounds__(kCholThreads) chol_ir_kernel(CholParams P) {
             // rooted) and give the slot column k - 1 + R of A; every thread reads the pivot of column k
             if (k > 0 && t <= bw) {
                 CT* prev = ring + ((k - 1) % R) * R;
-                band[(long long)(k - 1) * R + t] = round_to<FT>(prev[t]);
+                const FT v = round_to<FT>(prev[t]);
+                if (!isfinite((double)from_t<CT>(v))) breakdown = true;   // beyond the storage format's range
+                band[(long long)(k - 1) * R + t] = v;
                 const int nk = k - 1 + R;
                 prev[t] = nk < N ? a_band<CT>(S, nk, t) : (CT)0;
             }
@@ -181,9 +183,11 @@ __global__ void __launch_bounds__(kCholThreads) chol_ir_kernel(CholParams P) {
         }
         if (t <= bw) {
             CT* last = ring + ((N - 1) % R) * R;
-            band[(long long)(N - 1) * R + t] = round_to<FT>(last[t]);
+            const FT v = round_to<FT>(last[t]);
+            if (!isfinite((double)from_t<CT>(v))) breakdown = true;
+            band[(long long)(N - 1) * R + t] = v;
         }
-        __syncthreads();
+        breakdown = __syncthreads_or(breakdown ? 1 : 0) != 0;
     }
 
     // ---- refinement (Alg. 2.1)

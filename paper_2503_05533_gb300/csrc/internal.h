@@ -254,6 +254,8 @@ cudaError_t launch_apply_operator(int n, int S, const void* a, int a_fp64, int a
 // stats.cu
 cudaError_t launch_level_stats(int S, const double* Qf, const double* Qc, mlmc_acc* out_dev,
                                cudaStream_t st);
+// min and max nodal coefficient of each of S fields of V nodes: out_dev [S][2]
+cudaError_t launch_field_range(int S, int V, const void* a, int a_fp64, double* out_dev, cudaStream_t st);
 // adjoint.cu
 cudaError_t launch_adjoint_elements(int n, int S, const void* a, int a_fp64, const double* u,
                                     const double* lam, double* G, cudaStream_t st);

@@ -16,7 +16,7 @@ namespace mlmc {
 namespace {
 
 // Phi64[k][v] (row stride ld64) and the split FP16 operand phi16 = [hi; lo],
-// each [Vpad][Kpad] (K contiguous): Phi = hi + lo 2^-11.
+// each [Vpad][Kpad] (K contiguous): log2(e) Phi = hi + lo 2^-11.
 __global__ void expand_basis_kernel(int n, int K, int Kpad, int V, int Vpad, int ld64,
                                     const double* __restrict__ coef, const double* __restrict__ bx,
                                     const double* __restrict__ by, double* __restrict__ phi64,
@@ -31,8 +31,10 @@ __global__ void expand_basis_kernel(int n, int K, int Kpad, int V, int Vpad, int
         phi = coef[k] * bx[(size_t)k * (n + 1) + i] * by[(size_t)k * (n + 1) + j];
         phi64[(size_t)k * ld64 + v] = phi;
     }
-    const __half hi = __double2half(phi);
-    const double rem = (phi - (double)__half2float(hi)) * 2048.0;
+    // the tensor-core FP32 synthesis contracts log2(e) Phi, so that its accumulators hold log2 a
+    const double phi2 = phi * 1.4426950408889634;
+    const __half hi = __double2half(phi2);
+    const double rem = (phi2 - (double)__half2float(hi)) * 2048.0;
     phi16[tid] = hi;
     phi16[(size_t)Vpad * Kpad + tid] = __double2half(rem);
 }

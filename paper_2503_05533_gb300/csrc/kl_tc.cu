@@ -4,10 +4,11 @@
 // accumulation in tensor memory, in two forms:
 //
 // FP32 output.  Both operands are split x = hi + lo 2^-11 (hi = fp16(x),
-// lo = fp16((x - hi) 2^11), which keeps lo in FP16's normal range) and two
-// accumulators hold D0 = xi_hi Phi_hi^T and D1 = xi_hi Phi_lo^T + xi_lo Phi_hi^T
-// over all K; log a = D0 + 2^-11 D1 (the lo*lo term, 2^-22 relative, dropped)
-// and a = expf(log a).  About 1e-6 relative error in a.
+// lo = fp16((x - hi) 2^11), which keeps lo in FP16's normal range); the basis
+// is scaled by log2(e) before the split, and two accumulators hold
+// D0 = Phi_hi xi_hi^T and D1 = Phi_hi xi_lo^T + Phi_lo xi_hi^T over all K, so
+// log2 a = D0 + 2^-11 D1 (the lo*lo term, 2^-22 relative, dropped) and
+// a = 2^(log2 a) by the SFU's exp2.  About 1e-6 relative error in a.
 //
 // FP64 output (the master coefficient of the mixed-precision solves, where the
 // refinement residual of Alg. 2.1 is FP64).  Each sample row of xi is scaled by
@@ -37,13 +38,15 @@
 // value.  The FP32 pipe does all of this work: GB300's FP64 pipe is narrow.
 //
 // Execution: a persistent kernel, one CTA per SM walking output tiles of 128
-// samples x TN nodes.  Warp 0 streams the operand slices of every 64-term K
-// block by TMA (128-byte swizzle) through a ring of shared-memory stages;
+// nodes x TN samples.  The MMA's A operand is the basis (M = 128 node rows),
+// its B operand xi (N = TN sample rows), so a tensor-memory lane holds one node
+// and a column one sample.  Warp 0 streams the operand slices of every 64-term
+// K block by TMA (128-byte swizzle) through a ring of shared-memory stages;
 // warp 1 issues the MMAs (M = 128, N = TN, K = 16) into one of two tensor-
 // memory buffers and signals through mbarriers; TN / 8 epilogue warps drain
-// the other buffer (each warp 32 columns of one TMEM lane quarter, one sample
-// per lane), form the output and write it through a shared-memory transpose so
-// that stores are row-contiguous.  Loads of tile t+1 and the epilogue of tile t overlap its
+// the other buffer (each warp 32 sample columns of one TMEM lane quarter) and
+// write, sample by sample, the 32 consecutive nodes of their lanes with one
+// coalesced store.  Loads of tile t+1 and the epilogue of tile t overlap its
 // MMAs.  Every mbarrier wait is bounded in wall time; on expiry the CTA records
 // the context's error word, every role leaves its loop, the producer waits
 // (bounded) for its copies in flight, and the TMEM is freed.
@@ -61,21 +64,21 @@
 namespace mlmc {
 namespace {
 
-constexpr int TM = 128;              // samples per tile (MMA M, TMEM lanes)
+constexpr int TM = 128;              // nodes per tile (MMA M, TMEM lanes)
 constexpr int TKB = 64;              // terms per K block: 64 FP16 = one 128-byte swizzle row
-constexpr uint32_t kATile = TM * TKB * 2;   // 16 KiB: one slice of 128 sample rows
+constexpr uint32_t kATile = TM * TKB * 2;   // 16 KiB: one slice of 128 node rows
 
 // MODE 0: FP32 output (2 slices per operand); MODE 1: FP64 output (3 slices, exact lead).
 template <int MODE> struct KLCfg;
 // Warp 0 issues the TMA copies, warp 1 the MMAs; EW = TN / 8 epilogue warps follow, each draining one
 // 32-column chunk of one TMEM lane quarter (its warp index mod 4).
 template <> struct KLCfg<0> {
-    static constexpr int NA = 2, NB = 2, TN = 128, NACC = 2, NSTAGE = 2, EW = TN / 8;
+    static constexpr int NA = 2, NB = 2, TN = 128, NACC = 2, NSTAGE = 3, EW = TN / 8;
     static constexpr bool DRAIN = false;   // accumulate the whole K range in TMEM
     using Out = float;
 };
 template <> struct KLCfg<1> {
-    static constexpr int NA = 3, NB = 3, TN = 64, NACC = 3, NSTAGE = 2, EW = TN / 8;
+    static constexpr int NA = 3, NB = 3, TN = 64, NACC = 3, NSTAGE = 3, EW = TN / 8;
     static constexpr bool DRAIN = true;    // the epilogue drains every K block
     using Out = double;
 };
@@ -84,8 +87,8 @@ template <int MODE> struct KLLayout {
     using C = KLCfg<MODE>;
     static constexpr uint32_t kBTile = C::TN * TKB * 2;
     static constexpr uint32_t kStage = C::NA * kATile + C::NB * kBTile;   // multiple of 1024
-    static constexpr uint32_t kOffStg = C::NSTAGE * kStage;               // epilogue transpose staging
-    static constexpr uint32_t kStgBytes = C::EW * 32 * 33 * sizeof(typename C::Out);
+    static constexpr uint32_t kOffStg = C::NSTAGE * kStage;
+    static constexpr uint32_t kStgBytes = 0;
     static constexpr int kThreads = 64 + 32 * C::EW;
     static constexpr uint32_t kOffBar = (kOffStg + kStgBytes + 15) / 16 * 16;
     // full[NSTAGE], empty[NSTAGE], tfull[2], tempty[2], then the TMEM address and the abort flag
@@ -149,6 +152,12 @@ __device__ __forceinline__ void tmem_ld_x32(uint32_t taddr, uint32_t (&r)[32]) {
           "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]),
           "=r"(r[24]), "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
         : "r"(taddr));
+}
+// 2^x by the SFU's approximation (maximum relative error about 2^-22).
+__device__ __forceinline__ float ex2_approx(float x) {
+    float y;
+    asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+    return y;
 }
 __device__ __forceinline__ void tmem_wait_ld() { asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory"); }
 __device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
@@ -221,7 +230,7 @@ __device__ __forceinline__ void ff_exp(float xh, float xl, const FFExp& T, float
 template <int MODE>
 __global__ void __launch_bounds__(KLLayout<MODE>::kThreads, 1)
     kl_tc_kernel(const __grid_constant__ CUtensorMap mapA, const __grid_constant__ CUtensorMap mapB, int S, int Spad,
-                 int V, int Vpad, int Kpad, int num_m, int num_tiles, const int* __restrict__ es,
+                 int V, int Vpad, int Kpad, int num_st, int num_tiles, const int* __restrict__ es,
                  const int* __restrict__ ev, const __grid_constant__ FFExp ffx, typename KLCfg<MODE>::Out* __restrict__ out,
                  unsigned* err, unsigned long long timeout_ns, unsigned extra_tx) {
     using C = KLCfg<MODE>;
@@ -270,7 +279,7 @@ __global__ void __launch_bounds__(KLLayout<MODE>::kThreads, 1)
             unsigned issued = 0;
             bool ok = true;
             for (int t = blockIdx.x; t < num_tiles && ok; t += gridDim.x) {
-                const int s0 = (t % num_m) * TM, v0 = (t / num_m) * TN;
+                const int s0 = (t % num_st) * TN, v0 = (t / num_st) * TM;
                 for (int kb = 0; kb < nkb; ++kb) {
                     if (!kl_wait(empty + stage, phase ^ 1u, abort, err, timeout_ns)) {
                         ok = false;
@@ -280,10 +289,10 @@ __global__ void __launch_bounds__(KLLayout<MODE>::kThreads, 1)
                     mbar_expect_tx(full + stage, Lay::kStage + (issued == 0 ? extra_tx : 0u));
                     ++issued;
 #pragma unroll
-                    for (int q = 0; q < C::NA; ++q) tma_load_2d(st + q * kATile, &mapA, kb * TKB, q * Spad + s0, full + stage);
+                    for (int q = 0; q < C::NA; ++q) tma_load_2d(st + q * kATile, &mapA, kb * TKB, q * Vpad + v0, full + stage);
 #pragma unroll
                     for (int q = 0; q < C::NB; ++q)
-                        tma_load_2d(st + C::NA * kATile + q * Lay::kBTile, &mapB, kb * TKB, q * Vpad + v0, full + stage);
+                        tma_load_2d(st + C::NA * kATile + q * Lay::kBTile, &mapB, kb * TKB, q * Spad + s0, full + stage);
                     if (++stage == C::NSTAGE) {
                         stage = 0;
                         phase ^= 1u;
@@ -371,18 +380,19 @@ __global__ void __launch_bounds__(KLLayout<MODE>::kThreads, 1)
             if (*abort && last_bar) mbar_wait(last_bar, last_par, timeout_ns);
         }
     } else {
-        // ---- epilogue: warp 2 + e drains TMEM lanes 32 (warp % 4) .. + 31 (one sample per lane) of the
-        // tile's column chunk e / 4 (32 columns) and writes them
+        // ---- epilogue: warp 2 + e drains TMEM lanes 32 (warp % 4) .. + 31 -- one node per lane -- of the
+        // tile's sample chunk e / 4 (32 columns, one sample each) and writes, for every sample, the 32
+        // consecutive nodes of its lanes with one coalesced store
         const int e = warp - 2;
         const int q4 = warp & 3;
         const int c = e >> 2;
         const uint32_t lane_base = (uint32_t)(q4 * 32) << 16;
-        Out* stg = reinterpret_cast<Out*>(smem + Lay::kOffStg) + e * 32 * 33;
         int tb = 0;
         uint32_t tphase = 0;
         for (int t = blockIdx.x; t < num_tiles; t += gridDim.x) {
-            const int s0 = (t % num_m) * TM, v0 = (t / num_m) * TN;
-            const int srow = s0 + q4 * 32 + lane;   // this lane's sample
+            const int s0 = (t % num_st) * TN, v0 = (t / num_st) * TM;
+            const int v = v0 + q4 * 32 + lane;       // this lane's node
+            const int sc0 = s0 + c * 32;             // the chunk's first sample
             if (MODE == 0) {
                 if (!kl_warp_wait(tfull + tb, tphase, abort, err, timeout_ns)) break;
                 tc_fence_after();
@@ -399,10 +409,14 @@ __global__ void __launch_bounds__(KLLayout<MODE>::kThreads, 1)
                     tb = 0;
                     tphase ^= 1u;
                 }
+                // the basis tables carry log2(e): the accumulators hold log2 a
+                if (v < V) {
 #pragma unroll
-                for (int j = 0; j < 32; ++j) {
-                    const float lg = __uint_as_float(r0[j]) + __uint_as_float(r1[j]) * (1.0f / 2048.0f);
-                    stg[lane * 33 + j] = (Out)expf(lg);
+                    for (int j = 0; j < 32; ++j) {
+                        const int sj = sc0 + j;
+                        const float l2 = __fmaf_rn(__uint_as_float(r1[j]), 1.0f / 2048.0f, __uint_as_float(r0[j]));
+                        if (sj < S) out[(size_t)sj * V + v] = (Out)ex2_approx(l2);
+                    }
                 }
             } else {
                 int s0i[32];        // sum over K blocks of E0 (exact integers)
@@ -440,11 +454,11 @@ __global__ void __launch_bounds__(KLLayout<MODE>::kThreads, 1)
                     }
                 }
                 if (!ok) break;
-                const int esv = srow < Spad ? es[srow] : 0;
+                const int evv = ev[v < Vpad ? v : Vpad - 1];
 #pragma unroll
                 for (int j = 0; j < 32; ++j) {
-                    const int v = v0 + c * 32 + j;
-                    const int sc = esv + ev[v < Vpad ? v : Vpad - 1] - 18;
+                    const int sj = sc0 + j;
+                    const int sc = es[sj < Spad ? sj : Spad - 1] + evv - 18;
                     // float-float of the integer sum (up to 2^26) plus the FP32 correction sum
                     const int ii = s0i[j];
                     const float ih = (float)ii;
@@ -457,17 +471,9 @@ __global__ void __launch_bounds__(KLLayout<MODE>::kThreads, 1)
                     ll = ldexpf(ll, sc);
                     float ah, al;
                     ff_exp(lh, ll, ffx, ah, al);
-                    stg[lane * 33 + j] = (double)ah + (double)al;
+                    if (sj < S && v < V) out[(size_t)sj * V + v] = (double)ah + (double)al;
                 }
             }
-            __syncwarp();
-            const int v = v0 + c * 32 + lane;
-#pragma unroll 4
-            for (int rr = 0; rr < 32; ++rr) {
-                const int s = s0 + q4 * 32 + rr;
-                if (s < S && v < V) out[(size_t)s * V + v] = stg[rr * 33 + lane];
-            }
-            __syncwarp();
         }
     }
     tc_fence_before();
@@ -601,9 +607,10 @@ cudaError_t kl_launch(mlmc_ctx* ctx, int S, int Spad, int Kpad, int nodes, int n
                       const void* bops, const int* es, const int* ev, void* out, cudaStream_t st) {
     using C = KLCfg<MODE>;
     using Lay = KLLayout<MODE>;
+    // MMA operand A: the basis slices (128 node rows), B: the xi slices (TN sample rows)
     CUtensorMap mapA, mapB;
-    if (!make_map(&mapA, aops, (uint64_t)C::NA * Spad, (uint64_t)Kpad, TM) ||
-        !make_map(&mapB, bops, (uint64_t)C::NB * nodes_pad, (uint64_t)Kpad, C::TN))
+    if (!make_map(&mapA, bops, (uint64_t)C::NA * nodes_pad, (uint64_t)Kpad, TM) ||
+        !make_map(&mapB, aops, (uint64_t)C::NB * Spad, (uint64_t)Kpad, C::TN))
         return cudaErrorInvalidValue;
     static bool attr = false;
     cudaError_t e;
@@ -614,8 +621,8 @@ cudaError_t kl_launch(mlmc_ctx* ctx, int S, int Spad, int Kpad, int nodes, int n
         attr = true;
     }
     static const FFExp ffx = make_ffexp();
-    const int num_m = Spad / TM;
-    const int num_tiles = num_m * (nodes_pad / C::TN);
+    const int num_st = Spad / C::TN;
+    const int num_tiles = num_st * (nodes_pad / TM);
     const int grid = num_tiles < ctx->num_sms ? num_tiles : ctx->num_sms;
     Profile::Pending pend;
     if (ctx->prof.on) {
@@ -624,7 +631,7 @@ cudaError_t kl_launch(mlmc_ctx* ctx, int S, int Spad, int Kpad, int nodes, int n
         if ((e = cudaEventRecord(pend.a, st)) != cudaSuccess) return e;
     }
     kl_tc_kernel<MODE><<<(unsigned)grid, Lay::kThreads, Lay::kSmem, st>>>(
-        mapA, mapB, S, Spad, nodes, nodes_pad, Kpad, num_m, num_tiles, es, ev, ffx,
+        mapA, mapB, S, Spad, nodes, nodes_pad, Kpad, num_st, num_tiles, es, ev, ffx,
         static_cast<typename C::Out*>(out), ctx->kl_err, (unsigned long long)(ctx->wait_timeout_s * 1e9),
         16u * (unsigned)ctx->wait_extra);
     g_launches.fetch_add(1, std::memory_order_relaxed);

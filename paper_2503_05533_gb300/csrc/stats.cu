@@ -78,7 +78,44 @@ __global__ void __launch_bounds__(kThreads) level_stats_kernel(int S, const doub
     }
 }
 
+// Smallest and largest nodal coefficient of every sample (the contrast that bounds kappa(A): A is
+// the P1 operator with element means of a, so min(a) L <= A <= max(a) L for the Laplacian L).
+// One CTA per sample.
+__global__ void __launch_bounds__(kThreads) field_range_kernel(int V, const void* __restrict__ a, int a_fp64,
+                                                               double* __restrict__ out) {
+    __shared__ double smin[kThreads], smax[kThreads];
+    const int s = blockIdx.x, t = threadIdx.x;
+    double lo = INFINITY, hi = -INFINITY;
+    for (int v = t; v < V; v += kThreads) {
+        const size_t idx = (size_t)s * V + v;
+        const double x = a_fp64 ? static_cast<const double*>(a)[idx] : (double)static_cast<const float*>(a)[idx];
+        lo = fmin(lo, x);
+        hi = fmax(hi, x);
+    }
+    smin[t] = lo;
+    smax[t] = hi;
+    __syncthreads();
+    for (int w = kThreads / 2; w > 0; w >>= 1) {
+        if (t < w) {
+            smin[t] = fmin(smin[t], smin[t + w]);
+            smax[t] = fmax(smax[t], smax[t + w]);
+        }
+        __syncthreads();
+    }
+    if (t == 0) {
+        out[2 * s] = smin[0];
+        out[2 * s + 1] = smax[0];
+    }
+}
+
 }  // namespace
+
+cudaError_t launch_field_range(int S, int V, const void* a, int a_fp64, double* out_dev, cudaStream_t st) {
+    if (S <= 0) return cudaSuccess;
+    field_range_kernel<<<S, kThreads, 0, st>>>(V, a, a_fp64, out_dev);
+    g_launches.fetch_add(1, std::memory_order_relaxed);
+    return cudaGetLastError();
+}
 
 cudaError_t launch_level_stats(int S, const double* Qf, const double* Qc, mlmc_acc* out_dev, cudaStream_t st) {
     level_stats_kernel<<<1, kThreads, 0, st>>>(S, Qf, Qc, out_dev);

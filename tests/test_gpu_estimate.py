@@ -298,3 +298,37 @@ def test_seven_level_estimate_configuration(M):
             assert fl0 == M.MLMC_F_STAGNATED and rr.cpu().numpy()[0] >= d7[6]
     finally:
         M.mlmc_destroy(h)
+
+
+def test_calibrated_precision_rule_high_contrast(M):
+    # sigma^2 = 1.5, corr 0.1: pointwise contrasts of about e^7.  The calibrated rule measures each level's
+    # contrast on its own fields and takes FP64 inner arithmetic where Cor. 3.4's condition
+    # contrast h^-2 u_single <= 0.5 fails; no solve then needs the FP64 re-run
+    wl = dict(n0=16, m=2, L_max=4, kind=0, K=64, sigma2=1.5, corr_len=0.1, seed=9)
+    N = [16, 8, 8, 8, 8]
+    h = M.mlmc_create(M.make_problem(**wl), 0)
+    try:
+        o = M.mlmc_default_options()
+        o.L_start, o.prec_rule = 4, 1
+        keep, o.fixed_N = _fixed(M, N)
+        r = M.result_dict(M.mlmc_estimate(h, o))
+    finally:
+        M.mlmc_destroy(h)
+    assert r["flags_or"] & ~M.MLMC_F_CONVERGED == 0
+    assert all(x == 0 for x in r["fp64_retries"])
+    P = o_mlmc.Problem(n0=16, m=2, L_max=4, field_kind=0, K=64, sigma2=1.5, corr_len=0.1, seed=9)
+    picked64 = False
+    for l in range(5):
+        a = P.fields(l, 0, N[l])
+        contrast = float(np.max(a.max(axis=1) / a.min(axis=1)))
+        assert r["contrast"][l] == pytest.approx(contrast, rel=1e-6)
+        hl = 1.0 / (16 * 2 ** l)
+        if contrast / hl ** 2 * 2.0 ** -24 > 0.5:
+            assert r["prec"][l] == M.MLMC_FP64, l
+            picked64 = True
+        elif r["delta"][l] >= 1e-4:
+            ok16 = a.min() >= 6.2e-5 and a.max() <= 4e3
+            assert r["prec"][l] == (M.MLMC_FP16S if ok16 else M.MLMC_BF16S), l
+        else:
+            assert r["prec"][l] == M.MLMC_FP32, l
+    assert picked64 and r["prec"][4] == M.MLMC_FP64
