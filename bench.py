@@ -339,7 +339,7 @@ def main():
             launches = M.mlmc_launch_count() - l0
             prof = M.mlmc_profile_get(h) if profile else None
             if prof is not None:
-                prof["autotune"] = [{k: e[k] for k in ("shape", "med_items", "ring", "nu", "theta", "best_ms",
+                prof["autotune"] = [{k: e[k] for k in ("shape", "med_items", "ring", "nu", "theta", "tau_min", "best_ms",
                                                         "default_ms", "trials")} for e in tune]
         finally:
             M.mlmc_destroy(h)

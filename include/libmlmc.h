@@ -414,8 +414,9 @@ mlmc_status mlmc_set_inner_tolerance(mlmc_ctx* ctx, double theta, double tau_min
  * setting, changing one setting at a time from the library's own rules: the
  * group size of n = 91..128 systems (mlmc_debug_set_medium_items), the row-
  * pipeline depth of Jacobi-preconditioned CG (0, 2, 4 slots), the V-cycle's
- * smoothing sweeps (1, 2) and the inner tolerance factor theta (0.1, 0.3, 0.6;
- * mlmc_set_inner_tolerance).  Each candidate is timed twice with CUDA events;
+ * smoothing sweeps (1, 2), the inner tolerance factor theta (0.1, 0.3, 0.6)
+ * and its floor tau_min (0.3, 1 or 3 times the precision's default, unless the
+ * context sets one; mlmc_set_inner_tolerance).  Each candidate is timed twice with CUDA events;
  * a change is kept when at least 1% faster, and the fastest setting is cached
  * in the context for the shape.  Every candidate solves the same systems to
  * the same delta, so results agree to the solve tolerance whatever is chosen.
@@ -426,6 +427,7 @@ typedef struct {
     int prec, solver, precond;
     int med_items, ring, nu;   /* chosen settings; -3 (and nu 0) means the context's own rule    */
     double theta;          /* chosen inner tolerance factor; 0 means the context's (0.3)       */
+    double tau_min;        /* chosen floor of the inner tolerance; < 0 means the precision's    */
     double best_ms, default_ms;   /* launch time with the chosen and with the default settings */
     int trials;            /* timed trial launches                                              */
 } mlmc_tune_entry;

@@ -545,6 +545,7 @@ mlmc_status mlmc_autotune_entry(const mlmc_ctx* ctx, int i, mlmc_tune_entry* out
     out->ring = t.ring;
     out->nu = t.nu;
     out->theta = t.theta;
+    out->tau_min = t.tau_min;
     out->best_ms = t.best_ms;
     out->default_ms = t.default_ms;
     out->trials = t.trials;

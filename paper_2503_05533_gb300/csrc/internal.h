@@ -67,6 +67,7 @@ struct TuneChoice {
     int prec = 0, solver = 0, precond = 0;
     int med_items = kTuneUnset, ring = kTuneUnset, nu = 0;
     double theta = 0.0;
+    double tau_min = -1.0;      // floor of the inner tolerance (< 0: the precision's default)
     float best_ms = 0.f, default_ms = 0.f;
     int trials = 0;
 };

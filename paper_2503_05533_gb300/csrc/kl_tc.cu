@@ -55,6 +55,7 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <algorithm>
 #include <cmath>
 #include <cstring>
 
@@ -163,6 +164,18 @@ __device__ __forceinline__ void tmem_wait_ld() { asm volatile("tcgen05.wait::ld.
 __device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
 __device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
 
+// Tile t -> (sample tile st, node tile nt).  Node tiles go in groups of G; a group's tiles are
+// taken node tile fastest, so the tiles in flight at any time cover about G consecutive node tiles
+// of every sample row they touch (long contiguous runs of output per row), while the group's basis
+// rows stay in L2 for all its sample tiles.
+__device__ __forceinline__ void tile_coords(int t, int num_st, int num_nt, int G, int& st, int& nt) {
+    const int g = t / (G * num_st);
+    const int Gg = min(G, num_nt - g * G);
+    const int r = t - g * G * num_st;
+    nt = g * G + r % Gg;
+    st = r / Gg;
+}
+
 // Bounded wait that also gives up once another role has aborted the CTA.
 __device__ __forceinline__ bool kl_wait(uint64_t* bar, uint32_t parity, volatile int* abort, unsigned* err,
                                         uint64_t timeout_ns) {
@@ -230,7 +243,7 @@ __device__ __forceinline__ void ff_exp(float xh, float xl, const FFExp& T, float
 template <int MODE>
 __global__ void __launch_bounds__(KLLayout<MODE>::kThreads, 1)
     kl_tc_kernel(const __grid_constant__ CUtensorMap mapA, const __grid_constant__ CUtensorMap mapB, int S, int Spad,
-                 int V, int Vpad, int Kpad, int num_st, int num_tiles, const int* __restrict__ es,
+                 int V, int Vpad, int Kpad, int num_st, int num_tiles, int tile_group, const int* __restrict__ es,
                  const int* __restrict__ ev, const __grid_constant__ FFExp ffx, typename KLCfg<MODE>::Out* __restrict__ out,
                  unsigned* err, unsigned long long timeout_ns, unsigned extra_tx) {
     using C = KLCfg<MODE>;
@@ -279,7 +292,9 @@ __global__ void __launch_bounds__(KLLayout<MODE>::kThreads, 1)
             unsigned issued = 0;
             bool ok = true;
             for (int t = blockIdx.x; t < num_tiles && ok; t += gridDim.x) {
-                const int s0 = (t % num_st) * TN, v0 = (t / num_st) * TM;
+                int st_, nt_;
+                tile_coords(t, num_st, num_tiles / num_st, tile_group, st_, nt_);
+                const int s0 = st_ * TN, v0 = nt_ * TM;
                 for (int kb = 0; kb < nkb; ++kb) {
                     if (!kl_wait(empty + stage, phase ^ 1u, abort, err, timeout_ns)) {
                         ok = false;
@@ -390,7 +405,9 @@ __global__ void __launch_bounds__(KLLayout<MODE>::kThreads, 1)
         int tb = 0;
         uint32_t tphase = 0;
         for (int t = blockIdx.x; t < num_tiles; t += gridDim.x) {
-            const int s0 = (t % num_st) * TN, v0 = (t / num_st) * TM;
+            int st_, nt_;
+            tile_coords(t, num_st, num_tiles / num_st, tile_group, st_, nt_);
+            const int s0 = st_ * TN, v0 = nt_ * TM;
             const int v = v0 + q4 * 32 + lane;       // this lane's node
             const int sc0 = s0 + c * 32;             // the chunk's first sample
             if (MODE == 0) {
@@ -631,7 +648,7 @@ cudaError_t kl_launch(mlmc_ctx* ctx, int S, int Spad, int Kpad, int nodes, int n
         if ((e = cudaEventRecord(pend.a, st)) != cudaSuccess) return e;
     }
     kl_tc_kernel<MODE><<<(unsigned)grid, Lay::kThreads, Lay::kSmem, st>>>(
-        mapA, mapB, S, Spad, nodes, nodes_pad, Kpad, num_st, num_tiles, es, ev, ffx,
+        mapA, mapB, S, Spad, nodes, nodes_pad, Kpad, num_st, num_tiles, std::max(1, grid / 8), es, ev, ffx,
         static_cast<typename C::Out*>(out), ctx->kl_err, (unsigned long long)(ctx->wait_timeout_s * 1e9),
         16u * (unsigned)ctx->wait_extra);
     g_launches.fetch_add(1, std::memory_order_relaxed);

@@ -81,7 +81,8 @@ mlmc_status launch_batch(mlmc_ctx* ctx, const std::vector<SolveGroup>& groups, c
 // solved once per candidate setting, starting from the library's own rules and changing one setting
 // at a time (coordinate descent): the group size of n = 91..128 systems (2048 or 4096 chunks per
 // 128-thread group), the row-pipeline depth of Jacobi-preconditioned CG (0, 2, 4 slots), the
-// V-cycle's smoothing sweeps (1, 2) and the inner tolerance factor theta (0.1, 0.3, 0.6).  Each
+// V-cycle's smoothing sweeps (1, 2), the inner tolerance factor theta (0.1, 0.3, 0.6) and the inner
+// tolerance's floor (0.3, 1 or 3 times the precision's default).  Each
 // candidate is timed twice with CUDA events on the stream (the minimum counts); a change is kept if
 // it is at least 1% faster.  Every trial solves the same systems to the same accuracy, so the
 // outputs of the last trial are valid results.
@@ -104,6 +105,18 @@ void tune_apply(const TuneChoice& t, SolveConfig& cfg) {
     cfg.ring = t.ring;
     cfg.nu = t.nu;
     cfg.theta = t.theta;
+    cfg.tau_min = t.tau_min;
+}
+
+// The inner tolerance's default floor of an inner precision (the accuracy an inner solve in it can be
+// relied on to reach; make_params).
+double tau_floor(int prec) {
+    switch (prec) {
+        case MLMC_FP64: return 1e-14;
+        case MLMC_FP16S: return 1e-4;
+        case MLMC_BF16S: return 1e-3;
+        default: return 1e-6;
+    }
 }
 
 // One timed solve of the batch (minimum of `reps` runs) with the settings of t.
@@ -195,6 +208,12 @@ mlmc_status autotune_batch(mlmc_ctx* ctx, const std::vector<SolveGroup>& groups,
         c.theta = th;
         consider(c);
     }
+    if (ctx->inner_tau_min <= 0)
+        for (double f : {0.3, 3.0}) {
+            TuneChoice c = cur;
+            c.tau_min = f * tau_floor(cfg.prec);
+            consider(c);
+        }
     ctx->prof.on = prof;
     if (s != MLMC_OK) return s;
     cur.best_ms = best;
