@@ -47,7 +47,7 @@ L2_FLUSH_BYTES = 512 << 20
 # over the step's launches, from one ncu capture of dram__bytes_read.sum + dram__bytes_write.sum
 # (summary under profiles/).  None whenever the solve kernel or its launch shape has changed since
 # that capture.
-SOLVE_TRAFFIC_BYTES_PER_LAUNCH = 5.67e9
+SOLVE_TRAFFIC_BYTES_PER_LAUNCH = 5.71e9
 
 
 DESC = ("mixed-precision batched MLMC: 5 levels h=1/16..1/256, KL 64 terms (exp. covariance sigma^2=1, "
@@ -674,7 +674,63 @@ def paper_cholesky(M, torch, dev, args, flush, stream, prob_kw):
             "time_gain": sum(secs["mlmc"]) / sum(secs["mpml"]),
             "mpml_seconds": sum(secs["mpml"]) / len(secs["mpml"]),
             "mlmc_seconds": sum(secs["mlmc"]) / len(secs["mlmc"])}
+    out["quarter"] = paper_cholesky_quarter(M, torch, dev, args, stream)
     return out
+
+
+def paper_cholesky_quarter(M, torch, dev, args, stream):
+    """The quarter-precision variant of Sec. 5.2: s = 1 term, sigma = 1, q = 2, h_0 = 1/4, levels 0 to 3,
+    k_p = 0.4, MSE tolerance 2e-6; MPML solves with qhhh on level 0 (an FP8 E4M3 factor, the q43 format)
+    and hhss above, against an FP64 factor (dddd) on the sample counts of an adaptive standard-MLMC run and
+    the same seeds.  The paper reports a memory gain of about 3.5 and an MPML error 11 % above MLMC's."""
+    import ctypes
+    import math
+    kw = dict(n0=4, m=2, L_max=3, kind=1, K=1, sigma2=1.0, q=2.0, corr_len=0.3)
+    tol = math.sqrt(2e-6)
+    bits = {"mpml": [], "mlmc": []}
+    secs = {"mpml": [], "mlmc": []}
+    est = {"mpml": [], "mlmc": []}
+    flags = 0
+    for run in range(args.paper_runs):
+        kwr = dict(kw, seed=3025 + run)
+        h = M.mlmc_create(M.make_problem(**kwr), dev.index or 0)
+        try:
+            o = M.mlmc_default_options()
+            o.tol, o.form, o.solver, o.fixed_delta = tol, M.MLMC_FORM_FP64_FIXED, M.MLMC_CHOLESKY, 1e-10
+            o.kp = 0.4
+            r0 = M.result_dict(M.mlmc_estimate(h, o))
+        finally:
+            M.mlmc_destroy(h)
+        Nl = [int(x) for x in r0["N"][: r0["L"] + 1]]
+        arr = (ctypes.c_int64 * len(Nl))(*Nl)
+        for name, form in (("mpml", M.MLMC_FORM_MIXED), ("mlmc", M.MLMC_FORM_FP64_FIXED)):
+            h = M.mlmc_create(M.make_problem(**kwr), dev.index or 0)
+            try:
+                o = M.mlmc_default_options()
+                o.form, o.solver, o.fixed_delta, o.L_start = form, M.MLMC_CHOLESKY, 1e-10, len(Nl) - 1
+                o.kp, o.tol, o.chol_table = 0.4, tol, 1
+                o.fixed_N = ctypes.cast(arr, ctypes.POINTER(ctypes.c_int64))
+                M.mlmc_estimate(h, o)
+                M.mlmc_profile_enable(h, True)
+                M.mlmc_profile_reset(h)
+                e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                e0.record(stream)
+                r = M.result_dict(M.mlmc_estimate(h, o))
+                e1.record(stream)
+                e1.synchronize()
+                prof = M.mlmc_profile_get(h)
+            finally:
+                M.mlmc_destroy(h)
+            bits[name].append(prof["chol_bits"])
+            secs[name].append(e0.elapsed_time(e1) / 1e3)
+            est[name].append(r["estimate"])
+            flags |= r["flags_or"]
+    diff = [abs(a - b) for a, b in zip(est["mpml"], est["mlmc"])]
+    return {"setting": "Sec. 5.2 quarter precision: s=1, sigma=1, q=2, h0=1/4, levels 0-3, k_p=0.4, TOL^2=2e-6; "
+                       "qhhh on level 0 (FP8 E4M3 factor), hhss above",
+            "paper_memory_gain": 3.5, "memory_gain": sum(bits["mlmc"]) / sum(bits["mpml"]),
+            "time_gain": sum(secs["mlmc"]) / sum(secs["mpml"]),
+            "mean_abs_estimate_diff": sum(diff) / len(diff), "flags_or": flags}
 
 
 def adjoint_case(M, torch, dev, args, hbm_peak, peak_src, flush, stream):

@@ -57,8 +57,10 @@ typedef enum {
     MLMC_FP32 = 1,    /* inner FP32, coefficient stored FP32                     */
     MLMC_BF16S = 2,   /* inner FP32, coefficient stored bfloat16                 */
     MLMC_FP16S = 3,   /* inner FP32, coefficient stored IEEE half                */
-    MLMC_FP64TC = 4   /* fields only: FP64 field from the tensor-core contraction
+    MLMC_FP64TC = 4,  /* fields only: FP64 field from the tensor-core contraction
                          (see mlmc_sample_fields); not an inner precision        */
+    MLMC_FP8S = 5     /* Cholesky factor only: stored FP8 E4M3 (4 exponent and 3
+                         mantissa bits, the quarter precision q43 of Sec. 5.2)   */
 } mlmc_prec;
 
 /* Solvers of the correction equation in the refinement (Alg. 2.1): the Krylov
@@ -313,6 +315,10 @@ typedef struct {
                               condition contrast h^-2 u_single <= 0.5 fails, and a 16-bit stored
                               coefficient IEEE half where a and D^-1 fit its normal range
                               (min a >= 6.2e-5, max a <= 4e3), else bfloat16                        */
+    int chol_table;        /* Cholesky solver, mixed form: the per-level precisions (u_f u_s u u_r) of
+                              Sec. 5.2.  0 (default): Table 1 (right), hhss on level 0, ssss on level 1,
+                              ssdd above; 1: the quarter-precision setting, qhhh on level 0 and hhss
+                              above.  The FP64 forms use dddd.                                        */
 } mlmc_options;
 
 typedef struct {
@@ -391,11 +397,14 @@ mlmc_status mlmc_adjoint_grad(mlmc_ctx* ctx, int level, int S, const double* xi,
 mlmc_status mlmc_set_precond(mlmc_ctx* ctx, mlmc_precond pc, int nu, int coarse_sweeps, double omega);
 
 /* Working precision u (of the iterate x) and residual precision u_r of the
- * refinement of this context's Cholesky solves (MLMC_CHOLESKY), each MLMC_FP32
- * or MLMC_FP64 (default FP64, FP64); with the factor precision `prec` of
- * mlmc_level_solve they form the quadruple (u_f, u_s = u_f, u, u_r) of Sec. 5.2,
- * e.g. (half, half, single, single) for `hhss`.  mlmc_estimate with the
- * Cholesky solver sets these per level itself (Table 1, right). */
+ * refinement of this context's Cholesky solves (MLMC_CHOLESKY): (u, u_r) one of
+ * (MLMC_FP64, MLMC_FP64) (default), (MLMC_FP32, MLMC_FP64), (MLMC_FP32,
+ * MLMC_FP32) or (MLMC_FP16S, MLMC_FP16S) (x and the residual stored in IEEE
+ * half, formed in FP32).  With the factor precision `prec` of mlmc_level_solve
+ * (MLMC_FP8S, MLMC_FP16S, MLMC_BF16S, MLMC_FP32 or MLMC_FP64) they form the
+ * quadruple (u_f, u_s = u_f, u, u_r) of Sec. 5.2, e.g. (half, half, single,
+ * single) for `hhss`.  mlmc_estimate with the Cholesky solver sets these per
+ * level itself (mlmc_options.chol_table). */
 mlmc_status mlmc_set_cholesky_precision(mlmc_ctx* ctx, mlmc_prec u, mlmc_prec u_r);
 
 /* Inner tolerance of the refinement (Alg. 2.1) for this context's solves: each

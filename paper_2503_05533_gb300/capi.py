@@ -21,7 +21,7 @@ MLMC_OK, MLMC_E_ARG, MLMC_E_NOMEM, MLMC_E_CUDA, MLMC_E_NOCONV, MLMC_E_NONFINITE,
 STATUS_NAMES = ["MLMC_OK", "MLMC_E_ARG", "MLMC_E_NOMEM", "MLMC_E_CUDA", "MLMC_E_NOCONV", "MLMC_E_NONFINITE",
                 "MLMC_E_TIMEOUT", "MLMC_E_UNSUPPORTED"]
 # mlmc_prec
-MLMC_FP64, MLMC_FP32, MLMC_BF16S, MLMC_FP16S, MLMC_FP64TC = range(5)
+MLMC_FP64, MLMC_FP32, MLMC_BF16S, MLMC_FP16S, MLMC_FP64TC, MLMC_FP8S = range(6)
 # mlmc_solver
 MLMC_CG, MLMC_MINRES, MLMC_CHOLESKY = range(3)
 MLMC_PC_JACOBI, MLMC_PC_MG = range(2)
@@ -51,7 +51,7 @@ class mlmc_options(ctypes.Structure):
                 ("alpha", c_double), ("gamma", c_double), ("r", c_double), ("form", c_int),
                 ("fixed_delta", c_double), ("force_prec", c_int), ("solver", c_int), ("max_iters", c_int),
                 ("max_rounds", c_int), ("fixed_N", POINTER(c_int64)), ("contrast", c_double),
-                ("mixed_field", c_int), ("prec_rule", c_int)]
+                ("mixed_field", c_int), ("prec_rule", c_int), ("chol_table", c_int)]
 
 
 class mlmc_result(ctypes.Structure):

@@ -318,6 +318,10 @@ mlmc_status check_options(const mlmc_options* o, int L_max, std::string& err) {
         err = "options: bad form, precision, solver or max_iters";
         return MLMC_E_ARG;
     }
+    if (o->chol_table != 0 && o->chol_table != 1) {
+        err = "options: chol_table must be 0 or 1";
+        return MLMC_E_ARG;
+    }
     if (o->prec_rule != 0 && o->prec_rule != 1) {
         err = "options: prec_rule must be 0 or 1";
         return MLMC_E_ARG;
@@ -517,8 +521,11 @@ mlmc_status mlmc_set_inner_tolerance(mlmc_ctx* ctx, double theta, double tau_min
 
 mlmc_status mlmc_set_cholesky_precision(mlmc_ctx* ctx, mlmc_prec u, mlmc_prec u_r) {
     if (!ctx) return MLMC_E_ARG;
-    if ((u != MLMC_FP32 && u != MLMC_FP64) || (u_r != MLMC_FP32 && u_r != MLMC_FP64))
-        return fail(ctx, MLMC_E_ARG, "set_cholesky_precision: u and u_r must be MLMC_FP32 or MLMC_FP64");
+    const bool ok = (u == MLMC_FP64 && u_r == MLMC_FP64) || (u == MLMC_FP32 && (u_r == MLMC_FP32 || u_r == MLMC_FP64)) ||
+                    (u == MLMC_FP16S && u_r == MLMC_FP16S);
+    if (!ok)
+        return fail(ctx, MLMC_E_ARG, "set_cholesky_precision: (u, u_r) must be (FP64, FP64), (FP32, FP64), "
+                                     "(FP32, FP32) or (FP16S, FP16S)");
     ctx->chol_u = u;
     ctx->chol_ur = u_r;
     return MLMC_OK;
@@ -618,7 +625,8 @@ mlmc_status mlmc_level_solve(mlmc_ctx* ctx, int n, int S, const void* a, mlmc_pr
                              mlmc_prec prec, mlmc_solver solver, double delta, int max_iters, double* u,
                              double* Q, int32_t* iters, double* relres, int32_t* flags, void* stream) {
     if (!ctx) return MLMC_E_ARG;
-    if (n < 2 || n > 2048 || S < 0 || a_n < n || a_n % n != 0 || !is_master_prec(a_prec) || !is_prec(prec) ||
+    if (n < 2 || n > 2048 || S < 0 || a_n < n || a_n % n != 0 || !is_master_prec(a_prec) ||
+        !(is_prec(prec) || (solver == MLMC_CHOLESKY && prec == MLMC_FP8S)) ||
         (solver != MLMC_CG && solver != MLMC_MINRES && solver != MLMC_CHOLESKY) || !(delta > 0) || max_iters < 1)
         return fail(ctx, MLMC_E_ARG, "level_solve: bad n, S, a_n, precision, solver, delta or max_iters");
     if (S == 0) return MLMC_OK;
@@ -774,20 +782,27 @@ mlmc_status mlmc_estimate(mlmc_ctx* ctx, const mlmc_options* opts, mlmc_result* 
         auto prec_for = [&](int g, int fl) -> mlmc_prec {
             if (o.form != MLMC_FORM_MIXED) return MLMC_FP64;
             if (o.force_prec >= 0) return (mlmc_prec)o.force_prec;
-            // the Cholesky solver of Sec. 5.2 takes Table 1 (right): a half factor on level 0, single above
-            if (o.solver == MLMC_CHOLESKY) return g == 0 ? MLMC_FP16S : MLMC_FP32;
+            // the Cholesky solver of Sec. 5.2: Table 1 (right), a half factor on level 0 and single above; or
+            // the quarter-precision setting, q43 (FP8 E4M3) on level 0 and half above
+            if (o.solver == MLMC_CHOLESKY) {
+                if (o.chol_table == 1) return g == 0 ? MLMC_FP8S : MLMC_FP16S;
+                return g == 0 ? MLMC_FP16S : MLMC_FP32;
+            }
             if (calibrate) return pick_prec_calibrated(h[g], df[g], cal_contrast[fl], cal_amin[fl], cal_amax[fl]);
             return prec_rule[g];
         };
         auto prec_of = [&](int l) -> mlmc_prec { return prec_for(l, l); };
         // launch class of a solve: the factor / inner precision, plus for the Cholesky solver the working
-        // and residual precisions of Table 1 (right): single on levels 0 and 1 (hhss, ssss), double above
-        // (ssdd); double throughout for the FP64 forms (dddd)
+        // and residual precision (bits 4-5: 0 double, 1 single, 2 half) -- Table 1 (right): single on
+        // levels 0 and 1 (hhss, ssss), double above (ssdd); the quarter-precision setting: half on level 0
+        // (qhhh), single above (hhss); double throughout for the FP64 forms (dddd)
         auto class_of = [&](int g, int fl) -> int {
             const int p = prec_for(g, fl);
-            if (o.solver != MLMC_CHOLESKY) return p;
-            const bool dbl = o.form != MLMC_FORM_MIXED || g >= 2;
-            return p | (dbl ? 0 : 16);
+            if (o.solver != MLMC_CHOLESKY || o.form != MLMC_FORM_MIXED) return p;
+            int w = 0;
+            if (o.chol_table == 1) w = g == 0 ? 2 : 1;
+            else w = g <= 1 ? 1 : 0;
+            return p | (w << 4);
         };
         size_t fbytes = 0, xbytes = 0, qn = 0;
         std::vector<size_t> foff(req.size()), xoff(req.size()), qoff(req.size());
@@ -889,7 +904,8 @@ mlmc_status mlmc_estimate(mlmc_ctx* ctx, const mlmc_options* opts, mlmc_result* 
             b.cfg.prec = kv.first & 15;
             b.cfg.solver = o.solver;
             b.cfg.max_iters = o.max_iters;
-            b.cfg.chol_u = (kv.first & 16) ? MLMC_FP32 : MLMC_FP64;
+            const int w = (kv.first >> 4) & 3;
+            b.cfg.chol_u = w == 0 ? MLMC_FP64 : (w == 1 ? MLMC_FP32 : MLMC_FP16S);
             b.cfg.chol_ur = b.cfg.chol_u;
             batches.push_back(std::move(b));
         }
@@ -916,7 +932,10 @@ mlmc_status mlmc_estimate(mlmc_ctx* ctx, const mlmc_options* opts, mlmc_result* 
                     const size_t aV = (size_t)(g.a_n + 1) * (g.a_n + 1);
                     for (int smp = 0; smp < g.S; ++smp) {
                         const size_t q = (size_t)(g.flags - flf) + smp;
-                        if (!(hfl[q] & (MLMC_F_STAGNATED | MLMC_F_MAXIT))) continue;
+                        // a low-precision Cholesky factor that overflowed (Sec. 5.2) is retried like a stall
+                        const int32_t retry_on = MLMC_F_STAGNATED | MLMC_F_MAXIT |
+                                                 (o.solver == MLMC_CHOLESKY ? MLMC_F_NONFINITE : 0);
+                        if (!(hfl[q] & retry_on)) continue;
                         SolveGroup r = g;
                         r.S = 1;
                         r.a = static_cast<const char*>(g.a) + smp * aV * elem;

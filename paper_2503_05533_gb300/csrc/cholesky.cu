@@ -6,7 +6,8 @@
 // (i-1)); the P1 operator of Sec. 3.1 couples k with k +- 1 and k +- (n-1), so
 // A is banded with half-bandwidth bw = n - 1 and its Cholesky factor L fills
 // the band.  The factor is stored by columns, band[k][t] = L(k+t, k) for
-// t = 0..bw, in the storage type FT: IEEE half, bfloat16, single or double.
+// t = 0..bw, in the storage type FT: FP8 E4M3 (4 exponent and 3 mantissa bits:
+// the paper's quarter precision q43), IEEE half, bfloat16, single or double.
 //
 // Factorisation (right-looking, column by column): d = sqrt(A(k,k)), the column
 // below the diagonal is divided by d, and the trailing (bw x bw) triangle is
@@ -24,10 +25,12 @@
 // (u_f = u_s, u, u_r) are the paper's quadruple of Sec. 5.2, e.g. (h, h, s, s).
 #include <cuda_bf16.h>
 #include <cuda_fp16.h>
+#include <cuda_fp8.h>
 #include <cuda_runtime.h>
 
 #include <algorithm>
 #include <cmath>
+#include <type_traits>
 #include <vector>
 
 #include "device_common.cuh"
@@ -66,17 +69,29 @@ struct CholParams {
     double stag;
 };
 
+// FP8 E4M3 storage (the paper's q43); a value beyond its range becomes NaN (no saturation), so that an
+// overflowing factor is detected.
+struct q43 {
+    __nv_fp8_storage_t b;
+};
 template <class T> __device__ __forceinline__ T to_t(double v) { return (T)v; }
+template <> __device__ __forceinline__ q43 to_t<q43>(double v) {
+    return {__nv_cvt_float_to_fp8((float)v, __NV_NOSAT, __NV_E4M3)};
+}
 template <> __device__ __forceinline__ __half to_t<__half>(double v) { return __double2half(v); }
 template <> __device__ __forceinline__ __nv_bfloat16 to_t<__nv_bfloat16>(double v) { return __double2bfloat16(v); }
 template <class CT> __device__ __forceinline__ CT from_t(double v) { return (CT)v; }
 template <class CT> __device__ __forceinline__ CT from_t(float v) { return (CT)v; }
 template <class CT> __device__ __forceinline__ CT from_t(__half v) { return (CT)__half2float(v); }
 template <class CT> __device__ __forceinline__ CT from_t(__nv_bfloat16 v) { return (CT)__bfloat162float(v); }
+template <class CT> __device__ __forceinline__ CT from_t(q43 v) {
+    return (CT)__half2float(__half(__nv_cvt_fp8_to_halfraw(v.b, __NV_E4M3)));
+}
 template <class T> __device__ __forceinline__ T round_to(float v);
 template <> __device__ __forceinline__ float round_to<float>(float v) { return v; }
 template <> __device__ __forceinline__ __half round_to<__half>(float v) { return __float2half_rn(v); }
 template <> __device__ __forceinline__ __nv_bfloat16 round_to<__nv_bfloat16>(float v) { return __float2bfloat16_rn(v); }
+template <> __device__ __forceinline__ q43 round_to<q43>(float v) { return to_t<q43>((double)v); }
 template <class T> __device__ __forceinline__ T round_to(double v) { return to_t<T>(v); }
 
 __device__ __forceinline__ double chol_master(const CholSystem& S, int i, int j) {
@@ -129,9 +144,11 @@ __device__ __forceinline__ double cta_sum(double v, double* red) {
     return s;
 }
 
-// FT factor storage, CT factor and substitution arithmetic, WT working precision (x), RT residual.
+// FT factor storage, CT factor and substitution arithmetic, WT working precision (x), RT residual
+// precision (computed in RC: FP64 for a double residual, FP32 otherwise).
 template <class FT, class CT, class WT, class RT>
 __global__ void __launch_bounds__(kCholThreads) chol_ir_kernel(CholParams P) {
+    using RC = typename std::conditional<std::is_same<RT, double>::value, double, float>::type;
     extern __shared__ __align__(16) uint8_t chol_smem[];
     __shared__ double red[kCholThreads / 32];
     const CholSystem S = P.sys[blockIdx.x];
@@ -191,7 +208,7 @@ __global__ void __launch_bounds__(kCholThreads) chol_ir_kernel(CholParams P) {
     }
 
     // ---- refinement (Alg. 2.1)
-    for (int k = t; k < N; k += kCholThreads) X[k] = (WT)0;
+    for (int k = t; k < N; k += kCholThreads) X[k] = to_t<WT>(0.0);
     __syncthreads();
     double rho = 0.0, rho_prev = 0.0;
     int steps = 0, flag = 0;
@@ -200,19 +217,21 @@ __global__ void __launch_bounds__(kCholThreads) chol_ir_kernel(CholParams P) {
         double res = 0.0;
         for (int k = t; k < N; k += kCholThreads) {
             const int i = 1 + k % m, j = 1 + k / m;
-            const RT b = S.f == 0.0 ? (RT)0 : (RT)(S.f * S.h2);
-            RT rk = b;
+            const RC b = (RC)(S.f * S.h2);
+            RC rk = b;
             if (steps > 0) {
-                const RT x0 = (RT)X[k];
-                const RT xe = i < m ? (RT)X[k + 1] : (RT)0, xw = i > 1 ? (RT)X[k - 1] : (RT)0;
-                const RT xn = j < m ? (RT)X[k + m] : (RT)0, xs = j > 1 ? (RT)X[k - m] : (RT)0;
-                const RT ax = (weight_e<RT>(S, i, j) * (x0 - xe) + weight_e<RT>(S, i - 1, j) * (x0 - xw) +
-                               weight_n<RT>(S, i, j) * (x0 - xn) + weight_n<RT>(S, i, j - 1) * (x0 - xs)) *
-                              (RT)(1.0 / 6.0);
+                const RC x0 = from_t<RC>(X[k]);
+                const RC xe = i < m ? from_t<RC>(X[k + 1]) : (RC)0, xw = i > 1 ? from_t<RC>(X[k - 1]) : (RC)0;
+                const RC xn = j < m ? from_t<RC>(X[k + m]) : (RC)0, xs = j > 1 ? from_t<RC>(X[k - m]) : (RC)0;
+                const RC ax = (weight_e<RC>(S, i, j) * (x0 - xe) + weight_e<RC>(S, i - 1, j) * (x0 - xw) +
+                               weight_n<RC>(S, i, j) * (x0 - xn) + weight_n<RC>(S, i, j - 1) * (x0 - xs)) *
+                              (RC)(1.0 / 6.0);
                 rk = b - ax;
             }
-            rv[k] = (CT)rk;
-            res += (double)rk * (double)rk;
+            // the residual in u_r (a half u_r stores it rounded to half)
+            const double rq = from_t<double>(to_t<RT>((double)rk));
+            rv[k] = (CT)rq;
+            res += rq * rq;
         }
         res = cta_sum(res, red);   // (its barriers also publish rv)
         rho = sqrt(res) / S.bnorm;
@@ -238,7 +257,7 @@ __global__ void __launch_bounds__(kCholThreads) chol_ir_kernel(CholParams P) {
             if (t == 0) rv[k] = dk;
             __syncthreads();
         }
-        for (int k = t; k < N; k += kCholThreads) X[k] = (WT)((WT)X[k] + (WT)rv[k]);
+        for (int k = t; k < N; k += kCholThreads) X[k] = to_t<WT>(from_t<double>(X[k]) + (double)rv[k]);
         __syncthreads();
     }
 
@@ -246,14 +265,14 @@ __global__ void __launch_bounds__(kCholThreads) chol_ir_kernel(CholParams P) {
     double q = 0.0;
     for (int k = t; k < N; k += kCholThreads) {
         const int i = 1 + k % m, j = 1 + k / m;
-        q += chol_qoi_weight(S, i, j) * (double)X[k];
+        q += chol_qoi_weight(S, i, j) * from_t<double>(X[k]);
     }
     q = cta_sum(q, red);
     if (S.u) {
         double* u = S.u + (size_t)S.out * (S.n + 1) * (S.n + 1);
         for (int v = t; v < (S.n + 1) * (S.n + 1); v += kCholThreads) {
             const int i = v % (S.n + 1), j = v / (S.n + 1);
-            u[v] = (i >= 1 && i <= m && j >= 1 && j <= m) ? (double)X[(j - 1) * m + (i - 1)] : 0.0;
+            u[v] = (i >= 1 && i <= m && j >= 1 && j <= m) ? from_t<double>(X[(j - 1) * m + (i - 1)]) : 0.0;
         }
     }
     if (t == 0) {
@@ -356,10 +375,9 @@ mlmc_status chol_launch_typed(mlmc_ctx* ctx, const std::vector<SolveGroup>& grou
 template <class FT, class CT>
 mlmc_status chol_dispatch_w(mlmc_ctx* ctx, const std::vector<SolveGroup>& groups, const SolveConfig& cfg,
                             cudaStream_t st, std::vector<int>& ns, int32_t** steps) {
-    if (cfg.chol_u == MLMC_FP64) {
-        return cfg.chol_ur == MLMC_FP64 ? chol_launch_typed<FT, CT, double, double>(ctx, groups, cfg, st, ns, steps)
-                                        : chol_launch_typed<FT, CT, double, float>(ctx, groups, cfg, st, ns, steps);
-    }
+    // (u, u_r): (d, d), (s, d), (s, s), (h, h)
+    if (cfg.chol_u == MLMC_FP64) return chol_launch_typed<FT, CT, double, double>(ctx, groups, cfg, st, ns, steps);
+    if (cfg.chol_u == MLMC_FP16S) return chol_launch_typed<FT, CT, __half, __half>(ctx, groups, cfg, st, ns, steps);
     return cfg.chol_ur == MLMC_FP64 ? chol_launch_typed<FT, CT, float, double>(ctx, groups, cfg, st, ns, steps)
                                     : chol_launch_typed<FT, CT, float, float>(ctx, groups, cfg, st, ns, steps);
 }
@@ -368,6 +386,7 @@ double prec_bits(int p) {
     switch (p) {
         case MLMC_FP64: return 64.0;
         case MLMC_FP32: return 32.0;
+        case MLMC_FP8S: return 8.0;
         default: return 16.0;
     }
 }
@@ -396,6 +415,7 @@ mlmc_status run_cholesky_batch(mlmc_ctx* ctx, const std::vector<SolveGroup>& gro
         case MLMC_FP32: s = chol_dispatch_w<float, float>(ctx, groups, cfg, st, ns, &steps_dev); break;
         case MLMC_BF16S: s = chol_dispatch_w<__nv_bfloat16, float>(ctx, groups, cfg, st, ns, &steps_dev); break;
         case MLMC_FP16S: s = chol_dispatch_w<__half, float>(ctx, groups, cfg, st, ns, &steps_dev); break;
+        case MLMC_FP8S: s = chol_dispatch_w<q43, float>(ctx, groups, cfg, st, ns, &steps_dev); break;
         default: ctx->err = "cholesky: bad factor precision"; s = MLMC_E_ARG;
     }
     if (s != MLMC_OK) return s;
