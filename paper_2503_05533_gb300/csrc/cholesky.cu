@@ -298,7 +298,7 @@ mlmc_status chol_launch_typed(mlmc_ctx* ctx, const std::vector<SolveGroup>& grou
         const int n = g.n, m = n - 1;
         const int stride = g.a_n / n;
         const size_t elem = g.a_fp64 ? sizeof(double) : sizeof(float);
-        const long long aV = (long long)(g.a_n + 1) * (g.a_n + 1);
+        const long long aV = field_pitch(g);
         const double h = 1.0 / n;
         int bx0 = 0, bx1 = n, by0 = 0, by1 = n;
         if (pb.qoi == 1) {

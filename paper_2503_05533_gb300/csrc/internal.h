@@ -155,13 +155,15 @@ cudaError_t launch_philox_normals(uint64_t seed, int level, uint64_t first, int 
                                   cudaStream_t st);
 // kl_synth.cu
 cudaError_t upload_basis(GridBasis& gb, const mlmc_field& f, int n, std::string& err);
-cudaError_t launch_kl_fp64(const GridBasis& gb, int S, const double* xi, double* a, cudaStream_t st);
+// Field syntheses write sample s's (n+1)^2 nodes at a + s ld.
+cudaError_t launch_kl_fp64(const GridBasis& gb, int S, const double* xi, double* a, long long ld, cudaStream_t st);
 // kl_tc.cu: tensor-core synthesis into FP32
 cudaError_t launch_kl_fp32(mlmc_ctx* ctx, const GridBasis& gb, int S, const double* xi, float* a,
-                           cudaStream_t st);
+                           long long ld, cudaStream_t st);
 // kl_tc.cu: tensor-core synthesis into FP64 (exact integer lead slice, float-float exp); builds the
 // grid's exact-lead basis slices on first use
-cudaError_t launch_kl_tc64(mlmc_ctx* ctx, GridBasis& gb, int S, const double* xi, double* a, cudaStream_t st);
+cudaError_t launch_kl_tc64(mlmc_ctx* ctx, GridBasis& gb, int S, const double* xi, double* a, long long ld,
+                           cudaStream_t st);
 cudaError_t launch_kl_transpose_fp64(const GridBasis& gb, int S, const double* w, double* out,
                                      cudaStream_t st);
 // stencil / solver (solver.cu)
@@ -171,6 +173,7 @@ struct SolveGroup {
     const void* a = nullptr;   // master coefficient, dense nodal layout of grid a_n
     int a_fp64 = 1;        // master precision: 1 FP64, 0 FP32
     int a_n = 0;           // grid of `a` (multiple of n)
+    long long a_ld = 0;    // elements from one system's coefficient to the next (0: (a_n+1)^2)
     double delta = 1e-8;   // relative residual target
     double* Q = nullptr;   // out [S]
     double* u = nullptr;   // optional out [S][(n+1)^2]
@@ -179,6 +182,9 @@ struct SolveGroup {
     int32_t* flags = nullptr;
     const double* rhs_weights = nullptr;  // internal: adjoint right-hand side (g) instead of f
 };
+inline long long field_pitch(const SolveGroup& g) {
+    return g.a_ld > 0 ? g.a_ld : (long long)(g.a_n + 1) * (g.a_n + 1);
+}
 struct SolveConfig {
     int prec = MLMC_FP64;  // mlmc_prec of the inner solve
     int solver = MLMC_CG;
@@ -256,7 +262,8 @@ cudaError_t launch_apply_operator(int n, int S, const void* a, int a_fp64, int a
 cudaError_t launch_level_stats(int S, const double* Qf, const double* Qc, mlmc_acc* out_dev,
                                cudaStream_t st);
 // min and max nodal coefficient of each of S fields of V nodes: out_dev [S][2]
-cudaError_t launch_field_range(int S, int V, const void* a, int a_fp64, double* out_dev, cudaStream_t st);
+cudaError_t launch_field_range(int S, int V, long long ld, const void* a, int a_fp64, double* out_dev,
+                               cudaStream_t st);
 // adjoint.cu
 cudaError_t launch_adjoint_elements(int n, int S, const void* a, int a_fp64, const double* u,
                                     const double* lam, double* G, cudaStream_t st);

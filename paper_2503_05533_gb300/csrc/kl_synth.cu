@@ -46,7 +46,7 @@ template <class OutT>
 __global__ void __launch_bounds__(256) kl_fp64_kernel(int S, int K, int V, int ld64,
                                                       const double* __restrict__ xi,
                                                       const double* __restrict__ phi,
-                                                      OutT* __restrict__ out) {
+                                                      OutT* __restrict__ out, long long ldo) {
     constexpr int KC = 32;
     __shared__ double sx[32][KC + 1];
     const int tx = threadIdx.x, ty = threadIdx.y;
@@ -85,7 +85,7 @@ __global__ void __launch_bounds__(256) kl_fp64_kernel(int S, int K, int V, int l
 #pragma unroll
         for (int b = 0; b < 4; ++b) {
             const int v = v0 + b;
-            if (v < V) out[(size_t)s * V + v] = (OutT)exp(acc[a][b]);
+            if (v < V) out[(size_t)s * ldo + v] = (OutT)exp(acc[a][b]);
         }
     }
 }
@@ -172,17 +172,18 @@ cudaError_t upload_basis(GridBasis& gb, const mlmc_field& f, int n, std::string&
 }
 
 template <class OutT>
-static cudaError_t kl_fp64_launch(const GridBasis& gb, int S, const double* xi, OutT* a, cudaStream_t st) {
+static cudaError_t kl_fp64_launch(const GridBasis& gb, int S, const double* xi, OutT* a, long long ld,
+                                  cudaStream_t st) {
     if (S <= 0) return cudaSuccess;
     dim3 block(64, 4);
     dim3 grid((gb.nodes + 255) / 256, (S + 31) / 32);
-    kl_fp64_kernel<OutT><<<grid, block, 0, st>>>(S, gb.K, gb.nodes, gb.nodes_pad, xi, gb.phi64.as<double>(), a);
+    kl_fp64_kernel<OutT><<<grid, block, 0, st>>>(S, gb.K, gb.nodes, gb.nodes_pad, xi, gb.phi64.as<double>(), a, ld);
     g_launches.fetch_add(1, std::memory_order_relaxed);
     return cudaGetLastError();
 }
 
-cudaError_t launch_kl_fp64(const GridBasis& gb, int S, const double* xi, double* a, cudaStream_t st) {
-    return kl_fp64_launch<double>(gb, S, xi, a, st);
+cudaError_t launch_kl_fp64(const GridBasis& gb, int S, const double* xi, double* a, long long ld, cudaStream_t st) {
+    return kl_fp64_launch<double>(gb, S, xi, a, ld, st);
 }
 
 cudaError_t launch_kl_transpose_fp64(const GridBasis& gb, int S, const double* w, double* out,

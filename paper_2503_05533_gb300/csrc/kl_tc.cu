@@ -44,10 +44,15 @@
 // K block by TMA (128-byte swizzle) through a ring of shared-memory stages;
 // warp 1 issues the MMAs (M = 128, N = TN, K = 16) into one of two tensor-
 // memory buffers and signals through mbarriers; TN / 8 epilogue warps drain
-// the other buffer (each warp 32 sample columns of one TMEM lane quarter) and
-// write, sample by sample, the 32 consecutive nodes of their lanes with one
-// coalesced store.  Loads of tile t+1 and the epilogue of tile t overlap its
-// MMAs.  Every mbarrier wait is bounded in wall time; on expiry the CTA records
+// the other buffer (each warp 32 sample columns of one TMEM lane quarter).
+// Loads of tile t+1 and the epilogue of tile t overlap its MMAs.  Output rows
+// (one per sample) are `ldo` elements apart.  When they are whole 128-byte
+// lines (ldo a multiple of 32, aligned base: the layout the estimate uses),
+// each warp writes, sample by sample, the 32 consecutive nodes of its lanes
+// as one full line straight from registers.  Otherwise (dense rows of
+// (n+1)^2 elements, which start at any 4-byte offset) the FP32 form stages
+// each 32-sample chunk in shared memory and writes whole 128-node rows with
+// 16-byte stores, so that no store straddles two lines needlessly.  Every mbarrier wait is bounded in wall time; on expiry the CTA records
 // the context's error word, every role leaves its loop, the producer waits
 // (bounded) for its copies in flight, and the TMEM is freed.
 #include <cuda.h>
@@ -68,14 +73,22 @@ namespace {
 constexpr int TM = 128;              // nodes per tile (MMA M, TMEM lanes)
 constexpr int TKB = 64;              // terms per K block: 64 FP16 = one 128-byte swizzle row
 constexpr uint32_t kATile = TM * TKB * 2;   // 16 KiB: one slice of 128 node rows
+constexpr int kStgPitch = TM + 4;           // floats per staging row (528 bytes, a multiple of 16)
 
-// MODE 0: FP32 output (2 slices per operand); MODE 1: FP64 output (3 slices, exact lead).
+// MODE 0: FP32 output (2 slices per operand) through the shared-memory staging of the epilogue;
+// MODE 2: the same into rows of whole 128-byte lines, stored straight from registers (a third TMA stage
+// in place of the staging area); MODE 1: FP64 output (3 slices, exact lead).
 template <int MODE> struct KLCfg;
 // Warp 0 issues the TMA copies, warp 1 the MMAs; EW = TN / 8 epilogue warps follow, each draining one
 // 32-column chunk of one TMEM lane quarter (its warp index mod 4).
 template <> struct KLCfg<0> {
-    static constexpr int NA = 2, NB = 2, TN = 128, NACC = 2, NSTAGE = 3, EW = TN / 8;
+    static constexpr int NA = 2, NB = 2, TN = 128, NACC = 2, NSTAGE = 2, EW = TN / 8;
     static constexpr bool DRAIN = false;   // accumulate the whole K range in TMEM
+    using Out = float;
+};
+template <> struct KLCfg<2> {
+    static constexpr int NA = 2, NB = 2, TN = 128, NACC = 2, NSTAGE = 3, EW = TN / 8;
+    static constexpr bool DRAIN = false;
     using Out = float;
 };
 template <> struct KLCfg<1> {
@@ -89,7 +102,11 @@ template <int MODE> struct KLLayout {
     static constexpr uint32_t kBTile = C::TN * TKB * 2;
     static constexpr uint32_t kStage = C::NA * kATile + C::NB * kBTile;   // multiple of 1024
     static constexpr uint32_t kOffStg = C::NSTAGE * kStage;
-    static constexpr uint32_t kStgBytes = 0;
+    // FP32 form: per 32-sample chunk, 32 staging rows of kStgPitch floats (a tile row of 128 nodes plus a
+    // shift of up to 3 that aligns it with the output's 16-byte boundaries).  Two TMA stages make room
+    // for it; two rounds of 16 rows beside a third stage measured slower (the extra barriers).
+    // FP64 form: the exponential's table 2^(j/32) = th + tl (64 floats), indexed per lane
+    static constexpr uint32_t kStgBytes = MODE == 0 ? (C::TN / 32) * 32 * kStgPitch * 4 : (MODE == 1 ? 64 * 4 : 0);
     static constexpr int kThreads = 64 + 32 * C::EW;
     static constexpr uint32_t kOffBar = (kOffStg + kStgBytes + 15) / 16 * 16;
     // full[NSTAGE], empty[NSTAGE], tfull[2], tempty[2], then the TMEM address and the abort flag
@@ -163,6 +180,22 @@ __device__ __forceinline__ float ex2_approx(float x) {
 __device__ __forceinline__ void tmem_wait_ld() { asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory"); }
 __device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
 __device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
+// Named barrier `id` over `count` threads that also returns the OR of every thread's `v`.
+__device__ __forceinline__ bool bar_or(int id, int count, bool v) {
+    uint32_t r;
+    asm volatile(
+        "{\n\t.reg .pred p, q;\n\t"
+        "setp.ne.u32 q, %1, 0;\n\t"
+        "barrier.cta.red.or.pred p, %2, %3, q;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}"
+        : "=r"(r)
+        : "r"((uint32_t)v), "r"(id), "r"(count)
+        : "memory");
+    return r != 0;
+}
+__device__ __forceinline__ void bar_sync_n(int id, int count) {
+    asm volatile("barrier.cta.sync %0, %1;" ::"r"(id), "r"(count) : "memory");
+}
 
 // Tile t -> (sample tile st, node tile nt).  Node tiles go in groups of G; a group's tiles are
 // taken node tile fastest, so the tiles in flight at any time cover about G consecutive node tiles
@@ -204,8 +237,41 @@ __device__ __forceinline__ bool kl_warp_wait(uint64_t* bar, uint32_t parity, vol
     return ok;
 }
 
-// exp(xh + xl) as a float-float pair (Tang's table-driven method, see the file comment).
-__device__ __forceinline__ void ff_exp(float xh, float xl, const FFExp& T, float& rh, float& rl) {
+// x 2^e: one product with the power of two when 2^e is a normal float (the same single rounding as
+// ldexpf), else ldexpf.
+__device__ __forceinline__ float scale2(float x, int e) {
+    return (e >= -126 && e <= 127) ? __fmul_rn(x, __int_as_float((e + 127) << 23)) : ldexpf(x, e);
+}
+// The rare cases of ff_to_double, on the FP64 pipe (kept out of line, so that the common path never
+// executes FP64 instructions under a predicate).
+__device__ __noinline__ double ff_to_double_fp64(float ah, float al) { return (double)ah + (double)al; }
+
+// (double)ah + (double)al rounded to nearest, for a float-float pair with |al| <= ulp(ah) / 2, without the
+// FP64 pipe (GB300's is narrow): ah's double has its float mantissa followed by 29 zero bits, so al
+// amounts to k = al / ulp_double(ah) units of the last place, |k| <= 2^28; al 2^(52 - e) is an exact
+// power-of-two scaling, its rounding to the nearest integer (ties to even) is the rounding of the sum
+// (the last bit of the result is k's), and k is added to the bit pattern.  A sum that leaves ah's
+// binade downwards (ah a power of two, |ah + al| < |ah|), where the last place halves, and exponents
+// outside [-60, 100] take the FP64 instructions.
+__device__ __forceinline__ double ff_to_double(float ah, float al) {
+    const uint32_t u = __float_as_uint(ah);
+    const int Eb = (int)((u >> 23) & 0xFFu);
+    const uint32_t M = u & 0x7FFFFFu;
+    const int e = Eb - 127;
+    const bool down = (M == 0u) && ((al < 0.0f) != (ah < 0.0f)) && al != 0.0f;
+    if (e < -60 || e > 100 || down) return ff_to_double_fp64(ah, al);
+    const unsigned long long bits =
+        ((unsigned long long)((u & 0x80000000u) | ((uint32_t)(Eb + 896) << 20) | (M >> 3)) << 32) |
+        (unsigned long long)(u << 29);
+    int k = __float2int_rn(__fmul_rn(al, __int_as_float((52 - e + 127) << 23)));
+    if (u >> 31) k = -k;    // the bits hold |ah|: a negative ah grows in magnitude with a negative al
+    return __longlong_as_double((long long)(bits + (unsigned long long)(long long)k));
+}
+
+// exp(xh + xl) as a float-float pair (Tang's table-driven method, see the file comment); th, tl: the
+// table 2^(j/32) = th[j] + tl[j] (shared memory).
+__device__ __forceinline__ void ff_exp(float xh, float xl, const FFExp& T, const float* th_s, const float* tl_s,
+                                       float& rh, float& rl) {
     const int N = __float2int_rn(__fmul_rn(xh, T.inv));
     const float nf = (float)N;
     const int j = N & 31;
@@ -229,15 +295,15 @@ __device__ __forceinline__ void ff_exp(float xh, float xl, const FFExp& T, float
     float q, ql;
     ff_fast_two_sum(qh, ql0, q, ql);
     // 2^(j/32) (1 + q)
-    const float th = T.th[j], tl = T.tl[j];
+    const float th = th_s[j], tl = tl_s[j];
     float ph, phe, s1, s1e;
     ff_two_prod(th, q, ph, phe);
     ff_two_sum(th, ph, s1, s1e);
     const float lo2 = __fadd_rn(__fadd_rn(s1e, phe), __fmaf_rn(th, ql, __fmaf_rn(tl, q, tl)));
     float h, l;
     ff_fast_two_sum(s1, lo2, h, l);
-    rh = ldexpf(h, m);
-    rl = ldexpf(l, m);
+    rh = scale2(h, m);
+    rl = scale2(l, m);
 }
 
 template <int MODE>
@@ -245,6 +311,7 @@ __global__ void __launch_bounds__(KLLayout<MODE>::kThreads, 1)
     kl_tc_kernel(const __grid_constant__ CUtensorMap mapA, const __grid_constant__ CUtensorMap mapB, int S, int Spad,
                  int V, int Vpad, int Kpad, int num_st, int num_tiles, int tile_group, const int* __restrict__ es,
                  const int* __restrict__ ev, const __grid_constant__ FFExp ffx, typename KLCfg<MODE>::Out* __restrict__ out,
+                 long long ldo,
                  unsigned* err, unsigned long long timeout_ns, unsigned extra_tx) {
     using C = KLCfg<MODE>;
     using Lay = KLLayout<MODE>;
@@ -260,6 +327,14 @@ __global__ void __launch_bounds__(KLLayout<MODE>::kThreads, 1)
     volatile int* abort = reinterpret_cast<volatile int*>(tmem_slot + 1);
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int nkb = Kpad / TKB;
+    // FP64 form: the exponential's table in shared memory (lanes index it by their own j; the kernel
+    // parameter's constant bank would serialise distinct indices)
+    float* ffx_th = reinterpret_cast<float*>(smem + Lay::kOffStg);
+    float* ffx_tl = ffx_th + 32;
+    if (MODE == 1 && threadIdx.x < 32) {
+        ffx_th[threadIdx.x] = ffx.th[threadIdx.x];
+        ffx_tl[threadIdx.x] = ffx.tl[threadIdx.x];
+    }
 
     if (threadIdx.x == 0) {
         for (int i = 0; i < C::NSTAGE; ++i) {
@@ -402,6 +477,10 @@ __global__ void __launch_bounds__(KLLayout<MODE>::kThreads, 1)
         const int q4 = warp & 3;
         const int c = e >> 2;
         const uint32_t lane_base = (uint32_t)(q4 * 32) << 16;
+        // the output's offset from a 16-byte boundary, in elements (FP32 form)
+        const int mis = (int)((reinterpret_cast<uintptr_t>(out) / sizeof(Out)) & 3);
+        // FP32 form: rows of whole 128-byte lines (see the epilogue)
+        constexpr bool lines = MODE == 2;
         int tb = 0;
         uint32_t tphase = 0;
         for (int t = blockIdx.x; t < num_tiles; t += gridDim.x) {
@@ -410,29 +489,78 @@ __global__ void __launch_bounds__(KLLayout<MODE>::kThreads, 1)
             const int s0 = st_ * TN, v0 = nt_ * TM;
             const int v = v0 + q4 * 32 + lane;       // this lane's node
             const int sc0 = s0 + c * 32;             // the chunk's first sample
-            if (MODE == 0) {
-                if (!kl_warp_wait(tfull + tb, tphase, abort, err, timeout_ns)) break;
-                tc_fence_after();
-                const uint32_t base = tmem + lane_base + (uint32_t)(tb * C::NACC * TN + c * 32);
+            if constexpr (MODE != 1) {
+                // Output rows (one per sample) are `ldo` elements apart.  When ldo is a multiple of 32 and
+                // the output starts on a 128-byte boundary, every 32-node piece of a row is one full line:
+                // each warp stores its 32 nodes of every sample straight from registers.  Otherwise a row
+                // of the tile starts at any 4-byte offset and such a store would straddle two lines, so the
+                // four warps of chunk c (one per lane quarter) stage the chunk's 32 samples x 128 nodes in
+                // shared memory and each writes 8 whole rows of 128 nodes with 16-byte stores.
+                const bool ok = kl_warp_wait(tfull + tb, tphase, abort, err, timeout_ns);
                 uint32_t r0[32], r1[32];
-                tmem_ld_x32(base, r0);
-                tmem_ld_x32(base + (uint32_t)TN, r1);
-                tmem_wait_ld();
-                // this warp's values are in registers: its share of the buffer goes back to the MMA warp
-                tc_fence_before();
-                __syncwarp();
-                if (lane == 0) mbar_arrive(tempty + tb);
+                if (ok) {
+                    tc_fence_after();
+                    const uint32_t base = tmem + lane_base + (uint32_t)(tb * C::NACC * TN + c * 32);
+                    tmem_ld_x32(base, r0);
+                    tmem_ld_x32(base + (uint32_t)TN, r1);
+                    tmem_wait_ld();
+                    // this warp's values are in registers: its share of the buffer goes back to the MMA warp
+                    tc_fence_before();
+                    __syncwarp();
+                    if (lane == 0) mbar_arrive(tempty + tb);
+                }
                 if (++tb == 2) {
                     tb = 0;
                     tphase ^= 1u;
                 }
-                // the basis tables carry log2(e): the accumulators hold log2 a
-                if (v < V) {
+                if constexpr (lines) {
+                    if (!ok) break;
+                    if (v < V) {
+#pragma unroll
+                        for (int j = 0; j < 32; ++j) {
+                            const int sj = sc0 + j;
+                            // the basis tables carry log2(e): the accumulators hold log2 a
+                            const float l2 =
+                                __fmaf_rn(__uint_as_float(r1[j]), 1.0f / 2048.0f, __uint_as_float(r0[j]));
+                            if (sj < S) out[(size_t)sj * ldo + v] = (Out)ex2_approx(l2);
+                        }
+                    }
+                } else {
+                    // the chunk's warps agree to go on (a failed wait anywhere stops all four together); it also
+                    // orders their previous tile's reads of the staging rows before the writes below
+                    if (bar_or(1 + c, 128, !ok)) break;
+                    float* stg = reinterpret_cast<float*>(smem + Lay::kOffStg) + (size_t)c * 32 * kStgPitch;
+                    const int nv = min(TM, V - v0);   // nodes of this tile inside the grid
+                    // output index of (sample sc0, node v0) plus the output's offset, mod 4 (32-bit arithmetic
+                    // suffices for a residue mod 4); sample sc0 + j adds j ldo
+                    const uint32_t g4 = (uint32_t)sc0 * (uint32_t)ldo + (uint32_t)v0 + (uint32_t)mis;
+                    // staging row j holds sample sc0 + j, node v0 + k at slot k + sh_j with sh_j = (output index
+                    // + mis) mod 4, so that 16-byte-aligned output addresses meet 16-byte-aligned slots
 #pragma unroll
                     for (int j = 0; j < 32; ++j) {
-                        const int sj = sc0 + j;
+                        const int sh = (int)((g4 + (uint32_t)j * (uint32_t)ldo) & 3u);
                         const float l2 = __fmaf_rn(__uint_as_float(r1[j]), 1.0f / 2048.0f, __uint_as_float(r0[j]));
-                        if (sj < S) out[(size_t)sj * V + v] = (Out)ex2_approx(l2);
+                        stg[j * kStgPitch + sh + q4 * 32 + lane] = ex2_approx(l2);
+                    }
+                    bar_sync_n(1 + c, 128);
+                    // warp q4 writes staging rows 8 q4 .. 8 q4 + 7
+#pragma unroll 1
+                    for (int jj = 0; jj < 8; ++jj) {
+                        const int j = q4 * 8 + jj;
+                        const int s = sc0 + j;
+                        if (s >= S || nv <= 0) continue;
+                        const long long g0 = (long long)s * ldo + v0;
+                        const int sh = (int)((g0 + mis) & 3);
+                        const int h = min((4 - sh) & 3, nv);    // elements before the first aligned one
+                        const int nb = (nv - h) >> 2;           // aligned groups of four
+                        const int t0 = h + 4 * nb;              // first element of the tail
+                        const float* row = stg + j * kStgPitch + sh;
+                        Out* dst = out + g0;
+                        if (lane < h) dst[lane] = row[lane];
+                        if (lane < nb)
+                            *reinterpret_cast<float4*>(dst + h + 4 * lane) =
+                                *reinterpret_cast<const float4*>(row + h + 4 * lane);
+                        if (lane < nv - t0) dst[t0 + lane] = row[t0 + lane];
                     }
                 }
             } else {
@@ -484,11 +612,11 @@ __global__ void __launch_bounds__(KLLayout<MODE>::kThreads, 1)
                     ff_two_sum(ih, s1f[j], h, e2);
                     float lh, ll;
                     ff_fast_two_sum(h, __fadd_rn(e2, il), lh, ll);
-                    lh = ldexpf(lh, sc);
-                    ll = ldexpf(ll, sc);
+                    lh = scale2(lh, sc);
+                    ll = scale2(ll, sc);
                     float ah, al;
-                    ff_exp(lh, ll, ffx, ah, al);
-                    if (sj < S && v < V) out[(size_t)sj * V + v] = (double)ah + (double)al;
+                    ff_exp(lh, ll, ffx, ffx_th, ffx_tl, ah, al);
+                    if (sj < S && v < V) out[(size_t)sj * ldo + v] = ff_to_double(ah, al);
                 }
             }
         }
@@ -621,7 +749,7 @@ FFExp make_ffexp() {
 
 template <int MODE>
 cudaError_t kl_launch(mlmc_ctx* ctx, int S, int Spad, int Kpad, int nodes, int nodes_pad, const void* aops,
-                      const void* bops, const int* es, const int* ev, void* out, cudaStream_t st) {
+                      const void* bops, const int* es, const int* ev, void* out, long long ldo, cudaStream_t st) {
     using C = KLCfg<MODE>;
     using Lay = KLLayout<MODE>;
     // MMA operand A: the basis slices (128 node rows), B: the xi slices (TN sample rows)
@@ -649,7 +777,7 @@ cudaError_t kl_launch(mlmc_ctx* ctx, int S, int Spad, int Kpad, int nodes, int n
     }
     kl_tc_kernel<MODE><<<(unsigned)grid, Lay::kThreads, Lay::kSmem, st>>>(
         mapA, mapB, S, Spad, nodes, nodes_pad, Kpad, num_st, num_tiles, std::max(1, grid / 8), es, ev, ffx,
-        static_cast<typename C::Out*>(out), ctx->kl_err, (unsigned long long)(ctx->wait_timeout_s * 1e9),
+        static_cast<typename C::Out*>(out), ldo, ctx->kl_err, (unsigned long long)(ctx->wait_timeout_s * 1e9),
         16u * (unsigned)ctx->wait_extra);
     g_launches.fetch_add(1, std::memory_order_relaxed);
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
@@ -658,7 +786,7 @@ cudaError_t kl_launch(mlmc_ctx* ctx, int S, int Spad, int Kpad, int nodes, int n
         // written output, one read of both operands' slices (and the exponents)
         pend.bytes = (double)S * nodes * sizeof(typename C::Out) + (double)C::NA * Spad * Kpad * 2.0 +
                      (double)C::NB * nodes_pad * Kpad * 2.0 + (MODE == 1 ? 4.0 * (Spad + nodes_pad) : 0.0);
-        const int mmas = MODE == 0 ? 3 : 8;   // MMAs per 16-term step
+        const int mmas = MODE == 1 ? 8 : 3;   // MMAs per 16-term step
         pend.flops = 2.0 * mmas * Spad * (double)Kpad * nodes_pad;
         ctx->prof.kl_pending.push_back(pend);
     }
@@ -667,8 +795,10 @@ cudaError_t kl_launch(mlmc_ctx* ctx, int S, int Spad, int Kpad, int nodes, int n
 
 }  // namespace
 
-cudaError_t launch_kl_fp32(mlmc_ctx* ctx, const GridBasis& gb, int S, const double* xi, float* a, cudaStream_t st) {
+cudaError_t launch_kl_fp32(mlmc_ctx* ctx, const GridBasis& gb, int S, const double* xi, float* a, long long ld,
+                           cudaStream_t st) {
     if (S <= 0) return cudaSuccess;
+    if (reinterpret_cast<uintptr_t>(a) % sizeof(float) != 0) return cudaErrorMisalignedAddress;
     const int Spad = (S + TM - 1) / TM * TM;
     const int Kpad = gb.Kpad;
     cudaError_t e = ctx->ws.split.reserve((size_t)2 * Spad * Kpad * sizeof(__half));
@@ -678,10 +808,14 @@ cudaError_t launch_kl_fp32(mlmc_ctx* ctx, const GridBasis& gb, int S, const doub
     split_xi_kernel<<<(unsigned)((work + 255) / 256), 256, 0, st>>>(S, gb.K, Spad, Kpad, xi, a16);
     g_launches.fetch_add(1, std::memory_order_relaxed);
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
-    return kl_launch<0>(ctx, S, Spad, Kpad, gb.nodes, gb.nodes_pad, a16, gb.phi16.ptr, nullptr, nullptr, a, st);
+    // rows of whole 128-byte lines take the direct-store form
+    if (ld % 32 == 0 && reinterpret_cast<uintptr_t>(a) % 128 == 0)
+        return kl_launch<2>(ctx, S, Spad, Kpad, gb.nodes, gb.nodes_pad, a16, gb.phi16.ptr, nullptr, nullptr, a, ld, st);
+    return kl_launch<0>(ctx, S, Spad, Kpad, gb.nodes, gb.nodes_pad, a16, gb.phi16.ptr, nullptr, nullptr, a, ld, st);
 }
 
-cudaError_t launch_kl_tc64(mlmc_ctx* ctx, GridBasis& gb, int S, const double* xi, double* a, cudaStream_t st) {
+cudaError_t launch_kl_tc64(mlmc_ctx* ctx, GridBasis& gb, int S, const double* xi, double* a, long long ld,
+                           cudaStream_t st) {
     if (S <= 0) return cudaSuccess;
     cudaError_t e;
     if (!gb.phix.ptr) {
@@ -708,7 +842,7 @@ cudaError_t launch_kl_tc64(mlmc_ctx* ctx, GridBasis& gb, int S, const double* xi
     split_xi_exact_kernel<<<(unsigned)((threads + 255) / 256), 256, 0, st>>>(S, gb.K, Spad, Kpad, xi, a16, es);
     g_launches.fetch_add(1, std::memory_order_relaxed);
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
-    return kl_launch<1>(ctx, S, Spad, Kpad, gb.nodes, gb.nodes_pad, a16, gb.phix.ptr, es, gb.ev.as<int>(), a, st);
+    return kl_launch<1>(ctx, S, Spad, Kpad, gb.nodes, gb.nodes_pad, a16, gb.phix.ptr, es, gb.ev.as<int>(), a, ld, st);
 }
 
 }  // namespace mlmc

@@ -81,13 +81,13 @@ __global__ void __launch_bounds__(kThreads) level_stats_kernel(int S, const doub
 // Smallest and largest nodal coefficient of every sample (the contrast that bounds kappa(A): A is
 // the P1 operator with element means of a, so min(a) L <= A <= max(a) L for the Laplacian L).
 // One CTA per sample.
-__global__ void __launch_bounds__(kThreads) field_range_kernel(int V, const void* __restrict__ a, int a_fp64,
-                                                               double* __restrict__ out) {
+__global__ void __launch_bounds__(kThreads) field_range_kernel(int V, long long ld, const void* __restrict__ a,
+                                                               int a_fp64, double* __restrict__ out) {
     __shared__ double smin[kThreads], smax[kThreads];
     const int s = blockIdx.x, t = threadIdx.x;
     double lo = INFINITY, hi = -INFINITY;
     for (int v = t; v < V; v += kThreads) {
-        const size_t idx = (size_t)s * V + v;
+        const size_t idx = (size_t)s * ld + v;
         const double x = a_fp64 ? static_cast<const double*>(a)[idx] : (double)static_cast<const float*>(a)[idx];
         lo = fmin(lo, x);
         hi = fmax(hi, x);
@@ -110,9 +110,10 @@ __global__ void __launch_bounds__(kThreads) field_range_kernel(int V, const void
 
 }  // namespace
 
-cudaError_t launch_field_range(int S, int V, const void* a, int a_fp64, double* out_dev, cudaStream_t st) {
+cudaError_t launch_field_range(int S, int V, long long ld, const void* a, int a_fp64, double* out_dev,
+                               cudaStream_t st) {
     if (S <= 0) return cudaSuccess;
-    field_range_kernel<<<S, kThreads, 0, st>>>(V, a, a_fp64, out_dev);
+    field_range_kernel<<<S, kThreads, 0, st>>>(V, ld, a, a_fp64, out_dev);
     g_launches.fetch_add(1, std::memory_order_relaxed);
     return cudaGetLastError();
 }

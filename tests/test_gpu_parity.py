@@ -631,3 +631,38 @@ def test_two_asynchronous_solves_on_a_user_stream(M):
                 assert abs(Q[s].item() - Qo) <= tol * abs(Qo)
     finally:
         M.mlmc_destroy(h)
+
+
+@pytest.mark.parametrize("solver", ["CG", "CHOLESKY"])
+def test_level_solve_reads_padded_rows(M, solver):
+    # rows of the master coefficient a_ld apart (here padded to whole 128-byte lines, with garbage in the gap)
+    # give the same bits as the dense layout, for the fine grid and for a coarse view (a_n = 2 n)
+    S, n = 5, 32
+    af = smooth_lognormal_field(2 * n, S, seed=77, log_sd=1.0)
+    V2 = (2 * n + 1) ** 2
+    ld = (V2 + 31) // 32 * 32
+    padded = np.full((S, ld), 1e30)
+    padded[:, :V2] = af
+    sv = getattr(M, "MLMC_" + solver)
+    h = _ctx(M)
+    try:
+        outs = []
+        for a_np, a_ld in ((af, 0), (padded, ld)):
+            a = to_dev(a_np, torch.float64)
+            Q = torch.empty(S, dtype=torch.float64, device=device())
+            it = torch.zeros(S, dtype=torch.int32, device=device())
+            fl = torch.zeros(S, dtype=torch.int32, device=device())
+            M.mlmc_level_solve(h, n, S, a, M.MLMC_FP64, 2 * n, M.MLMC_FP32, sv, 1e-9, 100000, None, Q, it, None, fl,
+                               a_ld=a_ld)
+            M.mlmc_sync(h)
+            outs.append((Q.cpu().numpy(), it.cpu().numpy(), fl.cpu().numpy()))
+        assert np.array_equal(outs[0][0], outs[1][0]) and np.array_equal(outs[0][1], outs[1][1])
+        assert np.all(outs[0][2] == M.MLMC_F_CONVERGED) and np.array_equal(outs[0][2], outs[1][2])
+        for s in range(S):
+            Qo = o_fem.solve_sample(n, af[s].reshape(2 * n + 1, 2 * n + 1)[::2, ::2].ravel())[1]
+            assert abs(outs[1][0][s] - Qo) <= 1.5e-9 * abs(Qo) + 1e-15
+        with pytest.raises(M.MlmcError):
+            M.mlmc_level_solve(h, n, S, to_dev(af, torch.float64), M.MLMC_FP64, 2 * n, M.MLMC_FP32, sv, 1e-9, 100,
+                               None, torch.empty(S, dtype=torch.float64, device=device()), a_ld=V2 - 1)
+    finally:
+        M.mlmc_destroy(h)

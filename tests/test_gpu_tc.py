@@ -133,3 +133,35 @@ def test_fp64_tensor_core_field_extreme_coefficients(M):
         assert np.all(err <= _exact_lead_bound(xi_np, phi))
     finally:
         M.mlmc_destroy(h)
+
+
+@pytest.mark.parametrize("fprec", ["FP32", "FP64TC", "FP64"])
+@pytest.mark.parametrize("n0,S", [(8, 37), (16, 130)])
+def test_field_row_pitch_and_offset(M, fprec, n0, S):
+    # the same field into dense rows, into rows padded to whole 128-byte lines (the FP32 form's direct store
+    # path), into rows padded by 5 elements, and one element past a 128-byte boundary (the staged store path):
+    # identical bits everywhere, the gaps and the guard untouched
+    K = 64
+    p = getattr(M, "MLMC_" + fprec)
+    dt = torch.float32 if fprec == "FP32" else torch.float64
+    h = M.mlmc_create(M.make_problem(n0=n0, m=2, L_max=1, kind=0, K=K, sigma2=1.0, corr_len=0.3, seed=9), 0)
+    try:
+        n = 2 * n0
+        V = (n + 1) ** 2
+        xi = torch.empty((S, K), dtype=torch.float64, device=device())
+        dense = torch.empty((S, V), dtype=dt, device=device())
+        M.mlmc_sample_fields(h, 1, 0, S, xi, dense, p)
+        ref = dense.cpu().numpy()
+        for ld, off in (((V + 31) // 32 * 32, 0), (V + 5, 0), (V, 1), (V + 3, 3)):
+            buf = torch.full((off + S * ld + 256,), -7.0, dtype=dt, device=device())
+            view = buf[off:]
+            M.mlmc_synthesize_fields(h, 1, S, xi, view, p, a_ld=ld)
+            torch.cuda.synchronize()
+            got = buf.cpu().numpy()
+            rows = got[off: off + S * ld].reshape(S, ld)
+            assert np.array_equal(rows[:, :V], ref), (ld, off)
+            assert np.all(rows[:, V:] == -7.0) and np.all(got[:off] == -7.0) and np.all(got[off + S * ld:] == -7.0)
+        with pytest.raises(M.MlmcError):
+            M.mlmc_synthesize_fields(h, 1, S, xi, dense, p, a_ld=V - 1)
+    finally:
+        M.mlmc_destroy(h)
