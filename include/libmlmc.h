@@ -121,6 +121,10 @@ typedef struct {
  * *out is set to NULL on failure; the message is then in mlmc_last_error(NULL). */
 mlmc_status mlmc_create(const mlmc_problem* prob, int device, mlmc_ctx** out);
 void mlmc_destroy(mlmc_ctx* ctx);                 /* NULL is ignored */
+/* The Philox key of this context's samples (mlmc_problem.seed).  Nothing the
+ * context built depends on it (the KL basis, the workspaces), so estimates with
+ * new seeds reuse the context. */
+mlmc_status mlmc_set_seed(mlmc_ctx* ctx, uint64_t seed);
 const char* mlmc_last_error(const mlmc_ctx* ctx); /* never NULL; "" when no error */
 const char* mlmc_version(void);
 int64_t mlmc_launch_count(void);                  /* kernels launched by this library so far (process) */
@@ -135,7 +139,8 @@ int64_t mlmc_launch_count(void);                  /* kernels launched by this li
  * Wichura's AS241 inverse normal; sample indices are first .. first+S-1.
  * a[s][v] = exp(sum_k xi[s][k] Phi_k(x_v)) on the (n_l+1)^2 nodes of level l.
  *   xi    device FP64 [S][K], out (may be NULL when not wanted)
- *   a     device [S][(n_l+1)^2] dense nodal layout, out, by field_prec:
+ *   a     device, out: S rows of the (n_l+1)^2 nodal values, row s at a + s a_ld
+ *         elements, by field_prec:
  *         MLMC_FP64   FP64; contraction and exp on the FP64 pipe (plain FP64 form);
  *         MLMC_FP32   FP32; tensor-core contraction with split FP16 operands
  *                     (hi + 2^-11 lo) and FP32 accumulation, then expf: about
@@ -146,15 +151,23 @@ int64_t mlmc_launch_count(void);                  /* kernels launched by this li
  *                     (Tang's table-driven method): log a within about 1e-9
  *                     (a bound in terms of sum |xi_k| and sum |Phi_k| is given
  *                     in kl_tc.cu), the master coefficient of the mixed form.
+ *   a_ld  elements from one row of `a` to the next: 0 (dense, (n_l+1)^2) or at
+ *         least (n_l+1)^2; the gap is not written.  Rows of whole 128-byte lines
+ *         (a_ld a multiple of 32, `a` 128-byte aligned) let the tensor-core FP32
+ *         synthesis store full lines straight from its accumulators; other
+ *         pitches go through a shared-memory staging step (the estimate pads
+ *         its fields this way).
  * S = 0 is a no-op.  Errors: MLMC_E_ARG for level outside [0, L_max], S < 0,
- * null a with S > 0, field_prec not FP64/FP32/FP64TC. */
+ * null a with S > 0, a_ld nonzero and below (n_l+1)^2, field_prec not
+ * FP64/FP32/FP64TC. */
 mlmc_status mlmc_sample_fields(mlmc_ctx* ctx, int level, uint64_t first, int S,
-                               double* xi, void* a, mlmc_prec field_prec, void* stream);
+                               double* xi, void* a, int64_t a_ld, mlmc_prec field_prec, void* stream);
 
 /* A2 alone: the same field from caller-given coefficients xi (device FP64
- * [S][K]) on the grid of level `level`.  Used by the gradient path. */
+ * [S][K]) on the grid of level `level`, rows a_ld apart as above.  Used by the
+ * gradient path. */
 mlmc_status mlmc_synthesize_fields(mlmc_ctx* ctx, int level, int S, const double* xi,
-                                   void* a, mlmc_prec field_prec, void* stream);
+                                   void* a, int64_t a_ld, mlmc_prec field_prec, void* stream);
 
 /* ------------------------------------------------------------------------- */
 /* A3 + A4: the P1 stiffness operator applied matrix-free (Sec. 3.1; uniform
@@ -183,8 +196,10 @@ mlmc_status mlmc_apply_operator(int n, int S, const void* a, mlmc_prec a_prec, i
  * x += d in FP64.  All S solves run in one kernel launch.  Then Q_s = G(u_s) (Problem 4.5; the QoI of
  * the context's problem).
  *   n      cells per side of the solve grid, 2 <= n <= 2048
- *   a      device master coefficient [S][(a_n+1)^2], FP64 or FP32 (a_prec)
+ *   a      device master coefficient, S rows of (a_n+1)^2 nodes, FP64 or FP32 (a_prec)
  *   a_n    grid of `a`: n, or a multiple of n (coarse member of a level pair)
+ *   a_ld   elements from one row of `a` to the next: 0 (dense, (a_n+1)^2) or at
+ *          least (a_n+1)^2 (e.g. rows padded by mlmc_sample_fields)
  *   delta  target relative residual, > 0
  *   max_iters  inner-iteration budget per solve (summed over refinement steps)
  *   u      device FP64 [S][(n+1)^2] solution (dense nodal, zero boundary) or NULL
@@ -201,7 +216,7 @@ mlmc_status mlmc_apply_operator(int n, int S, const void* a, mlmc_prec a_prec, i
  * mlmc_estimate, mlmc_profile_get) as MLMC_E_TIMEOUT.  With profiling on
  * (mlmc_profile_enable) the call synchronises to read the launch's counters. */
 mlmc_status mlmc_level_solve(mlmc_ctx* ctx, int n, int S, const void* a, mlmc_prec a_prec, int a_n,
-                             mlmc_prec prec, mlmc_solver solver, double delta, int max_iters,
+                             int64_t a_ld, mlmc_prec prec, mlmc_solver solver, double delta, int max_iters,
                              double* u, double* Q, int32_t* iters, double* relres, int32_t* flags,
                              void* stream);
 
@@ -319,9 +334,21 @@ typedef struct {
                               Sec. 5.2.  0 (default): Table 1 (right), hhss on level 0, ssss on level 1,
                               ssdd above; 1: the quarter-precision setting, qhhh on level 0 and hhss
                               above.  The FP64 forms use dddd.                                        */
+    const struct mlmc_result_s* resume;   /* checkpoint: NULL (fresh start) or the result of an
+                              earlier adaptive estimate of the same problem and form (e.g. one stopped
+                              by max_rounds, or saved to disk and read back).  The estimate continues
+                              Alg. 4.1 from that state: its level accumulators, finest level and sample
+                              counts (new samples take the next indices, so an interrupted and resumed
+                              run draws exactly the samples of an uninterrupted one), its calibrated-
+                              rule state and its counters.  tol, max_rounds and the budgets may differ.
+                              Not with fixed_N.                                                       */
+    const char* log_path;  /* NULL, or a file to which the estimate appends one JSON object per Alg. 4.1
+                              round (one line each): round, L, samples and next targets per level,
+                              level means and variances, delta_l, the current RMSE estimate, the bias
+                              and sample-count tests, elapsed seconds                                   */
 } mlmc_options;
 
-typedef struct {
+typedef struct mlmc_result_s {
     double estimate;                 /* Q_hat = sum_l Y_hat_l (Eq. (4.1))                        */
     double rmse;                     /* sqrt(bias^2 + sum_l s_l^2 / N_l), bias = |Y_hat_L|/(m^alpha-1) */
     double var_est;                  /* sum_l s_l^2 / N_l                                          */
@@ -342,6 +369,8 @@ typedef struct {
                                                after their low-precision refinement stagnated or ran
                                                out of iterations (Cor. 3.4 conditions failed)     */
     double contrast[MLMC_MAX_LEVELS];       /* calibrated rule: measured contrast per level (else 0) */
+    double a_min[MLMC_MAX_LEVELS];          /* calibrated rule: smallest and largest nodal coefficient */
+    double a_max[MLMC_MAX_LEVELS];          /* seen per level (else 0); kept for a resumed estimate   */
 } mlmc_result;
 
 /* Fill *opts with the paper's defaults: kp 0.05, (2,1,4,2), alpha 2, gamma 2,
@@ -513,6 +542,14 @@ mlmc_status mlmc_debug_set_wait_extra(mlmc_ctx* ctx, int extra);
  * way, so results are bit-identical; exists to measure the pipeline and to test
  * that identity. */
 mlmc_status mlmc_debug_set_solve_ring(mlmc_ctx* ctx, int ring);
+
+/* Diagnostics: forced allocation failure (process-wide).  With after >= 0 the
+ * library's (after+1)-th next device allocation fails as if the device were out
+ * of memory, once; after = -1 disarms.  The failing call returns MLMC_E_NOMEM
+ * with the allocation named in mlmc_last_error, the context stays usable, and
+ * the next call allocates afresh.  The allocation-free entry point never
+ * allocates and is unaffected. */
+mlmc_status mlmc_debug_fail_allocation(int64_t after);
 
 /* Diagnostics.  Group size of this context's solves: a system of n cells has
  * (n - 1) ((n - 1)/4 + 1) four-node chunks; up to 512 chunks it is solved by

@@ -51,7 +51,8 @@ class mlmc_options(ctypes.Structure):
                 ("alpha", c_double), ("gamma", c_double), ("r", c_double), ("form", c_int),
                 ("fixed_delta", c_double), ("force_prec", c_int), ("solver", c_int), ("max_iters", c_int),
                 ("max_rounds", c_int), ("fixed_N", POINTER(c_int64)), ("contrast", c_double),
-                ("mixed_field", c_int), ("prec_rule", c_int), ("chol_table", c_int)]
+                ("mixed_field", c_int), ("prec_rule", c_int), ("chol_table", c_int), ("resume", c_void_p),
+                ("log_path", c_char_p)]
 
 
 class mlmc_result(ctypes.Structure):
@@ -61,7 +62,8 @@ class mlmc_result(ctypes.Structure):
                 ("s2", c_double * MLMC_MAX_LEVELS), ("delta", c_double * MLMC_MAX_LEVELS),
                 ("prec", c_int32 * MLMC_MAX_LEVELS), ("inner_iters", c_int64 * MLMC_MAX_LEVELS),
                 ("dofs", c_int64 * MLMC_MAX_LEVELS), ("acc", mlmc_acc * MLMC_MAX_LEVELS), ("seconds", c_double),
-                ("fp64_retries", c_int64 * MLMC_MAX_LEVELS), ("contrast", c_double * MLMC_MAX_LEVELS)]
+                ("fp64_retries", c_int64 * MLMC_MAX_LEVELS), ("contrast", c_double * MLMC_MAX_LEVELS),
+                ("a_min", c_double * MLMC_MAX_LEVELS), ("a_max", c_double * MLMC_MAX_LEVELS)]
 
 
 class mlmc_profile(ctypes.Structure):
@@ -87,11 +89,11 @@ _SIGS = {
     "mlmc_last_error": (c_char_p, [c_void_p]),
     "mlmc_version": (c_char_p, []),
     "mlmc_launch_count": (c_int64, []),
-    "mlmc_sample_fields": (c_int, [c_void_p, c_int, c_uint64, c_int, c_void_p, c_void_p, c_int, c_void_p]),
-    "mlmc_synthesize_fields": (c_int, [c_void_p, c_int, c_int, c_void_p, c_void_p, c_int, c_void_p]),
+    "mlmc_sample_fields": (c_int, [c_void_p, c_int, c_uint64, c_int, c_void_p, c_void_p, c_int64, c_int, c_void_p]),
+    "mlmc_synthesize_fields": (c_int, [c_void_p, c_int, c_int, c_void_p, c_void_p, c_int64, c_int, c_void_p]),
     "mlmc_apply_operator": (c_int, [c_int, c_int, c_void_p, c_int, c_int, c_int, c_void_p, c_void_p, c_int,
                                     c_void_p]),
-    "mlmc_level_solve": (c_int, [c_void_p, c_int, c_int, c_void_p, c_int, c_int, c_int, c_int, c_double, c_int,
+    "mlmc_level_solve": (c_int, [c_void_p, c_int, c_int, c_void_p, c_int, c_int, c_int64, c_int, c_int, c_double, c_int,
                                  c_void_p, c_void_p, c_void_p, c_void_p, c_void_p, c_void_p]),
     "mlmc_sync": (c_int, [c_void_p, c_void_p]),
     "mlmc_level_solve_noalloc": (c_int, [c_int, c_int, c_int, c_void_p, c_int, c_int, c_int, c_double, c_int,
@@ -114,6 +116,8 @@ _SIGS = {
     "mlmc_autotune_entry": (c_int, [c_void_p, c_int, c_void_p]),
     "mlmc_debug_set_wait_extra": (c_int, [c_void_p, c_int]),
     "mlmc_debug_set_solve_ring": (c_int, [c_void_p, c_int]),
+    "mlmc_debug_fail_allocation": (c_int, [c_int64]),
+    "mlmc_set_seed": (c_int, [c_void_p, c_uint64]),
     "mlmc_debug_set_medium_items": (c_int, [c_void_p, c_int]),
     "mlmc_set_precond": (c_int, [c_void_p, c_int, c_int, c_int, c_double]),
     "mlmc_set_inner_tolerance": (c_int, [c_void_p, c_double, c_double]),
@@ -194,6 +198,10 @@ def mlmc_destroy(ctx):
     lib().mlmc_destroy(ctx)
 
 
+def mlmc_set_seed(ctx, seed):
+    _check(lib().mlmc_set_seed(ctx, seed), ctx)
+
+
 def mlmc_last_error(ctx=None):
     msg = lib().mlmc_last_error(ctx)
     return msg.decode() if msg else ""
@@ -261,16 +269,49 @@ def mlmc_debug_set_solve_ring(ctx, ring):
     _check(lib().mlmc_debug_set_solve_ring(ctx, ring), ctx)
 
 
+def mlmc_debug_fail_allocation(after):
+    """Make the (after+1)-th next device allocation of the library fail once (-1 disarms)."""
+    _check(lib().mlmc_debug_fail_allocation(after))
+
+
+def set_resume(opts, res):
+    """Continue an estimate from the checkpoint `res` (an mlmc_result; None clears)."""
+    opts._resume_ref = res
+    opts.resume = ctypes.addressof(res) if res is not None else None
+
+
+def set_log_path(opts, path):
+    """Append one JSON line per Alg. 4.1 round to `path` (None turns logging off)."""
+    opts._log_ref = path.encode() if path is not None else None
+    opts.log_path = opts._log_ref
+
+
+def save_result(res, path):
+    """Write an mlmc_result (a checkpoint for mlmc_options.resume) to a file, as its raw bytes."""
+    with open(path, "wb") as f:
+        f.write(bytes(res))
+
+
+def load_result(path):
+    """Read a checkpoint written by save_result."""
+    with open(path, "rb") as f:
+        data = f.read()
+    if len(data) != ctypes.sizeof(mlmc_result):
+        raise ValueError("not an mlmc_result of this library version: %d bytes" % len(data))
+    return mlmc_result.from_buffer_copy(data)
+
+
 def mlmc_debug_set_medium_items(ctx, items):
     _check(lib().mlmc_debug_set_medium_items(ctx, items), ctx)
 
 
-def mlmc_sample_fields(ctx, level, first, S, xi, a, field_prec, stream=None):
-    _check(lib().mlmc_sample_fields(ctx, level, first, S, _ptr(xi), _ptr(a), field_prec, _stream(stream)), ctx)
+def mlmc_sample_fields(ctx, level, first, S, xi, a, field_prec, stream=None, a_ld=0):
+    _check(lib().mlmc_sample_fields(ctx, level, first, S, _ptr(xi), _ptr(a), a_ld, field_prec, _stream(stream)),
+           ctx)
 
 
-def mlmc_synthesize_fields(ctx, level, S, xi, a, field_prec, stream=None):
-    _check(lib().mlmc_synthesize_fields(ctx, level, S, _ptr(xi), _ptr(a), field_prec, _stream(stream)), ctx)
+def mlmc_synthesize_fields(ctx, level, S, xi, a, field_prec, stream=None, a_ld=0):
+    _check(lib().mlmc_synthesize_fields(ctx, level, S, _ptr(xi), _ptr(a), a_ld, field_prec, _stream(stream)), ctx)
 
 
 def mlmc_apply_operator(n, S, a, a_prec, a_n, op_prec, x, y, vec_prec, stream=None):
@@ -279,8 +320,8 @@ def mlmc_apply_operator(n, S, a, a_prec, a_n, op_prec, x, y, vec_prec, stream=No
 
 
 def mlmc_level_solve(ctx, n, S, a, a_prec, a_n, prec, solver, delta, max_iters, u, Q, iters=None, relres=None,
-                     flags=None, stream=None):
-    _check(lib().mlmc_level_solve(ctx, n, S, _ptr(a), a_prec, a_n, prec, solver, delta, max_iters, _ptr(u),
+                     flags=None, stream=None, a_ld=0):
+    _check(lib().mlmc_level_solve(ctx, n, S, _ptr(a), a_prec, a_n, a_ld, prec, solver, delta, max_iters, _ptr(u),
                                   _ptr(Q), _ptr(iters), _ptr(relres), _ptr(flags), _stream(stream)), ctx)
 
 

@@ -2,26 +2,50 @@
 // of Alg. 4.1 and the round scheduler that puts every sample of every level
 // of a round into one resident-solve launch per precision class.
 #include <cuda_runtime.h>
+#include <nvtx3/nvToolsExt.h>
 
 #include <algorithm>
 #include <chrono>
 #include <cmath>
+#include <cstdio>
 #include <cstring>
 #include <functional>
 #include <map>
 #include <new>
 #include <string>
+#include <type_traits>
 #include <vector>
 
 #include "internal.h"
 
 namespace mlmc {
 
+// An NVTX range for the scope (shows the estimate's rounds, field syntheses and solve launches on a
+// profiler's timeline; no cost without a tool attached).
+struct NvtxRange {
+    explicit NvtxRange(const char* name) { nvtxRangePushA(name); }
+    ~NvtxRange() { nvtxRangePop(); }
+    NvtxRange(const NvtxRange&) = delete;
+    NvtxRange& operator=(const NvtxRange&) = delete;
+};
+
 std::atomic<int64_t> g_launches{0};
 
 std::string& create_error() {
     static thread_local std::string s;
     return s;
+}
+
+// Forced allocation failure (mlmc_debug_fail_allocation): allocations left before the one that fails,
+// -1 when disarmed.
+static std::atomic<int64_t> g_fail_alloc{-1};
+
+static bool forced_alloc_failure() {
+    int64_t v = g_fail_alloc.load();
+    while (v >= 0) {
+        if (g_fail_alloc.compare_exchange_weak(v, v - 1)) return v == 0;   // 0 -> -1: this one fails
+    }
+    return false;
 }
 
 cudaError_t DevBuf::reserve(size_t want) {
@@ -32,6 +56,7 @@ cudaError_t DevBuf::reserve(size_t want) {
         if (e != cudaSuccess) return e;
     }
     release();
+    if (forced_alloc_failure()) return cudaErrorMemoryAllocation;
     const size_t grow = std::max(want, bytes + bytes / 4);
     cudaError_t e = cudaMalloc(&ptr, grow);
     if (e != cudaSuccess) {
@@ -183,13 +208,14 @@ mlmc_status check_problem(const mlmc_problem* p, std::string& err) {
 }
 
 // Field of S samples on level l from xi (device) into a (device), in field precision.
-mlmc_status synth(mlmc_ctx* ctx, int level, int S, const double* xi, void* a, mlmc_prec field_prec,
+mlmc_status synth(mlmc_ctx* ctx, int level, int S, const double* xi, void* a, long long ld, mlmc_prec field_prec,
                   cudaStream_t st) {
     const int n = level_n(ctx->prob, level);
     GridBasis& gb = ctx->basis.at(n);
-    cudaError_t e = (field_prec == MLMC_FP64)     ? launch_kl_fp64(gb, S, xi, static_cast<double*>(a), st)
-                    : (field_prec == MLMC_FP64TC) ? launch_kl_tc64(ctx, gb, S, xi, static_cast<double*>(a), st)
-                                                  : launch_kl_fp32(ctx, gb, S, xi, static_cast<float*>(a), st);
+    if (ld == 0) ld = (long long)(n + 1) * (n + 1);
+    cudaError_t e = (field_prec == MLMC_FP64)     ? launch_kl_fp64(gb, S, xi, static_cast<double*>(a), ld, st)
+                    : (field_prec == MLMC_FP64TC) ? launch_kl_tc64(ctx, gb, S, xi, static_cast<double*>(a), ld, st)
+                                                  : launch_kl_fp32(ctx, gb, S, xi, static_cast<float*>(a), ld, st);
     if (e != cudaSuccess) return fail(ctx, MLMC_E_CUDA, std::string("KL synthesis: ") + cudaGetErrorString(e));
     return MLMC_OK;
 }
@@ -224,8 +250,51 @@ using RoundFn = std::function<mlmc_status(const std::vector<Request>&, const std
                                           const std::vector<double>& delta_coarse, std::vector<mlmc_acc>& out,
                                           mlmc_result* res)>;
 
-mlmc_status alg41(int m, int L_max, int n0, const mlmc_options& o, const RoundFn& round, mlmc_result* res) {
+// One JSON array of the first n values.
+template <class T>
+void json_array(FILE* f, const T* v, int n) {
+    std::fputc('[', f);
+    for (int i = 0; i < n; ++i) {
+        if (i) std::fputc(',', f);
+        if (std::is_integral<T>::value) std::fprintf(f, "%lld", (long long)v[i]);
+        else std::fprintf(f, "%.17g", (double)v[i]);
+    }
+    std::fputc(']', f);
+}
+
+// Sample targets for the next round from the level accumulators (the optimal N_l of Alg. 4.1 with the
+// variance budget TOL^2 / 2), never below the samples done; a level without samples starts at N_init.
+// Returns whether every level already has its target.
+bool next_targets(int m, const mlmc_options& o, const std::vector<mlmc_acc>& acc, std::vector<int64_t>& N) {
+    const int L = (int)acc.size() - 1;
+    std::vector<double> V(L + 1), C(L + 1);
+    double sum_vc = 0.0;
+    for (int l = 0; l <= L; ++l) {
+        V[l] = acc[l].n > 0 ? acc[l].m2 / (double)acc[l].n : 0.0;
+        C[l] = std::pow((double)m, o.gamma * l);
+        sum_vc += std::sqrt(V[l] * C[l]);
+    }
+    N.assign(L + 1, 0);
+    bool enough = true;
+    for (int l = 0; l <= L; ++l) {
+        if (acc[l].n == 0) {
+            N[l] = o.N_init;
+            enough = false;
+            continue;
+        }
+        const int64_t Nopt = (int64_t)std::ceil(std::sqrt(V[l] / C[l]) * (2.0 / (o.tol * o.tol)) * sum_vc);
+        N[l] = std::max<int64_t>(Nopt, acc[l].n);
+        if (acc[l].n < Nopt) enough = false;
+    }
+    return enough;
+}
+
+mlmc_status alg41(int m, int L_max, int n0, const mlmc_options& o, const RoundFn& round, mlmc_result* res,
+                  std::string& err) {
     const auto t0 = std::chrono::steady_clock::now();
+    const mlmc_result* prev = o.resume;
+    mlmc_result keep;
+    if (prev) keep = *prev;   // res may be the checkpoint itself
     std::memset(res, 0, sizeof(*res));
     const bool fixed = o.fixed_N != nullptr;
     int L = std::min(std::max(o.L_start, 0), L_max);
@@ -234,10 +303,70 @@ mlmc_status alg41(int m, int L_max, int n0, const mlmc_options& o, const RoundFn
         for (int l = 0; l <= L; ++l) N[l] = o.fixed_N[l];
     std::vector<mlmc_acc> acc(L + 1);
     std::memset(acc.data(), 0, sizeof(mlmc_acc) * acc.size());
-    int rounds = 0;
+    int rounds = 0, rounds_before = 0;
+    double seconds_before = 0.0;
+    if (prev) {
+        // checkpoint: the finest level, the level accumulators and the targets they imply
+        if (fixed) {
+            err = "resume: not with fixed_N";
+            return MLMC_E_ARG;
+        }
+        if (keep.L < 0 || keep.L > L_max || keep.rounds < 0) {
+            err = "resume: the checkpoint's finest level or round count is outside this problem";
+            return MLMC_E_ARG;
+        }
+        L = keep.L;
+        acc.assign(keep.acc, keep.acc + L + 1);
+        for (int l = 0; l <= L; ++l)
+            if (acc[l].n < 0) {
+                err = "resume: negative sample count in the checkpoint";
+                return MLMC_E_ARG;
+            }
+        next_targets(m, o, acc, N);
+        rounds_before = keep.rounds;
+        seconds_before = keep.seconds;
+    }
     bool bias_failed = false;
     const double thr = (o.r * std::pow((double)m, o.alpha) - 1.0) * o.tol / std::sqrt(2.0);
     std::vector<double> delta;
+    FILE* logf = nullptr;
+    if (o.log_path) {
+        logf = std::fopen(o.log_path, "a");
+        if (!logf) {
+            err = std::string("log_path: cannot open ") + o.log_path;
+            return MLMC_E_ARG;
+        }
+    }
+    // one line per round: the state after it and the decisions taken from it
+    auto log_round = [&](bool enough, bool bias_ok) {
+        if (!logf) return;
+        const int Ll = (int)acc.size() - 1;
+        std::vector<int64_t> n(Ll + 1);
+        std::vector<double> y(Ll + 1), v(Ll + 1);
+        double var = 0.0;
+        for (int l = 0; l <= Ll; ++l) {
+            n[l] = acc[l].n;
+            y[l] = acc[l].mean;
+            v[l] = acc[l].n > 0 ? acc[l].m2 / (double)acc[l].n : 0.0;
+            if (acc[l].n > 0) var += v[l] / (double)acc[l].n;
+        }
+        const double bias = std::fabs(acc[Ll].mean) / (std::pow((double)m, o.alpha) - 1.0);
+        std::fprintf(logf, "{\"round\":%d,\"L\":%d,\"N\":", rounds_before + rounds, Ll);
+        json_array(logf, n.data(), Ll + 1);
+        std::fprintf(logf, ",\"N_next\":");
+        json_array(logf, N.data(), (int)N.size());
+        std::fprintf(logf, ",\"Yhat\":");
+        json_array(logf, y.data(), Ll + 1);
+        std::fprintf(logf, ",\"s2\":");
+        json_array(logf, v.data(), Ll + 1);
+        std::fprintf(logf, ",\"delta\":");
+        json_array(logf, delta.data(), (int)delta.size());
+        std::fprintf(logf, ",\"rmse\":%.17g,\"bias_ok\":%s,\"enough\":%s,\"seconds\":%.6f}\n",
+                     std::sqrt(bias * bias + var), bias_ok ? "true" : "false", enough ? "true" : "false",
+                     seconds_before + std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count());
+        std::fflush(logf);
+    };
+    mlmc_status status = MLMC_OK;
     while (rounds < std::max(1, o.max_rounds)) {
         ++rounds;
         std::vector<double> h(L + 1);
@@ -256,26 +385,17 @@ mlmc_status alg41(int m, int L_max, int n0, const mlmc_options& o, const RoundFn
         if (!req.empty()) {
             std::vector<mlmc_acc> got(req.size());
             std::memset(got.data(), 0, sizeof(mlmc_acc) * got.size());
-            const mlmc_status st = round(req, delta, dcoarse, got, res);
-            if (st != MLMC_OK) return st;
+            status = round(req, delta, dcoarse, got, res);
+            if (status != MLMC_OK) break;
             for (size_t i = 0; i < req.size(); ++i) acc_merge(&acc[req[i].level], got[i]);
         }
-        if (fixed) break;
-        std::vector<double> V(L + 1), C(L + 1);
-        double sum_vc = 0.0;
-        for (int l = 0; l <= L; ++l) {
-            V[l] = acc[l].n > 0 ? acc[l].m2 / (double)acc[l].n : 0.0;
-            C[l] = std::pow((double)m, o.gamma * l);
-            sum_vc += std::sqrt(V[l] * C[l]);
+        if (fixed) {
+            log_round(true, true);
+            break;
         }
-        std::vector<int64_t> Nopt(L + 1);
-        bool enough = true;
-        for (int l = 0; l <= L; ++l) {
-            Nopt[l] = (int64_t)std::ceil(std::sqrt(V[l] / C[l]) * (2.0 / (o.tol * o.tol)) * sum_vc);
-            N[l] = std::max<int64_t>(Nopt[l], acc[l].n);
-            if (acc[l].n < Nopt[l]) enough = false;
-        }
+        const bool enough = next_targets(m, o, acc, N);
         bias_failed = std::fabs(acc[L].mean) > thr;
+        log_round(enough, !bias_failed);
         if (bias_failed && L < L_max) {
             ++L;
             N.push_back(o.N_init);
@@ -286,8 +406,10 @@ mlmc_status alg41(int m, int L_max, int n0, const mlmc_options& o, const RoundFn
         }
         if (enough) break;
     }
+    if (logf) std::fclose(logf);
+    if (status != MLMC_OK) return status;
     res->L = L;
-    res->rounds = rounds;
+    res->rounds = rounds_before + rounds;
     res->bias_failed = bias_failed ? 1 : 0;
     double est = 0.0, var = 0.0;
     for (int l = 0; l <= L; ++l) {
@@ -303,7 +425,7 @@ mlmc_status alg41(int m, int L_max, int n0, const mlmc_options& o, const RoundFn
     res->estimate = est;
     res->var_est = var;
     res->rmse = std::sqrt(bias * bias + var);
-    res->seconds = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+    res->seconds = seconds_before + std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
     return MLMC_OK;
 }
 
@@ -392,6 +514,12 @@ mlmc_status mlmc_create(const mlmc_problem* prob, int device, mlmc_ctx** out) {
         }
     }
     *out = ctx;
+    return MLMC_OK;
+}
+
+mlmc_status mlmc_set_seed(mlmc_ctx* ctx, uint64_t seed) {
+    if (!ctx) return MLMC_E_ARG;
+    ctx->prob.seed = seed;
     return MLMC_OK;
 }
 
@@ -566,17 +694,30 @@ mlmc_status mlmc_debug_set_medium_items(mlmc_ctx* ctx, int items) {
     return MLMC_OK;
 }
 
+mlmc_status mlmc_debug_fail_allocation(int64_t after) {
+    if (after < -1) return MLMC_E_ARG;
+    g_fail_alloc.store(after);
+    return MLMC_OK;
+}
+
 mlmc_status mlmc_debug_set_solve_ring(mlmc_ctx* ctx, int ring) {
     if (!ctx || ring < -1 || ring == 1 || ring > 4) return MLMC_E_ARG;
     ctx->solve_ring = ring;
     return MLMC_OK;
 }
 
+// Pitch argument of the field calls: 0 (dense) or at least the level's (n+1)^2 nodes.
+bool good_pitch(const mlmc_ctx* ctx, int level, int64_t ld) {
+    const int n = level_n(ctx->prob, level);
+    return ld == 0 || ld >= (int64_t)(n + 1) * (n + 1);
+}
+
 mlmc_status mlmc_sample_fields(mlmc_ctx* ctx, int level, uint64_t first, int S, double* xi, void* a,
-                               mlmc_prec field_prec, void* stream) {
+                               int64_t a_ld, mlmc_prec field_prec, void* stream) {
     if (!ctx) return MLMC_E_ARG;
-    if (level < 0 || level > ctx->prob.L_max || S < 0 || (S > 0 && !a) || !is_field_prec(field_prec))
-        return fail(ctx, MLMC_E_ARG, "sample_fields: bad level, S, output or field precision");
+    if (level < 0 || level > ctx->prob.L_max || S < 0 || (S > 0 && !a) || !is_field_prec(field_prec) ||
+        !good_pitch(ctx, level, a_ld))
+        return fail(ctx, MLMC_E_ARG, "sample_fields: bad level, S, output, pitch or field precision");
     if (S == 0) return MLMC_OK;
     cudaSetDevice(ctx->device);
     cudaStream_t st = static_cast<cudaStream_t>(stream);
@@ -587,22 +728,23 @@ mlmc_status mlmc_sample_fields(mlmc_ctx* ctx, int level, uint64_t first, int S, 
     }
     MLMC_CUDA_RET(ctx->err, ctx_order_begin(ctx, st));
     MLMC_CUDA_RET(ctx->err, launch_philox_normals(ctx->prob.seed, level, first, S, ctx->prob.field.K, xbuf, st));
-    const mlmc_status s = synth(ctx, level, S, xbuf, a, field_prec, st);
+    const mlmc_status s = synth(ctx, level, S, xbuf, a, a_ld, field_prec, st);
     if (s != MLMC_OK) return s;
     MLMC_CUDA_RET(ctx->err, ctx_order_end(ctx, st));
     return MLMC_OK;
 }
 
-mlmc_status mlmc_synthesize_fields(mlmc_ctx* ctx, int level, int S, const double* xi, void* a,
+mlmc_status mlmc_synthesize_fields(mlmc_ctx* ctx, int level, int S, const double* xi, void* a, int64_t a_ld,
                                    mlmc_prec field_prec, void* stream) {
     if (!ctx) return MLMC_E_ARG;
-    if (level < 0 || level > ctx->prob.L_max || S < 0 || (S > 0 && (!a || !xi)) || !is_field_prec(field_prec))
-        return fail(ctx, MLMC_E_ARG, "synthesize_fields: bad level, S, pointers or field precision");
+    if (level < 0 || level > ctx->prob.L_max || S < 0 || (S > 0 && (!a || !xi)) || !is_field_prec(field_prec) ||
+        !good_pitch(ctx, level, a_ld))
+        return fail(ctx, MLMC_E_ARG, "synthesize_fields: bad level, S, pointers, pitch or field precision");
     if (S == 0) return MLMC_OK;
     cudaSetDevice(ctx->device);
     cudaStream_t st = static_cast<cudaStream_t>(stream);
     MLMC_CUDA_RET(ctx->err, ctx_order_begin(ctx, st));
-    const mlmc_status s = synth(ctx, level, S, xi, a, field_prec, st);
+    const mlmc_status s = synth(ctx, level, S, xi, a, a_ld, field_prec, st);
     if (s != MLMC_OK) return s;
     MLMC_CUDA_RET(ctx->err, ctx_order_end(ctx, st));
     return MLMC_OK;
@@ -621,14 +763,15 @@ mlmc_status mlmc_apply_operator(int n, int S, const void* a, mlmc_prec a_prec, i
     return e == cudaSuccess ? MLMC_OK : MLMC_E_CUDA;
 }
 
-mlmc_status mlmc_level_solve(mlmc_ctx* ctx, int n, int S, const void* a, mlmc_prec a_prec, int a_n,
+mlmc_status mlmc_level_solve(mlmc_ctx* ctx, int n, int S, const void* a, mlmc_prec a_prec, int a_n, int64_t a_ld,
                              mlmc_prec prec, mlmc_solver solver, double delta, int max_iters, double* u,
                              double* Q, int32_t* iters, double* relres, int32_t* flags, void* stream) {
     if (!ctx) return MLMC_E_ARG;
     if (n < 2 || n > 2048 || S < 0 || a_n < n || a_n % n != 0 || !is_master_prec(a_prec) ||
+        (a_ld != 0 && a_ld < (int64_t)(a_n + 1) * (a_n + 1)) ||
         !(is_prec(prec) || (solver == MLMC_CHOLESKY && prec == MLMC_FP8S)) ||
         (solver != MLMC_CG && solver != MLMC_MINRES && solver != MLMC_CHOLESKY) || !(delta > 0) || max_iters < 1)
-        return fail(ctx, MLMC_E_ARG, "level_solve: bad n, S, a_n, precision, solver, delta or max_iters");
+        return fail(ctx, MLMC_E_ARG, "level_solve: bad n, S, a_n, a_ld, precision, solver, delta or max_iters");
     if (S == 0) return MLMC_OK;
     if (!a || !Q) return fail(ctx, MLMC_E_ARG, "level_solve: null a or Q");
     cudaSetDevice(ctx->device);
@@ -638,6 +781,7 @@ mlmc_status mlmc_level_solve(mlmc_ctx* ctx, int n, int S, const void* a, mlmc_pr
     g.a = a;
     g.a_fp64 = (a_prec == MLMC_FP64);
     g.a_n = a_n;
+    g.a_ld = a_ld;
     g.delta = delta;
     g.Q = Q;
     g.u = u;
@@ -741,7 +885,7 @@ mlmc_status mlmc_estimate_host(int m, int L_max, int n0, const mlmc_options* opt
         }
         return MLMC_OK;
     };
-    return alg41(m, L_max, n0, *opts, round, res);
+    return alg41(m, L_max, n0, *opts, round, res, err);
 }
 
 mlmc_status mlmc_estimate(mlmc_ctx* ctx, const mlmc_options* opts, mlmc_result* res) {
@@ -769,6 +913,7 @@ mlmc_status mlmc_estimate(mlmc_ctx* ctx, const mlmc_options* opts, mlmc_result* 
 
     RoundFn round = [&](const std::vector<Request>& req, const std::vector<double>& df, const std::vector<double>& dc,
                         std::vector<mlmc_acc>& out, mlmc_result*) -> mlmc_status {
+        const NvtxRange range_round("mlmc round");
         // ---- memory plan of the round
         const int L = (int)df.size() - 1;
         std::vector<double> h(L + 1);
@@ -806,10 +951,14 @@ mlmc_status mlmc_estimate(mlmc_ctx* ctx, const mlmc_options* opts, mlmc_result* 
         };
         size_t fbytes = 0, xbytes = 0, qn = 0;
         std::vector<size_t> foff(req.size()), xoff(req.size()), qoff(req.size());
+        // each field row padded to whole 128-byte lines (32 elements), so that the synthesis writes full lines
+        auto fpitch = [&](int l) -> long long {
+            const int n = level_n(p, l);
+            return ((long long)(n + 1) * (n + 1) + 31) / 32 * 32;
+        };
         for (size_t i = 0; i < req.size(); ++i) {
-            const int n = level_n(p, req[i].level);
             foff[i] = fbytes;
-            fbytes += (size_t)req[i].count * (n + 1) * (n + 1) * felem;
+            fbytes += (size_t)req[i].count * (size_t)fpitch(req[i].level) * felem;
             fbytes = (fbytes + 255) / 256 * 256;
             xoff[i] = xbytes;
             xbytes += (size_t)req[i].count * K * sizeof(double);
@@ -836,9 +985,10 @@ mlmc_status mlmc_estimate(mlmc_ctx* ctx, const mlmc_options* opts, mlmc_result* 
         MLMC_CUDA_RET(ctx->err, cudaMemsetAsync(flc, 0, qn * sizeof(int32_t), st));
         // ---- fields of every request
         for (size_t i = 0; i < req.size(); ++i) {
+            const NvtxRange range_fields("fields");
             const mlmc_status s = mlmc_sample_fields(ctx, req[i].level, (uint64_t)req[i].first, req[i].count,
-                                                     xb + xoff[i] / sizeof(double), fb + foff[i], field_prec,
-                                                     (void*)st);
+                                                     xb + xoff[i] / sizeof(double), fb + foff[i],
+                                                     fpitch(req[i].level), field_prec, (void*)st);
             if (s != MLMC_OK) return s;
         }
         // ---- calibrated rule: the contrast of every new field, per level
@@ -846,7 +996,7 @@ mlmc_status mlmc_estimate(mlmc_ctx* ctx, const mlmc_options* opts, mlmc_result* 
             double* rng = ctx->ws.misc.as<double>();
             for (size_t i = 0; i < req.size(); ++i) {
                 const int n = level_n(p, req[i].level);
-                MLMC_CUDA_RET(ctx->err, launch_field_range(req[i].count, (n + 1) * (n + 1), fb + foff[i],
+                MLMC_CUDA_RET(ctx->err, launch_field_range(req[i].count, (n + 1) * (n + 1), fpitch(req[i].level), fb + foff[i],
                                                            field_prec != MLMC_FP32, rng + 2 * qoff[i], st));
             }
             std::vector<double> hr(2 * qn);
@@ -875,6 +1025,7 @@ mlmc_status mlmc_estimate(mlmc_ctx* ctx, const mlmc_options* opts, mlmc_result* 
             gf.a = fb + foff[i];
             gf.a_fp64 = field_prec != MLMC_FP32;
             gf.a_n = n;
+            gf.a_ld = fpitch(l);
             gf.delta = df[l];
             gf.Q = Qf + qoff[i];
             gf.iters = itf + qoff[i];
@@ -910,6 +1061,7 @@ mlmc_status mlmc_estimate(mlmc_ctx* ctx, const mlmc_options* opts, mlmc_result* 
             batches.push_back(std::move(b));
         }
         {
+            const NvtxRange range_solves("solves");
             const mlmc_status s = run_solve_batches(ctx, batches, st);
             if (s != MLMC_OK) return s;
         }
@@ -929,7 +1081,7 @@ mlmc_status mlmc_estimate(mlmc_ctx* ctx, const mlmc_options* opts, mlmc_result* 
                 for (size_t gi = 0; gi < kv.second.size(); ++gi) {
                     const SolveGroup& g = kv.second[gi];
                     const size_t elem = g.a_fp64 ? sizeof(double) : sizeof(float);
-                    const size_t aV = (size_t)(g.a_n + 1) * (g.a_n + 1);
+                    const size_t aV = (size_t)field_pitch(g);
                     for (int smp = 0; smp < g.S; ++smp) {
                         const size_t q = (size_t)(g.flags - flf) + smp;
                         // a low-precision Cholesky factor that overflowed (Sec. 5.2) is retried like a stall
@@ -984,7 +1136,25 @@ mlmc_status mlmc_estimate(mlmc_ctx* ctx, const mlmc_options* opts, mlmc_result* 
         }
         return MLMC_OK;
     };
-    const mlmc_status s = alg41(p.m, p.L_max, p.n0, o, round, res);
+    if (o.resume) {
+        // checkpoint: the counters and the calibrated rule's state continue from the earlier estimate
+        const mlmc_result prev = *o.resume;
+        for (int l = 0; l < MLMC_MAX_LEVELS && l <= prev.L; ++l) {
+            prec_lvl[l] = prev.prec[l];
+            iters_lvl[l] = prev.inner_iters[l];
+            dofs_lvl[l] = prev.dofs[l];
+            retries_lvl[l] = prev.fp64_retries[l];
+            if (calibrate) {
+                cal_contrast[l] = prev.contrast[l];
+                if (prev.a_min[l] > 0) cal_amin[l] = prev.a_min[l];
+                cal_amax[l] = prev.a_max[l];
+            }
+        }
+        flags_or = prev.flags_or;
+    }
+    nvtxRangePushA("mlmc_estimate");
+    const mlmc_status s = alg41(p.m, p.L_max, p.n0, o, round, res, ctx->err);
+    nvtxRangePop();
     MLMC_CUDA_RET(ctx->err, ctx_order_end(ctx, st));
     if (s != MLMC_OK) return s;
     for (int l = 0; l <= res->L; ++l) {
@@ -993,6 +1163,8 @@ mlmc_status mlmc_estimate(mlmc_ctx* ctx, const mlmc_options* opts, mlmc_result* 
         res->dofs[l] = dofs_lvl[l];
         res->fp64_retries[l] = retries_lvl[l];
         res->contrast[l] = calibrate ? cal_contrast[l] : 0.0;
+        res->a_min[l] = calibrate && cal_amin[l] < 1e300 ? cal_amin[l] : 0.0;
+        res->a_max[l] = calibrate ? cal_amax[l] : 0.0;
     }
     res->flags_or = flags_or;
     const int32_t bad = MLMC_F_MAXIT | MLMC_F_STAGNATED | MLMC_F_NONFINITE;
@@ -1025,7 +1197,7 @@ mlmc_status mlmc_adjoint_grad(mlmc_ctx* ctx, int level, int S, const double* xi,
     double* u = reinterpret_cast<double*>(base + abytes);
     double* lam = u + S * V;
     double* w = lam + S * V;
-    mlmc_status s = synth(ctx, level, S, xi, a, fp, st);
+    mlmc_status s = synth(ctx, level, S, xi, a, 0, fp, st);
     if (s != MLMC_OK) return s;
     // ||g||_2 of the adjoint right-hand side
     double g2 = 0.0;

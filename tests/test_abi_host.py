@@ -181,3 +181,71 @@ def test_host_loop_rmse_hand_computed(L):
     assert r["rmse"] == pytest.approx(5e-4, rel=1e-12)
     assert r["estimate"] == pytest.approx(0.0339, rel=1e-13)
     assert r["var_est"] == pytest.approx(1.6e-7, rel=1e-12)
+
+
+@pytest.mark.parametrize("cut", [1, 2, 3])
+def test_resume_from_checkpoint_equals_uninterrupted_run(L, tmp_path, cut):
+    # Alg. 4.1 stopped after `cut` rounds, its result saved to disk, read back and resumed: the same samples
+    # (indices continue from the checkpoint's counts), the same decisions, the same final state bit for bit
+    tol = 1e-3
+    thr = o_mlmc.bias_threshold(2, 2.0, tol)
+    mu = [0.05, 4 * thr, thr, thr / 8, thr / 30]
+    sd = [2e-2, 2e-3, 4e-4, 1e-4, 3e-5]
+    o = L.mlmc_default_options()
+    o.tol, o.N_init, o.L_start = tol, 40, 1
+    full_mock = _Mock(mu, sd, 5)
+    full = L.mlmc_estimate_host(2, 4, 8, o, full_mock)
+    assert full.rounds > cut
+    o.max_rounds = cut
+    first_mock = _Mock(mu, sd, 5)
+    part = L.mlmc_estimate_host(2, 4, 8, o, first_mock)
+    assert part.rounds == cut
+    L.save_result(part, str(tmp_path / "ckpt.bin"))
+    ck = L.load_result(str(tmp_path / "ckpt.bin"))
+    o.max_rounds = 100
+    L.set_resume(o, ck)
+    second_mock = _Mock(mu, sd, 5)
+    res = L.mlmc_estimate_host(2, 4, 8, o, second_mock)
+    assert first_mock.calls + second_mock.calls == full_mock.calls
+    a, b = L.result_dict(res), L.result_dict(full)
+    for key in ("L", "N", "Yhat", "s2", "estimate", "rmse", "rounds", "bias_failed"):
+        assert a[key] == b[key], key
+
+
+def test_resume_rejects_fixed_samples_and_bad_checkpoints(L):
+    o = L.mlmc_default_options()
+    o.L_start = 1
+    prev = L.mlmc_result()
+    prev.L, prev.rounds = 1, 1
+    N = (ctypes.c_int64 * 2)(10, 10)
+    o.fixed_N = ctypes.cast(N, ctypes.POINTER(ctypes.c_int64))
+    L.set_resume(o, prev)
+    with pytest.raises(L.MlmcError):
+        L.mlmc_estimate_host(2, 2, 4, o, _Mock([0, 0, 0], [1, 1, 1], 0))
+    o.fixed_N = None
+    prev.L = 7
+    with pytest.raises(L.MlmcError):
+        L.mlmc_estimate_host(2, 2, 4, o, _Mock([0, 0, 0], [1, 1, 1], 0))
+
+
+def test_round_log_lines(L, tmp_path):
+    # one JSON line per round; the last line's state is the result's
+    import json
+    tol = 1e-3
+    thr = o_mlmc.bias_threshold(2, 2.0, tol)
+    o = L.mlmc_default_options()
+    o.tol, o.N_init, o.L_start = tol, 40, 1
+    path = tmp_path / "rounds.jsonl"
+    L.set_log_path(o, str(path))
+    res = L.result_dict(L.mlmc_estimate_host(2, 4, 8, o, _Mock([0.05, 4 * thr, thr, thr / 8, thr / 30],
+                                                                [2e-2, 2e-3, 4e-4, 1e-4, 3e-5], 7)))
+    lines = [json.loads(x) for x in path.read_text().splitlines()]
+    assert len(lines) == res["rounds"] and [x["round"] for x in lines] == list(range(1, res["rounds"] + 1))
+    last = lines[-1]
+    assert last["L"] == res["L"] and last["N"] == res["N"] and last["Yhat"] == res["Yhat"]
+    assert last["enough"] and last["bias_ok"] and last["rmse"] == res["rmse"]
+    assert all(len(x["N"]) == x["L"] + 1 == len(x["Yhat"]) for x in lines)
+    assert all(b["seconds"] >= a["seconds"] for a, b in zip(lines, lines[1:]))
+    o.log_path = b"/nonexistent-dir/x.jsonl"
+    with pytest.raises(L.MlmcError):
+        L.mlmc_estimate_host(2, 4, 8, o, _Mock([0.0] * 5, [1.0] * 5, 7))

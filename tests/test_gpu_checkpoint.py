@@ -1,0 +1,100 @@
+"""Checkpoint and resume of the Alg. 4.1 state, the per-round log, and the
+forced-allocation-failure hook, on the GPU estimate."""
+import ctypes
+import json
+
+import numpy as np
+import pytest
+
+from gpu_common import device, lib, to_dev, torch
+from inputs import smooth_lognormal_field
+
+pytestmark = pytest.mark.gpu
+
+WL = dict(n0=8, m=2, L_max=3, kind=0, K=16, sigma2=1.0, corr_len=0.3, seed=21)
+
+
+@pytest.fixture(scope="module")
+def M():
+    device()
+    return lib()
+
+
+def _opts(M, **kw):
+    o = M.mlmc_default_options()
+    o.tol, o.N_init, o.L_start = 2e-3, 32, 1
+    for k, v in kw.items():
+        setattr(o, k, v)
+    return o
+
+
+@pytest.mark.parametrize("prec_rule", [0, 1])
+def test_resumed_estimate_equals_uninterrupted(M, tmp_path, prec_rule):
+    h = M.mlmc_create(M.make_problem(**WL), 0)
+    try:
+        full = M.mlmc_estimate(h, _opts(M, prec_rule=prec_rule))
+        assert full.rounds >= 2
+        part = M.mlmc_estimate(h, _opts(M, prec_rule=prec_rule, max_rounds=full.rounds - 1))
+        M.save_result(part, str(tmp_path / "ck.bin"))
+        o = _opts(M, prec_rule=prec_rule)
+        M.set_resume(o, M.load_result(str(tmp_path / "ck.bin")))
+        res = M.mlmc_estimate(h, o)
+    finally:
+        M.mlmc_destroy(h)
+    a, b = M.result_dict(res), M.result_dict(full)
+    # the same samples, solved by the same launches: identical bits and counters
+    for key in ("L", "N", "Yhat", "s2", "estimate", "rmse", "rounds", "prec", "inner_iters", "dofs", "delta",
+                "fp64_retries", "contrast"):
+        assert a[key] == b[key], key
+
+
+def test_round_log_of_the_gpu_estimate(M, tmp_path):
+    path = tmp_path / "rounds.jsonl"
+    h = M.mlmc_create(M.make_problem(**WL), 0)
+    try:
+        o = _opts(M)
+        M.set_log_path(o, str(path))
+        r = M.result_dict(M.mlmc_estimate(h, o))
+    finally:
+        M.mlmc_destroy(h)
+    lines = [json.loads(x) for x in path.read_text().splitlines()]
+    assert len(lines) == r["rounds"]
+    assert lines[-1]["N"] == r["N"] and lines[-1]["Yhat"] == r["Yhat"] and lines[-1]["delta"] == r["delta"]
+
+
+def test_forced_allocation_failure(M):
+    clean = None
+    h = M.mlmc_create(M.make_problem(**WL), 0)
+    try:
+        clean = M.result_dict(M.mlmc_estimate(h, _opts(M)))
+    finally:
+        M.mlmc_destroy(h)
+    try:
+        # creation: the first basis buffer cannot be had
+        M.mlmc_debug_fail_allocation(0)
+        with pytest.raises(M.MlmcError) as ei:
+            M.mlmc_create(M.make_problem(**WL), 0)
+        assert "out of memory" in str(ei.value)
+        # an estimate whose workspace cannot grow fails cleanly; the context works afterwards
+        h = M.mlmc_create(M.make_problem(**WL), 0)
+        try:
+            M.mlmc_debug_fail_allocation(2)
+            with pytest.raises(M.MlmcError) as ei:
+                M.mlmc_estimate(h, _opts(M))
+            assert "out of memory" in str(ei.value)
+            again = M.result_dict(M.mlmc_estimate(h, _opts(M)))
+            assert again["N"] == clean["N"] and again["Yhat"] == clean["Yhat"]
+        finally:
+            M.mlmc_destroy(h)
+        # the allocation-free entry point allocates nothing: an armed hook does not touch it
+        M.mlmc_debug_fail_allocation(0)
+        n, S = 32, 3
+        af = smooth_lognormal_field(n, S, seed=3, log_sd=0.5)
+        Q = torch.empty(S, dtype=torch.float64, device=device())
+        fl = torch.empty(S, dtype=torch.int32, device=device())
+        M.mlmc_level_solve_noalloc(0, n, S, to_dev(af, torch.float64), M.MLMC_FP64, n, M.MLMC_FP32, 1e-8, 10000, 0,
+                                   (0.0, 1.0, 0.0, 1.0), 1.0, Q, flags=fl)
+        torch.cuda.synchronize()
+        assert np.all(fl.cpu().numpy() == M.MLMC_F_CONVERGED)
+    finally:
+        M.mlmc_debug_fail_allocation(-1)
