@@ -516,13 +516,20 @@ __global__ void __launch_bounds__(KLLayout<MODE>::kThreads, 1)
                 if constexpr (lines) {
                     if (!ok) break;
                     if (v < V) {
+                        // the basis tables carry log2(e): the accumulators hold log2 a; one running pointer
+                        // down the chunk's 32 sample rows
+                        Out* p = out + (size_t)sc0 * ldo + v;
+                        if (sc0 + 32 <= S) {
 #pragma unroll
-                        for (int j = 0; j < 32; ++j) {
-                            const int sj = sc0 + j;
-                            // the basis tables carry log2(e): the accumulators hold log2 a
-                            const float l2 =
-                                __fmaf_rn(__uint_as_float(r1[j]), 1.0f / 2048.0f, __uint_as_float(r0[j]));
-                            if (sj < S) out[(size_t)sj * ldo + v] = (Out)ex2_approx(l2);
+                            for (int j = 0; j < 32; ++j, p += ldo)
+                                *p = (Out)ex2_approx(
+                                    __fmaf_rn(__uint_as_float(r1[j]), 1.0f / 2048.0f, __uint_as_float(r0[j])));
+                        } else {
+#pragma unroll
+                            for (int j = 0; j < 32; ++j, p += ldo)
+                                if (sc0 + j < S)
+                                    *p = (Out)ex2_approx(
+                                        __fmaf_rn(__uint_as_float(r1[j]), 1.0f / 2048.0f, __uint_as_float(r0[j])));
                         }
                     }
                 } else {
