@@ -1444,9 +1444,15 @@ __device__ void solve_system(const Params& P, const DevSolve& S, const Group<GT>
 
     double rho = 0.0, rho_prev = 0.0;
     int iters = 0, flag = 0, o = 0;
+    // right-hand side b_i = f h^2 (or the adjoint's g_i), formed once
+    const bool rhs_mode0 = S.rhs_mode == 0;
+    const double b0 = S.f * S.h2;
     for (;; ++o) {
         // ---- R: r = b - A x in FP64 with the master coefficient (r = b while x = 0); d = 0
-        double res = 0.0, rr0 = 0.0, rz0 = 0.0;
+        // the FP64 residual norm decides the refinement; the inner solve's starting (r, r) and (r, z) are
+        // the inner type's, summed like the sweeps' (and summed across the group in FP64)
+        double res = 0.0;
+        VT rr0v = 0, rz0v = 0;
         for (int it = tr; it < items; it += GT) {
             const int j = 1 + it / cpr, c = it - (j - 1) * cpr;
             const size_t base = (size_t)j * ld + 4 * c;
@@ -1457,7 +1463,7 @@ __device__ void solve_system(const Params& P, const DevSolve& S, const Group<GT>
 #pragma unroll
                 for (int q = 0; q < 4; ++q) {
                     const int i = 4 * c + q;
-                    r4[q] = (i >= 1 && i <= n - 1) ? rhs_value(S, i, j) : 0.0;
+                    r4[q] = (i >= 1 && i <= n - 1) ? (rhs_mode0 ? b0 : rhs_value(S, i, j)) : 0.0;
                 }
             } else {
                 // (A x)_ij = (WE(i,j)(x - x_E) + WE(i-1,j)(x - x_W) + WN(i,j)(x - x_N) + WN(i,j-1)(x - x_S)) / 6
@@ -1475,7 +1481,7 @@ __device__ void solve_system(const Params& P, const DevSolve& S, const Group<GT>
                     const double x0 = xc[q + 1];
                     const double ax = (we[q + 1] * (x0 - xc[q + 2]) + we[q] * (x0 - xc[q]) + wn[q] * (x0 - xn[q]) +
                                        ws[q] * (x0 - xs[q])) * (1.0 / 6.0);
-                    r4[q] = (i >= 1 && i <= n - 1) ? rhs_value(S, i, j) - ax : 0.0;
+                    r4[q] = (i >= 1 && i <= n - 1) ? (rhs_mode0 ? b0 : rhs_value(S, i, j)) - ax : 0.0;
                 }
             }
 #pragma unroll
@@ -1483,8 +1489,8 @@ __device__ void solve_system(const Params& P, const DevSolve& S, const Group<GT>
                 const double rq = r4[q];
                 rv[q] = (VT)rq;
                 res += rq * rq;
-                rr0 += (double)rv[q] * (double)rv[q];
-                rz0 += jac ? (double)rv[q] * (double)(rv[q] * zv[q]) : (double)rv[q] * (double)rv[q];
+                rr0v += rv[q] * rv[q];
+                rz0v += jac ? rv[q] * (rv[q] * zv[q]) : rv[q] * rv[q];
             }
             Vec4<VT>::store(R + base, rv);
             const VT z[4] = {(VT)0, (VT)0, (VT)0, (VT)0};
@@ -1501,7 +1507,14 @@ __device__ void solve_system(const Params& P, const DevSolve& S, const Group<GT>
             }
         }
         if (pipe_on) fence_proxy_async_global();
-        G.template sum3<double>(res, rr0, rz0, res, rr0, rz0);
+        double rr0, rz0;
+        {
+            double a0, b0s, c0s;
+            G.template sum3<double>(res, (double)rr0v, (double)rz0v, a0, b0s, c0s);
+            res = a0;
+            rr0 = b0s;
+            rz0 = c0s;
+        }
         rho = sqrt(res) / S.bnorm;
         if (pipe_on && pipe_aborted(*pipe)) { flag = MLMC_F_TIMEOUT; break; }
         if (!(rho == rho) || isinf(rho)) { flag = MLMC_F_NONFINITE; break; }
