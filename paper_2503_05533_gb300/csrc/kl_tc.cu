@@ -543,26 +543,27 @@ __global__ void __launch_bounds__(KLLayout<MODE>::kThreads, 1)
                     const uint32_t g4 = (uint32_t)sc0 * (uint32_t)ldo + (uint32_t)v0 + (uint32_t)mis;
                     // staging row j holds sample sc0 + j, node v0 + k at slot k + sh_j with sh_j = (output index
                     // + mis) mod 4, so that 16-byte-aligned output addresses meet 16-byte-aligned slots
+                    const uint32_t d4 = (uint32_t)ldo & 3u;
+                    uint32_t shj = g4 & 3u;
 #pragma unroll
                     for (int j = 0; j < 32; ++j) {
-                        const int sh = (int)((g4 + (uint32_t)j * (uint32_t)ldo) & 3u);
                         const float l2 = __fmaf_rn(__uint_as_float(r1[j]), 1.0f / 2048.0f, __uint_as_float(r0[j]));
-                        stg[j * kStgPitch + sh + q4 * 32 + lane] = ex2_approx(l2);
+                        stg[j * kStgPitch + (int)shj + q4 * 32 + lane] = ex2_approx(l2);
+                        shj = (shj + d4) & 3u;
                     }
                     bar_sync_n(1 + c, 128);
-                    // warp q4 writes staging rows 8 q4 .. 8 q4 + 7
+                    // warp q4 writes staging rows 8 q4 .. 8 q4 + 7, one running pointer down them
+                    const int j0 = q4 * 8;
+                    Out* dst = out + (size_t)(sc0 + j0) * ldo + v0;
+                    uint32_t shr = (g4 + (uint32_t)j0 * (uint32_t)ldo) & 3u;
+                    const int jn = min(8, S - (sc0 + j0));
 #pragma unroll 1
-                    for (int jj = 0; jj < 8; ++jj) {
-                        const int j = q4 * 8 + jj;
-                        const int s = sc0 + j;
-                        if (s >= S || nv <= 0) continue;
-                        const long long g0 = (long long)s * ldo + v0;
-                        const int sh = (int)((g0 + mis) & 3);
+                    for (int jj = 0; jj < jn && nv > 0; ++jj, dst += ldo, shr = (shr + d4) & 3u) {
+                        const int sh = (int)shr;
                         const int h = min((4 - sh) & 3, nv);    // elements before the first aligned one
                         const int nb = (nv - h) >> 2;           // aligned groups of four
                         const int t0 = h + 4 * nb;              // first element of the tail
-                        const float* row = stg + j * kStgPitch + sh;
-                        Out* dst = out + g0;
+                        const float* row = stg + (j0 + jj) * kStgPitch + sh;
                         if (lane < h) dst[lane] = row[lane];
                         if (lane < nb)
                             *reinterpret_cast<float4*>(dst + h + 4 * lane) =
@@ -607,10 +608,13 @@ __global__ void __launch_bounds__(KLLayout<MODE>::kThreads, 1)
                 }
                 if (!ok) break;
                 const int evv = ev[v < Vpad ? v : Vpad - 1];
+                // lane l holds the exponent of sample sc0 + l; sample j's is taken from lane j
+                const int esl = es[min(sc0 + lane, Spad - 1)];
+                Out* p = out + (size_t)sc0 * ldo + v;
+                const int jend = min(32, S - sc0);
 #pragma unroll
-                for (int j = 0; j < 32; ++j) {
-                    const int sj = sc0 + j;
-                    const int sc = es[sj < Spad ? sj : Spad - 1] + evv - 18;
+                for (int j = 0; j < 32; ++j, p += ldo) {
+                    const int sc = __shfl_sync(0xffffffffu, esl, j) + evv - 18;
                     // float-float of the integer sum (up to 2^26) plus the FP32 correction sum
                     const int ii = s0i[j];
                     const float ih = (float)ii;
@@ -623,7 +627,7 @@ __global__ void __launch_bounds__(KLLayout<MODE>::kThreads, 1)
                     ll = scale2(ll, sc);
                     float ah, al;
                     ff_exp(lh, ll, ffx, ffx_th, ffx_tl, ah, al);
-                    if (sj < S && v < V) out[(size_t)sj * ldo + v] = ff_to_double(ah, al);
+                    if (j < jend && v < V) *p = ff_to_double(ah, al);
                 }
             }
         }
