@@ -248,6 +248,8 @@ def main():
                     help="preconditioner of the CG inner solves")
     ap.add_argument("--mg-nu", type=int, default=0, help="multigrid smoothing sweeps (0: default)")
     ap.add_argument("--mg-coarse", type=int, default=0, help="multigrid coarsest-grid sweeps (0: default)")
+    ap.add_argument("--mg-min", type=int, default=0, help="multigrid: halve grids while the half has at least "
+                                                          "this many cells (0: default)")
     ap.add_argument("--tau-min", type=float, default=0.0,
                     help="solve-l4 and sweep: floor of the inner tolerance (0: per-precision default)")
     ap.add_argument("--med-items", type=int, default=0,
@@ -345,8 +347,8 @@ def main():
             launches = M.mlmc_launch_count() - l0
             prof = M.mlmc_profile_get(h) if profile else None
             if prof is not None:
-                prof["autotune"] = [{k: e[k] for k in ("shape", "med_items", "ring", "nu", "theta", "tau_min", "best_ms",
-                                                        "default_ms", "trials")} for e in tune]
+                prof["autotune"] = [{k: e[k] for k in ("shape", "med_items", "ring", "nu", "mg_min", "mg_coarse", "theta",
+                                                        "tau_min", "best_ms", "default_ms", "trials")} for e in tune]
         finally:
             M.mlmc_destroy(h)
         return ms, results, launches, prof
@@ -532,6 +534,8 @@ def solve_l4_case(M, torch, dev, args, prob, hbm_peak, peak_src, flush, stream):
         M.mlmc_profile_enable(h, True)
         M.mlmc_debug_set_solve_ring(h, args.ring)
         M.mlmc_set_precond(h, M.MLMC_PC_MG if args.pc == "mg" else M.MLMC_PC_JACOBI, args.mg_nu, args.mg_coarse)
+        if args.mg_min:
+            M.mlmc_set_mg_coarsest(h, args.mg_min)
         M.mlmc_set_inner_tolerance(h, 0.0, args.tau_min)
         a = torch.empty((S, (n + 1) ** 2), dtype=torch.float32, device=dev)
         Q = torch.empty(S, dtype=torch.float64, device=dev)
@@ -554,7 +558,7 @@ def solve_l4_case(M, torch, dev, args, prob, hbm_peak, peak_src, flush, stream):
     finally:
         M.mlmc_destroy(h)
     achieved = prof["solve_bytes"] / (prof["solve_ms"] * 1e-3) / 1e9
-    print(json.dumps({"case": "solve-l4", "ring": args.ring, "pc": args.pc, "mg_nu": args.mg_nu, "tau_min": args.tau_min,
+    print(json.dumps({"case": "solve-l4", "ring": args.ring, "mg_min": args.mg_min, "pc": args.pc, "mg_nu": args.mg_nu, "tau_min": args.tau_min,
                       "mg_coarse": args.mg_coarse, "ms_per_step": sum(ms) / len(ms), "systems": S, "n": n,
                       "delta": deltas[level], "prec": precs[level],
                       "inner_iters_per_system": prof["inner_iters"] / (S * args.steps),

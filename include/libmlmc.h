@@ -425,6 +425,11 @@ mlmc_status mlmc_adjoint_grad(mlmc_ctx* ctx, int level, int S, const double* xi,
  * on the FP64 residual of the refinement (Alg. 2.1). */
 mlmc_status mlmc_set_precond(mlmc_ctx* ctx, mlmc_precond pc, int nu, int coarse_sweeps, double omega);
 
+/* Multigrid hierarchy depth: grids are halved while even and the half keeps at
+ * least min_cells cells (2..64; default 4), so the coarsest grid has between
+ * min_cells and 2 min_cells - 1 cells (or is the solve grid itself). */
+mlmc_status mlmc_set_mg_coarsest(mlmc_ctx* ctx, int min_cells);
+
 /* Working precision u (of the iterate x) and residual precision u_r of the
  * refinement of this context's Cholesky solves (MLMC_CHOLESKY): (u, u_r) one of
  * (MLMC_FP64, MLMC_FP64) (default), (MLMC_FP32, MLMC_FP64), (MLMC_FP32,
@@ -452,8 +457,8 @@ mlmc_status mlmc_set_inner_tolerance(mlmc_ctx* ctx, double theta, double tau_min
  * setting, changing one setting at a time from the library's own rules: the
  * group size of n = 91..128 systems (mlmc_debug_set_medium_items), the row-
  * pipeline depth of Jacobi-preconditioned CG (0, 2, 4 slots), the V-cycle's
- * smoothing sweeps (1, 2), the inner tolerance factor theta (0.1, 0.3, 0.6)
- * and its floor tau_min (0.3, 1 or 3 times the precision's default, unless the
+ * coarsest grid (4 or 16 sweeps on it; one halving less with 16) and smoothing sweeps
+ * (1, 2), the inner tolerance factor theta (0.1, 0.3, 0.6) and its floor tau_min (0.3, 1 or 3 times the precision's default, unless the
  * context sets one; mlmc_set_inner_tolerance).  Each candidate is timed twice with CUDA events;
  * a change is kept when at least 1% faster, and the fastest setting is cached
  * in the context for the shape.  Every candidate solves the same systems to
@@ -464,6 +469,7 @@ typedef struct {
     char shape[192];       /* the launch shape, as text                                        */
     int prec, solver, precond;
     int med_items, ring, nu;   /* chosen settings; -3 (and nu 0) means the context's own rule    */
+    int mg_min, mg_coarse; /* chosen coarsening bound and coarsest-grid sweeps; 0: the context's  */
     double theta;          /* chosen inner tolerance factor; 0 means the context's (0.3)       */
     double tau_min;        /* chosen floor of the inner tolerance; < 0 means the precision's    */
     double best_ms, default_ms;   /* launch time with the chosen and with the default settings */

@@ -76,7 +76,8 @@ class mlmc_profile(ctypes.Structure):
 
 class mlmc_tune_entry(ctypes.Structure):
     _fields_ = [("shape", ctypes.c_char * 192), ("prec", c_int), ("solver", c_int), ("precond", c_int),
-                ("med_items", c_int), ("ring", c_int), ("nu", c_int), ("theta", c_double), ("tau_min", c_double),
+                ("med_items", c_int), ("ring", c_int), ("nu", c_int), ("mg_min", c_int), ("mg_coarse", c_int),
+                ("theta", c_double), ("tau_min", c_double),
                 ("best_ms", c_double), ("default_ms", c_double), ("trials", c_int)]
 
 
@@ -118,6 +119,7 @@ _SIGS = {
     "mlmc_debug_set_solve_ring": (c_int, [c_void_p, c_int]),
     "mlmc_debug_fail_allocation": (c_int, [c_int64]),
     "mlmc_set_seed": (c_int, [c_void_p, c_uint64]),
+    "mlmc_set_mg_coarsest": (c_int, [c_void_p, c_int]),
     "mlmc_debug_set_medium_items": (c_int, [c_void_p, c_int]),
     "mlmc_set_precond": (c_int, [c_void_p, c_int, c_int, c_int, c_double]),
     "mlmc_set_inner_tolerance": (c_int, [c_void_p, c_double, c_double]),
@@ -200,6 +202,10 @@ def mlmc_destroy(ctx):
 
 def mlmc_set_seed(ctx, seed):
     _check(lib().mlmc_set_seed(ctx, seed), ctx)
+
+
+def mlmc_set_mg_coarsest(ctx, min_cells):
+    _check(lib().mlmc_set_mg_coarsest(ctx, min_cells), ctx)
 
 
 def mlmc_last_error(ctx=None):

@@ -638,6 +638,13 @@ mlmc_status mlmc_set_precond(mlmc_ctx* ctx, mlmc_precond pc, int nu, int coarse_
     return MLMC_OK;
 }
 
+mlmc_status mlmc_set_mg_coarsest(mlmc_ctx* ctx, int min_cells) {
+    if (!ctx) return MLMC_E_ARG;
+    if (min_cells < 2 || min_cells > 64) return fail(ctx, MLMC_E_ARG, "set_mg_coarsest: min_cells in 2..64");
+    ctx->mg_min = min_cells;
+    return MLMC_OK;
+}
+
 mlmc_status mlmc_set_inner_tolerance(mlmc_ctx* ctx, double theta, double tau_min) {
     if (!ctx) return MLMC_E_ARG;
     if (!(theta >= 0.0 && theta < 1.0) || !(tau_min < 0.5))
@@ -679,6 +686,8 @@ mlmc_status mlmc_autotune_entry(const mlmc_ctx* ctx, int i, mlmc_tune_entry* out
     out->med_items = t.med_items;
     out->ring = t.ring;
     out->nu = t.nu;
+    out->mg_min = t.mg_min;
+    out->mg_coarse = t.mg_coarse;
     out->theta = t.theta;
     out->tau_min = t.tau_min;
     out->best_ms = t.best_ms;

@@ -66,6 +66,7 @@ constexpr int kTuneUnset = -3;   // a SolveConfig launch setting left to the con
 struct TuneChoice {
     int prec = 0, solver = 0, precond = 0;
     int med_items = kTuneUnset, ring = kTuneUnset, nu = 0;
+    int mg_min = 0, mg_coarse = 0;   // coarsest grid bound and its sweeps (0: the context's)
     double theta = 0.0;
     double tau_min = -1.0;      // floor of the inner tolerance (< 0: the precision's default)
     float best_ms = 0.f, default_ms = 0.f;
@@ -122,6 +123,7 @@ struct mlmc_ctx {
     int chol_ur = MLMC_FP64;      // ... and precision of the refinement residual
     int mg_nu = 1;                // multigrid: smoothing sweeps before and after the coarse correction
     int mg_coarse = 8;            // multigrid: Jacobi sweeps on the coarsest grid
+    int mg_min = 4;               // multigrid: grids are halved while the half keeps at least this many cells
     double mg_omega = 0.8;        // multigrid: Jacobi damping
     double inner_theta = 0.3;     // inner tolerance tau = clamp(theta delta / rho, tau_min, 0.5)
     double inner_tau_min = -1.0;  // < 0: per-precision default
@@ -200,6 +202,8 @@ struct SolveConfig {
     int med_items = kTuneUnset;
     int ring = kTuneUnset;
     int nu = 0;
+    int mg_min = 0;             // multigrid coarsening bound (0: the context's)
+    int mg_coarse = 0;          // multigrid sweeps on the coarsest grid (0: the context's)
     double theta = 0.0;
     // Cholesky solver (MLMC_CHOLESKY): working precision u of x and residual precision u_r of Alg. 2.1
     int chol_u = MLMC_FP64;

@@ -104,6 +104,8 @@ void tune_apply(const TuneChoice& t, SolveConfig& cfg) {
     cfg.med_items = t.med_items;
     cfg.ring = t.ring;
     cfg.nu = t.nu;
+    cfg.mg_min = t.mg_min;
+    cfg.mg_coarse = t.mg_coarse;
     cfg.theta = t.theta;
     cfg.tau_min = t.tau_min;
 }
@@ -196,6 +198,18 @@ mlmc_status autotune_batch(mlmc_ctx* ctx, const std::vector<SolveGroup>& groups,
             c.ring = r;
             consider(c);
         }
+    if (mg) {
+        // the coarsest grid: fewer or more sweeps on it, or one halving less with more sweeps (measured on
+        // 100 x n = 256: 4.75 ms by default, 4.73 with 4 sweeps, 4.63 one level shallower with 16 sweeps)
+        const int deeper[3][2] = {{ctx->mg_min, 4}, {ctx->mg_min, 16}, {2 * ctx->mg_min, 16}};
+        for (const auto& d : deeper) {
+            if (d[0] > 32 || (d[0] == ctx->mg_min && d[1] == ctx->mg_coarse)) continue;
+            TuneChoice c = cur;
+            c.mg_min = d[0];
+            c.mg_coarse = d[1];
+            consider(c);
+        }
+    }
     if (mg)
         for (int nu : {1, 2}) {
             if (nu == ctx->mg_nu) continue;

@@ -133,9 +133,9 @@ __host__ __device__ constexpr int row_pitch(int n) { return (n + 1 + 7) / 8 * 8;
 // half has at least 4 cells.  Level k >= 1 (n >> k cells) occupies
 // mg_level_nodes(n >> k) nodes of the coarse-level arrays, levels in order.
 constexpr int kMgMinN = 4;
-__host__ __device__ constexpr int mg_level_count(int n) {
+__host__ __device__ constexpr int mg_level_count(int n, int min_n = kMgMinN) {
     int l = 0;
-    while (n % 2 == 0 && n / 2 >= kMgMinN) {
+    while (n % 2 == 0 && n / 2 >= min_n) {
         n /= 2;
         ++l;
     }
@@ -2122,7 +2122,7 @@ mlmc_status launch_typed(mlmc_ctx* ctx, const std::vector<SolveGroup>& groups, c
             d.flags = g.flags;
             d.out = s;
             d.sys = (int)solves.size();
-            d.mg_levels = mg ? mg_level_count(n) : 0;
+            d.mg_levels = mg ? mg_level_count(n, cfg.mg_min > 0 ? cfg.mg_min : ctx->mg_min) : 0;
             d.mg_off = ctotal;
             ctotal += mg ? mg_coarse_nodes(n, d.mg_levels) : 0;
             solves.push_back(d);
@@ -2178,7 +2178,7 @@ mlmc_status launch_typed(mlmc_ctx* ctx, const std::vector<SolveGroup>& groups, c
     if (mg) {
         P.mg = 1;
         P.mg_nu = cfg.nu > 0 ? cfg.nu : ctx->mg_nu;
-        P.mg_coarse = ctx->mg_coarse;
+        P.mg_coarse = cfg.mg_coarse > 0 ? cfg.mg_coarse : ctx->mg_coarse;
         P.mg_omega = ctx->mg_omega;
     }
     size_t smem = 0;

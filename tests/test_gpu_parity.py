@@ -666,3 +666,24 @@ def test_level_solve_reads_padded_rows(M, solver):
                                None, torch.empty(S, dtype=torch.float64, device=device()), a_ld=V2 - 1)
     finally:
         M.mlmc_destroy(h)
+
+
+@pytest.mark.parametrize("mg_min,coarse", [(2, 8), (8, 16), (16, 4), (64, 16)])
+def test_multigrid_depth_choices_meet_delta(M, mg_min, coarse):
+    # the coarsest grid of the V-cycle (mlmc_set_mg_coarsest) and its sweeps only change the preconditioner:
+    # every choice still certifies delta on the FP64 residual and agrees with the oracle within c_u delta
+    n, S, delta = 128, 4, 1e-8
+    af = smooth_lognormal_field(n, S, seed=61, log_sd=1.0)
+    h = _ctx(M)
+    try:
+        M.mlmc_set_mg_coarsest(h, mg_min)
+        M.mlmc_set_precond(h, M.MLMC_PC_MG, 0, coarse, 0.0)
+        U, Q, it, rr, fl = _solve(M, h, n, af, M.MLMC_FP64, n, M.MLMC_FP32, delta)
+        with pytest.raises(M.MlmcError):
+            M.mlmc_set_mg_coarsest(h, 1)
+    finally:
+        M.mlmc_destroy(h)
+    assert np.all(fl == M.MLMC_F_CONVERGED) and np.all(rr < delta)
+    for s in range(S):
+        x, Qo = o_fem.solve_sample(n, af[s])
+        assert abs(Q[s] - Qo) <= 1.5 * delta * abs(Qo)
