@@ -347,7 +347,7 @@ def main():
             launches = M.mlmc_launch_count() - l0
             prof = M.mlmc_profile_get(h) if profile else None
             if prof is not None:
-                prof["autotune"] = [{k: e[k] for k in ("shape", "med_items", "ring", "nu", "mg_min", "mg_coarse", "theta",
+                prof["autotune"] = [{k: e[k] for k in ("shape", "med_items", "ring", "nu", "mg_min", "mg_coarse", "mg_omega", "mg_smem", "theta",
                                                         "tau_min", "best_ms", "default_ms", "trials")} for e in tune]
         finally:
             M.mlmc_destroy(h)
@@ -387,7 +387,8 @@ def main():
     create_s = time.perf_counter() - t0
     e2e_s, h2d, d2h = [], 0, 0
     try:
-        M.mlmc_estimate(h, opts())   # first use: workspace allocation
+        M.mlmc_set_autotune(h, not args.no_autotune)   # the launch settings of the timed estimates
+        M.mlmc_estimate(h, opts())   # first use: workspace allocation and tuning
         for s in range(args.steps):
             M.mlmc_profile_reset(h)
             torch.cuda.synchronize()

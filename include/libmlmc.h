@@ -454,22 +454,29 @@ mlmc_status mlmc_set_inner_tolerance(mlmc_ctx* ctx, double theta, double tau_min
  * default).  When on, the first launch of each new launch shape -- inner
  * precision, solver, preconditioner, and the batch's grid sizes with their
  * system counts rounded down to powers of two -- is solved once per candidate
- * setting, changing one setting at a time from the library's own rules: the
- * group size of n = 91..128 systems (mlmc_debug_set_medium_items), the row-
- * pipeline depth of Jacobi-preconditioned CG (0, 2, 4 slots), the V-cycle's
- * coarsest grid (4 or 16 sweeps on it; one halving less with 16) and smoothing sweeps
- * (1, 2), the inner tolerance factor theta (0.1, 0.3, 0.6) and its floor tau_min (0.3, 1 or 3 times the precision's default, unless the
- * context sets one; mlmc_set_inner_tolerance).  Each candidate is timed twice with CUDA events;
- * a change is kept when at least 1% faster, and the fastest setting is cached
- * in the context for the shape.  Every candidate solves the same systems to
- * the same delta, so results agree to the solve tolerance whatever is chosen.
- * A launch that tunes synchronises its stream (mlmc_level_solve included). */
+ * setting, changing one setting at a time from the library's own rules:
+ *   - the group size of n = 91..128 systems (mlmc_debug_set_medium_items);
+ *   - the row-pipeline depth of Jacobi-preconditioned CG (0, 2, 4 slots);
+ *   - the V-cycle's coarsest grid (4 or 16 sweeps on it, or one halving less
+ *     with 16; mlmc_set_mg_coarsest), its smoother damping (0.7, 0.9), the
+ *     deepest coarse grid kept in shared memory (32 cells) and its smoothing
+ *     sweeps (1, 2);
+ *   - the inner tolerance factor theta (0.1, 0.3, 0.6) and its floor tau_min
+ *     (0.3, 1 or 3 times the precision's default, unless the context sets one;
+ *     mlmc_set_inner_tolerance).
+ * Each candidate is timed twice with CUDA events; a change is kept when at
+ * least 1% faster, and the fastest setting is cached in the context for the
+ * shape.  Every candidate solves the same systems to the same delta, so
+ * results agree to the solve tolerance whatever is chosen.  A launch that
+ * tunes synchronises its stream (mlmc_level_solve included). */
 mlmc_status mlmc_set_autotune(mlmc_ctx* ctx, int on);
 typedef struct {
     char shape[192];       /* the launch shape, as text                                        */
     int prec, solver, precond;
     int med_items, ring, nu;   /* chosen settings; -3 (and nu 0) means the context's own rule    */
     int mg_min, mg_coarse; /* chosen coarsening bound and coarsest-grid sweeps; 0: the context's  */
+    double mg_omega;       /* chosen smoother damping; 0: the context's                           */
+    int mg_smem;           /* largest coarse grid kept in shared memory; 0: the library's rule (64) */
     double theta;          /* chosen inner tolerance factor; 0 means the context's (0.3)       */
     double tau_min;        /* chosen floor of the inner tolerance; < 0 means the precision's    */
     double best_ms, default_ms;   /* launch time with the chosen and with the default settings */

@@ -77,7 +77,7 @@ class mlmc_profile(ctypes.Structure):
 class mlmc_tune_entry(ctypes.Structure):
     _fields_ = [("shape", ctypes.c_char * 192), ("prec", c_int), ("solver", c_int), ("precond", c_int),
                 ("med_items", c_int), ("ring", c_int), ("nu", c_int), ("mg_min", c_int), ("mg_coarse", c_int),
-                ("theta", c_double), ("tau_min", c_double),
+                ("mg_omega", c_double), ("mg_smem", c_int), ("theta", c_double), ("tau_min", c_double),
                 ("best_ms", c_double), ("default_ms", c_double), ("trials", c_int)]
 
 

@@ -688,6 +688,8 @@ mlmc_status mlmc_autotune_entry(const mlmc_ctx* ctx, int i, mlmc_tune_entry* out
     out->nu = t.nu;
     out->mg_min = t.mg_min;
     out->mg_coarse = t.mg_coarse;
+    out->mg_omega = t.mg_omega;
+    out->mg_smem = t.mg_smem;
     out->theta = t.theta;
     out->tau_min = t.tau_min;
     out->best_ms = t.best_ms;

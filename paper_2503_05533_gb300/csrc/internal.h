@@ -67,6 +67,8 @@ struct TuneChoice {
     int prec = 0, solver = 0, precond = 0;
     int med_items = kTuneUnset, ring = kTuneUnset, nu = 0;
     int mg_min = 0, mg_coarse = 0;   // coarsest grid bound and its sweeps (0: the context's)
+    double mg_omega = 0.0;           // Jacobi damping of the smoother (0: the context's)
+    int mg_smem = 0;                 // largest coarse grid kept in shared memory (0: 64)
     double theta = 0.0;
     double tau_min = -1.0;      // floor of the inner tolerance (< 0: the precision's default)
     float best_ms = 0.f, default_ms = 0.f;
@@ -204,6 +206,8 @@ struct SolveConfig {
     int nu = 0;
     int mg_min = 0;             // multigrid coarsening bound (0: the context's)
     int mg_coarse = 0;          // multigrid sweeps on the coarsest grid (0: the context's)
+    double mg_omega = 0.0;      // multigrid smoother damping (0: the context's)
+    int mg_smem = 0;            // largest coarse grid of the 512-thread groups in shared memory (0: 64)
     double theta = 0.0;
     // Cholesky solver (MLMC_CHOLESKY): working precision u of x and residual precision u_r of Alg. 2.1
     int chol_u = MLMC_FP64;

@@ -106,6 +106,8 @@ void tune_apply(const TuneChoice& t, SolveConfig& cfg) {
     cfg.nu = t.nu;
     cfg.mg_min = t.mg_min;
     cfg.mg_coarse = t.mg_coarse;
+    cfg.mg_omega = t.mg_omega;
+    cfg.mg_smem = t.mg_smem;
     cfg.theta = t.theta;
     cfg.tau_min = t.tau_min;
 }
@@ -207,6 +209,17 @@ mlmc_status autotune_batch(mlmc_ctx* ctx, const std::vector<SolveGroup>& groups,
             TuneChoice c = cur;
             c.mg_min = d[0];
             c.mg_coarse = d[1];
+            consider(c);
+        }
+        // the smoother's damping, and the deepest grid kept in shared memory
+        for (double om : {0.7, 0.9}) {
+            TuneChoice c = cur;
+            c.mg_omega = om;
+            consider(c);
+        }
+        {
+            TuneChoice c = cur;
+            c.mg_smem = 32;
             consider(c);
         }
     }

@@ -2179,7 +2179,7 @@ mlmc_status launch_typed(mlmc_ctx* ctx, const std::vector<SolveGroup>& groups, c
         P.mg = 1;
         P.mg_nu = cfg.nu > 0 ? cfg.nu : ctx->mg_nu;
         P.mg_coarse = cfg.mg_coarse > 0 ? cfg.mg_coarse : ctx->mg_coarse;
-        P.mg_omega = ctx->mg_omega;
+        P.mg_omega = cfg.mg_omega > 0 ? cfg.mg_omega : ctx->mg_omega;
     }
     size_t smem = 0;
     if (cfg.solver == MLMC_CG) {
@@ -2198,6 +2198,7 @@ mlmc_status launch_typed(mlmc_ctx* ctx, const std::vector<SolveGroup>& groups, c
     if (mg && nbig > 0) {
         const size_t pipe_end = smem ? (smem + 127) / 128 * 128 : 0;
         for (int nmax : {64, 32, 16}) {
+            if (cfg.mg_smem > 0 && nmax > cfg.mg_smem) continue;
             // every large system's shared-memory levels must fit (halving chains differ by grid)
             size_t need = 0;
             for (int i : order) {
