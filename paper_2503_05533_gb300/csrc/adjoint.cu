@@ -5,7 +5,9 @@
 //   dQ/da_v = G_v = -(1/3) sum_{T contains v} |T| grad(lambda_h).grad(u_h)|_T,
 // and with a_v = exp(sum_k xi_k Phi_k(v)), dQ/dxi_k = sum_v Phi_k(v) a_v G_v
 // (the transposed KL contraction, kl_synth.cu).  This kernel forms
-// w[s][v] = a_v G_v on every node v of the (n+1)^2 grid.
+// w[s][v] = a_v G_v on every node v of the (n+1)^2 grid, in FP64, and stores it as
+// a float-float pair (hi = w rounded to FP32, lo = the remainder rounded to FP32; 48
+// significant bits) for the contraction, which runs on the FP32 pipe.
 //
 // On the right triangles T1(i,j) = (SW, SE, NE) and T2(i,j) = (SW, NE, NW) of
 // cell (i,j) with legs h, |T| grad(l).grad(u) = 1/2 (sum over the two legs of
@@ -35,7 +37,7 @@ __device__ __forceinline__ double leg_energy_t2(const double* u, const double* l
 }
 
 __global__ void adjoint_elements_kernel(int n, int S, const void* a, int a_fp64, const double* __restrict__ u,
-                                        const double* __restrict__ lam, double* __restrict__ wout) {
+                                        const double* __restrict__ lam, float* __restrict__ wff) {
     const long long tid = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     const int V = (n + 1) * (n + 1);
     if (tid >= (long long)S * V) return;
@@ -52,13 +54,16 @@ __global__ void adjoint_elements_kernel(int n, int S, const void* a, int a_fp64,
     if (hasE && hasS) e += leg_energy_t2(us, ls, n, i, j - 1);                                   // SE cell
     const double av = a_fp64 ? static_cast<const double*>(a)[(size_t)s * V + v]
                              : (double)static_cast<const float*>(a)[(size_t)s * V + v];
-    wout[(size_t)s * V + v] = -av * e * (1.0 / 3.0);
+    const double wv = -av * e * (1.0 / 3.0);
+    const float hi = __double2float_rn(wv);
+    wff[(size_t)s * V + v] = hi;
+    wff[(size_t)S * V + (size_t)s * V + v] = __double2float_rn(wv - (double)hi);
 }
 
 }  // namespace
 
 cudaError_t launch_adjoint_elements(int n, int S, const void* a, int a_fp64, const double* u, const double* lam,
-                                    double* G, cudaStream_t st) {
+                                    float* G, cudaStream_t st) {
     if (S <= 0) return cudaSuccess;
     const long long work = (long long)S * (n + 1) * (n + 1);
     adjoint_elements_kernel<<<(unsigned)((work + 255) / 256), 256, 0, st>>>(n, S, a, a_fp64, u, lam, G);

@@ -1200,14 +1200,18 @@ mlmc_status mlmc_adjoint_grad(mlmc_ctx* ctx, int level, int S, const double* xi,
     // (exact lead slice, about 1e-9 in log a) for the mixed-precision solves
     const mlmc_prec fp = (prec == MLMC_FP64) ? MLMC_FP64 : MLMC_FP64TC;
     const size_t felem = sizeof(double);
-    // layout: a [S][V] (field precision) | u [S][V] | lam [S][V] | w [S][V] (FP64)
+    // layout: a [S][V] (field precision) | u [S][V] | lam [S][V] (FP64) | w [2][S][V] (float-float) |
+    // the contraction's partial sums [splits][S][K] (FP64)
     const size_t abytes = (S * V * felem + 255) / 256 * 256;
-    MLMC_CUDA_RET(ctx->err, ctx->ws.adj.reserve(abytes + 3 * S * V * sizeof(double)));
+    const int splits = kl_transpose_splits(S, ctx->prob.field.K, ctx->num_sms);
+    const size_t pbytes = (size_t)splits * S * ctx->prob.field.K * sizeof(double);
+    MLMC_CUDA_RET(ctx->err, ctx->ws.adj.reserve(abytes + 3 * S * V * sizeof(double) + pbytes));
     char* base = ctx->ws.adj.as<char>();
     void* a = base;
     double* u = reinterpret_cast<double*>(base + abytes);
     double* lam = u + S * V;
-    double* w = lam + S * V;
+    float* wff = reinterpret_cast<float*>(lam + S * V);
+    double* part = lam + 2 * S * V;
     mlmc_status s = synth(ctx, level, S, xi, a, 0, fp, st);
     if (s != MLMC_OK) return s;
     // ||g||_2 of the adjoint right-hand side
@@ -1237,8 +1241,8 @@ mlmc_status mlmc_adjoint_grad(mlmc_ctx* ctx, int level, int S, const double* xi,
     cfg.max_iters = max_iters;
     s = launch_solve_async(ctx, {gf, ga}, cfg, st);
     if (s != MLMC_OK) return s;
-    MLMC_CUDA_RET(ctx->err, launch_adjoint_elements(n, S, a, 1, u, lam, w, st));
-    MLMC_CUDA_RET(ctx->err, launch_kl_transpose_fp64(ctx->basis.at(n), S, w, dQdxi, st));
+    MLMC_CUDA_RET(ctx->err, launch_adjoint_elements(n, S, a, 1, u, lam, wff, st));
+    MLMC_CUDA_RET(ctx->err, launch_kl_transpose_ff(ctx->basis.at(n), S, wff, part, splits, dQdxi, st));
     MLMC_CUDA_RET(ctx->err, ctx_order_end(ctx, st));
     return MLMC_OK;
 }

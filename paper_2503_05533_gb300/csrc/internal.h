@@ -55,6 +55,8 @@ struct GridBasis {
     DevBuf phi64;          // FP64 [K][nodes_pad]
     DevBuf phi16;          // FP16 [2][nodes_pad][Kpad]: hi rows then lo rows, Phi = hi + lo 2^-11 (K-major)
     DevBuf phix;           // FP16 [3][nodes_pad][Kpad]: exact-lead slices of the FP64-output synthesis (lazy)
+    DevBuf phiff;          // FP32 [2][K][nodes_pad]: Phi as float-float pairs (hi rows, then lo rows) for the
+                           // transposed contraction of the gradient (lazy)
     DevBuf ev;             // int [nodes_pad]: their per-node power-of-two exponents
 };
 
@@ -168,8 +170,12 @@ cudaError_t launch_kl_fp32(mlmc_ctx* ctx, const GridBasis& gb, int S, const doub
 // grid's exact-lead basis slices on first use
 cudaError_t launch_kl_tc64(mlmc_ctx* ctx, GridBasis& gb, int S, const double* xi, double* a, long long ld,
                            cudaStream_t st);
-cudaError_t launch_kl_transpose_fp64(const GridBasis& gb, int S, const double* w, double* out,
-                                     cudaStream_t st);
+// out[s][k] = sum_v Phi[k][v] w[s][v] with w given as float-float rows wff = [2][S][V] (hi, then lo), in
+// float-float arithmetic on the FP32 pipe; part: splits * S * K doubles of scratch (splits from
+// kl_transpose_splits)
+int kl_transpose_splits(int S, int K, int num_sms);
+cudaError_t launch_kl_transpose_ff(GridBasis& gb, int S, const float* wff, double* part, int splits, double* out,
+                                   cudaStream_t st);
 // stencil / solver (solver.cu)
 struct SolveGroup {
     int n = 0;             // solve grid
@@ -273,8 +279,9 @@ cudaError_t launch_level_stats(int S, const double* Qf, const double* Qc, mlmc_a
 cudaError_t launch_field_range(int S, int V, long long ld, const void* a, int a_fp64, double* out_dev,
                                cudaStream_t st);
 // adjoint.cu
+// w = a_v G_v as float-float rows [2][S][(n+1)^2] (hi rows, then lo rows)
 cudaError_t launch_adjoint_elements(int n, int S, const void* a, int a_fp64, const double* u,
-                                    const double* lam, double* G, cudaStream_t st);
+                                    const double* lam, float* wff, cudaStream_t st);
 
 // The context's device error words (api.cpp): synchronises `st`, reads and clears
 // them; MLMC_OK, or MLMC_E_TIMEOUT when a bounded wait of a synthesis or a solve ran out
