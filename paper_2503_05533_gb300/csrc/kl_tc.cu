@@ -43,8 +43,9 @@
 // and a column one sample.  Warp 0 streams the operand slices of every 64-term
 // K block by TMA (128-byte swizzle) through a ring of shared-memory stages;
 // warp 1 issues the MMAs (M = 128, N = TN, K = 16) into one of two tensor-
-// memory buffers and signals through mbarriers; TN / 8 epilogue warps drain
-// the other buffer (each warp 32 sample columns of one TMEM lane quarter).
+// memory buffers and signals through mbarriers; 16 epilogue warps drain the
+// other buffer (each warp 32 sample columns of one TMEM lane quarter in the
+// FP32 form, 16 in the FP64 form).
 // Loads of tile t+1 and the epilogue of tile t overlap its MMAs.  Output rows
 // (one per sample) are `ldo` elements apart.  When they are whole 128-byte
 // lines (ldo a multiple of 32, aligned base: the layout the estimate uses),
@@ -79,20 +80,21 @@ constexpr int kStgPitch = TM + 4;           // floats per staging row (528 bytes
 // MODE 2: the same into rows of whole 128-byte lines, stored straight from registers (a third TMA stage
 // in place of the staging area); MODE 1: FP64 output (3 slices, exact lead).
 template <int MODE> struct KLCfg;
-// Warp 0 issues the TMA copies, warp 1 the MMAs; EW = TN / 8 epilogue warps follow, each draining one
-// 32-column chunk of one TMEM lane quarter (its warp index mod 4).
+// Warp 0 issues the TMA copies, warp 1 the MMAs; EW = 4 TN / CW epilogue warps follow, each draining one
+// CW-column chunk of one TMEM lane quarter (its warp index mod 4).  The FP64 form's long per-element
+// epilogue takes 16-column chunks, so that twice as many warps hide its latency.
 template <> struct KLCfg<0> {
-    static constexpr int NA = 2, NB = 2, TN = 128, NACC = 2, NSTAGE = 2, EW = TN / 8;
+    static constexpr int NA = 2, NB = 2, TN = 128, NACC = 2, NSTAGE = 2, CW = 32, EW = 4 * TN / CW;
     static constexpr bool DRAIN = false;   // accumulate the whole K range in TMEM
     using Out = float;
 };
 template <> struct KLCfg<2> {
-    static constexpr int NA = 2, NB = 2, TN = 128, NACC = 2, NSTAGE = 3, EW = TN / 8;
+    static constexpr int NA = 2, NB = 2, TN = 128, NACC = 2, NSTAGE = 3, CW = 32, EW = 4 * TN / CW;
     static constexpr bool DRAIN = false;
     using Out = float;
 };
 template <> struct KLCfg<1> {
-    static constexpr int NA = 3, NB = 3, TN = 64, NACC = 3, NSTAGE = 3, EW = TN / 8;
+    static constexpr int NA = 3, NB = 3, TN = 64, NACC = 3, NSTAGE = 3, CW = 16, EW = 4 * TN / CW;
     static constexpr bool DRAIN = true;    // the epilogue drains every K block
     using Out = double;
 };
@@ -169,6 +171,14 @@ __device__ __forceinline__ void tmem_ld_x32(uint32_t taddr, uint32_t (&r)[32]) {
           "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15]),
           "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]),
           "=r"(r[24]), "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
+        : "r"(taddr));
+}
+__device__ __forceinline__ void tmem_ld_x16(uint32_t taddr, uint32_t (&r)[16]) {
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x16.b32 "
+        "{%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, %15}, [%16];"
+        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+          "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
         : "r"(taddr));
 }
 // 2^x by the SFU's approximation (maximum relative error about 2^-22).
@@ -488,7 +498,7 @@ __global__ void __launch_bounds__(KLLayout<MODE>::kThreads, 1)
             tile_coords(t, num_st, num_tiles / num_st, tile_group, st_, nt_);
             const int s0 = st_ * TN, v0 = nt_ * TM;
             const int v = v0 + q4 * 32 + lane;       // this lane's node
-            const int sc0 = s0 + c * 32;             // the chunk's first sample
+            const int sc0 = s0 + c * C::CW;          // the chunk's first sample
             if constexpr (MODE != 1) {
                 // Output rows (one per sample) are `ldo` elements apart.  When ldo is a multiple of 32 and
                 // the output starts on a 128-byte boundary, every 32-node piece of a row is one full line:
@@ -500,7 +510,7 @@ __global__ void __launch_bounds__(KLLayout<MODE>::kThreads, 1)
                 uint32_t r0[32], r1[32];
                 if (ok) {
                     tc_fence_after();
-                    const uint32_t base = tmem + lane_base + (uint32_t)(tb * C::NACC * TN + c * 32);
+                    const uint32_t base = tmem + lane_base + (uint32_t)(tb * C::NACC * TN + c * C::CW);
                     tmem_ld_x32(base, r0);
                     tmem_ld_x32(base + (uint32_t)TN, r1);
                     tmem_wait_ld();
@@ -572,10 +582,10 @@ __global__ void __launch_bounds__(KLLayout<MODE>::kThreads, 1)
                     }
                 }
             } else {
-                int s0i[32];        // sum over K blocks of E0 (exact integers)
-                float s1f[32];      // sum over K blocks of E1 + 2^-11 E2
+                int s0i[C::CW];        // sum over K blocks of E0 (exact integers)
+                float s1f[C::CW];      // sum over K blocks of E1 + 2^-11 E2
 #pragma unroll
-                for (int j = 0; j < 32; ++j) {
+                for (int j = 0; j < C::CW; ++j) {
                     s0i[j] = 0;
                     s1f[j] = 0.0f;
                 }
@@ -586,11 +596,11 @@ __global__ void __launch_bounds__(KLLayout<MODE>::kThreads, 1)
                         break;
                     }
                     tc_fence_after();
-                    const uint32_t base = tmem + lane_base + (uint32_t)(tb * C::NACC * TN + c * 32);
-                    uint32_t r0[32], r1[32], r2[32];
-                    tmem_ld_x32(base, r0);
-                    tmem_ld_x32(base + (uint32_t)TN, r1);
-                    tmem_ld_x32(base + (uint32_t)(2 * TN), r2);
+                    const uint32_t base = tmem + lane_base + (uint32_t)(tb * C::NACC * TN + c * C::CW);
+                    uint32_t r0[C::CW], r1[C::CW], r2[C::CW];
+                    tmem_ld_x16(base, r0);
+                    tmem_ld_x16(base + (uint32_t)TN, r1);
+                    tmem_ld_x16(base + (uint32_t)(2 * TN), r2);
                     tmem_wait_ld();
                     tc_fence_before();
                     __syncwarp();
@@ -600,7 +610,7 @@ __global__ void __launch_bounds__(KLLayout<MODE>::kThreads, 1)
                         tphase ^= 1u;
                     }
 #pragma unroll
-                    for (int j = 0; j < 32; ++j) {
+                    for (int j = 0; j < C::CW; ++j) {
                         s0i[j] += __float2int_rn(__uint_as_float(r0[j]));
                         s1f[j] = __fmaf_rn(__uint_as_float(r2[j]), 1.0f / 2048.0f,
                                            __fadd_rn(s1f[j], __uint_as_float(r1[j])));
@@ -611,9 +621,9 @@ __global__ void __launch_bounds__(KLLayout<MODE>::kThreads, 1)
                 // lane l holds the exponent of sample sc0 + l; sample j's is taken from lane j
                 const int esl = es[min(sc0 + lane, Spad - 1)];
                 Out* p = out + (size_t)sc0 * ldo + v;
-                const int jend = min(32, S - sc0);
+                const int jend = min(C::CW, S - sc0);
 #pragma unroll
-                for (int j = 0; j < 32; ++j, p += ldo) {
+                for (int j = 0; j < C::CW; ++j, p += ldo) {
                     const int sc = __shfl_sync(0xffffffffu, esl, j) + evv - 18;
                     // float-float of the integer sum (up to 2^26) plus the FP32 correction sum
                     const int ii = s0i[j];
