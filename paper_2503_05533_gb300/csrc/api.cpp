@@ -1076,15 +1076,37 @@ mlmc_status mlmc_estimate(mlmc_ctx* ctx, const mlmc_options* opts, mlmc_result* 
             const mlmc_status s = run_solve_batches(ctx, batches, st);
             if (s != MLMC_OK) return s;
         }
+        // ---- read-back: level statistics, iterations and flags of every solve, and the device error words,
+        // with one synchronisation (a retry below, rare, reads back again)
+        mlmc_acc* dacc = ctx->ws.misc.as<mlmc_acc>();
+        std::vector<int32_t> hit(4 * qn);   // itf, itc, flf, flc
+        auto read_back = [&]() -> mlmc_status {
+            for (size_t i = 0; i < req.size(); ++i) {
+                MLMC_CUDA_RET(ctx->err, launch_level_stats(req[i].count, Qf + qoff[i],
+                                                            req[i].level > 0 ? Qc + qoff[i] : nullptr, dacc + i, st));
+            }
+            unsigned w[2] = {0u, 0u};
+            MLMC_CUDA_RET(ctx->err, cudaMemcpyAsync(out.data(), dacc, sizeof(mlmc_acc) * req.size(),
+                                                    cudaMemcpyDeviceToHost, st));
+            MLMC_CUDA_RET(ctx->err,
+                          cudaMemcpyAsync(hit.data(), itf, 4 * qn * sizeof(int32_t), cudaMemcpyDeviceToHost, st));
+            MLMC_CUDA_RET(ctx->err, cudaMemcpyAsync(w, ctx->kl_err, sizeof(w), cudaMemcpyDeviceToHost, st));
+            MLMC_CUDA_RET(ctx->err, cudaStreamSynchronize(st));
+            ctx->prof.acc.d2h_bytes += (int64_t)(sizeof(mlmc_acc) * req.size() + 4 * qn * sizeof(int32_t));
+            if (w[0] != 0u || w[1] != 0u) return check_device_errors(ctx, st);   // clears them, reports
+            return MLMC_OK;
+        };
+        {
+            const mlmc_status s = read_back();
+            if (s != MLMC_OK) return s;
+        }
         // ---- Cor. 3.4 safety net: the low-precision conditions can fail for a sample
         // whose coefficient is rougher than the precision rule assumed; a refinement
         // that stagnated or ran out of iterations is re-run with FP64 inner arithmetic
         // to the same delta (Alg. 2.1 with u_f = u), in one more launch.
         if (o.form == MLMC_FORM_MIXED && classes.size() > (classes.count(MLMC_FP64) ? 1u : 0u)) {
-            std::vector<int32_t> hfl(2 * qn), hit2(2 * qn);
-            MLMC_CUDA_RET(ctx->err, cudaMemcpy(hfl.data(), flf, 2 * qn * sizeof(int32_t), cudaMemcpyDeviceToHost));
-            MLMC_CUDA_RET(ctx->err, cudaMemcpy(hit2.data(), itf, 2 * qn * sizeof(int32_t), cudaMemcpyDeviceToHost));
-            ctx->prof.acc.d2h_bytes += (int64_t)(4 * qn * sizeof(int32_t));
+            const int32_t* hfl = hit.data() + 2 * qn;   // fine then coarse flags
+            const int32_t* hit2 = hit.data();           // fine then coarse iterations
             std::vector<SolveGroup> retry;
             for (auto& kv : classes) {
                 if (kv.first == MLMC_FP64) continue;   // FP64 inner (or the dddd Cholesky)
@@ -1118,24 +1140,10 @@ mlmc_status mlmc_estimate(mlmc_ctx* ctx, const mlmc_options* opts, mlmc_result* 
                 cfg.max_iters = o.max_iters;
                 const mlmc_status s = run_solve_batch(ctx, retry, cfg, st);
                 if (s != MLMC_OK) return s;
+                const mlmc_status s2 = read_back();   // the statistics of the re-run samples
+                if (s2 != MLMC_OK) return s2;
             }
         }
-        {
-            const mlmc_status s = check_device_errors(ctx, st);
-            if (s != MLMC_OK) return s;
-        }
-        // ---- level statistics of the batch
-        mlmc_acc* dacc = ctx->ws.misc.as<mlmc_acc>();
-        for (size_t i = 0; i < req.size(); ++i) {
-            MLMC_CUDA_RET(ctx->err, launch_level_stats(req[i].count, Qf + qoff[i],
-                                                        req[i].level > 0 ? Qc + qoff[i] : nullptr, dacc + i, st));
-        }
-        MLMC_CUDA_RET(ctx->err, cudaMemcpyAsync(out.data(), dacc, sizeof(mlmc_acc) * req.size(),
-                                                cudaMemcpyDeviceToHost, st));
-        std::vector<int32_t> hit(4 * qn);
-        MLMC_CUDA_RET(ctx->err, cudaMemcpyAsync(hit.data(), itf, 4 * qn * sizeof(int32_t), cudaMemcpyDeviceToHost, st));
-        MLMC_CUDA_RET(ctx->err, cudaStreamSynchronize(st));
-        ctx->prof.acc.d2h_bytes += (int64_t)(sizeof(mlmc_acc) * req.size() + 4 * qn * sizeof(int32_t));
         for (size_t i = 0; i < req.size(); ++i) {
             for (int s = 0; s < req[i].count; ++s) {
                 const size_t q = qoff[i] + s;
