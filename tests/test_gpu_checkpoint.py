@@ -98,3 +98,24 @@ def test_forced_allocation_failure(M):
         assert np.all(fl.cpu().numpy() == M.MLMC_F_CONVERGED)
     finally:
         M.mlmc_debug_fail_allocation(-1)
+
+
+def test_set_seed_reuses_the_context(M):
+    # a new Philox key on a live context gives exactly the estimate of a context created with that key
+    h = M.mlmc_create(M.make_problem(**WL), 0)
+    try:
+        r1 = M.result_dict(M.mlmc_estimate(h, _opts(M)))
+        M.mlmc_set_seed(h, WL["seed"] + 1)
+        r2 = M.result_dict(M.mlmc_estimate(h, _opts(M)))
+        M.mlmc_set_seed(h, WL["seed"])
+        r3 = M.result_dict(M.mlmc_estimate(h, _opts(M)))
+    finally:
+        M.mlmc_destroy(h)
+    h = M.mlmc_create(M.make_problem(**dict(WL, seed=WL["seed"] + 1)), 0)
+    try:
+        r2f = M.result_dict(M.mlmc_estimate(h, _opts(M)))
+    finally:
+        M.mlmc_destroy(h)
+    assert r3["Yhat"] == r1["Yhat"] and r3["N"] == r1["N"]
+    assert r2f["Yhat"] == r2["Yhat"] and r2f["N"] == r2["N"]
+    assert r2["Yhat"] != r1["Yhat"]
