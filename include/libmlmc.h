@@ -470,6 +470,22 @@ mlmc_status mlmc_set_inner_tolerance(mlmc_ctx* ctx, double theta, double tau_min
  * results agree to the solve tolerance whatever is chosen.  A launch that
  * tunes synchronises its stream (mlmc_level_solve included). */
 mlmc_status mlmc_set_autotune(mlmc_ctx* ctx, int on);
+
+/* Samples solved ahead in mlmc_estimate (on = 1, the default; 0 off).  A round
+ * of Alg. 4.1 also solves, on each of its levels, the next samples up to the
+ * count that level ended with in the last estimate on this context, as long as
+ * they add at most a tenth of the round's unknowns; they run beside the round's
+ * own solves, on SMs the finest level's few large systems leave idle.  If the
+ * next round asks for them (same delta and precision class), it takes their
+ * QoIs, iteration counts and flags instead of solving again.  The result does
+ * not depend on it: a sample's field and solve do not depend on the batch it is
+ * solved in (with the autotuner off; with it on, each launch shape's chosen
+ * settings apply, as for any batch), the level statistics are taken over
+ * exactly the samples each round asks for, and every counter of a sample counts
+ * in the round that asks for it.  Levels with a member whose thread-group size
+ * follows the rest of its launch (91 <= n <= 128) are not solved ahead,
+ * nor is anything with fixed_N or under the calibrated precision rule. */
+mlmc_status mlmc_set_sample_ahead(mlmc_ctx* ctx, int on);
 typedef struct {
     char shape[192];       /* the launch shape, as text                                        */
     int prec, solver, precond;

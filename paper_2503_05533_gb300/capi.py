@@ -112,6 +112,7 @@ _SIGS = {
                                   c_void_p]),
     "mlmc_set_wait_timeout": (c_int, [c_void_p, c_double]),
     "mlmc_set_autotune": (c_int, [c_void_p, c_int]),
+    "mlmc_set_sample_ahead": (c_int, [c_void_p, c_int]),
     "mlmc_set_cholesky_precision": (c_int, [c_void_p, c_int, c_int]),
     "mlmc_autotune_count": (c_int, [c_void_p]),
     "mlmc_autotune_entry": (c_int, [c_void_p, c_int, c_void_p]),
@@ -227,6 +228,10 @@ def mlmc_set_cholesky_precision(ctx, u, u_r):
 
 def mlmc_set_autotune(ctx, on=True):
     _check(lib().mlmc_set_autotune(ctx, 1 if on else 0), ctx)
+
+
+def mlmc_set_sample_ahead(ctx, on=True):
+    _check(lib().mlmc_set_sample_ahead(ctx, 1 if on else 0), ctx)
 
 
 def mlmc_autotune_count(ctx):

@@ -531,6 +531,7 @@ void mlmc_destroy(mlmc_ctx* ctx) {
         kv.second.phi64.release();
         kv.second.phi16.release();
         kv.second.phix.release();
+        kv.second.phiff.release();
         kv.second.ev.release();
     }
     for (auto& p : ctx->prof.kl_pending) {
@@ -545,7 +546,7 @@ void mlmc_destroy(mlmc_ctx* ctx) {
         }
     Workspace& w = ctx->ws;
     for (DevBuf& b : w.solver_slot) b.release();
-    for (DevBuf* b : {&w.fields, &w.xi, &w.q, &w.misc, &w.split, &w.adj}) b->release();
+    for (DevBuf* b : {&w.fields, &w.xi, &w.q, &w.misc, &w.split, &w.adj, &w.chol, &w.ahead}) b->release();
     if (w.pinned) cudaFreeHost(w.pinned);
     if (ctx->kl_err) cudaFree(ctx->kl_err);
     if (ctx->order_ev) cudaEventDestroy(ctx->order_ev);
@@ -663,6 +664,12 @@ mlmc_status mlmc_set_cholesky_precision(mlmc_ctx* ctx, mlmc_prec u, mlmc_prec u_
                                      "(FP32, FP32) or (FP16S, FP16S)");
     ctx->chol_u = u;
     ctx->chol_ur = u_r;
+    return MLMC_OK;
+}
+
+mlmc_status mlmc_set_sample_ahead(mlmc_ctx* ctx, int on) {
+    if (!ctx || (on != 0 && on != 1)) return MLMC_E_ARG;
+    ctx->sample_ahead = on != 0;
     return MLMC_OK;
 }
 
@@ -922,6 +929,31 @@ mlmc_status mlmc_estimate(mlmc_ctx* ctx, const mlmc_options* opts, mlmc_result* 
     const bool calibrate = o.prec_rule == 1 && o.form == MLMC_FORM_MIXED && o.solver != MLMC_CHOLESKY &&
                            o.force_prec < 0;
 
+    // Samples solved ahead of the round that asks for them.  A round's launches leave SMs to spare beside
+    // the finest level's few large systems, so extra samples of the cheap levels, which the next round of
+    // Alg. 4.1 will probably ask for, cost little there; that round then copies their QoIs instead of
+    // synthesising fields and launching solves, and saves its launch latencies.  How many: up to the
+    // sample counts the last estimate on this context ended with, within a tenth of the round's unknowns.
+    // A wrong guess costs time, never a result: a sample's field and solve do not depend on the batch it
+    // is in, the level statistics cover exactly the range each round asks for, and the counters of a
+    // sample count in the round that asks for it.  They are kept for one round, and used only if that
+    // round solves their level to the same delta in the same precision class.
+    struct Ahead {
+        bool valid = false;
+        int64_t first = 0;
+        int count = 0;
+        double df = 0.0, dc = 0.0;
+        int cls_f = -1, cls_c = -1;
+        size_t qoff = 0;   // their rows in the ahead buffer: Qf at 2 qoff, Qc at 2 qoff + count (doubles)
+        std::vector<int32_t> it_f, it_c, fl_f, fl_c;   // final iterations and flags of each sample
+        std::vector<int64_t> abandoned;                // iterations of low-precision attempts retried in FP64
+        std::vector<int32_t> retried;
+    };
+    std::vector<Ahead> ahead(MLMC_MAX_LEVELS);
+    // not with fixed sample counts (one round), nor under the calibrated rule (whose precision choice
+    // depends on the fields of each round)
+    const bool use_ahead = ctx->sample_ahead && !o.fixed_N && !calibrate;
+
     RoundFn round = [&](const std::vector<Request>& req, const std::vector<double>& df, const std::vector<double>& dc,
                         std::vector<mlmc_acc>& out, mlmc_result*) -> mlmc_status {
         const NvtxRange range_round("mlmc round");
@@ -960,21 +992,76 @@ mlmc_status mlmc_estimate(mlmc_ctx* ctx, const mlmc_options* opts, mlmc_result* 
             else w = g <= 1 ? 1 : 0;
             return p | (w << 4);
         };
-        size_t fbytes = 0, xbytes = 0, qn = 0;
-        std::vector<size_t> foff(req.size()), xoff(req.size()), qoff(req.size());
         // each field row padded to whole 128-byte lines (32 elements), so that the synthesis writes full lines
         auto fpitch = [&](int l) -> long long {
             const int n = level_n(p, l);
             return ((long long)(n + 1) * (n + 1) + 31) / 32 * 32;
         };
+        // ---- samples of each request already solved ahead (previous round), and new ones to solve ahead
+        std::vector<int> used(req.size(), 0);
         for (size_t i = 0; i < req.size(); ++i) {
-            foff[i] = fbytes;
-            fbytes += (size_t)req[i].count * (size_t)fpitch(req[i].level) * felem;
-            fbytes = (fbytes + 255) / 256 * 256;
-            xoff[i] = xbytes;
-            xbytes += (size_t)req[i].count * K * sizeof(double);
+            const int l = req[i].level;
+            const Ahead& a = ahead[l];
+            if (a.valid && a.first == req[i].first && a.df == df[l] && a.cls_f == class_of(l, l) &&
+                (l == 0 || (a.dc == dc[l] && a.cls_c == class_of(l - 1, l))))
+                used[i] = std::min(req[i].count, a.count);
+        }
+        // the work of the round: what each request still needs, then the samples solved ahead (req < 0)
+        struct Work {
+            int level;
+            int64_t first;
+            int count;
+            int req;
+        };
+        std::vector<Work> work;
+        for (size_t i = 0; i < req.size(); ++i)
+            work.push_back({req[i].level, req[i].first + used[i], req[i].count - used[i], (int)i});
+        auto unknowns = [&](int l) {
+            const double n = level_n(p, l), nc = n / p.m;
+            return (n - 1) * (n - 1) + (l > 0 ? (nc - 1) * (nc - 1) : 0.0);
+        };
+        // whether a level's solves are the same in any batch: not if a member's group size follows the
+        // rest of its launch (the per-launch group choice)
+        auto batch_free = [&](int l) {
+            const int n = level_n(p, l);
+            auto fixed = [](int k) { return size_class(k, kMedItems) == size_class(k, kMedItemsWide); };
+            return fixed(n) && (l == 0 || fixed(n / p.m));
+        };
+        if (use_ahead) {
+            // up to the sample counts of the last estimate, within a tenth of the round's unknowns
+            double budget = 0.0;
+            for (const Request& r : req) budget += 0.1 * r.count * unknowns(r.level);
+            for (const Request& r : req) {
+                if (!batch_free(r.level)) continue;
+                const int64_t end = r.first + r.count;
+                const int64_t want = ctx->ahead_hint[r.level] - end;
+                const int64_t fit = (int64_t)(budget / unknowns(r.level));
+                const int extra = (int)std::min<int64_t>(std::min(want, fit), 1 << 30);
+                if (extra <= 0) continue;
+                budget -= extra * unknowns(r.level);
+                work.push_back({r.level, end, extra, -1});
+            }
+        }
+        // QoI rows: every request's whole range (solved-ahead part first), then the samples solved ahead
+        size_t fbytes = 0, xbytes = 0, qn = 0;
+        std::vector<size_t> qoff(req.size());
+        for (size_t i = 0; i < req.size(); ++i) {
             qoff[i] = qn;
             qn += (size_t)req[i].count;
+        }
+        std::vector<size_t> foff(work.size()), xoff(work.size()), wq(work.size());
+        for (size_t w = 0; w < work.size(); ++w) {
+            foff[w] = fbytes;
+            fbytes += (size_t)work[w].count * (size_t)fpitch(work[w].level) * felem;
+            fbytes = (fbytes + 255) / 256 * 256;
+            xoff[w] = xbytes;
+            xbytes += (size_t)work[w].count * K * sizeof(double);
+            if (work[w].req >= 0) {
+                wq[w] = qoff[work[w].req] + used[work[w].req];
+            } else {
+                wq[w] = qn;
+                qn += (size_t)work[w].count;
+            }
         }
         MLMC_CUDA_RET(ctx->err, ctx->ws.fields.reserve(fbytes));
         MLMC_CUDA_RET(ctx->err, ctx->ws.xi.reserve(std::max<size_t>(xbytes, 8)));
@@ -994,30 +1081,44 @@ mlmc_status mlmc_estimate(mlmc_ctx* ctx, const mlmc_options* opts, mlmc_result* 
         MLMC_CUDA_RET(ctx->err, cudaMemsetAsync(Qc, 0, qn * sizeof(double), st));
         MLMC_CUDA_RET(ctx->err, cudaMemsetAsync(itc, 0, qn * sizeof(int32_t), st));
         MLMC_CUDA_RET(ctx->err, cudaMemsetAsync(flc, 0, qn * sizeof(int32_t), st));
-        // ---- fields of every request
+        // ---- QoIs of the samples solved ahead, into their requests' rows
         for (size_t i = 0; i < req.size(); ++i) {
+            if (!used[i]) continue;
+            const Ahead& a = ahead[req[i].level];
+            const double* src = ctx->ws.ahead.as<double>() + 2 * a.qoff;
+            MLMC_CUDA_RET(ctx->err, cudaMemcpyAsync(Qf + qoff[i], src, used[i] * sizeof(double),
+                                                    cudaMemcpyDeviceToDevice, st));
+            if (req[i].level > 0)
+                MLMC_CUDA_RET(ctx->err, cudaMemcpyAsync(Qc + qoff[i], src + a.count, used[i] * sizeof(double),
+                                                        cudaMemcpyDeviceToDevice, st));
+        }
+        // ---- fields of the work
+        for (size_t w = 0; w < work.size(); ++w) {
+            if (work[w].count == 0) continue;
             const NvtxRange range_fields("fields");
-            const mlmc_status s = mlmc_sample_fields(ctx, req[i].level, (uint64_t)req[i].first, req[i].count,
-                                                     xb + xoff[i] / sizeof(double), fb + foff[i],
-                                                     fpitch(req[i].level), field_prec, (void*)st);
+            const mlmc_status s = mlmc_sample_fields(ctx, work[w].level, (uint64_t)work[w].first, work[w].count,
+                                                     xb + xoff[w] / sizeof(double), fb + foff[w],
+                                                     fpitch(work[w].level), field_prec, (void*)st);
             if (s != MLMC_OK) return s;
         }
-        // ---- calibrated rule: the contrast of every new field, per level
+        // ---- calibrated rule: the contrast of every new field, per level (no samples are solved ahead
+        // under this rule, so the work is the requests)
         if (calibrate) {
             double* rng = ctx->ws.misc.as<double>();
-            for (size_t i = 0; i < req.size(); ++i) {
-                const int n = level_n(p, req[i].level);
-                MLMC_CUDA_RET(ctx->err, launch_field_range(req[i].count, (n + 1) * (n + 1), fpitch(req[i].level), fb + foff[i],
-                                                           field_prec != MLMC_FP32, rng + 2 * qoff[i], st));
+            for (size_t w = 0; w < work.size(); ++w) {
+                const int n = level_n(p, work[w].level);
+                MLMC_CUDA_RET(ctx->err, launch_field_range(work[w].count, (n + 1) * (n + 1), fpitch(work[w].level),
+                                                           fb + foff[w], field_prec != MLMC_FP32, rng + 2 * wq[w],
+                                                           st));
             }
             std::vector<double> hr(2 * qn);
             MLMC_CUDA_RET(ctx->err, cudaMemcpyAsync(hr.data(), rng, 2 * qn * sizeof(double), cudaMemcpyDeviceToHost, st));
             MLMC_CUDA_RET(ctx->err, cudaStreamSynchronize(st));
             ctx->prof.acc.d2h_bytes += (int64_t)(2 * qn * sizeof(double));
-            for (size_t i = 0; i < req.size(); ++i) {
-                const int l = req[i].level;
-                for (int k = 0; k < req[i].count; ++k) {
-                    const double lo = hr[2 * (qoff[i] + k)], hi = hr[2 * (qoff[i] + k) + 1];
+            for (size_t w = 0; w < work.size(); ++w) {
+                const int l = work[w].level;
+                for (int k = 0; k < work[w].count; ++k) {
+                    const double lo = hr[2 * (wq[w] + k)], hi = hr[2 * (wq[w] + k) + 1];
                     cal_amin[l] = std::min(cal_amin[l], lo);
                     cal_amax[l] = std::max(cal_amax[l], hi);
                     if (lo > 0) cal_contrast[l] = std::max(cal_contrast[l], hi / lo);
@@ -1026,35 +1127,34 @@ mlmc_status mlmc_estimate(mlmc_ctx* ctx, const mlmc_options* opts, mlmc_result* 
         }
         // ---- one resident-solve launch per inner-precision class: every fine and coarse member
         std::map<int, std::vector<SolveGroup>> classes;
-        std::map<int, std::vector<int>> class_level;   // level of each group, for the counters
-        for (size_t i = 0; i < req.size(); ++i) {
-            const int l = req[i].level;
+        std::map<int, std::vector<int>> class_work;   // work item of each group, for the counters
+        for (const Request& r : req) prec_lvl[r.level] = prec_of(r.level);
+        for (size_t w = 0; w < work.size(); ++w) {
+            if (work[w].count == 0) continue;
+            const int l = work[w].level;
             const int n = level_n(p, l);
             SolveGroup gf;
             gf.n = n;
-            gf.S = req[i].count;
-            gf.a = fb + foff[i];
+            gf.S = work[w].count;
+            gf.a = fb + foff[w];
             gf.a_fp64 = field_prec != MLMC_FP32;
             gf.a_n = n;
             gf.a_ld = fpitch(l);
             gf.delta = df[l];
-            gf.Q = Qf + qoff[i];
-            gf.iters = itf + qoff[i];
-            gf.flags = flf + qoff[i];
+            gf.Q = Qf + wq[w];
+            gf.iters = itf + wq[w];
+            gf.flags = flf + wq[w];
             classes[class_of(l, l)].push_back(gf);
-            class_level[class_of(l, l)].push_back(l);
-            prec_lvl[l] = prec_of(l);
-            dofs_lvl[l] += (int64_t)req[i].count * (n - 1) * (n - 1);
+            class_work[class_of(l, l)].push_back((int)w);
             if (l > 0) {
                 SolveGroup gc = gf;
                 gc.n = n / p.m;
                 gc.delta = dc[l];
-                gc.Q = Qc + qoff[i];
-                gc.iters = itc + qoff[i];
-                gc.flags = flc + qoff[i];
+                gc.Q = Qc + wq[w];
+                gc.iters = itc + wq[w];
+                gc.flags = flc + wq[w];
                 classes[class_of(l - 1, l)].push_back(gc);
-                class_level[class_of(l - 1, l)].push_back(l);
-                dofs_lvl[l] += (int64_t)req[i].count * (gc.n - 1) * (gc.n - 1);
+                class_work[class_of(l - 1, l)].push_back((int)w);
             }
         }
         // the classes share no data: their launches run concurrently (the smaller ones fill the
@@ -1071,7 +1171,7 @@ mlmc_status mlmc_estimate(mlmc_ctx* ctx, const mlmc_options* opts, mlmc_result* 
             b.cfg.chol_ur = b.cfg.chol_u;
             batches.push_back(std::move(b));
         }
-        {
+        if (!batches.empty()) {
             const NvtxRange range_solves("solves");
             const mlmc_status s = run_solve_batches(ctx, batches, st);
             if (s != MLMC_OK) return s;
@@ -1100,6 +1200,9 @@ mlmc_status mlmc_estimate(mlmc_ctx* ctx, const mlmc_options* opts, mlmc_result* 
             const mlmc_status s = read_back();
             if (s != MLMC_OK) return s;
         }
+        // iterations of abandoned low-precision attempts and retry counts, per QoI row
+        std::vector<int64_t> abandoned(qn, 0);
+        std::vector<int32_t> retried(qn, 0);
         // ---- Cor. 3.4 safety net: the low-precision conditions can fail for a sample
         // whose coefficient is rougher than the precision rule assumed; a refinement
         // that stagnated or ran out of iterations is re-run with FP64 inner arithmetic
@@ -1110,7 +1213,6 @@ mlmc_status mlmc_estimate(mlmc_ctx* ctx, const mlmc_options* opts, mlmc_result* 
             std::vector<SolveGroup> retry;
             for (auto& kv : classes) {
                 if (kv.first == MLMC_FP64) continue;   // FP64 inner (or the dddd Cholesky)
-                const std::vector<int>& lv = class_level[kv.first];
                 for (size_t gi = 0; gi < kv.second.size(); ++gi) {
                     const SolveGroup& g = kv.second[gi];
                     const size_t elem = g.a_fp64 ? sizeof(double) : sizeof(float);
@@ -1128,8 +1230,11 @@ mlmc_status mlmc_estimate(mlmc_ctx* ctx, const mlmc_options* opts, mlmc_result* 
                         r.iters = g.iters + smp;
                         r.flags = g.flags + smp;
                         retry.push_back(r);
-                        iters_lvl[lv[gi]] += hit2[q];       // the abandoned attempt's iterations
-                        retries_lvl[lv[gi]] += 1;
+                        // the abandoned attempt's iterations (fine member's row q, coarse member's row q)
+                        const bool coarse = g.flags >= flc;
+                        const size_t row = coarse ? q - qn : q;
+                        abandoned[row] += hit2[q];
+                        retried[row] += 1;
                     }
                 }
             }
@@ -1144,13 +1249,60 @@ mlmc_status mlmc_estimate(mlmc_ctx* ctx, const mlmc_options* opts, mlmc_result* 
                 if (s2 != MLMC_OK) return s2;
             }
         }
+        // ---- counters of the requests: their samples solved ahead, then the rest
         for (size_t i = 0; i < req.size(); ++i) {
-            for (int s = 0; s < req[i].count; ++s) {
+            const int l = req[i].level;
+            const Ahead& a = ahead[l];
+            for (int s = 0; s < used[i]; ++s) {
+                iters_lvl[l] += a.abandoned[s] + a.it_f[s] + a.it_c[s];
+                retries_lvl[l] += a.retried[s];
+                flags_or |= a.fl_f[s];
+                if (l > 0) flags_or |= a.fl_c[s];
+            }
+            dofs_lvl[l] += (int64_t)req[i].count * (int64_t)unknowns(l);
+            for (int s = used[i]; s < req[i].count; ++s) {
                 const size_t q = qoff[i] + s;
-                iters_lvl[req[i].level] += hit[q] + hit[qn + q];
+                iters_lvl[l] += abandoned[q] + hit[q] + hit[qn + q];
+                retries_lvl[l] += retried[q];
                 const int32_t ff = hit[2 * qn + q], fc = hit[3 * qn + q];
                 flags_or |= ff;
-                if (req[i].level > 0) flags_or |= fc;
+                if (l > 0) flags_or |= fc;
+            }
+        }
+        // ---- keep this round's samples solved ahead for the next round (older ones are dropped)
+        for (Ahead& a : ahead) a.valid = false;
+        size_t an = 0;
+        for (const Work& wk : work)
+            if (wk.req < 0) an += (size_t)wk.count;
+        if (an) {
+            MLMC_CUDA_RET(ctx->err, ctx->ws.ahead.reserve(2 * an * sizeof(double)));
+            double* base = ctx->ws.ahead.as<double>();
+            size_t ao = 0;
+            for (size_t w = 0; w < work.size(); ++w) {
+                const Work& wk = work[w];
+                if (wk.req >= 0) continue;
+                const int l = wk.level;
+                const size_t q0 = wq[w], c = (size_t)wk.count;
+                Ahead& a = ahead[l];
+                a.valid = true;
+                a.first = wk.first;
+                a.count = wk.count;
+                a.df = df[l];
+                a.dc = l > 0 ? dc[l] : 0.0;
+                a.cls_f = class_of(l, l);
+                a.cls_c = l > 0 ? class_of(l - 1, l) : -1;
+                a.qoff = ao;
+                MLMC_CUDA_RET(ctx->err, cudaMemcpyAsync(base + 2 * ao, Qf + q0, c * sizeof(double),
+                                                        cudaMemcpyDeviceToDevice, st));
+                MLMC_CUDA_RET(ctx->err, cudaMemcpyAsync(base + 2 * ao + c, Qc + q0, c * sizeof(double),
+                                                        cudaMemcpyDeviceToDevice, st));
+                a.it_f.assign(hit.begin() + q0, hit.begin() + q0 + c);
+                a.it_c.assign(hit.begin() + qn + q0, hit.begin() + qn + q0 + c);
+                a.fl_f.assign(hit.begin() + 2 * qn + q0, hit.begin() + 2 * qn + q0 + c);
+                a.fl_c.assign(hit.begin() + 3 * qn + q0, hit.begin() + 3 * qn + q0 + c);
+                a.abandoned.assign(abandoned.begin() + q0, abandoned.begin() + q0 + c);
+                a.retried.assign(retried.begin() + q0, retried.begin() + q0 + c);
+                ao += c;
             }
         }
         return MLMC_OK;
@@ -1176,6 +1328,9 @@ mlmc_status mlmc_estimate(mlmc_ctx* ctx, const mlmc_options* opts, mlmc_result* 
     nvtxRangePop();
     MLMC_CUDA_RET(ctx->err, ctx_order_end(ctx, st));
     if (s != MLMC_OK) return s;
+    // the next estimate's samples to solve ahead
+    if (!o.fixed_N)
+        for (int l = 0; l < MLMC_MAX_LEVELS; ++l) ctx->ahead_hint[l] = l <= res->L ? res->N[l] : 0;
     for (int l = 0; l <= res->L; ++l) {
         res->prec[l] = prec_lvl[l];
         res->inner_iters[l] = iters_lvl[l];

@@ -63,6 +63,17 @@ struct GridBasis {
 constexpr int kSolveSlots = 4;   // solve batches that may run concurrently (one per precision class)
 constexpr int kTuneUnset = -3;   // a SolveConfig launch setting left to the context
 
+// Group size class of a resident solve's system: 2 a warp, 1 a 128-thread group, 0 a 512-thread CTA
+// (chunk items per thread stay around 8..32).  Systems with kMedItems < items <= kMedItemsWide take a
+// 128-thread group or a CTA depending on the rest of their launch (the per-launch group choice).
+constexpr int kMedItems = 2048, kMedItemsWide = 4096;
+inline int size_class(int n, int med_items = kMedItems) {
+    const long long items = (long long)(n - 1) * ((n - 1) / 4 + 1);
+    if (items <= 512) return 2;        // warp
+    if (items <= med_items) return 1;  // 128 threads
+    return 0;                          // 512 threads
+}
+
 // The autotuner's choice for one launch shape (see solver_common.cu): SolveConfig launch settings
 // (kTuneUnset / 0: the context's own) and the timings that chose them.
 struct TuneChoice {
@@ -86,6 +97,7 @@ struct Workspace {
     DevBuf split;          // split FP16 operands of the tensor-core synthesis
     DevBuf adj;            // adjoint path scratch
     DevBuf chol;           // Cholesky solver: band factors, iterates, descriptors
+    DevBuf ahead;          // estimate loop: QoIs of samples solved ahead of their round (Qf, Qc per level)
     void* pinned = nullptr;    // pinned host staging
     size_t pinned_bytes = 0;
 };
@@ -136,6 +148,10 @@ struct mlmc_ctx {
     bool autotune = false;        // time candidate launch settings for every new launch shape
     std::map<std::string, mlmc::TuneChoice> tune;   // launch shape -> chosen settings
     std::vector<std::string> tune_order;            // keys in the order they were tuned
+    // estimate loop: solve samples ahead of the round that asks for them (mlmc_set_sample_ahead), up to
+    // the sample counts the last estimate on this context ended with
+    bool sample_ahead = true;
+    int64_t ahead_hint[MLMC_MAX_LEVELS] = {};
 };
 
 namespace mlmc {

@@ -1822,15 +1822,6 @@ __global__ void __launch_bounds__(CTA, 1) resident_solve(Params P) {
     solve_system<VT, ST, SOLVER, G_SMALL>(P, P.solves[P.order[P.nbig + P.nmed + idx]], G, nullptr, nullptr);
 }
 
-// Group size class of a system: chunk items per thread stay around 8..32.
-constexpr int kMedItems = 2048, kMedItemsWide = 4096;
-int size_class(int n, int med_items = kMedItems) {
-    const long long items = (long long)(n - 1) * ((n - 1) / 4 + 1);
-    if (items <= 512) return 2;        // warp
-    if (items <= med_items) return 1;  // 128 threads
-    return 0;                          // 512 threads
-}
-
 size_t align_up(size_t v, size_t a) { return (v + a - 1) / a * a; }
 
 // ---------------------------------------------------------------------------

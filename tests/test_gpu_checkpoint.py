@@ -119,3 +119,35 @@ def test_set_seed_reuses_the_context(M):
     assert r3["Yhat"] == r1["Yhat"] and r3["N"] == r1["N"]
     assert r2f["Yhat"] == r2["Yhat"] and r2f["N"] == r2["N"]
     assert r2["Yhat"] != r1["Yhat"]
+
+
+_RESULT_KEYS = ("L", "rounds", "N", "Yhat", "s2", "estimate", "var_est", "rmse", "inner_iters", "dofs",
+                "fp64_retries", "prec", "flags_or")
+
+
+def _same(r, q):
+    return all(np.array_equal(np.asarray(r[k]), np.asarray(q[k])) for k in _RESULT_KEYS)
+
+
+@pytest.mark.parametrize("L_start,form", [(3, "MIXED"), (1, "MIXED"), (3, "FP64_ADAPTIVE")])
+def test_samples_solved_ahead_leave_the_estimate_unchanged(M, L_start, form):
+    # the second estimate on a context solves samples ahead of the rounds that ask for them (up to the
+    # first estimate's counts); it equals the first bit for bit, and so does one with it switched off
+    kw = dict(L_start=L_start, form=getattr(M, "MLMC_FORM_" + form))
+    h = M.mlmc_create(M.make_problem(**WL), 0)
+    try:
+        M.mlmc_profile_enable(h, True)
+        r1 = M.result_dict(M.mlmc_estimate(h, _opts(M, **kw)))
+        p1 = M.mlmc_profile_get(h)
+        M.mlmc_profile_reset(h)
+        r2 = M.result_dict(M.mlmc_estimate(h, _opts(M, **kw)))
+        p2 = M.mlmc_profile_get(h)
+        M.mlmc_set_sample_ahead(h, False)
+        r3 = M.result_dict(M.mlmc_estimate(h, _opts(M, **kw)))
+    finally:
+        M.mlmc_destroy(h)
+    assert r1["rounds"] >= 2
+    assert _same(r2, r1) and _same(r3, r1)
+    if L_start == 3:
+        # the finest level is fixed: the later rounds' samples were all solved in the first round
+        assert p2["solve_launches"] < p1["solve_launches"]
