@@ -69,11 +69,14 @@ def test_gradient_mixed_precision(M, prec):
     h = M.mlmc_create(M.make_problem(n0=16, m=2, L_max=0, kind=0, K=16, sigma2=1.0, corr_len=0.1, seed=0), 0)
     try:
         xi = np.random.default_rng(7).standard_normal((4, 16))
-        _, g = _grad(M, h, 0, xi, getattr(M, "MLMC_" + prec), 1e-9)
+        Q, g = _grad(M, h, 0, xi, getattr(M, "MLMC_" + prec), 1e-9)
         phi = o_kl.basis(0, 16, 16, 1.0, 0.1)
         for s in range(4):
-            _, go = o_adj.gradient(16, xi[s], phi)
-            assert np.max(np.abs(g[s] - go)) <= 1e-4 * np.max(np.abs(go))
+            # FP64 refinement to delta = 1e-9 around the low-precision inner solves, FP64 tensor-core field
+            # (about 1e-9 in log a): held to 1e-8 (observed about 6e-11)
+            Qo, go = o_adj.gradient(16, xi[s], phi)
+            assert abs(Q[s] - Qo) <= 1e-8 * abs(Qo)
+            assert np.max(np.abs(g[s] - go)) <= 1e-8 * np.max(np.abs(go))
     finally:
         M.mlmc_destroy(h)
 

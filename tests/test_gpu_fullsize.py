@@ -117,9 +117,10 @@ def test_adjoint_gradients_1024_samples_n256_box(M):
         phi = o_kl.basis(0, K, n, 1.0, 0.1)
         for s in (0, 511, 1023):
             Qo, go = o_adj.gradient(n, xi_np[s], phi, box)
-            # FP32 tensor-core field (about 1e-6 relative) and delta = 1e-8 solves
-            assert abs(Qg[s] - Qo) <= 1e-5 * abs(Qo)
-            assert np.max(np.abs(Gg[s] - go)) <= 1e-4 * np.max(np.abs(go))
+            # the mixed form's field is the FP64 tensor-core synthesis (about 1e-9 in log a) and the state and
+            # adjoint solves reach delta = 1e-8: QoI and gradient are held to delta (observed about 2e-10)
+            assert abs(Qg[s] - Qo) <= 1e-8 * abs(Qo)
+            assert np.max(np.abs(Gg[s] - go)) <= 1e-8 * np.max(np.abs(go))
     finally:
         M.mlmc_destroy(h)
 

@@ -377,7 +377,8 @@ def test_mixed_batch_many_sizes_one_launch(M):
             _, Q, _, _, fl = _solve(M, h, n, af, M.MLMC_FP32, n, M.MLMC_FP16S, 1e-7, u=False)
             assert np.all(fl == M.MLMC_F_CONVERGED)
             for s in range(3):
-                assert abs(Q[s] - o_fem.solve_sample(n, af[s])[1]) <= 1e-5 * abs(Q[s])
+                # FP32-exact coefficient, delta = 1e-7: held to 1e-6 (observed at most 1e-8)
+                assert abs(Q[s] - o_fem.solve_sample(n, af[s])[1]) <= 1e-6 * abs(Q[s])
     finally:
         M.mlmc_destroy(h)
 
