@@ -90,6 +90,10 @@ struct TuneChoice {
 
 struct Workspace {
     DevBuf solver_slot[kSolveSlots];   // solver scratch (vectors, descriptors), one per concurrent batch
+    // each slot's layout at its last launch (element sizes, array offsets, and per system its grid, row
+    // pitch and offsets), and the allocation it was laid out in
+    std::vector<long long> slot_layout[kSolveSlots];
+    void* slot_ptr[kSolveSlots] = {};
     DevBuf fields;         // coefficient fields of the estimate loop
     DevBuf xi;             // KL coefficients of the estimate loop
     DevBuf q;              // QoI values of the estimate loop

@@ -2155,8 +2155,30 @@ mlmc_status launch_typed(mlmc_ctx* ctx, const std::vector<SolveGroup>& groups, c
     mlmc::DevBuf& buf = ctx->ws.solver_slot[slot];
     MLMC_CUDA_RET(ctx->err, buf.reserve(L.total));
     char* base = buf.as<char>();
-    // vectors start at zero (boundary and padding entries stay zero forever)
-    MLMC_CUDA_RET(ctx->err, cudaMemsetAsync(base, 0, L.zero_end, st));
+    // Vectors start at zero.  Boundary and padding entries are never written and stay zero, and every
+    // interior entry except x (which the refinement accumulates) is written before it is read; so when
+    // the slot's last launch had this very layout, only x, the counters and the error word are cleared
+    // (the whole clear moved about 0.7 GB for the 5-level estimate's largest launch).
+    std::vector<long long> layout = {(long long)sizeof(VT), (long long)sizeof(ST), (long long)L.total};
+    for (size_t o : {L.o_x, L.o_r, L.o_p0, L.o_p1, L.o_d, L.o_as, L.o_dinv, L.o_vb, L.o_w0, L.o_w1, L.o_mz, L.o_mt,
+                     L.o_cx, L.o_ct, L.o_cb, L.o_cas, L.o_cdi, L.o_we, L.o_wn, L.o_stats, L.o_err, L.zero_end})
+        layout.push_back((long long)o);
+    for (const DevSolve& d : solves) {
+        layout.push_back(d.n);
+        layout.push_back(d.ld);
+        layout.push_back(d.off);
+        layout.push_back(d.mg_levels);
+        layout.push_back(d.mg_off);
+    }
+    if (buf.ptr == ctx->ws.slot_ptr[slot] && layout == ctx->ws.slot_layout[slot]) {
+        MLMC_CUDA_RET(ctx->err, cudaMemsetAsync(base + L.o_x, 0, L.o_r - L.o_x, st));
+        MLMC_CUDA_RET(ctx->err, cudaMemsetAsync(base + L.o_stats, 0, L.zero_end - L.o_stats, st));
+    } else {
+        ctx->ws.slot_ptr[slot] = nullptr;   // until the clear below is enqueued
+        MLMC_CUDA_RET(ctx->err, cudaMemsetAsync(base, 0, L.zero_end, st));
+        ctx->ws.slot_ptr[slot] = buf.ptr;
+        ctx->ws.slot_layout[slot] = std::move(layout);
+    }
     MLMC_CUDA_RET(ctx->err, cudaMemcpyAsync(base + L.o_solves, solves.data(), sizeof(DevSolve) * ns,
                                             cudaMemcpyHostToDevice, st));
     MLMC_CUDA_RET(ctx->err, cudaMemcpyAsync(base + L.o_order, order.data(), sizeof(int) * ns,

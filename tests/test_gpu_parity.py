@@ -688,3 +688,44 @@ def test_multigrid_depth_choices_meet_delta(M, mg_min, coarse):
     for s in range(S):
         x, Qo = o_fem.solve_sample(n, af[s])
         assert abs(Q[s] - Qo) <= 1.5 * delta * abs(Qo)
+
+
+@pytest.mark.parametrize("n,prec,solver,pc,ring", [
+    (160, "FP32", "CG", "MG", -1), (64, "FP16S", "CG", "MG", -1), (24, "FP32", "CG", "JACOBI", -1),
+    (160, "FP32", "MINRES", "MG", -1), (100, "FP64", "CG", "MG", -1), (128, "FP32", "CG", "JACOBI", 4),
+    (96, "BF16S", "MINRES", "JACOBI", -1)])
+def test_solve_in_a_reused_workspace_is_bit_identical(M, n, prec, solver, pc, ring):
+    # a batch solved in the workspace that another batch of the same shape has just used (its values left in
+    # place) gives bit for bit what a new context gives: nothing of a solve is read before it is written,
+    # except what the launch clears
+    S = 6
+    p = getattr(M, "MLMC_" + prec)
+    fa, fb = smooth_lognormal_field(n, S, seed=11), smooth_lognormal_field(n, S, seed=12)
+
+    def run(h, af):
+        dt = torch.float64 if p == M.MLMC_FP64 else torch.float32
+        a = to_dev(af, dt)
+        U = torch.zeros((S, (n + 1) ** 2), dtype=torch.float64, device=device())
+        Q = torch.empty(S, dtype=torch.float64, device=device())
+        it = torch.zeros(S, dtype=torch.int32, device=device())
+        rr = torch.zeros(S, dtype=torch.float64, device=device())
+        fl = torch.zeros(S, dtype=torch.int32, device=device())
+        M.mlmc_level_solve(h, n, S, a, M.MLMC_FP64 if p == M.MLMC_FP64 else M.MLMC_FP32, n, p,
+                           getattr(M, "MLMC_" + solver), 1e-9 if p == M.MLMC_FP64 else 1e-7, 200000, U, Q, it,
+                           rr, fl)
+        torch.cuda.synchronize()
+        return [x.cpu().numpy() for x in (U, Q, it, rr, fl)]
+
+    hs = [_ctx(M), _ctx(M)]
+    try:
+        for h in hs:
+            M.mlmc_set_precond(h, getattr(M, "MLMC_PC_" + pc))
+            M.mlmc_debug_set_solve_ring(h, ring)
+        run(hs[0], fa)
+        got, ref = run(hs[0], fb), run(hs[1], fb)
+        assert np.all(ref[4] == M.MLMC_F_CONVERGED)
+        for x, y in zip(got, ref):
+            assert np.array_equal(x.view(np.uint8), y.view(np.uint8))
+    finally:
+        for h in hs:
+            M.mlmc_destroy(h)
