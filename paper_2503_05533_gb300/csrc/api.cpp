@@ -547,7 +547,6 @@ void mlmc_destroy(mlmc_ctx* ctx) {
     Workspace& w = ctx->ws;
     for (DevBuf& b : w.solver_slot) b.release();
     for (DevBuf* b : {&w.fields, &w.xi, &w.q, &w.misc, &w.split, &w.adj, &w.chol, &w.ahead}) b->release();
-    if (w.pinned) cudaFreeHost(w.pinned);
     if (ctx->kl_err) cudaFree(ctx->kl_err);
     if (ctx->order_ev) cudaEventDestroy(ctx->order_ev);
     if (ctx->prof.t0) cudaEventDestroy(ctx->prof.t0);

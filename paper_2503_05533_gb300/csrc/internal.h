@@ -102,8 +102,6 @@ struct Workspace {
     DevBuf adj;            // adjoint path scratch
     DevBuf chol;           // Cholesky solver: band factors, iterates, descriptors
     DevBuf ahead;          // estimate loop: QoIs of samples solved ahead of their round (Qf, Qc per level)
-    void* pinned = nullptr;    // pinned host staging
-    size_t pinned_bytes = 0;
 };
 
 // Profiling state of a context (mlmc_profile_*).
