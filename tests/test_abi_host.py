@@ -183,6 +183,16 @@ def test_host_loop_rmse_hand_computed(L):
     assert r["var_est"] == pytest.approx(1.6e-7, rel=1e-12)
 
 
+def test_host_loop_sample_targets_hand_computed(L):
+    # level variances exactly 4e-4 and 1e-6 (alternating samples), TOL = 1.1e-3, m = 2, gamma = 2: the optimal
+    # counts are 728 and 19 (727.27 and 18.18 rounded up); level 1 keeps its 100 initial samples
+    o = L.mlmc_default_options()
+    o.tol, o.N_init, o.L_start = 1.1e-3, 100, 1
+    r = L.result_dict(L.mlmc_estimate_host(2, 1, 4, o, _Alternating([0.05, 0.0], [0.02, 0.001])))
+    assert r["N"] == [728, 100] and r["rounds"] == 2 and r["L"] == 1
+    assert r["var_est"] == pytest.approx(4e-4 / 728 + 1e-6 / 100, rel=1e-12)
+
+
 @pytest.mark.parametrize("cut", [1, 2, 3])
 def test_resume_from_checkpoint_equals_uninterrupted_run(L, tmp_path, cut):
     # Alg. 4.1 stopped after `cut` rounds, its result saved to disk, read back and resumed: the same samples

@@ -69,6 +69,14 @@ def test_optimal_samples_formula():
     assert np.sum(V / N) <= tol ** 2 / 2 * (1 + 1e-12)
 
 
+def test_optimal_samples_hand_computed():
+    # V = (4e-4, 1e-6), C = (1, 4) (m = 2, gamma = 2), TOL = 1.1e-3: sum sqrt(V C) = 0.02 + 0.002 = 0.022 and
+    # 2 / TOL^2 = 1652892.56, so N_0 = 0.02 * 1652892.56 * 0.022 = 727.27 -> 728 and
+    # N_1 = sqrt(1e-6 / 4) * 1652892.56 * 0.022 = 18.18 -> 19
+    N = mlmc.optimal_samples(np.array([4e-4, 1e-6]), np.array([1.0, 4.0]), 1.1e-3)
+    assert list(N) == [728, 19]
+
+
 class _MockSampler:
     """Y_l = mu_l + sd_l z with prescribed bias and variance decay (no PDE)."""
 
