@@ -472,9 +472,10 @@ mlmc_status mlmc_set_inner_tolerance(mlmc_ctx* ctx, double theta, double tau_min
 mlmc_status mlmc_set_autotune(mlmc_ctx* ctx, int on);
 
 /* Samples solved ahead in mlmc_estimate (on = 1, the default; 0 off).  A round
- * of Alg. 4.1 also solves, on each of its levels, the next samples up to the
- * count that level ended with in the last estimate on this context, as long as
- * they add at most a tenth of the round's unknowns; they run beside the round's
+ * of Alg. 4.1 also solves, on each of its levels that the last estimate on
+ * this context took further, the next samples up to 1.25 times the count that
+ * level ended with there, as long as they add at most a tenth of the round's
+ * unknowns; they run beside the round's
  * own solves, on SMs the finest level's few large systems leave idle.  If the
  * next round asks for them (same delta and precision class), it takes their
  * QoIs, iteration counts and flags instead of solving again.  The result does

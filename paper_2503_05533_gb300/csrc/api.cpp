@@ -546,7 +546,7 @@ void mlmc_destroy(mlmc_ctx* ctx) {
         }
     Workspace& w = ctx->ws;
     for (DevBuf& b : w.solver_slot) b.release();
-    for (DevBuf* b : {&w.fields, &w.xi, &w.q, &w.misc, &w.split, &w.adj, &w.chol, &w.ahead}) b->release();
+    for (DevBuf* b : {&w.fields, &w.xi, &w.q, &w.misc, &w.split, &w.adj, &w.chol, &w.ahead[0], &w.ahead[1]}) b->release();
     if (ctx->kl_err) cudaFree(ctx->kl_err);
     if (ctx->order_ev) cudaEventDestroy(ctx->order_ev);
     if (ctx->prof.t0) cudaEventDestroy(ctx->prof.t0);
@@ -931,24 +931,27 @@ mlmc_status mlmc_estimate(mlmc_ctx* ctx, const mlmc_options* opts, mlmc_result* 
     // Samples solved ahead of the round that asks for them.  A round's launches leave SMs to spare beside
     // the finest level's few large systems, so extra samples of the cheap levels, which the next round of
     // Alg. 4.1 will probably ask for, cost little there; that round then copies their QoIs instead of
-    // synthesising fields and launching solves, and saves its launch latencies.  How many: up to the
-    // sample counts the last estimate on this context ended with, within a tenth of the round's unknowns.
+    // synthesising fields and launching solves, and saves its launch latencies.  How many: up to 1.25 times
+    // the sample counts the last estimate on this context ended with, within a tenth of the round's
+    // unknowns.
     // A wrong guess costs time, never a result: a sample's field and solve do not depend on the batch it
     // is in, the level statistics cover exactly the range each round asks for, and the counters of a
-    // sample count in the round that asks for it.  They are kept for one round, and used only if that
-    // round solves their level to the same delta in the same precision class.
+    // sample count in the round that asks for it.  Those a round does not ask for are kept for the later
+    // rounds; they are used only by a round that solves their level to the same delta in the same
+    // precision class, and dropped otherwise.
     struct Ahead {
         bool valid = false;
-        int64_t first = 0;
+        int64_t first = 0;   // the samples first .. first + count - 1 of the level
         int count = 0;
         double df = 0.0, dc = 0.0;
         int cls_f = -1, cls_c = -1;
-        size_t qoff = 0;   // their rows in the ahead buffer: Qf at 2 qoff, Qc at 2 qoff + count (doubles)
+        size_t qf = 0, qc = 0;   // offsets (doubles) of their Qf and Qc rows in the current ahead buffer
         std::vector<int32_t> it_f, it_c, fl_f, fl_c;   // final iterations and flags of each sample
         std::vector<int64_t> abandoned;                // iterations of low-precision attempts retried in FP64
         std::vector<int32_t> retried;
     };
     std::vector<Ahead> ahead(MLMC_MAX_LEVELS);
+    int ahead_buf = 0;   // the ahead buffer holding the entries' rows (the other one receives the next round's)
     // not with fixed sample counts (one round), nor under the calibrated rule (whose precision choice
     // depends on the fields of each round)
     const bool use_ahead = ctx->sample_ahead && !o.fixed_N && !calibrate;
@@ -996,14 +999,17 @@ mlmc_status mlmc_estimate(mlmc_ctx* ctx, const mlmc_options* opts, mlmc_result* 
             const int n = level_n(p, l);
             return ((long long)(n + 1) * (n + 1) + 31) / 32 * 32;
         };
-        // ---- samples of each request already solved ahead (previous round), and new ones to solve ahead
+        // ---- samples of each request already solved ahead (earlier rounds), and new ones to solve ahead;
+        // an entry that does not fit its level's request is dropped
         std::vector<int> used(req.size(), 0);
         for (size_t i = 0; i < req.size(); ++i) {
             const int l = req[i].level;
-            const Ahead& a = ahead[l];
+            Ahead& a = ahead[l];
             if (a.valid && a.first == req[i].first && a.df == df[l] && a.cls_f == class_of(l, l) &&
                 (l == 0 || (a.dc == dc[l] && a.cls_c == class_of(l - 1, l))))
                 used[i] = std::min(req[i].count, a.count);
+            else
+                a.valid = false;
         }
         // the work of the round: what each request still needs, then the samples solved ahead (req < 0)
         struct Work {
@@ -1027,13 +1033,18 @@ mlmc_status mlmc_estimate(mlmc_ctx* ctx, const mlmc_options* opts, mlmc_result* 
             return fixed(n) && (l == 0 || fixed(n / p.m));
         };
         if (use_ahead) {
-            // up to the sample counts of the last estimate, within a tenth of the round's unknowns
+            // up to 1.25 times the sample counts of the last estimate, on the levels where that estimate
+            // went beyond this round's samples (the counts follow sampled variances: with 100 initial
+            // samples they vary by about a tenth between seeds), within a tenth of the round's unknowns
             double budget = 0.0;
             for (const Request& r : req) budget += 0.1 * r.count * unknowns(r.level);
-            for (const Request& r : req) {
+            for (size_t i = 0; i < req.size(); ++i) {
+                const Request& r = req[i];
                 if (!batch_free(r.level)) continue;
-                const int64_t end = r.first + r.count;
-                const int64_t want = ctx->ahead_hint[r.level] - end;
+                // after the samples already held beyond this request
+                const int64_t end = r.first + r.count + (used[i] ? ahead[r.level].count - used[i] : 0);
+                const int64_t hint = ctx->ahead_hint[r.level];
+                const int64_t want = hint > end ? hint + (hint + 3) / 4 - end : 0;
                 const int64_t fit = (int64_t)(budget / unknowns(r.level));
                 const int extra = (int)std::min<int64_t>(std::min(want, fit), 1 << 30);
                 if (extra <= 0) continue;
@@ -1084,11 +1095,11 @@ mlmc_status mlmc_estimate(mlmc_ctx* ctx, const mlmc_options* opts, mlmc_result* 
         for (size_t i = 0; i < req.size(); ++i) {
             if (!used[i]) continue;
             const Ahead& a = ahead[req[i].level];
-            const double* src = ctx->ws.ahead.as<double>() + 2 * a.qoff;
-            MLMC_CUDA_RET(ctx->err, cudaMemcpyAsync(Qf + qoff[i], src, used[i] * sizeof(double),
+            const double* src = ctx->ws.ahead[ahead_buf].as<double>();
+            MLMC_CUDA_RET(ctx->err, cudaMemcpyAsync(Qf + qoff[i], src + a.qf, used[i] * sizeof(double),
                                                     cudaMemcpyDeviceToDevice, st));
             if (req[i].level > 0)
-                MLMC_CUDA_RET(ctx->err, cudaMemcpyAsync(Qc + qoff[i], src + a.count, used[i] * sizeof(double),
+                MLMC_CUDA_RET(ctx->err, cudaMemcpyAsync(Qc + qoff[i], src + a.qc, used[i] * sizeof(double),
                                                         cudaMemcpyDeviceToDevice, st));
         }
         // ---- fields of the work
@@ -1268,41 +1279,81 @@ mlmc_status mlmc_estimate(mlmc_ctx* ctx, const mlmc_options* opts, mlmc_result* 
                 if (l > 0) flags_or |= fc;
             }
         }
-        // ---- keep this round's samples solved ahead for the next round (older ones are dropped)
-        for (Ahead& a : ahead) a.valid = false;
-        size_t an = 0;
-        for (const Work& wk : work)
-            if (wk.req < 0) an += (size_t)wk.count;
-        if (an) {
-            MLMC_CUDA_RET(ctx->err, ctx->ws.ahead.reserve(2 * an * sizeof(double)));
-            double* base = ctx->ws.ahead.as<double>();
-            size_t ao = 0;
-            for (size_t w = 0; w < work.size(); ++w) {
-                const Work& wk = work[w];
-                if (wk.req >= 0) continue;
-                const int l = wk.level;
-                const size_t q0 = wq[w], c = (size_t)wk.count;
-                Ahead& a = ahead[l];
-                a.valid = true;
-                a.first = wk.first;
-                a.count = wk.count;
-                a.df = df[l];
-                a.dc = l > 0 ? dc[l] : 0.0;
-                a.cls_f = class_of(l, l);
-                a.cls_c = l > 0 ? class_of(l - 1, l) : -1;
-                a.qoff = ao;
-                MLMC_CUDA_RET(ctx->err, cudaMemcpyAsync(base + 2 * ao, Qf + q0, c * sizeof(double),
-                                                        cudaMemcpyDeviceToDevice, st));
-                MLMC_CUDA_RET(ctx->err, cudaMemcpyAsync(base + 2 * ao + c, Qc + q0, c * sizeof(double),
-                                                        cudaMemcpyDeviceToDevice, st));
-                a.it_f.assign(hit.begin() + q0, hit.begin() + q0 + c);
-                a.it_c.assign(hit.begin() + qn + q0, hit.begin() + qn + q0 + c);
-                a.fl_f.assign(hit.begin() + 2 * qn + q0, hit.begin() + 2 * qn + q0 + c);
-                a.fl_c.assign(hit.begin() + 3 * qn + q0, hit.begin() + 3 * qn + q0 + c);
-                a.abandoned.assign(abandoned.begin() + q0, abandoned.begin() + q0 + c);
-                a.retried.assign(retried.begin() + q0, retried.begin() + q0 + c);
-                ao += c;
+        // ---- the samples held for later rounds: what is left of the earlier entries after this round's
+        // requests, followed by this round's new samples, laid out afresh in the other ahead buffer
+        {
+            std::vector<int> taken(MLMC_MAX_LEVELS, 0);
+            for (size_t i = 0; i < req.size(); ++i) taken[req[i].level] = used[i];
+            std::vector<int> fresh(MLMC_MAX_LEVELS, -1);   // work item of each level's new samples
+            for (size_t w = 0; w < work.size(); ++w)
+                if (work[w].req < 0) fresh[work[w].level] = (int)w;
+            size_t rows = 0;
+            for (int l = 0; l < MLMC_MAX_LEVELS; ++l) {
+                if (ahead[l].valid) rows += (size_t)(ahead[l].count - taken[l]);
+                if (fresh[l] >= 0) rows += (size_t)work[fresh[l]].count;
             }
+            const int nb = 1 - ahead_buf;
+            if (rows) MLMC_CUDA_RET(ctx->err, ctx->ws.ahead[nb].reserve(2 * rows * sizeof(double)));
+            const double* src = ctx->ws.ahead[ahead_buf].as<double>();
+            double* dst = ctx->ws.ahead[nb].as<double>();
+            size_t ao = 0;
+            auto rows_to = [&](const double* from, size_t c) -> cudaError_t {
+                if (!c) return cudaSuccess;
+                const cudaError_t e = cudaMemcpyAsync(dst + ao, from, c * sizeof(double), cudaMemcpyDeviceToDevice, st);
+                ao += c;
+                return e;
+            };
+            for (int l = 0; l < MLMC_MAX_LEVELS; ++l) {
+                Ahead& a = ahead[l];
+                size_t keep = a.valid ? (size_t)(a.count - taken[l]) : 0;
+                const int w = fresh[l];
+                const size_t add = w >= 0 ? (size_t)work[w].count : 0;
+                // new samples extend held ones only at the same delta and class (else the held ones go)
+                if (keep && add &&
+                    !(a.df == df[l] && a.cls_f == class_of(l, l) &&
+                      (l == 0 || (a.dc == dc[l] && a.cls_c == class_of(l - 1, l)))))
+                    keep = 0;
+                if (keep + add == 0) {
+                    a.valid = false;
+                    continue;
+                }
+                const size_t t = (size_t)taken[l];
+                Ahead b;
+                b.valid = true;
+                b.first = keep ? a.first + (int64_t)t : work[w].first;   // new samples follow held ones
+                b.count = (int)(keep + add);
+                if (keep) {
+                    b.df = a.df, b.dc = a.dc, b.cls_f = a.cls_f, b.cls_c = a.cls_c;
+                } else {
+                    b.df = df[l], b.dc = l > 0 ? dc[l] : 0.0, b.cls_f = class_of(l, l);
+                    b.cls_c = l > 0 ? class_of(l - 1, l) : -1;
+                }
+                auto tail = [&](const auto& v) { return std::decay_t<decltype(v)>(v.begin() + t, v.end()); };
+                b.it_f = keep ? tail(a.it_f) : std::vector<int32_t>();
+                b.it_c = keep ? tail(a.it_c) : std::vector<int32_t>();
+                b.fl_f = keep ? tail(a.fl_f) : std::vector<int32_t>();
+                b.fl_c = keep ? tail(a.fl_c) : std::vector<int32_t>();
+                b.abandoned = keep ? tail(a.abandoned) : std::vector<int64_t>();
+                b.retried = keep ? tail(a.retried) : std::vector<int32_t>();
+                b.qf = ao;
+                if (keep) MLMC_CUDA_RET(ctx->err, rows_to(src + a.qf + t, keep));
+                if (add) MLMC_CUDA_RET(ctx->err, rows_to(Qf + wq[w], add));
+                b.qc = ao;
+                if (keep) MLMC_CUDA_RET(ctx->err, rows_to(src + a.qc + t, keep));
+                if (add) MLMC_CUDA_RET(ctx->err, rows_to(Qc + wq[w], add));
+                if (add) {
+                    const size_t q0 = wq[w];
+                    auto append = [&](auto& v, const auto* from) { v.insert(v.end(), from + q0, from + q0 + add); };
+                    append(b.it_f, hit.data());
+                    append(b.it_c, hit.data() + qn);
+                    append(b.fl_f, hit.data() + 2 * qn);
+                    append(b.fl_c, hit.data() + 3 * qn);
+                    append(b.abandoned, abandoned.data());
+                    append(b.retried, retried.data());
+                }
+                a = std::move(b);
+            }
+            ahead_buf = nb;
         }
         return MLMC_OK;
     };

@@ -101,7 +101,8 @@ struct Workspace {
     DevBuf split;          // split FP16 operands of the tensor-core synthesis
     DevBuf adj;            // adjoint path scratch
     DevBuf chol;           // Cholesky solver: band factors, iterates, descriptors
-    DevBuf ahead;          // estimate loop: QoIs of samples solved ahead of their round (Qf, Qc per level)
+    DevBuf ahead[2];       // estimate loop: QoIs of samples solved ahead of their round (Qf, Qc per level),
+                           // the rows of one round and those of the next
 };
 
 // Profiling state of a context (mlmc_profile_*).
