@@ -1181,9 +1181,11 @@ mlmc_status mlmc_estimate(mlmc_ctx* ctx, const mlmc_options* opts, mlmc_result* 
             b.cfg.chol_ur = b.cfg.chol_u;
             batches.push_back(std::move(b));
         }
+        // the launches are read back with the statistics below: no wait here
+        std::vector<PendingSolve> pend;
         if (!batches.empty()) {
             const NvtxRange range_solves("solves");
-            const mlmc_status s = run_solve_batches(ctx, batches, st);
+            const mlmc_status s = launch_solve_batches(ctx, batches, st, pend);
             if (s != MLMC_OK) return s;
         }
         // ---- read-back: level statistics, iterations and flags of every solve, and the device error words,
@@ -1207,8 +1209,14 @@ mlmc_status mlmc_estimate(mlmc_ctx* ctx, const mlmc_options* opts, mlmc_result* 
             return MLMC_OK;
         };
         {
-            const mlmc_status s = read_back();
-            if (s != MLMC_OK) return s;
+            const mlmc_status s = read_back();   // synchronises st, which waited for every solve launch
+            if (s != MLMC_OK) {
+                cudaStreamSynchronize(st);
+                finish_solves(ctx, pend);
+                return s;
+            }
+            const mlmc_status f = finish_solves(ctx, pend);   // the launches' counters, while profiling
+            if (f != MLMC_OK) return f;
         }
         // iterations of abandoned low-precision attempts and retry counts, per QoI row
         std::vector<int64_t> abandoned(qn, 0);

@@ -289,6 +289,13 @@ struct SolveBatch {
     SolveConfig cfg;
 };
 mlmc_status run_solve_batches(mlmc_ctx* ctx, const std::vector<SolveBatch>& batches, cudaStream_t st);
+// The same launches, returning without waiting: st waits for every batch, and `pend` receives the launches'
+// records, which the caller finishes (finish_solves) once it has synchronised st; the device error words
+// are the caller's to read.  A single batch or Cholesky batches still run to completion.  On a failure
+// every launched batch has been waited for and finished.
+mlmc_status launch_solve_batches(mlmc_ctx* ctx, const std::vector<SolveBatch>& batches, cudaStream_t st,
+                                 std::vector<PendingSolve>& pend);
+mlmc_status finish_solves(mlmc_ctx* ctx, std::vector<PendingSolve>& pend);
 cudaError_t launch_apply_operator(int n, int S, const void* a, int a_fp64, int a_n, int op_prec,
                                   const void* x, void* y, int vec_fp64, cudaStream_t st);
 // stats.cu

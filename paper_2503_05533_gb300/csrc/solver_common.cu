@@ -280,7 +280,19 @@ mlmc_status launch_solve_async(mlmc_ctx* ctx, const std::vector<SolveGroup>& gro
     return launch_batch(ctx, groups, cfg, st, 0, p);
 }
 
-mlmc_status run_solve_batches(mlmc_ctx* ctx, const std::vector<SolveBatch>& batches, cudaStream_t st) {
+mlmc_status finish_solves(mlmc_ctx* ctx, std::vector<PendingSolve>& pend) {
+    mlmc_status status = MLMC_OK;
+    for (PendingSolve& p : pend) {
+        const mlmc_status f = finish_solve(ctx, p);
+        if (status == MLMC_OK) status = f;
+    }
+    pend.clear();
+    return status;
+}
+
+mlmc_status launch_solve_batches(mlmc_ctx* ctx, const std::vector<SolveBatch>& batches, cudaStream_t st,
+                                 std::vector<PendingSolve>& pend) {
+    pend.clear();
     if (batches.size() <= 1) return batches.empty() ? MLMC_OK : run_solve_batch(ctx, batches[0].groups,
                                                                                  batches[0].cfg, st);
     if (batches[0].cfg.solver == MLMC_CHOLESKY) {
@@ -308,7 +320,7 @@ mlmc_status run_solve_batches(mlmc_ctx* ctx, const std::vector<SolveBatch>& batc
     cudaEvent_t fork = nullptr;
     MLMC_CUDA_RET(ctx->err, cudaEventCreateWithFlags(&fork, cudaEventDisableTiming));
     MLMC_CUDA_RET(ctx->err, cudaEventRecord(fork, st));
-    std::vector<PendingSolve> pend(batches.size());
+    pend.resize(batches.size());
     std::vector<cudaEvent_t> done(batches.size(), nullptr);
     mlmc_status status = MLMC_OK;
     for (size_t i = 0; i < batches.size() && status == MLMC_OK; ++i) {
@@ -336,21 +348,31 @@ mlmc_status run_solve_batches(mlmc_ctx* ctx, const std::vector<SolveBatch>& batc
             }
         }
     }
-    // every launched batch is waited for, whatever failed
-    for (size_t i = 1; i < batches.size(); ++i)
-        if (ctx->aux[i - 1]) cudaStreamSynchronize(ctx->aux[i - 1]);
-    const cudaError_t se = cudaStreamSynchronize(st);
+    // (an event may be destroyed while work it waits for is pending: it is released when that completes)
     cudaEventDestroy(fork);
     for (cudaEvent_t e : done)
         if (e) cudaEventDestroy(e);
-    if (status == MLMC_OK && se != cudaSuccess) {
+    if (status != MLMC_OK) {
+        // every launched batch is waited for, whatever failed
+        for (size_t i = 1; i < batches.size(); ++i)
+            if (ctx->aux[i - 1]) cudaStreamSynchronize(ctx->aux[i - 1]);
+        cudaStreamSynchronize(st);
+        finish_solves(ctx, pend);
+    }
+    return status;
+}
+
+mlmc_status run_solve_batches(mlmc_ctx* ctx, const std::vector<SolveBatch>& batches, cudaStream_t st) {
+    std::vector<PendingSolve> pend;
+    mlmc_status status = launch_solve_batches(ctx, batches, st, pend);
+    if (status != MLMC_OK) return status;
+    const cudaError_t se = cudaStreamSynchronize(st);   // st waited for every batch
+    if (se != cudaSuccess) {
         ctx->err = std::string("run_solve_batches: ") + cudaGetErrorString(se);
         status = MLMC_E_CUDA;
     }
-    for (PendingSolve& p : pend) {
-        const mlmc_status f = finish_solve(ctx, p);
-        if (status == MLMC_OK) status = f;
-    }
+    const mlmc_status f = finish_solves(ctx, pend);
+    if (status == MLMC_OK) status = f;
     if (status == MLMC_OK) status = check_device_errors(ctx, st);
     return status;
 }

@@ -151,3 +151,26 @@ def test_samples_solved_ahead_leave_the_estimate_unchanged(M, L_start, form):
     if L_start == 3:
         # the finest level is fixed: the later rounds' samples were all solved in the first round
         assert p2["solve_launches"] < p1["solve_launches"]
+
+
+def test_samples_solved_ahead_for_new_seeds(M):
+    # the counts to solve ahead come from another seed's estimate, so rounds ask for more or fewer samples than
+    # were solved ahead and later rounds take the ones left over; every result equals a fresh context's
+    kw = dict(L_start=3)
+    h = M.mlmc_create(M.make_problem(**WL), 0)
+    got = []
+    try:
+        M.mlmc_estimate(h, _opts(M, **kw))
+        for seed in (WL["seed"] + 1, WL["seed"] + 2, WL["seed"] + 3):
+            M.mlmc_set_seed(h, seed)
+            got.append(M.result_dict(M.mlmc_estimate(h, _opts(M, **kw))))
+    finally:
+        M.mlmc_destroy(h)
+    for k, r in enumerate(got):
+        h = M.mlmc_create(M.make_problem(**dict(WL, seed=WL["seed"] + 1 + k)), 0)
+        try:
+            M.mlmc_set_sample_ahead(h, False)
+            ref = M.result_dict(M.mlmc_estimate(h, _opts(M, **kw)))
+        finally:
+            M.mlmc_destroy(h)
+        assert _same(r, ref)
