@@ -174,3 +174,31 @@ def test_samples_solved_ahead_for_new_seeds(M):
         finally:
             M.mlmc_destroy(h)
         assert _same(r, ref)
+
+
+def test_destroy_returns_the_device_memory(M):
+    # a context that used every workspace (estimate with samples solved ahead, direct solver, adjoint
+    # contraction) gives all of its device memory back on destroy
+    def cycle():
+        h = M.mlmc_create(M.make_problem(**WL), 0)
+        try:
+            M.mlmc_estimate(h, _opts(M, L_start=3))
+            M.mlmc_estimate(h, _opts(M, L_start=3))
+            M.mlmc_estimate(h, _opts(M, L_start=3, solver=M.MLMC_CHOLESKY, form=M.MLMC_FORM_FP64_FIXED,
+                                     fixed_delta=1e-10))
+            xi = torch.zeros((4, WL["K"]), dtype=torch.float64, device=device())
+            Q = torch.empty(4, dtype=torch.float64, device=device())
+            G = torch.empty((4, WL["K"]), dtype=torch.float64, device=device())
+            M.mlmc_adjoint_grad(h, 1, 4, xi, M.MLMC_FP32, 1e-8, 100000, Q, G)
+            torch.cuda.synchronize()
+        finally:
+            M.mlmc_destroy(h)
+        torch.cuda.synchronize()
+
+    cycle()   # first use: the runtime's and the kernels' own one-time allocations
+    torch.cuda.empty_cache()
+    free0 = torch.cuda.mem_get_info()[0]
+    for _ in range(3):
+        cycle()
+    torch.cuda.empty_cache()
+    assert free0 - torch.cuda.mem_get_info()[0] <= 16 << 20
