@@ -49,7 +49,7 @@ L2_FLUSH_BYTES = 512 << 20
 # over the step's launches, from one ncu capture of dram__bytes_read.sum + dram__bytes_write.sum
 # (summary under profiles/).  None whenever the solve kernel or its launch shape has changed since
 # that capture.
-SOLVE_TRAFFIC_BYTES_PER_LAUNCH = 8.61e9
+SOLVE_TRAFFIC_BYTES_PER_LAUNCH = None
 
 
 DESC = ("mixed-precision batched MLMC: 5 levels h=1/16..1/256, KL 64 terms (exp. covariance sigma^2=1, "

@@ -430,6 +430,14 @@ mlmc_status mlmc_set_precond(mlmc_ctx* ctx, mlmc_precond pc, int nu, int coarse_
  * min_cells and 2 min_cells - 1 cells (or is the solve grid itself). */
 mlmc_status mlmc_set_mg_coarsest(mlmc_ctx* ctx, int min_cells);
 
+/* Full-multigrid start of multigrid-preconditioned CG (on = 1, the default; 0
+ * off).  The first inner solve of a refinement (Alg. 2.1: x = 0, r = b) starts
+ * from the nested-iteration guess instead of zero: r restricted down the
+ * V-cycle's hierarchy, the coarsest grid smoothed, and on each finer grid the
+ * prolonged coarser solution improved by one V-cycle.  The inner tolerance and
+ * the FP64 stopping test are unchanged; MINRES and Jacobi-CG start from zero. */
+mlmc_status mlmc_set_full_multigrid(mlmc_ctx* ctx, int on);
+
 /* Working precision u (of the iterate x) and residual precision u_r of the
  * refinement of this context's Cholesky solves (MLMC_CHOLESKY): (u, u_r) one of
  * (MLMC_FP64, MLMC_FP64) (default), (MLMC_FP32, MLMC_FP64), (MLMC_FP32,

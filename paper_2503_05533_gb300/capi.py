@@ -121,6 +121,7 @@ _SIGS = {
     "mlmc_debug_fail_allocation": (c_int, [c_int64]),
     "mlmc_set_seed": (c_int, [c_void_p, c_uint64]),
     "mlmc_set_mg_coarsest": (c_int, [c_void_p, c_int]),
+    "mlmc_set_full_multigrid": (c_int, [c_void_p, c_int]),
     "mlmc_debug_set_medium_items": (c_int, [c_void_p, c_int]),
     "mlmc_set_precond": (c_int, [c_void_p, c_int, c_int, c_int, c_double]),
     "mlmc_set_inner_tolerance": (c_int, [c_void_p, c_double, c_double]),
@@ -207,6 +208,10 @@ def mlmc_set_seed(ctx, seed):
 
 def mlmc_set_mg_coarsest(ctx, min_cells):
     _check(lib().mlmc_set_mg_coarsest(ctx, min_cells), ctx)
+
+
+def mlmc_set_full_multigrid(ctx, on=True):
+    _check(lib().mlmc_set_full_multigrid(ctx, 1 if on else 0), ctx)
 
 
 def mlmc_last_error(ctx=None):

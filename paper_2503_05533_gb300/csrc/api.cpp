@@ -638,6 +638,12 @@ mlmc_status mlmc_set_precond(mlmc_ctx* ctx, mlmc_precond pc, int nu, int coarse_
     return MLMC_OK;
 }
 
+mlmc_status mlmc_set_full_multigrid(mlmc_ctx* ctx, int on) {
+    if (!ctx || (on != 0 && on != 1)) return MLMC_E_ARG;
+    ctx->mg_fmg = on;
+    return MLMC_OK;
+}
+
 mlmc_status mlmc_set_mg_coarsest(mlmc_ctx* ctx, int min_cells) {
     if (!ctx) return MLMC_E_ARG;
     if (min_cells < 2 || min_cells > 64) return fail(ctx, MLMC_E_ARG, "set_mg_coarsest: min_cells in 2..64");

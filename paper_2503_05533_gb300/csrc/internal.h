@@ -144,6 +144,7 @@ struct mlmc_ctx {
     int mg_coarse = 8;            // multigrid: Jacobi sweeps on the coarsest grid
     int mg_min = 4;               // multigrid: grids are halved while the half keeps at least this many cells
     double mg_omega = 0.8;        // multigrid: Jacobi damping
+    int mg_fmg = 1;               // multigrid CG: the first inner solve starts from a full-multigrid guess
     double inner_theta = 0.3;     // inner tolerance tau = clamp(theta delta / rho, tau_min, 0.5)
     double inner_tau_min = -1.0;  // < 0: per-precision default
     mlmc::Profile prof;

@@ -19,7 +19,8 @@
 //   ||r||/||b|| < delta (Eq. (2.1), C = 1); else solve A d = r with CG or MINRES
 //   (Sec. 2.2), preconditioned by a geometric multigrid V-cycle or by Jacobi, in the
 //   inner precision to ||r_k|| <= tau ||r_0||, tau = clamp(theta delta / rho,
-//   tau_min, tau_max); x += d (FP64).
+//   tau_min, tau_max); x += d (FP64).  With the V-cycle, CG's first inner solve
+//   starts from the full-multigrid (nested iteration) guess of d instead of 0.
 // QoI (Problem 4.5): Q = sum_i g_i x_i, g_i = int_B phi_i (B = D: g_i = h^2).
 //
 // Execution: each system is solved start to finish by one group of threads --
@@ -100,6 +101,7 @@ struct Params {
     double mg_omega;         // multigrid: Jacobi damping
     int mg_smem_nmax;        // multigrid: coarse levels of at most this many cells sit in shared memory
     int mg_smem_off;         // ... at this offset of the dynamic shared memory (512-thread groups)
+    int fmg;                 // multigrid CG: the first inner solve starts from a full-multigrid guess
     void* mz;                // multigrid: preconditioned residual z (fine grid)
     void* mt;                // multigrid: fine-grid scratch
     void* cx;                // multigrid: coarse-level iterate, scratch and right-hand side
@@ -1357,6 +1359,80 @@ __device__ VT mg_vcycle(const Params& P, const DevSolve& S, const Group<GT>& G, 
     return rz;
 }
 
+// v = 0 on the interior chunks of level L.
+template <class VT, class ST, int GT>
+__device__ __forceinline__ void mg_zero(const Group<GT>& G, const MGLevel<VT, ST>& L, VT* v) {
+    const int items = (L.n - 1) * L.cpr;
+    const VT z[4] = {(VT)0, (VT)0, (VT)0, (VT)0};
+    for (int it = G.rank; it < items; it += GT) {
+        const int j = 1 + it / L.cpr, c = it - (j - 1) * L.cpr;
+        Vec4<VT>::store(v + (size_t)j * L.ld + 4 * c, z);
+    }
+    G.sync();
+}
+
+// Full-multigrid guess for A d = r (d = 0 on entry): r restricted down the hierarchy, the coarsest grid
+// smoothed from zero, then on each finer grid the prolonged coarser solution improved by one V-cycle (nu
+// sweeps, coarse correction from zero, nu sweeps).  Leaves d in D and r - A d in R.  Level 0 of this
+// hierarchy is (x D, scratch T, right-hand side R); the coarse levels are the V-cycle's.
+// (Not inlined: its own register allocation leaves the solve's sweep loops as they are.)
+template <class VT, class ST, int GT>
+__device__ __noinline__ void mg_fmg(const Params& P, const DevSolve& S, const Group<GT>& G, VT* D, VT* T, VT* R,
+                                    const ST* AS, const ST* DI, uint8_t* cs) {
+    const int nl = S.mg_levels, nu = P.mg_nu;
+    const VT w = (VT)P.mg_omega;
+    for (int k = 0; k < nl; ++k) {
+        MGLevel<VT, ST> F = mg_level<VT, ST>(P, S, k, D, T, R, AS, DI, cs);
+        F.t = F.b;   // restrict the right-hand side itself
+        mg_restrict<VT, ST, GT>(G, F, mg_level<VT, ST>(P, S, k + 1, D, T, R, AS, DI, cs));
+    }
+    mg_sweeps_from_zero<VT, ST, GT>(G, mg_level<VT, ST>(P, S, nl, D, T, R, AS, DI, cs), P.mg_coarse, w);
+    for (int k = nl - 1; k >= 0; --k) {
+        MGLevel<VT, ST> L = mg_level<VT, ST>(P, S, k, D, T, R, AS, DI, cs);
+        if (k > 0) mg_zero<VT, ST, GT>(G, L, L.x);
+        mg_prolong<VT, ST, GT>(G, mg_level<VT, ST>(P, S, k + 1, D, T, R, AS, DI, cs), L, L.x);
+        // nu sweeps from the prolonged guess, alternating x and t (the iterate is in L.x after each pair)
+        for (int s = 0; s < nu; ++s) {
+            mg_smooth<VT, ST, GT, false>(G, L, L.x, L.t, w);
+            VT* q = L.x;
+            L.x = L.t;
+            L.t = q;
+        }
+        mg_residual<VT, ST, GT>(G, L);
+        mg_restrict<VT, ST, GT>(G, L, mg_level<VT, ST>(P, S, k + 1, D, T, R, AS, DI, cs));
+        // coarse correction from zero on levels k + 1 .. nl (the V-cycle's descent and ascent)
+        for (int j = k + 1; j < nl; ++j) {
+            const MGLevel<VT, ST> C = mg_level<VT, ST>(P, S, j, D, T, R, AS, DI, cs);
+            mg_sweeps_from_zero<VT, ST, GT>(G, C, nu, w);
+            mg_residual<VT, ST, GT>(G, C);
+            mg_restrict<VT, ST, GT>(G, C, mg_level<VT, ST>(P, S, j + 1, D, T, R, AS, DI, cs));
+        }
+        mg_sweeps_from_zero<VT, ST, GT>(G, mg_level<VT, ST>(P, S, nl, D, T, R, AS, DI, cs), P.mg_coarse, w);
+        for (int j = nl - 1; j > k; --j) {
+            const MGLevel<VT, ST> C = mg_level<VT, ST>(P, S, j, D, T, R, AS, DI, cs);
+            VT* corr = (nu % 2) ? C.t : C.x;
+            mg_prolong<VT, ST, GT>(G, mg_level<VT, ST>(P, S, j + 1, D, T, R, AS, DI, cs), C, corr);
+            const VT* in = corr;
+            for (int s = 1; s <= nu; ++s) {
+                VT* out = ((nu - s) % 2 == 0) ? C.x : C.t;
+                mg_smooth<VT, ST, GT, false>(G, C, in, out, w);
+                in = out;
+            }
+        }
+        mg_prolong<VT, ST, GT>(G, mg_level<VT, ST>(P, S, k + 1, D, T, R, AS, DI, cs), L, L.x);
+        for (int s = 0; s < nu; ++s) {
+            mg_smooth<VT, ST, GT, false>(G, L, L.x, L.t, w);
+            VT* q = L.x;
+            L.x = L.t;
+            L.t = q;
+        }
+    }
+    // r = r - A d (in place: each chunk reads its own r before writing it)
+    MGLevel<VT, ST> L0 = mg_level<VT, ST>(P, S, 0, D, T, R, AS, DI, cs);
+    L0.t = L0.b;
+    mg_residual<VT, ST, GT>(G, L0);
+}
+
 // One system, start to finish: set-up, refinement loop with the inner PCG, QoI.
 // `pipe` is non-null for a 512-thread CG group whose sweeps stream rows
 // through shared memory.
@@ -1523,6 +1599,13 @@ __device__ void solve_system(const Params& P, const DevSolve& S, const Group<GT>
         if (o >= 1 && rho > P.stag * rho_prev) { flag = MLMC_F_STAGNATED; break; }
         rho_prev = rho;
         const double tau = inner_tau(P, S, rho);
+        if constexpr (!minres) {
+            // the first inner solve starts from a full-multigrid guess (d and r replaced)
+            if (mg && P.fmg && o == 0 && S.mg_levels > 0) {
+                mg_fmg<VT, ST, GT>(P, S, G, D, MT, R, AS, DI, cs);
+                if (pipe_on) fence_proxy_async_global();
+            }
+        }
 
         int k = 0;
         if (minres) {
@@ -1900,6 +1983,27 @@ double mg_iter_flops(int n, int nl, int nu, int ncs, double s0) {
     return fl + 2.0 * (double)(n - 1) * (n - 1);
 }
 
+// The full-multigrid start (mg_fmg), once per solve: the right-hand side restricted down the hierarchy
+// (2 p_v per coarse unknown), the coarsest sweeps, and on each finer level k the guess cleared (k > 0) and
+// prolonged (3 p_v per unknown) and a V-cycle of levels k .. nl from it (counted as one from zero), then
+// the fine residual r - A d (3 p_v + p_s per unknown).
+double mg_fmg_bytes(int n, int nl, int nu, int ncs, double pv, double ps) {
+    auto unk = [&](int k) { return (double)((n >> k) - 1) * ((n >> k) - 1); };
+    double b = unk(nl) * ((2 * pv + ps) + (ncs - 1) * (3 * pv + 2 * ps)) + unk(0) * (3 * pv + ps);
+    for (int k = 0; k < nl; ++k)
+        b += unk(k + 1) * 2 * pv + unk(k) * (k > 0 ? 3 : 2) * pv + mg_iter_bytes(n >> k, nl - k, nu, ncs, pv, ps);
+    return b;
+}
+// Its operations: restriction 8 per coarse unknown, the coarsest sweeps, per finer level the prolongation
+// (2 per unknown) and a V-cycle, and the fine residual (a stencil plus 1).
+double mg_fmg_flops(int n, int nl, int nu, int ncs, double s0) {
+    auto unk = [&](int k) { return (double)((n >> k) - 1) * ((n >> k) - 1); };
+    double f = unk(nl) * (2.0 + (ncs - 1) * (kFlopStencil + 4.0)) + unk(0) * (s0 + 1.0);
+    for (int k = 0; k < nl; ++k)
+        f += unk(k + 1) * 8.0 + unk(k) * 2.0 + mg_iter_flops(n >> k, nl - k, nu, ncs, k == 0 ? s0 : kFlopStencil);
+    return f;
+}
+
 // Workspace of a batch: vectors, coefficient storage, descriptors, launch order.
 struct Layout {
     size_t o_x, o_r, o_p0, o_p1, o_d, o_as, o_dinv, o_vb, o_w0, o_w1, o_mz, o_mt, o_cx, o_ct, o_cb, o_cas, o_cdi,
@@ -2193,6 +2297,7 @@ mlmc_status launch_typed(mlmc_ctx* ctx, const std::vector<SolveGroup>& groups, c
         P.mg_nu = cfg.nu > 0 ? cfg.nu : ctx->mg_nu;
         P.mg_coarse = cfg.mg_coarse > 0 ? cfg.mg_coarse : ctx->mg_coarse;
         P.mg_omega = cfg.mg_omega > 0 ? cfg.mg_omega : ctx->mg_omega;
+        P.fmg = ctx->mg_fmg;
     }
     size_t smem = 0;
     if (cfg.solver == MLMC_CG) {
@@ -2263,7 +2368,9 @@ mlmc_status launch_typed(mlmc_ctx* ctx, const std::vector<SolveGroup>& groups, c
             // the weights written
             out.c_res.push_back(unk * (8 + 16 + 2 * pv + pd));
             out.c_upd.push_back(unk * (16 + pv));
-            out.c_set.push_back(unk * (8 + pm + ps + pd + 16));
+            const bool fmg = mg && P.fmg && cfg.solver == MLMC_CG && d.mg_levels > 0;
+            out.c_set.push_back(unk * (8 + pm + ps + pd + 16) +
+                                (fmg ? mg_fmg_bytes(d.n, d.mg_levels, P.mg_nu, P.mg_coarse, pv, ps) : 0.0));
             // operations: per inner iteration two stencil sweeps with their recurrences and dots, plus
             // the V-cycle (CG: 12 + 2 S with Jacobi, 10 + 2 S with multigrid; MINRES: 18 + 2 S and
             // 17 + 2 S); per refinement step the FP64 residual from the stored weights with its three
@@ -2276,7 +2383,8 @@ mlmc_status launch_typed(mlmc_ctx* ctx, const std::vector<SolveGroup>& groups, c
             out.f_it.push_back(unk * fit);
             out.f_res.push_back(unk * 20.0);
             out.f_upd.push_back(unk * 1.0);
-            out.f_set.push_back(unk * (8.0 + 21.0 + (mg ? 7.0 : 0.0) + 2.0));
+            out.f_set.push_back(unk * (8.0 + 21.0 + (mg ? 7.0 : 0.0) + 2.0) +
+                                (fmg ? mg_fmg_flops(d.n, d.mg_levels, P.mg_nu, P.mg_coarse, S_) : 0.0));
         }
     }
     return MLMC_OK;
