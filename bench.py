@@ -47,9 +47,10 @@ SEED = 1000          # Philox key of the timed estimate (rank r uses SEED + r)
 L2_FLUSH_BYTES = 512 << 20
 # DRAM bytes (read + write) per resident_solve launch of one timed step of this workload, averaged
 # over the step's launches, from one ncu capture of dram__bytes_read.sum + dram__bytes_write.sum
-# (summary under profiles/).  None whenever the solve kernel or its launch shape has changed since
-# that capture.
-SOLVE_TRAFFIC_BYTES_PER_LAUNCH = None
+# (summary under profiles/; taken with the library's fixed launch settings, since under ncu the
+# autotuner times serialised trials and picks other ones).  None whenever the solve kernel or its
+# launch shape has changed since that capture.
+SOLVE_TRAFFIC_BYTES_PER_LAUNCH = 7.38e9
 
 
 DESC = ("mixed-precision batched MLMC: 5 levels h=1/16..1/256, KL 64 terms (exp. covariance sigma^2=1, "
